@@ -1,0 +1,170 @@
+/*
+ * icgs.h -- C ABI of the GB300-native instant-colorization library (libicgs.so).
+ *
+ * The library computes, for a fixed Gaussian-splat scene and a set of calibrated target images,
+ * the per-Gaussian spherical-harmonic coefficients of the visibility-weighted least-squares problem
+ * of arXiv 2604.17155 (Sec. 3, Eq. 10-15, Alg. 1 lines 1-6):
+ *
+ *     c_i = (G_i + w_i Lambda)^-1 b_i,   G_i = sum_j V_i^j Y_ij Y_ij^T,   b_i = sum_j Y_ij S_ij^T,
+ *     w_i = sum_j V_i^j,  V_i^j = sum_{x,y} alpha_i T_i,  S_ij^k = sum_{x,y} alpha_i T_i t^{j,k}_{x,y},
+ *
+ * where alpha_i T_i is the front-to-back blend weight of Gaussian i in pixel (x,y) of camera j
+ * (Eq. 2, Eq. 4) and Y_ij is the real SH basis (Eq. 3) at the direction from camera j's centre to
+ * Gaussian i's mean (Sec. 3, below Eq. 9). It also renders (Eq. 1-3) and differentiates the
+ * coefficients with respect to the target images and the opacities.
+ *
+ * Rendering conventions (the paper renders "following Kerbl et al."; these are the 3DGS ones):
+ *   - camera: pinhole, looks down +z, image y axis down, world_to_cam = row-major [R|t]; pixel
+ *     (x,y) has its centre at (x+0.5, y+0.5); Gaussians with camera-space z <= near_z are culled;
+ *   - 2D covariance J W Sigma W^T J^T + 0.3 I, Jacobian taken at the mean with x/z, y/z clamped to
+ *     1.3 * (width/2)/fx, 1.3 * (height/2)/fy;
+ *   - alpha = min(0.99, opacity * exp(-q/2)); pairs with alpha < 1/255 are skipped; the walk of a
+ *     pixel stops before the first Gaussian that would bring T below 1e-4;
+ *   - depth order: ascending float32(z), z evaluated in double as ((W20 x + W21 y) + W22 z) + W23
+ *     with no fused multiply-add; equal keys in ascending Gaussian index;
+ *   - SH: real orthonormal harmonics, index l*l+l+m (m = -l..l), degree 1 = sqrt(3/(4 pi))*(y,z,x);
+ *     no 0.5 colour offset and no clamp (Eq. 3 is linear).
+ *
+ * Memory and threading:
+ *   - Pointers named "device" are CUDA device pointers owned by the caller; "host" pointers are
+ *     read during the call only. The library never allocates device memory: every call takes a
+ *     caller-owned workspace of at least the size returned by the matching *_workspace_size call.
+ *   - All work is enqueued on `stream` (a cudaStream_t, NULL = legacy default stream). Each call
+ *     ends by copying a small status block back to the host and synchronising `stream`, so results
+ *     are complete when the call returns ICGS_OK.
+ *   - Calls on different streams with different workspaces may run concurrently.
+ *   - On error the call returns a negative icgs_status; icgs_last_error() gives a message (per host
+ *     thread). Outputs are then unspecified.
+ */
+#ifndef ICGS_H
+#define ICGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ICGS_API __attribute__((visibility("default")))
+#else
+#define ICGS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ICGS_OK = 0,
+  ICGS_ERR_INVALID_ARG = -1,          /* bad shape, pointer, degree, dtype or option */
+  ICGS_ERR_WORKSPACE_TOO_SMALL = -2,  /* workspace_bytes below the *_workspace_size result */
+  ICGS_ERR_CUDA = -3,                 /* a CUDA runtime call failed (message has the CUDA error) */
+  ICGS_ERR_CAPACITY = -4,             /* more (Gaussian, tile) instances than the workspace was sized
+                                         for; icgs_last_required_instances() gives the count to pass
+                                         as icgs_options.instance_capacity */
+  ICGS_ERR_UNSUPPORTED = -5           /* valid request this build does not implement */
+} icgs_status;
+
+typedef enum { ICGS_F32 = 0, ICGS_BF16 = 1, ICGS_F16 = 2 } icgs_dtype;
+
+typedef enum {
+  ICGS_PRECISION_PLAIN = 0, /* FP32 weights, CUDA-core contraction, plain FP32 fold and Cholesky */
+  ICGS_PRECISION_MIXED = 1  /* compensated FP32 fold, FP32 Cholesky with FP64 for Gaussians whose
+                               pivot ratio falls below cond_tau; 16-bit targets with >= 16
+                               channels contract on tcgen05 tensor cores (BF16/FP16 in, FP32 acc) */
+} icgs_precision;
+
+/* Per-Gaussian status written to status_out. */
+enum { ICGS_GAUSSIAN_OK = 0, ICGS_GAUSSIAN_UNSEEN = 1, ICGS_GAUSSIAN_FP64 = 2 };
+
+/* The fixed scene (Alg. 1 "Data": Gaussian means and covariances; Sec. 3 Eq. 1). All device,
+ * float32, contiguous. quats are (w,x,y,z) and are normalised inside; scales are linear (> 0). */
+typedef struct {
+  int64_t n;
+  const float* means;    /* device [n,3] */
+  const float* scales;   /* device [n,3] */
+  const float* quats;    /* device [n,4] */
+  const float* opacity;  /* device [n], in (0,1) */
+} icgs_scene;
+
+/* Calibrated cameras P_j (Alg. 1 "Data": camera poses). All cameras share one image size. */
+typedef struct {
+  int32_t n_cams;
+  int32_t width, height;
+  float near_z;                /* <= 0 selects 0.2 */
+  const float* intrinsics;     /* host [n_cams,4]: fx, fy, cx, cy (pixels) */
+  const float* world_to_cam;   /* host [n_cams,12]: row-major 3x4 [R|t] */
+} icgs_cameras;
+
+/* Target images t^{j,k}_{x,y} (Alg. 1 "Data": GT images; Sec. 3: any number of channels). */
+typedef struct {
+  icgs_dtype dtype;
+  int32_t channels;            /* K >= 1 */
+  const void* data;            /* device [n_cams,height,width,channels], contiguous */
+} icgs_targets;
+
+typedef struct {
+  int32_t sh_degree;           /* L in 0..3; (L+1)^2 coefficients per channel */
+  const float* lambda;         /* host [(L+1)^2] Tikhonov weights lambda_m (Eq. 14); NULL selects
+                                  the paper's values (Sec. 4): 1e-5 / 1e-4 / 1e-3 / 1e-2 per band */
+  int32_t precision;           /* icgs_precision */
+  float cond_tau;              /* MIXED: FP64 refactorisation when min_k pivot_k / A_kk < cond_tau;
+                                  <= 0 selects 1e-3 */
+  int32_t cam_batch;           /* cameras accumulated per pass; <= 0 selects min(n_cams, 128) */
+  int64_t instance_capacity;   /* (Gaussian, tile) instances per pass the workspace holds; <= 0
+                                  selects an estimate (see ICGS_ERR_CAPACITY) */
+} icgs_options;
+
+/* Bytes of workspace icgs_colorize / icgs_colorize_backward need for these arguments. */
+ICGS_API size_t icgs_workspace_size(const icgs_scene* scene, const icgs_cameras* cams,
+                           const icgs_targets* targets, const icgs_options* opt);
+
+/* Colorize (Alg. 1 lines 1-6, Eq. 14). Writes
+ *   coeffs_out  device [n,(L+1)^2,K] float32: c_i (zero for Gaussians no pixel sees),
+ *   status_out  device [n] uint8 (nullable): ICGS_GAUSSIAN_{OK,UNSEEN,FP64},
+ *   chol_out    device [n,(L+1)^2((L+1)^2+1)/2] float32 (nullable): row-packed lower Cholesky
+ *               factor of A_i = G_i + w_i Lambda (rows 0..B-1, row r holds L_r0..L_rr), which
+ *               icgs_colorize_backward takes. */
+ICGS_API icgs_status icgs_colorize(const icgs_scene* scene, const icgs_cameras* cams,
+                          const icgs_targets* targets, const icgs_options* opt,
+                          void* workspace, size_t workspace_bytes,
+                          float* coeffs_out, uint8_t* status_out, float* chol_out, void* stream);
+
+/* Adjoint of icgs_colorize for a loss L(c): given dL/dc (grad_coeffs, device [n,(L+1)^2,K]),
+ * the coefficients and Cholesky factors returned by icgs_colorize on the same inputs, writes
+ *   grad_targets  device [n_cams,height,width,K] float32 (nullable): dL/dt,
+ *   grad_opacity  device [n] float32 (nullable): dL/d(opacity) (overwritten, not accumulated).
+ * The blend lists are recomputed, not stored. With u_i = A_i^-1 dL/dc_i: dL/dS_ij = Y_ij^T u_i,
+ * dL/dV_ij = -sum_k u_ik^T (Y_ij Y_ij^T + Lambda) c_ik, and the per-pixel walk applies
+ * d(alpha_m T_m)/d(alpha_n) (Eq. 2). Threshold decisions (alpha >= 1/255, the T stop, the 0.99 cap)
+ * are held fixed, as in any rasterizer's gradient. */
+ICGS_API icgs_status icgs_colorize_backward(const icgs_scene* scene, const icgs_cameras* cams,
+                                   const icgs_targets* targets, const icgs_options* opt,
+                                   const float* coeffs, const float* chol, const float* grad_coeffs,
+                                   void* workspace, size_t workspace_bytes,
+                                   float* grad_targets, float* grad_opacity, void* stream);
+
+/* Bytes of workspace icgs_render needs. */
+ICGS_API size_t icgs_render_workspace_size(const icgs_scene* scene, const icgs_cameras* cams,
+                                  int32_t sh_degree, int32_t channels, int64_t instance_capacity);
+
+/* Render (Eq. 1-3): images_out device [n_cams,height,width,channels] float32 from coeffs device
+ * [n,(L+1)^2,channels]; background 0. */
+ICGS_API icgs_status icgs_render(const icgs_scene* scene, const icgs_cameras* cams, int32_t sh_degree,
+                        int32_t channels, const float* coeffs, int64_t instance_capacity,
+                        void* workspace, size_t workspace_bytes, float* images_out, void* stream);
+
+/* Message of the last failed call on this host thread ("" if none). */
+ICGS_API const char* icgs_last_error(void);
+
+/* (Gaussian, tile) instances the last call on this host thread needed in its largest pass. */
+ICGS_API int64_t icgs_last_required_instances(void);
+
+/* Per-pass statistics of the last successful call on this host thread, for benchmarks:
+ * out[0] = instances, out[1] = blend pairs evaluated (pixel x list entry, before early stop)
+ * -- both summed over passes --, out[2] = Gaussians solved in FP64. */
+ICGS_API void icgs_last_stats(int64_t out[3]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ICGS_H */

@@ -1,0 +1,371 @@
+// api.cu -- the C ABI declared in include/icgs.h: argument checks, workspace layout and the
+// sequence of kernel launches for colorize (Alg. 1 lines 1-6), its adjoint, and render.
+//
+// One call processes the cameras in passes of cam_batch cameras. Per pass: project + count
+// (k_project), exclusive scan of tile counts, scatter of (depth key, index) into tile slots, per-tile
+// depth sort, then the walk (accumulate / render / adjoint). For L > 0 a fold turns the pass's
+// per-(camera, Gaussian) sums V and S into the normal equations; for L = 0 the walk accumulates
+// straight into one [n, 1+K] array. The call ends with one device->host copy of the status block
+// and a stream synchronisation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/icgs.h"
+#include "icgs_internal.h"
+
+using namespace icgs;
+
+namespace {
+
+thread_local char g_err[1024] = "";
+thread_local int64_t g_required = 0;
+thread_local int64_t g_stats[3] = {0, 0, 0};
+
+icgs_status fail(icgs_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+#define ICGS_TRY_CUDA(expr)                                                                  \
+  do {                                                                                       \
+    cudaError_t e_ = (expr);                                                                 \
+    if (e_ != cudaSuccess) return fail(ICGS_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr int kNeedAccumulate = 1, kNeedBackward = 2, kNeedRender = 4;
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Lays the regions out from `base` (or only sizes them when base is null).
+Workspace carve(char* base, const Problem& p, int need) {
+  Workspace ws;
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* ptr = base ? base + off : nullptr;
+    off += align256(bytes);
+    return ptr;
+  };
+  const int64_t cbn = (int64_t)p.cam_batch * p.n;
+  const int64_t ct = (int64_t)p.cam_batch * p.tiles;
+  ws.base = base;
+  ws.status = reinterpret_cast<DevStatus*>(take(sizeof(DevStatus)));
+  ws.cams = reinterpret_cast<DevCam*>(take(sizeof(DevCam) * (size_t)p.n_cams));
+  ws.lam = reinterpret_cast<float*>(take(sizeof(float) * kMaxSH));
+  ws.rec = reinterpret_cast<ProjRec*>(take(sizeof(ProjRec) * (size_t)cbn));
+  ws.rect = reinterpret_cast<uint2*>(take(sizeof(uint2) * (size_t)cbn));
+  ws.tile_off = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (size_t)(ct + 1)));
+  ws.tile_cur = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (size_t)ct));
+  ws.scan_tmp = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (size_t)(ct / 1024 + 2)));
+  ws.big_list = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (size_t)ct));
+  ws.entries = reinterpret_cast<uint64_t*>(take(sizeof(uint64_t) * (size_t)p.capacity));
+  ws.entries_tmp = reinterpret_cast<uint64_t*>(take(sizeof(uint64_t) * (size_t)p.capacity));
+  const size_t B = (size_t)p.B, K = (size_t)p.K, n = (size_t)p.n;
+  if (need & kNeedAccumulate) {
+    ws.acc = reinterpret_cast<float*>(take(sizeof(float) * (p.L == 0 ? n : (size_t)cbn) * (1 + K)));
+    if (p.L > 0) {
+      const bool mixed = p.precision == ICGS_PRECISION_MIXED;
+      ws.G = reinterpret_cast<float*>(take(sizeof(float) * n * B * B));
+      ws.bvec = reinterpret_cast<float*>(take(sizeof(float) * n * B * K));
+      ws.wsum = reinterpret_cast<float*>(take(sizeof(float) * n));
+      if (mixed) {
+        ws.Glo = reinterpret_cast<float*>(take(sizeof(float) * n * B * B));
+        ws.blo = reinterpret_cast<float*>(take(sizeof(float) * n * B * K));
+        ws.wlo = reinterpret_cast<float*>(take(sizeof(float) * n));
+      }
+    }
+  }
+  if (need & kNeedBackward) {
+    ws.payload = reinterpret_cast<float*>(take(sizeof(float) * (size_t)cbn * (K + 1)));
+    ws.u = reinterpret_cast<float*>(take(sizeof(float) * n * B * K));
+    ws.reg = reinterpret_cast<float*>(take(sizeof(float) * n));
+  } else if (need & kNeedRender) {
+    ws.payload = reinterpret_cast<float*>(take(sizeof(float) * (size_t)cbn * K));
+  }
+  ws.total = off;
+  ws.bytes = off;
+  return ws;
+}
+
+bool finite_all(const float* v, size_t m) {
+  for (size_t i = 0; i < m; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+icgs_status setup(const icgs_scene* sc, const icgs_cameras* cams, int K, int L, int precision,
+                  float cond_tau, int cam_batch, int64_t capacity, Problem& p) {
+  if (!sc || !cams) return fail(ICGS_ERR_INVALID_ARG, "scene and cameras must not be NULL");
+  if (sc->n < 0 || sc->n > 0x7FFFFFFF) return fail(ICGS_ERR_INVALID_ARG, "scene.n = %lld out of range", (long long)sc->n);
+  if (sc->n > 0 && (!sc->means || !sc->scales || !sc->quats || !sc->opacity))
+    return fail(ICGS_ERR_INVALID_ARG, "scene arrays must not be NULL");
+  if (cams->n_cams < 1) return fail(ICGS_ERR_INVALID_ARG, "n_cams = %d must be >= 1", cams->n_cams);
+  if (cams->width < 1 || cams->height < 1 || cams->width > 65535 * kTile || cams->height > 65535 * kTile)
+    return fail(ICGS_ERR_INVALID_ARG, "image size %dx%d out of range", cams->width, cams->height);
+  if (!cams->intrinsics || !cams->world_to_cam) return fail(ICGS_ERR_INVALID_ARG, "camera arrays must not be NULL");
+  if (!finite_all(cams->intrinsics, 4 * (size_t)cams->n_cams) || !finite_all(cams->world_to_cam, 12 * (size_t)cams->n_cams))
+    return fail(ICGS_ERR_INVALID_ARG, "camera parameters must be finite");
+  for (int j = 0; j < cams->n_cams; ++j)
+    if (!(cams->intrinsics[4 * j] > 0.0f) || !(cams->intrinsics[4 * j + 1] > 0.0f))
+      return fail(ICGS_ERR_INVALID_ARG, "camera %d: focal lengths must be > 0", j);
+  if (K < 1) return fail(ICGS_ERR_INVALID_ARG, "channels = %d must be >= 1", K);
+  if (L < 0 || L > 3) return fail(ICGS_ERR_INVALID_ARG, "sh_degree = %d must be in 0..3", L);
+  if (precision != ICGS_PRECISION_PLAIN && precision != ICGS_PRECISION_MIXED)
+    return fail(ICGS_ERR_INVALID_ARG, "precision = %d is not an icgs_precision", precision);
+  p.n = sc->n;
+  p.n_cams = cams->n_cams;
+  p.width = cams->width;
+  p.height = cams->height;
+  p.near_z = cams->near_z > 0.0f ? cams->near_z : 0.2f;
+  p.tiles_x = (p.width + kTile - 1) / kTile;
+  p.tiles_y = (p.height + kTile - 1) / kTile;
+  p.tiles = p.tiles_x * p.tiles_y;
+  p.K = K;
+  p.L = L;
+  p.B = (L + 1) * (L + 1);
+  p.precision = precision;
+  p.cond_tau = cond_tau > 0.0f ? cond_tau : 1e-3f;
+  p.cam_batch = cam_batch > 0 ? std::min(cam_batch, p.n_cams) : std::min(p.n_cams, 128);
+  p.cam_batch = std::min(p.cam_batch, 65535);  // grid y dimension of the per-pair kernels
+  if ((int64_t)p.cam_batch * p.tiles > 0x7FFFFFFFll)
+    return fail(ICGS_ERR_INVALID_ARG, "cam_batch x tiles too large; lower cam_batch");
+  int64_t cap = capacity > 0 ? capacity : 6 * (int64_t)p.n * p.cam_batch + (1 << 16);
+  p.capacity = (uint32_t)std::min<int64_t>(cap, kMaxCapacity);
+  return ICGS_OK;
+}
+
+std::vector<DevCam> build_cams(const icgs_cameras* cams) {
+  std::vector<DevCam> out((size_t)cams->n_cams);
+  for (int j = 0; j < cams->n_cams; ++j) {
+    DevCam& c = out[(size_t)j];
+    std::memset(&c, 0, sizeof c);
+    const float* in = cams->intrinsics + 4 * j;
+    const float* w = cams->world_to_cam + 12 * j;
+    c.fx = in[0]; c.fy = in[1]; c.cx = in[2]; c.cy = in[3];
+    for (int k = 0; k < 12; ++k) c.w[k] = w[k];
+    for (int a = 0; a < 3; ++a) {  // centre = -R^T t
+      double s = 0.0;
+      for (int r = 0; r < 3; ++r) s -= (double)w[4 * r + a] * (double)w[4 * r + 3];
+      c.centre[a] = (float)s;
+    }
+    c.limx = (float)(1.3 * ((double)cams->width / (2.0 * (double)in[0])));
+    c.limy = (float)(1.3 * ((double)cams->height / (2.0 * (double)in[1])));
+  }
+  return out;
+}
+
+void default_lambda(int L, float* lam) {
+  const float band[4] = {1e-5f, 1e-4f, 1e-3f, 1e-2f};  // Sec. 4, Implementation Details
+  for (int l = 0; l <= L; ++l)
+    for (int m = -l; m <= l; ++m) lam[l * l + l + m] = band[l];
+}
+
+icgs_status upload_common(const Problem& p, const icgs_cameras* cams, const float* lam_host,
+                          const Workspace& ws, cudaStream_t s) {
+  const std::vector<DevCam> dc = build_cams(cams);
+  ICGS_TRY_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(DevStatus), s));
+  ICGS_TRY_CUDA(cudaMemcpyAsync(ws.cams, dc.data(), sizeof(DevCam) * dc.size(), cudaMemcpyHostToDevice, s));
+  if (lam_host) ICGS_TRY_CUDA(cudaMemcpyAsync(ws.lam, lam_host, sizeof(float) * p.B, cudaMemcpyHostToDevice, s));
+  // pageable copies are staged before they return, so dc may go out of scope now
+  return ICGS_OK;
+}
+
+icgs_status bin_pass(const Problem& p, const icgs_scene* sc, int cb, const Workspace& wp, cudaStream_t s) {
+  const int64_t ct = (int64_t)cb * p.tiles;
+  ICGS_TRY_CUDA(cudaMemsetAsync(wp.tile_off, 0, sizeof(uint32_t) * (size_t)(ct + 1), s));
+  ICGS_TRY_CUDA(cudaMemsetAsync(wp.tile_cur, 0, sizeof(uint32_t) * (size_t)ct, s));
+  launch_project(p, sc->means, sc->scales, sc->quats, sc->opacity, cb, wp, s);
+  launch_scan(p, cb, wp, s);
+  launch_scatter(p, cb, wp, s);
+  launch_tile_sort(p, cb, wp, s);
+  return ICGS_OK;
+}
+
+icgs_status finish(const Workspace& ws, cudaStream_t s) {
+  ICGS_TRY_CUDA(cudaGetLastError());
+  DevStatus st;
+  ICGS_TRY_CUDA(cudaMemcpyAsync(&st, ws.status, sizeof st, cudaMemcpyDeviceToHost, s));
+  ICGS_TRY_CUDA(cudaStreamSynchronize(s));
+  g_required = (int64_t)st.instances_needed;
+  if (st.flags & kFlagOverflow)
+    return fail(ICGS_ERR_CAPACITY, "a pass needed %lld (Gaussian, tile) instances; pass at least that as "
+                "icgs_options.instance_capacity", (long long)st.instances_needed);
+  g_stats[0] = (int64_t)st.instances_total;
+  g_stats[1] = (int64_t)st.contrib_pairs;
+  g_stats[2] = (int64_t)st.fp64_count;
+  return ICGS_OK;
+}
+
+icgs_status check_targets(const icgs_targets* t) {
+  if (!t || !t->data) return fail(ICGS_ERR_INVALID_ARG, "targets must not be NULL");
+  if (t->dtype != ICGS_F32 && t->dtype != ICGS_BF16 && t->dtype != ICGS_F16)
+    return fail(ICGS_ERR_INVALID_ARG, "targets.dtype = %d is not an icgs_dtype", (int)t->dtype);
+  if (t->channels < 1) return fail(ICGS_ERR_INVALID_ARG, "targets.channels = %d must be >= 1", t->channels);
+  return ICGS_OK;
+}
+
+icgs_status lambda_of(const icgs_options* opt, int L, float* lam) {
+  const int B = (L + 1) * (L + 1);
+  if (opt && opt->lambda) {
+    for (int m = 0; m < B; ++m) {
+      lam[m] = opt->lambda[m];
+      if (!(lam[m] >= 0.0f) || !std::isfinite(lam[m]))
+        return fail(ICGS_ERR_INVALID_ARG, "lambda[%d] must be finite and >= 0", m);
+    }
+  } else {
+    default_lambda(L, lam);
+  }
+  return ICGS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t icgs_workspace_size(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
+                           const icgs_options* opt) {
+  if (!targets || !opt) return 0;
+  Problem p;
+  if (setup(scene, cams, targets->channels, opt->sh_degree, opt->precision, opt->cond_tau, opt->cam_batch,
+            opt->instance_capacity, p) != ICGS_OK)
+    return 0;
+  return carve(nullptr, p, kNeedAccumulate | kNeedBackward).total;
+}
+
+icgs_status icgs_colorize(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
+                          const icgs_options* opt, void* workspace, size_t workspace_bytes, float* coeffs_out,
+                          uint8_t* status_out, float* chol_out, void* stream) {
+  g_err[0] = '\0';
+  if (!opt) return fail(ICGS_ERR_INVALID_ARG, "options must not be NULL");
+  icgs_status st = check_targets(targets);
+  if (st != ICGS_OK) return st;
+  Problem p;
+  st = setup(scene, cams, targets->channels, opt->sh_degree, opt->precision, opt->cond_tau, opt->cam_batch,
+             opt->instance_capacity, p);
+  if (st != ICGS_OK) return st;
+  if (!coeffs_out) return fail(ICGS_ERR_INVALID_ARG, "coeffs_out must not be NULL");
+  float lam[kMaxSH];
+  if ((st = lambda_of(opt, p.L, lam)) != ICGS_OK) return st;
+  const Workspace need = carve(nullptr, p, kNeedAccumulate);
+  if (!workspace || workspace_bytes < need.total)
+    return fail(ICGS_ERR_WORKSPACE_TOO_SMALL, "workspace of %zu bytes, need %zu", workspace_bytes, need.total);
+  if (reinterpret_cast<uintptr_t>(workspace) % 256)
+    return fail(ICGS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Workspace ws = carve(static_cast<char*>(workspace), p, kNeedAccumulate);
+  if (p.n == 0) return ICGS_OK;
+  if ((st = upload_common(p, cams, lam, ws, s)) != ICGS_OK) return st;
+  if (p.L == 0)
+    ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)p.n * (1 + p.K), s));
+  for (int cam0 = 0; cam0 < p.n_cams; cam0 += p.cam_batch) {
+    const int cb = std::min(p.cam_batch, p.n_cams - cam0);
+    Workspace wp = ws;
+    wp.cams = ws.cams + cam0;
+    if (p.L > 0)
+      ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)cb * (size_t)p.n * (1 + p.K), s));
+    if ((st = bin_pass(p, scene, cb, wp, s)) != ICGS_OK) return st;
+    launch_blend_accumulate(p, cb, cam0, targets->data, (int)targets->dtype, wp, s);
+    if (p.L > 0) launch_fold(p, scene->means, cb, cam0 == 0, wp, s);
+  }
+  launch_solve(p, ws.lam, lam, ws, coeffs_out, status_out, chol_out, s);
+  return finish(ws, s);
+}
+
+icgs_status icgs_colorize_backward(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
+                                   const icgs_options* opt, const float* coeffs, const float* chol,
+                                   const float* grad_coeffs, void* workspace, size_t workspace_bytes,
+                                   float* grad_targets, float* grad_opacity, void* stream) {
+  g_err[0] = '\0';
+  if (!opt) return fail(ICGS_ERR_INVALID_ARG, "options must not be NULL");
+  icgs_status st = check_targets(targets);
+  if (st != ICGS_OK) return st;
+  Problem p;
+  st = setup(scene, cams, targets->channels, opt->sh_degree, opt->precision, opt->cond_tau, opt->cam_batch,
+             opt->instance_capacity, p);
+  if (st != ICGS_OK) return st;
+  if (p.K > 64) return fail(ICGS_ERR_UNSUPPORTED, "the adjoint supports up to 64 channels, got %d", p.K);
+  if (!coeffs || !chol || !grad_coeffs) return fail(ICGS_ERR_INVALID_ARG, "coeffs, chol and grad_coeffs are required");
+  float lam[kMaxSH];
+  if ((st = lambda_of(opt, p.L, lam)) != ICGS_OK) return st;
+  const Workspace need = carve(nullptr, p, kNeedBackward);
+  if (!workspace || workspace_bytes < need.total)
+    return fail(ICGS_ERR_WORKSPACE_TOO_SMALL, "workspace of %zu bytes, need %zu", workspace_bytes, need.total);
+  if (reinterpret_cast<uintptr_t>(workspace) % 256)
+    return fail(ICGS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Workspace ws = carve(static_cast<char*>(workspace), p, kNeedBackward);
+  if (p.n == 0) return ICGS_OK;
+  if ((st = upload_common(p, cams, lam, ws, s)) != ICGS_OK) return st;
+  ws.grad_o_acc = grad_opacity;
+  if (grad_opacity) ICGS_TRY_CUDA(cudaMemsetAsync(grad_opacity, 0, sizeof(float) * (size_t)p.n, s));
+  launch_adjoint_prepare(p, ws.lam, lam, coeffs, chol, grad_coeffs, ws, s);
+  for (int cam0 = 0; cam0 < p.n_cams; cam0 += p.cam_batch) {
+    const int cb = std::min(p.cam_batch, p.n_cams - cam0);
+    Workspace wp = ws;
+    wp.cams = ws.cams + cam0;
+    if ((st = bin_pass(p, scene, cb, wp, s)) != ICGS_OK) return st;
+    launch_payload_adjoint(p, scene->means, coeffs, cb, wp, s);
+    launch_blend_adjoint(p, cb, cam0, targets->data, (int)targets->dtype, wp, grad_targets, grad_opacity != nullptr, s);
+  }
+  return finish(ws, s);
+}
+
+size_t icgs_render_workspace_size(const icgs_scene* scene, const icgs_cameras* cams, int32_t sh_degree,
+                                  int32_t channels, int64_t instance_capacity) {
+  Problem p;
+  if (setup(scene, cams, channels, sh_degree, ICGS_PRECISION_PLAIN, 0.0f, 0, instance_capacity, p) != ICGS_OK) return 0;
+  return carve(nullptr, p, kNeedRender).total;
+}
+
+icgs_status icgs_render(const icgs_scene* scene, const icgs_cameras* cams, int32_t sh_degree, int32_t channels,
+                        const float* coeffs, int64_t instance_capacity, void* workspace, size_t workspace_bytes,
+                        float* images_out, void* stream) {
+  g_err[0] = '\0';
+  Problem p;
+  icgs_status st = setup(scene, cams, channels, sh_degree, ICGS_PRECISION_PLAIN, 0.0f, 0, instance_capacity, p);
+  if (st != ICGS_OK) return st;
+  if (!images_out || (!coeffs && p.n > 0)) return fail(ICGS_ERR_INVALID_ARG, "coeffs and images_out are required");
+  const Workspace need = carve(nullptr, p, kNeedRender);
+  if (!workspace || workspace_bytes < need.total)
+    return fail(ICGS_ERR_WORKSPACE_TOO_SMALL, "workspace of %zu bytes, need %zu", workspace_bytes, need.total);
+  if (reinterpret_cast<uintptr_t>(workspace) % 256)
+    return fail(ICGS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Workspace ws = carve(static_cast<char*>(workspace), p, kNeedRender);
+  if (p.n == 0) {
+    ICGS_TRY_CUDA(cudaMemsetAsync(images_out, 0, sizeof(float) * (size_t)p.n_cams * p.width * p.height * p.K, s));
+    ICGS_TRY_CUDA(cudaStreamSynchronize(s));
+    return ICGS_OK;
+  }
+  if ((st = upload_common(p, cams, nullptr, ws, s)) != ICGS_OK) return st;
+  for (int cam0 = 0; cam0 < p.n_cams; cam0 += p.cam_batch) {
+    const int cb = std::min(p.cam_batch, p.n_cams - cam0);
+    Workspace wp = ws;
+    wp.cams = ws.cams + cam0;
+    if ((st = bin_pass(p, scene, cb, wp, s)) != ICGS_OK) return st;
+    launch_payload_render(p, scene->means, coeffs, cb, wp, s);
+    launch_blend_render(p, cb, cam0, wp, images_out, s);
+  }
+  return finish(ws, s);
+}
+
+const char* icgs_last_error(void) { return g_err; }
+
+int64_t icgs_last_required_instances(void) { return g_required; }
+
+void icgs_last_stats(int64_t out[3]) {
+  if (!out) return;
+  out[0] = g_stats[0];
+  out[1] = g_stats[1];
+  out[2] = g_stats[2];
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// icgs_internal.h -- types shared by the CUDA translation units of libicgs.so (not public).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace icgs {
+
+constexpr int kTile = 16;            // screen tiles are 16x16 pixels; one CTA of 256 threads each
+constexpr int kTilePixels = kTile * kTile;
+constexpr int kMaxSH = 16;           // (L+1)^2 for L = 3
+constexpr int kSortCap = 4096;       // tile lists up to this length are sorted in shared memory
+constexpr uint32_t kMaxCapacity = 0x7FFFFFF0u;
+constexpr uint8_t kGaussOk = 0, kGaussUnseen = 1, kGaussFp64 = 2;  // icgs.h ICGS_GAUSSIAN_*
+
+// Device status block at the start of every workspace; read back at the end of each call.
+struct DevStatus {
+  uint32_t flags;             // kFlag* bits
+  uint32_t big_tiles;         // tiles longer than kSortCap in the current pass
+  uint64_t instances_needed;  // max over passes of (Gaussian, tile) instances
+  uint64_t instances_total;   // sum over passes
+  uint64_t contrib_pairs;     // pixel-Gaussian pairs with nonzero weight (sum over passes)
+  uint32_t fp64_count;        // Gaussians solved in FP64
+  uint32_t pad;
+};
+constexpr uint32_t kFlagOverflow = 1u;
+
+// One camera as the kernels see it (built on the host from icgs_cameras).
+struct DevCam {
+  float fx, fy, cx, cy;
+  float w[12];        // world_to_cam, row-major [R|t]
+  float centre[3];    // -R^T t (host double, rounded)
+  float limx, limy;   // 1.3 * tan(fov/2) in x and y
+  float pad;
+};
+
+// Projected Gaussian as the blend kernels read it: 32 bytes, one sector.
+//   a = (mean_x, mean_y, conic_a, conic_b), b = (conic_c, opacity, qthr, depth key)
+struct ProjRec {
+  float4 a;
+  float4 b;
+};
+
+// Sub-allocation of a caller workspace (every region 256-byte aligned).
+struct Workspace {
+  char* base = nullptr;
+  size_t bytes = 0;
+  DevStatus* status = nullptr;
+  DevCam* cams = nullptr;
+  ProjRec* rec = nullptr;          // [cb * n]
+  uint2* rect = nullptr;           // [cb * n] packed tile rectangle (tx0|ty0<<16, tx1|ty1<<16)
+  uint32_t* tile_off = nullptr;    // [cb * T + 1] counts, then exclusive offsets
+  uint32_t* tile_cur = nullptr;    // [cb * T]
+  uint32_t* scan_tmp = nullptr;    // [scan blocks + 1]
+  uint32_t* big_list = nullptr;    // [cb * T]
+  uint64_t* entries = nullptr;     // [capacity] (depth key << 32 | index)
+  uint64_t* entries_tmp = nullptr; // [capacity] merge buffer for long tiles
+  float* payload = nullptr;        // [cb * n * (K+1)] per (camera, Gaussian) colour / adjoint terms
+  float* acc = nullptr;            // [cb * n * (1+K)] (L>0) or [n * (1+K)] (L=0)
+  float* G = nullptr;              // [n * B * B] Gram rows, hi
+  float* Glo = nullptr;            // [n * B * B] compensation
+  float* bvec = nullptr;           // [n * B * K]
+  float* blo = nullptr;            // [n * B * K]
+  float* wsum = nullptr;           // [n]
+  float* wlo = nullptr;            // [n]
+  float* u = nullptr;              // [n * B * K] backward: A^-1 dL/dc
+  float* reg = nullptr;            // [n] backward: sum_mk lambda_m u_mk c_mk
+  float* grad_o_acc = nullptr;     // [n]
+  float* lam = nullptr;            // [B] Tikhonov weights
+  size_t total = 0;
+};
+
+struct Problem {
+  int64_t n = 0;
+  int n_cams = 0, width = 0, height = 0;
+  float near_z = 0.2f;
+  int tiles_x = 0, tiles_y = 0, tiles = 0;
+  int K = 0, L = 0, B = 1;
+  int cam_batch = 0;
+  uint32_t capacity = 0;
+  int precision = 0;
+  float cond_tau = 1e-3f;
+  int mode = 0;                     // 0 colorize, 1 backward, 2 render
+};
+
+// ---- launchers (each .cu file exposes host functions that enqueue its kernels) ----
+void launch_project(const Problem& p, const float* means, const float* scales, const float* quats,
+                    const float* opac, int cb, const Workspace& ws, cudaStream_t s);
+void launch_scan(const Problem& p, int cb, const Workspace& ws, cudaStream_t s);
+void launch_scatter(const Problem& p, int cb, const Workspace& ws, cudaStream_t s);
+void launch_tile_sort(const Problem& p, int cb, const Workspace& ws, cudaStream_t s);
+void launch_blend_accumulate(const Problem& p, int cb, int cam0, const void* targets, int dtype,
+                             const Workspace& ws, cudaStream_t s);
+void launch_fold(const Problem& p, const float* means, int cb, bool first, const Workspace& ws,
+                 cudaStream_t s);
+void launch_solve(const Problem& p, const float* lam_dev, const float* lam_host, const Workspace& ws,
+                  float* coeffs, uint8_t* status, float* chol, cudaStream_t s);
+void launch_payload_render(const Problem& p, const float* means, const float* coeffs, int cb,
+                           const Workspace& ws, cudaStream_t s);
+void launch_blend_render(const Problem& p, int cb, int cam0, const Workspace& ws, float* images,
+                         cudaStream_t s);
+void launch_adjoint_prepare(const Problem& p, const float* lam_dev, const float* lam_host,
+                            const float* coeffs, const float* chol, const float* grad_coeffs,
+                            const Workspace& ws, cudaStream_t s);
+void launch_payload_adjoint(const Problem& p, const float* means, const float* coeffs, int cb,
+                            const Workspace& ws, cudaStream_t s);
+void launch_blend_adjoint(const Problem& p, int cb, int cam0, const void* targets, int dtype,
+                          const Workspace& ws, float* grad_targets, bool want_grad_o,
+                          cudaStream_t s);
+
+}  // namespace icgs

@@ -1,0 +1,249 @@
+// project.cu -- projection of every (camera, Gaussian) pair and binning into 16x16 screen tiles.
+//
+// Per pair (Eq. 1 with the 3DGS EWA model the paper renders with): camera-space mean, culling at
+// the near plane, 2D covariance J W Sigma W^T J^T + 0.3 I, its inverse (the conic), the projected
+// mean, the support threshold q <= 2 ln(255 o) (alpha >= 1/255), and the rectangle of tiles whose
+// pixel centres can fall inside that support. The depth used for ordering is the float32 rounding
+// of z evaluated in double with the fixed, unfused sequence ((W20 x + W21 y) + W22 z) + W23, so the
+// ordering key is a well-defined function of the inputs.
+//
+// Binning is a counting sort: k_project counts instances per tile with atomics, an exclusive scan
+// turns counts into offsets, and k_scatter writes (depth key << 32 | index) into each tile's slot
+// range. The order inside a tile is fixed later by the per-tile sort.
+#include <cuda_runtime.h>
+
+#include "icgs_device.cuh"
+#include "icgs_internal.h"
+
+namespace icgs {
+
+namespace {
+
+__device__ __forceinline__ double depth_f64(const DevCam& c, float x, float y, float z) {
+  double t = __dadd_rn(__dmul_rn((double)c.w[8], (double)x), __dmul_rn((double)c.w[9], (double)y));
+  t = __dadd_rn(t, __dmul_rn((double)c.w[10], (double)z));
+  return __dadd_rn(t, (double)c.w[11]);
+}
+
+__global__ void __launch_bounds__(256) k_project(
+    const float* __restrict__ means, const float* __restrict__ scales,
+    const float* __restrict__ quats, const float* __restrict__ opac, int64_t n,
+    const DevCam* __restrict__ cams, int width, int height, float near_z, int tiles_x, int tiles,
+    ProjRec* __restrict__ rec, uint2* __restrict__ rect, uint32_t* __restrict__ tile_count) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= n) return;
+  const DevCam& c = cams[j];
+  const int64_t ji = (int64_t)j * n + i;
+  const float mx3 = means[3 * i], my3 = means[3 * i + 1], mz3 = means[3 * i + 2];
+  const float o = opac[i];
+  const double zd = depth_f64(c, mx3, my3, mz3);
+  if (!(zd > (double)near_z) || !(__dmul_rn((double)o, 255.0) >= 1.0)) {
+    rect[ji] = make_uint2(0xFFFFFFFFu, 0u);
+    return;
+  }
+  const float tz = __double2float_rn(zd);
+  const float tx = fmaf(c.w[0], mx3, fmaf(c.w[1], my3, fmaf(c.w[2], mz3, c.w[3])));
+  const float ty = fmaf(c.w[4], mx3, fmaf(c.w[5], my3, fmaf(c.w[6], mz3, c.w[7])));
+
+  // 3D covariance Sigma = M M^T with M = R(q) diag(s)
+  float qw = quats[4 * i], qx = quats[4 * i + 1], qy = quats[4 * i + 2], qz = quats[4 * i + 3];
+  const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+  qw *= qn; qx *= qn; qy *= qn; qz *= qn;
+  const float sx = scales[3 * i], sy = scales[3 * i + 1], sz = scales[3 * i + 2];
+  const float r00 = 1.f - 2.f * (qy * qy + qz * qz), r01 = 2.f * (qx * qy - qw * qz), r02 = 2.f * (qx * qz + qw * qy);
+  const float r10 = 2.f * (qx * qy + qw * qz), r11 = 1.f - 2.f * (qx * qx + qz * qz), r12 = 2.f * (qy * qz - qw * qx);
+  const float r20 = 2.f * (qx * qz - qw * qy), r21 = 2.f * (qy * qz + qw * qx), r22 = 1.f - 2.f * (qx * qx + qy * qy);
+  const float m00 = r00 * sx, m01 = r01 * sy, m02 = r02 * sz;
+  const float m10 = r10 * sx, m11 = r11 * sy, m12 = r12 * sz;
+  const float m20 = r20 * sx, m21 = r21 * sy, m22 = r22 * sz;
+  const float s00 = m00 * m00 + m01 * m01 + m02 * m02;
+  const float s01 = m00 * m10 + m01 * m11 + m02 * m12;
+  const float s02 = m00 * m20 + m01 * m21 + m02 * m22;
+  const float s11 = m10 * m10 + m11 * m11 + m12 * m12;
+  const float s12 = m10 * m20 + m11 * m21 + m12 * m22;
+  const float s22 = m20 * m20 + m21 * m21 + m22 * m22;
+
+  // EWA: T = J W (2x3), J at the clamped camera-space mean
+  const float iz = 1.0f / tz;
+  const float ux = fminf(c.limx, fmaxf(-c.limx, tx * iz));
+  const float uy = fminf(c.limy, fmaxf(-c.limy, ty * iz));
+  const float j00 = c.fx * iz, j02 = -c.fx * ux * iz;
+  const float j11 = c.fy * iz, j12 = -c.fy * uy * iz;
+  const float t00 = j00 * c.w[0] + j02 * c.w[8], t01 = j00 * c.w[1] + j02 * c.w[9], t02 = j00 * c.w[2] + j02 * c.w[10];
+  const float t10 = j11 * c.w[4] + j12 * c.w[8], t11 = j11 * c.w[5] + j12 * c.w[9], t12 = j11 * c.w[6] + j12 * c.w[10];
+  // Sigma' = T Sigma T^T + 0.3 I
+  const float u0 = s00 * t00 + s01 * t01 + s02 * t02;
+  const float u1 = s01 * t00 + s11 * t01 + s12 * t02;
+  const float u2 = s02 * t00 + s12 * t01 + s22 * t02;
+  const float v0 = s00 * t10 + s01 * t11 + s02 * t12;
+  const float v1 = s01 * t10 + s11 * t11 + s12 * t12;
+  const float v2 = s02 * t10 + s12 * t11 + s22 * t12;
+  const float ca2 = t00 * u0 + t01 * u1 + t02 * u2 + 0.3f;
+  const float cb2 = t10 * u0 + t11 * u1 + t12 * u2;
+  const float cc2 = t10 * v0 + t11 * v1 + t12 * v2 + 0.3f;
+  const float det = ca2 * cc2 - cb2 * cb2;
+  const float mx = fmaf(c.fx, tx * iz, c.cx);
+  const float my = fmaf(c.fy, ty * iz, c.cy);
+  if (!(det > 0.0f) || !isfinite(mx) || !isfinite(my)) {
+    rect[ji] = make_uint2(0xFFFFFFFFu, 0u);
+    return;
+  }
+  const float idet = 1.0f / det;
+  const float qthr = 2.0f * logf(255.0f * o);
+  // x-extent of {q <= qthr} is sqrt(qthr * Sigma'_xx); pad so the box contains every pixel centre
+  // that the blend kernel's own float32 alpha test can accept.
+  const float hx = sqrtf(fmaxf(qthr, 0.0f) * ca2) * 1.0001f + 0.01f;
+  const float hy = sqrtf(fmaxf(qthr, 0.0f) * cc2) * 1.0001f + 0.01f;
+  const float fx0 = fmaxf(ceilf(mx - hx - 0.5f), 0.0f), fx1 = fminf(floorf(mx + hx - 0.5f), (float)(width - 1));
+  const float fy0 = fmaxf(ceilf(my - hy - 0.5f), 0.0f), fy1 = fminf(floorf(my + hy - 0.5f), (float)(height - 1));
+  if (!(fx0 <= fx1) || !(fy0 <= fy1)) {
+    rect[ji] = make_uint2(0xFFFFFFFFu, 0u);
+    return;
+  }
+  const int tx0 = (int)fx0 / kTile, tx1 = (int)fx1 / kTile;
+  const int ty0 = (int)fy0 / kTile, ty1 = (int)fy1 / kTile;
+  ProjRec r;
+  r.a = make_float4(mx, my, cc2 * idet, -cb2 * idet);
+  r.b = make_float4(ca2 * idet, o, qthr, tz);
+  rec[ji] = r;
+  rect[ji] = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16));
+  uint32_t* base = tile_count + (int64_t)j * tiles;
+  for (int ty = ty0; ty <= ty1; ++ty)
+    for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(base + ty * tiles_x + tx, 1u);
+}
+
+__global__ void __launch_bounds__(256) k_scatter(
+    int64_t n, const ProjRec* __restrict__ rec, const uint2* __restrict__ rect, int tiles_x, int tiles,
+    const uint32_t* __restrict__ tile_off, uint32_t* __restrict__ tile_cur, uint64_t* __restrict__ entries,
+    uint32_t capacity, DevStatus* status) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= n) return;
+  const int64_t ji = (int64_t)j * n + i;
+  const uint2 rc = rect[ji];
+  const int tx0 = rc.x & 0xFFFF, ty0 = rc.x >> 16, tx1 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
+  if (rc.x == 0xFFFFFFFFu) return;
+  const uint64_t key = ((uint64_t)__float_as_uint(rec[ji].b.w) << 32) | (uint64_t)(uint32_t)i;
+  bool overflow = false;
+  for (int ty = ty0; ty <= ty1; ++ty)
+    for (int tx = tx0; tx <= tx1; ++tx) {
+      const int64_t t = (int64_t)j * tiles + ty * tiles_x + tx;
+      const uint32_t pos = atomicAdd(tile_cur + t, 1u);
+      const uint64_t slot = (uint64_t)tile_off[t] + pos;
+      if (slot < capacity) entries[slot] = key;
+      else overflow = true;
+    }
+  if (overflow) atomicOr(&status->flags, kFlagOverflow);
+}
+
+// ---- exclusive scan of uint32 counts (reduce, scan the block sums, add) ----
+constexpr int kScanBlock = 1024;
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_reduce(const uint32_t* __restrict__ in, int64_t m,
+                                                            uint32_t* __restrict__ sums) {
+  __shared__ uint32_t warp_sums[kScanBlock / 32];
+  const int64_t i = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+  uint32_t v = i < m ? in[i] : 0u;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    uint32_t s = warp_sums[threadIdx.x];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    if (threadIdx.x == 0) sums[blockIdx.x] = s;
+  }
+}
+
+// One CTA scans the block sums in place (exclusive) and records the 64-bit total.
+__global__ void __launch_bounds__(kScanBlock) k_scan_sums(uint32_t* __restrict__ sums, int nblocks,
+                                                          DevStatus* status, uint32_t* __restrict__ total_out) {
+  __shared__ unsigned long long warp_tot[kScanBlock / 32];
+  __shared__ unsigned long long carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int base = 0; base < nblocks; base += kScanBlock) {
+    const int i = base + threadIdx.x;
+    unsigned long long v = i < nblocks ? sums[i] : 0ull;
+    unsigned long long x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      unsigned long long w = warp_tot[lane];
+      unsigned long long z = w;
+      for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, z, o);
+        if (lane >= o) z += y;
+      }
+      warp_tot[lane] = z - w;  // exclusive prefix of warp totals
+    }
+    __syncthreads();
+    const unsigned long long excl = carry + warp_tot[wid] + x - v;
+    if (i < nblocks) sums[i] = (uint32_t)excl;
+    __syncthreads();
+    if (threadIdx.x == kScanBlock - 1) carry = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const unsigned long long tot = carry;
+    *total_out = tot > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)tot;
+    if (tot > status->instances_needed) status->instances_needed = tot;
+    status->instances_total += tot;
+  }
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_apply(uint32_t* __restrict__ data, int64_t m,
+                                                           const uint32_t* __restrict__ sums) {
+  __shared__ uint32_t warp_tot[kScanBlock / 32];
+  const int64_t i = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t v = i < m ? data[i] : 0u;
+  uint32_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = warp_tot[lane];
+    uint32_t z = w;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, z, o);
+      if (lane >= o) z += y;
+    }
+    warp_tot[lane] = z - w;
+  }
+  __syncthreads();
+  if (i < m) data[i] = sums[blockIdx.x] + warp_tot[wid] + x - v;
+}
+
+}  // namespace
+
+void launch_project(const Problem& p, const float* means, const float* scales, const float* quats,
+                    const float* opac, int cb, const Workspace& ws, cudaStream_t s) {
+  dim3 grid((unsigned)((p.n + 255) / 256), (unsigned)cb);
+  k_project<<<grid, 256, 0, s>>>(means, scales, quats, opac, p.n, ws.cams, p.width, p.height, p.near_z,
+                                 p.tiles_x, p.tiles, ws.rec, ws.rect, ws.tile_off);
+}
+
+void launch_scan(const Problem& p, int cb, const Workspace& ws, cudaStream_t s) {
+  const int64_t m = (int64_t)cb * p.tiles;
+  const int nblocks = (int)((m + kScanBlock - 1) / kScanBlock);
+  k_scan_reduce<<<nblocks, kScanBlock, 0, s>>>(ws.tile_off, m, ws.scan_tmp);
+  k_scan_sums<<<1, kScanBlock, 0, s>>>(ws.scan_tmp, nblocks, ws.status, ws.tile_off + m);
+  k_scan_apply<<<nblocks, kScanBlock, 0, s>>>(ws.tile_off, m, ws.scan_tmp);
+}
+
+void launch_scatter(const Problem& p, int cb, const Workspace& ws, cudaStream_t s) {
+  dim3 grid((unsigned)((p.n + 255) / 256), (unsigned)cb);
+  k_scatter<<<grid, 256, 0, s>>>(p.n, ws.rec, ws.rect, p.tiles_x, p.tiles, ws.tile_off, ws.tile_cur,
+                                 ws.entries, p.capacity, ws.status);
+}
+
+}  // namespace icgs

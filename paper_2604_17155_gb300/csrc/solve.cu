@@ -1,0 +1,466 @@
+// solve.cu -- the normal equations and the batched regularised solve (Eq. 12-14, Alg. 1 lines 5-6).
+//
+//   k_fold          G_i += sum_j V_ij Y_ij Y_ij^T, b_i += sum_j Y_ij S_ij^T, w_i += sum_j V_ij over the
+//                   cameras of one pass (L > 0). One 16-lane group per Gaussian, lane r owns row r of
+//                   G_i and b_i. MIXED keeps a TwoSum compensation term per entry.
+//   k_solve         A_i = G_i + w_i Lambda; Cholesky with the rows in registers of the group (pivots
+//                   and columns exchanged by shuffles); forward and back substitution per channel.
+//                   MIXED: a Gaussian whose smallest pivot ratio d_k / A_kk is below cond_tau, or
+//                   with a non-positive pivot, is refactored in FP64 from G + compensation.
+//   k_solve_l0      L = 0: c = b / (G + w lambda) with G = V / (4 pi), b = S / sqrt(4 pi).
+//   k_adjoint_prep  u_i = A_i^-1 dL/dc_i from the stored factor, reg_i = sum lambda_m u_mk c_mk.
+//   k_payload_*     per (camera, Gaussian): C = Y . c (render) or (a = Y . u, beta) (adjoint).
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "icgs_device.cuh"
+#include "icgs_internal.h"
+
+namespace icgs {
+
+namespace {
+
+constexpr int kGroup = 16;
+constexpr int kSolveThreads = 128;  // 8 Gaussians per CTA
+constexpr float kY0 = 0.28209479177387814f;
+
+// Shuffles name only the 16 lanes of the caller's group, so a neighbouring group that has
+// finished (or never started) in the same warp does not take part.
+__device__ __forceinline__ unsigned group_mask() {
+  return 0xFFFFu << (threadIdx.x & 16u);
+}
+template <typename F>
+__device__ __forceinline__ F group_sum(F v) {
+  const unsigned m = group_mask();
+#pragma unroll
+  for (int o = kGroup / 2; o > 0; o >>= 1) v += __shfl_xor_sync(m, v, o, kGroup);
+  return v;
+}
+
+// ------------------------------------------------------------------------------------------
+// fold
+// ------------------------------------------------------------------------------------------
+template <int B, int KC, bool MIXED>
+__global__ void __launch_bounds__(kSolveThreads) k_fold(
+    const float* __restrict__ means, int64_t n, const DevCam* __restrict__ cams, int cb,
+    const float* __restrict__ acc, int K, int k0, bool first, float* __restrict__ G,
+    float* __restrict__ Glo, float* __restrict__ bvec, float* __restrict__ blo,
+    float* __restrict__ wsum, float* __restrict__ wlo) {
+  const int64_t i = (blockIdx.x * (int64_t)kSolveThreads + threadIdx.x) / kGroup;
+  const int r = threadIdx.x % kGroup;
+  if (i >= n) return;  // whole groups exit together
+  const bool row = r < B;
+  const bool do_gram = k0 == 0;
+  float g[B], gl[B], bb[KC], bl[KC];
+  float w = 0.0f, wl = 0.0f;
+#pragma unroll
+  for (int c = 0; c < B; ++c) { g[c] = 0.0f; gl[c] = 0.0f; }
+#pragma unroll
+  for (int k = 0; k < KC; ++k) { bb[k] = 0.0f; bl[k] = 0.0f; }
+  if (!first && row) {
+    if (do_gram) {
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        g[c] = G[(i * B + r) * B + c];
+        if (MIXED) gl[c] = Glo[(i * B + r) * B + c];
+      }
+      w = wsum[i];
+      if (MIXED) wl = wlo[i];
+    }
+#pragma unroll
+    for (int k = 0; k < KC; ++k)
+      if (k0 + k < K) {
+        bb[k] = bvec[(i * B + r) * K + k0 + k];
+        if (MIXED) bl[k] = blo[(i * B + r) * K + k0 + k];
+      }
+  }
+  const float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
+  const int64_t stride = n * (int64_t)(1 + K);
+  for (int j = 0; j < cb; ++j) {
+    const float* a = acc + j * stride + i * (1 + K);
+    const float v = a[0];
+    if (!(v > 0.0f)) continue;
+    const float3 d = view_dir(mu, cams[j]);
+    float Y[B];
+    sh_basis<B>(d.x, d.y, d.z, Y);
+    if (!row) continue;
+    float Yr = Y[0];
+#pragma unroll
+    for (int c = 1; c < B; ++c)
+      if (c == r) Yr = Y[c];
+    if (do_gram) {
+      const float vy = v * Yr;
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        if (MIXED) two_sum_acc(g[c], gl[c], vy * Y[c]);
+        else g[c] = fmaf(vy, Y[c], g[c]);
+      }
+      if (MIXED) two_sum_acc(w, wl, v);
+      else w += v;
+    }
+#pragma unroll
+    for (int k = 0; k < KC; ++k)
+      if (k0 + k < K) {
+        const float s = a[1 + k0 + k];
+        if (MIXED) two_sum_acc(bb[k], bl[k], Yr * s);
+        else bb[k] = fmaf(Yr, s, bb[k]);
+      }
+  }
+  if (!row) return;
+  if (do_gram) {
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      G[(i * B + r) * B + c] = g[c];
+      if (MIXED) Glo[(i * B + r) * B + c] = gl[c];
+    }
+    if (r == 0) {
+      wsum[i] = w;
+      if (MIXED) wlo[i] = wl;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < KC; ++k)
+    if (k0 + k < K) {
+      bvec[(i * B + r) * K + k0 + k] = bb[k];
+      if (MIXED) blo[(i * B + r) * K + k0 + k] = bl[k];
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Cholesky in a 16-lane group: lane r holds row r of A (a[0..B-1]); on return a[0..r] is row r of
+// the lower factor L. Returns the smallest pivot ratio d_k / A_kk (<= 0 if a pivot was not
+// positive; such pivots are replaced by 1 so the arithmetic stays finite).
+// ------------------------------------------------------------------------------------------
+template <int B, typename F>
+__device__ __forceinline__ F group_cholesky(F (&a)[B], int r) {
+  F diag0 = 0;
+#pragma unroll
+  for (int c = 0; c < B; ++c)
+    if (c == r) diag0 = a[c];
+  F minratio = 1;
+  const unsigned m = group_mask();
+#pragma unroll
+  for (int k = 0; k < B; ++k) {
+    F d = __shfl_sync(m, a[k], k, kGroup);
+    const F d0 = __shfl_sync(m, diag0, k, kGroup);
+    const F ratio = d / d0;
+    if (!(ratio >= minratio)) minratio = ratio;  // also catches NaN
+    if (!(d > 0)) d = 1;
+    const F lkk = sqrt(d);
+    const F inv = F(1) / lkk;
+    const F lrk = r > k ? a[k] * inv : (r == k ? lkk : F(0));
+    a[k] = lrk;
+#pragma unroll
+    for (int c = k + 1; c < B; ++c) {
+      const F lck = __shfl_sync(m, lrk, c, kGroup);
+      if (r >= c) a[c] -= lrk * lck;
+    }
+  }
+  return minratio;
+}
+
+// Solve L L^T x = rhs for one right-hand side; lane r holds rhs_r in x and L's row r in a.
+template <int B, typename F>
+__device__ __forceinline__ void group_chol_solve(const F (&a)[B], int r, F& x) {
+  F lrr = 1;
+#pragma unroll
+  for (int c = 0; c < B; ++c)
+    if (c == r) lrr = a[c];
+  const F inv_rr = F(1) / lrr;
+  const unsigned m = group_mask();
+  // forward: L y = rhs
+#pragma unroll
+  for (int k = 0; k < B; ++k) {
+    if (r == k) x *= inv_rr;
+    const F yk = __shfl_sync(m, x, k, kGroup);
+    if (r > k && r < B) x -= a[k] * yk;
+  }
+  // backward: L^T x = y; at step k subtract sum_{m>k} L_mk x_m, held by lanes m > k
+#pragma unroll
+  for (int k = B - 1; k >= 0; --k) {
+    const F part = (r > k && r < B) ? a[k] * x : F(0);
+    const F s = group_sum(part);
+    if (r == k) x = (x - s) * inv_rr;
+  }
+}
+
+template <int B, bool MIXED>
+__global__ void __launch_bounds__(kSolveThreads) k_solve(
+    int64_t n, int K, const float* __restrict__ G, const float* __restrict__ Glo,
+    const float* __restrict__ bvec, const float* __restrict__ blo, const float* __restrict__ wsum,
+    const float* __restrict__ wlo, const float* __restrict__ lam, float cond_tau,
+    float* __restrict__ coeffs, uint8_t* __restrict__ status_out, float* __restrict__ chol,
+    DevStatus* status) {
+  const int64_t i = (blockIdx.x * (int64_t)kSolveThreads + threadIdx.x) / kGroup;
+  const int r = threadIdx.x % kGroup;
+  if (i >= n) return;
+  const bool row = r < B;
+  const float w = wsum[i];
+  const float lam_r = row ? lam[r] : 0.0f;
+  if (!(w > 0.0f)) {
+    if (row) {
+      for (int k = 0; k < K; ++k) coeffs[(i * B + r) * K + k] = 0.0f;
+      if (chol)
+        for (int c = 0; c <= r; ++c) chol[i * (B * (B + 1) / 2) + r * (r + 1) / 2 + c] = 0.0f;  // no register array
+    }
+    if (r == 0 && status_out) status_out[i] = kGaussUnseen;
+    return;
+  }
+  float a[B];
+#pragma unroll
+  for (int c = 0; c < B; ++c) {
+    a[c] = row ? G[(i * B + r) * B + c] : 0.0f;
+    if (c == r) a[c] += w * lam_r;
+  }
+  const float minratio = group_cholesky<B, float>(a, r);
+  const bool fp64 = MIXED && !(minratio >= cond_tau);
+  if (!fp64) {
+    for (int k = 0; k < K; ++k) {
+      float x = row ? bvec[(i * B + r) * K + k] : 0.0f;
+      group_chol_solve<B, float>(a, r, x);
+      if (row) coeffs[(i * B + r) * K + k] = x;
+    }
+    if (chol && row) {
+#pragma unroll
+      for (int c = 0; c < B; ++c)
+        if (c <= r) chol[i * (B * (B + 1) / 2) + r * (r + 1) / 2 + c] = a[c];
+    }
+    if (r == 0 && status_out) status_out[i] = kGaussOk;
+    return;
+  }
+  // FP64 refactorisation from the compensated sums
+  double ad[B];
+  const double wd = (double)w + (double)(wlo ? wlo[i] : 0.0f);
+#pragma unroll
+  for (int c = 0; c < B; ++c) {
+    ad[c] = row ? (double)G[(i * B + r) * B + c] + (double)Glo[(i * B + r) * B + c] : 0.0;
+    if (c == r) ad[c] += wd * (double)lam_r;
+  }
+  group_cholesky<B, double>(ad, r);
+  for (int k = 0; k < K; ++k) {
+    double x = row ? (double)bvec[(i * B + r) * K + k] + (double)blo[(i * B + r) * K + k] : 0.0;
+    group_chol_solve<B, double>(ad, r, x);
+    if (row) coeffs[(i * B + r) * K + k] = (float)x;
+  }
+  if (chol && row) {
+#pragma unroll
+    for (int c = 0; c < B; ++c)
+      if (c <= r) chol[i * (B * (B + 1) / 2) + r * (r + 1) / 2 + c] = (float)ad[c];
+  }
+  if (r == 0) {
+    if (status_out) status_out[i] = kGaussFp64;
+    atomicAdd(&status->fp64_count, 1u);
+  }
+}
+
+// L = 0: acc[i] = (V, S_0..S_{K-1}) summed over every camera.
+__global__ void k_solve_l0(int64_t n, int K, const float* __restrict__ acc, float lam0,
+                           float* __restrict__ coeffs, uint8_t* __restrict__ status_out,
+                           float* __restrict__ chol) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n * (int64_t)K) return;
+  const int64_t i = idx / K;
+  const int k = (int)(idx - i * K);
+  const float V = acc[i * (1 + K)];
+  float c = 0.0f;
+  if (V > 0.0f) {
+    // (Y0^2 V + V lambda) c = Y0 S
+    const float A = V * (kY0 * kY0 + lam0);
+    c = kY0 * acc[i * (1 + K) + 1 + k] / A;
+    if (k == 0 && chol) chol[i] = sqrtf(A);
+  } else if (k == 0 && chol) {
+    chol[i] = 0.0f;
+  }
+  coeffs[i * K + k] = c;
+  if (k == 0 && status_out) status_out[i] = V > 0.0f ? kGaussOk : kGaussUnseen;
+}
+
+// ------------------------------------------------------------------------------------------
+// adjoint preparation: u = A^-1 g from the factor, reg = sum_mk lambda_m u_mk c_mk
+// ------------------------------------------------------------------------------------------
+template <int B>
+__global__ void __launch_bounds__(kSolveThreads) k_adjoint_prep(
+    int64_t n, int K, const float* __restrict__ chol, const float* __restrict__ grad_c,
+    const float* __restrict__ coeffs, const float* __restrict__ lam, float* __restrict__ u,
+    float* __restrict__ reg) {
+  const int64_t i = (blockIdx.x * (int64_t)kSolveThreads + threadIdx.x) / kGroup;
+  const int r = threadIdx.x % kGroup;
+  if (i >= n) return;
+  const bool row = r < B;
+  float a[B];
+#pragma unroll
+  for (int c = 0; c < B; ++c) a[c] = (row && c <= r) ? chol[i * (B * (B + 1) / 2) + r * (r + 1) / 2 + c] : 0.0f;
+  const float l00 = __shfl_sync(group_mask(), a[0], 0, kGroup);
+  const bool seen = l00 > 0.0f;
+  float rg = 0.0f;
+  for (int k = 0; k < K; ++k) {
+    float x = row ? grad_c[(i * B + r) * K + k] : 0.0f;
+    if (seen) group_chol_solve<B, float>(a, r, x);
+    else x = 0.0f;
+    if (row) {
+      u[(i * B + r) * K + k] = x;
+      rg = fmaf(lam[r] * x, coeffs[(i * B + r) * K + k], rg);
+    }
+  }
+  rg = group_sum(rg);
+  if (r == 0) reg[i] = rg;
+}
+
+__global__ void k_adjoint_prep_l0(int64_t n, int K, const float* __restrict__ chol,
+                                  const float* __restrict__ grad_c, const float* __restrict__ coeffs,
+                                  float lam0, float* __restrict__ u, float* __restrict__ reg) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float l = chol[i];
+  const float inv = l > 0.0f ? 1.0f / (l * l) : 0.0f;
+  float rg = 0.0f;
+  for (int k = 0; k < K; ++k) {
+    const float x = grad_c[i * K + k] * inv;
+    u[i * K + k] = x;
+    rg = fmaf(lam0 * x, coeffs[i * K + k], rg);
+  }
+  reg[i] = rg;
+}
+
+// ------------------------------------------------------------------------------------------
+// per (camera, Gaussian) payloads
+// ------------------------------------------------------------------------------------------
+template <int B>
+__global__ void k_payload_render(int64_t n, int K, const float* __restrict__ means,
+                                 const DevCam* __restrict__ cams, int cb,
+                                 const float* __restrict__ coeffs, float* __restrict__ payload) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
+  const float* ci = coeffs + i * B * K;
+  for (int j = 0; j < cb; ++j) {
+    const float3 d = view_dir(mu, cams[j]);
+    float Y[B];
+    sh_basis<B>(d.x, d.y, d.z, Y);
+    float* out = payload + ((int64_t)j * n + i) * K;
+    for (int k = 0; k < K; ++k) {
+      float s = 0.0f;
+#pragma unroll
+      for (int m = 0; m < B; ++m) s = fmaf(Y[m], ci[m * K + k], s);
+      out[k] = s;
+    }
+  }
+}
+
+template <int B>
+__global__ void k_payload_adjoint(int64_t n, int K, const float* __restrict__ means,
+                                  const DevCam* __restrict__ cams, int cb,
+                                  const float* __restrict__ coeffs, const float* __restrict__ u,
+                                  const float* __restrict__ reg, float* __restrict__ payload) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
+  const float* ci = coeffs + i * B * K;
+  const float* ui = u + i * B * K;
+  const float rg = reg[i];
+  for (int j = 0; j < cb; ++j) {
+    const float3 d = view_dir(mu, cams[j]);
+    float Y[B];
+    sh_basis<B>(d.x, d.y, d.z, Y);
+    float* out = payload + ((int64_t)j * n + i) * (K + 1);
+    float beta = -rg;
+    for (int k = 0; k < K; ++k) {
+      float a = 0.0f, yc = 0.0f;
+#pragma unroll
+      for (int m = 0; m < B; ++m) {
+        a = fmaf(Y[m], ui[m * K + k], a);
+        yc = fmaf(Y[m], ci[m * K + k], yc);
+      }
+      out[k] = a;
+      beta = fmaf(-a, yc, beta);
+    }
+    out[K] = beta;
+  }
+}
+
+template <int B, bool MIXED>
+void fold_b(const Problem& p, const float* means, int cb, const Workspace& ws, bool first, cudaStream_t s) {
+  const unsigned grid = (unsigned)((p.n * kGroup + kSolveThreads - 1) / kSolveThreads);
+  for (int k0 = 0; k0 < p.K; k0 += 4) {
+    k_fold<B, 4, MIXED><<<grid, kSolveThreads, 0, s>>>(means, p.n, ws.cams, cb, ws.acc, p.K, k0, first, ws.G, ws.Glo,
+                                                        ws.bvec, ws.blo, ws.wsum, ws.wlo);
+  }
+}
+
+template <int B, bool MIXED>
+void solve_b(const Problem& p, const float* lam_dev, const Workspace& ws, float* coeffs, uint8_t* st,
+             float* chol, cudaStream_t s) {
+  const unsigned grid = (unsigned)((p.n * kGroup + kSolveThreads - 1) / kSolveThreads);
+  k_solve<B, MIXED><<<grid, kSolveThreads, 0, s>>>(p.n, p.K, ws.G, ws.Glo, ws.bvec, ws.blo, ws.wsum, ws.wlo,
+                                                       lam_dev, p.cond_tau, coeffs, st, chol, ws.status);
+}
+
+}  // namespace
+
+// The first pass of a call writes G, b, w; later passes add to them.
+void launch_fold(const Problem& p, const float* means, int cb, bool first, const Workspace& ws,
+                      cudaStream_t s) {
+  const bool mixed = p.precision == 1;
+#define ICGS_FOLD(B)                                         \
+  if (mixed) fold_b<B, true>(p, means, cb, ws, first, s);   \
+  else fold_b<B, false>(p, means, cb, ws, first, s)
+  if (p.B == 4) { ICGS_FOLD(4); }
+  else if (p.B == 9) { ICGS_FOLD(9); }
+  else { ICGS_FOLD(16); }
+#undef ICGS_FOLD
+}
+
+void launch_solve(const Problem& p, const float* lam_dev, const float* lam_host, const Workspace& ws,
+                  float* coeffs, uint8_t* status, float* chol, cudaStream_t s) {
+  if (p.B == 1) {
+    const int64_t m = p.n * (int64_t)p.K;
+    k_solve_l0<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(p.n, p.K, ws.acc, lam_host[0], coeffs, status, chol);
+    return;
+  }
+  const bool mixed = p.precision == 1;
+#define ICGS_SOLVE(B)                                                       \
+  if (mixed) solve_b<B, true>(p, lam_dev, ws, coeffs, status, chol, s);    \
+  else solve_b<B, false>(p, lam_dev, ws, coeffs, status, chol, s)
+  if (p.B == 4) { ICGS_SOLVE(4); }
+  else if (p.B == 9) { ICGS_SOLVE(9); }
+  else { ICGS_SOLVE(16); }
+#undef ICGS_SOLVE
+}
+
+void launch_payload_render(const Problem& p, const float* means, const float* coeffs, int cb,
+                           const Workspace& ws, cudaStream_t s) {
+  const unsigned grid = (unsigned)((p.n + 127) / 128);
+  if (p.B == 1) k_payload_render<1><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.payload);
+  else if (p.B == 4) k_payload_render<4><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.payload);
+  else if (p.B == 9) k_payload_render<9><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.payload);
+  else k_payload_render<16><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.payload);
+}
+
+void launch_adjoint_prepare(const Problem& p, const float* lam_dev, const float* lam_host,
+                                const float* coeffs, const float* chol, const float* grad_coeffs,
+                                const Workspace& ws, cudaStream_t s) {
+  if (p.B == 1) {
+    k_adjoint_prep_l0<<<(unsigned)((p.n + 255) / 256), 256, 0, s>>>(p.n, p.K, chol, grad_coeffs, coeffs,
+                                                                     lam_host[0], ws.u, ws.reg);
+    return;
+  }
+  const unsigned grid = (unsigned)((p.n * kGroup + kSolveThreads - 1) / kSolveThreads);
+  if (p.B == 4)
+    k_adjoint_prep<4><<<grid, kSolveThreads, 0, s>>>(p.n, p.K, chol, grad_coeffs, coeffs, lam_dev, ws.u, ws.reg);
+  else if (p.B == 9)
+    k_adjoint_prep<9><<<grid, kSolveThreads, 0, s>>>(p.n, p.K, chol, grad_coeffs, coeffs, lam_dev, ws.u, ws.reg);
+  else
+    k_adjoint_prep<16><<<grid, kSolveThreads, 0, s>>>(p.n, p.K, chol, grad_coeffs, coeffs, lam_dev, ws.u, ws.reg);
+}
+
+void launch_payload_adjoint(const Problem& p, const float* means, const float* coeffs, int cb,
+                            const Workspace& ws, cudaStream_t s) {
+  const unsigned grid = (unsigned)((p.n + 127) / 128);
+  if (p.B == 1) k_payload_adjoint<1><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.u, ws.reg, ws.payload);
+  else if (p.B == 4) k_payload_adjoint<4><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.u, ws.reg, ws.payload);
+  else if (p.B == 9) k_payload_adjoint<9><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.u, ws.reg, ws.payload);
+  else k_payload_adjoint<16><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.u, ws.reg, ws.payload);
+}
+
+}  // namespace icgs

@@ -1,0 +1,353 @@
+"""Thin Python binding of libicgs.so (include/icgs.h): argument marshalling only.
+
+Every step of colorize / render / the adjoint runs in the library's CUDA kernels. PyTorch supplies
+device memory (inputs, outputs and the workspace) and the current CUDA stream. There is no CPU
+path: if libicgs.so is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libicgs.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "icgs.h")
+
+OK, ERR_INVALID_ARG, ERR_WORKSPACE_TOO_SMALL, ERR_CUDA, ERR_CAPACITY, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
+F32, BF16, F16 = 0, 1, 2
+PLAIN, MIXED = 0, 1
+GAUSSIAN_OK, GAUSSIAN_UNSEEN, GAUSSIAN_FP64 = 0, 1, 2
+
+
+class IcgsError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"icgs error {status}: {message}")
+        self.status = status
+
+
+class _Scene(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("means", ctypes.c_void_p), ("scales", ctypes.c_void_p),
+                ("quats", ctypes.c_void_p), ("opacity", ctypes.c_void_p)]
+
+
+class _Cameras(ctypes.Structure):
+    _fields_ = [("n_cams", ctypes.c_int32), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("near_z", ctypes.c_float), ("intrinsics", ctypes.c_void_p), ("world_to_cam", ctypes.c_void_p)]
+
+
+class _Targets(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("channels", ctypes.c_int32), ("data", ctypes.c_void_p)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("sh_degree", ctypes.c_int32), ("lambda_", ctypes.c_void_p), ("precision", ctypes.c_int32),
+                ("cond_tau", ctypes.c_float), ("cam_batch", ctypes.c_int32), ("instance_capacity", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def exported_names():
+    """Function names declared in include/icgs.h."""
+    txt = open(HEADER_PATH).read()
+    return re.findall(r"ICGS_API\s+[\w\s\*]*?\b(icgs_\w+)\s*\(", txt)
+
+
+def load(path: str = LIB_PATH):
+    """Loads libicgs.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libicgs.so not found at {path}; build it with "
+                           "`python -m paper_2604_17155_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    P, S = ctypes.c_void_p, ctypes.c_size_t
+    lib.icgs_workspace_size.argtypes = [P, P, P, P]
+    lib.icgs_workspace_size.restype = S
+    lib.icgs_colorize.argtypes = [P, P, P, P, P, S, P, P, P, P]
+    lib.icgs_colorize.restype = ctypes.c_int
+    lib.icgs_colorize_backward.argtypes = [P, P, P, P, P, P, P, P, S, P, P, P]
+    lib.icgs_colorize_backward.restype = ctypes.c_int
+    lib.icgs_render_workspace_size.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64]
+    lib.icgs_render_workspace_size.restype = S
+    lib.icgs_render.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int64, P, S, P, P]
+    lib.icgs_render.restype = ctypes.c_int
+    lib.icgs_last_error.argtypes = []
+    lib.icgs_last_error.restype = ctypes.c_char_p
+    lib.icgs_last_required_instances.argtypes = []
+    lib.icgs_last_required_instances.restype = ctypes.c_int64
+    lib.icgs_last_stats.argtypes = [P]
+    lib.icgs_last_stats.restype = None
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != OK:
+        raise IcgsError(status, load().icgs_last_error().decode(errors="replace"))
+
+
+def last_stats():
+    out = (ctypes.c_int64 * 3)()
+    load().icgs_last_stats(out)
+    return {"instances": int(out[0]), "contrib_pairs": int(out[1]), "fp64": int(out[2])}
+
+
+# ------------------------------------------------------------------------------------------
+# marshalling helpers
+# ------------------------------------------------------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+def _dev_f32(x, device):
+    torch = _torch()
+    t = torch.as_tensor(x, device=device)
+    if t.dtype != torch.float32:
+        t = t.float()
+    return t.contiguous()
+
+
+class Scene:
+    """Device-resident scene: means [n,3], scales [n,3], quats [n,4] (w,x,y,z), opacity [n]."""
+
+    def __init__(self, means, scales, quats, opacity, device="cuda"):
+        self.means = _dev_f32(means, device)
+        self.scales = _dev_f32(scales, device)
+        self.quats = _dev_f32(quats, device)
+        self.opacity = _dev_f32(opacity, device)
+
+    @classmethod
+    def from_workload(cls, scene, device="cuda"):
+        return cls(scene.means, scene.scales, scene.quats, scene.opacity, device)
+
+    @property
+    def n(self):
+        return int(self.means.shape[0])
+
+    def _struct(self, opacity=None):
+        o = self.opacity if opacity is None else opacity
+        return _Scene(self.n, self.means.data_ptr(), self.scales.data_ptr(), self.quats.data_ptr(), o.data_ptr())
+
+
+class Cameras:
+    """Host-side camera rig: intrinsics [C,4] (fx, fy, cx, cy) and world_to_cam [C,12]."""
+
+    def __init__(self, width, height, intrinsics, world_to_cam, near_z=0.2):
+        self.width, self.height = int(width), int(height)
+        self.intrinsics = np.ascontiguousarray(intrinsics, np.float32).reshape(-1, 4)
+        self.world_to_cam = np.ascontiguousarray(world_to_cam, np.float32).reshape(-1, 12)
+        self.near_z = float(near_z)
+
+    @classmethod
+    def from_workload(cls, cams):
+        intr = np.stack([cams.fx, cams.fy, cams.cx, cams.cy], 1)
+        return cls(cams.width, cams.height, intr, cams.world_to_cam.reshape(-1, 12), cams.near_z)
+
+    @property
+    def n(self):
+        return int(self.intrinsics.shape[0])
+
+    def _struct(self):
+        return _Cameras(self.n, self.width, self.height, self.near_z,
+                        self.intrinsics.ctypes.data, self.world_to_cam.ctypes.data)
+
+
+def _targets_struct(targets):
+    torch = _torch()
+    dt = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}.get(targets.dtype)
+    if dt is None:
+        raise TypeError(f"targets dtype {targets.dtype} is not float32, bfloat16 or float16")
+    if not targets.is_cuda or not targets.is_contiguous() or targets.dim() != 4:
+        raise ValueError("targets must be a contiguous CUDA tensor [n_cams,H,W,K]")
+    return _Targets(dt, int(targets.shape[-1]), targets.data_ptr())
+
+
+def _options(sh_degree, lam, precision, cond_tau, cam_batch, capacity):
+    lam_arr = None if lam is None else np.ascontiguousarray(lam, np.float32)
+    o = _Options(int(sh_degree), None if lam_arr is None else lam_arr.ctypes.data,
+                 {"plain": PLAIN, "mixed": MIXED}.get(precision, precision), float(cond_tau), int(cam_batch),
+                 int(capacity))
+    return o, lam_arr
+
+
+def _stream_ptr(device):
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class _WorkspaceCache:
+    """One growing byte buffer per device; instance capacity learned from ICGS_ERR_CAPACITY."""
+
+    def __init__(self):
+        self.buf = {}
+        self.capacity = {}
+
+    def get(self, device, nbytes):
+        torch = _torch()
+        key = str(device)
+        b = self.buf.get(key)
+        if b is None or b.numel() < nbytes:
+            self.buf[key] = None
+            b = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+            self.buf[key] = b
+        return b
+
+
+_ws = _WorkspaceCache()
+
+
+def _run_with_capacity(device, size_fn, call_fn, capacity):
+    """Calls call_fn(ws_ptr, ws_bytes, capacity); on ICGS_ERR_CAPACITY retries once with the
+    reported requirement (plus 10%)."""
+    lib = load()
+    cap = capacity if capacity > 0 else _ws.capacity.get(str(device), 0)
+    for _ in range(2):
+        nbytes = size_fn(cap)
+        if nbytes == 0:
+            _check(ERR_INVALID_ARG)
+        ws = _ws.get(device, nbytes)
+        st = call_fn(ws.data_ptr(), ws.numel(), cap)
+        if st == ERR_CAPACITY:
+            cap = int(lib.icgs_last_required_instances() * 1.1) + 1024
+            _ws.capacity[str(device)] = cap
+            continue
+        _check(st)
+        return
+    _check(st)
+
+
+# ------------------------------------------------------------------------------------------
+# public calls
+# ------------------------------------------------------------------------------------------
+def colorize(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, precision="mixed",
+             cond_tau=0.0, cam_batch=0, instance_capacity=0, opacity=None):
+    """Alg. 1 lines 1-6: per-Gaussian SH coefficients [n,(L+1)^2,K] (float32), status [n] (uint8)
+    and the row-packed Cholesky factors [n, B(B+1)/2] of A_i = G_i + w_i Lambda."""
+    torch = _torch()
+    lib = load()
+    dev = targets.device
+    B = (sh_degree + 1) ** 2
+    K = int(targets.shape[-1])
+    coeffs = torch.empty((scene.n, B, K), dtype=torch.float32, device=dev)
+    status = torch.empty((scene.n,), dtype=torch.uint8, device=dev)
+    chol = torch.empty((scene.n, B * (B + 1) // 2), dtype=torch.float32, device=dev)
+    sc = scene._struct(opacity)
+    cm = cams._struct()
+    tg = _targets_struct(targets)
+
+    def size_fn(cap):
+        o, _keep = _options(sh_degree, lam, precision, cond_tau, cam_batch, cap)
+        return lib.icgs_workspace_size(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(o))
+
+    def call_fn(ptr, nbytes, cap):
+        o, _keep = _options(sh_degree, lam, precision, cond_tau, cam_batch, cap)
+        return lib.icgs_colorize(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(o),
+                                 ctypes.c_void_p(ptr), nbytes, ctypes.c_void_p(coeffs.data_ptr()),
+                                 ctypes.c_void_p(status.data_ptr()), ctypes.c_void_p(chol.data_ptr()),
+                                 _stream_ptr(dev))
+
+    _run_with_capacity(dev, size_fn, call_fn, instance_capacity)
+    return coeffs, status, chol
+
+
+def colorize_backward(scene: Scene, cams: Cameras, targets, sh_degree, coeffs, chol, grad_coeffs, lam=None,
+                      precision="mixed", cam_batch=0, instance_capacity=0, want_targets=True,
+                      want_opacity=True, opacity=None):
+    """dL/d(targets) [n_cams,H,W,K] and dL/d(opacity) [n] for a given dL/dc."""
+    torch = _torch()
+    lib = load()
+    dev = targets.device
+    gt = torch.empty(targets.shape, dtype=torch.float32, device=dev) if want_targets else None
+    go = torch.empty((scene.n,), dtype=torch.float32, device=dev) if want_opacity else None
+    sc = scene._struct(opacity)
+    cm = cams._struct()
+    tg = _targets_struct(targets)
+    grad_coeffs = grad_coeffs.contiguous().float()
+    coeffs = coeffs.contiguous()
+    chol = chol.contiguous()
+
+    def size_fn(cap):
+        o, _keep = _options(sh_degree, lam, precision, 0.0, cam_batch, cap)
+        return lib.icgs_workspace_size(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(o))
+
+    def call_fn(ptr, nbytes, cap):
+        o, _keep = _options(sh_degree, lam, precision, 0.0, cam_batch, cap)
+        return lib.icgs_colorize_backward(
+            ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(o), ctypes.c_void_p(coeffs.data_ptr()),
+            ctypes.c_void_p(chol.data_ptr()), ctypes.c_void_p(grad_coeffs.data_ptr()), ctypes.c_void_p(ptr), nbytes,
+            ctypes.c_void_p(gt.data_ptr() if gt is not None else 0), ctypes.c_void_p(go.data_ptr() if go is not None else 0),
+            _stream_ptr(dev))
+
+    _run_with_capacity(dev, size_fn, call_fn, instance_capacity)
+    return gt, go
+
+
+def render(scene: Scene, cams: Cameras, coeffs, sh_degree, instance_capacity=0):
+    """Eq. 1-3: images [n_cams,H,W,K] float32 from coefficients [n,(L+1)^2,K]."""
+    torch = _torch()
+    lib = load()
+    coeffs = coeffs.contiguous().float()
+    dev = coeffs.device
+    K = int(coeffs.shape[-1])
+    images = torch.empty((cams.n, cams.height, cams.width, K), dtype=torch.float32, device=dev)
+    sc = scene._struct()
+    cm = cams._struct()
+
+    def size_fn(cap):
+        return lib.icgs_render_workspace_size(ctypes.byref(sc), ctypes.byref(cm), int(sh_degree), K, int(cap))
+
+    def call_fn(ptr, nbytes, cap):
+        return lib.icgs_render(ctypes.byref(sc), ctypes.byref(cm), int(sh_degree), K, ctypes.c_void_p(coeffs.data_ptr()),
+                               int(cap), ctypes.c_void_p(ptr), nbytes, ctypes.c_void_p(images.data_ptr()),
+                               _stream_ptr(dev))
+
+    _run_with_capacity(dev, size_fn, call_fn, instance_capacity)
+    return images
+
+
+def _make_autograd():
+    torch = _torch()
+
+    class ColorizeFn(torch.autograd.Function):
+        """c = colorize(targets, opacity) with the hand-written adjoint in backward()."""
+
+        @staticmethod
+        def forward(ctx, targets, opacity, scene, cams, sh_degree, lam, precision):
+            coeffs, status, chol = colorize(scene, cams, targets, sh_degree, lam=lam, precision=precision,
+                                            opacity=opacity.detach().contiguous().float())
+            ctx.save_for_backward(targets, opacity, coeffs, chol)
+            ctx.cfg = (scene, cams, sh_degree, lam, precision)
+            ctx.mark_non_differentiable(status)
+            return coeffs, status
+
+        @staticmethod
+        def backward(ctx, grad_coeffs, _grad_status):
+            targets, opacity, coeffs, chol = ctx.saved_tensors
+            scene, cams, sh_degree, lam, precision = ctx.cfg
+            gt, go = colorize_backward(scene, cams, targets, sh_degree, coeffs, chol, grad_coeffs, lam=lam,
+                                       precision=precision, want_targets=ctx.needs_input_grad[0],
+                                       want_opacity=ctx.needs_input_grad[1],
+                                       opacity=opacity.detach().contiguous().float())
+            if gt is not None:
+                gt = gt.to(targets.dtype)
+            return gt, go, None, None, None, None, None
+
+    return ColorizeFn
+
+
+_ColorizeFn = None
+
+
+def colorize_differentiable(scene: Scene, cams: Cameras, targets, opacity, sh_degree, lam=None, precision="mixed"):
+    """Autograd entry: returns coefficients differentiable with respect to targets and opacity."""
+    global _ColorizeFn
+    if _ColorizeFn is None:
+        _ColorizeFn = _make_autograd()
+    coeffs, _status = _ColorizeFn.apply(targets, opacity, scene, cams, sh_degree, lam, precision)
+    return coeffs

@@ -1,0 +1,81 @@
+"""The C ABI library builds for sm_103a, loads, exports every function include/icgs.h declares,
+and rejects bad arguments on the host before any device work. No GPU is needed."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2604_17155_gb300 import build as B
+from paper_2604_17155_gb300 import icgs
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return icgs.load()
+
+
+def test_header_declares_the_calls():
+    names = icgs.exported_names()
+    for want in ["icgs_workspace_size", "icgs_colorize", "icgs_colorize_backward", "icgs_render_workspace_size",
+                 "icgs_render", "icgs_last_error", "icgs_last_required_instances", "icgs_last_stats"]:
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in icgs.exported_names():
+        assert hasattr(lib, name), name
+
+
+def _structs(n=10, n_cams=2, w=40, h=30, K=3, L=3):
+    sc = icgs._Scene(n, 16, 16, 16, 16)  # fake non-null device pointers: never dereferenced on the host
+    intr = np.tile(np.array([50.0, 50.0, w / 2, h / 2], np.float32), (n_cams, 1))
+    w2c = np.tile(np.array([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 3], np.float32), (n_cams, 1))
+    cm = icgs._Cameras(n_cams, w, h, 0.2, intr.ctypes.data, w2c.ctypes.data)
+    tg = icgs._Targets(icgs.F32, K, 16)
+    opt = icgs._Options(L, None, icgs.MIXED, 0.0, 0, 0)
+    return sc, cm, tg, opt, (intr, w2c)
+
+
+def test_workspace_size_grows_with_capacity(lib):
+    sc, cm, tg, opt, keep = _structs()
+    sizes = []
+    for cap in (1000, 2000, 100000):
+        opt.instance_capacity = cap
+        sizes.append(lib.icgs_workspace_size(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(opt)))
+    assert sizes[0] > 0 and sizes[0] < sizes[1] < sizes[2]
+    assert sizes[2] - sizes[1] >= 2 * 8 * (100000 - 2000) - 512  # keys + merge buffer (256-B aligned)
+
+
+def test_bad_arguments_rejected_on_host(lib):
+    sc, cm, tg, opt, keep = _structs()
+    R = lambda *a: lib.icgs_colorize(*a)
+    assert R(None, ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(opt), None, 0, None, None, None, None) == icgs.ERR_INVALID_ARG
+    assert "NULL" in lib.icgs_last_error().decode()
+    opt.sh_degree = 4
+    assert R(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(opt), None, 0, ctypes.c_void_p(16), None, None, None) == icgs.ERR_INVALID_ARG
+    assert "sh_degree" in lib.icgs_last_error().decode()
+    opt.sh_degree = 3
+    # workspace too small is reported before anything is enqueued
+    assert R(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(opt), ctypes.c_void_p(256), 1024,
+             ctypes.c_void_p(16), None, None, None) == icgs.ERR_WORKSPACE_TOO_SMALL
+    tg.dtype = 7
+    assert R(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(opt), None, 0, ctypes.c_void_p(16), None, None, None) == icgs.ERR_INVALID_ARG
+    tg.dtype = icgs.F32
+    bad = np.array([[0.0, 50.0, 20.0, 15.0]] * 2, np.float32)
+    cm.intrinsics = bad.ctypes.data
+    assert R(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(opt), None, 0, ctypes.c_void_p(16), None, None, None) == icgs.ERR_INVALID_ARG
+    assert "focal" in lib.icgs_last_error().decode()
+    lam = np.full(16, -1.0, np.float32)
+    cm.intrinsics = keep[0].ctypes.data
+    opt.lambda_ = lam.ctypes.data
+    assert R(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(opt), ctypes.c_void_p(256), 1 << 40,
+             ctypes.c_void_p(16), None, None, None) == icgs.ERR_INVALID_ARG
+    assert "lambda" in lib.icgs_last_error().decode()
+
+
+def test_backward_rejects_too_many_channels(lib):
+    sc, cm, tg, opt, keep = _structs(K=65)
+    st = lib.icgs_colorize_backward(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(opt),
+                                    ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), None, 0, None, None, None)
+    assert st == icgs.ERR_UNSUPPORTED

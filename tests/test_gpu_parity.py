@@ -1,0 +1,227 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on seeded synthetic scenes:
+render (Eq. 1-3), colorize (Alg. 1 lines 1-6, Eq. 14) in both precisions and every target dtype,
+camera passes, long tile lists, capacity retry, degenerate inputs and the adjoint."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2604_17155_gb300 import workloads as W
+
+from _parity import TOL_BF16, TOL_FP32, coefficient_report, to_np
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def icgs():
+    from paper_2604_17155_gb300 import build as B
+    B.build()
+    from paper_2604_17155_gb300 import icgs as I
+    I.load()
+    return I
+
+
+DEV = "cuda"
+
+
+def _gpu(icgs, sc, cams):
+    return icgs.Scene.from_workload(sc, DEV), icgs.Cameras.from_workload(cams)
+
+
+def _mid_scene(n=4000, seed=11, n_cams=24, w=120, h=90):
+    sc = W.cluster_scene(n, seed, radius=1.5, log_scale_mean=-3.6, log_scale_std=0.4)
+    cams = W.hemisphere_cameras(n_cams, 4.0, w, h, 50.0)
+    return sc, cams
+
+
+# ------------------------------------------------------------------------------------------
+def test_render_matches_oracle(icgs):
+    sc, cams = _mid_scene(n=3000, n_cams=6, w=70, h=50)  # ragged 16x16 tiles in x and y
+    L = 3
+    coeffs = W.sh_coefficients(sc.n, L, 3, seed=12)
+    ref = O.render(sc, cams, coeffs, L)
+    gs, gc = _gpu(icgs, sc, cams)
+    img = to_np(icgs.render(gs, gc, torch.tensor(coeffs, device=DEV), L))
+    d = np.abs(img - ref)
+    scale = np.abs(ref).max()
+    frac_tight = float((d <= 1e-4 * scale).mean())
+    print(f"render: max|d| {d.max():.3e}, frac within 1e-4*max {frac_tight:.5f}")
+    assert frac_tight > 0.999
+    assert d.max() <= 2e-2 * scale  # threshold flips only
+
+
+def test_colorize_tiny_workload(icgs):
+    """The tiny workload: 1,000 Gaussians, 8 ring cameras, 128x128, RGB rendered from degree-0
+    colours plus N(0, 0.01) noise, ridge 1e-6."""
+    sc = W.make_scene("tiny", 1000)
+    cams = W.make_cameras("tiny")
+    colors = np.random.default_rng(1001).uniform(0, 1, (sc.n, 3))
+    t = O.render(sc, cams, W.dc_coefficients_from_colors(colors), 0)
+    t = (t + W.gaussian_noise(t.shape, 0.01, 1002)).astype(np.float32)
+    col = O.colorize(sc, cams, t.astype(np.float64), 0, [1e-6])
+    gs, gc = _gpu(icgs, sc, cams)
+    for prec in ("plain", "mixed"):
+        c, status, chol = icgs.colorize(gs, gc, torch.tensor(t, device=DEV), 0, lam=[1e-6], precision=prec)
+        rep, err, checked = coefficient_report(to_np(c), col)
+        print("tiny", prec, rep)
+        assert rep["checked"] > 0.8 * rep["seen"]
+        assert rep["max_checked"] <= TOL_FP32
+        assert rep["p99_seen"] <= 1e-3
+        st = to_np(status)
+        np.testing.assert_array_equal(st == icgs.GAUSSIAN_UNSEEN, col["w"] == 0)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "plain"])
+def test_colorize_sh3_rgb(icgs, prec):
+    sc, cams = _mid_scene()
+    L = 3
+    t = O.render(sc, cams, W.sh_coefficients(sc.n, L, 3, seed=13), L).astype(np.float32)
+    col = O.colorize(sc, cams, t.astype(np.float64), L)
+    gs, gc = _gpu(icgs, sc, cams)
+    c, status, chol = icgs.colorize(gs, gc, torch.tensor(t, device=DEV), L, precision=prec)
+    rep, err, checked = coefficient_report(to_np(c), col)
+    print("sh3", prec, rep, icgs.last_stats())
+    assert rep["checked"] > 0.7 * rep["seen"]
+    if prec == "mixed":
+        assert rep["max_checked"] <= TOL_FP32
+    else:
+        assert rep["p99_checked"] <= 1e-2
+    # the Cholesky factor reproduces A = G + w Lambda of the oracle
+    B = 16
+    ch = to_np(chol)
+    idx = np.where(checked)[0][:50]
+    for i in idx:
+        Lm = np.zeros((B, B))
+        Lm[np.tril_indices(B)] = ch[i]
+        A = col["A"][i]
+        np.testing.assert_allclose(Lm @ Lm.T, A, rtol=0, atol=2e-4 * np.abs(A).max())
+
+
+@pytest.mark.parametrize("K,dtype", [(1, "f32"), (16, "f16"), (64, "bf16")])
+def test_colorize_channels_and_dtypes(icgs, K, dtype):
+    sc, cams = _mid_scene(n=2500, seed=21, n_cams=12, w=96, h=72)
+    rng = np.random.default_rng(22)
+    if dtype == "f16":  # one-hot masks
+        labels = W.voronoi_labels(sc.means, K, 23, 1.5)
+        img = O.render(sc, cams, W.one_hot_dc(labels, K), 0)
+        t = np.eye(K, dtype=np.float32)[img.argmax(-1)]
+        tt = torch.tensor(t, device=DEV).half()
+    elif dtype == "bf16":
+        t = W.fourier_fields(cams.n, 72, 96, K, 24, n_modes=6)
+        tt = torch.tensor(t, device=DEV).bfloat16()
+    else:
+        t = rng.uniform(0, 1, (cams.n, 72, 96, K)).astype(np.float32)
+        tt = torch.tensor(t, device=DEV)
+    t_exact = tt.float().cpu().numpy().astype(np.float64)  # the oracle sees the same 16-bit values
+    lam = [1e-5]
+    col = O.colorize(sc, cams, t_exact, 0, lam)
+    gs, gc = _gpu(icgs, sc, cams)
+    for prec in ("plain", "mixed"):
+        c, status, chol = icgs.colorize(gs, gc, tt, 0, lam=lam, precision=prec)
+        rep, err, checked = coefficient_report(to_np(c), col)
+        print(K, dtype, prec, rep)
+        tol = TOL_FP32 if (prec == "plain" or K < 16 or dtype == "f32") else TOL_BF16
+        assert rep["max_checked"] <= tol
+
+
+def test_camera_passes_match_single_pass(icgs):
+    sc, cams = _mid_scene(n=3000, n_cams=20)
+    L = 3
+    t = torch.tensor(O.render(sc, cams, W.sh_coefficients(sc.n, L, 3, seed=31), L), dtype=torch.float32, device=DEV)
+    gs, gc = _gpu(icgs, sc, cams)
+    c1, s1, _ = icgs.colorize(gs, gc, t, L, cam_batch=0)
+    c2, s2, _ = icgs.colorize(gs, gc, t, L, cam_batch=7)
+    assert torch.equal(s1, s2)
+    e = O.relative_errors(to_np(c2), to_np(c1).astype(np.float64))
+    assert np.percentile(e[to_np(s1) == 0], 99) < 1e-5
+
+
+def test_long_tile_lists_and_capacity_retry(icgs):
+    """6,000 small Gaussians stacked in front of one tile: that tile's list exceeds the
+    shared-memory sort and goes through the merge path; a tiny capacity forces one retry."""
+    rng = np.random.default_rng(41)
+    n = 6000
+    means = np.zeros((n, 3), np.float32)
+    means[:, 0] = rng.uniform(-0.02, 0.02, n)
+    means[:, 1] = rng.uniform(-0.02, 0.02, n)
+    means[:, 2] = rng.uniform(2.0, 6.0, n)
+    sc = W.Scene(means, np.full((n, 3), 0.004, np.float32), rng.standard_normal((n, 4)).astype(np.float32),
+                 rng.uniform(0.02, 0.3, n).astype(np.float32))
+    w2c = np.concatenate([np.eye(3), np.zeros((3, 1))], 1).astype(np.float32)[None]
+    cams = W.Cameras(64, 64, np.array([400.0], np.float32), np.array([400.0], np.float32),
+                     np.array([32.0], np.float32), np.array([32.0], np.float32), w2c)
+    t = rng.uniform(0, 1, (1, 64, 64, 3)).astype(np.float32)
+    col = O.colorize(sc, cams, t.astype(np.float64), 0, [1e-5])
+    gs, gc = _gpu(icgs, sc, cams)
+    c, status, _ = icgs.colorize(gs, gc, torch.tensor(t, device=DEV), 0, lam=[1e-5], instance_capacity=1000)
+    assert icgs.last_stats()["instances"] > 4096
+    rep, err, checked = coefficient_report(to_np(c), col)
+    print("long tiles", rep)
+    assert rep["checked"] > 100
+    assert rep["max_checked"] <= TOL_FP32
+
+
+def test_degenerate_inputs(icgs):
+    cams = W.hemisphere_cameras(3, 4.0, 40, 30, 50.0)
+    gc = icgs.Cameras.from_workload(cams)
+    t = torch.rand((3, 30, 40, 3), device=DEV)
+    # empty scene
+    empty = W.Scene(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32), np.zeros((0, 4), np.float32),
+                    np.zeros((0,), np.float32))
+    c, s, _ = icgs.colorize(icgs.Scene.from_workload(empty, DEV), gc, t, 3)
+    assert c.shape == (0, 16, 3)
+    # every Gaussian behind the cameras (outside the camera sphere, on the far side) or too transparent
+    sc = W.uniform_scene(50, 51, box=0.3)
+    sc.opacity[:] = 0.5 / 255.0
+    c, s, _ = icgs.colorize(icgs.Scene.from_workload(sc, DEV), gc, t, 3)
+    assert (to_np(s) == icgs.GAUSSIAN_UNSEEN).all() and (to_np(c) == 0).all()
+    # a single Gaussian
+    sc1 = W.uniform_scene(1, 52, box=0.01, log_scale_mean=-2.0)
+    sc1.opacity[:] = 0.7
+    tt = O.render(sc1, cams, np.ones((1, 16, 3), np.float32), 3).astype(np.float32)
+    col = O.colorize(sc1, cams, tt.astype(np.float64), 3)
+    c, s, _ = icgs.colorize(icgs.Scene.from_workload(sc1, DEV), gc, torch.tensor(tt, device=DEV), 3)
+    assert O.relative_errors(to_np(c), col["c"])[0] <= TOL_FP32
+
+
+def test_adjoint_matches_oracle(icgs):
+    sc, cams = _mid_scene(n=1500, seed=61, n_cams=8, w=64, h=48)
+    L = 3
+    t = O.render(sc, cams, W.sh_coefficients(sc.n, L, 3, seed=62), L).astype(np.float32)
+    t64 = t.astype(np.float64)
+    col = O.colorize(sc, cams, t64, L)
+    r = np.random.default_rng(63).standard_normal(col["c"].shape)
+    gt_ref, go_ref = O.adjoint(sc, cams, t64, L, None, 2 * r * col["c"], col=col)
+    gs, gc = _gpu(icgs, sc, cams)
+    tt = torch.tensor(t, device=DEV)
+    c, status, chol = icgs.colorize(gs, gc, tt, L)
+    gcoef = torch.tensor(2 * r * col["c"], dtype=torch.float32, device=DEV)  # same dL/dc on both sides
+    gt, go = icgs.colorize_backward(gs, gc, tt, L, torch.tensor(col["c"], dtype=torch.float32, device=DEV), chol, gcoef)
+    gt, go = to_np(gt), to_np(go)
+    dt = np.abs(gt - gt_ref)
+    print(f"adjoint dL/dt: max|d|/max|ref| {dt.max() / np.abs(gt_ref).max():.3e}")
+    rep, err, checked = coefficient_report(to_np(c), col)
+    ok = checked
+    eo = np.abs(go - go_ref)[ok] / np.maximum(np.abs(go_ref[ok]), 1e-3 * np.abs(go_ref).max())
+    print(f"adjoint dL/do: checked {ok.sum()}, p99 rel {np.percentile(eo, 99):.3e} max rel {eo.max():.3e}")
+    assert np.percentile(dt, 99.9) <= 1e-3 * np.abs(gt_ref).max()
+    assert np.percentile(eo, 99) <= 1e-2
+
+
+def test_autograd_function(icgs):
+    sc, cams = _mid_scene(n=800, seed=71, n_cams=6, w=48, h=40)
+    L = 2
+    t = torch.tensor(O.render(sc, cams, W.sh_coefficients(sc.n, L, 3, seed=72), L), dtype=torch.float32,
+                     device=DEV, requires_grad=True)
+    gs, gc = _gpu(icgs, sc, cams)
+    op = gs.opacity.clone().requires_grad_(True)
+    c = icgs.colorize_differentiable(gs, gc, t, op, L)
+    r = torch.randn_like(c)
+    (r * c * c).sum().backward()
+    c2, s2, chol = icgs.colorize(gs, gc, t.detach(), L)
+    gt, go = icgs.colorize_backward(gs, gc, t.detach(), L, c2, chol, 2 * r * c2)
+    torch.testing.assert_close(t.grad, gt)
+    torch.testing.assert_close(op.grad, go)
