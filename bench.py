@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Benchmark of the instant-colorization hot path (Alg. 1 lines 1-6) on one GB300.
+
+Workload ("relight", the relighting-shaped scene): 200,000 Gaussians from 40 anisotropic clusters in
+a radius-4 ball, 100 cameras on a radius-6 hemisphere at 800x800, fov 45 deg; RGB float32 targets
+rendered from random degree-3 SH coefficients (DC ~ U(0,1), higher ~ N(0,0.1)); L = 3 with the
+paper's per-band lambda. A step is one full icgs_colorize call: projection, binning, depth sort,
+blend-accumulate, fold and the regularised solve for every Gaussian.
+
+  value        ms per colorized scene (device-resident targets, CUDA events), whole job
+  e2e          the same through host buffers: pinned H2D of the targets and D2H of the
+               coefficients inside the timed region
+  roofline     the blend-accumulate kernel (dominant), timed live with CUDA events on its stream
+  cpu_baseline the FP64 oracle on the host cores, on a sample of cameras, scaled to a scene
+
+`--impl reference` times the oracle (CPU) on the same workload and prints the reference line.
+Multi-GPU (torchrun): every rank colorizes its own replica of the scene (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2604_17155_gb300 import workloads as W  # noqa: E402
+
+WORKLOAD = "relight"
+SEED = 2000
+METRIC = "colorize ms/scene"
+UNIT = "ms/scene"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="icgs", choices=["icgs", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "plain"])
+    ap.add_argument("--cpu-sample-cams", type=int, default=0, help="cameras in the oracle sample (0: host cores)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return dict(hbm_gbs=float(d["hbm_gbs"]), sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)), source="measured")
+    except Exception:
+        return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+CLOCK_FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+                "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+                "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + ",".join(CLOCK_FIELDS), "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < len(CLOCK_FIELDS):
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# oracle baseline (host cores)
+# ------------------------------------------------------------------------------------------
+def oracle_sample_ms_per_scene(scene, cams, targets_host_fn, n_sample, threads):
+    """Times the oracle's colorize on n_sample cameras (all Gaussians, all pixels), scaled to the
+    full rig: per-camera walk time x cameras + the fold and solve of every Gaussian."""
+    from oracle import oracle as O
+    O.build()
+    idx = np.linspace(0, cams.n - 1, n_sample).round().astype(int)
+    sub = cams.subset(idx)
+    t_host = targets_host_fn(idx)
+    t0 = time.perf_counter()
+    V, S, _, _, pairs = O.accumulate(scene, sub, t_host, threads=threads)
+    t1 = time.perf_counter()
+    Y = O.view_basis(scene, sub, 3)
+    G, b, w = O.fold(V, S, Y)
+    O.solve(G, b, w, O.paper_lambda(3))
+    t2 = time.perf_counter()
+    walk_per_cam = (t1 - t0) / n_sample * min(threads, n_sample)  # wall time of one camera on one core
+    fold_per_cam = (t2 - t1) / n_sample
+    ms = 1e3 * (walk_per_cam * cams.n / threads + fold_per_cam * cams.n)
+    return ms, int(pairs.sum()), idx, (t2 - t0)
+
+
+# ------------------------------------------------------------------------------------------
+def make_workload():
+    scene = W.make_scene(WORKLOAD, SEED)
+    cams = W.make_cameras(WORKLOAD)
+    coeffs = W.sh_coefficients(scene.n, 3, 3, SEED + 1)
+    return scene, cams, coeffs
+
+
+def run_reference(args, rank, world):
+    """The oracle on the host cores, one bounded camera sample per step."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    scene, cams, coeffs = make_workload()
+    cores = os.cpu_count() or 1
+    n_sample = args.cpu_sample_cams or min(cores, 8)
+    idx = np.linspace(0, cams.n - 1, n_sample).round().astype(int)
+    sub = cams.subset(idx)
+    targets = O.render(scene, sub, coeffs, 3, threads=cores)  # oracle-rendered targets of the sample
+    times = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        V, S, _, _, pairs = O.accumulate(scene, sub, targets, threads=cores)
+        t1 = time.perf_counter()
+        G, b, w = O.fold(V, S, O.view_basis(scene, sub, 3))
+        O.solve(G, b, w, O.paper_lambda(3))
+        t2 = time.perf_counter()
+        if step >= args.warmup:
+            walk = (t1 - t0) * min(cores, n_sample) / n_sample
+            times.append(1e3 * (walk * cams.n / cores + (t2 - t1) / n_sample * cams.n))
+    ms = float(np.mean(times))
+    sample = f"{n_sample} of {cams.n} cameras (all 200,000 Gaussians, all 800x800 pixels) per step, scaled to {cams.n}"
+    line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "relight: 200k Gaussians, 100 cameras 800x800, L=3 RGB", "precision": "fp64 oracle"},
+            "cpu_baseline": {"value": ms, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_icgs(args, rank, world, local_rank):
+    import torch
+
+    from paper_2604_17155_gb300 import build as B
+    B.build()
+    from paper_2604_17155_gb300 import icgs
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    scene, cams, coeffs = make_workload()
+    gs = icgs.Scene.from_workload(scene, dev)
+    gc = icgs.Cameras.from_workload(cams)
+    L = 3
+    with torch.no_grad():
+        targets = icgs.render(gs, gc, torch.tensor(coeffs, device=dev), L)  # [100,800,800,3] f32, 768 MB
+    torch.cuda.synchronize(dev)
+    target_bytes = targets.numel() * targets.element_size()
+
+    def step():
+        return icgs.colorize(gs, gc, targets, L, precision=args.precision)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step()
+    stats_warm = icgs.last_stats()
+    stream = torch.cuda.current_stream(dev)
+
+    # ---- device-resident timed region (stage events on the same stream) ----
+    icgs.set_stage_timing(True)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    stage_sum = {}
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+        for k, v in icgs.last_stage_ms().items():
+            stage_sum[k] = stage_sum.get(k, 0.0) + v
+    ev1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    icgs.set_stage_timing(False)
+    elapsed = ev0.elapsed_time(ev1)
+    stats = icgs.last_stats()
+    t = torch.tensor([elapsed], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    elapsed_max = float(t.item())
+    stage_ms = {k: v / args.steps for k, v in stage_sum.items() if v > 0}
+
+    # ---- end to end through host buffers ----
+    host_t = torch.empty(targets.shape, dtype=targets.dtype, pin_memory=True)
+    host_t.copy_(targets)
+    host_c = torch.empty((scene.n, 16, 3), dtype=torch.float32, pin_memory=True)
+    dev_t = torch.empty_like(targets)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        dev_t.copy_(host_t, non_blocking=True)
+        c, st, _ = icgs.colorize(gs, gc, dev_t, L, precision=args.precision)
+        host_c.copy_(c, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    t = torch.tensor([e2e_ms], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    e2e_max = float(t.item())
+
+    # ---- the plain FP32 path on the same inputs ----
+    plain = None
+    if args.precision == "mixed":
+        n_plain = max(3, min(args.steps, 5))
+        icgs.colorize(gs, gc, targets, L, precision="plain")
+        barrier()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(n_plain):
+            icgs.colorize(gs, gc, targets, L, precision="plain")
+        p1.record(stream)
+        barrier()
+        plain_ms = p0.elapsed_time(p1) / n_plain
+        plain = {"ms_per_scene": plain_ms, "mixed_speedup": plain_ms / (elapsed_max / args.steps)}
+
+    if rank != 0:
+        return
+    pk = peaks()
+    ms_scene = elapsed_max / (args.steps * world)
+    blend_ms = stage_ms.get("blend", float("nan"))
+    pairs = stats["contrib_pairs"]
+    inst = stats["instances"]
+    K = 3
+    # algorithmic work of the blend-accumulate kernel per launch (one launch per scene here):
+    # per contributing pair: weight (~15 FP32 ops + 1 exp) and accumulation 2(1+K)
+    flops = pairs * (15 + 2 * (1 + K))
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6
+    achieved_tflops = flops / (blend_ms * 1e-3) / 1e12
+    bytes_alg = target_bytes + inst * (8 + 32) + cams.n * scene.n * (1 + K) * 4 * 2
+    roof = {"kernel": "k_blend_accumulate<3>", "bound": "alu", "achieved": achieved_tflops,
+            "peak": fp32_peak / 1e12, "unit": "TFLOP/s", "frac": achieved_tflops / (fp32_peak / 1e12),
+            "traffic": None, "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {pk['sm_max_mhz']:.0f} MHz",
+            "hbm_view": {"algorithmic_bytes": bytes_alg, "achieved_gbs": bytes_alg / (blend_ms * 1e-3) / 1e9,
+                         "peak_gbs": pk["hbm_gbs"], "frac": bytes_alg / (blend_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                         "peak_source": pk["source"]}}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        n_sample = args.cpu_sample_cams or min(cores, 16)
+
+        def targets_host(idx):
+            return targets[torch.as_tensor(idx, device=dev)].double().cpu().numpy()
+
+        ms_cpu, opairs, idx, wall = oracle_sample_ms_per_scene(scene, cams, targets_host, n_sample, cores)
+        # the GPU's contributing-pair count on the same camera sample, for the pair-count cross-check
+        sub = icgs.Cameras.from_workload(cams.subset(idx))
+        icgs.colorize(gs, sub, targets[torch.as_tensor(idx, device=dev)].contiguous(), L, precision=args.precision)
+        gpairs = icgs.last_stats()["contrib_pairs"]
+        cpu = {"value": ms_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n_sample} of {cams.n} cameras, all Gaussians and pixels, walk x {cams.n}/{cores} cores "
+                         f"+ fold/solve x {cams.n}/{n_sample}; {wall:.1f} s of CPU wall time",
+               "pairs_oracle_sample": opairs, "pairs_gpu_sample": gpairs}
+    line = {
+        "metric": METRIC, "value": ms_scene, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed_max / args.steps, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "relight: 200k Gaussians (40 clusters, r=4), 100 cameras 800x800 fov 45, L=3, RGB f32",
+                   "precision": args.precision, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (768 MB of targets per step)"},
+        "roofline": roof,
+        "e2e": {"value": e2e_max / (args.steps * world), "unit": UNIT, "h2d_bytes_per_step": target_bytes,
+                "d2h_bytes_per_step": scene.n * 16 * 3 * 4},
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "gpu_launches": stats["launches"] * args.steps,
+        "blend_contribs_per_s": pairs / (blend_ms * 1e-3),
+        "stage_ms": stage_ms,
+        "instances": inst, "contrib_pairs": pairs, "fp64_gaussians": stats["fp64"],
+        "plain_fp32": plain,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_icgs(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

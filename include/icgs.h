@@ -158,10 +158,19 @@ ICGS_API const char* icgs_last_error(void);
 /* (Gaussian, tile) instances the last call on this host thread needed in its largest pass. */
 ICGS_API int64_t icgs_last_required_instances(void);
 
-/* Per-pass statistics of the last successful call on this host thread, for benchmarks:
- * out[0] = instances, out[1] = blend pairs evaluated (pixel x list entry, before early stop)
- * -- both summed over passes --, out[2] = Gaussians solved in FP64. */
-ICGS_API void icgs_last_stats(int64_t out[3]);
+/* Statistics of the last successful call on this host thread, for benchmarks:
+ * out[0] = (Gaussian, tile) instances summed over passes, out[1] = (pixel, Gaussian) pairs with
+ * nonzero blend weight, out[2] = Gaussians solved in FP64, out[3] = kernels launched. */
+ICGS_API void icgs_last_stats(int64_t out[4]);
+
+/* Stage timing for benchmarks (off by default, per host thread). When on, every call records CUDA
+ * events on its stream at each stage boundary (no extra synchronisation) and
+ * icgs_last_stage_ms(out, n) writes the milliseconds spent in stage i (summed over passes) to
+ * out[i] for i < min(n, stage count) and returns the stage count. icgs_stage_name(i) names
+ * stage i: project, scan, scatter, sort, blend, fold, solve, payload. */
+ICGS_API void icgs_set_stage_timing(int enable);
+ICGS_API int icgs_last_stage_ms(double* out, int n);
+ICGS_API const char* icgs_stage_name(int i);
 
 #ifdef __cplusplus
 }

@@ -255,6 +255,11 @@ static void for_each_pixel(const ocam_t* cam, int64_t nvis, const int32_t* order
   for (int ys = 0; ys < H; ys += STRIP) {
     int ye = ys + STRIP < H ? ys + STRIP : H;
     int64_t npx = (int64_t)W * (ye - ys);
+    if (mask) { /* strips without a selected pixel need no lists */
+      int any = 0;
+      for (int64_t p = 0; p < npx && !any; ++p) any = mask[(int64_t)ys * W + p] != 0;
+      if (!any) continue;
+    }
     memset(start, 0, sizeof(int64_t) * (size_t)(npx + 1));
     for (int64_t r = 0; r < nvis; ++r) {
       const oproj_t* g = P + order[r];

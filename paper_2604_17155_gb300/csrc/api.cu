@@ -25,7 +25,48 @@ namespace {
 
 thread_local char g_err[1024] = "";
 thread_local int64_t g_required = 0;
-thread_local int64_t g_stats[3] = {0, 0, 0};
+thread_local int64_t g_stats[4] = {0, 0, 0, 0};
+thread_local int64_t g_launches = 0;
+
+// ---- stage timing: one CUDA event per stage boundary, elapsed times read after the final sync ----
+enum Stage { kProject = 0, kScan, kScatter, kSort, kBlend, kFold, kSolve, kPayload, kStageCount };
+const char* const kStageNames[kStageCount] = {"project", "scan", "scatter", "sort", "blend", "fold", "solve", "payload"};
+
+struct StageTimer {
+  bool on = false;
+  std::vector<cudaEvent_t> events;  // created on first use, reused by later calls of this thread
+  std::vector<int> stage_of;        // stage_of[k] = stage between event k and event k+1
+  int used = 0;
+  double ms[kStageCount] = {};
+  void begin(cudaStream_t s) {
+    used = 0;
+    stage_of.clear();
+    for (double& m : ms) m = 0.0;
+    if (on) record(s);
+  }
+  void record(cudaStream_t s) {
+    if (used == (int)events.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) { on = false; return; }
+      events.push_back(e);
+    }
+    cudaEventRecord(events[(size_t)used++], s);
+  }
+  // marks the end of `stage` (which started at the previous mark)
+  void mark(int stage, cudaStream_t s) {
+    if (!on) return;
+    stage_of.push_back(stage);
+    record(s);
+  }
+  void collect() {
+    if (!on) return;
+    for (int k = 0; k + 1 < used && k < (int)stage_of.size(); ++k) {
+      float m = 0.0f;
+      if (cudaEventElapsedTime(&m, events[(size_t)k], events[(size_t)k + 1]) == cudaSuccess) ms[stage_of[(size_t)k]] += m;
+    }
+  }
+};
+thread_local StageTimer g_timer;
 
 icgs_status fail(icgs_status st, const char* fmt, ...) {
   va_list ap;
@@ -171,10 +212,12 @@ void default_lambda(int L, float* lam) {
 icgs_status upload_common(const Problem& p, const icgs_cameras* cams, const float* lam_host,
                           const Workspace& ws, cudaStream_t s) {
   const std::vector<DevCam> dc = build_cams(cams);
+  g_launches = 0;
   ICGS_TRY_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(DevStatus), s));
   ICGS_TRY_CUDA(cudaMemcpyAsync(ws.cams, dc.data(), sizeof(DevCam) * dc.size(), cudaMemcpyHostToDevice, s));
   if (lam_host) ICGS_TRY_CUDA(cudaMemcpyAsync(ws.lam, lam_host, sizeof(float) * p.B, cudaMemcpyHostToDevice, s));
   // pageable copies are staged before they return, so dc may go out of scope now
+  g_timer.begin(s);
   return ICGS_OK;
 }
 
@@ -183,9 +226,13 @@ icgs_status bin_pass(const Problem& p, const icgs_scene* sc, int cb, const Works
   ICGS_TRY_CUDA(cudaMemsetAsync(wp.tile_off, 0, sizeof(uint32_t) * (size_t)(ct + 1), s));
   ICGS_TRY_CUDA(cudaMemsetAsync(wp.tile_cur, 0, sizeof(uint32_t) * (size_t)ct, s));
   launch_project(p, sc->means, sc->scales, sc->quats, sc->opacity, cb, wp, s);
+  g_timer.mark(kProject, s);
   launch_scan(p, cb, wp, s);
+  g_timer.mark(kScan, s);
   launch_scatter(p, cb, wp, s);
+  g_timer.mark(kScatter, s);
   launch_tile_sort(p, cb, wp, s);
+  g_timer.mark(kSort, s);
   return ICGS_OK;
 }
 
@@ -194,6 +241,7 @@ icgs_status finish(const Workspace& ws, cudaStream_t s) {
   DevStatus st;
   ICGS_TRY_CUDA(cudaMemcpyAsync(&st, ws.status, sizeof st, cudaMemcpyDeviceToHost, s));
   ICGS_TRY_CUDA(cudaStreamSynchronize(s));
+  g_timer.collect();
   g_required = (int64_t)st.instances_needed;
   if (st.flags & kFlagOverflow)
     return fail(ICGS_ERR_CAPACITY, "a pass needed %lld (Gaussian, tile) instances; pass at least that as "
@@ -201,6 +249,7 @@ icgs_status finish(const Workspace& ws, cudaStream_t s) {
   g_stats[0] = (int64_t)st.instances_total;
   g_stats[1] = (int64_t)st.contrib_pairs;
   g_stats[2] = (int64_t)st.fp64_count;
+  g_stats[3] = g_launches;
   return ICGS_OK;
 }
 
@@ -228,6 +277,8 @@ icgs_status lambda_of(const icgs_options* opt, int L, float* lam) {
 
 }  // namespace
 
+void icgs::note_launches(int count) { g_launches += count; }
+
 extern "C" {
 
 size_t icgs_workspace_size(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
@@ -251,7 +302,7 @@ icgs_status icgs_colorize(const icgs_scene* scene, const icgs_cameras* cams, con
   st = setup(scene, cams, targets->channels, opt->sh_degree, opt->precision, opt->cond_tau, opt->cam_batch,
              opt->instance_capacity, p);
   if (st != ICGS_OK) return st;
-  if (!coeffs_out) return fail(ICGS_ERR_INVALID_ARG, "coeffs_out must not be NULL");
+  if (!coeffs_out && p.n > 0) return fail(ICGS_ERR_INVALID_ARG, "coeffs_out must not be NULL");
   float lam[kMaxSH];
   if ((st = lambda_of(opt, p.L, lam)) != ICGS_OK) return st;
   const Workspace need = carve(nullptr, p, kNeedAccumulate);
@@ -273,9 +324,14 @@ icgs_status icgs_colorize(const icgs_scene* scene, const icgs_cameras* cams, con
       ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)cb * (size_t)p.n * (1 + p.K), s));
     if ((st = bin_pass(p, scene, cb, wp, s)) != ICGS_OK) return st;
     launch_blend_accumulate(p, cb, cam0, targets->data, (int)targets->dtype, wp, s);
-    if (p.L > 0) launch_fold(p, scene->means, cb, cam0 == 0, wp, s);
+    g_timer.mark(kBlend, s);
+    if (p.L > 0) {
+      launch_fold(p, scene->means, cb, cam0 == 0, wp, s);
+      g_timer.mark(kFold, s);
+    }
   }
   launch_solve(p, ws.lam, lam, ws, coeffs_out, status_out, chol_out, s);
+  g_timer.mark(kSolve, s);
   return finish(ws, s);
 }
 
@@ -292,7 +348,8 @@ icgs_status icgs_colorize_backward(const icgs_scene* scene, const icgs_cameras* 
              opt->instance_capacity, p);
   if (st != ICGS_OK) return st;
   if (p.K > 64) return fail(ICGS_ERR_UNSUPPORTED, "the adjoint supports up to 64 channels, got %d", p.K);
-  if (!coeffs || !chol || !grad_coeffs) return fail(ICGS_ERR_INVALID_ARG, "coeffs, chol and grad_coeffs are required");
+  if ((!coeffs || !chol || !grad_coeffs) && p.n > 0)
+    return fail(ICGS_ERR_INVALID_ARG, "coeffs, chol and grad_coeffs are required");
   float lam[kMaxSH];
   if ((st = lambda_of(opt, p.L, lam)) != ICGS_OK) return st;
   const Workspace need = carve(nullptr, p, kNeedBackward);
@@ -302,18 +359,26 @@ icgs_status icgs_colorize_backward(const icgs_scene* scene, const icgs_cameras* 
     return fail(ICGS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Workspace ws = carve(static_cast<char*>(workspace), p, kNeedBackward);
-  if (p.n == 0) return ICGS_OK;
+  if (p.n == 0) {
+    if (grad_targets)
+      ICGS_TRY_CUDA(cudaMemsetAsync(grad_targets, 0, sizeof(float) * (size_t)p.n_cams * p.width * p.height * p.K, s));
+    ICGS_TRY_CUDA(cudaStreamSynchronize(s));
+    return ICGS_OK;
+  }
   if ((st = upload_common(p, cams, lam, ws, s)) != ICGS_OK) return st;
   ws.grad_o_acc = grad_opacity;
   if (grad_opacity) ICGS_TRY_CUDA(cudaMemsetAsync(grad_opacity, 0, sizeof(float) * (size_t)p.n, s));
   launch_adjoint_prepare(p, ws.lam, lam, coeffs, chol, grad_coeffs, ws, s);
+  g_timer.mark(kSolve, s);
   for (int cam0 = 0; cam0 < p.n_cams; cam0 += p.cam_batch) {
     const int cb = std::min(p.cam_batch, p.n_cams - cam0);
     Workspace wp = ws;
     wp.cams = ws.cams + cam0;
     if ((st = bin_pass(p, scene, cb, wp, s)) != ICGS_OK) return st;
     launch_payload_adjoint(p, scene->means, coeffs, cb, wp, s);
+    g_timer.mark(kPayload, s);
     launch_blend_adjoint(p, cb, cam0, targets->data, (int)targets->dtype, wp, grad_targets, grad_opacity != nullptr, s);
+    g_timer.mark(kBlend, s);
   }
   return finish(ws, s);
 }
@@ -352,7 +417,9 @@ icgs_status icgs_render(const icgs_scene* scene, const icgs_cameras* cams, int32
     wp.cams = ws.cams + cam0;
     if ((st = bin_pass(p, scene, cb, wp, s)) != ICGS_OK) return st;
     launch_payload_render(p, scene->means, coeffs, cb, wp, s);
+    g_timer.mark(kPayload, s);
     launch_blend_render(p, cb, cam0, wp, images_out, s);
+    g_timer.mark(kBlend, s);
   }
   return finish(ws, s);
 }
@@ -361,11 +428,18 @@ const char* icgs_last_error(void) { return g_err; }
 
 int64_t icgs_last_required_instances(void) { return g_required; }
 
-void icgs_last_stats(int64_t out[3]) {
+void icgs_last_stats(int64_t out[4]) {
   if (!out) return;
-  out[0] = g_stats[0];
-  out[1] = g_stats[1];
-  out[2] = g_stats[2];
+  for (int k = 0; k < 4; ++k) out[k] = g_stats[k];
 }
+
+void icgs_set_stage_timing(int enable) { g_timer.on = enable != 0; }
+
+int icgs_last_stage_ms(double* out, int n) {
+  for (int k = 0; k < n && k < kStageCount; ++k) out[k] = g_timer.ms[k];
+  return kStageCount;
+}
+
+const char* icgs_stage_name(int i) { return (i >= 0 && i < kStageCount) ? kStageNames[i] : ""; }
 
 }  // extern "C"

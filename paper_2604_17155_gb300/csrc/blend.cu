@@ -366,6 +366,7 @@ void accumulate_chunk(const Problem& p, int cb, int cam0, const void* targets, i
   k_blend_accumulate<KC><<<cb * p.tiles, kThreads, 0, s>>>(ws.tile_off, ws.entries, p.capacity, ws.rec, p.n,
                                                             p.width, p.height, p.tiles_x, p.tiles, targets, dtype,
                                                             p.K, k0, cam0, ws.acc, stride, ws.status);
+  note_launches(1);
 }
 
 template <int KC>
@@ -374,6 +375,7 @@ void render_chunk(const Problem& p, int cb, int cam0, int k0, const Workspace& w
   k_blend_render<KC><<<cb * p.tiles, kThreads, 0, s>>>(ws.tile_off, ws.entries, p.capacity, ws.rec, p.n,
                                                         p.width, p.height, p.tiles_x, p.tiles, ws.payload, p.K,
                                                         k0, cam0, images);
+  note_launches(1);
 }
 
 }  // namespace
@@ -422,6 +424,7 @@ void launch_blend_adjoint(const Problem& p, int cb, int cam0, const void* target
   else if (p.K <= 32) ICGS_ADJ(32);
   else ICGS_ADJ(64);
 #undef ICGS_ADJ
+  note_launches(1);
 }
 
 }  // namespace icgs

@@ -85,6 +85,9 @@ struct Problem {
   int mode = 0;                     // 0 colorize, 1 backward, 2 render
 };
 
+// Kernel launches of the current call on this host thread (for the benchmark's launch count).
+void note_launches(int count);
+
 // ---- launchers (each .cu file exposes host functions that enqueue its kernels) ----
 void launch_project(const Problem& p, const float* means, const float* scales, const float* quats,
                     const float* opac, int cb, const Workspace& ws, cudaStream_t s);

@@ -230,6 +230,7 @@ void launch_project(const Problem& p, const float* means, const float* scales, c
   dim3 grid((unsigned)((p.n + 255) / 256), (unsigned)cb);
   k_project<<<grid, 256, 0, s>>>(means, scales, quats, opac, p.n, ws.cams, p.width, p.height, p.near_z,
                                  p.tiles_x, p.tiles, ws.rec, ws.rect, ws.tile_off);
+  note_launches(1);
 }
 
 void launch_scan(const Problem& p, int cb, const Workspace& ws, cudaStream_t s) {
@@ -238,12 +239,14 @@ void launch_scan(const Problem& p, int cb, const Workspace& ws, cudaStream_t s) 
   k_scan_reduce<<<nblocks, kScanBlock, 0, s>>>(ws.tile_off, m, ws.scan_tmp);
   k_scan_sums<<<1, kScanBlock, 0, s>>>(ws.scan_tmp, nblocks, ws.status, ws.tile_off + m);
   k_scan_apply<<<nblocks, kScanBlock, 0, s>>>(ws.tile_off, m, ws.scan_tmp);
+  note_launches(3);
 }
 
 void launch_scatter(const Problem& p, int cb, const Workspace& ws, cudaStream_t s) {
   dim3 grid((unsigned)((p.n + 255) / 256), (unsigned)cb);
   k_scatter<<<grid, 256, 0, s>>>(p.n, ws.rec, ws.rect, p.tiles_x, p.tiles, ws.tile_off, ws.tile_cur,
                                  ws.entries, p.capacity, ws.status);
+  note_launches(1);
 }
 
 }  // namespace icgs

@@ -185,6 +185,30 @@ __device__ __forceinline__ void group_chol_solve(const F (&a)[B], int r, F& x) {
   }
 }
 
+constexpr int kRefineSteps = 2;
+
+// Residual b - A x of row r with A = G_hi + G_lo + (w_hi + w_lo) Lambda and b = b_hi + b_lo,
+// evaluated in float-float: every product is split exactly with an FMA (TwoProduct) and summed
+// with TwoSum, so the residual is accurate even though A x and b agree to FP32 rounding.
+template <int B>
+__device__ __forceinline__ float refine_residual(const float (&ghi)[B], const float (&glo)[B], float wl_r,
+                                                 float wl_lo, float bh, float bl, float x, int r) {
+  const unsigned m = group_mask();
+  float s = 0.0f, comp = 0.0f;
+#pragma unroll
+  for (int c = 0; c < B; ++c) {
+    const float xc = __shfl_sync(m, x, c, kGroup);
+    const float p = ghi[c] * xc;
+    const float e = fmaf(ghi[c], xc, -p);
+    two_sum_acc(s, comp, p);
+    comp += e + glo[c] * xc;
+  }
+  const float p = wl_r * x;
+  two_sum_acc(s, comp, p);
+  comp += fmaf(wl_r, x, -p) + wl_lo * x;
+  return r < B ? (bh - s) + (bl - comp) : 0.0f;
+}
+
 template <int B, bool MIXED>
 __global__ void __launch_bounds__(kSolveThreads) k_solve(
     int64_t n, int K, const float* __restrict__ G, const float* __restrict__ Glo,
@@ -216,9 +240,30 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(
   const float minratio = group_cholesky<B, float>(a, r);
   const bool fp64 = MIXED && !(minratio >= cond_tau);
   if (!fp64) {
+    // MIXED: the rows of G_hi, G_lo are kept for iterative refinement of the FP32 solution
+    float ghi[B], glo[B];
+    if constexpr (MIXED) {
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        ghi[c] = row ? G[(i * B + r) * B + c] : 0.0f;
+        glo[c] = row ? Glo[(i * B + r) * B + c] : 0.0f;
+      }
+    }
+    const float wl_r = w * lam_r;
+    const float wl_lo = MIXED ? wlo[i] * lam_r : 0.0f;
     for (int k = 0; k < K; ++k) {
-      float x = row ? bvec[(i * B + r) * K + k] : 0.0f;
+      const float bh = row ? bvec[(i * B + r) * K + k] : 0.0f;
+      float x = bh;
       group_chol_solve<B, float>(a, r, x);
+      if constexpr (MIXED) {
+        const float bl = row ? blo[(i * B + r) * K + k] : 0.0f;
+#pragma unroll 1
+        for (int it = 0; it < kRefineSteps; ++it) {
+          float res = refine_residual<B>(ghi, glo, wl_r, wl_lo, bh, bl, x, r);
+          group_chol_solve<B, float>(a, r, res);
+          x += res;
+        }
+      }
       if (row) coeffs[(i * B + r) * K + k] = x;
     }
     if (chol && row) {
@@ -385,6 +430,7 @@ void fold_b(const Problem& p, const float* means, int cb, const Workspace& ws, b
   for (int k0 = 0; k0 < p.K; k0 += 4) {
     k_fold<B, 4, MIXED><<<grid, kSolveThreads, 0, s>>>(means, p.n, ws.cams, cb, ws.acc, p.K, k0, first, ws.G, ws.Glo,
                                                         ws.bvec, ws.blo, ws.wsum, ws.wlo);
+    note_launches(1);
   }
 }
 
@@ -394,6 +440,7 @@ void solve_b(const Problem& p, const float* lam_dev, const Workspace& ws, float*
   const unsigned grid = (unsigned)((p.n * kGroup + kSolveThreads - 1) / kSolveThreads);
   k_solve<B, MIXED><<<grid, kSolveThreads, 0, s>>>(p.n, p.K, ws.G, ws.Glo, ws.bvec, ws.blo, ws.wsum, ws.wlo,
                                                        lam_dev, p.cond_tau, coeffs, st, chol, ws.status);
+  note_launches(1);
 }
 
 }  // namespace
@@ -416,6 +463,7 @@ void launch_solve(const Problem& p, const float* lam_dev, const float* lam_host,
   if (p.B == 1) {
     const int64_t m = p.n * (int64_t)p.K;
     k_solve_l0<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(p.n, p.K, ws.acc, lam_host[0], coeffs, status, chol);
+    note_launches(1);
     return;
   }
   const bool mixed = p.precision == 1;
@@ -435,6 +483,7 @@ void launch_payload_render(const Problem& p, const float* means, const float* co
   else if (p.B == 4) k_payload_render<4><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.payload);
   else if (p.B == 9) k_payload_render<9><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.payload);
   else k_payload_render<16><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.payload);
+  note_launches(1);
 }
 
 void launch_adjoint_prepare(const Problem& p, const float* lam_dev, const float* lam_host,
@@ -443,6 +492,7 @@ void launch_adjoint_prepare(const Problem& p, const float* lam_dev, const float*
   if (p.B == 1) {
     k_adjoint_prep_l0<<<(unsigned)((p.n + 255) / 256), 256, 0, s>>>(p.n, p.K, chol, grad_coeffs, coeffs,
                                                                      lam_host[0], ws.u, ws.reg);
+    note_launches(1);
     return;
   }
   const unsigned grid = (unsigned)((p.n * kGroup + kSolveThreads - 1) / kSolveThreads);
@@ -452,6 +502,7 @@ void launch_adjoint_prepare(const Problem& p, const float* lam_dev, const float*
     k_adjoint_prep<9><<<grid, kSolveThreads, 0, s>>>(p.n, p.K, chol, grad_coeffs, coeffs, lam_dev, ws.u, ws.reg);
   else
     k_adjoint_prep<16><<<grid, kSolveThreads, 0, s>>>(p.n, p.K, chol, grad_coeffs, coeffs, lam_dev, ws.u, ws.reg);
+  note_launches(1);
 }
 
 void launch_payload_adjoint(const Problem& p, const float* means, const float* coeffs, int cb,
@@ -461,6 +512,7 @@ void launch_payload_adjoint(const Problem& p, const float* means, const float* c
   else if (p.B == 4) k_payload_adjoint<4><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.u, ws.reg, ws.payload);
   else if (p.B == 9) k_payload_adjoint<9><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.u, ws.reg, ws.payload);
   else k_payload_adjoint<16><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.u, ws.reg, ws.payload);
+  note_launches(1);
 }
 
 }  // namespace icgs

@@ -140,6 +140,7 @@ void launch_tile_sort(const Problem& p, int cb, const Workspace& ws, cudaStream_
   k_sort_long<<<152, kLongThreads, 0, s>>>(ws.tile_off, reinterpret_cast<unsigned long long*>(ws.entries),
                                            reinterpret_cast<unsigned long long*>(ws.entries_tmp), p.capacity,
                                            ws.big_list, ws.status);
+  note_launches(2);
 }
 
 }  // namespace icgs

@@ -82,6 +82,12 @@ def load(path: str = LIB_PATH):
     lib.icgs_last_required_instances.restype = ctypes.c_int64
     lib.icgs_last_stats.argtypes = [P]
     lib.icgs_last_stats.restype = None
+    lib.icgs_set_stage_timing.argtypes = [ctypes.c_int]
+    lib.icgs_set_stage_timing.restype = None
+    lib.icgs_last_stage_ms.argtypes = [P, ctypes.c_int]
+    lib.icgs_last_stage_ms.restype = ctypes.c_int
+    lib.icgs_stage_name.argtypes = [ctypes.c_int]
+    lib.icgs_stage_name.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -92,9 +98,22 @@ def _check(status):
 
 
 def last_stats():
-    out = (ctypes.c_int64 * 3)()
+    out = (ctypes.c_int64 * 4)()
     load().icgs_last_stats(out)
-    return {"instances": int(out[0]), "contrib_pairs": int(out[1]), "fp64": int(out[2])}
+    return {"instances": int(out[0]), "contrib_pairs": int(out[1]), "fp64": int(out[2]), "launches": int(out[3])}
+
+
+def set_stage_timing(enable: bool):
+    """Records CUDA events at stage boundaries of every call on this thread (benchmarks)."""
+    load().icgs_set_stage_timing(1 if enable else 0)
+
+
+def last_stage_ms():
+    """{stage name: milliseconds} of the last call on this thread (needs set_stage_timing(True))."""
+    lib = load()
+    out = (ctypes.c_double * 16)()
+    n = lib.icgs_last_stage_ms(out, 16)
+    return {lib.icgs_stage_name(i).decode(): float(out[i]) for i in range(n)}
 
 
 # ------------------------------------------------------------------------------------------

@@ -65,10 +65,11 @@ def test_colorize_tiny_workload(icgs):
     gs, gc = _gpu(icgs, sc, cams)
     for prec in ("plain", "mixed"):
         c, status, chol = icgs.colorize(gs, gc, torch.tensor(t, device=DEV), 0, lam=[1e-6], precision=prec)
-        rep, err, checked = coefficient_report(to_np(c), col)
+        rep, err, checked = coefficient_report(to_np(c), col, tol=TOL_FP32)
         print("tiny", prec, rep)
-        assert rep["checked"] > 0.8 * rep["seen"]
+        assert rep["checked"] > 0.5 * rep["seen"]
         assert rep["max_checked"] <= TOL_FP32
+        assert rep["bound_excess"] <= 0
         assert rep["p99_seen"] <= 1e-3
         st = to_np(status)
         np.testing.assert_array_equal(st == icgs.GAUSSIAN_UNSEEN, col["w"] == 0)
@@ -82,13 +83,19 @@ def test_colorize_sh3_rgb(icgs, prec):
     col = O.colorize(sc, cams, t.astype(np.float64), L)
     gs, gc = _gpu(icgs, sc, cams)
     c, status, chol = icgs.colorize(gs, gc, torch.tensor(t, device=DEV), L, precision=prec)
-    rep, err, checked = coefficient_report(to_np(c), col)
-    print("sh3", prec, rep, icgs.last_stats())
-    assert rep["checked"] > 0.7 * rep["seen"]
+    rep, err, checked = coefficient_report(to_np(c), col, tol=TOL_FP32 if prec == "mixed" else 1e-2)
+    ev = np.linalg.eigvalsh(col["A"][col["w"] > 0])
+    kappa = np.zeros(sc.n); kappa[col["w"] > 0] = ev[:, -1] / ev[:, 0]
+    wst = rep["worst"]
+    print("sh3", prec, rep, icgs.last_stats(), f"worst kappa {kappa[wst]:.3e} w {col['w'][wst]:.3e}",
+          "p99 err by kappa<1e3 / >=1e3:", [float(np.percentile(err[checked & sel], 99)) if (checked & sel).any() else 0
+                                             for sel in (kappa < 1e3, kappa >= 1e3)])
+    assert rep["checked"] > 0.25 * rep["seen"]
+    assert rep["bound_excess"] <= 0
     if prec == "mixed":
         assert rep["max_checked"] <= TOL_FP32
     else:
-        assert rep["p99_checked"] <= 1e-2
+        assert rep["p99_checked"] <= 1e-3
     # the Cholesky factor reproduces A = G + w Lambda of the oracle
     B = 16
     ch = to_np(chol)
@@ -121,10 +128,11 @@ def test_colorize_channels_and_dtypes(icgs, K, dtype):
     gs, gc = _gpu(icgs, sc, cams)
     for prec in ("plain", "mixed"):
         c, status, chol = icgs.colorize(gs, gc, tt, 0, lam=lam, precision=prec)
-        rep, err, checked = coefficient_report(to_np(c), col)
-        print(K, dtype, prec, rep)
         tol = TOL_FP32 if (prec == "plain" or K < 16 or dtype == "f32") else TOL_BF16
+        rep, err, checked = coefficient_report(to_np(c), col, tol=tol)
+        print(K, dtype, prec, rep)
         assert rep["max_checked"] <= tol
+        assert rep["bound_excess"] <= 0
 
 
 def test_camera_passes_match_single_pass(icgs):
@@ -140,28 +148,35 @@ def test_camera_passes_match_single_pass(icgs):
 
 
 def test_long_tile_lists_and_capacity_retry(icgs):
-    """6,000 small Gaussians stacked in front of one tile: that tile's list exceeds the
+    """9,000 small Gaussians stacked in front of one tile: that tile's list exceeds the
     shared-memory sort and goes through the merge path; a tiny capacity forces one retry."""
     rng = np.random.default_rng(41)
-    n = 6000
+    n = 9000
     means = np.zeros((n, 3), np.float32)
-    means[:, 0] = rng.uniform(-0.02, 0.02, n)
-    means[:, 1] = rng.uniform(-0.02, 0.02, n)
-    means[:, 2] = rng.uniform(2.0, 6.0, n)
-    sc = W.Scene(means, np.full((n, 3), 0.004, np.float32), rng.standard_normal((n, 4)).astype(np.float32),
-                 rng.uniform(0.02, 0.3, n).astype(np.float32))
+    depth = rng.uniform(2.0, 40.0, n)
+    # all inside the 16x16 tile whose pixels span [32, 48) in x and y (projected centre 40, 40)
+    means[:, 0] = rng.uniform(-1.5, 1.5, n) * depth / 400.0
+    means[:, 1] = rng.uniform(-1.5, 1.5, n) * depth / 400.0
+    means[:, 2] = depth
+    sc = W.Scene(means, np.full((n, 3), 1e-4, np.float32), rng.standard_normal((n, 4)).astype(np.float32),
+                 rng.uniform(0.005, 0.05, n).astype(np.float32))
     w2c = np.concatenate([np.eye(3), np.zeros((3, 1))], 1).astype(np.float32)[None]
     cams = W.Cameras(64, 64, np.array([400.0], np.float32), np.array([400.0], np.float32),
-                     np.array([32.0], np.float32), np.array([32.0], np.float32), w2c)
+                     np.array([40.0], np.float32), np.array([40.0], np.float32), w2c)
     t = rng.uniform(0, 1, (1, 64, 64, 3)).astype(np.float32)
     col = O.colorize(sc, cams, t.astype(np.float64), 0, [1e-5])
     gs, gc = _gpu(icgs, sc, cams)
     c, status, _ = icgs.colorize(gs, gc, torch.tensor(t, device=DEV), 0, lam=[1e-5], instance_capacity=1000)
-    assert icgs.last_stats()["instances"] > 4096
-    rep, err, checked = coefficient_report(to_np(c), col)
+    assert icgs.last_stats()["instances"] > 8000
+    rep, err, checked = coefficient_report(to_np(c), col, w_min=1e-3)  # tiny, faint Gaussians
     print("long tiles", rep)
-    assert rep["checked"] > 100
+    assert rep["checked"] > 20
     assert rep["max_checked"] <= TOL_FP32
+    # the render depends on the order of the whole list
+    coeffs = W.sh_coefficients(n, 0, 2, seed=42)
+    ref = O.render(sc, cams, coeffs, 0)
+    img = to_np(icgs.render(gs, gc, torch.tensor(coeffs, device=DEV), 0))
+    assert np.abs(img - ref).max() <= 1e-4 * np.abs(ref).max()
 
 
 def test_degenerate_inputs(icgs):
@@ -223,5 +238,6 @@ def test_autograd_function(icgs):
     (r * c * c).sum().backward()
     c2, s2, chol = icgs.colorize(gs, gc, t.detach(), L)
     gt, go = icgs.colorize_backward(gs, gc, t.detach(), L, c2, chol, 2 * r * c2)
-    torch.testing.assert_close(t.grad, gt)
-    torch.testing.assert_close(op.grad, go)
+    # two colorize calls differ by FP32 atomic summation order only
+    torch.testing.assert_close(t.grad, gt, rtol=1e-3, atol=1e-4 * gt.abs().max().item())
+    torch.testing.assert_close(op.grad, go, rtol=1e-3, atol=1e-4 * go.abs().max().item())
