@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "plain"])
     ap.add_argument("--cpu-sample-cams", type=int, default=0, help="cameras in the oracle sample (0: host cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cams", type=int, default=0, help="profiling only: use the first N cameras of the rig")
     return ap.parse_args()
 
 
@@ -139,9 +140,11 @@ def oracle_sample_ms_per_scene(scene, cams, targets_host_fn, n_sample, threads):
 
 
 # ------------------------------------------------------------------------------------------
-def make_workload():
+def make_workload(n_cams=0):
     scene = W.make_scene(WORKLOAD, SEED)
     cams = W.make_cameras(WORKLOAD)
+    if n_cams:
+        cams = cams.subset(np.arange(min(n_cams, cams.n)))
     coeffs = W.sh_coefficients(scene.n, 3, 3, SEED + 1)
     return scene, cams, coeffs
 
@@ -189,7 +192,7 @@ def run_icgs(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    scene, cams, coeffs = make_workload()
+    scene, cams, coeffs = make_workload(args.cams)
     gs = icgs.Scene.from_workload(scene, dev)
     gc = icgs.Cameras.from_workload(cams)
     L = 3
@@ -314,9 +317,9 @@ def run_icgs(args, rank, world, local_rank):
         "metric": METRIC, "value": ms_scene, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_max / args.steps, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "relight: 200k Gaussians (40 clusters, r=4), 100 cameras 800x800 fov 45, L=3, RGB f32",
+        "config": {"workload": f"relight: 200k Gaussians (40 clusters, r=4), {cams.n} cameras 800x800 fov 45, L=3, RGB f32",
                    "precision": args.precision, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (768 MB of targets per step)"},
+                   "l2": f"inputs larger than L2 ({target_bytes / 1e6:.0f} MB of targets per step)"},
         "roofline": roof,
         "e2e": {"value": e2e_max / (args.steps * world), "unit": UNIT, "h2d_bytes_per_step": target_bytes,
                 "d2h_bytes_per_step": scene.n * 16 * 3 * 4},

@@ -102,7 +102,7 @@ Workspace carve(char* base, const Problem& p, int need) {
   ws.cams = reinterpret_cast<DevCam*>(take(sizeof(DevCam) * (size_t)p.n_cams));
   ws.lam = reinterpret_cast<float*>(take(sizeof(float) * kMaxSH));
   ws.rec = reinterpret_cast<ProjRec*>(take(sizeof(ProjRec) * (size_t)cbn));
-  ws.rect = reinterpret_cast<uint2*>(take(sizeof(uint2) * (size_t)cbn));
+  ws.rect = reinterpret_cast<uint4*>(take(sizeof(uint4) * (size_t)cbn));
   ws.tile_off = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (size_t)(ct + 1)));
   ws.tile_cur = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (size_t)ct));
   ws.scan_tmp = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (size_t)(ct / 1024 + 2)));

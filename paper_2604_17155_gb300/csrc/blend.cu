@@ -3,17 +3,19 @@
 //
 //   k_blend_accumulate  colorize: for every (pixel, Gaussian) blend weight w = alpha T (Eq. 4)
 //                       accumulate V = sum w (Eq. 5) and S_k = sum w t_k (Eq. 6 numerator). The
-//                       tile's pixels are reduced per Gaussian with warp shuffles and shared-memory
-//                       atomics, then ONE global atomic group per (Gaussian, tile) lands in the
-//                       per-(camera, Gaussian) accumulator.
+//                       tile's pixels are reduced per Gaussian inside each warp (a halving
+//                       "transpose" butterfly that leaves value v's warp sum in lane v * 32/NP) and
+//                       across warps with shared-memory atomics; then ONE global atomic group per
+//                       (Gaussian, tile) lands in the per-(camera, Gaussian) accumulator.
 //   k_blend_render      render: img_k = sum w C_k (Eq. 1-3) with C from the payload.
 //   k_blend_adjoint     gradient: dL/dt_k = sum w a_k and, per Gaussian, dL/do = sum over pixels of
 //                       (g T - sum_{n>m} g_n w_n / (1-alpha)) * alpha/o with g = beta + a . t.
 //
-// Warp w of a CTA covers the 8x4 pixel block ((w&1)*8, (w>>1)*4) of the tile, so a small Gaussian
-// touches few warps; warps whose pixels all stopped skip the batch. Every kernel evaluates
-// alpha and the transmittance update through blend_step(), written with explicit round-to-nearest
-// intrinsics so that all walks take the same threshold decisions for the same inputs.
+// Warp w of a CTA covers the 8x4 pixel block ((w&1)*8, (w>>1)*4) of the tile. A warp skips a
+// Gaussian whose padded support box misses its block (a warp-uniform test), and skips a whole
+// batch once all its pixels stopped. Every walk takes its decisions through warp_hits() and
+// blend_step(), written with explicit round-to-nearest intrinsics, so all walks take the same
+// threshold decisions for the same inputs.
 #include <cuda_runtime.h>
 
 #include "icgs_device.cuh"
@@ -31,6 +33,7 @@ struct TileCtx {
   int j, t, px, py;
   bool inside;
   float pxf, pyf;
+  float wx0, wx1, wy0, wy1;  // pixel-centre rectangle of this thread's warp block
   uint32_t b, len;
 };
 
@@ -42,11 +45,16 @@ __device__ __forceinline__ TileCtx tile_ctx(const uint32_t* tile_off, uint32_t c
   c.t = bid - c.j * tiles;
   const int tyi = c.t / tiles_x, txi = c.t - tyi * tiles_x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  c.px = txi * kTile + (warp & 1) * 8 + (lane & 7);
-  c.py = tyi * kTile + (warp >> 1) * 4 + (lane >> 3);
+  const int bx = txi * kTile + (warp & 1) * 8, by = tyi * kTile + (warp >> 1) * 4;
+  c.px = bx + (lane & 7);
+  c.py = by + (lane >> 3);
   c.inside = c.px < width && c.py < height;
   c.pxf = (float)c.px + 0.5f;
   c.pyf = (float)c.py + 0.5f;
+  c.wx0 = (float)bx + 0.5f;
+  c.wx1 = (float)bx + 7.5f;
+  c.wy0 = (float)by + 0.5f;
+  c.wy1 = (float)by + 3.5f;
   const uint32_t b = min(tile_off[bid], capacity);
   uint32_t e = min(tile_off[bid + 1], capacity);
   if (e < b) e = b;
@@ -55,20 +63,25 @@ __device__ __forceinline__ TileCtx tile_ctx(const uint32_t* tile_off, uint32_t c
   return c;
 }
 
-// One step of the walk for Gaussian record (A, Bv) at pixel centre (pxf, pyf).
+// Does the Gaussian's padded support box touch the warp's pixel block? (warp-uniform)
+__device__ __forceinline__ bool warp_hits(const float4 box, const TileCtx& c) {
+  return box.x + box.z >= c.wx0 && box.x - box.z <= c.wx1 && box.y + box.w >= c.wy0 && box.y - box.w <= c.wy1;
+}
+
+// One step of the walk for a Gaussian (box, par, q threshold) at pixel centre (pxf, pyf).
 // Returns the weight w = alpha T (0 if skipped); sets `done` when the pixel stops here.
 // e_out receives exp(-q/2) and capped whether alpha hit 0.99 (both only meaningful if w > 0).
-__device__ __forceinline__ float blend_step(const float4 A, const float4 Bv, float pxf, float pyf,
+__device__ __forceinline__ float blend_step(const float4 box, const float4 par, float qthr, float pxf, float pyf,
                                             float& T, bool& done, float& alpha_out, float& e_out,
                                             bool& capped) {
-  const float dx = __fsub_rn(pxf, A.x), dy = __fsub_rn(pyf, A.y);
+  const float dx = __fsub_rn(pxf, box.x), dy = __fsub_rn(pyf, box.y);
   // q = a dx^2 + 2 b dx dy + c dy^2
-  const float q = __fmaf_rn(__fmul_rn(A.z, dx), dx,
-                            __fmaf_rn(__fmul_rn(__fmul_rn(2.0f, A.w), dx), dy, __fmul_rn(__fmul_rn(Bv.x, dy), dy)));
+  const float q = __fmaf_rn(__fmul_rn(par.x, dx), dx,
+                            __fmaf_rn(__fmul_rn(__fmul_rn(2.0f, par.y), dx), dy, __fmul_rn(__fmul_rn(par.z, dy), dy)));
   // beyond the support threshold (with margin) alpha < 1/255 for certain: skip the exponential
-  if (!(q <= __fmaf_rn(Bv.z, 1.0001f, 1e-4f))) return 0.0f;
+  if (!(q <= qthr)) return 0.0f;
   const float e = __expf(__fmul_rn(-0.5f, q));
-  const float oe = __fmul_rn(Bv.y, e);
+  const float oe = __fmul_rn(par.w, e);
   const float alpha = fminf(kAlphaMax, oe);
   if (!(alpha >= kAlphaMin)) return 0.0f;
   const float tT = __fmul_rn(T, __fsub_rn(1.0f, alpha));
@@ -86,21 +99,62 @@ __device__ __forceinline__ float blend_step(const float4 A, const float4 Bv, flo
 
 // Slot ranges are only fully written when the pass fit its capacity; an overflowed pass (reported
 // to the caller as ICGS_ERR_CAPACITY) may leave stale slots, so indices are clamped to the scene.
+// The fast-reject threshold is 2 ln(255 o) with a relative margin of 1e-4 (and 1e-4 absolute),
+// beyond which alpha < 1/255 holds by more than the float32 error of alpha.
 __device__ __forceinline__ void load_batch(const uint64_t* __restrict__ entries, uint32_t first, int nb,
-                                           const ProjRec* __restrict__ rec_cam, int64_t n, float4* s_a,
-                                           float4* s_b, uint32_t* s_id) {
+                                           const ProjRec* __restrict__ rec_cam, int64_t n, float4* s_box,
+                                           float4* s_par, float* s_thr, uint32_t* s_id) {
   if ((int)threadIdx.x < nb) {
     const uint32_t id = min((uint32_t)entries[first + threadIdx.x], (uint32_t)(n - 1));
     const ProjRec r = rec_cam[id];
     s_id[threadIdx.x] = id;
-    s_a[threadIdx.x] = r.a;
-    s_b[threadIdx.x] = r.b;
+    s_box[threadIdx.x] = r.box;
+    s_par[threadIdx.x] = r.par;
+    s_thr[threadIdx.x] = __fmaf_rn(2.0f * logf(255.0f * r.par.w), 1.0001f, 1e-4f);
   }
 }
 
 __device__ __forceinline__ void add_pair_count(uint32_t npairs, DevStatus* status) {
   const uint32_t warp_sum = __reduce_add_sync(kFull, npairs);
   if ((threadIdx.x & 31) == 0 && warp_sum) atomicAdd((unsigned long long*)&status->contrib_pairs, (unsigned long long)warp_sum);
+}
+
+template <int N>
+struct Log2 {
+  static constexpr int value = 1 + Log2<N / 2>::value;
+};
+template <>
+struct Log2<1> {
+  static constexpr int value = 0;
+};
+
+template <int N>
+struct NextPow2 {
+  static constexpr int value = N <= 1 ? 1 : N <= 2 ? 2 : N <= 4 ? 4 : N <= 8 ? 8 : N <= 16 ? 16 : 32;
+};
+
+// Warp sums of NP values (NP a power of two <= 32) with NP - 1 + 5 - log2(NP) shuffles: at each of
+// the first log2(NP) levels a lane keeps half of its values and trades the other half with its
+// partner. Lane l returns the warp sum of value index (l >> (5 - log2 NP)) & (NP - 1).
+template <int NP>
+__device__ __forceinline__ float warp_transpose_reduce(float (&v)[NP], int lane) {
+  constexpr int P = Log2<NP>::value;
+#pragma unroll
+  for (int lvl = 0; lvl < P; ++lvl) {
+    const int off = 16 >> lvl;
+    const int half = NP >> (lvl + 1);
+    const bool upper = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const float send = upper ? v[i] : v[i + half];
+      const float keep = upper ? v[i + half] : v[i];
+      v[i] = keep + __shfl_xor_sync(kFull, send, off);
+    }
+  }
+  float r = v[0];
+#pragma unroll
+  for (int off = 16 >> P; off > 0; off >>= 1) r += __shfl_xor_sync(kFull, r, off);
+  return r;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -112,9 +166,13 @@ __global__ void __launch_bounds__(kThreads) k_blend_accumulate(
     const ProjRec* __restrict__ rec, int64_t n, int width, int height, int tiles_x, int tiles,
     const void* __restrict__ targets, int dtype, int K, int k0, int cam0, float* __restrict__ acc,
     int64_t acc_cam_stride, DevStatus* status) {
-  __shared__ float4 s_a[kBatch], s_b[kBatch];
+  constexpr int NV = KC + 1;                      // V and S_0..S_{KC-1}
+  constexpr int NP = NextPow2<NV>::value;
+  constexpr int SHIFT = 5 - Log2<NP>::value;      // the sum of value v lands in lane v << SHIFT
+  __shared__ float4 s_box[kBatch], s_par[kBatch];
+  __shared__ float s_thr[kBatch];
   __shared__ uint32_t s_id[kBatch];
-  __shared__ float s_acc[kBatch][KC + 1];
+  __shared__ float s_acc[kBatch][NV];
   const TileCtx c = tile_ctx(tile_off, capacity, tiles, tiles_x, width, height);
   const int lane = threadIdx.x & 31;
   float tv[KC];
@@ -126,37 +184,36 @@ __global__ void __launch_bounds__(kThreads) k_blend_accumulate(
     for (int k = 0; k < KC; ++k)
       if (k0 + k < K) tv[k] = load_target(targets, base + k, dtype);
   }
-  for (int k = threadIdx.x; k < kBatch * (KC + 1); k += kThreads) (&s_acc[0][0])[k] = 0.0f;
+  for (int k = threadIdx.x; k < kBatch * NV; k += kThreads) (&s_acc[0][0])[k] = 0.0f;
   const ProjRec* rec_cam = rec + (int64_t)c.j * n;
   float* acc_cam = acc + (int64_t)c.j * acc_cam_stride;
+  const int my_value = lane >> SHIFT;
+  const bool reducer = (lane & ((1 << SHIFT) - 1)) == 0 && my_value < NV;
   float T = 1.0f;
   bool done = !c.inside;
   uint32_t npairs = 0;
   for (uint32_t start = 0; start < c.len; start += kBatch) {
     const int nb = (int)min((uint32_t)kBatch, c.len - start);
     __syncthreads();
-    load_batch(entries, c.b + start, nb, rec_cam, n, s_a, s_b, s_id);
+    load_batch(entries, c.b + start, nb, rec_cam, n, s_box, s_par, s_thr, s_id);
     __syncthreads();
     if (!__all_sync(kFull, done)) {
       for (int g = 0; g < nb; ++g) {
+        const float4 box = s_box[g];
+        if (!warp_hits(box, c)) continue;  // uniform across the warp
         float w = 0.0f, al, ex;
         bool cap;
-        if (!done) w = blend_step(s_a[g], s_b[g], c.pxf, c.pyf, T, done, al, ex, cap);
+        if (!done) w = blend_step(box, s_par[g], s_thr[g], c.pxf, c.pyf, T, done, al, ex, cap);
         if (__any_sync(kFull, w > 0.0f)) {
           npairs += w > 0.0f;
-          float v[KC + 1];
+          float v[NP];
           v[0] = w;
 #pragma unroll
           for (int k = 0; k < KC; ++k) v[k + 1] = w * tv[k];
 #pragma unroll
-          for (int k = 0; k <= KC; ++k) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], o);
-          }
-          if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k <= KC; ++k) atomicAdd(&s_acc[g][k], v[k]);
-          }
+          for (int k = NV; k < NP; ++k) v[k] = 0.0f;
+          const float r = warp_transpose_reduce<NP>(v, lane);
+          if (reducer) atomicAdd(&s_acc[g][my_value], r);
         }
       }
     }
@@ -179,7 +236,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_accumulate(
             if (k0 + k < K) atomicAdd(dst + 1 + k0 + k, s_acc[g][k + 1]);
         }
 #pragma unroll
-        for (int k = 0; k <= KC; ++k) s_acc[g][k] = 0.0f;
+        for (int k = 0; k < NV; ++k) s_acc[g][k] = 0.0f;
       }
     }
     if (__syncthreads_and(done)) break;
@@ -195,7 +252,8 @@ __global__ void __launch_bounds__(kThreads) k_blend_render(
     const uint32_t* __restrict__ tile_off, const uint64_t* __restrict__ entries, uint32_t capacity,
     const ProjRec* __restrict__ rec, int64_t n, int width, int height, int tiles_x, int tiles,
     const float* __restrict__ payload, int K, int k0, int cam0, float* __restrict__ images) {
-  __shared__ float4 s_a[kBatch], s_b[kBatch];
+  __shared__ float4 s_box[kBatch], s_par[kBatch];
+  __shared__ float s_thr[kBatch];
   __shared__ uint32_t s_id[kBatch];
   __shared__ float s_col[kBatch][KC];
   const TileCtx c = tile_ctx(tile_off, capacity, tiles, tiles_x, width, height);
@@ -209,7 +267,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_render(
   for (uint32_t start = 0; start < c.len; start += kBatch) {
     const int nb = (int)min((uint32_t)kBatch, c.len - start);
     __syncthreads();
-    load_batch(entries, c.b + start, nb, rec_cam, n, s_a, s_b, s_id);
+    load_batch(entries, c.b + start, nb, rec_cam, n, s_box, s_par, s_thr, s_id);
     __syncthreads();
     for (int idx = threadIdx.x; idx < nb * KC; idx += kThreads) {
       const int g = idx / KC, k = idx - g * KC;
@@ -218,9 +276,11 @@ __global__ void __launch_bounds__(kThreads) k_blend_render(
     __syncthreads();
     if (!__all_sync(kFull, done)) {
       for (int g = 0; g < nb && !done; ++g) {
+        const float4 box = s_box[g];
+        if (!warp_hits(box, c)) continue;
         float al, ex;
         bool cap;
-        const float w = blend_step(s_a[g], s_b[g], c.pxf, c.pyf, T, done, al, ex, cap);
+        const float w = blend_step(box, s_par[g], s_thr[g], c.pxf, c.pyf, T, done, al, ex, cap);
         if (w > 0.0f) {
 #pragma unroll
           for (int k = 0; k < KC; ++k) img[k] = fmaf(w, s_col[g][k], img[k]);
@@ -241,12 +301,28 @@ __global__ void __launch_bounds__(kThreads) k_blend_render(
 // adjoint: dL/dt and dL/do. Payload per (camera, Gaussian) = (a_0..a_{K-1}, beta).
 // ------------------------------------------------------------------------------------------
 template <int KC>
+__device__ __forceinline__ void load_payload(const float* __restrict__ pay_cam, int nb, int K, const uint32_t* s_id,
+                                             float (*s_pay)[KC + 1]) {
+  for (int idx = threadIdx.x; idx < nb * (KC + 1); idx += kThreads) {
+    const int g = idx / (KC + 1), k = idx - g * (KC + 1);
+    float v = 0.0f;
+    if (k < KC) {
+      if (k < K) v = pay_cam[(int64_t)s_id[g] * (K + 1) + k];
+    } else {
+      v = pay_cam[(int64_t)s_id[g] * (K + 1) + K];
+    }
+    s_pay[g][k] = v;
+  }
+}
+
+template <int KC>
 __global__ void __launch_bounds__(kThreads) k_blend_adjoint(
     const uint32_t* __restrict__ tile_off, const uint64_t* __restrict__ entries, uint32_t capacity,
     const ProjRec* __restrict__ rec, int64_t n, int width, int height, int tiles_x, int tiles,
     const void* __restrict__ targets, int dtype, const float* __restrict__ payload, int K, int cam0,
     float* __restrict__ grad_t, float* __restrict__ grad_o) {
-  __shared__ float4 s_a[kBatch], s_b[kBatch];
+  __shared__ float4 s_box[kBatch], s_par[kBatch];
+  __shared__ float s_thr[kBatch];
   __shared__ uint32_t s_id[kBatch];
   __shared__ float s_pay[kBatch][KC + 1];
   __shared__ float s_go[kBatch];
@@ -271,21 +347,17 @@ __global__ void __launch_bounds__(kThreads) k_blend_adjoint(
     for (uint32_t start = 0; start < c.len; start += kBatch) {
       const int nb = (int)min((uint32_t)kBatch, c.len - start);
       __syncthreads();
-      load_batch(entries, c.b + start, nb, rec_cam, n, s_a, s_b, s_id);
+      load_batch(entries, c.b + start, nb, rec_cam, n, s_box, s_par, s_thr, s_id);
       __syncthreads();
-      for (int idx = threadIdx.x; idx < nb * (KC + 1); idx += kThreads) {
-        const int g = idx / (KC + 1), k = idx - g * (KC + 1);
-        float v = 0.0f;
-        if (k < KC) { if (k < K) v = pay_cam[(int64_t)s_id[g] * (K + 1) + k]; }
-        else v = pay_cam[(int64_t)s_id[g] * (K + 1) + K];
-        s_pay[g][k] = v;
-      }
+      load_payload<KC>(pay_cam, nb, K, s_id, s_pay);
       __syncthreads();
       if (!__all_sync(kFull, done)) {
         for (int g = 0; g < nb && !done; ++g) {
+          const float4 box = s_box[g];
+          if (!warp_hits(box, c)) continue;
           float al, ex;
           bool cap;
-          const float w = blend_step(s_a[g], s_b[g], c.pxf, c.pyf, T, done, al, ex, cap);
+          const float w = blend_step(box, s_par[g], s_thr[g], c.pxf, c.pyf, T, done, al, ex, cap);
           if (w > 0.0f) {
             float gg = s_pay[g][KC];
 #pragma unroll
@@ -313,24 +385,20 @@ __global__ void __launch_bounds__(kThreads) k_blend_adjoint(
   for (uint32_t start = 0; start < c.len; start += kBatch) {
     const int nb = (int)min((uint32_t)kBatch, c.len - start);
     __syncthreads();
-    load_batch(entries, c.b + start, nb, rec_cam, n, s_a, s_b, s_id);
+    load_batch(entries, c.b + start, nb, rec_cam, n, s_box, s_par, s_thr, s_id);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nb * (KC + 1); idx += kThreads) {
-      const int g = idx / (KC + 1), k = idx - g * (KC + 1);
-      float v = 0.0f;
-      if (k < KC) { if (k < K) v = pay_cam[(int64_t)s_id[g] * (K + 1) + k]; }
-      else v = pay_cam[(int64_t)s_id[g] * (K + 1) + K];
-      s_pay[g][k] = v;
-    }
+    load_payload<KC>(pay_cam, nb, K, s_id, s_pay);
     __syncthreads();
     if (!__all_sync(kFull, done)) {
       for (int g = 0; g < nb; ++g) {
+        const float4 box = s_box[g];
+        if (!warp_hits(box, c)) continue;
         float d_o = 0.0f;
         if (!done) {
           const float Tm = T;
           float al = 0.0f, ex = 0.0f;
           bool cap = false;
-          const float w = blend_step(s_a[g], s_b[g], c.pxf, c.pyf, T, done, al, ex, cap);
+          const float w = blend_step(box, s_par[g], s_thr[g], c.pxf, c.pyf, T, done, al, ex, cap);
           if (w > 0.0f) {
             float gg = s_pay[g][KC];
 #pragma unroll
@@ -381,7 +449,8 @@ void render_chunk(const Problem& p, int cb, int cam0, int k0, const Workspace& w
 }  // namespace
 
 // Channels are processed in chunks of at most 16 per walk; the chunk width is the smallest
-// instantiated width that covers the remaining channels.
+// instantiated width that covers the remaining channels (1+KC values are reduced per Gaussian,
+// padded to a power of two).
 void launch_blend_accumulate(const Problem& p, int cb, int cam0, const void* targets, int dtype,
                              const Workspace& ws, cudaStream_t s) {
   for (int k0 = 0; k0 < p.K; k0 += 16) {
@@ -389,8 +458,8 @@ void launch_blend_accumulate(const Problem& p, int cb, int cam0, const void* tar
     if (kc == 1) accumulate_chunk<1>(p, cb, cam0, targets, dtype, k0, ws, s);
     else if (kc == 2) accumulate_chunk<2>(p, cb, cam0, targets, dtype, k0, ws, s);
     else if (kc == 3) accumulate_chunk<3>(p, cb, cam0, targets, dtype, k0, ws, s);
-    else if (kc == 4) accumulate_chunk<4>(p, cb, cam0, targets, dtype, k0, ws, s);
-    else if (kc <= 8) accumulate_chunk<8>(p, cb, cam0, targets, dtype, k0, ws, s);
+    else if (kc <= 7) accumulate_chunk<7>(p, cb, cam0, targets, dtype, k0, ws, s);
+    else if (kc <= 15) accumulate_chunk<15>(p, cb, cam0, targets, dtype, k0, ws, s);
     else accumulate_chunk<16>(p, cb, cam0, targets, dtype, k0, ws, s);
   }
 }

@@ -37,10 +37,11 @@ struct DevCam {
 };
 
 // Projected Gaussian as the blend kernels read it: 32 bytes, one sector.
-//   a = (mean_x, mean_y, conic_a, conic_b), b = (conic_c, opacity, qthr, depth key)
+//   box = (mean_x, mean_y, half-width, half-height) of the padded support box {q <= 2 ln(255 o)},
+//   par = (conic_a, conic_b, conic_c, opacity) with q = a dx^2 + 2 b dx dy + c dy^2.
 struct ProjRec {
-  float4 a;
-  float4 b;
+  float4 box;
+  float4 par;
 };
 
 // Sub-allocation of a caller workspace (every region 256-byte aligned).
@@ -50,7 +51,7 @@ struct Workspace {
   DevStatus* status = nullptr;
   DevCam* cams = nullptr;
   ProjRec* rec = nullptr;          // [cb * n]
-  uint2* rect = nullptr;           // [cb * n] packed tile rectangle (tx0|ty0<<16, tx1|ty1<<16)
+  uint4* rect = nullptr;           // [cb * n] (tx0|ty0<<16, tx1|ty1<<16, depth key bits, 0)
   uint32_t* tile_off = nullptr;    // [cb * T + 1] counts, then exclusive offsets
   uint32_t* tile_cur = nullptr;    // [cb * T]
   uint32_t* scan_tmp = nullptr;    // [scan blocks + 1]

@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(256) k_project(
     const float* __restrict__ means, const float* __restrict__ scales,
     const float* __restrict__ quats, const float* __restrict__ opac, int64_t n,
     const DevCam* __restrict__ cams, int width, int height, float near_z, int tiles_x, int tiles,
-    ProjRec* __restrict__ rec, uint2* __restrict__ rect, uint32_t* __restrict__ tile_count) {
+    ProjRec* __restrict__ rec, uint4* __restrict__ rect, uint32_t* __restrict__ tile_count) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (i >= n) return;
@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256) k_project(
   const float o = opac[i];
   const double zd = depth_f64(c, mx3, my3, mz3);
   if (!(zd > (double)near_z) || !(__dmul_rn((double)o, 255.0) >= 1.0)) {
-    rect[ji] = make_uint2(0xFFFFFFFFu, 0u);
+    rect[ji] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
     return;
   }
   const float tz = __double2float_rn(zd);
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256) k_project(
   const float mx = fmaf(c.fx, tx * iz, c.cx);
   const float my = fmaf(c.fy, ty * iz, c.cy);
   if (!(det > 0.0f) || !isfinite(mx) || !isfinite(my)) {
-    rect[ji] = make_uint2(0xFFFFFFFFu, 0u);
+    rect[ji] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
     return;
   }
   const float idet = 1.0f / det;
@@ -98,33 +98,34 @@ __global__ void __launch_bounds__(256) k_project(
   const float fx0 = fmaxf(ceilf(mx - hx - 0.5f), 0.0f), fx1 = fminf(floorf(mx + hx - 0.5f), (float)(width - 1));
   const float fy0 = fmaxf(ceilf(my - hy - 0.5f), 0.0f), fy1 = fminf(floorf(my + hy - 0.5f), (float)(height - 1));
   if (!(fx0 <= fx1) || !(fy0 <= fy1)) {
-    rect[ji] = make_uint2(0xFFFFFFFFu, 0u);
+    rect[ji] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
     return;
   }
   const int tx0 = (int)fx0 / kTile, tx1 = (int)fx1 / kTile;
   const int ty0 = (int)fy0 / kTile, ty1 = (int)fy1 / kTile;
   ProjRec r;
-  r.a = make_float4(mx, my, cc2 * idet, -cb2 * idet);
-  r.b = make_float4(ca2 * idet, o, qthr, tz);
+  r.box = make_float4(mx, my, hx, hy);
+  r.par = make_float4(cc2 * idet, -cb2 * idet, ca2 * idet, o);
   rec[ji] = r;
-  rect[ji] = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16));
+  rect[ji] = make_uint4((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16),
+                        __float_as_uint(tz), 0u);
   uint32_t* base = tile_count + (int64_t)j * tiles;
   for (int ty = ty0; ty <= ty1; ++ty)
     for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(base + ty * tiles_x + tx, 1u);
 }
 
 __global__ void __launch_bounds__(256) k_scatter(
-    int64_t n, const ProjRec* __restrict__ rec, const uint2* __restrict__ rect, int tiles_x, int tiles,
+    int64_t n, const uint4* __restrict__ rect, int tiles_x, int tiles,
     const uint32_t* __restrict__ tile_off, uint32_t* __restrict__ tile_cur, uint64_t* __restrict__ entries,
     uint32_t capacity, DevStatus* status) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (i >= n) return;
   const int64_t ji = (int64_t)j * n + i;
-  const uint2 rc = rect[ji];
+  const uint4 rc = rect[ji];
   const int tx0 = rc.x & 0xFFFF, ty0 = rc.x >> 16, tx1 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
   if (rc.x == 0xFFFFFFFFu) return;
-  const uint64_t key = ((uint64_t)__float_as_uint(rec[ji].b.w) << 32) | (uint64_t)(uint32_t)i;
+  const uint64_t key = ((uint64_t)rc.z << 32) | (uint64_t)(uint32_t)i;
   bool overflow = false;
   for (int ty = ty0; ty <= ty1; ++ty)
     for (int tx = tx0; tx <= tx1; ++tx) {
@@ -244,7 +245,7 @@ void launch_scan(const Problem& p, int cb, const Workspace& ws, cudaStream_t s) 
 
 void launch_scatter(const Problem& p, int cb, const Workspace& ws, cudaStream_t s) {
   dim3 grid((unsigned)((p.n + 255) / 256), (unsigned)cb);
-  k_scatter<<<grid, 256, 0, s>>>(p.n, ws.rec, ws.rect, p.tiles_x, p.tiles, ws.tile_off, ws.tile_cur,
+  k_scatter<<<grid, 256, 0, s>>>(p.n, ws.rect, p.tiles_x, p.tiles, ws.tile_off, ws.tile_cur,
                                  ws.entries, p.capacity, ws.status);
   note_launches(1);
 }
