@@ -152,6 +152,31 @@ ICGS_API icgs_status icgs_render(const icgs_scene* scene, const icgs_cameras* ca
                         int32_t channels, const float* coeffs, int64_t instance_capacity,
                         void* workspace, size_t workspace_bytes, float* images_out, void* stream);
 
+/* Colorize without a caller workspace -- no counterpart in the paper; this is a library service.
+ *
+ * For callers that cannot allocate device memory: a plugin inside an application that owns every
+ * byte of device memory through its own allocator, or a latency-critical loop that may not
+ * allocate (or risk failing to) once it runs. Such callers cannot hand icgs_colorize a workspace,
+ * so this call takes it from a fixed scratch array of icgs_noalloc_scratch_bytes() (64 MiB) that
+ * the library places on every GPU that loads it and keeps until the process exits. It allocates
+ * nothing itself; inputs, outputs and `stream` are as for icgs_colorize, and so are the results.
+ *   - The first call on a device resolves the scratch's device address for that device; make that
+ *     first call before any stream capture.
+ *   - A problem whose workspace does not fit returns ICGS_ERR_WORKSPACE_TOO_SMALL (or
+ *     ICGS_ERR_CAPACITY when the Gaussian-tile instances of one pass do not fit), with a message
+ *     naming the limit; use icgs_colorize with a caller workspace then. opt->instance_capacity <= 0
+ *     gives the instance buffers all the scratch the other regions leave free.
+ *   - Every call on a device shares the one array and leaves its contents behind (each call
+ *     clears what must start at zero). Calls that overlap on the GPU -- on two streams, or from
+ *     two host threads -- race on it and must not be issued. */
+ICGS_API icgs_status icgs_colorize_noalloc(const icgs_scene* scene, const icgs_cameras* cams,
+                                           const icgs_targets* targets, const icgs_options* opt,
+                                           float* coeffs_out, uint8_t* status_out, float* chol_out,
+                                           void* stream);
+
+/* Size in bytes of the built-in scratch icgs_colorize_noalloc works in. */
+ICGS_API size_t icgs_noalloc_scratch_bytes(void);
+
 /* Message of the last failed call on this host thread ("" if none). */
 ICGS_API const char* icgs_last_error(void);
 

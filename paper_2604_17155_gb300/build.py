@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libicgs.so")
-SOURCES = ["api.cu", "project.cu", "tilesort.cu", "blend.cu", "solve.cu"]
+SOURCES = ["api.cu", "project.cu", "tilesort.cu", "blend.cu", "solve.cu", "noalloc.cu"]
 HEADERS = ["icgs_internal.h", "icgs_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

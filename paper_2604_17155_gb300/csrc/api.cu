@@ -279,6 +279,13 @@ icgs_status lambda_of(const icgs_options* opt, int L, float* lam) {
 
 void icgs::note_launches(int count) { g_launches += count; }
 
+void icgs::set_error_message(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
 extern "C" {
 
 size_t icgs_workspace_size(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,

@@ -89,6 +89,9 @@ struct Problem {
 // Kernel launches of the current call on this host thread (for the benchmark's launch count).
 void note_launches(int count);
 
+// Replaces the message icgs_last_error() returns on this host thread (printf-style).
+void set_error_message(const char* fmt, ...);
+
 // ---- launchers (each .cu file exposes host functions that enqueue its kernels) ----
 void launch_project(const Problem& p, const float* means, const float* scales, const float* quats,
                     const float* opac, int cb, const Workspace& ws, cudaStream_t s);

@@ -82,6 +82,10 @@ def load(path: str = LIB_PATH):
     lib.icgs_last_required_instances.restype = ctypes.c_int64
     lib.icgs_last_stats.argtypes = [P]
     lib.icgs_last_stats.restype = None
+    lib.icgs_colorize_noalloc.argtypes = [P, P, P, P, P, P, P, P]
+    lib.icgs_colorize_noalloc.restype = ctypes.c_int
+    lib.icgs_noalloc_scratch_bytes.argtypes = []
+    lib.icgs_noalloc_scratch_bytes.restype = S
     lib.icgs_set_stage_timing.argtypes = [ctypes.c_int]
     lib.icgs_set_stage_timing.restype = None
     lib.icgs_last_stage_ms.argtypes = [P, ctypes.c_int]
@@ -272,6 +276,30 @@ def colorize(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, precisio
                                  _stream_ptr(dev))
 
     _run_with_capacity(dev, size_fn, call_fn, instance_capacity)
+    return coeffs, status, chol
+
+
+def colorize_noalloc(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, precision="mixed",
+                     cond_tau=0.0, cam_batch=0, instance_capacity=0, opacity=None):
+    """Like colorize(), but the library works in its own built-in device scratch instead of a
+    workspace, for callers that cannot allocate device memory (see icgs_colorize_noalloc in
+    include/icgs.h). The outputs are still the caller's tensors; problems larger than the scratch
+    raise IcgsError with ERR_WORKSPACE_TOO_SMALL or ERR_CAPACITY."""
+    torch = _torch()
+    lib = load()
+    dev = targets.device
+    B = (sh_degree + 1) ** 2
+    K = int(targets.shape[-1])
+    coeffs = torch.empty((scene.n, B, K), dtype=torch.float32, device=dev)
+    status = torch.empty((scene.n,), dtype=torch.uint8, device=dev)
+    chol = torch.empty((scene.n, B * (B + 1) // 2), dtype=torch.float32, device=dev)
+    sc = scene._struct(opacity)
+    cm = cams._struct()
+    tg = _targets_struct(targets)
+    o, _keep = _options(sh_degree, lam, precision, cond_tau, cam_batch, instance_capacity)
+    _check(lib.icgs_colorize_noalloc(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(o),
+                                     ctypes.c_void_p(coeffs.data_ptr()), ctypes.c_void_p(status.data_ptr()),
+                                     ctypes.c_void_p(chol.data_ptr()), _stream_ptr(dev)))
     return coeffs, status, chol
 
 
