@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--cpu-sample-cams", type=int, default=0, help="cameras in the oracle sample (0: host cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cams", type=int, default=0, help="profiling only: use the first N cameras of the rig")
+    ap.add_argument("--workload", default="relight", choices=["relight", "features", "segmentation", "segmentation_rgb"],
+                    help="relight (the headline); the others document the feature / mask / large-RGB workloads")
     return ap.parse_args()
 
 
@@ -140,13 +142,54 @@ def oracle_sample_ms_per_scene(scene, cams, targets_host_fn, n_sample, threads):
 
 
 # ------------------------------------------------------------------------------------------
-def make_workload(n_cams=0):
-    scene = W.make_scene(WORKLOAD, SEED)
-    cams = W.make_cameras(WORKLOAD)
+def make_workload(n_cams=0, workload=WORKLOAD):
+    name = {"relight": "relight", "features": "features", "segmentation": "segmentation",
+            "segmentation_rgb": "segmentation"}[workload]
+    seed = {"relight": SEED, "features": 3000, "segmentation": 4000, "segmentation_rgb": 4000}[workload]
+    scene = W.make_scene(name, seed)
+    cams = W.make_cameras(name)
     if n_cams:
         cams = cams.subset(np.arange(min(n_cams, cams.n)))
-    coeffs = W.sh_coefficients(scene.n, 3, 3, SEED + 1)
+    coeffs = W.sh_coefficients(scene.n, 3, 3, seed + 1)
     return scene, cams, coeffs
+
+
+def device_fourier_fields(n_views, height, width, channels, seed, dev, n_modes=32, max_freq=4.0):
+    """The smooth unit-variance field recipe of workloads.fourier_fields, evaluated on the device
+    (the 64-channel feature targets are 14 GB): sqrt(2/n_modes) sum_q cos(2 pi (a x/W + b y/H) + phi)."""
+    import torch
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    out = torch.empty((n_views, height, width, channels), dtype=torch.bfloat16, device=dev)
+    xs = (torch.arange(width, device=dev, dtype=torch.float32) + 0.5) / width
+    ys = (torch.arange(height, device=dev, dtype=torch.float32) + 0.5) / height
+    amp = math.sqrt(2.0 / n_modes)
+    for v in range(n_views):
+        a = (torch.rand((channels, n_modes), generator=g) * 2 - 1) * max_freq
+        b = (torch.rand((channels, n_modes), generator=g) * 2 - 1) * max_freq
+        ph = torch.rand((channels, n_modes), generator=g) * 2 * math.pi
+        a, b, ph = a.to(dev), b.to(dev), ph.to(dev)
+        u = 2 * math.pi * a[:, :, None] * xs[None, None, :] + ph[:, :, None]       # [K,Q,W]
+        w = 2 * math.pi * b[:, :, None] * ys[None, None, :]                        # [K,Q,H]
+        f = torch.einsum("kqh,kqw->hwk", torch.cos(w), torch.cos(u)) - torch.einsum("kqh,kqw->hwk", torch.sin(w), torch.sin(u))
+        out[v] = (amp * f).to(torch.bfloat16)
+    return out
+
+
+def make_targets(workload, scene, cams, coeffs, gs, gc, dev, icgs):
+    """Device-resident targets of each workload and its (L, lambda)."""
+    import torch
+    if workload in ("relight", "segmentation_rgb"):
+        return icgs.render(gs, gc, torch.tensor(coeffs, device=dev), 3), 3
+    if workload == "features":
+        return device_fourier_fields(cams.n, cams.height, cams.width, 64, 3002, dev), 0
+    # segmentation: one-hot labels of a 16-cell Voronoi partition, rendered per view, argmax -> FP16
+    labels = W.voronoi_labels(scene.means, 16, 4002, W.WORKLOADS["segmentation"]["radius"])
+    img = icgs.render(gs, gc, torch.tensor(W.one_hot_dc(labels, 16), device=dev), 0)
+    t = torch.empty(img.shape, dtype=torch.float16, device=dev)
+    for v in range(img.shape[0]):  # per view, to keep the int64 temporaries small
+        t[v] = torch.nn.functional.one_hot(img[v].argmax(-1), 16).to(torch.float16)
+    del img
+    return t, 0
 
 
 def run_reference(args, rank, world):
@@ -192,13 +235,14 @@ def run_icgs(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    scene, cams, coeffs = make_workload(args.cams)
+    scene, cams, coeffs = make_workload(args.cams, args.workload)
     gs = icgs.Scene.from_workload(scene, dev)
     gc = icgs.Cameras.from_workload(cams)
-    L = 3
     with torch.no_grad():
-        targets = icgs.render(gs, gc, torch.tensor(coeffs, device=dev), L)  # [100,800,800,3] f32, 768 MB
+        targets, L = make_targets(args.workload, scene, cams, coeffs, gs, gc, dev, icgs)
     torch.cuda.synchronize(dev)
+    K = int(targets.shape[-1])
+    B = (L + 1) ** 2
     target_bytes = targets.numel() * targets.element_size()
 
     def step():
@@ -242,7 +286,7 @@ def run_icgs(args, rank, world, local_rank):
     # ---- end to end through host buffers ----
     host_t = torch.empty(targets.shape, dtype=targets.dtype, pin_memory=True)
     host_t.copy_(targets)
-    host_c = torch.empty((scene.n, 16, 3), dtype=torch.float32, pin_memory=True)
+    host_c = torch.empty((scene.n, B, K), dtype=torch.float32, pin_memory=True)
     dev_t = torch.empty_like(targets)
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -283,21 +327,23 @@ def run_icgs(args, rank, world, local_rank):
     blend_ms = stage_ms.get("blend", float("nan"))
     pairs = stats["contrib_pairs"]
     inst = stats["instances"]
-    K = 3
     # algorithmic work of the blend-accumulate kernel per launch (one launch per scene here):
     # per contributing pair: weight (~15 FP32 ops + 1 exp) and accumulation 2(1+K)
     flops = pairs * (15 + 2 * (1 + K))
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6
     achieved_tflops = flops / (blend_ms * 1e-3) / 1e12
-    bytes_alg = target_bytes + inst * (8 + 32) + cams.n * scene.n * (1 + K) * 4 * 2
-    roof = {"kernel": "k_blend_accumulate<3>", "bound": "alu", "achieved": achieved_tflops,
+    acc_rows = scene.n * (1 if L == 0 else cams.n)
+    bytes_alg = target_bytes + inst * (8 + 32) + acc_rows * (1 + K) * 4 * 2
+    tc = args.precision == "mixed" and K >= 16 and targets.dtype != torch.float32
+    kname = f"k_blend_accumulate_tc<{16 if K <= 16 else 32 if K <= 32 else 64}>" if tc else f"k_blend_accumulate<{min(K, 16)}>"
+    roof = {"kernel": kname, "bound": "alu", "achieved": achieved_tflops,
             "peak": fp32_peak / 1e12, "unit": "TFLOP/s", "frac": achieved_tflops / (fp32_peak / 1e12),
             "traffic": None, "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {pk['sm_max_mhz']:.0f} MHz",
             "hbm_view": {"algorithmic_bytes": bytes_alg, "achieved_gbs": bytes_alg / (blend_ms * 1e-3) / 1e9,
                          "peak_gbs": pk["hbm_gbs"], "frac": bytes_alg / (blend_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
                          "peak_source": pk["source"]}}
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and args.workload == "relight":
         cores = os.cpu_count() or 1
         n_sample = args.cpu_sample_cams or min(cores, 16)
 
@@ -316,13 +362,14 @@ def run_icgs(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": ms_scene, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_max / args.steps, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"relight: 200k Gaussians (40 clusters, r=4), {cams.n} cameras 800x800 fov 45, L=3, RGB f32",
+        "dtype": "f32" if targets.dtype == torch.float32 else ("f16" if tc else "f32"), "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {scene.n} Gaussians, {cams.n} cameras {cams.width}x{cams.height}, "
+                               f"L={L}, {K} channels {str(targets.dtype).replace('torch.', '')}",
                    "precision": args.precision, "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2 ({target_bytes / 1e6:.0f} MB of targets per step)"},
         "roofline": roof,
         "e2e": {"value": e2e_max / (args.steps * world), "unit": UNIT, "h2d_bytes_per_step": target_bytes,
-                "d2h_bytes_per_step": scene.n * 16 * 3 * 4},
+                "d2h_bytes_per_step": scene.n * B * K * 4},
         "cpu_baseline": cpu,
         "clocks": clocks,
         "gpu_launches": stats["launches"] * args.steps,

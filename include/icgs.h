@@ -60,7 +60,9 @@ typedef enum {
   ICGS_ERR_CAPACITY = -4,             /* more (Gaussian, tile) instances than the workspace was sized
                                          for; icgs_last_required_instances() gives the count to pass
                                          as icgs_options.instance_capacity */
-  ICGS_ERR_UNSUPPORTED = -5           /* valid request this build does not implement */
+  ICGS_ERR_UNSUPPORTED = -5,          /* valid request this build does not implement */
+  ICGS_ERR_DEVICE_TIMEOUT = -6        /* a bounded wait inside a kernel gave up (the kernel freed its
+                                         resources and returned; results are unspecified) */
 } icgs_status;
 
 typedef enum { ICGS_F32 = 0, ICGS_BF16 = 1, ICGS_F16 = 2 } icgs_dtype;
@@ -176,6 +178,13 @@ ICGS_API icgs_status icgs_colorize_noalloc(const icgs_scene* scene, const icgs_c
 
 /* Size in bytes of the built-in scratch icgs_colorize_noalloc works in. */
 ICGS_API size_t icgs_noalloc_scratch_bytes(void);
+
+/* Diagnostic: D[128 x N] = A[128 x 256] * B[N x 256]^T through the tensor-core (tcgen05) operand
+ * layout, MMA issue and TMEM read-back that the 16-bit accumulate walk uses. A and B are device,
+ * row-major 16-bit (bf16 != 0: BF16, else FP16), D device float32 [128 x N]; N is 32 or 80;
+ * workspace is device memory of at least 256 bytes. Synchronises `stream`. */
+ICGS_API icgs_status icgs_selftest_tc(const void* A, const void* B, int32_t N, int32_t bf16, float* D,
+                                      void* workspace, void* stream);
 
 /* Message of the last failed call on this host thread ("" if none). */
 ICGS_API const char* icgs_last_error(void);

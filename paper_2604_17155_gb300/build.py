@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libicgs.so")
-SOURCES = ["api.cu", "project.cu", "tilesort.cu", "blend.cu", "solve.cu", "noalloc.cu"]
-HEADERS = ["icgs_internal.h", "icgs_device.cuh"]
+SOURCES = ["api.cu", "project.cu", "tilesort.cu", "blend.cu", "contract_tc.cu", "solve.cu", "noalloc.cu"]
+HEADERS = ["icgs_internal.h", "icgs_device.cuh", "walk.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -111,7 +111,7 @@ Workspace carve(char* base, const Problem& p, int need) {
   ws.entries_tmp = reinterpret_cast<uint64_t*>(take(sizeof(uint64_t) * (size_t)p.capacity));
   const size_t B = (size_t)p.B, K = (size_t)p.K, n = (size_t)p.n;
   if (need & kNeedAccumulate) {
-    ws.acc = reinterpret_cast<float*>(take(sizeof(float) * (p.L == 0 ? n : (size_t)cbn) * (1 + K)));
+    ws.acc = reinterpret_cast<float*>(take(sizeof(float) * (p.L == 0 ? n : (size_t)cbn) * (size_t)p.acc_stride));
     if (p.L > 0) {
       const bool mixed = p.precision == ICGS_PRECISION_MIXED;
       ws.G = reinterpret_cast<float*>(take(sizeof(float) * n * B * B));
@@ -170,6 +170,7 @@ icgs_status setup(const icgs_scene* sc, const icgs_cameras* cams, int K, int L, 
   p.tiles_y = (p.height + kTile - 1) / kTile;
   p.tiles = p.tiles_x * p.tiles_y;
   p.K = K;
+  p.acc_stride = (1 + K + 3) & ~3;
   p.L = L;
   p.B = (L + 1) * (L + 1);
   p.precision = precision;
@@ -243,6 +244,8 @@ icgs_status finish(const Workspace& ws, cudaStream_t s) {
   ICGS_TRY_CUDA(cudaStreamSynchronize(s));
   g_timer.collect();
   g_required = (int64_t)st.instances_needed;
+  if (st.flags & kFlagTimeout)
+    return fail(ICGS_ERR_DEVICE_TIMEOUT, "a bounded wait for the tensor-core MMAs gave up");
   if (st.flags & kFlagOverflow)
     return fail(ICGS_ERR_CAPACITY, "a pass needed %lld (Gaussian, tile) instances; pass at least that as "
                 "icgs_options.instance_capacity", (long long)st.instances_needed);
@@ -322,13 +325,13 @@ icgs_status icgs_colorize(const icgs_scene* scene, const icgs_cameras* cams, con
   if (p.n == 0) return ICGS_OK;
   if ((st = upload_common(p, cams, lam, ws, s)) != ICGS_OK) return st;
   if (p.L == 0)
-    ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)p.n * (1 + p.K), s));
+    ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)p.n * p.acc_stride, s));
   for (int cam0 = 0; cam0 < p.n_cams; cam0 += p.cam_batch) {
     const int cb = std::min(p.cam_batch, p.n_cams - cam0);
     Workspace wp = ws;
     wp.cams = ws.cams + cam0;
     if (p.L > 0)
-      ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)cb * (size_t)p.n * (1 + p.K), s));
+      ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)cb * (size_t)p.n * p.acc_stride, s));
     if ((st = bin_pass(p, scene, cb, wp, s)) != ICGS_OK) return st;
     launch_blend_accumulate(p, cb, cam0, targets->data, (int)targets->dtype, wp, s);
     g_timer.mark(kBlend, s);
@@ -428,6 +431,21 @@ icgs_status icgs_render(const icgs_scene* scene, const icgs_cameras* cams, int32
     launch_blend_render(p, cb, cam0, wp, images_out, s);
     g_timer.mark(kBlend, s);
   }
+  return finish(ws, s);
+}
+
+icgs_status icgs_selftest_tc(const void* A, const void* B, int32_t N, int32_t bf16, float* D, void* workspace,
+                             void* stream) {
+  g_err[0] = '\0';
+  if (!A || !B || !D || !workspace) return fail(ICGS_ERR_INVALID_ARG, "A, B, D and workspace are required");
+  if (N != 32 && N != 80) return fail(ICGS_ERR_INVALID_ARG, "N = %d must be 32 or 80", N);
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(ICGS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Workspace ws;
+  ws.status = static_cast<DevStatus*>(workspace);
+  ICGS_TRY_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(DevStatus), s));
+  ICGS_TRY_CUDA(launch_tc_selftest(static_cast<const uint16_t*>(A), static_cast<const uint16_t*>(B), N, bf16 != 0, D,
+                                   ws.status, s));
   return finish(ws, s);
 }
 

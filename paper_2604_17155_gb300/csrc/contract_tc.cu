@@ -1,0 +1,410 @@
+// contract_tc.cu -- the blend-accumulate walk (Eq. 4-6) with its per-tile contraction on the
+// 5th-generation tensor cores (tcgen05), for 16-bit targets with 16..64 channels.
+//
+// Per tile and batch of G = 128 Gaussians (the MMA's M), the S terms of Eq. 6 summed over the tile's
+// 256 pixels form a dense product
+//     D[g][n] = sum_p W[g][p] * B[n][p],   W[g][p] = alpha T of Gaussian g at pixel p (Eq. 4),
+// with B's rows 0..KT-1 the tile's target channels and rows KT..KT+15 all ones, so that the same
+// product also yields V = sum_p W[g][p] (Eq. 5). The threads evaluate W exactly like the CUDA-core
+// walk (walk.cuh) and store it as FP16 into a K-major, 128-byte-swizzled shared-memory operand; the
+// tile's targets (BF16 or FP16) are transposed once into B as FP16. Both operands are scaled by
+// powers of two -- W by 2^14, the targets so that the tile's largest magnitude lands in
+// [2^14, 2^15) -- which makes every BF16 target exact in FP16, keeps small weights out of FP16's
+// subnormal range, and is undone exactly in the epilogue. One thread issues 16
+// tcgen05.mma (kind::f16, M=128, N=KT+16, K=16, FP32 accumulation in TMEM) and commits them to an
+// mbarrier; warps 0-3 then read D back with tcgen05.ld (one Gaussian per thread) and add
+// (V, S_0..S_{KT-1}) to the accumulator with float4 atomics -- one atomic group per (Gaussian, tile).
+//
+// Every wait on the mbarrier is bounded: after kSpinLimit polls the kernel sets kFlagTimeout in the
+// status block (reported as ICGS_ERR_DEVICE_TIMEOUT), waits once more (also bounded) for the MMAs it
+// issued, frees its TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "icgs_device.cuh"
+#include "icgs_internal.h"
+#include "walk.cuh"
+
+namespace icgs {
+
+namespace {
+
+using namespace walk;
+
+constexpr int kG = 128;                 // Gaussians per batch (MMA M)
+constexpr int kKPix = 256;              // pixels per tile (MMA K in total, 16 instructions of 16)
+constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr uint32_t kTmemCols = 128;     // power of two >= KT + 16 for KT <= 64
+
+// ---- inline PTX ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(mbar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; returns false (and the caller reports a timeout) after kSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t parity) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it)
+    if (mbar_try_wait(mbar, parity)) return true;
+  return false;
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, both operands K-major, kind::f16 (BF16 or FP16 in, FP32 out)
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrive on the mbarrier once every MMA this thread issued has completed.
+__device__ __forceinline__ void umma_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+               : "memory");
+}
+// 16 consecutive 32-bit columns of this warp's 32 TMEM lanes (one lane per thread).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ---- operand layout -------------------------------------------------------------------------
+// A [rows x 256] 16-bit matrix stored K-major with the 128-byte swizzle: four K blocks of 64
+// elements, each block rows x 128 bytes, rows grouped by 8 into 1024-byte atoms, and the 16-byte
+// chunk index of each row XOR-ed with the row's index inside its atom.
+__device__ __forceinline__ uint32_t kmajor_sw128(int row, int k, int rows) {
+  return (uint32_t)((k >> 6) * (rows * 128) + (row >> 3) * 1024 + (row & 7) * 128 +
+                    ((((k & 63) >> 3) ^ (row & 7)) << 4) + ((k & 7) << 1));
+}
+
+// Shared-memory matrix descriptor (tcgen05 format): start address >> 4 in bits 0-13, leading byte
+// offset >> 4 in bits 16-29 (unused for swizzled K-major; 1 by convention), stride byte offset
+// >> 4 in bits 32-45 (1024 B between 8-row atoms), descriptor version 1 in bits 46-47, layout type
+// in bits 61-63 (2 = 128-byte swizzle).
+__device__ __forceinline__ uint64_t desc_kmajor_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor of kind::f16: D format F32 (bits 4-5 = 1), A and B format (bits 7-9,
+// 10-12: 0 = F16, 1 = BF16), both K-major (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in
+// bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool bf16) {
+  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+constexpr int kWScaleExp = 14;  // W is stored as W * 2^14 (W < 1)
+
+__device__ __forceinline__ uint16_t half_bits(float x) { return __half_as_ushort(__float2half_rn(x)); }
+__device__ __forceinline__ float target_value(uint16_t raw, bool bf16) {
+  return bf16 ? __uint_as_float((uint32_t)raw << 16) : __half2float(__ushort_as_half(raw));
+}
+
+// Issues the 16 MMAs of one batch (K = 256 pixels) and commits them to mbar.
+template <int NB>
+__device__ __forceinline__ void issue_batch(uint32_t a_addr, uint32_t b_addr, uint32_t d_tmem, uint32_t idesc,
+                                            uint64_t* mbar) {
+  tc_fence_after();
+#pragma unroll
+  for (int ks = 0; ks < kKPix / 16; ++ks) {
+    const int kb = ks >> 2, kk = ks & 3;
+    const uint64_t ad = desc_kmajor_sw128(a_addr + kb * (kG * 128) + kk * 32);
+    const uint64_t bd = desc_kmajor_sw128(b_addr + kb * (NB * 128) + kk * 32);
+    umma_f16(d_tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+  }
+  umma_commit(mbar);
+}
+
+// ---- self-test: D[128 x N] = A[128 x 256] B[N x 256]^T through the same layout and MMA path ----
+template <int NB, bool BF16>
+__global__ void __launch_bounds__(256) k_tc_selftest(const uint16_t* __restrict__ A, const uint16_t* __restrict__ Bm,
+                                                     float* __restrict__ D, DevStatus* status) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  uint8_t* A_s = base;
+  uint8_t* B_s = base + kG * kKPix * 2;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(B_s + NB * kKPix * 2);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+  for (int e = threadIdx.x; e < kG * kKPix; e += blockDim.x) {
+    const int m = e / kKPix, k = e % kKPix;
+    *reinterpret_cast<uint16_t*>(A_s + kmajor_sw128(m, k, kG)) = A[e];
+  }
+  for (int e = threadIdx.x; e < NB * kKPix; e += blockDim.x) {
+    const int nn = e / kKPix, k = e % kKPix;
+    *reinterpret_cast<uint16_t*>(B_s + kmajor_sw128(nn, k, NB)) = Bm[e];
+  }
+  if (threadIdx.x == 0) mbar_init(mbar, 1);
+  if (threadIdx.x < 32) {
+    tmem_alloc(tmem_slot, kTmemCols);
+    tmem_relinquish();
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  if (threadIdx.x == 0) issue_batch<NB>(smem_u32(A_s), smem_u32(B_s), tmem, idesc_f16(kG, NB, BF16), mbar);
+  const bool ok = mbar_wait_bounded(mbar, 0);
+  if (!ok && (threadIdx.x & 31) == 0) atomicOr(&status->flags, kFlagTimeout);
+  tc_fence_after();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < 4 && ok) {
+#pragma unroll
+    for (int c0 = 0; c0 < NB; c0 += 16) {
+      uint32_t r[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+      tmem_wait_ld();
+#pragma unroll
+      for (int q = 0; q < 16; ++q) D[(warp * 32 + lane) * NB + c0 + q] = __uint_as_float(r[q]);
+    }
+  }
+  if (!ok) mbar_wait_bounded(mbar, 0);
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// ---- the accumulate walk with the tensor-core contraction --------------------------------------
+template <int KT, bool BF16_TARGETS>
+__global__ void __launch_bounds__(256, 2) k_blend_accumulate_tc(
+    const uint32_t* __restrict__ tile_off, const uint64_t* __restrict__ entries, uint32_t capacity,
+    const ProjRec* __restrict__ rec, int64_t n, int width, int height, int tiles_x, int tiles,
+    const uint16_t* __restrict__ targets, int K, int cam0, float* __restrict__ acc, int RS,
+    int64_t acc_cam_stride, DevStatus* status) {
+  constexpr int NB = KT + 16;  // target channels + 16 rows of ones (V)
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  uint8_t* A_s = base;                                 // kG x 256, 64 KB
+  uint8_t* B_s = base + kG * kKPix * 2;                // NB x 256
+  float4* s_box = reinterpret_cast<float4*>(B_s + NB * kKPix * 2);
+  float4* s_par = s_box + kG;
+  float* s_thr = reinterpret_cast<float*>(s_par + kG);
+  uint32_t* s_id = reinterpret_cast<uint32_t*>(s_thr + kG);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(s_id + kG);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+  uint32_t* s_tmax = tmem_slot + 1;  // [8]
+
+  const TileCtx c = tile_ctx(tile_off, capacity, tiles, tiles_x, width, height);
+  if (c.len == 0) return;  // uniform: nothing binned to this tile
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tx0 = (c.t % tiles_x) * kTile, ty0 = (c.t / tiles_x) * kTile;
+  const int p = (c.py - ty0) * kTile + (c.px - tx0);  // this thread's pixel index in the tile (MMA k)
+
+  // B: the tile's targets, transposed to [channel][pixel] and scaled by 2^s (the tile's largest
+  // magnitude in [2^14, 2^15)), then 16 rows of ones
+  float t_scale_inv;
+  {
+    const uint16_t* src = targets + ((((int64_t)(cam0 + c.j) * height + c.py) * width + c.px) * K);
+    float tmax = 0.0f;
+    for (int k = 0; k < KT; ++k)
+      if (c.inside && k < K) tmax = fmaxf(tmax, fabsf(target_value(src[k], BF16_TARGETS)));
+    // non-negative floats order like their bit patterns
+    uint32_t m = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(tmax));
+    if (lane == 0) s_tmax[warp] = m;
+    __syncthreads();
+    m = s_tmax[0];
+#pragma unroll
+    for (int w2 = 1; w2 < 8; ++w2) m = max(m, s_tmax[w2]);
+    const float gmax = __uint_as_float(m);
+    int e = 0;
+    if (gmax > 0.0f && isfinite(gmax)) frexpf(gmax, &e);  // gmax in [2^(e-1), 2^e)
+    const int sexp = gmax > 0.0f ? 15 - e : 0;           // gmax * 2^sexp in [2^14, 2^15)
+    t_scale_inv = ldexpf(1.0f, -(sexp + kWScaleExp));
+#pragma unroll 8
+    for (int k = 0; k < KT; ++k) {
+      const float v = (c.inside && k < K) ? ldexpf(target_value(src[k], BF16_TARGETS), sexp) : 0.0f;
+      *reinterpret_cast<uint16_t*>(B_s + kmajor_sw128(k, p, NB)) = half_bits(v);
+    }
+#pragma unroll
+    for (int k = KT; k < NB; ++k) *reinterpret_cast<uint16_t*>(B_s + kmajor_sw128(k, p, NB)) = (uint16_t)0x3C00u;
+  }
+  const float v_scale_inv = ldexpf(1.0f, -kWScaleExp);
+  if (threadIdx.x == 0) mbar_init(mbar, 1);
+  if (warp == 0) {
+    tmem_alloc(tmem_slot, kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t a_addr = smem_u32(A_s), b_addr = smem_u32(B_s);
+  constexpr uint32_t kIdesc = idesc_f16(kG, NB, false);
+  const ProjRec* rec_cam = rec + (int64_t)c.j * n;
+  float* acc_cam = acc + (int64_t)c.j * acc_cam_stride;
+  float T = 1.0f;
+  bool done = !c.inside;
+  uint32_t npairs = 0, phase = 0;
+  bool timed_out = false;
+  for (uint32_t start = 0; start < c.len; start += kG) {
+    const int nb = (int)min((uint32_t)kG, c.len - start);
+    load_batch(entries, c.b + start, nb, rec_cam, n, s_box, s_par, s_thr, s_id);
+    __syncthreads();
+    // W column of this pixel: the weight of every Gaussian of the batch (0 where it does not blend)
+    for (int g = 0; g < kG; ++g) {
+      float w = 0.0f;
+      if (g < nb && !done) {
+        const float4 box = s_box[g];
+        if (warp_hits(box, c)) {
+          float al, ex;
+          bool cap;
+          w = blend_step(box, s_par[g], s_thr[g], c.pxf, c.pyf, T, done, al, ex, cap);
+          npairs += w > 0.0f;
+        }
+      }
+      *reinterpret_cast<uint16_t*>(A_s + kmajor_sw128(g, p, kG)) = half_bits(ldexpf(w, kWScaleExp));
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0) issue_batch<NB>(a_addr, b_addr, tmem, kIdesc, mbar);
+    const bool ok = mbar_wait_bounded(mbar, phase);
+    phase ^= 1u;
+    tc_fence_after();
+    if (warp < 4 && ok) {
+      const int g = warp * 32 + lane;
+      const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+      uint32_t vr[16];
+      tmem_ld16(trow + (uint32_t)KT, vr);  // the ones block: every column holds V
+      float v[KT + 4];
+      {
+        uint32_t r[16];
+#pragma unroll
+        for (int c0 = 0; c0 < KT; c0 += 16) {
+          tmem_ld16(trow + (uint32_t)c0, r);
+          tmem_wait_ld();
+#pragma unroll
+          for (int q = 0; q < 16; ++q) v[1 + c0 + q] = __uint_as_float(r[q]) * t_scale_inv;
+        }
+      }
+      tmem_wait_ld();
+      v[0] = __uint_as_float(vr[0]) * v_scale_inv;
+#pragma unroll
+      for (int q = KT + 1; q < KT + 4; ++q) v[q] = 0.0f;
+      if (g < nb && v[0] > 0.0f) {
+        float* dst = acc_cam + (int64_t)s_id[g] * RS;
+#pragma unroll
+        for (int q = 0; q < (KT + 4) / 4; ++q)
+          if (4 * q < RS) atomicAdd(reinterpret_cast<float4*>(dst + 4 * q), make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+      }
+    }
+    if (!ok) timed_out = true;
+    tc_fence_before();
+    if (__syncthreads_or(timed_out)) {
+      if ((threadIdx.x & 31) == 0) atomicOr(&status->flags, kFlagTimeout);
+      mbar_wait_bounded(mbar, phase ^ 1u);  // give the outstanding MMAs a last chance to finish
+      break;
+    }
+    if (__syncthreads_and(done)) break;
+  }
+  const uint32_t warp_sum = __reduce_add_sync(0xFFFFFFFFu, npairs);
+  if (lane == 0 && warp_sum) atomicAdd((unsigned long long*)&status->contrib_pairs, (unsigned long long)warp_sum);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+template <int NB>
+constexpr size_t selftest_smem() {
+  return 1024 + (size_t)kG * kKPix * 2 + (size_t)NB * kKPix * 2 + 16;
+}
+template <int KT>
+constexpr size_t tc_smem() {
+  return 1024 + (size_t)kG * kKPix * 2 + (size_t)(KT + 16) * kKPix * 2 + (size_t)kG * (16 + 16 + 4 + 4) + 64;
+}
+
+template <int KT, bool BF16_TARGETS>
+void accumulate_tc(const Problem& p, int cb, int cam0, const void* targets, const Workspace& ws, cudaStream_t s) {
+  const size_t smem = tc_smem<KT>();
+  cudaFuncSetAttribute(k_blend_accumulate_tc<KT, BF16_TARGETS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  const int64_t stride = p.L == 0 ? 0 : p.n * (int64_t)p.acc_stride;
+  k_blend_accumulate_tc<KT, BF16_TARGETS><<<cb * p.tiles, 256, smem, s>>>(
+      ws.tile_off, ws.entries, p.capacity, ws.rec, p.n, p.width, p.height, p.tiles_x, p.tiles,
+      static_cast<const uint16_t*>(targets), p.K, cam0, ws.acc, p.acc_stride, stride, ws.status);
+  note_launches(1);
+}
+
+template <bool BF16_TARGETS>
+void accumulate_tc_dispatch(const Problem& p, int cb, int cam0, const void* targets, const Workspace& ws,
+                            cudaStream_t s) {
+  if (p.K <= 16) accumulate_tc<16, BF16_TARGETS>(p, cb, cam0, targets, ws, s);
+  else if (p.K <= 32) accumulate_tc<32, BF16_TARGETS>(p, cb, cam0, targets, ws, s);
+  else accumulate_tc<64, BF16_TARGETS>(p, cb, cam0, targets, ws, s);
+}
+
+}  // namespace
+
+bool tc_accumulate_applies(const Problem& p, int dtype) {
+  return p.precision == 1 && (dtype == 1 || dtype == 2) && p.K >= 16 && p.K <= 64;
+}
+
+void launch_blend_accumulate_tc(const Problem& p, int cb, int cam0, const void* targets, int dtype,
+                                const Workspace& ws, cudaStream_t s) {
+  if (dtype == 1) accumulate_tc_dispatch<true>(p, cb, cam0, targets, ws, s);
+  else accumulate_tc_dispatch<false>(p, cb, cam0, targets, ws, s);
+}
+
+cudaError_t launch_tc_selftest(const uint16_t* A, const uint16_t* B, int N, bool bf16, float* D, DevStatus* status,
+                               cudaStream_t s) {
+#define ICGS_ST(NB, BF)                                                                                        \
+  do {                                                                                                         \
+    cudaFuncSetAttribute(k_tc_selftest<NB, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,                 \
+                         (int)selftest_smem<NB>());                                                           \
+    k_tc_selftest<NB, BF><<<1, 256, selftest_smem<NB>(), s>>>(A, B, D, status);                                \
+  } while (0)
+  if (N == 32 && bf16) ICGS_ST(32, true);
+  else if (N == 32) ICGS_ST(32, false);
+  else if (N == 80 && bf16) ICGS_ST(80, true);
+  else if (N == 80) ICGS_ST(80, false);
+  else return cudaErrorInvalidValue;
+#undef ICGS_ST
+  return cudaGetLastError();
+}
+
+}  // namespace icgs

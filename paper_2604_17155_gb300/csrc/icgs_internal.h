@@ -26,6 +26,7 @@ struct DevStatus {
   uint32_t pad;
 };
 constexpr uint32_t kFlagOverflow = 1u;
+constexpr uint32_t kFlagTimeout = 2u;  // a bounded device-side wait gave up
 
 // One camera as the kernels see it (built on the host from icgs_cameras).
 struct DevCam {
@@ -59,7 +60,7 @@ struct Workspace {
   uint64_t* entries = nullptr;     // [capacity] (depth key << 32 | index)
   uint64_t* entries_tmp = nullptr; // [capacity] merge buffer for long tiles
   float* payload = nullptr;        // [cb * n * (K+1)] per (camera, Gaussian) colour / adjoint terms
-  float* acc = nullptr;            // [cb * n * (1+K)] (L>0) or [n * (1+K)] (L=0)
+  float* acc = nullptr;            // [cb * n * RS] (L>0) or [n * RS] (L=0), RS = acc_stride
   float* G = nullptr;              // [n * B * B] Gram rows, hi
   float* Glo = nullptr;            // [n * B * B] compensation
   float* bvec = nullptr;           // [n * B * K]
@@ -79,6 +80,7 @@ struct Problem {
   float near_z = 0.2f;
   int tiles_x = 0, tiles_y = 0, tiles = 0;
   int K = 0, L = 0, B = 1;
+  int acc_stride = 4;               // floats per accumulator row (V, S_0..S_{K-1}), padded to 4
   int cam_batch = 0;
   uint32_t capacity = 0;
   int precision = 0;
@@ -100,6 +102,12 @@ void launch_scatter(const Problem& p, int cb, const Workspace& ws, cudaStream_t 
 void launch_tile_sort(const Problem& p, int cb, const Workspace& ws, cudaStream_t s);
 void launch_blend_accumulate(const Problem& p, int cb, int cam0, const void* targets, int dtype,
                              const Workspace& ws, cudaStream_t s);
+// Tensor-core contraction of the accumulate walk (MIXED precision, 16-bit targets, 16..64 channels).
+bool tc_accumulate_applies(const Problem& p, int dtype);
+void launch_blend_accumulate_tc(const Problem& p, int cb, int cam0, const void* targets, int dtype,
+                                const Workspace& ws, cudaStream_t s);
+cudaError_t launch_tc_selftest(const uint16_t* A, const uint16_t* B, int N, bool bf16, float* D,
+                               DevStatus* status, cudaStream_t s);
 void launch_fold(const Problem& p, const float* means, int cb, bool first, const Workspace& ws,
                  cudaStream_t s);
 void launch_solve(const Problem& p, const float* lam_dev, const float* lam_host, const Workspace& ws,

@@ -44,7 +44,7 @@ __device__ __forceinline__ F group_sum(F v) {
 template <int B, int KC, bool MIXED>
 __global__ void __launch_bounds__(kSolveThreads) k_fold(
     const float* __restrict__ means, int64_t n, const DevCam* __restrict__ cams, int cb,
-    const float* __restrict__ acc, int K, int k0, bool first, float* __restrict__ G,
+    const float* __restrict__ acc, int K, int RS, int k0, bool first, float* __restrict__ G,
     float* __restrict__ Glo, float* __restrict__ bvec, float* __restrict__ blo,
     float* __restrict__ wsum, float* __restrict__ wlo) {
   const int64_t i = (blockIdx.x * (int64_t)kSolveThreads + threadIdx.x) / kGroup;
@@ -76,9 +76,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_fold(
       }
   }
   const float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
-  const int64_t stride = n * (int64_t)(1 + K);
+  const int64_t stride = n * (int64_t)RS;
   for (int j = 0; j < cb; ++j) {
-    const float* a = acc + j * stride + i * (1 + K);
+    const float* a = acc + j * stride + i * RS;
     const float v = a[0];
     if (!(v > 0.0f)) continue;
     const float3 d = view_dir(mu, cams[j]);
@@ -300,19 +300,19 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(
 }
 
 // L = 0: acc[i] = (V, S_0..S_{K-1}) summed over every camera.
-__global__ void k_solve_l0(int64_t n, int K, const float* __restrict__ acc, float lam0,
+__global__ void k_solve_l0(int64_t n, int K, int RS, const float* __restrict__ acc, float lam0,
                            float* __restrict__ coeffs, uint8_t* __restrict__ status_out,
                            float* __restrict__ chol) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= n * (int64_t)K) return;
   const int64_t i = idx / K;
   const int k = (int)(idx - i * K);
-  const float V = acc[i * (1 + K)];
+  const float V = acc[i * RS];
   float c = 0.0f;
   if (V > 0.0f) {
     // (Y0^2 V + V lambda) c = Y0 S
     const float A = V * (kY0 * kY0 + lam0);
-    c = kY0 * acc[i * (1 + K) + 1 + k] / A;
+    c = kY0 * acc[i * RS + 1 + k] / A;
     if (k == 0 && chol) chol[i] = sqrtf(A);
   } else if (k == 0 && chol) {
     chol[i] = 0.0f;
@@ -428,7 +428,7 @@ template <int B, bool MIXED>
 void fold_b(const Problem& p, const float* means, int cb, const Workspace& ws, bool first, cudaStream_t s) {
   const unsigned grid = (unsigned)((p.n * kGroup + kSolveThreads - 1) / kSolveThreads);
   for (int k0 = 0; k0 < p.K; k0 += 4) {
-    k_fold<B, 4, MIXED><<<grid, kSolveThreads, 0, s>>>(means, p.n, ws.cams, cb, ws.acc, p.K, k0, first, ws.G, ws.Glo,
+    k_fold<B, 4, MIXED><<<grid, kSolveThreads, 0, s>>>(means, p.n, ws.cams, cb, ws.acc, p.K, p.acc_stride, k0, first, ws.G, ws.Glo,
                                                         ws.bvec, ws.blo, ws.wsum, ws.wlo);
     note_launches(1);
   }
@@ -462,7 +462,7 @@ void launch_solve(const Problem& p, const float* lam_dev, const float* lam_host,
                   float* coeffs, uint8_t* status, float* chol, cudaStream_t s) {
   if (p.B == 1) {
     const int64_t m = p.n * (int64_t)p.K;
-    k_solve_l0<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(p.n, p.K, ws.acc, lam_host[0], coeffs, status, chol);
+    k_solve_l0<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(p.n, p.K, p.acc_stride, ws.acc, lam_host[0], coeffs, status, chol);
     note_launches(1);
     return;
   }

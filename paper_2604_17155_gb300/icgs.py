@@ -16,7 +16,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libicgs.so")
 HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "icgs.h")
 
-OK, ERR_INVALID_ARG, ERR_WORKSPACE_TOO_SMALL, ERR_CUDA, ERR_CAPACITY, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
+OK, ERR_INVALID_ARG, ERR_WORKSPACE_TOO_SMALL, ERR_CUDA, ERR_CAPACITY, ERR_UNSUPPORTED, ERR_DEVICE_TIMEOUT = \
+    0, -1, -2, -3, -4, -5, -6
 F32, BF16, F16 = 0, 1, 2
 PLAIN, MIXED = 0, 1
 GAUSSIAN_OK, GAUSSIAN_UNSEEN, GAUSSIAN_FP64 = 0, 1, 2
@@ -86,6 +87,8 @@ def load(path: str = LIB_PATH):
     lib.icgs_colorize_noalloc.restype = ctypes.c_int
     lib.icgs_noalloc_scratch_bytes.argtypes = []
     lib.icgs_noalloc_scratch_bytes.restype = S
+    lib.icgs_selftest_tc.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, P, P, P]
+    lib.icgs_selftest_tc.restype = ctypes.c_int
     lib.icgs_set_stage_timing.argtypes = [ctypes.c_int]
     lib.icgs_set_stage_timing.restype = None
     lib.icgs_last_stage_ms.argtypes = [P, ctypes.c_int]
@@ -301,6 +304,21 @@ def colorize_noalloc(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, 
                                      ctypes.c_void_p(coeffs.data_ptr()), ctypes.c_void_p(status.data_ptr()),
                                      ctypes.c_void_p(chol.data_ptr()), _stream_ptr(dev)))
     return coeffs, status, chol
+
+
+def selftest_tc(A, B, bf16=True):
+    """Diagnostic: A [128,256] @ B [N,256]^T (N = 32 or 80) through the tensor-core path of the
+    16-bit accumulate walk; A and B are 16-bit CUDA tensors. Returns float32 [128, N]."""
+    torch = _torch()
+    lib = load()
+    A = A.contiguous()
+    B = B.contiguous()
+    N = int(B.shape[0])
+    D = torch.empty((128, N), dtype=torch.float32, device=A.device)
+    ws = _ws.get(A.device, 256)
+    _check(lib.icgs_selftest_tc(ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()), N, 1 if bf16 else 0,
+                                ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(ws.data_ptr()), _stream_ptr(A.device)))
+    return D
 
 
 def colorize_backward(scene: Scene, cams: Cameras, targets, sh_degree, coeffs, chol, grad_coeffs, lam=None,
