@@ -107,9 +107,13 @@ __global__ void __launch_bounds__(kThreads) k_blend_accumulate(
     load_batch(entries, c.b + start, nb, rec_cam, n, s_box, s_par, s_thr, s_id);
     __syncthreads();
     if (!__all_sync(kFull, done)) {
-      for (int g = 0; g < nb; ++g) {
+#pragma unroll
+      for (int half = 0; half < kBatch / 32; ++half) {
+       uint32_t bits = warp_hit_bits(s_box, half * 32, nb, c);
+       while (bits) {  // only the Gaussians whose box touches this warp's block, in depth order
+        const int g = half * 32 + __ffs(bits) - 1;
+        bits &= bits - 1;
         const float4 box = s_box[g];
-        if (!warp_hits(box, c)) continue;  // uniform across the warp
         float w = 0.0f, al, ex;
         bool cap;
         if (!done) w = blend_step(box, s_par[g], s_thr[g], c.pxf, c.pyf, T, done, al, ex, cap);
@@ -124,6 +128,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_accumulate(
           const float r = warp_transpose_reduce<NP>(v, lane);
           if (reducer) atomicAdd(&s_acc[g][my_value], r);
         }
+       }
       }
     }
     __syncthreads();
@@ -184,15 +189,19 @@ __global__ void __launch_bounds__(kThreads) k_blend_render(
     }
     __syncthreads();
     if (!__all_sync(kFull, done)) {
-      for (int g = 0; g < nb && !done; ++g) {
-        const float4 box = s_box[g];
-        if (!warp_hits(box, c)) continue;
-        float al, ex;
-        bool cap;
-        const float w = blend_step(box, s_par[g], s_thr[g], c.pxf, c.pyf, T, done, al, ex, cap);
-        if (w > 0.0f) {
 #pragma unroll
-          for (int k = 0; k < KC; ++k) img[k] = fmaf(w, s_col[g][k], img[k]);
+      for (int half = 0; half < kBatch / 32; ++half) {
+        uint32_t bits = warp_hit_bits(s_box, half * 32, nb, c);
+        while (bits && !done) {
+          const int g = half * 32 + __ffs(bits) - 1;
+          bits &= bits - 1;
+          float al, ex;
+          bool cap;
+          const float w = blend_step(s_box[g], s_par[g], s_thr[g], c.pxf, c.pyf, T, done, al, ex, cap);
+          if (w > 0.0f) {
+#pragma unroll
+            for (int k = 0; k < KC; ++k) img[k] = fmaf(w, s_col[g][k], img[k]);
+          }
         }
       }
     }
@@ -261,20 +270,24 @@ __global__ void __launch_bounds__(kThreads) k_blend_adjoint(
       load_payload<KC>(pay_cam, nb, K, s_id, s_pay);
       __syncthreads();
       if (!__all_sync(kFull, done)) {
-        for (int g = 0; g < nb && !done; ++g) {
-          const float4 box = s_box[g];
-          if (!warp_hits(box, c)) continue;
-          float al, ex;
-          bool cap;
-          const float w = blend_step(box, s_par[g], s_thr[g], c.pxf, c.pyf, T, done, al, ex, cap);
-          if (w > 0.0f) {
-            float gg = s_pay[g][KC];
 #pragma unroll
-            for (int k = 0; k < KC; ++k) {
-              gg = fmaf(s_pay[g][k], tv[k], gg);
-              gt[k] = fmaf(w, s_pay[g][k], gt[k]);
+        for (int half = 0; half < kBatch / 32; ++half) {
+          uint32_t bits = warp_hit_bits(s_box, half * 32, nb, c);
+          while (bits && !done) {
+            const int g = half * 32 + __ffs(bits) - 1;
+            bits &= bits - 1;
+            float al, ex;
+            bool cap;
+            const float w = blend_step(s_box[g], s_par[g], s_thr[g], c.pxf, c.pyf, T, done, al, ex, cap);
+            if (w > 0.0f) {
+              float gg = s_pay[g][KC];
+#pragma unroll
+              for (int k = 0; k < KC; ++k) {
+                gg = fmaf(s_pay[g][k], tv[k], gg);
+                gt[k] = fmaf(w, s_pay[g][k], gt[k]);
+              }
+              F = fmaf(gg, w, F);
             }
-            F = fmaf(gg, w, F);
           }
         }
       }
@@ -299,9 +312,13 @@ __global__ void __launch_bounds__(kThreads) k_blend_adjoint(
     load_payload<KC>(pay_cam, nb, K, s_id, s_pay);
     __syncthreads();
     if (!__all_sync(kFull, done)) {
-      for (int g = 0; g < nb; ++g) {
+#pragma unroll
+      for (int half = 0; half < kBatch / 32; ++half) {
+       uint32_t bits = warp_hit_bits(s_box, half * 32, nb, c);
+       while (bits) {
+        const int g = half * 32 + __ffs(bits) - 1;
+        bits &= bits - 1;
         const float4 box = s_box[g];
-        if (!warp_hits(box, c)) continue;
         float d_o = 0.0f;
         if (!done) {
           const float Tm = T;
@@ -322,6 +339,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_adjoint(
           for (int o = 16; o > 0; o >>= 1) d_o += __shfl_xor_sync(kFull, d_o, o);
           if (lane == 0) atomicAdd(&s_go[g], d_o);
         }
+       }
       }
     }
     __syncthreads();

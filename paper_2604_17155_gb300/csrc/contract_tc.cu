@@ -237,9 +237,26 @@ __global__ void __launch_bounds__(256, 2) k_blend_accumulate_tc(
   float t_scale_inv;
   {
     const uint16_t* src = targets + ((((int64_t)(cam0 + c.j) * height + c.py) * width + c.px) * K);
+    // this pixel's channels, loaded 16 bytes at a time when the row allows it
+    uint16_t tv[KT];
+    if (c.inside && K == KT && (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+#pragma unroll
+      for (int q = 0; q < KT / 8; ++q) {
+        const uint4 u = __ldg(reinterpret_cast<const uint4*>(src) + q);
+        const uint32_t wd[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          tv[8 * q + 2 * h] = (uint16_t)(wd[h] & 0xFFFFu);
+          tv[8 * q + 2 * h + 1] = (uint16_t)(wd[h] >> 16);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < KT; ++k) tv[k] = (c.inside && k < K) ? src[k] : (uint16_t)0;
+    }
     float tmax = 0.0f;
-    for (int k = 0; k < KT; ++k)
-      if (c.inside && k < K) tmax = fmaxf(tmax, fabsf(target_value(src[k], BF16_TARGETS)));
+#pragma unroll
+    for (int k = 0; k < KT; ++k) tmax = fmaxf(tmax, fabsf(target_value(tv[k], BF16_TARGETS)));
     // non-negative floats order like their bit patterns
     uint32_t m = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(tmax));
     if (lane == 0) s_tmax[warp] = m;
@@ -252,9 +269,9 @@ __global__ void __launch_bounds__(256, 2) k_blend_accumulate_tc(
     if (gmax > 0.0f && isfinite(gmax)) frexpf(gmax, &e);  // gmax in [2^(e-1), 2^e)
     const int sexp = gmax > 0.0f ? 15 - e : 0;           // gmax * 2^sexp in [2^14, 2^15)
     t_scale_inv = ldexpf(1.0f, -(sexp + kWScaleExp));
-#pragma unroll 8
+#pragma unroll
     for (int k = 0; k < KT; ++k) {
-      const float v = (c.inside && k < K) ? ldexpf(target_value(src[k], BF16_TARGETS), sexp) : 0.0f;
+      const float v = ldexpf(target_value(tv[k], BF16_TARGETS), sexp);
       *reinterpret_cast<uint16_t*>(B_s + kmajor_sw128(k, p, NB)) = half_bits(v);
     }
 #pragma unroll
@@ -281,20 +298,25 @@ __global__ void __launch_bounds__(256, 2) k_blend_accumulate_tc(
   for (uint32_t start = 0; start < c.len; start += kG) {
     const int nb = (int)min((uint32_t)kG, c.len - start);
     load_batch(entries, c.b + start, nb, rec_cam, n, s_box, s_par, s_thr, s_id);
+    // the previous batch's MMAs have completed: clear W (16-byte stores), then write its nonzeros
+    for (int i = threadIdx.x; i < kG * kKPix * 2 / 16; i += 256) reinterpret_cast<uint4*>(A_s)[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
-    // W column of this pixel: the weight of every Gaussian of the batch (0 where it does not blend)
-    for (int g = 0; g < kG; ++g) {
-      float w = 0.0f;
-      if (g < nb && !done) {
-        const float4 box = s_box[g];
-        if (warp_hits(box, c)) {
+    if (!__all_sync(0xFFFFFFFFu, done)) {
+#pragma unroll
+      for (int q = 0; q < kG / 32; ++q) {
+        uint32_t bits = warp_hit_bits(s_box, q * 32, nb, c);
+        while (bits && !done) {  // only Gaussians whose box touches this warp's block, in depth order
+          const int g = q * 32 + __ffs(bits) - 1;
+          bits &= bits - 1;
           float al, ex;
           bool cap;
-          w = blend_step(box, s_par[g], s_thr[g], c.pxf, c.pyf, T, done, al, ex, cap);
-          npairs += w > 0.0f;
+          const float w = blend_step(s_box[g], s_par[g], s_thr[g], c.pxf, c.pyf, T, done, al, ex, cap);
+          if (w > 0.0f) {
+            ++npairs;
+            *reinterpret_cast<uint16_t*>(A_s + kmajor_sw128(g, p, kG)) = half_bits(w * (float)(1 << kWScaleExp));
+          }
         }
       }
-      *reinterpret_cast<uint16_t*>(A_s + kmajor_sw128(g, p, kG)) = half_bits(ldexpf(w, kWScaleExp));
     }
     fence_async_smem();
     tc_fence_before();
@@ -303,9 +325,11 @@ __global__ void __launch_bounds__(256, 2) k_blend_accumulate_tc(
     const bool ok = mbar_wait_bounded(mbar, phase);
     phase ^= 1u;
     tc_fence_after();
-    if (warp < 4 && ok) {
-      const int g = warp * 32 + lane;
-      const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    if (ok) {
+      // warps w and w+4 share TMEM lanes 32(w%4)..+31 (one Gaussian per thread) and split its chunks
+      const int quarter = warp & 3, part = warp >> 2;
+      const int g = quarter * 32 + lane;
+      const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
       uint32_t vr[16];
       tmem_ld16(trow + (uint32_t)KT, vr);  // the ones block: every column holds V
       float v[KT + 4];
@@ -325,9 +349,11 @@ __global__ void __launch_bounds__(256, 2) k_blend_accumulate_tc(
       for (int q = KT + 1; q < KT + 4; ++q) v[q] = 0.0f;
       if (g < nb && v[0] > 0.0f) {
         float* dst = acc_cam + (int64_t)s_id[g] * RS;
+        constexpr int kChunks = (KT + 4) / 4;
 #pragma unroll
-        for (int q = 0; q < (KT + 4) / 4; ++q)
-          if (4 * q < RS) atomicAdd(reinterpret_cast<float4*>(dst + 4 * q), make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+        for (int q = 0; q < kChunks; ++q)
+          if ((q < (kChunks + 1) / 2) == (part == 0) && 4 * q < RS)
+            atomicAdd(reinterpret_cast<float4*>(dst + 4 * q), make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
       }
     }
     if (!ok) timed_out = true;

@@ -54,6 +54,15 @@ __device__ __forceinline__ bool warp_hits(const float4 box, const TileCtx& c) {
   return box.x + box.z >= c.wx0 && box.x - box.z <= c.wx1 && box.y + box.w >= c.wy0 && box.y - box.w <= c.wy1;
 }
 
+// Box-hit masks of this warp for the batch's Gaussians [base, base + 32): bit i is set when
+// Gaussian base + i (< nb) touches the warp's pixel block. One Gaussian per lane, one ballot;
+// iterating the set bits in ascending order keeps the depth order.
+__device__ __forceinline__ uint32_t warp_hit_bits(const float4* s_box, int base, int nb, const TileCtx& c) {
+  const int g = base + (int)(threadIdx.x & 31);
+  const bool h = g < nb && warp_hits(s_box[g], c);
+  return __ballot_sync(kFull, h);
+}
+
 // One step of the walk for a Gaussian (box, par, q threshold) at pixel centre (pxf, pyf).
 // Returns the weight w = alpha T (0 if skipped); sets `done` when the pixel stops here.
 // e_out receives exp(-q/2) and capped whether alpha hit 0.99 (both only meaningful if w > 0).
