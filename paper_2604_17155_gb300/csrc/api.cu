@@ -222,7 +222,10 @@ icgs_status upload_common(const Problem& p, const icgs_cameras* cams, const floa
   return ICGS_OK;
 }
 
-icgs_status bin_pass(const Problem& p, const icgs_scene* sc, int cb, const Workspace& wp, cudaStream_t s) {
+// sort_all: every tile list is ordered in global memory (the tensor-core walk reads them there);
+// otherwise only the long lists are, and the CUDA-core walks sort the rest in shared memory.
+icgs_status bin_pass(const Problem& p, const icgs_scene* sc, int cb, bool sort_all, const Workspace& wp,
+                     cudaStream_t s) {
   const int64_t ct = (int64_t)cb * p.tiles;
   ICGS_TRY_CUDA(cudaMemsetAsync(wp.tile_off, 0, sizeof(uint32_t) * (size_t)(ct + 1), s));
   ICGS_TRY_CUDA(cudaMemsetAsync(wp.tile_cur, 0, sizeof(uint32_t) * (size_t)ct, s));
@@ -232,7 +235,7 @@ icgs_status bin_pass(const Problem& p, const icgs_scene* sc, int cb, const Works
   g_timer.mark(kScan, s);
   launch_scatter(p, cb, wp, s);
   g_timer.mark(kScatter, s);
-  launch_tile_sort(p, cb, wp, s);
+  launch_tile_sort(p, cb, sort_all, wp, s);
   g_timer.mark(kSort, s);
   return ICGS_OK;
 }
@@ -332,7 +335,7 @@ icgs_status icgs_colorize(const icgs_scene* scene, const icgs_cameras* cams, con
     wp.cams = ws.cams + cam0;
     if (p.L > 0)
       ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)cb * (size_t)p.n * p.acc_stride, s));
-    if ((st = bin_pass(p, scene, cb, wp, s)) != ICGS_OK) return st;
+    if ((st = bin_pass(p, scene, cb, tc_accumulate_applies(p, (int)targets->dtype), wp, s)) != ICGS_OK) return st;
     launch_blend_accumulate(p, cb, cam0, targets->data, (int)targets->dtype, wp, s);
     g_timer.mark(kBlend, s);
     if (p.L > 0) {
@@ -384,7 +387,7 @@ icgs_status icgs_colorize_backward(const icgs_scene* scene, const icgs_cameras* 
     const int cb = std::min(p.cam_batch, p.n_cams - cam0);
     Workspace wp = ws;
     wp.cams = ws.cams + cam0;
-    if ((st = bin_pass(p, scene, cb, wp, s)) != ICGS_OK) return st;
+    if ((st = bin_pass(p, scene, cb, false, wp, s)) != ICGS_OK) return st;
     launch_payload_adjoint(p, scene->means, coeffs, cb, wp, s);
     g_timer.mark(kPayload, s);
     launch_blend_adjoint(p, cb, cam0, targets->data, (int)targets->dtype, wp, grad_targets, grad_opacity != nullptr, s);
@@ -425,7 +428,7 @@ icgs_status icgs_render(const icgs_scene* scene, const icgs_cameras* cams, int32
     const int cb = std::min(p.cam_batch, p.n_cams - cam0);
     Workspace wp = ws;
     wp.cams = ws.cams + cam0;
-    if ((st = bin_pass(p, scene, cb, wp, s)) != ICGS_OK) return st;
+    if ((st = bin_pass(p, scene, cb, false, wp, s)) != ICGS_OK) return st;
     launch_payload_render(p, scene->means, coeffs, cb, wp, s);
     g_timer.mark(kPayload, s);
     launch_blend_render(p, cb, cam0, wp, images_out, s);

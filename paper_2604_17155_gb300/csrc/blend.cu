@@ -82,7 +82,9 @@ __global__ void __launch_bounds__(kThreads) k_blend_accumulate(
   __shared__ float s_thr[kBatch];
   __shared__ uint32_t s_id[kBatch];
   __shared__ float s_acc[kBatch][NV];
+  __shared__ unsigned long long s_keys[kWalkSortCap];
   const TileCtx c = tile_ctx(tile_off, capacity, tiles, tiles_x, width, height);
+  const unsigned long long* list = stage_tile_list(entries, c.b, c.len, s_keys);
   const int lane = threadIdx.x & 31;
   float tv[KC];
 #pragma unroll
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_accumulate(
   for (uint32_t start = 0; start < c.len; start += kBatch) {
     const int nb = (int)min((uint32_t)kBatch, c.len - start);
     __syncthreads();
-    load_batch(entries, c.b + start, nb, rec_cam, n, s_box, s_par, s_thr, s_id);
+    load_batch(list, start, nb, rec_cam, n, s_box, s_par, s_thr, s_id);
     __syncthreads();
     if (!__all_sync(kFull, done)) {
 #pragma unroll
@@ -170,7 +172,9 @@ __global__ void __launch_bounds__(kThreads) k_blend_render(
   __shared__ float s_thr[kBatch];
   __shared__ uint32_t s_id[kBatch];
   __shared__ float s_col[kBatch][KC];
+  __shared__ unsigned long long s_keys[kWalkSortCap];
   const TileCtx c = tile_ctx(tile_off, capacity, tiles, tiles_x, width, height);
+  const unsigned long long* list = stage_tile_list(entries, c.b, c.len, s_keys);
   const ProjRec* rec_cam = rec + (int64_t)c.j * n;
   const float* pay_cam = payload + (int64_t)c.j * n * K;
   float img[KC];
@@ -181,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_render(
   for (uint32_t start = 0; start < c.len; start += kBatch) {
     const int nb = (int)min((uint32_t)kBatch, c.len - start);
     __syncthreads();
-    load_batch(entries, c.b + start, nb, rec_cam, n, s_box, s_par, s_thr, s_id);
+    load_batch(list, start, nb, rec_cam, n, s_box, s_par, s_thr, s_id);
     __syncthreads();
     for (int idx = threadIdx.x; idx < nb * KC; idx += kThreads) {
       const int g = idx / KC, k = idx - g * KC;
@@ -244,7 +248,9 @@ __global__ void __launch_bounds__(kThreads) k_blend_adjoint(
   __shared__ uint32_t s_id[kBatch];
   __shared__ float s_pay[kBatch][KC + 1];
   __shared__ float s_go[kBatch];
+  __shared__ unsigned long long s_keys[kWalkSortCap];
   const TileCtx c = tile_ctx(tile_off, capacity, tiles, tiles_x, width, height);
+  const unsigned long long* list = stage_tile_list(entries, c.b, c.len, s_keys);
   const int lane = threadIdx.x & 31;
   const ProjRec* rec_cam = rec + (int64_t)c.j * n;
   const float* pay_cam = payload + (int64_t)c.j * n * (K + 1);
@@ -265,7 +271,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_adjoint(
     for (uint32_t start = 0; start < c.len; start += kBatch) {
       const int nb = (int)min((uint32_t)kBatch, c.len - start);
       __syncthreads();
-      load_batch(entries, c.b + start, nb, rec_cam, n, s_box, s_par, s_thr, s_id);
+      load_batch(list, start, nb, rec_cam, n, s_box, s_par, s_thr, s_id);
       __syncthreads();
       load_payload<KC>(pay_cam, nb, K, s_id, s_pay);
       __syncthreads();
@@ -307,7 +313,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_adjoint(
   for (uint32_t start = 0; start < c.len; start += kBatch) {
     const int nb = (int)min((uint32_t)kBatch, c.len - start);
     __syncthreads();
-    load_batch(entries, c.b + start, nb, rec_cam, n, s_box, s_par, s_thr, s_id);
+    load_batch(list, start, nb, rec_cam, n, s_box, s_par, s_thr, s_id);
     __syncthreads();
     load_payload<KC>(pay_cam, nb, K, s_id, s_pay);
     __syncthreads();

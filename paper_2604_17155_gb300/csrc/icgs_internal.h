@@ -99,7 +99,7 @@ void launch_project(const Problem& p, const float* means, const float* scales, c
                     const float* opac, int cb, const Workspace& ws, cudaStream_t s);
 void launch_scan(const Problem& p, int cb, const Workspace& ws, cudaStream_t s);
 void launch_scatter(const Problem& p, int cb, const Workspace& ws, cudaStream_t s);
-void launch_tile_sort(const Problem& p, int cb, const Workspace& ws, cudaStream_t s);
+void launch_tile_sort(const Problem& p, int cb, bool sort_all, const Workspace& ws, cudaStream_t s);
 void launch_blend_accumulate(const Problem& p, int cb, int cam0, const void* targets, int dtype,
                              const Workspace& ws, cudaStream_t s);
 // Tensor-core contraction of the accumulate walk (MIXED precision, 16-bit targets, 16..64 channels).

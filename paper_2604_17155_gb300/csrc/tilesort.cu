@@ -8,34 +8,17 @@
 #include <cuda_runtime.h>
 
 #include "icgs_internal.h"
+#include "walk.cuh"
 
 namespace icgs {
 
 namespace {
 
+using walk::bitonic_sort_smem;
+
 constexpr int kSortThreads = 256;
 constexpr int kLongThreads = 1024;
 constexpr unsigned long long kPad = ~0ull;
-
-// Ascending bitonic sort of s[0, P) (P a power of two) by all threads of the CTA.
-template <int NT>
-__device__ void bitonic_sort_smem(unsigned long long* s, int P) {
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int jj = k >> 1; jj > 0; jj >>= 1) {
-      for (int t = threadIdx.x; t < (P >> 1); t += NT) {
-        const int i = 2 * jj * (t / jj) + (t % jj);
-        const int l = i + jj;
-        const unsigned long long a = s[i], b = s[l];
-        const bool up = (i & k) == 0;
-        if ((a > b) == up) {
-          s[i] = b;
-          s[l] = a;
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
 
 __device__ __forceinline__ void tile_range(const uint32_t* tile_off, int t, uint32_t capacity,
                                            uint32_t& b, uint32_t& e) {
@@ -57,11 +40,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(const uint32_t* __r
     if (threadIdx.x == 0) big_list[atomicAdd(&status->big_tiles, 1u)] = blockIdx.x;
     return;
   }
-  int P = 2;
-  while (P < n) P <<= 1;
-  for (int k = threadIdx.x; k < P; k += kSortThreads) s[k] = k < n ? entries[b + k] : kPad;
-  __syncthreads();
-  bitonic_sort_smem<kSortThreads>(s, P);
+  walk::sort_keys_block<kSortCap / kSortThreads>(entries + b, (uint32_t)n, s);
   for (int k = threadIdx.x; k < n; k += kSortThreads) entries[b + k] = s[k];
 }
 
@@ -130,13 +109,31 @@ __global__ void __launch_bounds__(kLongThreads) k_sort_long(const uint32_t* __re
   }
 }
 
+// Queues the tiles whose list is longer than the walks sort in shared memory (kWalkSortCap).
+__global__ void __launch_bounds__(kSortThreads) k_queue_long_tiles(const uint32_t* __restrict__ tile_off, int ntiles,
+                                                                   uint32_t capacity, uint32_t* __restrict__ big_list,
+                                                                   DevStatus* status) {
+  const int t = blockIdx.x * kSortThreads + threadIdx.x;
+  if (t >= ntiles) return;
+  uint32_t b, e;
+  tile_range(tile_off, t, capacity, b, e);
+  if (e - b > (uint32_t)walk::kWalkSortCap) big_list[atomicAdd(&status->big_tiles, 1u)] = (uint32_t)t;
+}
+
 }  // namespace
 
-void launch_tile_sort(const Problem& p, int cb, const Workspace& ws, cudaStream_t s) {
+// sort_all: order every tile list here (walks that read the lists from global memory); otherwise
+// only the lists longer than the walks' shared-memory sort (kWalkSortCap).
+void launch_tile_sort(const Problem& p, int cb, bool sort_all, const Workspace& ws, cudaStream_t s) {
+  static_assert(walk::kWalkSortCap <= kSortCap, "the long-list sort takes everything the walks do not");
   const int ntiles = cb * p.tiles;
   cudaMemsetAsync(&ws.status->big_tiles, 0, sizeof(uint32_t), s);
-  k_sort_tiles<<<ntiles, kSortThreads, 0, s>>>(ws.tile_off, reinterpret_cast<unsigned long long*>(ws.entries),
-                                               p.capacity, ws.big_list, ws.status);
+  if (sort_all)
+    k_sort_tiles<<<ntiles, kSortThreads, 0, s>>>(ws.tile_off, reinterpret_cast<unsigned long long*>(ws.entries),
+                                                 p.capacity, ws.big_list, ws.status);
+  else
+    k_queue_long_tiles<<<(ntiles + kSortThreads - 1) / kSortThreads, kSortThreads, 0, s>>>(
+        ws.tile_off, ntiles, p.capacity, ws.big_list, ws.status);
   k_sort_long<<<152, kLongThreads, 0, s>>>(ws.tile_off, reinterpret_cast<unsigned long long*>(ws.entries),
                                            reinterpret_cast<unsigned long long*>(ws.entries_tmp), p.capacity,
                                            ws.big_list, ws.status);

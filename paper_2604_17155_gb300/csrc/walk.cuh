@@ -49,6 +49,140 @@ __device__ __forceinline__ TileCtx tile_ctx(const uint32_t* tile_off, uint32_t c
   return c;
 }
 
+// Ascending bitonic sort of s[0, P) (P a power of two) by the NT threads of the CTA; the pair
+// indices are formed with shifts and masks (the strides are powers of two).
+template <int NT>
+__device__ __forceinline__ void bitonic_sort_smem(unsigned long long* s, int P) {
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int t = threadIdx.x; t < (P >> 1); t += NT) {
+        const int i = ((t & ~(jj - 1)) << 1) | (t & (jj - 1));
+        const int l = i + jj;
+        const unsigned long long a = s[i], b = s[l];
+        if ((a > b) == ((i & k) == 0)) {
+          s[i] = b;
+          s[l] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+constexpr int kWalkSortCap = 1024;  // tile lists up to this length are sorted inside the walk
+
+// Keeps min or max of (a, partner) so that element i ends up ordered against element i ^ jj in a
+// bitonic merge of span k.
+__device__ __forceinline__ unsigned long long cmpx_keep(unsigned long long a, unsigned long long partner, int i,
+                                                        int jj, int k) {
+  const bool lower = (i & jj) == 0, up = (i & k) == 0;
+  const unsigned long long mn = a < partner ? a : partner, mx = a < partner ? partner : a;
+  return (lower == up) ? mn : mx;
+}
+
+// Ascending bitonic sort of P = 256 * E keys (E = 1, 2, 4, 8, 16) by the 256 threads of the CTA,
+// thread t holding keys t, t + 256, ..., t + 256 (E-1) in v. Strides of 256 or more are compare-
+// exchanges inside a thread, strides below 32 are warp shuffles, and only strides 32..128 go
+// through shared memory (s, P keys), so a 256-key sort has 6 barrier-separated stages instead of 36.
+// On return s holds the sorted keys.
+template <int E>
+__device__ __forceinline__ void block_bitonic_sort(unsigned long long (&v)[E], unsigned long long* s, int P) {
+  const int t = threadIdx.x;
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      if (jj >= kThreads) {
+#pragma unroll
+        for (int m = 1; m < E; m <<= 1) {  // m = jj / 256, unrolled so that v is indexed statically
+          if (m * kThreads != jj) continue;
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int pe = e ^ m;
+            if (pe > e) {
+              const int i = e * kThreads + t;
+              const unsigned long long a = v[e], b = v[pe];
+              const bool up = (i & k) == 0;
+              const bool swap = (a > b) == up;
+              v[e] = swap ? b : a;
+              v[pe] = swap ? a : b;
+            }
+          }
+        }
+      } else if (jj >= 32) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) s[e * kThreads + t] = v[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = e * kThreads + t;
+          v[e] = cmpx_keep(v[e], s[i ^ jj], i, jj, k);
+        }
+        __syncthreads();
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = e * kThreads + t;
+          v[e] = cmpx_keep(v[e], __shfl_xor_sync(kFull, v[e], jj), i, jj, k);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) s[e * kThreads + t] = v[e];
+  __syncthreads();
+}
+
+template <int E>
+__device__ __forceinline__ void sort_into_smem(const unsigned long long* g, uint32_t len, unsigned long long* s,
+                                               int P) {
+  unsigned long long v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = e * kThreads + (int)threadIdx.x;
+    v[e] = i < (int)len ? g[i] : ~0ull;
+  }
+  block_bitonic_sort<E>(v, s, P);
+}
+
+// Sorts the len (<= 256 * MAXE) keys at g into s[0, len) (ascending); callable by all threads.
+// Lists of up to 256 keys take the plain network padded to the next power of two (short lists
+// are the common case and pay for fewer stages); longer ones take block_bitonic_sort.
+template <int MAXE>
+__device__ __forceinline__ void sort_keys_block(const unsigned long long* g, uint32_t len, unsigned long long* s) {
+  if (len <= (uint32_t)kThreads) {
+    int P = 2;
+    while (P < (int)len) P <<= 1;
+    for (int k = threadIdx.x; k < P; k += kThreads) s[k] = k < (int)len ? g[k] : ~0ull;
+    __syncthreads();
+    bitonic_sort_smem<kThreads>(s, P);
+    return;
+  }
+  int P = kThreads;
+  while (P < (int)len) P <<= 1;
+  const int E = P / kThreads;
+  if (E == 1) sort_into_smem<1>(g, len, s, P);
+  else if (E == 2 || MAXE == 2) sort_into_smem<(MAXE < 2 ? 1 : 2)>(g, len, s, P);
+  else if (E == 4 || MAXE == 4) sort_into_smem<(MAXE < 4 ? 1 : 4)>(g, len, s, P);
+  else if (E == 8 || MAXE == 8) sort_into_smem<(MAXE < 8 ? 1 : 8)>(g, len, s, P);
+  else sort_into_smem<(MAXE < 16 ? 1 : 16)>(g, len, s, P);
+}
+
+// The tile's depth-ordered list: sorted here into shared memory when it fits, else the global
+// slot range that the long-list sort has already ordered. Keys are unique ((depth bits << 32) |
+// index), so the ascending order is depth order with ties in index order.
+__device__ __forceinline__ const unsigned long long* stage_tile_list(const uint64_t* __restrict__ entries,
+                                                                     uint32_t b, uint32_t len,
+                                                                     unsigned long long* s_keys) {
+  const unsigned long long* g = reinterpret_cast<const unsigned long long*>(entries) + b;
+  if (len > (uint32_t)kWalkSortCap) return g;  // uniform
+  // the plain network only: the register-blocked one costs the walk occupancy even when unused
+  int P = 2;
+  while (P < (int)len) P <<= 1;
+  for (int k = threadIdx.x; k < P; k += kThreads) s_keys[k] = k < (int)len ? g[k] : ~0ull;
+  __syncthreads();
+  bitonic_sort_smem<kThreads>(s_keys, P);
+  return s_keys;
+}
+
 // Does the Gaussian's padded support box touch the warp's pixel block? (warp-uniform)
 __device__ __forceinline__ bool warp_hits(const float4 box, const TileCtx& c) {
   return box.x + box.z >= c.wx0 && box.x - box.z <= c.wx1 && box.y + box.w >= c.wy0 && box.y - box.w <= c.wy1;
@@ -96,11 +230,11 @@ __device__ __forceinline__ float blend_step(const float4 box, const float4 par, 
 // to the caller as ICGS_ERR_CAPACITY) may leave stale slots, so indices are clamped to the scene.
 // The fast-reject threshold is 2 ln(255 o) with a relative margin of 1e-4 (and 1e-4 absolute),
 // beyond which alpha < 1/255 holds by more than the float32 error of alpha.
-__device__ __forceinline__ void load_batch(const uint64_t* __restrict__ entries, uint32_t first, int nb,
+__device__ __forceinline__ void load_batch(const unsigned long long* list, uint32_t first, int nb,
                                            const ProjRec* __restrict__ rec_cam, int64_t n, float4* s_box,
                                            float4* s_par, float* s_thr, uint32_t* s_id) {
   if ((int)threadIdx.x < nb) {
-    const uint32_t id = min((uint32_t)entries[first + threadIdx.x], (uint32_t)(n - 1));
+    const uint32_t id = min((uint32_t)list[first + threadIdx.x], (uint32_t)(n - 1));
     const ProjRec r = rec_cam[id];
     s_id[threadIdx.x] = id;
     s_box[threadIdx.x] = r.box;
