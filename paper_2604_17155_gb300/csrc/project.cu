@@ -7,9 +7,11 @@
 // of z evaluated in double with the fixed, unfused sequence ((W20 x + W21 y) + W22 z) + W23, so the
 // ordering key is a well-defined function of the inputs.
 //
-// Binning is a counting sort: k_project counts instances per tile with atomics, an exclusive scan
-// turns counts into offsets, and k_scatter writes (depth key << 32 | index) into each tile's slot
-// range. The order inside a tile is fixed later by the per-tile sort.
+// Binning is a counting sort: k_project_hist counts instances per tile, an exclusive scan turns
+// counts into offsets, and k_scatter_hist writes (depth key << 32 | index) into each tile's slot
+// range. Both work on CTAs of 2048 Gaussians of one camera that count in a shared-memory
+// histogram of the camera's tiles, so a global atomic is issued per (CTA, touched tile) rather
+// than per instance. The order inside a tile is fixed later by the per-tile sort.
 #include <cuda_runtime.h>
 
 #include "icgs_device.cuh"
@@ -25,22 +27,19 @@ __device__ __forceinline__ double depth_f64(const DevCam& c, float x, float y, f
   return __dadd_rn(t, (double)c.w[11]);
 }
 
-__global__ void __launch_bounds__(256) k_project(
-    const float* __restrict__ means, const float* __restrict__ scales,
-    const float* __restrict__ quats, const float* __restrict__ opac, int64_t n,
-    const DevCam* __restrict__ cams, int width, int height, float near_z, int tiles_x, int tiles,
-    ProjRec* __restrict__ rec, uint4* __restrict__ rect, uint32_t* __restrict__ tile_count) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int j = blockIdx.y;
-  if (i >= n) return;
-  const DevCam& c = cams[j];
-  const int64_t ji = (int64_t)j * n + i;
+// Projects Gaussian i into camera c, writes its record and tile rectangle at slot ji and returns
+// the rectangle (tx0, ty0, tx1, ty1); tx0 > tx1 when the Gaussian has no pixel in the image.
+__device__ __forceinline__ int4 project_pair(const float* __restrict__ means, const float* __restrict__ scales,
+                                             const float* __restrict__ quats, const float* __restrict__ opac,
+                                             int64_t i, const DevCam& c, int width, int height, float near_z,
+                                             int64_t ji, ProjRec* __restrict__ rec, uint4* __restrict__ rect) {
+  const int4 none = make_int4(1, 0, 0, 0);
   const float mx3 = means[3 * i], my3 = means[3 * i + 1], mz3 = means[3 * i + 2];
   const float o = opac[i];
   const double zd = depth_f64(c, mx3, my3, mz3);
   if (!(zd > (double)near_z) || !(__dmul_rn((double)o, 255.0) >= 1.0)) {
     rect[ji] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
-    return;
+    return none;
   }
   const float tz = __double2float_rn(zd);
   const float tx = fmaf(c.w[0], mx3, fmaf(c.w[1], my3, fmaf(c.w[2], mz3, c.w[3])));
@@ -87,7 +86,7 @@ __global__ void __launch_bounds__(256) k_project(
   const float my = fmaf(c.fy, ty * iz, c.cy);
   if (!(det > 0.0f) || !isfinite(mx) || !isfinite(my)) {
     rect[ji] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
-    return;
+    return none;
   }
   const float idet = 1.0f / det;
   const float qthr = 2.0f * logf(255.0f * o);
@@ -99,7 +98,7 @@ __global__ void __launch_bounds__(256) k_project(
   const float fy0 = fmaxf(ceilf(my - hy - 0.5f), 0.0f), fy1 = fminf(floorf(my + hy - 0.5f), (float)(height - 1));
   if (!(fx0 <= fx1) || !(fy0 <= fy1)) {
     rect[ji] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
-    return;
+    return none;
   }
   const int tx0 = (int)fx0 / kTile, tx1 = (int)fx1 / kTile;
   const int ty0 = (int)fy0 / kTile, ty1 = (int)fy1 / kTile;
@@ -109,9 +108,52 @@ __global__ void __launch_bounds__(256) k_project(
   rec[ji] = r;
   rect[ji] = make_uint4((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16),
                         __float_as_uint(tz), 0u);
+  return make_int4(tx0, ty0, tx1, ty1);
+}
+
+constexpr int kPerThread = 8;                 // Gaussians per thread in the histogram kernels
+constexpr int kPerCta = 256 * kPerThread;     // Gaussians of one camera per CTA
+constexpr int kHistTiles = 12288;             // largest tile grid the shared-memory histograms take
+
+// One CTA per (camera, 2048 Gaussians): counts the CTA's instances per tile in shared memory, then
+// adds each nonzero bin to the global count with one atomic.
+__global__ void __launch_bounds__(256) k_project_hist(
+    const float* __restrict__ means, const float* __restrict__ scales, const float* __restrict__ quats,
+    const float* __restrict__ opac, int64_t n, const DevCam* __restrict__ cams, int width, int height,
+    float near_z, int tiles_x, int tiles, ProjRec* __restrict__ rec, uint4* __restrict__ rect,
+    uint32_t* __restrict__ tile_count) {
+  extern __shared__ uint32_t s_hist[];
+  const int j = blockIdx.y;
+  const DevCam& c = cams[j];
+  for (int t = threadIdx.x; t < tiles; t += 256) s_hist[t] = 0u;
+  __syncthreads();
+  const int64_t i0 = (int64_t)blockIdx.x * kPerCta;
+  for (int r = 0; r < kPerThread; ++r) {
+    const int64_t i = i0 + r * 256 + threadIdx.x;
+    if (i >= n) break;
+    const int4 tr = project_pair(means, scales, quats, opac, i, c, width, height, near_z, (int64_t)j * n + i, rec, rect);
+    for (int ty = tr.y; ty <= tr.w; ++ty)
+      for (int tx = tr.x; tx <= tr.z; ++tx) atomicAdd(&s_hist[ty * tiles_x + tx], 1u);
+  }
+  __syncthreads();
   uint32_t* base = tile_count + (int64_t)j * tiles;
-  for (int ty = ty0; ty <= ty1; ++ty)
-    for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(base + ty * tiles_x + tx, 1u);
+  for (int t = threadIdx.x; t < tiles; t += 256)
+    if (s_hist[t]) atomicAdd(base + t, s_hist[t]);
+}
+
+// Fallback for tile grids beyond kHistTiles: one global atomic per instance.
+__global__ void __launch_bounds__(256) k_project(
+    const float* __restrict__ means, const float* __restrict__ scales,
+    const float* __restrict__ quats, const float* __restrict__ opac, int64_t n,
+    const DevCam* __restrict__ cams, int width, int height, float near_z, int tiles_x, int tiles,
+    ProjRec* __restrict__ rec, uint4* __restrict__ rect, uint32_t* __restrict__ tile_count) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= n) return;
+  const int4 tr = project_pair(means, scales, quats, opac, i, cams[j], width, height, near_z, (int64_t)j * n + i, rec, rect);
+  uint32_t* base = tile_count + (int64_t)j * tiles;
+  for (int ty = tr.y; ty <= tr.w; ++ty)
+    for (int tx = tr.x; tx <= tr.z; ++tx) atomicAdd(base + ty * tiles_x + tx, 1u);
 }
 
 __global__ void __launch_bounds__(256) k_scatter(
@@ -135,6 +177,54 @@ __global__ void __launch_bounds__(256) k_scatter(
       if (slot < capacity) entries[slot] = key;
       else overflow = true;
     }
+  if (overflow) atomicOr(&status->flags, kFlagOverflow);
+}
+
+// Same CTA tiling as k_project_hist: the CTA counts its instances per tile, reserves one contiguous
+// run per tile with a single global atomic, then places its instances with shared-memory cursors.
+__global__ void __launch_bounds__(256) k_scatter_hist(
+    int64_t n, const uint4* __restrict__ rect, int tiles_x, int tiles, const uint32_t* __restrict__ tile_off,
+    uint32_t* __restrict__ tile_cur, uint64_t* __restrict__ entries, uint32_t capacity, DevStatus* status) {
+  extern __shared__ uint32_t s_mem[];
+  uint32_t* s_cnt = s_mem;          // [tiles] count, then running cursor
+  uint32_t* s_base = s_mem + tiles;  // [tiles] start of the CTA's run in the tile's slot range
+  const int j = blockIdx.y;
+  for (int t = threadIdx.x; t < tiles; t += 256) s_cnt[t] = 0u;
+  __syncthreads();
+  const int64_t i0 = (int64_t)blockIdx.x * kPerCta;
+  for (int r = 0; r < kPerThread; ++r) {
+    const int64_t i = i0 + r * 256 + threadIdx.x;
+    if (i >= n) break;
+    const uint4 rc = rect[(int64_t)j * n + i];
+    if (rc.x == 0xFFFFFFFFu) continue;
+    const int tx0 = rc.x & 0xFFFF, ty0 = rc.x >> 16, tx1 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
+    for (int ty = ty0; ty <= ty1; ++ty)
+      for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&s_cnt[ty * tiles_x + tx], 1u);
+  }
+  __syncthreads();
+  const int64_t tj = (int64_t)j * tiles;
+  for (int t = threadIdx.x; t < tiles; t += 256) {
+    const uint32_t cnt = s_cnt[t];
+    s_base[t] = cnt ? tile_off[tj + t] + atomicAdd(tile_cur + tj + t, cnt) : 0u;
+    s_cnt[t] = 0u;
+  }
+  __syncthreads();
+  bool overflow = false;
+  for (int r = 0; r < kPerThread; ++r) {
+    const int64_t i = i0 + r * 256 + threadIdx.x;
+    if (i >= n) break;
+    const uint4 rc = rect[(int64_t)j * n + i];
+    if (rc.x == 0xFFFFFFFFu) continue;
+    const int tx0 = rc.x & 0xFFFF, ty0 = rc.x >> 16, tx1 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
+    const uint64_t key = ((uint64_t)rc.z << 32) | (uint64_t)(uint32_t)i;
+    for (int ty = ty0; ty <= ty1; ++ty)
+      for (int tx = tx0; tx <= tx1; ++tx) {
+        const int t = ty * tiles_x + tx;
+        const uint64_t slot = (uint64_t)s_base[t] + atomicAdd(&s_cnt[t], 1u);
+        if (slot < capacity) entries[slot] = key;
+        else overflow = true;
+      }
+  }
   if (overflow) atomicOr(&status->flags, kFlagOverflow);
 }
 
@@ -228,6 +318,16 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_apply(uint32_t* __restrict_
 
 void launch_project(const Problem& p, const float* means, const float* scales, const float* quats,
                     const float* opac, int cb, const Workspace& ws, cudaStream_t s) {
+  if (p.tiles <= kHistTiles) {
+    const size_t smem = sizeof(uint32_t) * (size_t)p.tiles;
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_project_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid((unsigned)((p.n + kPerCta - 1) / kPerCta), (unsigned)cb);
+    k_project_hist<<<grid, 256, smem, s>>>(means, scales, quats, opac, p.n, ws.cams, p.width, p.height, p.near_z,
+                                           p.tiles_x, p.tiles, ws.rec, ws.rect, ws.tile_off);
+    note_launches(1);
+    return;
+  }
   dim3 grid((unsigned)((p.n + 255) / 256), (unsigned)cb);
   k_project<<<grid, 256, 0, s>>>(means, scales, quats, opac, p.n, ws.cams, p.width, p.height, p.near_z,
                                  p.tiles_x, p.tiles, ws.rec, ws.rect, ws.tile_off);
@@ -244,6 +344,16 @@ void launch_scan(const Problem& p, int cb, const Workspace& ws, cudaStream_t s) 
 }
 
 void launch_scatter(const Problem& p, int cb, const Workspace& ws, cudaStream_t s) {
+  if (p.tiles <= kHistTiles) {
+    const size_t smem = 2 * sizeof(uint32_t) * (size_t)p.tiles;
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_scatter_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid((unsigned)((p.n + kPerCta - 1) / kPerCta), (unsigned)cb);
+    k_scatter_hist<<<grid, 256, smem, s>>>(p.n, ws.rect, p.tiles_x, p.tiles, ws.tile_off, ws.tile_cur, ws.entries,
+                                           p.capacity, ws.status);
+    note_launches(1);
+    return;
+  }
   dim3 grid((unsigned)((p.n + 255) / 256), (unsigned)cb);
   k_scatter<<<grid, 256, 0, s>>>(p.n, ws.rect, p.tiles_x, p.tiles, ws.tile_off, ws.tile_cur,
                                  ws.entries, p.capacity, ws.status);
