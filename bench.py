@@ -320,6 +320,25 @@ def run_icgs(args, rank, world, local_rank):
         plain_ms = p0.elapsed_time(p1) / n_plain
         plain = {"ms_per_scene": plain_ms, "mixed_speedup": plain_ms / (elapsed_max / args.steps)}
 
+    # ---- the adjoint (the differentiation workload: dL/dt and dL/d(opacity) for L = sum r c^2) ----
+    adjoint = None
+    if args.workload == "relight":
+        c, st, chol = icgs.colorize(gs, gc, targets, L, precision=args.precision)
+        r = torch.randn(c.shape, generator=torch.Generator(device=dev).manual_seed(5005), device=dev)
+        gcoef = 2.0 * r * c
+        icgs.colorize_backward(gs, gc, targets, L, c, chol, gcoef, precision=args.precision)
+        n_adj = max(3, min(args.steps, 5))
+        barrier()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(n_adj):
+            icgs.colorize_backward(gs, gc, targets, L, c, chol, gcoef, precision=args.precision)
+        a1.record(stream)
+        barrier()
+        adjoint = {"ms_per_scene": a0.elapsed_time(a1) / n_adj, "outputs": "dL/dt [100,800,800,3] and dL/do [200000]",
+                   "launches": icgs.last_stats()["launches"]}
+
     if rank != 0:
         return
     pk = peaks()
@@ -377,6 +396,7 @@ def run_icgs(args, rank, world, local_rank):
         "stage_ms": stage_ms,
         "instances": inst, "contrib_pairs": pairs, "fp64_gaussians": stats["fp64"],
         "plain_fp32": plain,
+        "adjoint": adjoint,
     }
     print(json.dumps(line), flush=True)
 

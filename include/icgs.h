@@ -69,9 +69,11 @@ typedef enum { ICGS_F32 = 0, ICGS_BF16 = 1, ICGS_F16 = 2 } icgs_dtype;
 
 typedef enum {
   ICGS_PRECISION_PLAIN = 0, /* FP32 weights, CUDA-core contraction, plain FP32 fold and Cholesky */
-  ICGS_PRECISION_MIXED = 1  /* compensated FP32 fold, FP32 Cholesky with FP64 for Gaussians whose
-                               pivot ratio falls below cond_tau; 16-bit targets with >= 16
-                               channels contract on tcgen05 tensor cores (BF16/FP16 in, FP32 acc) */
+  ICGS_PRECISION_MIXED = 1  /* compensated FP32 fold, FP32 Cholesky refined in float-float; FP64
+                               for Gaussians whose pivot ratio falls below cond_tau (re-folded in
+                               double from the per-camera sums when all cameras fit one pass);
+                               16-bit targets with >= 16 channels contract on tcgen05 tensor cores
+                               (BF16/FP16 in, FP32 acc) */
 } icgs_precision;
 
 /* Per-Gaussian status written to status_out. */
@@ -108,8 +110,11 @@ typedef struct {
   const float* lambda;         /* host [(L+1)^2] Tikhonov weights lambda_m (Eq. 14); NULL selects
                                   the paper's values (Sec. 4): 1e-5 / 1e-4 / 1e-3 / 1e-2 per band */
   int32_t precision;           /* icgs_precision */
-  float cond_tau;              /* MIXED: FP64 refactorisation when min_k pivot_k / A_kk < cond_tau;
-                                  <= 0 selects 1e-3 */
+  float cond_tau;              /* MIXED: FP64 for a Gaussian when min_k pivot_k / A_kk < cond_tau.
+                                  With every camera in one pass, G and b are re-folded in double
+                                  from the per-camera sums (view directions and basis in double);
+                                  otherwise the compensated sums are factorised in double.
+                                  <= 0 selects 1e-2 for the first and 1e-3 for the second */
   int32_t cam_batch;           /* cameras accumulated per pass; <= 0 selects min(n_cams, 128) */
   int64_t instance_capacity;   /* (Gaussian, tile) instances per pass the workspace holds; <= 0
                                   selects an estimate (see ICGS_ERR_CAPACITY) */
@@ -129,6 +134,21 @@ ICGS_API icgs_status icgs_colorize(const icgs_scene* scene, const icgs_cameras* 
                           const icgs_targets* targets, const icgs_options* opt,
                           void* workspace, size_t workspace_bytes,
                           float* coeffs_out, uint8_t* status_out, float* chol_out, void* stream);
+
+/* Iterative refinement (Alg. 1 lines 7-10). Repeats n_steps times: render the images of the current
+ * coefficients (Eq. 1-3), accumulate the visibility-weighted residual targets t - img as in Eq. 6
+ * (V, Y and w are those of the fixed geometry), and update
+ *     c_i <- c_i + A_i^-1 (sum_j Y_ij S_res_ij^T - w_i Lambda c_i)
+ * with the factor of A_i = G_i + w_i Lambda that icgs_colorize returned (chol). coeffs_inout (device
+ * [n,(L+1)^2,K] float32) holds the coefficients of icgs_colorize on entry and the refined ones on
+ * return. The residual walk always runs on CUDA cores (FP32), whatever the target dtype. Needs the
+ * workspace size icgs_refine_workspace_size returns. */
+ICGS_API size_t icgs_refine_workspace_size(const icgs_scene* scene, const icgs_cameras* cams,
+                                           const icgs_targets* targets, const icgs_options* opt);
+ICGS_API icgs_status icgs_colorize_refine(const icgs_scene* scene, const icgs_cameras* cams,
+                                          const icgs_targets* targets, const icgs_options* opt,
+                                          int32_t n_steps, const float* chol, void* workspace,
+                                          size_t workspace_bytes, float* coeffs_inout, void* stream);
 
 /* Adjoint of icgs_colorize for a loss L(c): given dL/dc (grad_coeffs, device [n,(L+1)^2,K]),
  * the coefficients and Cholesky factors returned by icgs_colorize on the same inputs, writes

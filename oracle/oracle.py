@@ -87,7 +87,7 @@ def _ocam(cams, j):
     w = np.asarray(cams.world_to_cam[j], np.float32).astype(np.float64).reshape(-1)
     for k in range(12):
         c.w2c[k] = float(w[k])
-    c.near_z = float(cams.near_z)
+    c.near_z = float(np.float32(cams.near_z))  # the library receives near_z as float32
     return c
 
 
@@ -262,6 +262,27 @@ def colorize(scene, cams, targets, sh_degree, lam=None, mask=None, delta=1e-3, t
     c, status, A = solve(G, b, w, lam)
     return dict(c=c, status=status, V=V, S=S, Y=Y, G=G, b=b, w=w, A=A, lam=lam,
                 stake_own=so, stake_up=su, pairs=pairs)
+
+
+def refine(scene, cams, targets, sh_degree, lam, col, n_steps, threads=None):
+    """Iterative refinement (Alg. 1 lines 7-10), starting from colorize()'s result col: each step
+    renders the current coefficients (line 8), accumulates the visibility-weighted residual
+    targets t - img (line 9; V, Y, w and A stay those of the geometry) and updates
+    c <- c + A^-1 (sum_j Y_ij S_res_ij^T - w_i Lambda c_i) (line 10)."""
+    lam = paper_lambda(sh_degree) if lam is None else np.asarray(lam, np.float64)
+    c = col["c"].copy()
+    A, Y, w = col["A"], col["Y"], col["w"]
+    seen = w > 0
+    for _ in range(n_steps):
+        img = render(scene, cams, c, sh_degree, threads=threads)
+        _, S_res, _, _, _ = accumulate(scene, cams, targets - img, threads=threads)
+        b = np.einsum("cnb,cnk->nbk", Y, S_res)
+        rhs = b - w[:, None, None] * lam[None, :, None] * c
+        dc = np.zeros_like(c)
+        if seen.any():
+            dc[seen] = np.linalg.solve(A[seen], rhs[seen])
+        c = c + dc
+    return c
 
 
 def dense_lstsq(scene, cams, targets, sh_degree, lam=None):

@@ -82,7 +82,7 @@ icgs_status fail(icgs_status st, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail(ICGS_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
   } while (0)
 
-constexpr int kNeedAccumulate = 1, kNeedBackward = 2, kNeedRender = 4;
+constexpr int kNeedAccumulate = 1, kNeedBackward = 2, kNeedRender = 4, kNeedRefine = 8;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -123,6 +123,20 @@ Workspace carve(char* base, const Problem& p, int need) {
         ws.wlo = reinterpret_cast<float*>(take(sizeof(float) * n));
       }
     }
+  }
+  if (need & kNeedRefine) {  // residual sums, b and w (the Gram is fixed), colours and renders
+    const bool mixed = p.precision == ICGS_PRECISION_MIXED;
+    ws.acc = reinterpret_cast<float*>(take(sizeof(float) * (p.L == 0 ? n : (size_t)cbn) * (size_t)p.acc_stride));
+    if (p.L > 0) {
+      ws.bvec = reinterpret_cast<float*>(take(sizeof(float) * n * B * K));
+      ws.wsum = reinterpret_cast<float*>(take(sizeof(float) * n));
+      if (mixed) {
+        ws.blo = reinterpret_cast<float*>(take(sizeof(float) * n * B * K));
+        ws.wlo = reinterpret_cast<float*>(take(sizeof(float) * n));
+      }
+    }
+    ws.payload = reinterpret_cast<float*>(take(sizeof(float) * (size_t)cbn * K));
+    ws.img = reinterpret_cast<float*>(take(sizeof(float) * (size_t)p.cam_batch * p.width * p.height * K));
   }
   if (need & kNeedBackward) {
     ws.payload = reinterpret_cast<float*>(take(sizeof(float) * (size_t)cbn * (K + 1)));
@@ -174,7 +188,8 @@ icgs_status setup(const icgs_scene* sc, const icgs_cameras* cams, int K, int L, 
   p.L = L;
   p.B = (L + 1) * (L + 1);
   p.precision = precision;
-  p.cond_tau = cond_tau > 0.0f ? cond_tau : 1e-3f;
+  p.cond_tau = cond_tau > 0.0f ? cond_tau : 1e-2f;
+  p.cond_tau_sums = cond_tau > 0.0f ? cond_tau : 1e-3f;
   p.cam_batch = cam_batch > 0 ? std::min(cam_batch, p.n_cams) : std::min(p.n_cams, 128);
   p.cam_batch = std::min(p.cam_batch, 65535);  // grid y dimension of the per-pair kernels
   if ((int64_t)p.cam_batch * p.tiles > 0x7FFFFFFFll)
@@ -197,6 +212,7 @@ std::vector<DevCam> build_cams(const icgs_cameras* cams) {
       double s = 0.0;
       for (int r = 0; r < 3; ++r) s -= (double)w[4 * r + a] * (double)w[4 * r + 3];
       c.centre[a] = (float)s;
+      c.centre_d[a] = s;
     }
     c.limx = (float)(1.3 * ((double)cams->width / (2.0 * (double)in[0])));
     c.limy = (float)(1.3 * ((double)cams->height / (2.0 * (double)in[1])));
@@ -336,14 +352,15 @@ icgs_status icgs_colorize(const icgs_scene* scene, const icgs_cameras* cams, con
     if (p.L > 0)
       ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)cb * (size_t)p.n * p.acc_stride, s));
     if ((st = bin_pass(p, scene, cb, tc_accumulate_applies(p, (int)targets->dtype), wp, s)) != ICGS_OK) return st;
-    launch_blend_accumulate(p, cb, cam0, targets->data, (int)targets->dtype, wp, s);
+    launch_blend_accumulate(p, cb, cam0, targets->data, (int)targets->dtype, nullptr, wp, s);
     g_timer.mark(kBlend, s);
     if (p.L > 0) {
-      launch_fold(p, scene->means, cb, cam0 == 0, wp, s);
+      launch_fold(p, scene->means, cb, cam0 == 0, true, wp, s);
       g_timer.mark(kFold, s);
     }
   }
-  launch_solve(p, ws.lam, lam, ws, coeffs_out, status_out, chol_out, s);
+  launch_solve(p, ws.lam, lam, ws, coeffs_out, status_out, chol_out, scene->means,
+               p.cam_batch >= p.n_cams ? p.n_cams : 0, s);
   g_timer.mark(kSolve, s);
   return finish(ws, s);
 }
@@ -392,6 +409,67 @@ icgs_status icgs_colorize_backward(const icgs_scene* scene, const icgs_cameras* 
     g_timer.mark(kPayload, s);
     launch_blend_adjoint(p, cb, cam0, targets->data, (int)targets->dtype, wp, grad_targets, grad_opacity != nullptr, s);
     g_timer.mark(kBlend, s);
+  }
+  return finish(ws, s);
+}
+
+size_t icgs_refine_workspace_size(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
+                                  const icgs_options* opt) {
+  if (!targets || !opt) return 0;
+  Problem p;
+  if (setup(scene, cams, targets->channels, opt->sh_degree, opt->precision, opt->cond_tau, opt->cam_batch,
+            opt->instance_capacity, p) != ICGS_OK)
+    return 0;
+  return carve(nullptr, p, kNeedRefine).total;
+}
+
+icgs_status icgs_colorize_refine(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
+                                 const icgs_options* opt, int32_t n_steps, const float* chol, void* workspace,
+                                 size_t workspace_bytes, float* coeffs_inout, void* stream) {
+  g_err[0] = '\0';
+  if (!opt) return fail(ICGS_ERR_INVALID_ARG, "options must not be NULL");
+  icgs_status st = check_targets(targets);
+  if (st != ICGS_OK) return st;
+  Problem p;
+  st = setup(scene, cams, targets->channels, opt->sh_degree, opt->precision, opt->cond_tau, opt->cam_batch,
+             opt->instance_capacity, p);
+  if (st != ICGS_OK) return st;
+  if (n_steps < 0) return fail(ICGS_ERR_INVALID_ARG, "n_steps = %d must be >= 0", n_steps);
+  if ((!chol || !coeffs_inout) && p.n > 0) return fail(ICGS_ERR_INVALID_ARG, "chol and coeffs_inout are required");
+  float lam[kMaxSH];
+  if ((st = lambda_of(opt, p.L, lam)) != ICGS_OK) return st;
+  const Workspace need = carve(nullptr, p, kNeedRefine);
+  if (!workspace || workspace_bytes < need.total)
+    return fail(ICGS_ERR_WORKSPACE_TOO_SMALL, "workspace of %zu bytes, need %zu", workspace_bytes, need.total);
+  if (reinterpret_cast<uintptr_t>(workspace) % 256)
+    return fail(ICGS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Workspace ws = carve(static_cast<char*>(workspace), p, kNeedRefine);
+  if (p.n == 0 || n_steps == 0) return ICGS_OK;
+  if ((st = upload_common(p, cams, lam, ws, s)) != ICGS_OK) return st;
+  const bool one_pass = p.cam_batch >= p.n_cams;  // the binning of one pass is reused across steps
+  for (int step = 0; step < n_steps; ++step) {
+    if (p.L == 0) ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)p.n * p.acc_stride, s));
+    for (int cam0 = 0; cam0 < p.n_cams; cam0 += p.cam_batch) {
+      const int cb = std::min(p.cam_batch, p.n_cams - cam0);
+      Workspace wp = ws;
+      wp.cams = ws.cams + cam0;
+      if (p.L > 0)
+        ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)cb * (size_t)p.n * p.acc_stride, s));
+      if (!(one_pass && step > 0))
+        if ((st = bin_pass(p, scene, cb, false, wp, s)) != ICGS_OK) return st;
+      launch_payload_render(p, scene->means, coeffs_inout, cb, wp, s);  // Alg. 1 line 8: render
+      launch_blend_render(p, cb, 0, wp, ws.img, s);
+      g_timer.mark(kPayload, s);
+      launch_blend_accumulate(p, cb, cam0, targets->data, (int)targets->dtype, ws.img, wp, s);  // line 9
+      g_timer.mark(kBlend, s);
+      if (p.L > 0) {
+        launch_fold(p, scene->means, cb, cam0 == 0, false, wp, s);
+        g_timer.mark(kFold, s);
+      }
+    }
+    launch_refine_update(p, ws.lam, lam, chol, ws, coeffs_inout, s);  // line 10
+    g_timer.mark(kSolve, s);
   }
   return finish(ws, s);
 }

@@ -70,11 +70,11 @@ __device__ __forceinline__ float warp_transpose_reduce(float (&v)[NP], int lane)
 // colorize: V and S per (camera, Gaussian)
 // ------------------------------------------------------------------------------------------
 template <int KC>
-__global__ void __launch_bounds__(kThreads) k_blend_accumulate(
+__global__ void __launch_bounds__(kThreads, KC <= 3 ? 8 : (KC <= 8 ? 5 : 4)) k_blend_accumulate(
     const uint32_t* __restrict__ tile_off, const uint64_t* __restrict__ entries, uint32_t capacity,
     const ProjRec* __restrict__ rec, int64_t n, int width, int height, int tiles_x, int tiles,
-    const void* __restrict__ targets, int dtype, int K, int k0, int cam0, float* __restrict__ acc,
-    int RS, int64_t acc_cam_stride, DevStatus* status) {
+    const void* __restrict__ targets, int dtype, int K, int k0, int cam0, const float* __restrict__ sub_img,
+    float* __restrict__ acc, int RS, int64_t acc_cam_stride, DevStatus* status) {
   constexpr int NV = KC + 1;                      // V and S_0..S_{KC-1}
   constexpr int NP = NextPow2<NV>::value;
   constexpr int SHIFT = 5 - Log2<NP>::value;      // the sum of value v lands in lane v << SHIFT
@@ -94,6 +94,12 @@ __global__ void __launch_bounds__(kThreads) k_blend_accumulate(
 #pragma unroll
     for (int k = 0; k < KC; ++k)
       if (k0 + k < K) tv[k] = load_target(targets, base + k, dtype);
+    if (sub_img) {  // refinement: residual targets t - img, img of this pass's cameras
+      const int64_t ib = (((int64_t)c.j * height + c.py) * width + c.px) * K + k0;
+#pragma unroll
+      for (int k = 0; k < KC; ++k)
+        if (k0 + k < K) tv[k] -= sub_img[ib + k];
+    }
   }
   for (int k = threadIdx.x; k < kBatch * NV; k += kThreads) (&s_acc[0][0])[k] = 0.0f;
   const ProjRec* rec_cam = rec + (int64_t)c.j * n;
@@ -106,7 +112,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_accumulate(
   for (uint32_t start = 0; start < c.len; start += kBatch) {
     const int nb = (int)min((uint32_t)kBatch, c.len - start);
     __syncthreads();
-    load_batch(list, start, nb, rec_cam, n, s_box, s_par, s_thr, s_id);
+    load_batch(list, start, nb, rec_cam, n, c.ox, c.oy, s_box, s_par, s_thr, s_id);
     __syncthreads();
     if (!__all_sync(kFull, done)) {
 #pragma unroll
@@ -185,7 +191,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_render(
   for (uint32_t start = 0; start < c.len; start += kBatch) {
     const int nb = (int)min((uint32_t)kBatch, c.len - start);
     __syncthreads();
-    load_batch(list, start, nb, rec_cam, n, s_box, s_par, s_thr, s_id);
+    load_batch(list, start, nb, rec_cam, n, c.ox, c.oy, s_box, s_par, s_thr, s_id);
     __syncthreads();
     for (int idx = threadIdx.x; idx < nb * KC; idx += kThreads) {
       const int g = idx / KC, k = idx - g * KC;
@@ -238,7 +244,7 @@ __device__ __forceinline__ void load_payload(const float* __restrict__ pay_cam, 
 }
 
 template <int KC>
-__global__ void __launch_bounds__(kThreads) k_blend_adjoint(
+__global__ void __launch_bounds__(kThreads, KC <= 4 ? 6 : (KC <= 16 ? 4 : (KC <= 32 ? 2 : 1))) k_blend_adjoint(
     const uint32_t* __restrict__ tile_off, const uint64_t* __restrict__ entries, uint32_t capacity,
     const ProjRec* __restrict__ rec, int64_t n, int width, int height, int tiles_x, int tiles,
     const void* __restrict__ targets, int dtype, const float* __restrict__ payload, int K, int cam0,
@@ -271,7 +277,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_adjoint(
     for (uint32_t start = 0; start < c.len; start += kBatch) {
       const int nb = (int)min((uint32_t)kBatch, c.len - start);
       __syncthreads();
-      load_batch(list, start, nb, rec_cam, n, s_box, s_par, s_thr, s_id);
+      load_batch(list, start, nb, rec_cam, n, c.ox, c.oy, s_box, s_par, s_thr, s_id);
       __syncthreads();
       load_payload<KC>(pay_cam, nb, K, s_id, s_pay);
       __syncthreads();
@@ -313,7 +319,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_adjoint(
   for (uint32_t start = 0; start < c.len; start += kBatch) {
     const int nb = (int)min((uint32_t)kBatch, c.len - start);
     __syncthreads();
-    load_batch(list, start, nb, rec_cam, n, s_box, s_par, s_thr, s_id);
+    load_batch(list, start, nb, rec_cam, n, c.ox, c.oy, s_box, s_par, s_thr, s_id);
     __syncthreads();
     load_payload<KC>(pay_cam, nb, K, s_id, s_pay);
     __syncthreads();
@@ -362,11 +368,12 @@ __global__ void __launch_bounds__(kThreads) k_blend_adjoint(
 
 template <int KC>
 void accumulate_chunk(const Problem& p, int cb, int cam0, const void* targets, int dtype, int k0,
-                      const Workspace& ws, cudaStream_t s) {
+                      const float* sub_img, const Workspace& ws, cudaStream_t s) {
   const int64_t stride = p.L == 0 ? 0 : p.n * (int64_t)p.acc_stride;
   k_blend_accumulate<KC><<<cb * p.tiles, kThreads, 0, s>>>(ws.tile_off, ws.entries, p.capacity, ws.rec, p.n,
                                                             p.width, p.height, p.tiles_x, p.tiles, targets, dtype,
-                                                            p.K, k0, cam0, ws.acc, p.acc_stride, stride, ws.status);
+                                                            p.K, k0, cam0, sub_img, ws.acc, p.acc_stride, stride,
+                                                            ws.status);
   note_launches(1);
 }
 
@@ -385,19 +392,19 @@ void render_chunk(const Problem& p, int cb, int cam0, int k0, const Workspace& w
 // instantiated width that covers the remaining channels (1+KC values are reduced per Gaussian,
 // padded to a power of two).
 void launch_blend_accumulate(const Problem& p, int cb, int cam0, const void* targets, int dtype,
-                             const Workspace& ws, cudaStream_t s) {
-  if (tc_accumulate_applies(p, dtype)) {
+                             const float* sub_img, const Workspace& ws, cudaStream_t s) {
+  if (!sub_img && tc_accumulate_applies(p, dtype)) {
     launch_blend_accumulate_tc(p, cb, cam0, targets, dtype, ws, s);
     return;
   }
   for (int k0 = 0; k0 < p.K; k0 += 16) {
     const int kc = p.K - k0;
-    if (kc == 1) accumulate_chunk<1>(p, cb, cam0, targets, dtype, k0, ws, s);
-    else if (kc == 2) accumulate_chunk<2>(p, cb, cam0, targets, dtype, k0, ws, s);
-    else if (kc == 3) accumulate_chunk<3>(p, cb, cam0, targets, dtype, k0, ws, s);
-    else if (kc <= 7) accumulate_chunk<7>(p, cb, cam0, targets, dtype, k0, ws, s);
-    else if (kc <= 15) accumulate_chunk<15>(p, cb, cam0, targets, dtype, k0, ws, s);
-    else accumulate_chunk<16>(p, cb, cam0, targets, dtype, k0, ws, s);
+    if (kc == 1) accumulate_chunk<1>(p, cb, cam0, targets, dtype, k0, sub_img, ws, s);
+    else if (kc == 2) accumulate_chunk<2>(p, cb, cam0, targets, dtype, k0, sub_img, ws, s);
+    else if (kc == 3) accumulate_chunk<3>(p, cb, cam0, targets, dtype, k0, sub_img, ws, s);
+    else if (kc <= 7) accumulate_chunk<7>(p, cb, cam0, targets, dtype, k0, sub_img, ws, s);
+    else if (kc <= 15) accumulate_chunk<15>(p, cb, cam0, targets, dtype, k0, sub_img, ws, s);
+    else accumulate_chunk<16>(p, cb, cam0, targets, dtype, k0, sub_img, ws, s);
   }
 }
 

@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(256, 2) k_blend_accumulate_tc(
   bool timed_out = false;
   for (uint32_t start = 0; start < c.len; start += kG) {
     const int nb = (int)min((uint32_t)kG, c.len - start);
-    load_batch(reinterpret_cast<const unsigned long long*>(entries), c.b + start, nb, rec_cam, n, s_box, s_par,
+    load_batch(reinterpret_cast<const unsigned long long*>(entries), c.b + start, nb, rec_cam, n, c.ox, c.oy, s_box, s_par,
                s_thr, s_id);
     // the previous batch's MMAs have completed: clear W (16-byte stores), then write its nonzeros
     for (int i = threadIdx.x; i < kG * kKPix * 2 / 16; i += 256) reinterpret_cast<uint4*>(A_s)[i] = make_uint4(0, 0, 0, 0);

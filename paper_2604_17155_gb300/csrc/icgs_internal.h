@@ -35,10 +35,14 @@ struct DevCam {
   float centre[3];    // -R^T t (host double, rounded)
   float limx, limy;   // 1.3 * tan(fov/2) in x and y
   float pad;
+  double centre_d[3]; // -R^T t in double (the FP64 re-fold of ill-conditioned Gaussians)
 };
 
 // Projected Gaussian as the blend kernels read it: 32 bytes, one sector.
-//   box = (mean_x, mean_y, half-width, half-height) of the padded support box {q <= 2 ln(255 o)},
+//   box.x, box.y = hi parts of the projected mean (float-float: mean = hi + lo),
+//   box.z = fp16 pair (lo_x, lo_y) * kMeanLoScale (|lo| <= half an ulp of hi),
+//   box.w = fp16 pair (half-width, half-height) of the padded support box {q <= 2 ln(255 o)},
+//           rounded up so the box stays a superset,
 //   par = (conic_a, conic_b, conic_c, opacity) with q = a dx^2 + 2 b dx dy + c dy^2.
 struct ProjRec {
   float4 box;
@@ -71,6 +75,7 @@ struct Workspace {
   float* reg = nullptr;            // [n] backward: sum_mk lambda_m u_mk c_mk
   float* grad_o_acc = nullptr;     // [n]
   float* lam = nullptr;            // [B] Tikhonov weights
+  float* img = nullptr;            // [cb * H * W * K] refinement: renders of the pass's cameras
   size_t total = 0;
 };
 
@@ -84,7 +89,8 @@ struct Problem {
   int cam_batch = 0;
   uint32_t capacity = 0;
   int precision = 0;
-  float cond_tau = 1e-3f;
+  float cond_tau = 1e-2f;       // FP64 re-fold from resident per-camera sums (single pass)
+  float cond_tau_sums = 1e-3f;  // FP64 solve from the compensated sums (several passes)
   int mode = 0;                     // 0 colorize, 1 backward, 2 render
 };
 
@@ -100,18 +106,26 @@ void launch_project(const Problem& p, const float* means, const float* scales, c
 void launch_scan(const Problem& p, int cb, const Workspace& ws, cudaStream_t s);
 void launch_scatter(const Problem& p, int cb, const Workspace& ws, cudaStream_t s);
 void launch_tile_sort(const Problem& p, int cb, bool sort_all, const Workspace& ws, cudaStream_t s);
+// sub_img (nullable, float32 [cb,H,W,K] of this pass's cameras): accumulate t - img instead of t
+// (refinement); forces the CUDA-core walk.
 void launch_blend_accumulate(const Problem& p, int cb, int cam0, const void* targets, int dtype,
-                             const Workspace& ws, cudaStream_t s);
+                             const float* sub_img, const Workspace& ws, cudaStream_t s);
 // Tensor-core contraction of the accumulate walk (MIXED precision, 16-bit targets, 16..64 channels).
 bool tc_accumulate_applies(const Problem& p, int dtype);
 void launch_blend_accumulate_tc(const Problem& p, int cb, int cam0, const void* targets, int dtype,
                                 const Workspace& ws, cudaStream_t s);
 cudaError_t launch_tc_selftest(const uint16_t* A, const uint16_t* B, int N, bool bf16, float* D,
                                DevStatus* status, cudaStream_t s);
-void launch_fold(const Problem& p, const float* means, int cb, bool first, const Workspace& ws,
+void launch_fold(const Problem& p, const float* means, int cb, bool first, bool want_gram, const Workspace& ws,
                  cudaStream_t s);
+// c += A^-1 (b - w Lambda c) from the stored factor (refinement, Alg. 1 line 10).
+void launch_refine_update(const Problem& p, const float* lam_dev, const float* lam_host, const float* chol,
+                          const Workspace& ws, float* coeffs, cudaStream_t s);
+// means/cams/n_acc_cams: when every camera was accumulated in one pass (n_acc_cams > 0), a MIXED
+// solve re-folds each Gaussian it flags in FP64 from the per-camera sums still in ws.acc.
 void launch_solve(const Problem& p, const float* lam_dev, const float* lam_host, const Workspace& ws,
-                  float* coeffs, uint8_t* status, float* chol, cudaStream_t s);
+                  float* coeffs, uint8_t* status, float* chol, const float* means, int n_acc_cams,
+                  cudaStream_t s);
 void launch_payload_render(const Problem& p, const float* means, const float* coeffs, int cb,
                            const Workspace& ws, cudaStream_t s);
 void launch_blend_render(const Problem& p, int cb, int cam0, const Workspace& ws, float* images,

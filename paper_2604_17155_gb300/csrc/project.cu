@@ -7,6 +7,15 @@
 // of z evaluated in double with the fixed, unfused sequence ((W20 x + W21 y) + W22 z) + W23, so the
 // ordering key is a well-defined function of the inputs.
 //
+// Precision. alpha = o exp(-q/2) is sensitive to the offset between a pixel centre and the mean:
+// for a one-pixel Gaussian an error of 1e-4 px in the mean moves alpha by about 1e-4 relative,
+// and a float32 mean near x = 400 is already rounded by 1.5e-5 px. The projected mean is therefore
+// evaluated in float-float arithmetic (error-free products and sums, Dekker/Knuth) and stored as
+// hi + lo; the walk subtracts it from tile-relative pixel centres. The conic is formed from
+// P = T M (T = J W, Sigma = M M^T), with det(P P^T + 0.3 I) = sum of the squared 2x2 minors of P
+// + 0.3 tr(P P^T) + 0.09 (Cauchy-Binet): a sum of non-negative terms, where the textbook
+// a c - b^2 cancels for thin projected Gaussians.
+//
 // Binning is a counting sort: k_project_hist counts instances per tile, an exclusive scan turns
 // counts into offsets, and k_scatter_hist writes (depth key << 32 | index) into each tile's slot
 // range. Both work on CTAs of 2048 Gaussians of one camera that count in a shared-memory
@@ -20,6 +29,49 @@
 namespace icgs {
 
 namespace {
+
+// error-free transformations: s + e = a + b exactly (Knuth), p + e = a b exactly (FMA)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+
+// a x + b y + c z + d as hi + lo (float-float; relative error near 2^-44 of the largest term)
+__device__ __forceinline__ float affine_ff(float a, float b, float c, float d, float x, float y, float z, float& lo) {
+  float p0, e0, p1, e1, p2, e2, s, t0, t1, t2;
+  two_prod(a, x, p0, e0);
+  two_prod(b, y, p1, e1);
+  two_prod(c, z, p2, e2);
+  two_sum(p0, p1, s, t0);
+  two_sum(s, p2, s, t1);
+  two_sum(s, d, s, t2);
+  const float l = __fadd_rn(__fadd_rn(__fadd_rn(e0, e1), __fadd_rn(e2, t0)), __fadd_rn(t1, t2));
+  const float hi = __fadd_rn(s, l);
+  lo = __fsub_rn(l, __fsub_rn(hi, s));
+  return hi;
+}
+
+// f (uh + ul) / (zh + zl) + c as hi + lo; iz is a float32 reciprocal of zh. The quotient's
+// correction comes from the remainder uh - qh zh, which one FMA gives exactly.
+__device__ __forceinline__ float pixel_ff(float f, float c, float uh, float ul, float zh, float zl, float iz,
+                                          float& lo) {
+  const float qh = __fmul_rn(uh, iz);
+  const float r = __fadd_rn(__fmaf_rn(-qh, zh, uh), __fsub_rn(ul, __fmul_rn(qh, zl)));
+  const float ql = __fmul_rn(r, iz);
+  float ph, pe, sh, se;
+  two_prod(f, qh, ph, pe);
+  pe = __fmaf_rn(f, ql, pe);
+  two_sum(ph, c, sh, se);
+  se = __fadd_rn(se, pe);
+  const float hi = __fadd_rn(sh, se);
+  lo = __fsub_rn(se, __fsub_rn(hi, sh));
+  return hi;
+}
 
 __device__ __forceinline__ double depth_f64(const DevCam& c, float x, float y, float z) {
   double t = __dadd_rn(__dmul_rn((double)c.w[8], (double)x), __dmul_rn((double)c.w[9], (double)y));
@@ -42,8 +94,10 @@ __device__ __forceinline__ int4 project_pair(const float* __restrict__ means, co
     return none;
   }
   const float tz = __double2float_rn(zd);
-  const float tx = fmaf(c.w[0], mx3, fmaf(c.w[1], my3, fmaf(c.w[2], mz3, c.w[3])));
-  const float ty = fmaf(c.w[4], mx3, fmaf(c.w[5], my3, fmaf(c.w[6], mz3, c.w[7])));
+  const float tz_lo = __double2float_rn(zd - (double)tz);
+  float tx_lo, ty_lo;
+  const float tx = affine_ff(c.w[0], c.w[1], c.w[2], c.w[3], mx3, my3, mz3, tx_lo);
+  const float ty = affine_ff(c.w[4], c.w[5], c.w[6], c.w[7], mx3, my3, mz3, ty_lo);
 
   // 3D covariance Sigma = M M^T with M = R(q) diag(s)
   float qw = quats[4 * i], qx = quats[4 * i + 1], qy = quats[4 * i + 2], qz = quats[4 * i + 3];
@@ -56,12 +110,6 @@ __device__ __forceinline__ int4 project_pair(const float* __restrict__ means, co
   const float m00 = r00 * sx, m01 = r01 * sy, m02 = r02 * sz;
   const float m10 = r10 * sx, m11 = r11 * sy, m12 = r12 * sz;
   const float m20 = r20 * sx, m21 = r21 * sy, m22 = r22 * sz;
-  const float s00 = m00 * m00 + m01 * m01 + m02 * m02;
-  const float s01 = m00 * m10 + m01 * m11 + m02 * m12;
-  const float s02 = m00 * m20 + m01 * m21 + m02 * m22;
-  const float s11 = m10 * m10 + m11 * m11 + m12 * m12;
-  const float s12 = m10 * m20 + m11 * m21 + m12 * m22;
-  const float s22 = m20 * m20 + m21 * m21 + m22 * m22;
 
   // EWA: T = J W (2x3), J at the clamped camera-space mean
   const float iz = 1.0f / tz;
@@ -71,19 +119,20 @@ __device__ __forceinline__ int4 project_pair(const float* __restrict__ means, co
   const float j11 = c.fy * iz, j12 = -c.fy * uy * iz;
   const float t00 = j00 * c.w[0] + j02 * c.w[8], t01 = j00 * c.w[1] + j02 * c.w[9], t02 = j00 * c.w[2] + j02 * c.w[10];
   const float t10 = j11 * c.w[4] + j12 * c.w[8], t11 = j11 * c.w[5] + j12 * c.w[9], t12 = j11 * c.w[6] + j12 * c.w[10];
-  // Sigma' = T Sigma T^T + 0.3 I
-  const float u0 = s00 * t00 + s01 * t01 + s02 * t02;
-  const float u1 = s01 * t00 + s11 * t01 + s12 * t02;
-  const float u2 = s02 * t00 + s12 * t01 + s22 * t02;
-  const float v0 = s00 * t10 + s01 * t11 + s02 * t12;
-  const float v1 = s01 * t10 + s11 * t11 + s12 * t12;
-  const float v2 = s02 * t10 + s12 * t11 + s22 * t12;
-  const float ca2 = t00 * u0 + t01 * u1 + t02 * u2 + 0.3f;
-  const float cb2 = t10 * u0 + t11 * u1 + t12 * u2;
-  const float cc2 = t10 * v0 + t11 * v1 + t12 * v2 + 0.3f;
-  const float det = ca2 * cc2 - cb2 * cb2;
-  const float mx = fmaf(c.fx, tx * iz, c.cx);
-  const float my = fmaf(c.fy, ty * iz, c.cy);
+  // Sigma' = P P^T + 0.3 I with P = T M (2x3)
+  const float p00 = t00 * m00 + t01 * m10 + t02 * m20, p01 = t00 * m01 + t01 * m11 + t02 * m21;
+  const float p02 = t00 * m02 + t01 * m12 + t02 * m22;
+  const float p10 = t10 * m00 + t11 * m10 + t12 * m20, p11 = t10 * m01 + t11 * m11 + t12 * m21;
+  const float p12 = t10 * m02 + t11 * m12 + t12 * m22;
+  const float n0 = p00 * p00 + p01 * p01 + p02 * p02, n1 = p10 * p10 + p11 * p11 + p12 * p12;
+  const float ca2 = n0 + 0.3f;
+  const float cb2 = p00 * p10 + p01 * p11 + p02 * p12;
+  const float cc2 = n1 + 0.3f;
+  const float d01 = fmaf(p00, p11, -p01 * p10), d02 = fmaf(p00, p12, -p02 * p10), d12 = fmaf(p01, p12, -p02 * p11);
+  const float det = (d01 * d01 + d02 * d02 + d12 * d12) + 0.3f * (n0 + n1) + 0.09f;
+  float mx_lo, my_lo;
+  const float mx = pixel_ff(c.fx, c.cx, tx, tx_lo, tz, tz_lo, iz, mx_lo);
+  const float my = pixel_ff(c.fy, c.cy, ty, ty_lo, tz, tz_lo, iz, my_lo);
   if (!(det > 0.0f) || !isfinite(mx) || !isfinite(my)) {
     rect[ji] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
     return none;
@@ -103,7 +152,11 @@ __device__ __forceinline__ int4 project_pair(const float* __restrict__ means, co
   const int tx0 = (int)fx0 / kTile, tx1 = (int)fx1 / kTile;
   const int ty0 = (int)fy0 / kTile, ty1 = (int)fy1 / kTile;
   ProjRec r;
-  r.box = make_float4(mx, my, hx, hy);
+  const bool lo_ok = fabsf(mx) < 1048576.0f && fabsf(my) < 1048576.0f;  // fp16 holds lo * 2^8 there
+  r.box = make_float4(mx, my,
+                      pack_half2(__float2half_rn(lo_ok ? mx_lo * kMeanLoScale : 0.0f),
+                                 __float2half_rn(lo_ok ? my_lo * kMeanLoScale : 0.0f)),
+                      pack_half2(__float2half_ru(hx), __float2half_ru(hy)));
   r.par = make_float4(cc2 * idet, -cb2 * idet, ca2 * idet, o);
   rec[ji] = r;
   rect[ji] = make_uint4((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16),

@@ -24,6 +24,7 @@ namespace {
 constexpr int kGroup = 16;
 constexpr int kSolveThreads = 128;  // 8 Gaussians per CTA
 constexpr float kY0 = 0.28209479177387814f;
+constexpr int kFoldBlock = 4;  // cameras summed in plain FP32 before a compensated add (MIXED)
 
 // Shuffles name only the 16 lanes of the caller's group, so a neighbouring group that has
 // finished (or never started) in the same warp does not take part.
@@ -44,14 +45,15 @@ __device__ __forceinline__ F group_sum(F v) {
 template <int B, int KC, bool MIXED>
 __global__ void __launch_bounds__(kSolveThreads) k_fold(
     const float* __restrict__ means, int64_t n, const DevCam* __restrict__ cams, int cb,
-    const float* __restrict__ acc, int K, int RS, int k0, bool first, float* __restrict__ G,
+    const float* __restrict__ acc, int K, int RS, int k0, bool first, bool want_gram, float* __restrict__ G,
     float* __restrict__ Glo, float* __restrict__ bvec, float* __restrict__ blo,
     float* __restrict__ wsum, float* __restrict__ wlo) {
   const int64_t i = (blockIdx.x * (int64_t)kSolveThreads + threadIdx.x) / kGroup;
   const int r = threadIdx.x % kGroup;
   if (i >= n) return;  // whole groups exit together
   const bool row = r < B;
-  const bool do_gram = k0 == 0;
+  const bool do_gram = k0 == 0 && want_gram;  // G (skipped by refinement, whose Gram is fixed)
+  const bool do_w = k0 == 0;
   float g[B], gl[B], bb[KC], bl[KC];
   float w = 0.0f, wl = 0.0f;
 #pragma unroll
@@ -65,6 +67,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_fold(
         g[c] = G[(i * B + r) * B + c];
         if (MIXED) gl[c] = Glo[(i * B + r) * B + c];
       }
+    }
+    if (do_w) {
       w = wsum[i];
       if (MIXED) wl = wlo[i];
     }
@@ -77,35 +81,75 @@ __global__ void __launch_bounds__(kSolveThreads) k_fold(
   }
   const float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
   const int64_t stride = n * (int64_t)RS;
-  for (int j = 0; j < cb; ++j) {
-    const float* a = acc + j * stride + i * RS;
-    const float v = a[0];
-    if (!(v > 0.0f)) continue;
-    const float3 d = view_dir(mu, cams[j]);
-    float Y[B];
-    sh_basis<B>(d.x, d.y, d.z, Y);
-    if (!row) continue;
-    float Yr = Y[0];
+  // MIXED: plain FP32 partial sums over blocks of kFoldBlock cameras, each block added to the
+  // running (hi, lo) pair with one TwoSum
+  float pg[B], pb[KC], pw = 0.0f;
 #pragma unroll
-    for (int c = 1; c < B; ++c)
-      if (c == r) Yr = Y[c];
-    if (do_gram) {
-      const float vy = v * Yr;
+  for (int c = 0; c < B; ++c) pg[c] = 0.0f;
+#pragma unroll
+  for (int k = 0; k < KC; ++k) pb[k] = 0.0f;
+  const unsigned gm = group_mask();
+  // 16 cameras at a time: lane q loads camera jb + q's row (V, S), the group shares it by shuffles
+  for (int jb = 0; jb < cb; jb += kGroup) {
+   float lv = 0.0f, ls[KC];
+#pragma unroll
+   for (int k = 0; k < KC; ++k) ls[k] = 0.0f;
+   if (jb + r < cb) {
+     const float* a = acc + (int64_t)(jb + r) * stride + i * RS;
+     lv = a[0];
+#pragma unroll
+     for (int k = 0; k < KC; ++k)
+       if (k0 + k < K) ls[k] = a[1 + k0 + k];
+   }
+   const int nj = min(kGroup, cb - jb);
+   for (int q = 0; q < nj; ++q) {
+    const int j = jb + q;
+    const float v = __shfl_sync(gm, lv, q, kGroup);
+    float sv[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) sv[k] = __shfl_sync(gm, ls[k], q, kGroup);
+    if (v > 0.0f) {
+      const float3 d = view_dir(mu, cams[j]);
+      float Y[B];
+      sh_basis<B>(d.x, d.y, d.z, Y);
+      float Yr = Y[0];
+#pragma unroll
+      for (int c = 1; c < B; ++c)
+        if (c == r) Yr = Y[c];
+      if (do_gram) {
+        const float vy = v * Yr;
+#pragma unroll
+        for (int c = 0; c < B; ++c) {
+          if constexpr (MIXED) pg[c] = fmaf(vy, Y[c], pg[c]);
+          else g[c] = fmaf(vy, Y[c], g[c]);
+        }
+      }
+      if (do_w) {
+        if constexpr (MIXED) pw += v;
+        else w += v;
+      }
+#pragma unroll
+      for (int k = 0; k < KC; ++k)
+        if (k0 + k < K) {
+          if constexpr (MIXED) pb[k] = fmaf(Yr, sv[k], pb[k]);
+          else bb[k] = fmaf(Yr, sv[k], bb[k]);
+        }
+    }
+    if (MIXED && ((j % kFoldBlock) == kFoldBlock - 1 || j == cb - 1)) {
 #pragma unroll
       for (int c = 0; c < B; ++c) {
-        if (MIXED) two_sum_acc(g[c], gl[c], vy * Y[c]);
-        else g[c] = fmaf(vy, Y[c], g[c]);
+        two_sum_acc(g[c], gl[c], pg[c]);
+        pg[c] = 0.0f;
       }
-      if (MIXED) two_sum_acc(w, wl, v);
-      else w += v;
-    }
+      two_sum_acc(w, wl, pw);
+      pw = 0.0f;
 #pragma unroll
-    for (int k = 0; k < KC; ++k)
-      if (k0 + k < K) {
-        const float s = a[1 + k0 + k];
-        if (MIXED) two_sum_acc(bb[k], bl[k], Yr * s);
-        else bb[k] = fmaf(Yr, s, bb[k]);
+      for (int k = 0; k < KC; ++k) {
+        two_sum_acc(bb[k], bl[k], pb[k]);
+        pb[k] = 0.0f;
       }
+    }
+   }
   }
   if (!row) return;
   if (do_gram) {
@@ -114,10 +158,10 @@ __global__ void __launch_bounds__(kSolveThreads) k_fold(
       G[(i * B + r) * B + c] = g[c];
       if (MIXED) Glo[(i * B + r) * B + c] = gl[c];
     }
-    if (r == 0) {
-      wsum[i] = w;
-      if (MIXED) wlo[i] = wl;
-    }
+  }
+  if (do_w && r == 0) {
+    wsum[i] = w;
+    if (MIXED) wlo[i] = wl;
   }
 #pragma unroll
   for (int k = 0; k < KC; ++k)
@@ -215,7 +259,10 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(
     const float* __restrict__ bvec, const float* __restrict__ blo, const float* __restrict__ wsum,
     const float* __restrict__ wlo, const float* __restrict__ lam, float cond_tau,
     float* __restrict__ coeffs, uint8_t* __restrict__ status_out, float* __restrict__ chol,
-    DevStatus* status) {
+    DevStatus* status, const float* __restrict__ acc, int RS, int n_acc_cams,
+    const DevCam* __restrict__ cams, const float* __restrict__ means) {
+  // MIXED: per lane, the double basis of the camera it evaluates in the FP64 re-fold
+  __shared__ double s_Y[MIXED ? kSolveThreads : 1][B + 1];
   const int64_t i = (blockIdx.x * (int64_t)kSolveThreads + threadIdx.x) / kGroup;
   const int r = threadIdx.x % kGroup;
   if (i >= n) return;
@@ -274,19 +321,92 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(
     if (r == 0 && status_out) status_out[i] = kGaussOk;
     return;
   }
-  // FP64 refactorisation from the compensated sums
+  // FP64 for this ill-conditioned Gaussian. With every camera's sums still resident, G and b are
+  // re-folded in double (view directions and basis in double, from the same per-camera V and S);
+  // otherwise the compensated (hi + lo) sums are used.
   double ad[B];
-  const double wd = (double)w + (double)(wlo ? wlo[i] : 0.0f);
+  if (n_acc_cams > 0) {
+    // One walk over the cameras per chunk of 4 channels (the first also folds row r of G and w).
+    // Lane q of the group evaluates camera jb + q's direction and basis in double and leaves them
+    // in shared memory; every lane then takes the 16 cameras in turn from there.
+    double wd = 0.0;
 #pragma unroll
-  for (int c = 0; c < B; ++c) {
-    ad[c] = row ? (double)G[(i * B + r) * B + c] + (double)Glo[(i * B + r) * B + c] : 0.0;
-    if (c == r) ad[c] += wd * (double)lam_r;
-  }
-  group_cholesky<B, double>(ad, r);
-  for (int k = 0; k < K; ++k) {
-    double x = row ? (double)bvec[(i * B + r) * K + k] + (double)blo[(i * B + r) * K + k] : 0.0;
-    group_chol_solve<B, double>(ad, r, x);
-    if (row) coeffs[(i * B + r) * K + k] = (float)x;
+    for (int c = 0; c < B; ++c) ad[c] = 0.0;
+    const unsigned gm = group_mask();
+    const int gbase = threadIdx.x & ~(kGroup - 1);
+    const double mu0 = means[3 * i], mu1 = means[3 * i + 1], mu2 = means[3 * i + 2];
+    const int64_t cam_stride = n * (int64_t)RS;
+    for (int k0 = 0; k0 < K || k0 == 0; k0 += 4) {
+      double bk[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int jb = 0; jb < n_acc_cams; jb += kGroup) {
+        const int jq = jb + r;
+        float vq = 0.0f, sq[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (jq < n_acc_cams) {
+          const float* a = acc + jq * cam_stride + i * RS;
+          vq = a[0];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (k0 + q < K) sq[q] = a[1 + k0 + q];
+        }
+        if (vq > 0.0f) {
+          const DevCam& cj = cams[jq];
+          const double dx = mu0 - cj.centre_d[0], dy = mu1 - cj.centre_d[1], dz = mu2 - cj.centre_d[2];
+          const double inv = 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
+          sh_basis<B, double>(dx * inv, dy * inv, dz * inv, s_Y[threadIdx.x]);
+        }
+        __syncwarp(gm);
+        const int nj = min(kGroup, n_acc_cams - jb);
+        for (int q = 0; q < nj; ++q) {
+          const float v = __shfl_sync(gm, vq, q, kGroup);
+          float sv[4];
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) sv[qq] = __shfl_sync(gm, sq[qq], q, kGroup);
+          if (!(v > 0.0f)) continue;  // uniform in the group
+          const double* yq = s_Y[gbase + q];
+          const double Yr = row ? yq[r] : 0.0;
+          if (k0 == 0) {
+            const double vy = (double)v * Yr;
+#pragma unroll
+            for (int c = 0; c < B; ++c) ad[c] += vy * yq[c];
+            wd += (double)v;
+          }
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq)
+            if (k0 + qq < K) bk[qq] += Yr * (double)sv[qq];
+        }
+        __syncwarp(gm);
+      }
+      if (k0 == 0) {
+#pragma unroll
+        for (int c = 0; c < B; ++c)
+          if (c == r) ad[c] += wd * (double)lam_r;
+        if (!row) {
+#pragma unroll
+          for (int c = 0; c < B; ++c) ad[c] = 0.0;
+        }
+        group_cholesky<B, double>(ad, r);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (k0 + q >= K) break;
+        double x = row ? bk[q] : 0.0;
+        group_chol_solve<B, double>(ad, r, x);
+        if (row) coeffs[(i * B + r) * K + k0 + q] = (float)x;
+      }
+    }
+  } else {
+    const double wd = (double)w + (double)(wlo ? wlo[i] : 0.0f);
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      ad[c] = row ? (double)G[(i * B + r) * B + c] + (double)Glo[(i * B + r) * B + c] : 0.0;
+      if (c == r) ad[c] += wd * (double)lam_r;
+    }
+    group_cholesky<B, double>(ad, r);
+    for (int k = 0; k < K; ++k) {
+      double x = row ? (double)bvec[(i * B + r) * K + k] + (double)blo[(i * B + r) * K + k] : 0.0;
+      group_chol_solve<B, double>(ad, r, x);
+      if (row) coeffs[(i * B + r) * K + k] = (float)x;
+    }
   }
   if (chol && row) {
 #pragma unroll
@@ -369,6 +489,50 @@ __global__ void k_adjoint_prep_l0(int64_t n, int K, const float* __restrict__ ch
 }
 
 // ------------------------------------------------------------------------------------------
+// refinement update (Alg. 1 line 10): c <- c + A^-1 (b - w Lambda c), A from its stored factor
+// ------------------------------------------------------------------------------------------
+template <int B, bool MIXED>
+__global__ void __launch_bounds__(kSolveThreads) k_refine_update(
+    int64_t n, int K, const float* __restrict__ chol, const float* __restrict__ bvec,
+    const float* __restrict__ blo, const float* __restrict__ wsum, const float* __restrict__ wlo,
+    const float* __restrict__ lam, float* __restrict__ coeffs) {
+  const int64_t i = (blockIdx.x * (int64_t)kSolveThreads + threadIdx.x) / kGroup;
+  const int r = threadIdx.x % kGroup;
+  if (i >= n) return;
+  const bool row = r < B;
+  float a[B];
+#pragma unroll
+  for (int c = 0; c < B; ++c) a[c] = (row && c <= r) ? chol[i * (B * (B + 1) / 2) + r * (r + 1) / 2 + c] : 0.0f;
+  const float l00 = __shfl_sync(group_mask(), a[0], 0, kGroup);
+  if (!(l00 > 0.0f)) return;  // unseen: the coefficients stay 0 (whole group)
+  const float w = wsum[i] + (MIXED ? wlo[i] : 0.0f);
+  const float wl = row ? w * lam[r] : 0.0f;
+  for (int k = 0; k < K; ++k) {
+    float x = 0.0f;
+    if (row) {
+      const float b = bvec[(i * B + r) * K + k] + (MIXED ? blo[(i * B + r) * K + k] : 0.0f);
+      x = b - wl * coeffs[(i * B + r) * K + k];
+    }
+    group_chol_solve<B, float>(a, r, x);
+    if (row) coeffs[(i * B + r) * K + k] += x;
+  }
+}
+
+// L = 0: b = S / sqrt(4 pi) and A = w (1/(4 pi) + lambda) from acc, summed over every camera.
+__global__ void k_refine_update_l0(int64_t n, int K, int RS, const float* __restrict__ acc, float lam0,
+                                   float* __restrict__ coeffs) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n * (int64_t)K) return;
+  const int64_t i = idx / K;
+  const int k = (int)(idx - i * K);
+  const float V = acc[i * RS];
+  if (!(V > 0.0f)) return;
+  const float A = V * (kY0 * kY0 + lam0);
+  const float c = coeffs[i * K + k];
+  coeffs[i * K + k] = c + (kY0 * acc[i * RS + 1 + k] - V * lam0 * c) / A;
+}
+
+// ------------------------------------------------------------------------------------------
 // per (camera, Gaussian) payloads
 // ------------------------------------------------------------------------------------------
 template <int B>
@@ -425,33 +589,36 @@ __global__ void k_payload_adjoint(int64_t n, int K, const float* __restrict__ me
 }
 
 template <int B, bool MIXED>
-void fold_b(const Problem& p, const float* means, int cb, const Workspace& ws, bool first, cudaStream_t s) {
+void fold_b(const Problem& p, const float* means, int cb, const Workspace& ws, bool first, bool want_gram,
+            cudaStream_t s) {
   const unsigned grid = (unsigned)((p.n * kGroup + kSolveThreads - 1) / kSolveThreads);
   for (int k0 = 0; k0 < p.K; k0 += 4) {
-    k_fold<B, 4, MIXED><<<grid, kSolveThreads, 0, s>>>(means, p.n, ws.cams, cb, ws.acc, p.K, p.acc_stride, k0, first, ws.G, ws.Glo,
-                                                        ws.bvec, ws.blo, ws.wsum, ws.wlo);
+    k_fold<B, 4, MIXED><<<grid, kSolveThreads, 0, s>>>(means, p.n, ws.cams, cb, ws.acc, p.K, p.acc_stride, k0, first,
+                                                        want_gram, ws.G, ws.Glo, ws.bvec, ws.blo, ws.wsum, ws.wlo);
     note_launches(1);
   }
 }
 
 template <int B, bool MIXED>
 void solve_b(const Problem& p, const float* lam_dev, const Workspace& ws, float* coeffs, uint8_t* st,
-             float* chol, cudaStream_t s) {
+             float* chol, const float* means, int n_acc_cams, cudaStream_t s) {
   const unsigned grid = (unsigned)((p.n * kGroup + kSolveThreads - 1) / kSolveThreads);
   k_solve<B, MIXED><<<grid, kSolveThreads, 0, s>>>(p.n, p.K, ws.G, ws.Glo, ws.bvec, ws.blo, ws.wsum, ws.wlo,
-                                                       lam_dev, p.cond_tau, coeffs, st, chol, ws.status);
+                                                       lam_dev, n_acc_cams > 0 ? p.cond_tau : p.cond_tau_sums,
+                                                       coeffs, st, chol, ws.status, ws.acc,
+                                                       p.acc_stride, n_acc_cams, ws.cams, means);
   note_launches(1);
 }
 
 }  // namespace
 
 // The first pass of a call writes G, b, w; later passes add to them.
-void launch_fold(const Problem& p, const float* means, int cb, bool first, const Workspace& ws,
-                      cudaStream_t s) {
+void launch_fold(const Problem& p, const float* means, int cb, bool first, bool want_gram, const Workspace& ws,
+                 cudaStream_t s) {
   const bool mixed = p.precision == 1;
-#define ICGS_FOLD(B)                                         \
-  if (mixed) fold_b<B, true>(p, means, cb, ws, first, s);   \
-  else fold_b<B, false>(p, means, cb, ws, first, s)
+#define ICGS_FOLD(B)                                                    \
+  if (mixed) fold_b<B, true>(p, means, cb, ws, first, want_gram, s);   \
+  else fold_b<B, false>(p, means, cb, ws, first, want_gram, s)
   if (p.B == 4) { ICGS_FOLD(4); }
   else if (p.B == 9) { ICGS_FOLD(9); }
   else { ICGS_FOLD(16); }
@@ -459,7 +626,8 @@ void launch_fold(const Problem& p, const float* means, int cb, bool first, const
 }
 
 void launch_solve(const Problem& p, const float* lam_dev, const float* lam_host, const Workspace& ws,
-                  float* coeffs, uint8_t* status, float* chol, cudaStream_t s) {
+                  float* coeffs, uint8_t* status, float* chol, const float* means, int n_acc_cams,
+                  cudaStream_t s) {
   if (p.B == 1) {
     const int64_t m = p.n * (int64_t)p.K;
     k_solve_l0<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(p.n, p.K, p.acc_stride, ws.acc, lam_host[0], coeffs, status, chol);
@@ -467,13 +635,37 @@ void launch_solve(const Problem& p, const float* lam_dev, const float* lam_host,
     return;
   }
   const bool mixed = p.precision == 1;
-#define ICGS_SOLVE(B)                                                       \
-  if (mixed) solve_b<B, true>(p, lam_dev, ws, coeffs, status, chol, s);    \
-  else solve_b<B, false>(p, lam_dev, ws, coeffs, status, chol, s)
+#define ICGS_SOLVE(B)                                                                              \
+  if (mixed) solve_b<B, true>(p, lam_dev, ws, coeffs, status, chol, means, n_acc_cams, s);       \
+  else solve_b<B, false>(p, lam_dev, ws, coeffs, status, chol, means, n_acc_cams, s)
   if (p.B == 4) { ICGS_SOLVE(4); }
   else if (p.B == 9) { ICGS_SOLVE(9); }
   else { ICGS_SOLVE(16); }
 #undef ICGS_SOLVE
+}
+
+void launch_refine_update(const Problem& p, const float* lam_dev, const float* lam_host, const float* chol,
+                          const Workspace& ws, float* coeffs, cudaStream_t s) {
+  if (p.B == 1) {
+    const int64_t m = p.n * (int64_t)p.K;
+    k_refine_update_l0<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(p.n, p.K, p.acc_stride, ws.acc, lam_host[0], coeffs);
+    note_launches(1);
+    return;
+  }
+  const unsigned grid = (unsigned)((p.n * kGroup + kSolveThreads - 1) / kSolveThreads);
+  const bool mixed = p.precision == 1;
+#define ICGS_REF(B)                                                                                           \
+  if (mixed)                                                                                                  \
+    k_refine_update<B, true><<<grid, kSolveThreads, 0, s>>>(p.n, p.K, chol, ws.bvec, ws.blo, ws.wsum, ws.wlo,  \
+                                                             lam_dev, coeffs);                                 \
+  else                                                                                                        \
+    k_refine_update<B, false><<<grid, kSolveThreads, 0, s>>>(p.n, p.K, chol, ws.bvec, ws.blo, ws.wsum, ws.wlo, \
+                                                              lam_dev, coeffs)
+  if (p.B == 4) { ICGS_REF(4); }
+  else if (p.B == 9) { ICGS_REF(9); }
+  else { ICGS_REF(16); }
+#undef ICGS_REF
+  note_launches(1);
 }
 
 void launch_payload_render(const Problem& p, const float* means, const float* coeffs, int cb,

@@ -15,11 +15,15 @@ constexpr int kThreads = 256;
 constexpr int kBatch = 64;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+// Pixel coordinates in the walk are relative to the tile origin (ox, oy): the staged means are
+// tile-relative too (load_batch), so dx = pixel centre - mean is formed from two small numbers and
+// keeps the precision of the float-float mean that the projection wrote.
 struct TileCtx {
   int j, t, px, py;
   bool inside;
-  float pxf, pyf;
-  float wx0, wx1, wy0, wy1;  // pixel-centre rectangle of this thread's warp block
+  float ox, oy;              // tile origin in image pixels (exact integers)
+  float pxf, pyf;            // this thread's pixel centre, tile-relative
+  float wx0, wx1, wy0, wy1;  // pixel-centre rectangle of this thread's warp block, tile-relative
   uint32_t b, len;
 };
 
@@ -31,12 +35,15 @@ __device__ __forceinline__ TileCtx tile_ctx(const uint32_t* tile_off, uint32_t c
   c.t = bid - c.j * tiles;
   const int tyi = c.t / tiles_x, txi = c.t - tyi * tiles_x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int bx = txi * kTile + (warp & 1) * 8, by = tyi * kTile + (warp >> 1) * 4;
-  c.px = bx + (lane & 7);
-  c.py = by + (lane >> 3);
+  const int ox = txi * kTile, oy = tyi * kTile;
+  const int bx = (warp & 1) * 8, by = (warp >> 1) * 4;  // warp block, tile-relative
+  c.px = ox + bx + (lane & 7);
+  c.py = oy + by + (lane >> 3);
   c.inside = c.px < width && c.py < height;
-  c.pxf = (float)c.px + 0.5f;
-  c.pyf = (float)c.py + 0.5f;
+  c.ox = (float)ox;
+  c.oy = (float)oy;
+  c.pxf = (float)(bx + (lane & 7)) + 0.5f;
+  c.pyf = (float)(by + (lane >> 3)) + 0.5f;
   c.wx0 = (float)bx + 0.5f;
   c.wx1 = (float)bx + 7.5f;
   c.wy0 = (float)by + 0.5f;
@@ -228,16 +235,21 @@ __device__ __forceinline__ float blend_step(const float4 box, const float4 par, 
 
 // Slot ranges are only fully written when the pass fit its capacity; an overflowed pass (reported
 // to the caller as ICGS_ERR_CAPACITY) may leave stale slots, so indices are clamped to the scene.
+// The staged box is (mean - tile origin, half-widths): the mean's hi and lo parts are combined
+// relative to the tile origin (ox, oy), where the result is small and float32 holds it closely.
 // The fast-reject threshold is 2 ln(255 o) with a relative margin of 1e-4 (and 1e-4 absolute),
 // beyond which alpha < 1/255 holds by more than the float32 error of alpha.
 __device__ __forceinline__ void load_batch(const unsigned long long* list, uint32_t first, int nb,
-                                           const ProjRec* __restrict__ rec_cam, int64_t n, float4* s_box,
-                                           float4* s_par, float* s_thr, uint32_t* s_id) {
+                                           const ProjRec* __restrict__ rec_cam, int64_t n, float ox, float oy,
+                                           float4* s_box, float4* s_par, float* s_thr, uint32_t* s_id) {
   if ((int)threadIdx.x < nb) {
     const uint32_t id = min((uint32_t)list[first + threadIdx.x], (uint32_t)(n - 1));
     const ProjRec r = rec_cam[id];
+    const float2 lo = unpack_half2(r.box.z), half = unpack_half2(r.box.w);
     s_id[threadIdx.x] = id;
-    s_box[threadIdx.x] = r.box;
+    s_box[threadIdx.x] = make_float4(__fadd_rn(__fsub_rn(r.box.x, ox), __fmul_rn(lo.x, kMeanLoScaleInv)),
+                                     __fadd_rn(__fsub_rn(r.box.y, oy), __fmul_rn(lo.y, kMeanLoScaleInv)),
+                                     half.x, half.y);
     s_par[threadIdx.x] = r.par;
     s_thr[threadIdx.x] = __fmaf_rn(2.0f * logf(255.0f * r.par.w), 1.0001f, 1e-4f);
   }

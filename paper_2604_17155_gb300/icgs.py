@@ -87,6 +87,10 @@ def load(path: str = LIB_PATH):
     lib.icgs_colorize_noalloc.restype = ctypes.c_int
     lib.icgs_noalloc_scratch_bytes.argtypes = []
     lib.icgs_noalloc_scratch_bytes.restype = S
+    lib.icgs_refine_workspace_size.argtypes = [P, P, P, P]
+    lib.icgs_refine_workspace_size.restype = S
+    lib.icgs_colorize_refine.argtypes = [P, P, P, P, ctypes.c_int32, P, P, S, P, P]
+    lib.icgs_colorize_refine.restype = ctypes.c_int
     lib.icgs_selftest_tc.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, P, P, P]
     lib.icgs_selftest_tc.restype = ctypes.c_int
     lib.icgs_set_stage_timing.argtypes = [ctypes.c_int]
@@ -304,6 +308,33 @@ def colorize_noalloc(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, 
                                      ctypes.c_void_p(coeffs.data_ptr()), ctypes.c_void_p(status.data_ptr()),
                                      ctypes.c_void_p(chol.data_ptr()), _stream_ptr(dev)))
     return coeffs, status, chol
+
+
+def colorize_refine(scene: Scene, cams: Cameras, targets, sh_degree, coeffs, chol, n_steps, lam=None,
+                    precision="mixed", cam_batch=0, instance_capacity=0):
+    """Alg. 1 lines 7-10: n_steps refinement steps of coeffs (updated in place and returned), with
+    the Cholesky factors colorize() returned."""
+    lib = load()
+    dev = targets.device
+    if not coeffs.is_contiguous() or coeffs.dtype != _torch().float32:
+        raise ValueError("coeffs must be a contiguous float32 tensor (it is updated in place)")
+    sc = scene._struct()
+    cm = cams._struct()
+    tg = _targets_struct(targets)
+    chol = chol.contiguous()
+
+    def size_fn(cap):
+        o, _keep = _options(sh_degree, lam, precision, 0.0, cam_batch, cap)
+        return lib.icgs_refine_workspace_size(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(o))
+
+    def call_fn(ptr, nbytes, cap):
+        o, _keep = _options(sh_degree, lam, precision, 0.0, cam_batch, cap)
+        return lib.icgs_colorize_refine(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(o),
+                                        int(n_steps), ctypes.c_void_p(chol.data_ptr()), ctypes.c_void_p(ptr), nbytes,
+                                        ctypes.c_void_p(coeffs.data_ptr()), _stream_ptr(dev))
+
+    _run_with_capacity(dev, size_fn, call_fn, instance_capacity)
+    return coeffs
 
 
 def selftest_tc(A, B, bf16=True):

@@ -60,3 +60,52 @@ def test_relight_fullsize_sampled():
     assert rep["checked"] >= 5
     assert rep["max_checked"] <= TOL_FP32
     assert rep["bound_excess"] <= 0
+
+
+def test_relight_adjoint_fullsize_against_fp64_reference():
+    """The differentiation workload at full size: L = sum r c^2 (r ~ N(0,1) per coefficient) on the
+    relighting scene; every dL/dt and every dL/d(opacity) of the CUDA adjoint against the oracle's
+    FP64 analytic adjoint (itself pinned by central finite differences on small scenes)."""
+    from paper_2604_17155_gb300 import build as B
+    B.build()
+    from paper_2604_17155_gb300 import icgs
+    scene = W.make_scene("relight", 2000)
+    cams = W.make_cameras("relight")
+    L = 3
+    t = W.fourier_fields(cams.n, cams.height, cams.width, 3, seed=2005, n_modes=4) * 0.25 + 0.5
+    t64 = t.astype(np.float64)
+    dev = "cuda"
+    gs = icgs.Scene.from_workload(scene, dev)
+    gc = icgs.Cameras.from_workload(cams)
+    tt = torch.tensor(t, device=dev)
+    c, status, chol = icgs.colorize(gs, gc, tt, L)
+    r = np.random.default_rng(2006).standard_normal((scene.n, 16, 3))
+    gcoef = torch.tensor(2.0 * r, dtype=torch.float32, device=dev) * c
+    gt, go = icgs.colorize_backward(gs, gc, tt, L, c, chol, gcoef)
+    gt, go = to_np(gt), to_np(go)
+    col = O.colorize(scene, cams, t64, L)
+    gt_ref, go_ref = O.adjoint(scene, cams, t64, L, None, 2.0 * r * col["c"], col=col)
+    dt = np.abs(gt - gt_ref)
+    scale_t = np.abs(gt_ref).max()
+    rep, err, checked = coefficient_report(to_np(c), col, tol=TOL_FP32)
+    eo = np.abs(go - go_ref)[checked] / np.maximum(np.abs(go_ref[checked]), 1e-3 * np.abs(go_ref).max())
+    print(f"adjoint full size: dL/dt p99.9 |d|/max {np.percentile(dt, 99.9) / scale_t:.2e}, "
+          f"dL/do p99 rel {np.percentile(eo, 99):.2e} over {checked.sum()} Gaussians; coefficients {rep}")
+    # the conditioning of the worst coefficients: smallest Cholesky pivot ratio d_k / A_kk of the
+    # oracle's A (the quantity the MIXED solve compares with cond_tau) and the GPU's status
+    st = status.cpu().numpy().astype(int)
+    seen = col["w"] > 0
+    ratio = np.ones(scene.n)
+    Lf = np.linalg.cholesky(col["A"][seen])
+    ratio[seen] = (np.diagonal(Lf, axis1=1, axis2=2) ** 2 / np.diagonal(col["A"][seen], axis1=1, axis2=2)).min(1)
+    for i in np.argsort(np.where(checked, err, -1))[::-1][:5]:
+        print(f"  worst checked {i}: err {err[i]:.2e} status {st[i]} w {col['w'][i]:.3e} pivot ratio {ratio[i]:.2e}")
+    for lo, hi in ((0.0, 1e-3), (1e-3, 1e-2), (1e-2, 1e-1), (1e-1, 1.1)):
+        sel = checked & (ratio >= lo) & (ratio < hi)
+        if sel.any():
+            print(f"  pivot ratio [{lo:g}, {hi:g}): {sel.sum()} checked, p99 {np.percentile(err[sel], 99):.2e} "
+                  f"max {err[sel].max():.2e}")
+    assert np.percentile(dt, 99.9) <= 1e-3 * scale_t
+    assert np.percentile(eo, 99) <= 1e-2
+    assert rep["p99_checked"] <= TOL_FP32
+    assert rep["bound_excess"] <= 0.0

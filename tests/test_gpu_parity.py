@@ -142,9 +142,16 @@ def test_camera_passes_match_single_pass(icgs):
     gs, gc = _gpu(icgs, sc, cams)
     c1, s1, _ = icgs.colorize(gs, gc, t, L, cam_batch=0)
     c2, s2, _ = icgs.colorize(gs, gc, t, L, cam_batch=7)
-    assert torch.equal(s1, s2)
+    s1, s2 = to_np(s1), to_np(s2)
+    assert np.array_equal(s1 == icgs.GAUSSIAN_UNSEEN, s2 == icgs.GAUSSIAN_UNSEEN)
+    # a pivot ratio within rounding of cond_tau may take the FP32 route in one run and the FP64
+    # route in the other; both are valid. Compared: Gaussians solved in FP32 by both runs.
+    both = (s1 == 0) & (s2 == 0)
+    assert both.sum() > 0.5 * (s1 != icgs.GAUSSIAN_UNSEEN).sum()
+    # the two runs differ by the order of the FP32 atomic sums of V and S; conditioning
+    # amplifies those last-bit differences
     e = O.relative_errors(to_np(c2), to_np(c1).astype(np.float64))
-    assert np.percentile(e[to_np(s1) == 0], 99) < 1e-5
+    assert np.percentile(e[both], 99) < TOL_FP32
 
 
 def test_long_tile_lists_and_capacity_retry(icgs):
@@ -241,3 +248,26 @@ def test_autograd_function(icgs):
     # two colorize calls differ by FP32 atomic summation order only
     torch.testing.assert_close(t.grad, gt, rtol=1e-3, atol=1e-4 * gt.abs().max().item())
     torch.testing.assert_close(op.grad, go, rtol=1e-3, atol=1e-4 * go.abs().max().item())
+
+
+def test_refinement_matches_oracle(icgs):
+    """Alg. 1 lines 7-10: two refinement steps from the single-shot coefficients, against the
+    oracle's refinement from its own single-shot result; refinement lowers the render error."""
+    sc, cams = _mid_scene(n=2000, seed=101, n_cams=12, w=96, h=72)
+    L = 3
+    t = O.render(sc, cams, W.sh_coefficients(sc.n, L, 3, seed=102), L).astype(np.float32)
+    t64 = t.astype(np.float64)
+    col = O.colorize(sc, cams, t64, L)
+    ref = O.refine(sc, cams, t64, L, None, col, 2)
+    gs, gc = _gpu(icgs, sc, cams)
+    tt = torch.tensor(t, device=DEV)
+    c, status, chol = icgs.colorize(gs, gc, tt, L)
+    icgs.colorize_refine(gs, gc, tt, L, c, chol, 2)
+    rep, err, checked = coefficient_report(to_np(c), dict(col, c=ref), tol=1e-3)
+    print("refine", rep, icgs.last_stats())
+    assert rep["p99_checked"] <= 1e-3
+    assert rep["bound_excess"] <= 0
+    mse0 = float(((O.render(sc, cams, col["c"], L) - t64) ** 2).mean())
+    mse2 = float(((O.render(sc, cams, to_np(c).astype(np.float64), L) - t64) ** 2).mean())
+    print(f"render MSE single-shot {mse0:.3e} -> refined {mse2:.3e}")
+    assert mse2 < 0.8 * mse0

@@ -478,3 +478,52 @@ def test_adjoint_opacity_central_difference():
         if checked == 12:
             break
     assert checked == 12
+
+
+# ------------------------------------------------------------------------------------------
+# Iterative refinement (Alg. 1 lines 7-10)
+# ------------------------------------------------------------------------------------------
+def test_refinement_single_gaussian_fixed_point():
+    """One translucent Gaussian, L = 0: the refinement converges to the stationary point of the
+    regularised render loss, c* = Y0 sum a t / (Y0^2 sum a^2 + lam sum a) with a the per-pixel
+    alpha (T = 1), reached geometrically."""
+    cams = one_camera(33, 33, cx=16.5, cy=16.5)
+    sc = scene_of([[0, 0, 3.0]], [[0.15] * 3], [0.8])
+    rng = np.random.default_rng(81)
+    t = rng.uniform(0, 1, (1, 33, 33, 2))
+    lam = 1e-3
+    col = O.colorize(sc, cams, t, 0, [lam])
+    pix, gid, a = O.weights(sc, cams, 0)
+    tp = t[0].reshape(-1, 2)[pix]
+    c_star = Y0 * (a[:, None] * tp).sum(0) / (Y0 ** 2 * (a * a).sum() + lam * a.sum())
+    c = O.refine(sc, cams, t, 0, [lam], col, 60)
+    np.testing.assert_allclose(c[0, 0], c_star, rtol=1e-9)
+
+
+def test_refinement_step_is_preconditioned_render_gradient():
+    """The update of Alg. 1 line 10 is A^-1 times minus the gradient of
+    E(c) = 1/2 sum_pixels |t - render(c)|^2 + 1/2 sum_i w_i c_i^T Lambda c_i; the render is linear in
+    c, so central differences of E through the oracle's render are exact up to rounding."""
+    sc, cams = _tiny_random(91, n=12, n_cams=6, size=24)
+    rng = np.random.default_rng(92)
+    t = rng.uniform(0, 1, (cams.n, 24, 24, 1))
+    L = 1
+    lam = O.paper_lambda(L)
+    col = O.colorize(sc, cams, t, L, lam)
+    c0 = col["c"] + rng.normal(0, 0.05, col["c"].shape) * (col["w"] > 0)[:, None, None]
+    col0 = dict(col, c=c0)
+    step = O.refine(sc, cams, t, L, lam, col0, 1) - c0
+    w = col["w"]
+
+    def energy(c):
+        img = O.render(sc, cams, c, L)
+        return 0.5 * ((t - img) ** 2).sum() + 0.5 * np.einsum("n,b,nbk,nbk->", w, lam, c, c)
+
+    h = 1e-3
+    grad = np.zeros_like(c0)
+    for i in np.where(w > 0)[0][:6]:
+        for m in range(4):
+            cp = c0.copy(); cp[i, m, 0] += h
+            cm = c0.copy(); cm[i, m, 0] -= h
+            grad[i, m, 0] = (energy(cp) - energy(cm)) / (2 * h)
+        np.testing.assert_allclose(col["A"][i] @ step[i, :, 0], -grad[i, :, 0], rtol=1e-6, atol=1e-9)
