@@ -336,7 +336,7 @@ def run_icgs(args, rank, world, local_rank):
             icgs.colorize_backward(gs, gc, targets, L, c, chol, gcoef, precision=args.precision)
         a1.record(stream)
         barrier()
-        adjoint = {"ms_per_scene": a0.elapsed_time(a1) / n_adj, "outputs": "dL/dt [100,800,800,3] and dL/do [200000]",
+        adjoint = {"ms_per_scene": a0.elapsed_time(a1) / n_adj, "outputs": f"dL/dt [{cams.n},{cams.height},{cams.width},{K}] and dL/do [{scene.n}]",
                    "launches": icgs.last_stats()["launches"]}
 
     if rank != 0:
@@ -394,7 +394,7 @@ def run_icgs(args, rank, world, local_rank):
         "gpu_launches": stats["launches"] * args.steps,
         "blend_contribs_per_s": pairs / (blend_ms * 1e-3),
         "stage_ms": stage_ms,
-        "instances": inst, "contrib_pairs": pairs, "fp64_gaussians": stats["fp64"],
+        "instances": inst, "contrib_pairs": pairs, "fp64_gaussians": stats["fp64"], "refolded_gaussians": stats["refold"],
         "plain_fp32": plain,
         "adjoint": adjoint,
     }

@@ -69,11 +69,11 @@ typedef enum { ICGS_F32 = 0, ICGS_BF16 = 1, ICGS_F16 = 2 } icgs_dtype;
 
 typedef enum {
   ICGS_PRECISION_PLAIN = 0, /* FP32 weights, CUDA-core contraction, plain FP32 fold and Cholesky */
-  ICGS_PRECISION_MIXED = 1  /* compensated FP32 fold, FP32 Cholesky refined in float-float; FP64
-                               for Gaussians whose pivot ratio falls below cond_tau (re-folded in
-                               double from the per-camera sums when all cameras fit one pass);
-                               16-bit targets with >= 16 channels contract on tcgen05 tensor cores
-                               (BF16/FP16 in, FP32 acc) */
+  ICGS_PRECISION_MIXED = 1  /* compensated FP32 fold, FP32 Cholesky refined in float-float;
+                               ill-conditioned Gaussians re-folded exactly from the per-camera sums
+                               (one pass) and, below cond_tau, solved in FP64; 16-bit targets
+                               with >= 16 channels contract on tcgen05 tensor cores (BF16/FP16
+                               in, FP32 acc) */
 } icgs_precision;
 
 /* Per-Gaussian status written to status_out. */
@@ -110,11 +110,14 @@ typedef struct {
   const float* lambda;         /* host [(L+1)^2] Tikhonov weights lambda_m (Eq. 14); NULL selects
                                   the paper's values (Sec. 4): 1e-5 / 1e-4 / 1e-3 / 1e-2 per band */
   int32_t precision;           /* icgs_precision */
-  float cond_tau;              /* MIXED: FP64 for a Gaussian when min_k pivot_k / A_kk < cond_tau.
-                                  With every camera in one pass, G and b are re-folded in double
-                                  from the per-camera sums (view directions and basis in double);
-                                  otherwise the compensated sums are factorised in double.
-                                  <= 0 selects 1e-2 for the first and 1e-3 for the second */
+  float cond_tau;              /* MIXED: FP64 for a Gaussian when min_k pivot_k / A_kk < cond_tau
+                                  (<= 0 selects 1e-3); for a re-folded Gaussian (below) the test
+                                  is against cond_tau * 1e-2 */
+  float refold_tau;            /* MIXED, every camera in one pass: a Gaussian whose pivot ratio is
+                                  below refold_tau is re-folded exactly (float-float products and
+                                  sums) from its per-camera sums, removing the rounding of the
+                                  fast fold that the condition number amplifies. <= 0 selects
+                                  1e-2; > 1 re-folds every Gaussian */
   int32_t cam_batch;           /* cameras accumulated per pass; <= 0 selects min(n_cams, 128) */
   int64_t instance_capacity;   /* (Gaussian, tile) instances per pass the workspace holds; <= 0
                                   selects an estimate (see ICGS_ERR_CAPACITY) */
@@ -214,8 +217,9 @@ ICGS_API int64_t icgs_last_required_instances(void);
 
 /* Statistics of the last successful call on this host thread, for benchmarks:
  * out[0] = (Gaussian, tile) instances summed over passes, out[1] = (pixel, Gaussian) pairs with
- * nonzero blend weight, out[2] = Gaussians solved in FP64, out[3] = kernels launched. */
-ICGS_API void icgs_last_stats(int64_t out[4]);
+ * nonzero blend weight, out[2] = Gaussians solved in FP64, out[3] = kernels launched,
+ * out[4] = Gaussians re-folded exactly from the per-camera sums (MIXED, single pass). */
+ICGS_API void icgs_last_stats(int64_t out[5]);
 
 /* Stage timing for benchmarks (off by default, per host thread). When on, every call records CUDA
  * events on its stream at each stage boundary (no extra synchronisation) and

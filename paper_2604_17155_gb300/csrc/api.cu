@@ -25,7 +25,7 @@ namespace {
 
 thread_local char g_err[1024] = "";
 thread_local int64_t g_required = 0;
-thread_local int64_t g_stats[4] = {0, 0, 0, 0};
+thread_local int64_t g_stats[5] = {0, 0, 0, 0, 0};
 thread_local int64_t g_launches = 0;
 
 // ---- stage timing: one CUDA event per stage boundary, elapsed times read after the final sync ----
@@ -157,7 +157,7 @@ bool finite_all(const float* v, size_t m) {
 }
 
 icgs_status setup(const icgs_scene* sc, const icgs_cameras* cams, int K, int L, int precision,
-                  float cond_tau, int cam_batch, int64_t capacity, Problem& p) {
+                  float cond_tau, float refold_tau, int cam_batch, int64_t capacity, Problem& p) {
   if (!sc || !cams) return fail(ICGS_ERR_INVALID_ARG, "scene and cameras must not be NULL");
   if (sc->n < 0 || sc->n > 0x7FFFFFFF) return fail(ICGS_ERR_INVALID_ARG, "scene.n = %lld out of range", (long long)sc->n);
   if (sc->n > 0 && (!sc->means || !sc->scales || !sc->quats || !sc->opacity))
@@ -188,8 +188,8 @@ icgs_status setup(const icgs_scene* sc, const icgs_cameras* cams, int K, int L, 
   p.L = L;
   p.B = (L + 1) * (L + 1);
   p.precision = precision;
-  p.cond_tau = cond_tau > 0.0f ? cond_tau : 1e-2f;
-  p.cond_tau_sums = cond_tau > 0.0f ? cond_tau : 1e-3f;
+  p.cond_tau = cond_tau > 0.0f ? cond_tau : 1e-3f;
+  p.refold_tau = refold_tau > 0.0f ? refold_tau : 1e-2f;
   p.cam_batch = cam_batch > 0 ? std::min(cam_batch, p.n_cams) : std::min(p.n_cams, 128);
   p.cam_batch = std::min(p.cam_batch, 65535);  // grid y dimension of the per-pair kernels
   if ((int64_t)p.cam_batch * p.tiles > 0x7FFFFFFFll)
@@ -272,6 +272,7 @@ icgs_status finish(const Workspace& ws, cudaStream_t s) {
   g_stats[1] = (int64_t)st.contrib_pairs;
   g_stats[2] = (int64_t)st.fp64_count;
   g_stats[3] = g_launches;
+  g_stats[4] = (int64_t)st.refold_count;
   return ICGS_OK;
 }
 
@@ -314,7 +315,7 @@ size_t icgs_workspace_size(const icgs_scene* scene, const icgs_cameras* cams, co
                            const icgs_options* opt) {
   if (!targets || !opt) return 0;
   Problem p;
-  if (setup(scene, cams, targets->channels, opt->sh_degree, opt->precision, opt->cond_tau, opt->cam_batch,
+  if (setup(scene, cams, targets->channels, opt->sh_degree, opt->precision, opt->cond_tau, opt->refold_tau, opt->cam_batch,
             opt->instance_capacity, p) != ICGS_OK)
     return 0;
   return carve(nullptr, p, kNeedAccumulate | kNeedBackward).total;
@@ -328,7 +329,7 @@ icgs_status icgs_colorize(const icgs_scene* scene, const icgs_cameras* cams, con
   icgs_status st = check_targets(targets);
   if (st != ICGS_OK) return st;
   Problem p;
-  st = setup(scene, cams, targets->channels, opt->sh_degree, opt->precision, opt->cond_tau, opt->cam_batch,
+  st = setup(scene, cams, targets->channels, opt->sh_degree, opt->precision, opt->cond_tau, opt->refold_tau, opt->cam_batch,
              opt->instance_capacity, p);
   if (st != ICGS_OK) return st;
   if (!coeffs_out && p.n > 0) return fail(ICGS_ERR_INVALID_ARG, "coeffs_out must not be NULL");
@@ -374,7 +375,7 @@ icgs_status icgs_colorize_backward(const icgs_scene* scene, const icgs_cameras* 
   icgs_status st = check_targets(targets);
   if (st != ICGS_OK) return st;
   Problem p;
-  st = setup(scene, cams, targets->channels, opt->sh_degree, opt->precision, opt->cond_tau, opt->cam_batch,
+  st = setup(scene, cams, targets->channels, opt->sh_degree, opt->precision, opt->cond_tau, opt->refold_tau, opt->cam_batch,
              opt->instance_capacity, p);
   if (st != ICGS_OK) return st;
   if (p.K > 64) return fail(ICGS_ERR_UNSUPPORTED, "the adjoint supports up to 64 channels, got %d", p.K);
@@ -417,7 +418,7 @@ size_t icgs_refine_workspace_size(const icgs_scene* scene, const icgs_cameras* c
                                   const icgs_options* opt) {
   if (!targets || !opt) return 0;
   Problem p;
-  if (setup(scene, cams, targets->channels, opt->sh_degree, opt->precision, opt->cond_tau, opt->cam_batch,
+  if (setup(scene, cams, targets->channels, opt->sh_degree, opt->precision, opt->cond_tau, opt->refold_tau, opt->cam_batch,
             opt->instance_capacity, p) != ICGS_OK)
     return 0;
   return carve(nullptr, p, kNeedRefine).total;
@@ -431,7 +432,7 @@ icgs_status icgs_colorize_refine(const icgs_scene* scene, const icgs_cameras* ca
   icgs_status st = check_targets(targets);
   if (st != ICGS_OK) return st;
   Problem p;
-  st = setup(scene, cams, targets->channels, opt->sh_degree, opt->precision, opt->cond_tau, opt->cam_batch,
+  st = setup(scene, cams, targets->channels, opt->sh_degree, opt->precision, opt->cond_tau, opt->refold_tau, opt->cam_batch,
              opt->instance_capacity, p);
   if (st != ICGS_OK) return st;
   if (n_steps < 0) return fail(ICGS_ERR_INVALID_ARG, "n_steps = %d must be >= 0", n_steps);
@@ -477,7 +478,7 @@ icgs_status icgs_colorize_refine(const icgs_scene* scene, const icgs_cameras* ca
 size_t icgs_render_workspace_size(const icgs_scene* scene, const icgs_cameras* cams, int32_t sh_degree,
                                   int32_t channels, int64_t instance_capacity) {
   Problem p;
-  if (setup(scene, cams, channels, sh_degree, ICGS_PRECISION_PLAIN, 0.0f, 0, instance_capacity, p) != ICGS_OK) return 0;
+  if (setup(scene, cams, channels, sh_degree, ICGS_PRECISION_PLAIN, 0.0f, 0.0f, 0, instance_capacity, p) != ICGS_OK) return 0;
   return carve(nullptr, p, kNeedRender).total;
 }
 
@@ -486,7 +487,7 @@ icgs_status icgs_render(const icgs_scene* scene, const icgs_cameras* cams, int32
                         float* images_out, void* stream) {
   g_err[0] = '\0';
   Problem p;
-  icgs_status st = setup(scene, cams, channels, sh_degree, ICGS_PRECISION_PLAIN, 0.0f, 0, instance_capacity, p);
+  icgs_status st = setup(scene, cams, channels, sh_degree, ICGS_PRECISION_PLAIN, 0.0f, 0.0f, 0, instance_capacity, p);
   if (st != ICGS_OK) return st;
   if (!images_out || (!coeffs && p.n > 0)) return fail(ICGS_ERR_INVALID_ARG, "coeffs and images_out are required");
   const Workspace need = carve(nullptr, p, kNeedRender);
@@ -536,7 +537,7 @@ int64_t icgs_last_required_instances(void) { return g_required; }
 
 void icgs_last_stats(int64_t out[4]) {
   if (!out) return;
-  for (int k = 0; k < 4; ++k) out[k] = g_stats[k];
+  for (int k = 0; k < 5; ++k) out[k] = g_stats[k];
 }
 
 void icgs_set_stage_timing(int enable) { g_timer.on = enable != 0; }

@@ -23,7 +23,7 @@ struct DevStatus {
   uint64_t instances_total;   // sum over passes
   uint64_t contrib_pairs;     // pixel-Gaussian pairs with nonzero weight (sum over passes)
   uint32_t fp64_count;        // Gaussians solved in FP64
-  uint32_t pad;
+  uint32_t refold_count;      // Gaussians re-folded exactly from the per-camera sums
 };
 constexpr uint32_t kFlagOverflow = 1u;
 constexpr uint32_t kFlagTimeout = 2u;  // a bounded device-side wait gave up
@@ -89,8 +89,8 @@ struct Problem {
   int cam_batch = 0;
   uint32_t capacity = 0;
   int precision = 0;
-  float cond_tau = 1e-2f;       // FP64 re-fold from resident per-camera sums (single pass)
-  float cond_tau_sums = 1e-3f;  // FP64 solve from the compensated sums (several passes)
+  float cond_tau = 1e-3f;       // MIXED: FP64 solve below this pivot ratio
+  float refold_tau = 1e-2f;     // MIXED, single pass: exact re-fold below this pivot ratio
   int mode = 0;                     // 0 colorize, 1 backward, 2 render
 };
 

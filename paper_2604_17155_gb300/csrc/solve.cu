@@ -5,8 +5,10 @@
 //                   G_i and b_i. MIXED keeps a TwoSum compensation term per entry.
 //   k_solve         A_i = G_i + w_i Lambda; Cholesky with the rows in registers of the group (pivots
 //                   and columns exchanged by shuffles); forward and back substitution per channel.
-//                   MIXED: a Gaussian whose smallest pivot ratio d_k / A_kk is below cond_tau, or
-//                   with a non-positive pivot, is refactored in FP64 from G + compensation.
+//                   MIXED: the FP32 solution is refined in float-float against the compensated sums;
+//                   a Gaussian whose smallest pivot ratio d_k / A_kk is below refold_tau is first
+//                   re-folded exactly from the resident per-camera sums (single pass), one below
+//                   cond_tau (or with a non-positive pivot) is solved in FP64.
 //   k_solve_l0      L = 0: c = b / (G + w lambda) with G = V / (4 pi), b = S / sqrt(4 pi).
 //   k_adjoint_prep  u_i = A_i^-1 dL/dc_i from the stored factor, reg_i = sum lambda_m u_mk c_mk.
 //   k_payload_*     per (camera, Gaussian): C = Y . c (render) or (a = Y . u, beta) (adjoint).
@@ -230,6 +232,10 @@ __device__ __forceinline__ void group_chol_solve(const F (&a)[B], int r, F& x) {
 }
 
 constexpr int kRefineSteps = 2;
+constexpr int kRefineStepsRefold = 4;  // re-folded Gaussians: pivot ratio below refold_tau
+// A re-folded Gaussian's sums are exact to float-float, so the refined FP32 solve converges down to
+// much smaller pivot ratios; FP64 takes over below cond_tau * kRefoldFp64Scale.
+constexpr float kRefoldFp64Scale = 1e-2f;
 
 // Residual b - A x of row r with A = G_hi + G_lo + (w_hi + w_lo) Lambda and b = b_hi + b_lo,
 // evaluated in float-float: every product is split exactly with an FMA (TwoProduct) and summed
@@ -253,21 +259,90 @@ __device__ __forceinline__ float refine_residual(const float (&ghi)[B], const fl
   return r < B ? (bh - s) + (bl - comp) : 0.0f;
 }
 
+// Exact float-float fold of one Gaussian's row r from the per-camera sums still resident in acc:
+// every product split with an FMA (TwoProduct) and every addition with TwoSum, so (hi + lo) holds
+// sum_j V_j Y_j Y_j^T (and sum_j Y_j S_j for channels k0..k0+3, and w) to about 2^-44 relative.
+// The basis stays float32: a consistent perturbation of the directions barely moves the solution,
+// whereas the independent rounding of each product in the fast fold is amplified by the condition
+// number. Lane q evaluates camera jb + q's basis into s_Y; the group then walks the 16 cameras.
+// Group-collective (all 16 lanes).
+template <int B>
+__device__ __forceinline__ void exact_fold(const float* __restrict__ acc, int64_t cam_stride, int64_t i, int RS,
+                                           int n_cams, const DevCam* __restrict__ cams, const float* mu, int r,
+                                           bool gram, int k0, int K, float (&gh)[B], float (&gl)[B], float& wh,
+                                           float& wl, float (&bh)[4], float (&bl)[4], float (*s_Y)[B + 1]) {
+  const unsigned gm = group_mask();
+  const int gbase = threadIdx.x & ~(kGroup - 1);
+  const bool row = r < B;
+  for (int jb = 0; jb < n_cams; jb += kGroup) {
+    const int jq = jb + r;
+    float vq = 0.0f, sq[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (jq < n_cams) {
+      const float* a = acc + jq * cam_stride + i * RS;
+      vq = a[0];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (k0 + q < K) sq[q] = a[1 + k0 + q];
+    }
+    if (vq > 0.0f) {
+      const float3 d = view_dir(mu, cams[jq]);
+      sh_basis<B>(d.x, d.y, d.z, s_Y[threadIdx.x]);
+    }
+    __syncwarp(gm);
+    const int nj = min(kGroup, n_cams - jb);
+    for (int q = 0; q < nj; ++q) {
+      const float v = __shfl_sync(gm, vq, q, kGroup);
+      float sv[4];
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq) sv[qq] = __shfl_sync(gm, sq[qq], q, kGroup);
+      if (!(v > 0.0f)) continue;  // uniform in the group
+      const float* yq = s_Y[gbase + q];
+      const float Yr = row ? yq[r] : 0.0f;
+      if (gram) {
+        const float vh = v * Yr, vl = fmaf(v, Yr, -vh);
+#pragma unroll
+        for (int c = 0; c < B; ++c) {
+          const float y = yq[c];
+          const float p = vh * y;
+          const float e = fmaf(vh, y, -p);
+          two_sum_acc(gh[c], gl[c], p);
+          gl[c] += fmaf(vl, y, e);
+        }
+        two_sum_acc(wh, wl, v);
+      }
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq)
+        if (k0 + qq < K) {
+          const float p = Yr * sv[qq];
+          const float e = fmaf(Yr, sv[qq], -p);
+          two_sum_acc(bh[qq], bl[qq], p);
+          bl[qq] += e;
+        }
+    }
+    __syncwarp(gm);
+  }
+}
+
+// MIXED: every Gaussian is factorised in FP32 from the fold's G_hi. When all cameras were
+// accumulated in one pass (n_acc_cams > 0) and the smallest pivot ratio is below refold_tau, the
+// row is re-folded exactly from the resident per-camera sums (exact_fold) and refactorised; the
+// FP32 solution is then refined in float-float against (G_hi + G_lo, b_hi + b_lo) for
+// kRefineStepsRefold steps. Below cond_tau (cond_tau * kRefoldFp64Scale after a re-fold), or with
+// a non-positive pivot, the Gaussian is solved in FP64.
 template <int B, bool MIXED>
 __global__ void __launch_bounds__(kSolveThreads) k_solve(
     int64_t n, int K, const float* __restrict__ G, const float* __restrict__ Glo,
     const float* __restrict__ bvec, const float* __restrict__ blo, const float* __restrict__ wsum,
-    const float* __restrict__ wlo, const float* __restrict__ lam, float cond_tau,
+    const float* __restrict__ wlo, const float* __restrict__ lam, float cond_tau, float refold_tau,
     float* __restrict__ coeffs, uint8_t* __restrict__ status_out, float* __restrict__ chol,
     DevStatus* status, const float* __restrict__ acc, int RS, int n_acc_cams,
     const DevCam* __restrict__ cams, const float* __restrict__ means) {
-  // MIXED: per lane, the double basis of the camera it evaluates in the FP64 re-fold
-  __shared__ double s_Y[MIXED ? kSolveThreads : 1][B + 1];
+  __shared__ float s_Y[MIXED ? kSolveThreads : 1][B + 1];  // per lane: basis of its camera (re-fold)
   const int64_t i = (blockIdx.x * (int64_t)kSolveThreads + threadIdx.x) / kGroup;
   const int r = threadIdx.x % kGroup;
   if (i >= n) return;
   const bool row = r < B;
-  const float w = wsum[i];
+  float w = wsum[i];
   const float lam_r = row ? lam[r] : 0.0f;
   if (!(w > 0.0f)) {
     if (row) {
@@ -284,34 +359,75 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(
     a[c] = row ? G[(i * B + r) * B + c] : 0.0f;
     if (c == r) a[c] += w * lam_r;
   }
-  const float minratio = group_cholesky<B, float>(a, r);
-  const bool fp64 = MIXED && !(minratio >= cond_tau);
-  if (!fp64) {
-    // MIXED: the rows of G_hi, G_lo are kept for iterative refinement of the FP32 solution
-    float ghi[B], glo[B];
-    if constexpr (MIXED) {
+  float minratio = group_cholesky<B, float>(a, r);
+  // MIXED: rows of G_hi, G_lo (and w_lo) for the residuals of the refinement
+  float ghi[B], glo[B];
+  float wl = 0.0f;
+  bool refold = false;
+  float rb_h[4] = {0.0f, 0.0f, 0.0f, 0.0f}, rb_l[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // re-fold: b, channels 0-3
+  const float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
+  const int64_t cam_stride = n * (int64_t)RS;
+  if constexpr (MIXED) {
+    refold = n_acc_cams > 0 && !(minratio >= refold_tau);
+    if (refold) {
+#pragma unroll
+      for (int c = 0; c < B; ++c) { ghi[c] = 0.0f; glo[c] = 0.0f; }
+      w = 0.0f;
+      exact_fold<B>(acc, cam_stride, i, RS, n_acc_cams, cams, mu, r, true, 0, K, ghi, glo, w, wl, rb_h, rb_l, s_Y);
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        a[c] = row ? ghi[c] : 0.0f;
+        if (c == r) a[c] += w * lam_r;
+      }
+      minratio = group_cholesky<B, float>(a, r);
+      if (r == 0) atomicAdd(&status->refold_count, 1u);
+    } else {
+      wl = wlo[i];
 #pragma unroll
       for (int c = 0; c < B; ++c) {
         ghi[c] = row ? G[(i * B + r) * B + c] : 0.0f;
         glo[c] = row ? Glo[(i * B + r) * B + c] : 0.0f;
       }
     }
+  }
+  const bool fp64 = MIXED && !(minratio >= (refold ? cond_tau * kRefoldFp64Scale : cond_tau));
+  if (!fp64) {
     const float wl_r = w * lam_r;
-    const float wl_lo = MIXED ? wlo[i] * lam_r : 0.0f;
-    for (int k = 0; k < K; ++k) {
-      const float bh = row ? bvec[(i * B + r) * K + k] : 0.0f;
-      float x = bh;
-      group_chol_solve<B, float>(a, r, x);
-      if constexpr (MIXED) {
-        const float bl = row ? blo[(i * B + r) * K + k] : 0.0f;
-#pragma unroll 1
-        for (int it = 0; it < kRefineSteps; ++it) {
-          float res = refine_residual<B>(ghi, glo, wl_r, wl_lo, bh, bl, x, r);
-          group_chol_solve<B, float>(a, r, res);
-          x += res;
-        }
+    const float wl_lo = MIXED ? wl * lam_r : 0.0f;
+    const int steps = refold ? kRefineStepsRefold : kRefineSteps;
+    for (int k0 = 0; k0 < K; k0 += 4) {
+      float bh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, bl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      if (refold && k0 == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { bh[q] = rb_h[q]; bl[q] = rb_l[q]; }
+      } else if (refold) {
+        float gdummy[B], gldummy[B], wdummy = 0.0f, wldummy = 0.0f;
+        exact_fold<B>(acc, cam_stride, i, RS, n_acc_cams, cams, mu, r, false, k0, K, gdummy, gldummy, wdummy,
+                      wldummy, bh, bl, s_Y);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (k0 + q < K && row) {
+            bh[q] = bvec[(i * B + r) * K + k0 + q];
+            if (MIXED) bl[q] = blo[(i * B + r) * K + k0 + q];
+          }
       }
-      if (row) coeffs[(i * B + r) * K + k] = x;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (k0 + q >= K) break;
+        const float bq = row ? bh[q] : 0.0f, blq = row ? bl[q] : 0.0f;
+        float x = bq;
+        group_chol_solve<B, float>(a, r, x);
+        if constexpr (MIXED) {
+#pragma unroll 1
+          for (int it = 0; it < steps; ++it) {
+            float res = refine_residual<B>(ghi, glo, wl_r, wl_lo, bq, blq, x, r);
+            group_chol_solve<B, float>(a, r, res);
+            x += res;
+          }
+        }
+        if (row) coeffs[(i * B + r) * K + k0 + q] = x;
+      }
     }
     if (chol && row) {
 #pragma unroll
@@ -321,91 +437,39 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(
     if (r == 0 && status_out) status_out[i] = kGaussOk;
     return;
   }
-  // FP64 for this ill-conditioned Gaussian. With every camera's sums still resident, G and b are
-  // re-folded in double (view directions and basis in double, from the same per-camera V and S);
-  // otherwise the compensated (hi + lo) sums are used.
+  // FP64 from (G_hi + G_lo, b_hi + b_lo): the exact re-fold when it ran, else the fold's
+  // compensated sums
   double ad[B];
-  if (n_acc_cams > 0) {
-    // One walk over the cameras per chunk of 4 channels (the first also folds row r of G and w).
-    // Lane q of the group evaluates camera jb + q's direction and basis in double and leaves them
-    // in shared memory; every lane then takes the 16 cameras in turn from there.
-    double wd = 0.0;
+  const double wd = (double)w + (double)wl;
 #pragma unroll
-    for (int c = 0; c < B; ++c) ad[c] = 0.0;
-    const unsigned gm = group_mask();
-    const int gbase = threadIdx.x & ~(kGroup - 1);
-    const double mu0 = means[3 * i], mu1 = means[3 * i + 1], mu2 = means[3 * i + 2];
-    const int64_t cam_stride = n * (int64_t)RS;
-    for (int k0 = 0; k0 < K || k0 == 0; k0 += 4) {
-      double bk[4] = {0.0, 0.0, 0.0, 0.0};
-      for (int jb = 0; jb < n_acc_cams; jb += kGroup) {
-        const int jq = jb + r;
-        float vq = 0.0f, sq[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (jq < n_acc_cams) {
-          const float* a = acc + jq * cam_stride + i * RS;
-          vq = a[0];
+  for (int c = 0; c < B; ++c) {
+    ad[c] = row ? (double)ghi[c] + (double)glo[c] : 0.0;
+    if (c == r) ad[c] += wd * (double)lam_r;
+  }
+  group_cholesky<B, double>(ad, r);
+  for (int k0 = 0; k0 < K; k0 += 4) {
+    float bh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, bl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (refold && k0 == 0) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if (k0 + q < K) sq[q] = a[1 + k0 + q];
+      for (int q = 0; q < 4; ++q) { bh[q] = rb_h[q]; bl[q] = rb_l[q]; }
+    } else if (refold) {
+      float gdummy[B], gldummy[B], wdummy = 0.0f, wldummy = 0.0f;
+      exact_fold<B>(acc, cam_stride, i, RS, n_acc_cams, cams, mu, r, false, k0, K, gdummy, gldummy, wdummy,
+                    wldummy, bh, bl, s_Y);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (k0 + q < K && row) {
+          bh[q] = bvec[(i * B + r) * K + k0 + q];
+          bl[q] = blo[(i * B + r) * K + k0 + q];
         }
-        if (vq > 0.0f) {
-          const DevCam& cj = cams[jq];
-          const double dx = mu0 - cj.centre_d[0], dy = mu1 - cj.centre_d[1], dz = mu2 - cj.centre_d[2];
-          const double inv = 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
-          sh_basis<B, double>(dx * inv, dy * inv, dz * inv, s_Y[threadIdx.x]);
-        }
-        __syncwarp(gm);
-        const int nj = min(kGroup, n_acc_cams - jb);
-        for (int q = 0; q < nj; ++q) {
-          const float v = __shfl_sync(gm, vq, q, kGroup);
-          float sv[4];
-#pragma unroll
-          for (int qq = 0; qq < 4; ++qq) sv[qq] = __shfl_sync(gm, sq[qq], q, kGroup);
-          if (!(v > 0.0f)) continue;  // uniform in the group
-          const double* yq = s_Y[gbase + q];
-          const double Yr = row ? yq[r] : 0.0;
-          if (k0 == 0) {
-            const double vy = (double)v * Yr;
-#pragma unroll
-            for (int c = 0; c < B; ++c) ad[c] += vy * yq[c];
-            wd += (double)v;
-          }
-#pragma unroll
-          for (int qq = 0; qq < 4; ++qq)
-            if (k0 + qq < K) bk[qq] += Yr * (double)sv[qq];
-        }
-        __syncwarp(gm);
-      }
-      if (k0 == 0) {
-#pragma unroll
-        for (int c = 0; c < B; ++c)
-          if (c == r) ad[c] += wd * (double)lam_r;
-        if (!row) {
-#pragma unroll
-          for (int c = 0; c < B; ++c) ad[c] = 0.0;
-        }
-        group_cholesky<B, double>(ad, r);
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (k0 + q >= K) break;
-        double x = row ? bk[q] : 0.0;
-        group_chol_solve<B, double>(ad, r, x);
-        if (row) coeffs[(i * B + r) * K + k0 + q] = (float)x;
-      }
     }
-  } else {
-    const double wd = (double)w + (double)(wlo ? wlo[i] : 0.0f);
 #pragma unroll
-    for (int c = 0; c < B; ++c) {
-      ad[c] = row ? (double)G[(i * B + r) * B + c] + (double)Glo[(i * B + r) * B + c] : 0.0;
-      if (c == r) ad[c] += wd * (double)lam_r;
-    }
-    group_cholesky<B, double>(ad, r);
-    for (int k = 0; k < K; ++k) {
-      double x = row ? (double)bvec[(i * B + r) * K + k] + (double)blo[(i * B + r) * K + k] : 0.0;
+    for (int q = 0; q < 4; ++q) {
+      if (k0 + q >= K) break;
+      double x = row ? (double)bh[q] + (double)bl[q] : 0.0;
       group_chol_solve<B, double>(ad, r, x);
-      if (row) coeffs[(i * B + r) * K + k] = (float)x;
+      if (row) coeffs[(i * B + r) * K + k0 + q] = (float)x;
     }
   }
   if (chol && row) {
@@ -604,8 +668,8 @@ void solve_b(const Problem& p, const float* lam_dev, const Workspace& ws, float*
              float* chol, const float* means, int n_acc_cams, cudaStream_t s) {
   const unsigned grid = (unsigned)((p.n * kGroup + kSolveThreads - 1) / kSolveThreads);
   k_solve<B, MIXED><<<grid, kSolveThreads, 0, s>>>(p.n, p.K, ws.G, ws.Glo, ws.bvec, ws.blo, ws.wsum, ws.wlo,
-                                                       lam_dev, n_acc_cams > 0 ? p.cond_tau : p.cond_tau_sums,
-                                                       coeffs, st, chol, ws.status, ws.acc,
+                                                       lam_dev, p.cond_tau, p.refold_tau, coeffs, st, chol,
+                                                       ws.status, ws.acc,
                                                        p.acc_stride, n_acc_cams, ws.cams, means);
   note_launches(1);
 }

@@ -45,7 +45,8 @@ class _Targets(ctypes.Structure):
 
 class _Options(ctypes.Structure):
     _fields_ = [("sh_degree", ctypes.c_int32), ("lambda_", ctypes.c_void_p), ("precision", ctypes.c_int32),
-                ("cond_tau", ctypes.c_float), ("cam_batch", ctypes.c_int32), ("instance_capacity", ctypes.c_int64)]
+                ("cond_tau", ctypes.c_float), ("refold_tau", ctypes.c_float), ("cam_batch", ctypes.c_int32),
+                ("instance_capacity", ctypes.c_int64)]
 
 
 _lib = None
@@ -109,9 +110,10 @@ def _check(status):
 
 
 def last_stats():
-    out = (ctypes.c_int64 * 4)()
+    out = (ctypes.c_int64 * 5)()
     load().icgs_last_stats(out)
-    return {"instances": int(out[0]), "contrib_pairs": int(out[1]), "fp64": int(out[2]), "launches": int(out[3])}
+    return {"instances": int(out[0]), "contrib_pairs": int(out[1]), "fp64": int(out[2]), "launches": int(out[3]),
+            "refold": int(out[4])}
 
 
 def set_stage_timing(enable: bool):
@@ -198,11 +200,11 @@ def _targets_struct(targets):
     return _Targets(dt, int(targets.shape[-1]), targets.data_ptr())
 
 
-def _options(sh_degree, lam, precision, cond_tau, cam_batch, capacity):
+def _options(sh_degree, lam, precision, cond_tau, cam_batch, capacity, refold_tau=0.0):
     lam_arr = None if lam is None else np.ascontiguousarray(lam, np.float32)
     o = _Options(int(sh_degree), None if lam_arr is None else lam_arr.ctypes.data,
-                 {"plain": PLAIN, "mixed": MIXED}.get(precision, precision), float(cond_tau), int(cam_batch),
-                 int(capacity))
+                 {"plain": PLAIN, "mixed": MIXED}.get(precision, precision), float(cond_tau), float(refold_tau),
+                 int(cam_batch), int(capacity))
     return o, lam_arr
 
 
@@ -256,7 +258,7 @@ def _run_with_capacity(device, size_fn, call_fn, capacity):
 # public calls
 # ------------------------------------------------------------------------------------------
 def colorize(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, precision="mixed",
-             cond_tau=0.0, cam_batch=0, instance_capacity=0, opacity=None):
+             cond_tau=0.0, cam_batch=0, instance_capacity=0, opacity=None, refold_tau=0.0):
     """Alg. 1 lines 1-6: per-Gaussian SH coefficients [n,(L+1)^2,K] (float32), status [n] (uint8)
     and the row-packed Cholesky factors [n, B(B+1)/2] of A_i = G_i + w_i Lambda."""
     torch = _torch()
@@ -272,11 +274,11 @@ def colorize(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, precisio
     tg = _targets_struct(targets)
 
     def size_fn(cap):
-        o, _keep = _options(sh_degree, lam, precision, cond_tau, cam_batch, cap)
+        o, _keep = _options(sh_degree, lam, precision, cond_tau, cam_batch, cap, refold_tau)
         return lib.icgs_workspace_size(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(o))
 
     def call_fn(ptr, nbytes, cap):
-        o, _keep = _options(sh_degree, lam, precision, cond_tau, cam_batch, cap)
+        o, _keep = _options(sh_degree, lam, precision, cond_tau, cam_batch, cap, refold_tau)
         return lib.icgs_colorize(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(o),
                                  ctypes.c_void_p(ptr), nbytes, ctypes.c_void_p(coeffs.data_ptr()),
                                  ctypes.c_void_p(status.data_ptr()), ctypes.c_void_p(chol.data_ptr()),
@@ -287,7 +289,7 @@ def colorize(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, precisio
 
 
 def colorize_noalloc(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, precision="mixed",
-                     cond_tau=0.0, cam_batch=0, instance_capacity=0, opacity=None):
+                     cond_tau=0.0, cam_batch=0, instance_capacity=0, opacity=None, refold_tau=0.0):
     """Like colorize(), but the library works in its own built-in device scratch instead of a
     workspace, for callers that cannot allocate device memory (see icgs_colorize_noalloc in
     include/icgs.h). The outputs are still the caller's tensors; problems larger than the scratch
@@ -303,7 +305,7 @@ def colorize_noalloc(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, 
     sc = scene._struct(opacity)
     cm = cams._struct()
     tg = _targets_struct(targets)
-    o, _keep = _options(sh_degree, lam, precision, cond_tau, cam_batch, instance_capacity)
+    o, _keep = _options(sh_degree, lam, precision, cond_tau, cam_batch, instance_capacity, refold_tau)
     _check(lib.icgs_colorize_noalloc(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(o),
                                      ctypes.c_void_p(coeffs.data_ptr()), ctypes.c_void_p(status.data_ptr()),
                                      ctypes.c_void_p(chol.data_ptr()), _stream_ptr(dev)))

@@ -135,6 +135,28 @@ def test_colorize_channels_and_dtypes(icgs, K, dtype):
         assert rep["bound_excess"] <= 0
 
 
+def test_exact_refold_of_every_gaussian(icgs):
+    """refold_tau > 1 re-folds every seen Gaussian exactly (float-float products and sums) from its
+    resident per-camera sums: every one is counted, and parity with the FP64 oracle is at least as
+    tight as with the default threshold, whose fast fold rounds each product and partial sum."""
+    sc, cams = _mid_scene()
+    L = 3
+    t = O.render(sc, cams, W.sh_coefficients(sc.n, L, 3, seed=13), L).astype(np.float32)
+    col = O.colorize(sc, cams, t.astype(np.float64), L)
+    gs, gc = _gpu(icgs, sc, cams)
+    tt = torch.tensor(t, device=DEV)
+    c0, s0, _ = icgs.colorize(gs, gc, tt, L)
+    rep0, err0, checked = coefficient_report(to_np(c0), col, tol=TOL_FP32)
+    c1, s1, _ = icgs.colorize(gs, gc, tt, L, refold_tau=2.0)
+    stats = icgs.last_stats()
+    rep1, err1, _ = coefficient_report(to_np(c1), col, tol=TOL_FP32)
+    print("refold all", rep1, stats, "default", rep0)
+    assert stats["refold"] == int((to_np(s1) != icgs.GAUSSIAN_UNSEEN).sum())
+    assert rep1["max_checked"] <= TOL_FP32
+    assert rep1["bound_excess"] <= 0
+    assert rep1["p99_checked"] <= rep0["p99_checked"]
+
+
 def test_camera_passes_match_single_pass(icgs):
     sc, cams = _mid_scene(n=3000, n_cams=20)
     L = 3
