@@ -78,8 +78,8 @@ __global__ void __launch_bounds__(kThreads, KC <= 3 ? 8 : (KC <= 8 ? 5 : 4)) k_b
   constexpr int NV = KC + 1;                      // V and S_0..S_{KC-1}
   constexpr int NP = NextPow2<NV>::value;
   constexpr int SHIFT = 5 - Log2<NP>::value;      // the sum of value v lands in lane v << SHIFT
-  __shared__ float4 s_box[kBatch], s_par[kBatch];
-  __shared__ float s_thr[kBatch];
+  __shared__ float4 s_geo[kBatch], s_aux[kBatch];
+  __shared__ float2 s_half[kBatch];
   __shared__ uint32_t s_id[kBatch];
   __shared__ float s_acc[kBatch][NV];
   __shared__ unsigned long long s_keys[kWalkSortCap];
@@ -112,19 +112,18 @@ __global__ void __launch_bounds__(kThreads, KC <= 3 ? 8 : (KC <= 8 ? 5 : 4)) k_b
   for (uint32_t start = 0; start < c.len; start += kBatch) {
     const int nb = (int)min((uint32_t)kBatch, c.len - start);
     __syncthreads();
-    load_batch(list, start, nb, rec_cam, n, c.ox, c.oy, s_box, s_par, s_thr, s_id);
+    load_batch(list, start, nb, rec_cam, n, c.ox, c.oy, s_geo, s_aux, s_half, s_id);
     __syncthreads();
     if (!__all_sync(kFull, done)) {
 #pragma unroll
       for (int half = 0; half < kBatch / 32; ++half) {
-       uint32_t bits = warp_hit_bits(s_box, half * 32, nb, c);
+       uint32_t bits = warp_hit_bits(s_geo, s_half, half * 32, nb, c);
        while (bits) {  // only the Gaussians whose box touches this warp's block, in depth order
         const int g = half * 32 + __ffs(bits) - 1;
         bits &= bits - 1;
-        const float4 box = s_box[g];
         float w = 0.0f, al, ex;
         bool cap;
-        if (!done) w = blend_step(box, s_par[g], s_thr[g], c.pxf, c.pyf, T, done, al, ex, cap);
+        if (!done) w = blend_step(s_geo[g], s_aux[g], c.pxf, c.pyf, T, done, al, ex, cap);
         if (__any_sync(kFull, w > 0.0f)) {
           npairs += w > 0.0f;
           float v[NP];
@@ -174,8 +173,8 @@ __global__ void __launch_bounds__(kThreads) k_blend_render(
     const uint32_t* __restrict__ tile_off, const uint64_t* __restrict__ entries, uint32_t capacity,
     const ProjRec* __restrict__ rec, int64_t n, int width, int height, int tiles_x, int tiles,
     const float* __restrict__ payload, int K, int k0, int cam0, float* __restrict__ images) {
-  __shared__ float4 s_box[kBatch], s_par[kBatch];
-  __shared__ float s_thr[kBatch];
+  __shared__ float4 s_geo[kBatch], s_aux[kBatch];
+  __shared__ float2 s_half[kBatch];
   __shared__ uint32_t s_id[kBatch];
   __shared__ float s_col[kBatch][KC];
   __shared__ unsigned long long s_keys[kWalkSortCap];
@@ -191,7 +190,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_render(
   for (uint32_t start = 0; start < c.len; start += kBatch) {
     const int nb = (int)min((uint32_t)kBatch, c.len - start);
     __syncthreads();
-    load_batch(list, start, nb, rec_cam, n, c.ox, c.oy, s_box, s_par, s_thr, s_id);
+    load_batch(list, start, nb, rec_cam, n, c.ox, c.oy, s_geo, s_aux, s_half, s_id);
     __syncthreads();
     for (int idx = threadIdx.x; idx < nb * KC; idx += kThreads) {
       const int g = idx / KC, k = idx - g * KC;
@@ -201,13 +200,13 @@ __global__ void __launch_bounds__(kThreads) k_blend_render(
     if (!__all_sync(kFull, done)) {
 #pragma unroll
       for (int half = 0; half < kBatch / 32; ++half) {
-        uint32_t bits = warp_hit_bits(s_box, half * 32, nb, c);
+        uint32_t bits = warp_hit_bits(s_geo, s_half, half * 32, nb, c);
         while (bits && !done) {
           const int g = half * 32 + __ffs(bits) - 1;
           bits &= bits - 1;
           float al, ex;
           bool cap;
-          const float w = blend_step(s_box[g], s_par[g], s_thr[g], c.pxf, c.pyf, T, done, al, ex, cap);
+          const float w = blend_step(s_geo[g], s_aux[g], c.pxf, c.pyf, T, done, al, ex, cap);
           if (w > 0.0f) {
 #pragma unroll
             for (int k = 0; k < KC; ++k) img[k] = fmaf(w, s_col[g][k], img[k]);
@@ -249,8 +248,8 @@ __global__ void __launch_bounds__(kThreads, KC <= 4 ? 6 : (KC <= 16 ? 4 : (KC <=
     const ProjRec* __restrict__ rec, int64_t n, int width, int height, int tiles_x, int tiles,
     const void* __restrict__ targets, int dtype, const float* __restrict__ payload, int K, int cam0,
     float* __restrict__ grad_t, float* __restrict__ grad_o) {
-  __shared__ float4 s_box[kBatch], s_par[kBatch];
-  __shared__ float s_thr[kBatch];
+  __shared__ float4 s_geo[kBatch], s_aux[kBatch];
+  __shared__ float2 s_half[kBatch];
   __shared__ uint32_t s_id[kBatch];
   __shared__ float s_pay[kBatch][KC + 1];
   __shared__ float s_go[kBatch];
@@ -277,20 +276,20 @@ __global__ void __launch_bounds__(kThreads, KC <= 4 ? 6 : (KC <= 16 ? 4 : (KC <=
     for (uint32_t start = 0; start < c.len; start += kBatch) {
       const int nb = (int)min((uint32_t)kBatch, c.len - start);
       __syncthreads();
-      load_batch(list, start, nb, rec_cam, n, c.ox, c.oy, s_box, s_par, s_thr, s_id);
+      load_batch(list, start, nb, rec_cam, n, c.ox, c.oy, s_geo, s_aux, s_half, s_id);
       __syncthreads();
       load_payload<KC>(pay_cam, nb, K, s_id, s_pay);
       __syncthreads();
       if (!__all_sync(kFull, done)) {
 #pragma unroll
         for (int half = 0; half < kBatch / 32; ++half) {
-          uint32_t bits = warp_hit_bits(s_box, half * 32, nb, c);
+          uint32_t bits = warp_hit_bits(s_geo, s_half, half * 32, nb, c);
           while (bits && !done) {
             const int g = half * 32 + __ffs(bits) - 1;
             bits &= bits - 1;
             float al, ex;
             bool cap;
-            const float w = blend_step(s_box[g], s_par[g], s_thr[g], c.pxf, c.pyf, T, done, al, ex, cap);
+            const float w = blend_step(s_geo[g], s_aux[g], c.pxf, c.pyf, T, done, al, ex, cap);
             if (w > 0.0f) {
               float gg = s_pay[g][KC];
 #pragma unroll
@@ -319,24 +318,24 @@ __global__ void __launch_bounds__(kThreads, KC <= 4 ? 6 : (KC <= 16 ? 4 : (KC <=
   for (uint32_t start = 0; start < c.len; start += kBatch) {
     const int nb = (int)min((uint32_t)kBatch, c.len - start);
     __syncthreads();
-    load_batch(list, start, nb, rec_cam, n, c.ox, c.oy, s_box, s_par, s_thr, s_id);
+    load_batch(list, start, nb, rec_cam, n, c.ox, c.oy, s_geo, s_aux, s_half, s_id);
     __syncthreads();
     load_payload<KC>(pay_cam, nb, K, s_id, s_pay);
     __syncthreads();
     if (!__all_sync(kFull, done)) {
 #pragma unroll
       for (int half = 0; half < kBatch / 32; ++half) {
-       uint32_t bits = warp_hit_bits(s_box, half * 32, nb, c);
+       uint32_t bits = warp_hit_bits(s_geo, s_half, half * 32, nb, c);
        while (bits) {
         const int g = half * 32 + __ffs(bits) - 1;
         bits &= bits - 1;
-        const float4 box = s_box[g];
+
         float d_o = 0.0f;
         if (!done) {
           const float Tm = T;
           float al = 0.0f, ex = 0.0f;
           bool cap = false;
-          const float w = blend_step(box, s_par[g], s_thr[g], c.pxf, c.pyf, T, done, al, ex, cap);
+          const float w = blend_step(s_geo[g], s_aux[g], c.pxf, c.pyf, T, done, al, ex, cap);
           if (w > 0.0f) {
             float gg = s_pay[g][KC];
 #pragma unroll

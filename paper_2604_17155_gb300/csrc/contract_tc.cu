@@ -218,10 +218,10 @@ __global__ void __launch_bounds__(256, 2) k_blend_accumulate_tc(
   uint8_t* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
   uint8_t* A_s = base;                                 // kG x 256, 64 KB
   uint8_t* B_s = base + kG * kKPix * 2;                // NB x 256
-  float4* s_box = reinterpret_cast<float4*>(B_s + NB * kKPix * 2);
-  float4* s_par = s_box + kG;
-  float* s_thr = reinterpret_cast<float*>(s_par + kG);
-  uint32_t* s_id = reinterpret_cast<uint32_t*>(s_thr + kG);
+  float4* s_geo = reinterpret_cast<float4*>(B_s + NB * kKPix * 2);
+  float4* s_aux = s_geo + kG;
+  float2* s_half = reinterpret_cast<float2*>(s_aux + kG);
+  uint32_t* s_id = reinterpret_cast<uint32_t*>(s_half + kG);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(s_id + kG);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
   uint32_t* s_tmax = tmem_slot + 1;  // [8]
@@ -297,21 +297,21 @@ __global__ void __launch_bounds__(256, 2) k_blend_accumulate_tc(
   bool timed_out = false;
   for (uint32_t start = 0; start < c.len; start += kG) {
     const int nb = (int)min((uint32_t)kG, c.len - start);
-    load_batch(reinterpret_cast<const unsigned long long*>(entries), c.b + start, nb, rec_cam, n, c.ox, c.oy, s_box, s_par,
-               s_thr, s_id);
+    load_batch(reinterpret_cast<const unsigned long long*>(entries), c.b + start, nb, rec_cam, n, c.ox, c.oy, s_geo, s_aux,
+               s_half, s_id);
     // the previous batch's MMAs have completed: clear W (16-byte stores), then write its nonzeros
     for (int i = threadIdx.x; i < kG * kKPix * 2 / 16; i += 256) reinterpret_cast<uint4*>(A_s)[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
     if (!__all_sync(0xFFFFFFFFu, done)) {
 #pragma unroll
       for (int q = 0; q < kG / 32; ++q) {
-        uint32_t bits = warp_hit_bits(s_box, q * 32, nb, c);
+        uint32_t bits = warp_hit_bits(s_geo, s_half, q * 32, nb, c);
         while (bits && !done) {  // only Gaussians whose box touches this warp's block, in depth order
           const int g = q * 32 + __ffs(bits) - 1;
           bits &= bits - 1;
           float al, ex;
           bool cap;
-          const float w = blend_step(s_box[g], s_par[g], s_thr[g], c.pxf, c.pyf, T, done, al, ex, cap);
+          const float w = blend_step(s_geo[g], s_aux[g], c.pxf, c.pyf, T, done, al, ex, cap);
           if (w > 0.0f) {
             ++npairs;
             *reinterpret_cast<uint16_t*>(A_s + kmajor_sw128(g, p, kG)) = half_bits(w * (float)(1 << kWScaleExp));
@@ -382,7 +382,7 @@ constexpr size_t selftest_smem() {
 }
 template <int KT>
 constexpr size_t tc_smem() {
-  return 1024 + (size_t)kG * kKPix * 2 + (size_t)(KT + 16) * kKPix * 2 + (size_t)kG * (16 + 16 + 4 + 4) + 64;
+  return 1024 + (size_t)kG * kKPix * 2 + (size_t)(KT + 16) * kKPix * 2 + (size_t)kG * (16 + 16 + 8 + 4) + 64;
 }
 
 template <int KT, bool BF16_TARGETS>

@@ -190,34 +190,48 @@ __device__ __forceinline__ const unsigned long long* stage_tile_list(const uint6
   return s_keys;
 }
 
+// A Gaussian of the current batch as the walk evaluates it, staged in shared memory:
+//   geo  = (mean_x - ox, mean_y - oy, A, Bc)
+//   aux  = (C, opacity, E_thr, 0)
+//   half = (half-width, half-height) of the support box (read by the warp ballot only)
+// with the conic (a, b, c) scaled by -log2(e)/2: A = -a log2(e)/2, Bc = -b log2(e), C = -c log2(e)/2,
+// so that E = A dx^2 + Bc dx dy + C dy^2 = -q log2(e)/2 and exp(-q/2) = 2^E. E_thr is the fast-reject
+// threshold 2 ln(255 o) in the same units (E < E_thr => alpha < 1/255 for certain).
+constexpr float kHalfLog2e = 0.72134752044448170f;  // log2(e) / 2
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Does the Gaussian's padded support box touch the warp's pixel block? (warp-uniform)
-__device__ __forceinline__ bool warp_hits(const float4 box, const TileCtx& c) {
-  return box.x + box.z >= c.wx0 && box.x - box.z <= c.wx1 && box.y + box.w >= c.wy0 && box.y - box.w <= c.wy1;
+__device__ __forceinline__ bool warp_hits(const float4 geo, const float2 half, const TileCtx& c) {
+  return geo.x + half.x >= c.wx0 && geo.x - half.x <= c.wx1 && geo.y + half.y >= c.wy0 && geo.y - half.y <= c.wy1;
 }
 
 // Box-hit masks of this warp for the batch's Gaussians [base, base + 32): bit i is set when
 // Gaussian base + i (< nb) touches the warp's pixel block. One Gaussian per lane, one ballot;
 // iterating the set bits in ascending order keeps the depth order.
-__device__ __forceinline__ uint32_t warp_hit_bits(const float4* s_box, int base, int nb, const TileCtx& c) {
+__device__ __forceinline__ uint32_t warp_hit_bits(const float4* s_geo, const float2* s_half, int base, int nb,
+                                                  const TileCtx& c) {
   const int g = base + (int)(threadIdx.x & 31);
-  const bool h = g < nb && warp_hits(s_box[g], c);
+  const bool h = g < nb && warp_hits(s_geo[g], s_half[g], c);
   return __ballot_sync(kFull, h);
 }
 
-// One step of the walk for a Gaussian (box, par, q threshold) at pixel centre (pxf, pyf).
-// Returns the weight w = alpha T (0 if skipped); sets `done` when the pixel stops here.
+// One step of the walk for a staged Gaussian (geo, aux) at the tile-relative pixel centre
+// (pxf, pyf). Returns the weight w = alpha T (0 if skipped); sets `done` when the pixel stops here.
 // e_out receives exp(-q/2) and capped whether alpha hit 0.99 (both only meaningful if w > 0).
-__device__ __forceinline__ float blend_step(const float4 box, const float4 par, float qthr, float pxf, float pyf,
-                                            float& T, bool& done, float& alpha_out, float& e_out,
-                                            bool& capped) {
-  const float dx = __fsub_rn(pxf, box.x), dy = __fsub_rn(pyf, box.y);
-  // q = a dx^2 + 2 b dx dy + c dy^2
-  const float q = __fmaf_rn(__fmul_rn(par.x, dx), dx,
-                            __fmaf_rn(__fmul_rn(__fmul_rn(2.0f, par.y), dx), dy, __fmul_rn(__fmul_rn(par.z, dy), dy)));
+__device__ __forceinline__ float blend_step(const float4 geo, const float4 aux, float pxf, float pyf, float& T,
+                                            bool& done, float& alpha_out, float& e_out, bool& capped) {
+  const float dx = __fsub_rn(pxf, geo.x), dy = __fsub_rn(pyf, geo.y);
+  // E = (A dx + Bc dy) dx + (C dy) dy
+  const float E = __fmaf_rn(__fmaf_rn(geo.z, dx, __fmul_rn(geo.w, dy)), dx, __fmul_rn(__fmul_rn(aux.x, dy), dy));
   // beyond the support threshold (with margin) alpha < 1/255 for certain: skip the exponential
-  if (!(q <= qthr)) return 0.0f;
-  const float e = __expf(__fmul_rn(-0.5f, q));
-  const float oe = __fmul_rn(par.w, e);
+  if (!(E >= aux.z)) return 0.0f;
+  const float e = ex2_approx(E);
+  const float oe = __fmul_rn(aux.y, e);
   const float alpha = fminf(kAlphaMax, oe);
   if (!(alpha >= kAlphaMin)) return 0.0f;
   const float tT = __fmul_rn(T, __fsub_rn(1.0f, alpha));
@@ -235,23 +249,24 @@ __device__ __forceinline__ float blend_step(const float4 box, const float4 par, 
 
 // Slot ranges are only fully written when the pass fit its capacity; an overflowed pass (reported
 // to the caller as ICGS_ERR_CAPACITY) may leave stale slots, so indices are clamped to the scene.
-// The staged box is (mean - tile origin, half-widths): the mean's hi and lo parts are combined
-// relative to the tile origin (ox, oy), where the result is small and float32 holds it closely.
-// The fast-reject threshold is 2 ln(255 o) with a relative margin of 1e-4 (and 1e-4 absolute),
-// beyond which alpha < 1/255 holds by more than the float32 error of alpha.
+// The staged mean is relative to the tile origin (ox, oy): the record's hi and lo parts are
+// combined there, where the result is small and float32 holds it closely. The fast-reject
+// threshold is 2 ln(255 o) with a relative margin of 1e-4 (and 1e-4 absolute), beyond which
+// alpha < 1/255 holds by more than the float32 error of alpha.
 __device__ __forceinline__ void load_batch(const unsigned long long* list, uint32_t first, int nb,
                                            const ProjRec* __restrict__ rec_cam, int64_t n, float ox, float oy,
-                                           float4* s_box, float4* s_par, float* s_thr, uint32_t* s_id) {
+                                           float4* s_geo, float4* s_aux, float2* s_half, uint32_t* s_id) {
   if ((int)threadIdx.x < nb) {
     const uint32_t id = min((uint32_t)list[first + threadIdx.x], (uint32_t)(n - 1));
     const ProjRec r = rec_cam[id];
     const float2 lo = unpack_half2(r.box.z), half = unpack_half2(r.box.w);
+    const float qthr = __fmaf_rn(2.0f * logf(255.0f * r.par.w), 1.0001f, 1e-4f);
     s_id[threadIdx.x] = id;
-    s_box[threadIdx.x] = make_float4(__fadd_rn(__fsub_rn(r.box.x, ox), __fmul_rn(lo.x, kMeanLoScaleInv)),
+    s_geo[threadIdx.x] = make_float4(__fadd_rn(__fsub_rn(r.box.x, ox), __fmul_rn(lo.x, kMeanLoScaleInv)),
                                      __fadd_rn(__fsub_rn(r.box.y, oy), __fmul_rn(lo.y, kMeanLoScaleInv)),
-                                     half.x, half.y);
-    s_par[threadIdx.x] = r.par;
-    s_thr[threadIdx.x] = __fmaf_rn(2.0f * logf(255.0f * r.par.w), 1.0001f, 1e-4f);
+                                     -kHalfLog2e * r.par.x, -2.0f * kHalfLog2e * r.par.y);
+    s_aux[threadIdx.x] = make_float4(-kHalfLog2e * r.par.z, r.par.w, -kHalfLog2e * qthr, 0.0f);
+    s_half[threadIdx.x] = half;
   }
 }
 
