@@ -181,7 +181,17 @@ __device__ __forceinline__ const unsigned long long* stage_tile_list(const uint6
                                                                      unsigned long long* s_keys) {
   const unsigned long long* g = reinterpret_cast<const unsigned long long*>(entries) + b;
   if (len > (uint32_t)kWalkSortCap) return g;  // uniform
-  // the plain network only: the register-blocked one costs the walk occupancy even when unused
+  if (len <= (uint32_t)kThreads) {
+    // one key per thread: strides below 32 by shuffles, 32..128 through shared memory (at most 6
+    // barrier-separated stages for 256 keys). Threads t >= P sort padding among themselves.
+    int P = 32;
+    while (P < (int)len) P <<= 1;
+    unsigned long long v[1];
+    v[0] = threadIdx.x < len ? g[threadIdx.x] : ~0ull;
+    block_bitonic_sort<1>(v, s_keys, P);
+    return s_keys;
+  }
+  // longer lists: the plain network (a register-blocked one would cost the walk registers)
   int P = 2;
   while (P < (int)len) P <<= 1;
   for (int k = threadIdx.x; k < P; k += kThreads) s_keys[k] = k < (int)len ? g[k] : ~0ull;
