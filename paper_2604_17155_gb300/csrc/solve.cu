@@ -50,6 +50,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_fold(
     const float* __restrict__ acc, int K, int RS, int k0, bool first, bool want_gram, float* __restrict__ G,
     float* __restrict__ Glo, float* __restrict__ bvec, float* __restrict__ blo,
     float* __restrict__ wsum, float* __restrict__ wlo) {
+  // per lane: the basis of the camera it evaluates (rows padded so 16-byte stores do not collide)
+  constexpr int kYStride = (B + 3) / 4 * 4 + 4;
+  __shared__ __align__(16) float s_Y[kSolveThreads][kYStride];
   const int64_t i = (blockIdx.x * (int64_t)kSolveThreads + threadIdx.x) / kGroup;
   const int r = threadIdx.x % kGroup;
   if (i >= n) return;  // whole groups exit together
@@ -91,7 +94,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_fold(
 #pragma unroll
   for (int k = 0; k < KC; ++k) pb[k] = 0.0f;
   const unsigned gm = group_mask();
-  // 16 cameras at a time: lane q loads camera jb + q's row (V, S), the group shares it by shuffles
+  const int gbase = threadIdx.x & ~(kGroup - 1);
+  // 16 cameras at a time: lane q loads camera jb + q's row (V, S) and evaluates its view direction
+  // and basis into s_Y; the group shares V, S by shuffles and reads the basis rows back
   for (int jb = 0; jb < cb; jb += kGroup) {
    float lv = 0.0f, ls[KC];
 #pragma unroll
@@ -103,6 +108,17 @@ __global__ void __launch_bounds__(kSolveThreads) k_fold(
      for (int k = 0; k < KC; ++k)
        if (k0 + k < K) ls[k] = a[1 + k0 + k];
    }
+   if (lv > 0.0f) {
+     const float3 d = view_dir(mu, cams[jb + r]);
+     float Yl[kYStride];
+     sh_basis<B>(d.x, d.y, d.z, Yl);
+#pragma unroll
+     for (int c4 = 0; c4 < (B + 3) / 4; ++c4)
+       reinterpret_cast<float4*>(s_Y[threadIdx.x])[c4] =
+           make_float4(Yl[4 * c4], 4 * c4 + 1 < B ? Yl[4 * c4 + 1] : 0.0f, 4 * c4 + 2 < B ? Yl[4 * c4 + 2] : 0.0f,
+                       4 * c4 + 3 < B ? Yl[4 * c4 + 3] : 0.0f);
+   }
+   __syncwarp(gm);
    const int nj = min(kGroup, cb - jb);
    for (int q = 0; q < nj; ++q) {
     const int j = jb + q;
@@ -111,13 +127,13 @@ __global__ void __launch_bounds__(kSolveThreads) k_fold(
 #pragma unroll
     for (int k = 0; k < KC; ++k) sv[k] = __shfl_sync(gm, ls[k], q, kGroup);
     if (v > 0.0f) {
-      const float3 d = view_dir(mu, cams[j]);
-      float Y[B];
-      sh_basis<B>(d.x, d.y, d.z, Y);
-      float Yr = Y[0];
+      float Y[(B + 3) / 4 * 4];
 #pragma unroll
-      for (int c = 1; c < B; ++c)
-        if (c == r) Yr = Y[c];
+      for (int c4 = 0; c4 < (B + 3) / 4; ++c4) {
+        const float4 y4 = reinterpret_cast<const float4*>(s_Y[gbase + q])[c4];
+        Y[4 * c4] = y4.x; Y[4 * c4 + 1] = y4.y; Y[4 * c4 + 2] = y4.z; Y[4 * c4 + 3] = y4.w;
+      }
+      const float Yr = row ? s_Y[gbase + q][r] : 0.0f;
       if (do_gram) {
         const float vy = v * Yr;
 #pragma unroll
@@ -152,6 +168,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_fold(
       }
     }
    }
+   __syncwarp(gm);
   }
   if (!row) return;
   if (do_gram) {
@@ -228,6 +245,50 @@ __device__ __forceinline__ void group_chol_solve(const F (&a)[B], int r, F& x) {
     const F part = (r > k && r < B) ? a[k] * x : F(0);
     const F s = group_sum(part);
     if (r == k) x = (x - s) * inv_rr;
+  }
+}
+
+// Solves L L^T x_q = rhs_q for NR right-hand sides at once: lane r holds rhs_q,r in x[q] and row r
+// of L in a; s_L holds the same rows (s_L[k (B + 1) + c] = L_kc). Both substitutions go by
+// columns, one broadcast shuffle per step and right-hand side: the forward one reads L_rk from a,
+// the backward one the column entry L_kr from s_L.
+template <int B, int NR>
+__device__ __forceinline__ void group_chol_solve_rows(const float (&a)[B], int r, float (&x)[NR],
+                                                      const float* s_L) {
+  float lrr = 1.0f;
+#pragma unroll
+  for (int c = 0; c < B; ++c)
+    if (c == r) lrr = a[c];
+  const float inv_rr = 1.0f / lrr;
+  const unsigned m = group_mask();
+#pragma unroll
+  for (int k = 0; k < B; ++k) {  // L y = rhs
+    if (r == k) {
+#pragma unroll
+      for (int q = 0; q < NR; ++q) x[q] *= inv_rr;
+    }
+    float yk[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) yk[q] = __shfl_sync(m, x[q], k, kGroup);
+    if (r > k && r < B) {
+#pragma unroll
+      for (int q = 0; q < NR; ++q) x[q] -= a[k] * yk[q];
+    }
+  }
+#pragma unroll
+  for (int k = B - 1; k >= 0; --k) {  // L^T x = y: x_k final, then x_j -= L_kj x_k for j < k
+    if (r == k) {
+#pragma unroll
+      for (int q = 0; q < NR; ++q) x[q] *= inv_rr;
+    }
+    float xk[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) xk[q] = __shfl_sync(m, x[q], k, kGroup);
+    if (r < k) {
+      const float l = s_L[k * (B + 1) + r];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) x[q] -= l * xk[q];
+    }
   }
 }
 
@@ -338,6 +399,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(
     DevStatus* status, const float* __restrict__ acc, int RS, int n_acc_cams,
     const DevCam* __restrict__ cams, const float* __restrict__ means) {
   __shared__ float s_Y[MIXED ? kSolveThreads : 1][B + 1];  // per lane: basis of its camera (re-fold)
+  __shared__ float s_L[(kSolveThreads / kGroup) * B * (B + 1)];  // per group: the rows of L
   const int64_t i = (blockIdx.x * (int64_t)kSolveThreads + threadIdx.x) / kGroup;
   const int r = threadIdx.x % kGroup;
   if (i >= n) return;
@@ -395,6 +457,13 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(
     const float wl_r = w * lam_r;
     const float wl_lo = MIXED ? wl * lam_r : 0.0f;
     const int steps = refold ? kRefineStepsRefold : kRefineSteps;
+    float* s_Lg = s_L + (threadIdx.x / kGroup) * (B * (B + 1));
+    if (row) {
+#pragma unroll
+      for (int c = 0; c < B; ++c)
+        if (c <= r) s_Lg[r * (B + 1) + c] = a[c];
+    }
+    __syncwarp(group_mask());
     for (int k0 = 0; k0 < K; k0 += 4) {
       float bh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, bl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
       if (refold && k0 == 0) {
@@ -412,22 +481,28 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(
             if (MIXED) bl[q] = blo[(i * B + r) * K + k0 + q];
           }
       }
+      // four channels at once (padding channels carry zeros)
+      float x[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        if (k0 + q >= K) break;
-        const float bq = row ? bh[q] : 0.0f, blq = row ? bl[q] : 0.0f;
-        float x = bq;
-        group_chol_solve<B, float>(a, r, x);
-        if constexpr (MIXED) {
-#pragma unroll 1
-          for (int it = 0; it < steps; ++it) {
-            float res = refine_residual<B>(ghi, glo, wl_r, wl_lo, bq, blq, x, r);
-            group_chol_solve<B, float>(a, r, res);
-            x += res;
-          }
-        }
-        if (row) coeffs[(i * B + r) * K + k0 + q] = x;
+        if (!(row && k0 + q < K)) { bh[q] = 0.0f; bl[q] = 0.0f; }
+        x[q] = bh[q];
       }
+      group_chol_solve_rows<B, 4>(a, r, x, s_Lg);
+      if constexpr (MIXED) {
+#pragma unroll 1
+        for (int it = 0; it < steps; ++it) {
+          float res[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) res[q] = refine_residual<B>(ghi, glo, wl_r, wl_lo, bh[q], bl[q], x[q], r);
+          group_chol_solve_rows<B, 4>(a, r, res, s_Lg);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) x[q] += res[q];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (row && k0 + q < K) coeffs[(i * B + r) * K + k0 + q] = x[q];
     }
     if (chol && row) {
 #pragma unroll
