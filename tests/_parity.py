@@ -43,3 +43,14 @@ def coefficient_report(c_gpu, col, w_min=W_MIN, stake_rel=STAKE_REL, tol=None):
 
 def to_np(t):
     return t.detach().float().cpu().numpy()
+
+
+def psnr_delta(scene, cams, targets, c_gpu, c_ref, sh_degree):
+    """Re-rendered image PSNR against the targets (FP64 oracle render of both coefficient sets, peak
+    = the targets' largest magnitude) of the GPU's coefficients minus that of the oracle's: the
+    image-space effect of the coefficient differences. Returns (delta dB, oracle's PSNR dB)."""
+    targets = np.asarray(targets, np.float64)
+    peak = float(np.abs(targets).max())
+    p_gpu = O.psnr(O.render(scene, cams, np.asarray(c_gpu, np.float64), sh_degree), targets, peak)
+    p_ref = O.psnr(O.render(scene, cams, c_ref, sh_degree), targets, peak)
+    return p_gpu - p_ref, p_ref

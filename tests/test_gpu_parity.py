@@ -9,7 +9,7 @@ import pytest
 from oracle import oracle as O
 from paper_2604_17155_gb300 import workloads as W
 
-from _parity import TOL_BF16, TOL_FP32, coefficient_report, to_np
+from _parity import TOL_BF16, TOL_FP32, coefficient_report, psnr_delta, to_np
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -96,6 +96,9 @@ def test_colorize_sh3_rgb(icgs, prec):
         assert rep["max_checked"] <= TOL_FP32
     else:
         assert rep["p99_checked"] <= 1e-3
+    dpsnr, p_ref = psnr_delta(sc, cams, t, to_np(c), col["c"], L)
+    print(f"sh3 {prec}: re-rendered PSNR {p_ref:.3f} dB (oracle), delta {dpsnr:+.2e} dB")
+    assert abs(dpsnr) <= 1e-3
     # the Cholesky factor reproduces A = G + w Lambda of the oracle
     B = 16
     ch = to_np(chol)
@@ -130,9 +133,11 @@ def test_colorize_channels_and_dtypes(icgs, K, dtype):
         c, status, chol = icgs.colorize(gs, gc, tt, 0, lam=lam, precision=prec)
         tol = TOL_FP32 if (prec == "plain" or K < 16 or dtype == "f32") else TOL_BF16
         rep, err, checked = coefficient_report(to_np(c), col, tol=tol)
-        print(K, dtype, prec, rep)
+        dpsnr, p_ref = psnr_delta(sc, cams, t_exact, to_np(c), col["c"], 0)
+        print(K, dtype, prec, rep, f"re-rendered PSNR {p_ref:.3f} dB (oracle), delta {dpsnr:+.2e} dB")
         assert rep["max_checked"] <= tol
         assert rep["bound_excess"] <= 0
+        assert abs(dpsnr) <= (1e-3 if tol == TOL_FP32 else 1e-2)
 
 
 def test_exact_refold_of_every_gaussian(icgs):
