@@ -8,7 +8,7 @@ paper's per-band lambda. A step is one full icgs_colorize call: projection, binn
 blend-accumulate, fold and the regularised solve for every Gaussian.
 
   value        ms per colorized scene (device-resident targets, CUDA events), whole job
-  e2e          the same through host buffers: pinned H2D of the targets and D2H of the
+  e2e          the same through icgs_colorize_host: pinned H2D of the targets and D2H of the
                coefficients inside the timed region
   roofline     the blend-accumulate kernel (dominant), timed live with CUDA events on its stream
   cpu_baseline the FP64 oracle on the host cores, on a sample of cameras, scaled to a scene
@@ -315,19 +315,20 @@ def run_icgs(args, rank, world, local_rank):
     elapsed_max = float(t.item())
     stage_ms = {k: v / args.steps for k, v in stage_sum.items() if v > 0}
 
-    # ---- end to end through host buffers ----
+    # ---- end to end through the C ABI with host buffers (icgs_colorize_host): every step copies
+    # the targets from pinned host memory (staged per camera chunk, overlapped with the walk) and
+    # returns the coefficients and status to pinned host memory ----
     host_t = torch.empty(targets.shape, dtype=targets.dtype, pin_memory=True)
     host_t.copy_(targets)
     host_c = torch.empty((scene.n, B, K), dtype=torch.float32, pin_memory=True)
-    dev_t = torch.empty_like(targets)
+    host_s = torch.empty((scene.n,), dtype=torch.uint8, pin_memory=True)
+    icgs.colorize_host(gs, gc, host_t, L, precision=args.precision, coeffs_out=host_c, status_out=host_s)
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        dev_t.copy_(host_t, non_blocking=True)
-        c, st, _ = icgs.colorize(gs, gc, dev_t, L, precision=args.precision)
-        host_c.copy_(c, non_blocking=True)
+        icgs.colorize_host(gs, gc, host_t, L, precision=args.precision, coeffs_out=host_c, status_out=host_s)
     e1.record(stream)
     barrier()
     e2e_ms = e0.elapsed_time(e1)
@@ -424,7 +425,7 @@ def run_icgs(args, rank, world, local_rank):
                    "l2": f"inputs larger than L2 ({target_bytes / 1e6:.0f} MB of targets per step)"},
         "roofline": roof,
         "e2e": {"value": e2e_max / (args.steps * world), "unit": UNIT, "h2d_bytes_per_step": target_bytes,
-                "d2h_bytes_per_step": scene.n * B * K * 4},
+                "d2h_bytes_per_step": scene.n * B * K * 4 + scene.n, "call": "icgs_colorize_host"},
         "cpu_baseline": cpu,
         "clocks": clocks,
         "gpu_launches": stats["launches"] * args.steps,

@@ -199,6 +199,29 @@ ICGS_API icgs_status icgs_colorize_noalloc(const icgs_scene* scene, const icgs_c
                                            float* coeffs_out, uint8_t* status_out, float* chol_out,
                                            void* stream);
 
+/* icgs_colorize with the targets in HOST memory and the coefficients and status written to HOST
+ * memory: the call a user makes when the images and results live on the host. There is no paper
+ * counterpart; it computes exactly what icgs_colorize computes (Alg. 1 lines 1-6).
+ *   targets->data  HOST pointer to [n_cams, H, W, channels] of targets->dtype, row-major. Page-locked
+ *                  (pinned) memory lets the copies run asynchronously; pageable memory works but the
+ *                  driver stages it.
+ *   coeffs_host    HOST [n, (L+1)^2, channels] float32, written before the call returns.
+ *   status_host    HOST [n] ICGS_GAUSSIAN_*, or NULL.
+ *   chol_out       DEVICE, as for icgs_colorize (for icgs_colorize_backward), or NULL.
+ *   workspace      DEVICE, 256-byte aligned, icgs_colorize_host_workspace_size() bytes: the
+ *                  colorize workspace followed by the staged targets, coefficients and status.
+ * The targets are copied to the device in chunks of cameras on a copy stream owned by the library
+ * (one per host thread and device), and each chunk's walk waits only for its own copy, so the
+ * copies overlap the projection, binning and the walk of earlier chunks. The call synchronises
+ * `stream` before returning. The staging region is overwritten only after the work already queued
+ * on `stream` has finished. Errors as for icgs_colorize. */
+ICGS_API size_t icgs_colorize_host_workspace_size(const icgs_scene* scene, const icgs_cameras* cams,
+                                                  const icgs_targets* targets, const icgs_options* opt);
+ICGS_API icgs_status icgs_colorize_host(const icgs_scene* scene, const icgs_cameras* cams,
+                                        const icgs_targets* targets, const icgs_options* opt, void* workspace,
+                                        size_t workspace_bytes, float* coeffs_host, uint8_t* status_host,
+                                        float* chol_out, void* stream);
+
 /* Size in bytes of the built-in scratch icgs_colorize_noalloc works in. */
 ICGS_API size_t icgs_noalloc_scratch_bytes(void);
 

@@ -366,6 +366,153 @@ icgs_status icgs_colorize(const icgs_scene* scene, const icgs_cameras* cams, con
   return finish(ws, s);
 }
 
+namespace {
+
+// Copy stream and event pool of icgs_colorize_host, one per host thread and device.
+struct HostPipe {
+  int device = -1;
+  cudaStream_t copy = nullptr;
+  cudaEvent_t start = nullptr;
+  std::vector<cudaEvent_t> ready;
+};
+thread_local HostPipe g_pipe;
+
+constexpr int kHostChunks = 8;  // camera chunks per pass: copy of chunk c+1 overlaps the walk of c
+
+icgs_status host_pipe(int n_events, HostPipe*& out) {
+  int dev = 0;
+  ICGS_TRY_CUDA(cudaGetDevice(&dev));
+  HostPipe& hp = g_pipe;
+  if (hp.device != dev) {  // first use on this thread, or another device: a fresh stream and pool
+    hp = HostPipe();
+    ICGS_TRY_CUDA(cudaStreamCreateWithFlags(&hp.copy, cudaStreamNonBlocking));
+    ICGS_TRY_CUDA(cudaEventCreateWithFlags(&hp.start, cudaEventDisableTiming));
+    hp.device = dev;
+  }
+  while ((int)hp.ready.size() < n_events) {
+    cudaEvent_t e;
+    ICGS_TRY_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    hp.ready.push_back(e);
+  }
+  out = &hp;
+  return ICGS_OK;
+}
+
+size_t target_elem_bytes(int dtype) { return dtype == ICGS_F32 ? 4 : 2; }
+
+// Sizes of the regions icgs_colorize_host adds after the colorize workspace: the staged targets,
+// the coefficients and the status bytes.
+void host_regions(const Problem& p, int dtype, size_t& t_bytes, size_t& c_bytes, size_t& s_bytes) {
+  t_bytes = align256((size_t)p.n_cams * p.height * p.width * p.K * target_elem_bytes(dtype));
+  c_bytes = align256((size_t)p.n * p.B * p.K * sizeof(float));
+  s_bytes = align256((size_t)p.n);
+}
+
+}  // namespace
+
+size_t icgs_colorize_host_workspace_size(const icgs_scene* scene, const icgs_cameras* cams,
+                                         const icgs_targets* targets, const icgs_options* opt) {
+  if (!targets || !opt) return 0;
+  Problem p;
+  if (setup(scene, cams, targets->channels, opt->sh_degree, opt->precision, opt->cond_tau, opt->refold_tau,
+            opt->cam_batch, opt->instance_capacity, p) != ICGS_OK)
+    return 0;
+  size_t t_bytes, c_bytes, s_bytes;
+  host_regions(p, (int)targets->dtype, t_bytes, c_bytes, s_bytes);
+  return carve(nullptr, p, kNeedAccumulate).total + t_bytes + c_bytes + s_bytes;
+}
+
+icgs_status icgs_colorize_host(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
+                               const icgs_options* opt, void* workspace, size_t workspace_bytes, float* coeffs_host,
+                               uint8_t* status_host, float* chol_out, void* stream) {
+  g_err[0] = '\0';
+  if (!opt) return fail(ICGS_ERR_INVALID_ARG, "options must not be NULL");
+  icgs_status st = check_targets(targets);
+  if (st != ICGS_OK) return st;
+  Problem p;
+  st = setup(scene, cams, targets->channels, opt->sh_degree, opt->precision, opt->cond_tau, opt->refold_tau,
+             opt->cam_batch, opt->instance_capacity, p);
+  if (st != ICGS_OK) return st;
+  if (!coeffs_host && p.n > 0) return fail(ICGS_ERR_INVALID_ARG, "coeffs_host must not be NULL");
+  float lam[kMaxSH];
+  if ((st = lambda_of(opt, p.L, lam)) != ICGS_OK) return st;
+  const Workspace need = carve(nullptr, p, kNeedAccumulate);
+  size_t t_bytes, c_bytes, s_bytes;
+  const int dtype = (int)targets->dtype;
+  host_regions(p, dtype, t_bytes, c_bytes, s_bytes);
+  const size_t total = need.total + t_bytes + c_bytes + s_bytes;
+  if (!workspace || workspace_bytes < total)
+    return fail(ICGS_ERR_WORKSPACE_TOO_SMALL, "workspace of %zu bytes, need %zu", workspace_bytes, total);
+  if (reinterpret_cast<uintptr_t>(workspace) % 256)
+    return fail(ICGS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(workspace);
+  const Workspace ws = carve(base, p, kNeedAccumulate);
+  char* t_dev = base + need.total;
+  float* c_dev = reinterpret_cast<float*>(t_dev + t_bytes);
+  uint8_t* st_dev = reinterpret_cast<uint8_t*>(t_dev + t_bytes + c_bytes);
+  if (p.n == 0) return ICGS_OK;
+  const size_t cam_bytes = (size_t)p.height * p.width * p.K * target_elem_bytes(dtype);
+  const char* t_host = static_cast<const char*>(targets->data);
+
+  // camera chunks of every pass, in order; chunk c of the whole call waits on ready[c]
+  std::vector<int> chunk_cam0, chunk_n;
+  for (int cam0 = 0; cam0 < p.n_cams; cam0 += p.cam_batch) {
+    const int cb = std::min(p.cam_batch, p.n_cams - cam0);
+    const int per = std::max(1, (cb + kHostChunks - 1) / kHostChunks);
+    for (int j0 = 0; j0 < cb; j0 += per) {
+      chunk_cam0.push_back(cam0 + j0);
+      chunk_n.push_back(std::min(per, cb - j0));
+    }
+  }
+  HostPipe* hp = nullptr;
+  if ((st = host_pipe((int)chunk_cam0.size(), hp)) != ICGS_OK) return st;
+  // the staging buffer is overwritten only after the work already queued on `stream` (which may
+  // read it) has finished
+  ICGS_TRY_CUDA(cudaEventRecord(hp->start, s));
+  ICGS_TRY_CUDA(cudaStreamWaitEvent(hp->copy, hp->start, 0));
+  for (size_t c = 0; c < chunk_cam0.size(); ++c) {
+    const size_t off = (size_t)chunk_cam0[c] * cam_bytes;
+    ICGS_TRY_CUDA(cudaMemcpyAsync(t_dev + off, t_host + off, (size_t)chunk_n[c] * cam_bytes, cudaMemcpyHostToDevice,
+                                  hp->copy));
+    ICGS_TRY_CUDA(cudaEventRecord(hp->ready[c], hp->copy));
+  }
+
+  if ((st = upload_common(p, cams, lam, ws, s)) != ICGS_OK) return st;
+  if (p.L == 0)
+    ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)p.n * p.acc_stride, s));
+  size_t chunk = 0;
+  for (int cam0 = 0; cam0 < p.n_cams; cam0 += p.cam_batch) {
+    const int cb = std::min(p.cam_batch, p.n_cams - cam0);
+    Workspace wp = ws;
+    wp.cams = ws.cams + cam0;
+    if (p.L > 0)
+      ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)cb * (size_t)p.n * p.acc_stride, s));
+    // projection, binning and sorting need no targets: they run while the first chunks arrive
+    if ((st = bin_pass(p, scene, cb, tc_accumulate_applies(p, dtype), wp, s)) != ICGS_OK) return st;
+    for (; chunk < chunk_cam0.size() && chunk_cam0[chunk] < cam0 + cb; ++chunk) {
+      const int j0 = chunk_cam0[chunk] - cam0, jc = chunk_n[chunk];
+      ICGS_TRY_CUDA(cudaStreamWaitEvent(s, hp->ready[chunk], 0));
+      Workspace wc = wp;  // the chunk's cameras are a contiguous slice of the pass
+      wc.tile_off = wp.tile_off + (size_t)j0 * p.tiles;
+      wc.rec = wp.rec + (size_t)j0 * p.n;
+      if (p.L > 0) wc.acc = wp.acc + (size_t)j0 * p.n * p.acc_stride;
+      launch_blend_accumulate(p, jc, cam0 + j0, t_dev, dtype, nullptr, wc, s);
+    }
+    g_timer.mark(kBlend, s);
+    if (p.L > 0) {
+      launch_fold(p, scene->means, cb, cam0 == 0, true, wp, s);
+      g_timer.mark(kFold, s);
+    }
+  }
+  launch_solve(p, ws.lam, lam, ws, c_dev, st_dev, chol_out, scene->means, p.cam_batch >= p.n_cams ? p.n_cams : 0,
+               s);
+  g_timer.mark(kSolve, s);
+  ICGS_TRY_CUDA(cudaMemcpyAsync(coeffs_host, c_dev, (size_t)p.n * p.B * p.K * sizeof(float), cudaMemcpyDeviceToHost, s));
+  if (status_host) ICGS_TRY_CUDA(cudaMemcpyAsync(status_host, st_dev, (size_t)p.n, cudaMemcpyDeviceToHost, s));
+  return finish(ws, s);
+}
+
 icgs_status icgs_colorize_backward(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
                                    const icgs_options* opt, const float* coeffs, const float* chol,
                                    const float* grad_coeffs, void* workspace, size_t workspace_bytes,

@@ -92,6 +92,10 @@ def load(path: str = LIB_PATH):
     lib.icgs_refine_workspace_size.restype = S
     lib.icgs_colorize_refine.argtypes = [P, P, P, P, ctypes.c_int32, P, P, S, P, P]
     lib.icgs_colorize_refine.restype = ctypes.c_int
+    lib.icgs_colorize_host_workspace_size.argtypes = [P, P, P, P]
+    lib.icgs_colorize_host_workspace_size.restype = S
+    lib.icgs_colorize_host.argtypes = [P, P, P, P, P, S, P, P, P, P]
+    lib.icgs_colorize_host.restype = ctypes.c_int
     lib.icgs_selftest_tc.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, P, P, P]
     lib.icgs_selftest_tc.restype = ctypes.c_int
     lib.icgs_set_stage_timing.argtypes = [ctypes.c_int]
@@ -286,6 +290,50 @@ def colorize(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, precisio
 
     _run_with_capacity(dev, size_fn, call_fn, instance_capacity)
     return coeffs, status, chol
+
+
+def colorize_host(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, precision="mixed",
+                  cond_tau=0.0, cam_batch=0, instance_capacity=0, opacity=None, refold_tau=0.0,
+                  coeffs_out=None, status_out=None):
+    """colorize() with the targets in host memory and the results returned in host memory
+    (icgs_colorize_host): targets is a contiguous CPU tensor [n_cams,H,W,K] (float32, bfloat16 or
+    float16; page-locked for copies that overlap the compute). Returns CPU coefficients
+    [n,(L+1)^2,K] float32 and status [n] uint8, written into coeffs_out / status_out when given."""
+    torch = _torch()
+    lib = load()
+    dev = scene.means.device
+    dt = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}.get(targets.dtype)
+    if dt is None:
+        raise TypeError(f"targets dtype {targets.dtype} is not float32, bfloat16 or float16")
+    if targets.is_cuda or not targets.is_contiguous() or targets.dim() != 4:
+        raise ValueError("targets must be a contiguous CPU tensor [n_cams,H,W,K]")
+    B = (sh_degree + 1) ** 2
+    K = int(targets.shape[-1])
+    pin = torch.cuda.is_available()
+    coeffs = coeffs_out if coeffs_out is not None else torch.empty((scene.n, B, K), dtype=torch.float32,
+                                                                   pin_memory=pin)
+    status = status_out if status_out is not None else torch.empty((scene.n,), dtype=torch.uint8, pin_memory=pin)
+    if coeffs.shape != (scene.n, B, K) or coeffs.dtype != torch.float32 or coeffs.is_cuda or not coeffs.is_contiguous():
+        raise ValueError("coeffs_out must be a contiguous CPU float32 tensor [n,(L+1)^2,K]")
+    if status.shape != (scene.n,) or status.dtype != torch.uint8 or status.is_cuda:
+        raise ValueError("status_out must be a CPU uint8 tensor [n]")
+    sc = scene._struct(opacity)
+    cm = cams._struct()
+    tg = _Targets(dt, K, targets.data_ptr())
+
+    def size_fn(cap):
+        o, _keep = _options(sh_degree, lam, precision, cond_tau, cam_batch, cap, refold_tau)
+        return lib.icgs_colorize_host_workspace_size(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg),
+                                                     ctypes.byref(o))
+
+    def call_fn(ptr, nbytes, cap):
+        o, _keep = _options(sh_degree, lam, precision, cond_tau, cam_batch, cap, refold_tau)
+        return lib.icgs_colorize_host(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(o),
+                                      ctypes.c_void_p(ptr), nbytes, ctypes.c_void_p(coeffs.data_ptr()),
+                                      ctypes.c_void_p(status.data_ptr()), None, _stream_ptr(dev))
+
+    _run_with_capacity(dev, size_fn, call_fn, instance_capacity)
+    return coeffs, status
 
 
 def colorize_noalloc(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, precision="mixed",

@@ -20,7 +20,8 @@ def test_header_declares_the_calls():
     for want in ["icgs_workspace_size", "icgs_colorize", "icgs_colorize_backward", "icgs_render_workspace_size",
                  "icgs_render", "icgs_last_error", "icgs_last_required_instances", "icgs_last_stats",
                  "icgs_colorize_noalloc", "icgs_noalloc_scratch_bytes", "icgs_selftest_tc",
-                 "icgs_refine_workspace_size", "icgs_colorize_refine"]:
+                 "icgs_refine_workspace_size", "icgs_colorize_refine", "icgs_colorize_host_workspace_size",
+                 "icgs_colorize_host"]:
         assert want in names
 
 
@@ -35,7 +36,8 @@ def _structs(n=10, n_cams=2, w=40, h=30, K=3, L=3):
     w2c = np.tile(np.array([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 3], np.float32), (n_cams, 1))
     cm = icgs._Cameras(n_cams, w, h, 0.2, intr.ctypes.data, w2c.ctypes.data)
     tg = icgs._Targets(icgs.F32, K, 16)
-    opt = icgs._Options(L, None, icgs.MIXED, 0.0, 0, 0)
+    opt = icgs._Options(sh_degree=L, lambda_=None, precision=icgs.MIXED, cond_tau=0.0, refold_tau=0.0, cam_batch=0,
+                        instance_capacity=0)
     return sc, cm, tg, opt, (intr, w2c)
 
 
@@ -47,6 +49,22 @@ def test_workspace_size_grows_with_capacity(lib):
         sizes.append(lib.icgs_workspace_size(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(opt)))
     assert sizes[0] > 0 and sizes[0] < sizes[1] < sizes[2]
     assert sizes[2] - sizes[1] >= 2 * 8 * (100000 - 2000) - 512  # keys + merge buffer (256-B aligned)
+
+
+def test_host_workspace_adds_the_staging_regions(lib):
+    """icgs_colorize_host's workspace is the colorize (accumulate) workspace followed by the staged
+    targets, the coefficients and the status bytes (each 256-byte aligned): with 16-bit targets it
+    is smaller by exactly the difference in staged target bytes."""
+    n, n_cams, w, h, K, L = 10, 2, 40, 30, 3, 3
+    sc, cm, tg, opt, keep = _structs(n, n_cams, w, h, K, L)
+    a = lambda x: (x + 255) // 256 * 256
+    host32 = lib.icgs_colorize_host_workspace_size(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg),
+                                                   ctypes.byref(opt))
+    tg16 = icgs._Targets(icgs.BF16, K, 16)
+    host16 = lib.icgs_colorize_host_workspace_size(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg16),
+                                                   ctypes.byref(opt))
+    assert host32 - host16 == a(n_cams * h * w * K * 4) - a(n_cams * h * w * K * 2)
+    assert host32 > a(n_cams * h * w * K * 4) + a(n * 16 * K * 4) + a(n)
 
 
 def test_bad_arguments_rejected_on_host(lib):
