@@ -2,9 +2,11 @@
 //
 // After binning, each tile owns a contiguous slot range of 64-bit keys (float32 depth bits << 32 |
 // Gaussian index); the keys are unique, so sorting them ascending gives depth order with ties in
-// index order. Lists up to kSortCap keys are bitonic-sorted in shared memory by one CTA per tile;
-// longer lists are queued and sorted by k_sort_long: shared-memory runs of kSortCap keys, then
-// merge-path merges between the slot range and a scratch range of the same place.
+// index order. For the tensor-core walk every list is sorted here, one CTA per tile (k_sort_tiles).
+// The CUDA-core walks sort lists of up to kWalkSortCap keys themselves; the longer ones are queued
+// (k_queue_tiles) and sorted by a persistent kernel (k_sort_queued). Up to kSortCap keys are sorted
+// in shared memory with the register/shuffle bitonic network; longer lists as runs of kSortCap keys
+// followed by merge-path merges between the slot range and a scratch range of the same place.
 #include <cuda_runtime.h>
 
 #include "icgs_internal.h"
@@ -14,11 +16,8 @@ namespace icgs {
 
 namespace {
 
-using walk::bitonic_sort_smem;
-
 constexpr int kSortThreads = 256;
-constexpr int kLongThreads = 1024;
-constexpr unsigned long long kPad = ~0ull;
+constexpr int kSortGrid = 152 * 6;  // persistent CTAs (32 KB of shared memory each)
 
 __device__ __forceinline__ void tile_range(const uint32_t* tile_off, int t, uint32_t capacity,
                                            uint32_t& b, uint32_t& e) {
@@ -27,9 +26,33 @@ __device__ __forceinline__ void tile_range(const uint32_t* tile_off, int t, uint
   if (e < b) e = b;
 }
 
+// Queues every tile whose list has more than min_len keys (one thread per tile; one counter
+// atomic per warp).
+__global__ void __launch_bounds__(kSortThreads) k_queue_tiles(const uint32_t* __restrict__ tile_off, int ntiles,
+                                                              uint32_t capacity, int min_len,
+                                                              uint32_t* __restrict__ queue, DevStatus* status) {
+  const int t = blockIdx.x * kSortThreads + threadIdx.x;
+  bool want = false;
+  if (t < ntiles) {
+    uint32_t b, e;
+    tile_range(tile_off, t, capacity, b, e);
+    const uint32_t n = e - b;
+    want = n > 1u && n > (uint32_t)min_len;
+  }
+  const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, want);
+  if (!ballot) return;  // uniform per warp
+  const int lane = threadIdx.x & 31;
+  uint32_t base = 0;
+  if (lane == 0) base = atomicAdd(&status->big_tiles, (uint32_t)__popc(ballot));
+  base = __shfl_sync(0xFFFFFFFFu, base, 0);
+  if (want) queue[base + __popc(ballot & ((1u << lane) - 1u))] = (uint32_t)t;
+}
+
+// Every tile list: sorted in place when it has at most kSortCap keys (one CTA per tile), queued
+// for k_sort_queued when longer.
 __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(const uint32_t* __restrict__ tile_off,
                                                              unsigned long long* __restrict__ entries,
-                                                             uint32_t capacity, uint32_t* __restrict__ big_list,
+                                                             uint32_t capacity, uint32_t* __restrict__ queue,
                                                              DevStatus* status) {
   __shared__ unsigned long long s[kSortCap];
   uint32_t b, e;
@@ -37,7 +60,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(const uint32_t* __r
   const int n = (int)(e - b);
   if (n <= 1) return;
   if (n > kSortCap) {
-    if (threadIdx.x == 0) big_list[atomicAdd(&status->big_tiles, 1u)] = blockIdx.x;
+    if (threadIdx.x == 0) queue[atomicAdd(&status->big_tiles, 1u)] = blockIdx.x;
     return;
   }
   walk::sort_keys_block<kSortCap / kSortThreads>(entries + b, (uint32_t)n, s);
@@ -56,28 +79,28 @@ __device__ __forceinline__ int merge_path(const unsigned long long* A, int na, c
   return lo;
 }
 
-__global__ void __launch_bounds__(kLongThreads) k_sort_long(const uint32_t* __restrict__ tile_off,
-                                                            unsigned long long* __restrict__ entries,
-                                                            unsigned long long* __restrict__ scratch,
-                                                            uint32_t capacity,
-                                                            const uint32_t* __restrict__ big_list,
-                                                            const DevStatus* status) {
+// Sorts the queued tile lists in place, a grid-stride loop over the queue. A list of up to
+// kSortCap keys is sorted in shared memory with the register/shuffle bitonic network sized to it;
+// a longer one as runs of kSortCap keys, then pairwise merge-path merges ping-ponging between its
+// slot range and the same range of the scratch array.
+__global__ void __launch_bounds__(kSortThreads) k_sort_queued(const uint32_t* __restrict__ tile_off,
+                                                              unsigned long long* __restrict__ entries,
+                                                              unsigned long long* __restrict__ scratch,
+                                                              uint32_t capacity, const uint32_t* __restrict__ queue,
+                                                              const DevStatus* status) {
   __shared__ unsigned long long s[kSortCap];
   const uint32_t count = status->big_tiles;
   for (uint32_t q = blockIdx.x; q < count; q += gridDim.x) {
     uint32_t b, e;
-    tile_range(tile_off, big_list[q], capacity, b, e);
+    tile_range(tile_off, queue[q], capacity, b, e);
     const int n = (int)(e - b);
-    // 1. sorted runs of kSortCap in shared memory
-    for (int r0 = 0; r0 < n; r0 += kSortCap) {
+    for (int r0 = 0; r0 < n; r0 += kSortCap) {  // sorted runs (the whole list when it fits)
       const int m = min(kSortCap, n - r0);
-      for (int k = threadIdx.x; k < kSortCap; k += kLongThreads) s[k] = k < m ? entries[b + r0 + k] : kPad;
-      __syncthreads();
-      bitonic_sort_smem<kLongThreads>(s, kSortCap);
-      for (int k = threadIdx.x; k < m; k += kLongThreads) entries[b + r0 + k] = s[k];
+      walk::sort_keys_block<kSortCap / kSortThreads>(entries + b + r0, (uint32_t)m, s);
+      for (int k = threadIdx.x; k < m; k += kSortThreads) entries[b + r0 + k] = s[k];
       __syncthreads();
     }
-    // 2. pairwise merges, ping-ponging between the slot range and the scratch range
+    if (n <= kSortCap) continue;  // uniform
     unsigned long long* src = entries + b;
     unsigned long long* dst = scratch + b;
     for (int width = kSortCap; width < n; width <<= 1) {
@@ -87,7 +110,7 @@ __global__ void __launch_bounds__(kLongThreads) k_sort_long(const uint32_t* __re
         const unsigned long long* A = src + lo;
         const unsigned long long* Bp = src + lo + na;
         const int tot = na + nb;
-        const int per = (tot + kLongThreads - 1) / kLongThreads;
+        const int per = (tot + kSortThreads - 1) / kSortThreads;
         const int d0 = min(tot, (int)threadIdx.x * per), d1 = min(tot, d0 + per);
         if (d0 < d1) {
           int ia = merge_path(A, na, Bp, nb, d0);
@@ -104,39 +127,28 @@ __global__ void __launch_bounds__(kLongThreads) k_sort_long(const uint32_t* __re
       dst = tmp;
     }
     if (src != entries + b)
-      for (int k = threadIdx.x; k < n; k += kLongThreads) entries[b + k] = src[k];
+      for (int k = threadIdx.x; k < n; k += kSortThreads) entries[b + k] = src[k];
     __syncthreads();
   }
 }
 
-// Queues the tiles whose list is longer than the walks sort in shared memory (kWalkSortCap).
-__global__ void __launch_bounds__(kSortThreads) k_queue_long_tiles(const uint32_t* __restrict__ tile_off, int ntiles,
-                                                                   uint32_t capacity, uint32_t* __restrict__ big_list,
-                                                                   DevStatus* status) {
-  const int t = blockIdx.x * kSortThreads + threadIdx.x;
-  if (t >= ntiles) return;
-  uint32_t b, e;
-  tile_range(tile_off, t, capacity, b, e);
-  if (e - b > (uint32_t)walk::kWalkSortCap) big_list[atomicAdd(&status->big_tiles, 1u)] = (uint32_t)t;
-}
-
 }  // namespace
 
-// sort_all: order every tile list here (walks that read the lists from global memory); otherwise
-// only the lists longer than the walks' shared-memory sort (kWalkSortCap).
+// sort_all: order every tile list here (walks that read the lists from global memory): one CTA per
+// tile, lists longer than kSortCap queued. Otherwise only the lists longer than the walks'
+// shared-memory sort (kWalkSortCap), queued and sorted by the persistent kernel.
 void launch_tile_sort(const Problem& p, int cb, bool sort_all, const Workspace& ws, cudaStream_t s) {
-  static_assert(walk::kWalkSortCap <= kSortCap, "the long-list sort takes everything the walks do not");
   const int ntiles = cb * p.tiles;
   cudaMemsetAsync(&ws.status->big_tiles, 0, sizeof(uint32_t), s);
   if (sort_all)
     k_sort_tiles<<<ntiles, kSortThreads, 0, s>>>(ws.tile_off, reinterpret_cast<unsigned long long*>(ws.entries),
                                                  p.capacity, ws.big_list, ws.status);
   else
-    k_queue_long_tiles<<<(ntiles + kSortThreads - 1) / kSortThreads, kSortThreads, 0, s>>>(
-        ws.tile_off, ntiles, p.capacity, ws.big_list, ws.status);
-  k_sort_long<<<152, kLongThreads, 0, s>>>(ws.tile_off, reinterpret_cast<unsigned long long*>(ws.entries),
-                                           reinterpret_cast<unsigned long long*>(ws.entries_tmp), p.capacity,
-                                           ws.big_list, ws.status);
+    k_queue_tiles<<<(ntiles + kSortThreads - 1) / kSortThreads, kSortThreads, 0, s>>>(
+        ws.tile_off, ntiles, p.capacity, walk::kWalkSortCap, ws.big_list, ws.status);
+  k_sort_queued<<<kSortGrid, kSortThreads, 0, s>>>(ws.tile_off, reinterpret_cast<unsigned long long*>(ws.entries),
+                                                   reinterpret_cast<unsigned long long*>(ws.entries_tmp), p.capacity,
+                                                   ws.big_list, ws.status);
   note_launches(2);
 }
 

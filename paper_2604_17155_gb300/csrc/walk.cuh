@@ -155,12 +155,12 @@ __device__ __forceinline__ void sort_into_smem(const unsigned long long* g, uint
 // are the common case and pay for fewer stages); longer ones take block_bitonic_sort.
 template <int MAXE>
 __device__ __forceinline__ void sort_keys_block(const unsigned long long* g, uint32_t len, unsigned long long* s) {
-  if (len <= (uint32_t)kThreads) {
-    int P = 2;
+  if (len <= (uint32_t)kThreads) {  // one key per thread (threads t >= P sort padding)
+    int P = 32;
     while (P < (int)len) P <<= 1;
-    for (int k = threadIdx.x; k < P; k += kThreads) s[k] = k < (int)len ? g[k] : ~0ull;
-    __syncthreads();
-    bitonic_sort_smem<kThreads>(s, P);
+    unsigned long long v[1];
+    v[0] = threadIdx.x < len ? g[threadIdx.x] : ~0ull;
+    block_bitonic_sort<1>(v, s, P);
     return;
   }
   int P = kThreads;
