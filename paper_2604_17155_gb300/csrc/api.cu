@@ -216,6 +216,19 @@ std::vector<DevCam> build_cams(const icgs_cameras* cams) {
     }
     c.limx = (float)(1.3 * ((double)cams->width / (2.0 * (double)in[0])));
     c.limy = (float)(1.3 * ((double)cams->height / (2.0 * (double)in[1])));
+    // upper bound on the squared spectral norm of R: the largest absolute row sum of R^T R
+    // (Gershgorin; exactly 1 for a rotation)
+    double bound = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      double row = 0.0;
+      for (int b = 0; b < 3; ++b) {
+        double g = 0.0;
+        for (int r = 0; r < 3; ++r) g += (double)w[4 * r + a] * (double)w[4 * r + b];
+        row += std::fabs(g);
+      }
+      bound = std::max(bound, row);
+    }
+    c.rnorm2 = (float)(bound * (1.0 + 1e-6));
   }
   return out;
 }

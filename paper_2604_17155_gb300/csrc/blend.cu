@@ -118,22 +118,59 @@ __global__ void __launch_bounds__(kThreads, KC <= 3 ? 8 : (KC <= 8 ? 5 : 4)) k_b
 #pragma unroll
       for (int half = 0; half < kBatch / 32; ++half) {
        uint32_t bits = warp_hit_bits(s_geo, s_half, half * 32, nb, c);
-       while (bits) {  // only the Gaussians whose box touches this warp's block, in depth order
-        const int g = half * 32 + __ffs(bits) - 1;
-        bits &= bits - 1;
-        float w = 0.0f, al, ex;
-        bool cap;
-        if (!done) w = blend_step(s_geo[g], s_aux[g], c.pxf, c.pyf, T, done, al, ex, cap);
-        if (__any_sync(kFull, w > 0.0f)) {
-          npairs += w > 0.0f;
-          float v[NP];
-          v[0] = w;
+       if constexpr (NP <= 4) {
+        // two consecutive hits share one reduction of 2 NP values (their order is kept: the
+        // second Gaussian is blended with the transmittance the first one leaves)
+        constexpr int NP2 = 2 * NP;
+        constexpr int SHIFT2 = 5 - Log2<NP2>::value;
+        while (bits) {
+          const int g1 = half * 32 + __ffs(bits) - 1;
+          bits &= bits - 1;
+          const int g2 = bits ? half * 32 + __ffs(bits) - 1 : -1;
+          bits &= bits - 1;
+          float w1 = 0.0f, w2 = 0.0f, al, ex;
+          bool cap;
+          if (!done) w1 = blend_step(s_geo[g1], s_aux[g1], c.pxf, c.pyf, T, done, al, ex, cap);
+          if (g2 >= 0 && !done) w2 = blend_step(s_geo[g2], s_aux[g2], c.pxf, c.pyf, T, done, al, ex, cap);
+          if (__any_sync(kFull, w1 > 0.0f || w2 > 0.0f)) {
+            npairs += (w1 > 0.0f) + (w2 > 0.0f);
+            float v[NP2];
+            v[0] = w1;
+            v[NP] = w2;
 #pragma unroll
-          for (int k = 0; k < KC; ++k) v[k + 1] = w * tv[k];
+            for (int k = 0; k < KC; ++k) {
+              v[k + 1] = w1 * tv[k];
+              v[NP + k + 1] = w2 * tv[k];
+            }
 #pragma unroll
-          for (int k = NV; k < NP; ++k) v[k] = 0.0f;
-          const float r = warp_transpose_reduce<NP>(v, lane);
-          if (reducer) atomicAdd(&s_acc[g][my_value], r);
+            for (int k = NV; k < NP; ++k) {
+              v[k] = 0.0f;
+              v[NP + k] = 0.0f;
+            }
+            const float r = warp_transpose_reduce<NP2>(v, lane);
+            const int vi = lane >> SHIFT2, vk = vi & (NP - 1);
+            const int gg = vi < NP ? g1 : g2;
+            if ((lane & ((1 << SHIFT2) - 1)) == 0 && vk < NV && gg >= 0) atomicAdd(&s_acc[gg][vk], r);
+          }
+        }
+       } else {
+        while (bits) {  // only the Gaussians whose box touches this warp's block, in depth order
+          const int g = half * 32 + __ffs(bits) - 1;
+          bits &= bits - 1;
+          float w = 0.0f, al, ex;
+          bool cap;
+          if (!done) w = blend_step(s_geo[g], s_aux[g], c.pxf, c.pyf, T, done, al, ex, cap);
+          if (__any_sync(kFull, w > 0.0f)) {
+            npairs += w > 0.0f;
+            float v[NP];
+            v[0] = w;
+#pragma unroll
+            for (int k = 0; k < KC; ++k) v[k + 1] = w * tv[k];
+#pragma unroll
+            for (int k = NV; k < NP; ++k) v[k] = 0.0f;
+            const float r = warp_transpose_reduce<NP>(v, lane);
+            if (reducer) atomicAdd(&s_acc[g][my_value], r);
+          }
         }
        }
       }

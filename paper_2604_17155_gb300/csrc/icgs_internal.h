@@ -34,7 +34,7 @@ struct DevCam {
   float w[12];        // world_to_cam, row-major [R|t]
   float centre[3];    // -R^T t (host double, rounded)
   float limx, limy;   // 1.3 * tan(fov/2) in x and y
-  float pad;
+  float rnorm2;       // >= squared spectral norm of R (the early frustum cull of the projection)
   double centre_d[3]; // -R^T t in double (the FP64 re-fold of ill-conditioned Gaussians)
 };
 

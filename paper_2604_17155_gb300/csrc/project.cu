@@ -98,12 +98,29 @@ __device__ __forceinline__ int4 project_pair(const float* __restrict__ means, co
   float tx_lo, ty_lo;
   const float tx = affine_ff(c.w[0], c.w[1], c.w[2], c.w[3], mx3, my3, mz3, tx_lo);
   const float ty = affine_ff(c.w[4], c.w[5], c.w[6], c.w[7], mx3, my3, mz3, ty_lo);
+  const float iz = 1.0f / tz;
+  const float qthr = 2.0f * logf(255.0f * o);
+  const float sx = scales[3 * i], sy = scales[3 * i + 1], sz = scales[3 * i + 2];
+  {
+    // Early cull. Sigma'_xx = |T_0 M|^2 + 0.3 <= |J_0|^2 |R|^2 s_max^2 + 0.3 with
+    // |J_0| <= (f/z) sqrt(1 + lim^2) (the Jacobian's clamp), so the support half-width is at most
+    // sqrt(qthr (that bound)). A mean farther outside the image than this (plus a pixel) has no
+    // pixel centre in its support: the box test below would reject it after the full covariance.
+    const float smax = fmaxf(fmaxf(sx, sy), sz);
+    const float fz = fmaxf(c.fx, c.fy) * iz;
+    const float jb = 1.0f + fmaxf(c.limx * c.limx, c.limy * c.limy);
+    const float hmax = sqrtf(fmaxf(qthr, 0.0f) * (fz * fz * jb * c.rnorm2 * smax * smax + 0.3f)) * 1.001f + 1.0f;
+    const float mxa = fmaf(c.fx, tx * iz, c.cx), mya = fmaf(c.fy, ty * iz, c.cy);
+    if (mxa + hmax < 0.0f || mxa - hmax > (float)width || mya + hmax < 0.0f || mya - hmax > (float)height) {
+      rect[ji] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+      return none;
+    }
+  }
 
   // 3D covariance Sigma = M M^T with M = R(q) diag(s)
   float qw = quats[4 * i], qx = quats[4 * i + 1], qy = quats[4 * i + 2], qz = quats[4 * i + 3];
   const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
   qw *= qn; qx *= qn; qy *= qn; qz *= qn;
-  const float sx = scales[3 * i], sy = scales[3 * i + 1], sz = scales[3 * i + 2];
   const float r00 = 1.f - 2.f * (qy * qy + qz * qz), r01 = 2.f * (qx * qy - qw * qz), r02 = 2.f * (qx * qz + qw * qy);
   const float r10 = 2.f * (qx * qy + qw * qz), r11 = 1.f - 2.f * (qx * qx + qz * qz), r12 = 2.f * (qy * qz - qw * qx);
   const float r20 = 2.f * (qx * qz - qw * qy), r21 = 2.f * (qy * qz + qw * qx), r22 = 1.f - 2.f * (qx * qx + qy * qy);
@@ -112,7 +129,6 @@ __device__ __forceinline__ int4 project_pair(const float* __restrict__ means, co
   const float m20 = r20 * sx, m21 = r21 * sy, m22 = r22 * sz;
 
   // EWA: T = J W (2x3), J at the clamped camera-space mean
-  const float iz = 1.0f / tz;
   const float ux = fminf(c.limx, fmaxf(-c.limx, tx * iz));
   const float uy = fminf(c.limy, fmaxf(-c.limy, ty * iz));
   const float j00 = c.fx * iz, j02 = -c.fx * ux * iz;
@@ -138,7 +154,6 @@ __device__ __forceinline__ int4 project_pair(const float* __restrict__ means, co
     return none;
   }
   const float idet = 1.0f / det;
-  const float qthr = 2.0f * logf(255.0f * o);
   // x-extent of {q <= qthr} is sqrt(qthr * Sigma'_xx); pad so the box contains every pixel centre
   // that the blend kernel's own float32 alpha test can accept.
   const float hx = sqrtf(fmaxf(qthr, 0.0f) * ca2) * 1.0001f + 0.01f;
