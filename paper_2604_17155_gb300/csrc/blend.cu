@@ -363,29 +363,37 @@ __global__ void __launch_bounds__(kThreads, KC <= 4 ? 6 : (KC <= 16 ? 4 : (KC <=
 #pragma unroll
       for (int half = 0; half < kBatch / 32; ++half) {
        uint32_t bits = warp_hit_bits(s_geo, s_half, half * 32, nb, c);
+       // dL/dalpha_m of one hit for this pixel (0 when skipped or capped); updates T and P
+       auto d_opacity = [&](int g) -> float {
+         if (done) return 0.0f;
+         const float Tm = T;
+         float al = 0.0f, ex = 0.0f;
+         bool cap = false;
+         const float w = blend_step(s_geo[g], s_aux[g], c.pxf, c.pyf, T, done, al, ex, cap);
+         if (!(w > 0.0f)) return 0.0f;
+         float gg = s_pay[g][KC];
+#pragma unroll
+         for (int k = 0; k < KC; ++k) gg = fmaf(s_pay[g][k], tv[k], gg);
+         P = fmaf(gg, w, P);
+         const float dalpha = gg * Tm - __fdividef(F - P, 1.0f - al);
+         return cap ? 0.0f : dalpha * ex;
+       };
+       // two consecutive hits (in depth order) share one warp reduction of their two values
        while (bits) {
-        const int g = half * 32 + __ffs(bits) - 1;
+        const int g1 = half * 32 + __ffs(bits) - 1;
         bits &= bits - 1;
-
-        float d_o = 0.0f;
-        if (!done) {
-          const float Tm = T;
-          float al = 0.0f, ex = 0.0f;
-          bool cap = false;
-          const float w = blend_step(s_geo[g], s_aux[g], c.pxf, c.pyf, T, done, al, ex, cap);
-          if (w > 0.0f) {
-            float gg = s_pay[g][KC];
+        const int g2 = bits ? half * 32 + __ffs(bits) - 1 : -1;
+        bits &= bits - 1;
+        const float d1 = d_opacity(g1);
+        const float d2 = g2 >= 0 ? d_opacity(g2) : 0.0f;
+        if (__any_sync(kFull, d1 != 0.0f || d2 != 0.0f)) {
+          // lanes < 16 end with the sum of d1, lanes >= 16 with the sum of d2
+          const bool upper = (lane & 16) != 0;
+          float r = (upper ? d2 : d1) + __shfl_xor_sync(kFull, upper ? d1 : d2, 16);
 #pragma unroll
-            for (int k = 0; k < KC; ++k) gg = fmaf(s_pay[g][k], tv[k], gg);
-            P = fmaf(gg, w, P);
-            const float dalpha = gg * Tm - (F - P) / (1.0f - al);
-            if (!cap) d_o = dalpha * ex;
-          }
-        }
-        if (__any_sync(kFull, d_o != 0.0f)) {
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) d_o += __shfl_xor_sync(kFull, d_o, o);
-          if (lane == 0) atomicAdd(&s_go[g], d_o);
+          for (int o = 8; o > 0; o >>= 1) r += __shfl_xor_sync(kFull, r, o);
+          if (lane == 0) atomicAdd(&s_go[g1], r);
+          if (lane == 16 && g2 >= 0) atomicAdd(&s_go[g2], r);
         }
        }
       }

@@ -674,25 +674,27 @@ __global__ void k_refine_update_l0(int64_t n, int K, int RS, const float* __rest
 // ------------------------------------------------------------------------------------------
 // per (camera, Gaussian) payloads
 // ------------------------------------------------------------------------------------------
+// One thread per (camera j, Gaussian i) of the pass, i fastest, so consecutive threads write
+// consecutive payload rows.
 template <int B>
 __global__ void k_payload_render(int64_t n, int K, const float* __restrict__ means,
                                  const DevCam* __restrict__ cams, int cb,
                                  const float* __restrict__ coeffs, float* __restrict__ payload) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)cb * n) return;
+  const int j = (int)(t / n);
+  const int64_t i = t - (int64_t)j * n;
   const float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
+  const float3 d = view_dir(mu, cams[j]);
+  float Y[B];
+  sh_basis<B>(d.x, d.y, d.z, Y);
   const float* ci = coeffs + i * B * K;
-  for (int j = 0; j < cb; ++j) {
-    const float3 d = view_dir(mu, cams[j]);
-    float Y[B];
-    sh_basis<B>(d.x, d.y, d.z, Y);
-    float* out = payload + ((int64_t)j * n + i) * K;
-    for (int k = 0; k < K; ++k) {
-      float s = 0.0f;
+  float* out = payload + t * K;
+  for (int k = 0; k < K; ++k) {
+    float s = 0.0f;
 #pragma unroll
-      for (int m = 0; m < B; ++m) s = fmaf(Y[m], ci[m * K + k], s);
-      out[k] = s;
-    }
+    for (int m = 0; m < B; ++m) s = fmaf(Y[m], ci[m * K + k], s);
+    out[k] = s;
   }
 }
 
@@ -701,30 +703,29 @@ __global__ void k_payload_adjoint(int64_t n, int K, const float* __restrict__ me
                                   const DevCam* __restrict__ cams, int cb,
                                   const float* __restrict__ coeffs, const float* __restrict__ u,
                                   const float* __restrict__ reg, float* __restrict__ payload) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)cb * n) return;
+  const int j = (int)(t / n);
+  const int64_t i = t - (int64_t)j * n;
   const float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
+  const float3 d = view_dir(mu, cams[j]);
+  float Y[B];
+  sh_basis<B>(d.x, d.y, d.z, Y);
   const float* ci = coeffs + i * B * K;
   const float* ui = u + i * B * K;
-  const float rg = reg[i];
-  for (int j = 0; j < cb; ++j) {
-    const float3 d = view_dir(mu, cams[j]);
-    float Y[B];
-    sh_basis<B>(d.x, d.y, d.z, Y);
-    float* out = payload + ((int64_t)j * n + i) * (K + 1);
-    float beta = -rg;
-    for (int k = 0; k < K; ++k) {
-      float a = 0.0f, yc = 0.0f;
+  float* out = payload + t * (K + 1);
+  float beta = -reg[i];
+  for (int k = 0; k < K; ++k) {
+    float a = 0.0f, yc = 0.0f;
 #pragma unroll
-      for (int m = 0; m < B; ++m) {
-        a = fmaf(Y[m], ui[m * K + k], a);
-        yc = fmaf(Y[m], ci[m * K + k], yc);
-      }
-      out[k] = a;
-      beta = fmaf(-a, yc, beta);
+    for (int m = 0; m < B; ++m) {
+      a = fmaf(Y[m], ui[m * K + k], a);
+      yc = fmaf(Y[m], ci[m * K + k], yc);
     }
-    out[K] = beta;
+    out[k] = a;
+    beta = fmaf(-a, yc, beta);
   }
+  out[K] = beta;
 }
 
 template <int B, bool MIXED>
@@ -809,7 +810,7 @@ void launch_refine_update(const Problem& p, const float* lam_dev, const float* l
 
 void launch_payload_render(const Problem& p, const float* means, const float* coeffs, int cb,
                            const Workspace& ws, cudaStream_t s) {
-  const unsigned grid = (unsigned)((p.n + 127) / 128);
+  const unsigned grid = (unsigned)(((int64_t)cb * p.n + 127) / 128);
   if (p.B == 1) k_payload_render<1><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.payload);
   else if (p.B == 4) k_payload_render<4><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.payload);
   else if (p.B == 9) k_payload_render<9><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.payload);
@@ -838,7 +839,7 @@ void launch_adjoint_prepare(const Problem& p, const float* lam_dev, const float*
 
 void launch_payload_adjoint(const Problem& p, const float* means, const float* coeffs, int cb,
                             const Workspace& ws, cudaStream_t s) {
-  const unsigned grid = (unsigned)((p.n + 127) / 128);
+  const unsigned grid = (unsigned)(((int64_t)cb * p.n + 127) / 128);
   if (p.B == 1) k_payload_adjoint<1><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.u, ws.reg, ws.payload);
   else if (p.B == 4) k_payload_adjoint<4><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.u, ws.reg, ws.payload);
   else if (p.B == 9) k_payload_adjoint<9><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.u, ws.reg, ws.payload);
