@@ -172,7 +172,8 @@ ICGS_API size_t icgs_render_workspace_size(const icgs_scene* scene, const icgs_c
                                   int32_t sh_degree, int32_t channels, int64_t instance_capacity);
 
 /* Render (Eq. 1-3): images_out device [n_cams,height,width,channels] float32 from coeffs device
- * [n,(L+1)^2,channels]; background 0. */
+ * [n,(L+1)^2,channels]; background 0. (L+1)^2 x channels must be at most 12287
+ * (ICGS_ERR_UNSUPPORTED otherwise); the same limit applies to icgs_colorize_refine. */
 ICGS_API icgs_status icgs_render(const icgs_scene* scene, const icgs_cameras* cams, int32_t sh_degree,
                         int32_t channels, const float* coeffs, int64_t instance_capacity,
                         void* workspace, size_t workspace_bytes, float* images_out, void* stream);
@@ -210,8 +211,9 @@ ICGS_API icgs_status icgs_colorize_noalloc(const icgs_scene* scene, const icgs_c
  *   chol_out       DEVICE, as for icgs_colorize (for icgs_colorize_backward), or NULL.
  *   workspace      DEVICE, 256-byte aligned, icgs_colorize_host_workspace_size() bytes: the
  *                  colorize workspace followed by the staged targets, coefficients and status.
- * The targets are copied to the device in chunks of cameras on a copy stream owned by the library
- * (one per host thread and device), and each chunk's walk waits only for its own copy, so the
+ * The targets are copied to the device in chunks of cameras, alternating between two copy streams
+ * owned by the library (one pair per host thread and device), and each chunk's walk waits only for
+ * its own copy, so the
  * copies overlap the projection, binning and the walk of earlier chunks. The call synchronises
  * `stream` before returning. The staging region is overwritten only after the work already queued
  * on `stream` has finished. Errors as for icgs_colorize. */

@@ -381,10 +381,10 @@ icgs_status icgs_colorize(const icgs_scene* scene, const icgs_cameras* cams, con
 
 namespace {
 
-// Copy stream and event pool of icgs_colorize_host, one per host thread and device.
+// Copy streams and event pool of icgs_colorize_host, one set per host thread and device.
 struct HostPipe {
   int device = -1;
-  cudaStream_t copy = nullptr;
+  cudaStream_t copy[2] = {nullptr, nullptr};  // chunks alternate between two copy streams
   cudaEvent_t start = nullptr;
   std::vector<cudaEvent_t> ready;
 };
@@ -398,7 +398,7 @@ icgs_status host_pipe(int n_events, HostPipe*& out) {
   HostPipe& hp = g_pipe;
   if (hp.device != dev) {  // first use on this thread, or another device: a fresh stream and pool
     hp = HostPipe();
-    ICGS_TRY_CUDA(cudaStreamCreateWithFlags(&hp.copy, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) ICGS_TRY_CUDA(cudaStreamCreateWithFlags(&hp.copy[k], cudaStreamNonBlocking));
     ICGS_TRY_CUDA(cudaEventCreateWithFlags(&hp.start, cudaEventDisableTiming));
     hp.device = dev;
   }
@@ -483,12 +483,12 @@ icgs_status icgs_colorize_host(const icgs_scene* scene, const icgs_cameras* cams
   // the staging buffer is overwritten only after the work already queued on `stream` (which may
   // read it) has finished
   ICGS_TRY_CUDA(cudaEventRecord(hp->start, s));
-  ICGS_TRY_CUDA(cudaStreamWaitEvent(hp->copy, hp->start, 0));
+  for (int k = 0; k < 2; ++k) ICGS_TRY_CUDA(cudaStreamWaitEvent(hp->copy[k], hp->start, 0));
   for (size_t c = 0; c < chunk_cam0.size(); ++c) {
     const size_t off = (size_t)chunk_cam0[c] * cam_bytes;
-    ICGS_TRY_CUDA(cudaMemcpyAsync(t_dev + off, t_host + off, (size_t)chunk_n[c] * cam_bytes, cudaMemcpyHostToDevice,
-                                  hp->copy));
-    ICGS_TRY_CUDA(cudaEventRecord(hp->ready[c], hp->copy));
+    cudaStream_t cs = hp->copy[c & 1];
+    ICGS_TRY_CUDA(cudaMemcpyAsync(t_dev + off, t_host + off, (size_t)chunk_n[c] * cam_bytes, cudaMemcpyHostToDevice, cs));
+    ICGS_TRY_CUDA(cudaEventRecord(hp->ready[c], cs));
   }
 
   if ((st = upload_common(p, cams, lam, ws, s)) != ICGS_OK) return st;
@@ -596,6 +596,8 @@ icgs_status icgs_colorize_refine(const icgs_scene* scene, const icgs_cameras* ca
              opt->instance_capacity, p);
   if (st != ICGS_OK) return st;
   if (n_steps < 0) return fail(ICGS_ERR_INVALID_ARG, "n_steps = %d must be >= 0", n_steps);
+  if (p.B * p.K > kMaxPayloadRow)
+    return fail(ICGS_ERR_UNSUPPORTED, "(L+1)^2 x channels = %d exceeds %d for the render", p.B * p.K, kMaxPayloadRow);
   if ((!chol || !coeffs_inout) && p.n > 0) return fail(ICGS_ERR_INVALID_ARG, "chol and coeffs_inout are required");
   float lam[kMaxSH];
   if ((st = lambda_of(opt, p.L, lam)) != ICGS_OK) return st;
@@ -650,6 +652,8 @@ icgs_status icgs_render(const icgs_scene* scene, const icgs_cameras* cams, int32
   icgs_status st = setup(scene, cams, channels, sh_degree, ICGS_PRECISION_PLAIN, 0.0f, 0.0f, 0, instance_capacity, p);
   if (st != ICGS_OK) return st;
   if (!images_out || (!coeffs && p.n > 0)) return fail(ICGS_ERR_INVALID_ARG, "coeffs and images_out are required");
+  if (p.B * p.K > kMaxPayloadRow)
+    return fail(ICGS_ERR_UNSUPPORTED, "(L+1)^2 x channels = %d exceeds %d for the render", p.B * p.K, kMaxPayloadRow);
   const Workspace need = carve(nullptr, p, kNeedRender);
   if (!workspace || workspace_bytes < need.total)
     return fail(ICGS_ERR_WORKSPACE_TOO_SMALL, "workspace of %zu bytes, need %zu", workspace_bytes, need.total);

@@ -11,6 +11,8 @@ namespace icgs {
 constexpr int kTile = 16;            // screen tiles are 16x16 pixels; one CTA of 256 threads each
 constexpr int kTilePixels = kTile * kTile;
 constexpr int kMaxSH = 16;           // (L+1)^2 for L = 3
+// A payload CTA stages at least one Gaussian's (L+1)^2 x K coefficients in 48 KB of shared memory.
+constexpr int kMaxPayloadRow = 12287;
 constexpr int kSortCap = 4096;       // tile lists up to this length are sorted in shared memory
 constexpr uint32_t kMaxCapacity = 0x7FFFFFF0u;
 constexpr uint8_t kGaussOk = 0, kGaussUnseen = 1, kGaussFp64 = 2;  // icgs.h ICGS_GAUSSIAN_*

@@ -674,58 +674,100 @@ __global__ void k_refine_update_l0(int64_t n, int K, int RS, const float* __rest
 // ------------------------------------------------------------------------------------------
 // per (camera, Gaussian) payloads
 // ------------------------------------------------------------------------------------------
-// One thread per (camera j, Gaussian i) of the pass, i fastest, so consecutive threads write
-// consecutive payload rows.
-template <int B>
-__global__ void k_payload_render(int64_t n, int K, const float* __restrict__ means,
-                                 const DevCam* __restrict__ cams, int cb,
-                                 const float* __restrict__ coeffs, float* __restrict__ payload) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= (int64_t)cb * n) return;
-  const int j = (int)(t / n);
-  const int64_t i = t - (int64_t)j * n;
-  const float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
-  const float3 d = view_dir(mu, cams[j]);
-  float Y[B];
-  sh_basis<B>(d.x, d.y, d.z, Y);
-  const float* ci = coeffs + i * B * K;
-  float* out = payload + t * K;
-  for (int k = 0; k < K; ++k) {
-    float s = 0.0f;
-#pragma unroll
-    for (int m = 0; m < B; ++m) s = fmaf(Y[m], ci[m * K + k], s);
-    out[k] = s;
+// Payload kernels. A CTA takes G consecutive Gaussians (G = 64 when their coefficient rows fit):
+// the rows (contiguous in global memory) are staged in shared memory with coalesced loads, at an
+// odd row stride RW so that the threads' row reads fall in distinct banks. The 256 threads are G
+// Gaussians x (256 / G) camera lanes; a lane loops over its cameras, and the threads of a warp
+// write consecutive payload rows of one camera.
+constexpr int kPayThreads = 256;
+
+__device__ __forceinline__ void stage_rows(const float* __restrict__ src, int64_t i0, int gcount, int BK, int RW,
+                                           float* dst) {
+  const float* base = src + i0 * BK;
+  for (int e = threadIdx.x; e < gcount * BK; e += kPayThreads) {
+    const int g = e / BK;
+    dst[g * RW + (e - g * BK)] = base[e];
   }
 }
 
 template <int B>
-__global__ void k_payload_adjoint(int64_t n, int K, const float* __restrict__ means,
-                                  const DevCam* __restrict__ cams, int cb,
-                                  const float* __restrict__ coeffs, const float* __restrict__ u,
-                                  const float* __restrict__ reg, float* __restrict__ payload) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= (int64_t)cb * n) return;
-  const int j = (int)(t / n);
-  const int64_t i = t - (int64_t)j * n;
+__global__ void __launch_bounds__(kPayThreads) k_payload_render(int64_t n, int K, int G, const float* __restrict__ means,
+                                                                const DevCam* __restrict__ cams, int cb,
+                                                                const float* __restrict__ coeffs,
+                                                                float* __restrict__ payload) {
+  extern __shared__ float s_rows[];
+  const int BK = B * K, RW = BK | 1;
+  const int64_t i0 = blockIdx.x * (int64_t)G;
+  const int gcount = (int)min((int64_t)G, n - i0);
+  stage_rows(coeffs, i0, gcount, BK, RW, s_rows);
+  __syncthreads();
+  const int g = threadIdx.x % G, lanes = kPayThreads / G, cl = threadIdx.x / G;
+  if (g >= gcount) return;
+  const int64_t i = i0 + g;
   const float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
-  const float3 d = view_dir(mu, cams[j]);
-  float Y[B];
-  sh_basis<B>(d.x, d.y, d.z, Y);
-  const float* ci = coeffs + i * B * K;
-  const float* ui = u + i * B * K;
-  float* out = payload + t * (K + 1);
-  float beta = -reg[i];
-  for (int k = 0; k < K; ++k) {
-    float a = 0.0f, yc = 0.0f;
+  const float* ci = s_rows + g * RW;
+  for (int j = cl; j < cb; j += lanes) {
+    const float3 d = view_dir(mu, cams[j]);
+    float Y[B];
+    sh_basis<B>(d.x, d.y, d.z, Y);
+    float* out = payload + ((int64_t)j * n + i) * K;
+    for (int k = 0; k < K; ++k) {
+      float acc = 0.0f;
 #pragma unroll
-    for (int m = 0; m < B; ++m) {
-      a = fmaf(Y[m], ui[m * K + k], a);
-      yc = fmaf(Y[m], ci[m * K + k], yc);
+      for (int m = 0; m < B; ++m) acc = fmaf(Y[m], ci[m * K + k], acc);
+      out[k] = acc;
     }
-    out[k] = a;
-    beta = fmaf(-a, yc, beta);
   }
-  out[K] = beta;
+}
+
+template <int B>
+__global__ void __launch_bounds__(kPayThreads) k_payload_adjoint(int64_t n, int K, int G, const float* __restrict__ means,
+                                                                 const DevCam* __restrict__ cams, int cb,
+                                                                 const float* __restrict__ coeffs,
+                                                                 const float* __restrict__ u,
+                                                                 const float* __restrict__ reg,
+                                                                 float* __restrict__ payload) {
+  extern __shared__ float s_rows[];
+  const int BK = B * K, RW = BK | 1;
+  const int64_t i0 = blockIdx.x * (int64_t)G;
+  const int gcount = (int)min((int64_t)G, n - i0);
+  stage_rows(coeffs, i0, gcount, BK, RW, s_rows);
+  stage_rows(u, i0, gcount, BK, RW, s_rows + G * RW);
+  __syncthreads();
+  const int g = threadIdx.x % G, lanes = kPayThreads / G, cl = threadIdx.x / G;
+  if (g >= gcount) return;
+  const int64_t i = i0 + g;
+  const float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
+  const float* ci = s_rows + g * RW;
+  const float* ui = s_rows + (G + g) * RW;
+  const float rg = reg[i];
+  for (int j = cl; j < cb; j += lanes) {
+    const float3 d = view_dir(mu, cams[j]);
+    float Y[B];
+    sh_basis<B>(d.x, d.y, d.z, Y);
+    float* out = payload + ((int64_t)j * n + i) * (K + 1);
+    float beta = -rg;
+    for (int k = 0; k < K; ++k) {
+      float a = 0.0f, yc = 0.0f;
+#pragma unroll
+      for (int m = 0; m < B; ++m) {
+        a = fmaf(Y[m], ui[m * K + k], a);
+        yc = fmaf(Y[m], ci[m * K + k], yc);
+      }
+      out[k] = a;
+      beta = fmaf(-a, yc, beta);
+    }
+    out[K] = beta;
+  }
+}
+
+// Gaussians per payload CTA: the largest power of two <= 64 whose staged rows (arrays of them)
+// fit in 48 KB of shared memory.
+int payload_group(int B, int K, int arrays) {
+  const size_t row = (size_t)((B * K) | 1) * sizeof(float) * arrays;
+  int G = 64;
+  while (G > 1 && (size_t)G * row > 48 * 1024) G >>= 1;
+  return G;
 }
 
 template <int B, bool MIXED>
@@ -810,11 +852,13 @@ void launch_refine_update(const Problem& p, const float* lam_dev, const float* l
 
 void launch_payload_render(const Problem& p, const float* means, const float* coeffs, int cb,
                            const Workspace& ws, cudaStream_t s) {
-  const unsigned grid = (unsigned)(((int64_t)cb * p.n + 127) / 128);
-  if (p.B == 1) k_payload_render<1><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.payload);
-  else if (p.B == 4) k_payload_render<4><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.payload);
-  else if (p.B == 9) k_payload_render<9><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.payload);
-  else k_payload_render<16><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.payload);
+  const int G = payload_group(p.B, p.K, 1);
+  const unsigned grid = (unsigned)((p.n + G - 1) / G);
+  const size_t smem = (size_t)G * ((p.B * p.K) | 1) * sizeof(float);
+  if (p.B == 1) k_payload_render<1><<<grid, kPayThreads, smem, s>>>(p.n, p.K, G, means, ws.cams, cb, coeffs, ws.payload);
+  else if (p.B == 4) k_payload_render<4><<<grid, kPayThreads, smem, s>>>(p.n, p.K, G, means, ws.cams, cb, coeffs, ws.payload);
+  else if (p.B == 9) k_payload_render<9><<<grid, kPayThreads, smem, s>>>(p.n, p.K, G, means, ws.cams, cb, coeffs, ws.payload);
+  else k_payload_render<16><<<grid, kPayThreads, smem, s>>>(p.n, p.K, G, means, ws.cams, cb, coeffs, ws.payload);
   note_launches(1);
 }
 
@@ -839,11 +883,17 @@ void launch_adjoint_prepare(const Problem& p, const float* lam_dev, const float*
 
 void launch_payload_adjoint(const Problem& p, const float* means, const float* coeffs, int cb,
                             const Workspace& ws, cudaStream_t s) {
-  const unsigned grid = (unsigned)(((int64_t)cb * p.n + 127) / 128);
-  if (p.B == 1) k_payload_adjoint<1><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.u, ws.reg, ws.payload);
-  else if (p.B == 4) k_payload_adjoint<4><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.u, ws.reg, ws.payload);
-  else if (p.B == 9) k_payload_adjoint<9><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.u, ws.reg, ws.payload);
-  else k_payload_adjoint<16><<<grid, 128, 0, s>>>(p.n, p.K, means, ws.cams, cb, coeffs, ws.u, ws.reg, ws.payload);
+  const int G = payload_group(p.B, p.K, 2);
+  const unsigned grid = (unsigned)((p.n + G - 1) / G);
+  const size_t smem = 2 * (size_t)G * ((p.B * p.K) | 1) * sizeof(float);
+#define ICGS_PAYADJ(BB)                                                                              \
+  k_payload_adjoint<BB><<<grid, kPayThreads, smem, s>>>(p.n, p.K, G, means, ws.cams, cb, coeffs, ws.u, \
+                                                        ws.reg, ws.payload)
+  if (p.B == 1) ICGS_PAYADJ(1);
+  else if (p.B == 4) ICGS_PAYADJ(4);
+  else if (p.B == 9) ICGS_PAYADJ(9);
+  else ICGS_PAYADJ(16);
+#undef ICGS_PAYADJ
   note_launches(1);
 }
 
