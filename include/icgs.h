@@ -224,6 +224,33 @@ ICGS_API icgs_status icgs_colorize_host(const icgs_scene* scene, const icgs_came
                                         size_t workspace_bytes, float* coeffs_host, uint8_t* status_host,
                                         float* chol_out, void* stream);
 
+/* Camera sharding of the normal equations (Eq. 12-14). The sums over cameras split over any
+ * partition of the cameras: a caller with several GPUs (or several calls on one GPU) accumulates
+ * each subset with icgs_accumulate, adds the results elementwise (an all-reduce across GPUs), and
+ * solves once with icgs_solve. The paper has no such split; it is the same arithmetic in two steps.
+ *
+ * icgs_accumulate: the normal equations of these cameras, written as float64 device arrays
+ *   G_out [n, (L+1)^2, (L+1)^2]  sum_j V_ij Y_ij Y_ij^T (full symmetric matrix),
+ *   b_out [n, (L+1)^2, channels] sum_j Y_ij S_ij^T,
+ *   w_out [n]                    sum_j V_ij.
+ * MIXED returns its compensated sums (hi + lo) in float64; add shards in float64. Workspace:
+ * icgs_workspace_size() bytes (DEVICE, 256-byte aligned). Synchronises `stream`. */
+ICGS_API icgs_status icgs_accumulate(const icgs_scene* scene, const icgs_cameras* cams,
+                                     const icgs_targets* targets, const icgs_options* opt, void* workspace,
+                                     size_t workspace_bytes, double* G_out, double* b_out, double* w_out,
+                                     void* stream);
+
+/* icgs_solve: c_i = (G_i + w_i Lambda)^-1 b_i (Eq. 14) from float64 device sums laid out as
+ * icgs_accumulate writes them, with the precision, lambda and cond_tau of opt (scene and camera
+ * fields are not used). MIXED factorises in FP32 and refines in float-float against the sums split
+ * into (hi, lo); below cond_tau it solves in FP64. There is no exact re-fold: the per-camera sums are
+ * not available here. Outputs as for icgs_colorize (device). Workspace: icgs_solve_workspace_size()
+ * bytes (DEVICE, 256-byte aligned). Synchronises `stream`. */
+ICGS_API size_t icgs_solve_workspace_size(int64_t n, int32_t sh_degree, int32_t channels, const icgs_options* opt);
+ICGS_API icgs_status icgs_solve(int64_t n, int32_t sh_degree, int32_t channels, const double* G, const double* b,
+                                const double* w, const icgs_options* opt, void* workspace, size_t workspace_bytes,
+                                float* coeffs_out, uint8_t* status_out, float* chol_out, void* stream);
+
 /* Size in bytes of the built-in scratch icgs_colorize_noalloc works in. */
 ICGS_API size_t icgs_noalloc_scratch_bytes(void);
 

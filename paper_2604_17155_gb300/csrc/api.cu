@@ -526,6 +526,137 @@ icgs_status icgs_colorize_host(const icgs_scene* scene, const icgs_cameras* cams
   return finish(ws, s);
 }
 
+icgs_status icgs_accumulate(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
+                            const icgs_options* opt, void* workspace, size_t workspace_bytes, double* G_out,
+                            double* b_out, double* w_out, void* stream) {
+  g_err[0] = '\0';
+  if (!opt) return fail(ICGS_ERR_INVALID_ARG, "options must not be NULL");
+  icgs_status st = check_targets(targets);
+  if (st != ICGS_OK) return st;
+  Problem p;
+  st = setup(scene, cams, targets->channels, opt->sh_degree, opt->precision, opt->cond_tau, opt->refold_tau,
+             opt->cam_batch, opt->instance_capacity, p);
+  if (st != ICGS_OK) return st;
+  if ((!G_out || !b_out || !w_out) && p.n > 0) return fail(ICGS_ERR_INVALID_ARG, "G_out, b_out and w_out are required");
+  const Workspace need = carve(nullptr, p, kNeedAccumulate);
+  if (!workspace || workspace_bytes < need.total)
+    return fail(ICGS_ERR_WORKSPACE_TOO_SMALL, "workspace of %zu bytes, need %zu", workspace_bytes, need.total);
+  if (reinterpret_cast<uintptr_t>(workspace) % 256)
+    return fail(ICGS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Workspace ws = carve(static_cast<char*>(workspace), p, kNeedAccumulate);
+  if (p.n == 0) return ICGS_OK;
+  if ((st = upload_common(p, cams, nullptr, ws, s)) != ICGS_OK) return st;
+  if (p.L == 0)
+    ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)p.n * p.acc_stride, s));
+  for (int cam0 = 0; cam0 < p.n_cams; cam0 += p.cam_batch) {
+    const int cb = std::min(p.cam_batch, p.n_cams - cam0);
+    Workspace wp = ws;
+    wp.cams = ws.cams + cam0;
+    if (p.L > 0)
+      ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)cb * (size_t)p.n * p.acc_stride, s));
+    if ((st = bin_pass(p, scene, cb, tc_accumulate_applies(p, (int)targets->dtype), wp, s)) != ICGS_OK) return st;
+    launch_blend_accumulate(p, cb, cam0, targets->data, (int)targets->dtype, nullptr, wp, s);
+    g_timer.mark(kBlend, s);
+    if (p.L > 0) {
+      launch_fold(p, scene->means, cb, cam0 == 0, true, wp, s);
+      g_timer.mark(kFold, s);
+    }
+  }
+  launch_export_normal(p, ws, G_out, b_out, w_out, s);
+  return finish(ws, s);
+}
+
+namespace {
+
+// Workspace of icgs_solve: the status block, lambda and the normal equations in the layout the
+// solve kernels read (hi, lo for MIXED; for L = 0 one accumulator row per Gaussian).
+Workspace carve_solve(char* base, const Problem& p) {
+  Workspace ws;
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* ptr = base ? base + off : nullptr;
+    off += align256(bytes);
+    return ptr;
+  };
+  const size_t B = (size_t)p.B, K = (size_t)p.K, n = (size_t)p.n;
+  ws.base = base;
+  ws.status = reinterpret_cast<DevStatus*>(take(sizeof(DevStatus)));
+  ws.lam = reinterpret_cast<float*>(take(sizeof(float) * kMaxSH));
+  if (p.L == 0) {
+    ws.acc = reinterpret_cast<float*>(take(sizeof(float) * n * (size_t)p.acc_stride));
+  } else {
+    const bool mixed = p.precision == ICGS_PRECISION_MIXED;
+    ws.G = reinterpret_cast<float*>(take(sizeof(float) * n * B * B));
+    ws.bvec = reinterpret_cast<float*>(take(sizeof(float) * n * B * K));
+    ws.wsum = reinterpret_cast<float*>(take(sizeof(float) * n));
+    if (mixed) {
+      ws.Glo = reinterpret_cast<float*>(take(sizeof(float) * n * B * B));
+      ws.blo = reinterpret_cast<float*>(take(sizeof(float) * n * B * K));
+      ws.wlo = reinterpret_cast<float*>(take(sizeof(float) * n));
+    }
+  }
+  ws.total = off;
+  ws.bytes = off;
+  return ws;
+}
+
+icgs_status setup_solve(int64_t n, int32_t sh_degree, int32_t channels, const icgs_options* opt, Problem& p) {
+  if (!opt) return fail(ICGS_ERR_INVALID_ARG, "options must not be NULL");
+  if (n < 0) return fail(ICGS_ERR_INVALID_ARG, "n = %lld must be >= 0", (long long)n);
+  if (sh_degree < 0 || sh_degree > 3) return fail(ICGS_ERR_INVALID_ARG, "sh_degree = %d must be in 0..3", sh_degree);
+  if (channels < 1) return fail(ICGS_ERR_INVALID_ARG, "channels = %d must be >= 1", channels);
+  if (opt->precision != ICGS_PRECISION_PLAIN && opt->precision != ICGS_PRECISION_MIXED)
+    return fail(ICGS_ERR_INVALID_ARG, "precision = %d is not an icgs_precision", opt->precision);
+  p = Problem();
+  p.n = n;
+  p.L = sh_degree;
+  p.B = (sh_degree + 1) * (sh_degree + 1);
+  p.K = channels;
+  p.acc_stride = (1 + channels + 3) & ~3;
+  p.precision = opt->precision;
+  p.cond_tau = opt->cond_tau > 0.0f ? opt->cond_tau : 1e-3f;
+  return ICGS_OK;
+}
+
+}  // namespace
+
+size_t icgs_solve_workspace_size(int64_t n, int32_t sh_degree, int32_t channels, const icgs_options* opt) {
+  Problem p;
+  if (setup_solve(n, sh_degree, channels, opt, p) != ICGS_OK) return 0;
+  return carve_solve(nullptr, p).total;
+}
+
+icgs_status icgs_solve(int64_t n, int32_t sh_degree, int32_t channels, const double* G, const double* b,
+                       const double* w, const icgs_options* opt, void* workspace, size_t workspace_bytes,
+                       float* coeffs_out, uint8_t* status_out, float* chol_out, void* stream) {
+  g_err[0] = '\0';
+  Problem p;
+  icgs_status st = setup_solve(n, sh_degree, channels, opt, p);
+  if (st != ICGS_OK) return st;
+  if (p.n > 0 && (!G || !b || !w || !coeffs_out))
+    return fail(ICGS_ERR_INVALID_ARG, "G, b, w and coeffs_out are required");
+  float lam[kMaxSH];
+  if ((st = lambda_of(opt, p.L, lam)) != ICGS_OK) return st;
+  const Workspace need = carve_solve(nullptr, p);
+  if (!workspace || workspace_bytes < need.total)
+    return fail(ICGS_ERR_WORKSPACE_TOO_SMALL, "workspace of %zu bytes, need %zu", workspace_bytes, need.total);
+  if (reinterpret_cast<uintptr_t>(workspace) % 256)
+    return fail(ICGS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Workspace ws = carve_solve(static_cast<char*>(workspace), p);
+  if (p.n == 0) return ICGS_OK;
+  g_launches = 0;
+  ICGS_TRY_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(DevStatus), s));
+  ICGS_TRY_CUDA(cudaMemcpyAsync(ws.lam, lam, sizeof(float) * p.B, cudaMemcpyHostToDevice, s));
+  g_timer.begin(s);
+  launch_import_normal(p, ws, G, b, w, s);
+  // the per-camera sums are not available here: no exact re-fold, FP64 below cond_tau
+  launch_solve(p, ws.lam, lam, ws, coeffs_out, status_out, chol_out, nullptr, 0, s);
+  g_timer.mark(kSolve, s);
+  return finish(ws, s);
+}
+
 icgs_status icgs_colorize_backward(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
                                    const icgs_options* opt, const float* coeffs, const float* chol,
                                    const float* grad_coeffs, void* workspace, size_t workspace_bytes,

@@ -128,6 +128,10 @@ void launch_refine_update(const Problem& p, const float* lam_dev, const float* l
 void launch_solve(const Problem& p, const float* lam_dev, const float* lam_host, const Workspace& ws,
                   float* coeffs, uint8_t* status, float* chol, const float* means, int n_acc_cams,
                   cudaStream_t s);
+// The normal equations of the current workspace as double (hi + lo), and back (camera sharding).
+void launch_export_normal(const Problem& p, const Workspace& ws, double* G, double* b, double* w, cudaStream_t s);
+void launch_import_normal(const Problem& p, const Workspace& ws, const double* G, const double* b, const double* w,
+                          cudaStream_t s);
 void launch_payload_render(const Problem& p, const float* means, const float* coeffs, int cb,
                            const Workspace& ws, cudaStream_t s);
 void launch_blend_render(const Problem& p, int cb, int cam0, const Workspace& ws, float* images,

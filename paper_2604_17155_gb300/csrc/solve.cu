@@ -427,10 +427,18 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(
   float wl = 0.0f;
   bool refold = false;
   float rb_h[4] = {0.0f, 0.0f, 0.0f, 0.0f}, rb_l[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // re-fold: b, channels 0-3
-  const float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
+  // the mean is read only by the exact re-fold, which needs the resident per-camera sums (callers
+  // without them pass no means)
+  const bool have_sums = n_acc_cams > 0 && means != nullptr;
+  float mu[3] = {0.0f, 0.0f, 0.0f};
+  if (have_sums) {
+    mu[0] = means[3 * i];
+    mu[1] = means[3 * i + 1];
+    mu[2] = means[3 * i + 2];
+  }
   const int64_t cam_stride = n * (int64_t)RS;
   if constexpr (MIXED) {
-    refold = n_acc_cams > 0 && !(minratio >= refold_tau);
+    refold = have_sums && !(minratio >= refold_tau);
     if (refold) {
 #pragma unroll
       for (int c = 0; c < B; ++c) { ghi[c] = 0.0f; glo[c] = 0.0f; }
@@ -805,6 +813,109 @@ void launch_fold(const Problem& p, const float* means, int cb, bool first, bool 
   else if (p.B == 9) { ICGS_FOLD(9); }
   else { ICGS_FOLD(16); }
 #undef ICGS_FOLD
+}
+
+// ------------------------------------------------------------------------------------------
+// normal equations in and out (camera sharding): the sums of Eq. 12-14 as double, hi + lo
+// ------------------------------------------------------------------------------------------
+namespace {
+
+constexpr double kY0d = 0.28209479177387814;
+
+__global__ void k_export_normal(int64_t nG, int64_t nb, int64_t n, const float* __restrict__ G,
+                                const float* __restrict__ Glo, const float* __restrict__ b,
+                                const float* __restrict__ blo, const float* __restrict__ w,
+                                const float* __restrict__ wlo, double* __restrict__ Gd, double* __restrict__ bd,
+                                double* __restrict__ wd) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nG + nb + n; e += stride) {
+    if (e < nG) Gd[e] = (double)G[e] + (Glo ? (double)Glo[e] : 0.0);
+    else if (e < nG + nb) bd[e - nG] = (double)b[e - nG] + (blo ? (double)blo[e - nG] : 0.0);
+    else wd[e - nG - nb] = (double)w[e - nG - nb] + (wlo ? (double)wlo[e - nG - nb] : 0.0);
+  }
+}
+
+// L = 0: acc[i] = (V, S_0..S_{K-1}) gives G = Y0^2 V, b = Y0 S, w = V
+__global__ void k_export_normal_l0(int64_t n, int K, int RS, const float* __restrict__ acc, double* __restrict__ Gd,
+                                   double* __restrict__ bd, double* __restrict__ wd) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * (int64_t)(K + 1)) return;
+  const int64_t i = e / (K + 1);
+  const int k = (int)(e - i * (K + 1));
+  const double V = (double)acc[i * RS];
+  if (k == K) {
+    Gd[i] = kY0d * kY0d * V;
+    wd[i] = V;
+  } else {
+    bd[i * K + k] = kY0d * (double)acc[i * RS + 1 + k];
+  }
+}
+
+__device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+
+__global__ void k_import_normal(int64_t nG, int64_t nb, int64_t n, const double* __restrict__ Gd,
+                                const double* __restrict__ bd, const double* __restrict__ wd, float* __restrict__ G,
+                                float* __restrict__ Glo, float* __restrict__ b, float* __restrict__ blo,
+                                float* __restrict__ w, float* __restrict__ wlo) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nG + nb + n; e += stride) {
+    float hi, lo;
+    if (e < nG) {
+      split_double(Gd[e], hi, lo);
+      G[e] = hi;
+      if (Glo) Glo[e] = lo;
+    } else if (e < nG + nb) {
+      split_double(bd[e - nG], hi, lo);
+      b[e - nG] = hi;
+      if (blo) blo[e - nG] = lo;
+    } else {
+      split_double(wd[e - nG - nb], hi, lo);
+      w[e - nG - nb] = hi;
+      if (wlo) wlo[e - nG - nb] = lo;
+    }
+  }
+}
+
+// L = 0: back to acc[i] = (V, S) with V = w, S = b / Y0
+__global__ void k_import_normal_l0(int64_t n, int K, int RS, const double* __restrict__ bd,
+                                   const double* __restrict__ wd, float* __restrict__ acc) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * (int64_t)(K + 1)) return;
+  const int64_t i = e / (K + 1);
+  const int k = (int)(e - i * (K + 1));
+  if (k == K) acc[i * RS] = (float)wd[i];
+  else acc[i * RS + 1 + k] = (float)(bd[i * K + k] / kY0d);
+}
+
+}  // namespace
+
+void launch_export_normal(const Problem& p, const Workspace& ws, double* G, double* b, double* w, cudaStream_t s) {
+  if (p.B == 1) {
+    const int64_t m = p.n * (int64_t)(p.K + 1);
+    k_export_normal_l0<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(p.n, p.K, p.acc_stride, ws.acc, G, b, w);
+  } else {
+    const bool mixed = p.precision == 1;
+    k_export_normal<<<1216, 256, 0, s>>>(p.n * p.B * p.B, p.n * p.B * p.K, p.n, ws.G, mixed ? ws.Glo : nullptr,
+                                         ws.bvec, mixed ? ws.blo : nullptr, ws.wsum, mixed ? ws.wlo : nullptr, G, b, w);
+  }
+  note_launches(1);
+}
+
+void launch_import_normal(const Problem& p, const Workspace& ws, const double* G, const double* b, const double* w,
+                          cudaStream_t s) {
+  if (p.B == 1) {
+    const int64_t m = p.n * (int64_t)(p.K + 1);
+    k_import_normal_l0<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(p.n, p.K, p.acc_stride, b, w, ws.acc);
+  } else {
+    const bool mixed = p.precision == 1;
+    k_import_normal<<<1216, 256, 0, s>>>(p.n * p.B * p.B, p.n * p.B * p.K, p.n, G, b, w, ws.G,
+                                         mixed ? ws.Glo : nullptr, ws.bvec, mixed ? ws.blo : nullptr, ws.wsum,
+                                         mixed ? ws.wlo : nullptr);
+  }
+  note_launches(1);
 }
 
 void launch_solve(const Problem& p, const float* lam_dev, const float* lam_host, const Workspace& ws,

@@ -96,6 +96,12 @@ def load(path: str = LIB_PATH):
     lib.icgs_colorize_host_workspace_size.restype = S
     lib.icgs_colorize_host.argtypes = [P, P, P, P, P, S, P, P, P, P]
     lib.icgs_colorize_host.restype = ctypes.c_int
+    lib.icgs_accumulate.argtypes = [P, P, P, P, P, S, P, P, P, P]
+    lib.icgs_accumulate.restype = ctypes.c_int
+    lib.icgs_solve_workspace_size.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P]
+    lib.icgs_solve_workspace_size.restype = S
+    lib.icgs_solve.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, S, P, P, P, P]
+    lib.icgs_solve.restype = ctypes.c_int
     lib.icgs_selftest_tc.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, P, P, P]
     lib.icgs_selftest_tc.restype = ctypes.c_int
     lib.icgs_set_stage_timing.argtypes = [ctypes.c_int]
@@ -188,6 +194,11 @@ class Cameras:
     @property
     def n(self):
         return int(self.intrinsics.shape[0])
+
+    def subset(self, idx):
+        """The cameras at the given indices, in that order."""
+        idx = np.asarray(idx, np.int64)
+        return Cameras(self.width, self.height, self.intrinsics[idx], self.world_to_cam[idx], self.near_z)
 
     def _struct(self):
         return _Cameras(self.n, self.width, self.height, self.near_z,
@@ -334,6 +345,91 @@ def colorize_host(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, pre
 
     _run_with_capacity(dev, size_fn, call_fn, instance_capacity)
     return coeffs, status
+
+
+def accumulate(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, precision="mixed", cam_batch=0,
+               instance_capacity=0, opacity=None):
+    """icgs_accumulate: the normal equations of these cameras (Eq. 12-14) as float64 device tensors
+    G [n,B,B], b [n,B,K], w [n] (B = (L+1)^2). Sums over disjoint camera subsets add up to the sums
+    over their union."""
+    torch = _torch()
+    lib = load()
+    dev = targets.device
+    B = (sh_degree + 1) ** 2
+    K = int(targets.shape[-1])
+    G = torch.empty((scene.n, B, B), dtype=torch.float64, device=dev)
+    b = torch.empty((scene.n, B, K), dtype=torch.float64, device=dev)
+    w = torch.empty((scene.n,), dtype=torch.float64, device=dev)
+    sc = scene._struct(opacity)
+    cm = cams._struct()
+    tg = _targets_struct(targets)
+
+    def size_fn(cap):
+        o, _keep = _options(sh_degree, lam, precision, 0.0, cam_batch, cap)
+        return lib.icgs_workspace_size(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(o))
+
+    def call_fn(ptr, nbytes, cap):
+        o, _keep = _options(sh_degree, lam, precision, 0.0, cam_batch, cap)
+        return lib.icgs_accumulate(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(o),
+                                   ctypes.c_void_p(ptr), nbytes, ctypes.c_void_p(G.data_ptr()),
+                                   ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(w.data_ptr()), _stream_ptr(dev))
+
+    _run_with_capacity(dev, size_fn, call_fn, instance_capacity)
+    return G, b, w
+
+
+def solve(G, b, w, sh_degree, lam=None, precision="mixed", cond_tau=0.0):
+    """icgs_solve: coefficients [n,B,K] float32, status [n] uint8 and Cholesky factors from float64
+    device sums G [n,B,B], b [n,B,K], w [n] (as accumulate() returns them, or their sum over
+    camera subsets)."""
+    torch = _torch()
+    lib = load()
+    dev = G.device
+    n = int(w.shape[0])
+    B = (sh_degree + 1) ** 2
+    K = int(b.shape[-1])
+    for x, shape in ((G, (n, B, B)), (b, (n, B, K)), (w, (n,))):
+        if x.dtype != torch.float64 or not x.is_cuda or not x.is_contiguous() or tuple(x.shape) != shape:
+            raise ValueError(f"expected a contiguous float64 CUDA tensor of shape {shape}")
+    coeffs = torch.empty((n, B, K), dtype=torch.float32, device=dev)
+    status = torch.empty((n,), dtype=torch.uint8, device=dev)
+    chol = torch.empty((n, B * (B + 1) // 2), dtype=torch.float32, device=dev)
+    o, _keep = _options(sh_degree, lam, precision, cond_tau, 0, 0)
+    nbytes = lib.icgs_solve_workspace_size(n, sh_degree, K, ctypes.byref(o))
+    if nbytes == 0:
+        _check(ERR_INVALID_ARG)
+    ws = _ws.get(dev, nbytes)
+    _check(lib.icgs_solve(n, sh_degree, K, ctypes.c_void_p(G.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                          ctypes.c_void_p(w.data_ptr()), ctypes.byref(o), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                          ctypes.c_void_p(coeffs.data_ptr()), ctypes.c_void_p(status.data_ptr()),
+                          ctypes.c_void_p(chol.data_ptr()), _stream_ptr(dev)))
+    return coeffs, status, chol
+
+
+def shard_cameras(n_cams, rank, world):
+    """The camera indices of one rank in a round-robin partition of n_cams cameras."""
+    return np.arange(rank, n_cams, world)
+
+
+def colorize_sharded(scene, cams, targets, sh_degree, rank, world, group=None, lam=None, precision="mixed",
+                     accumulate_fn=None, solve_fn=None):
+    """Camera-sharded colorize: this rank accumulates the normal equations of its round-robin share
+    of the cameras, the ranks sum them (one torch.distributed all-reduce each of G, b and w; NCCL
+    for GPU tensors), and every rank solves. targets holds all cameras' images; only this rank's
+    slice is read. accumulate_fn(scene, cams_subset, targets_subset, sh_degree, lam, precision) ->
+    (G, b, w) and solve_fn(G, b, w, sh_degree, lam, precision) -> result default to accumulate()
+    and solve()."""
+    import torch.distributed as dist
+    accumulate_fn = accumulate_fn or (lambda sc, cm, t, L, lm, pr: accumulate(sc, cm, t, L, lam=lm, precision=pr))
+    solve_fn = solve_fn or (lambda G, b, w, L, lm, pr: solve(G, b, w, L, lam=lm, precision=pr))
+    mine = shard_cameras(cams.n, rank, world)
+    idx = _torch().as_tensor(mine, device=targets.device)
+    G, b, w = accumulate_fn(scene, cams.subset(mine), targets.index_select(0, idx).contiguous(), sh_degree, lam,
+                            precision)
+    if world > 1:
+        for x in (G, b, w):
+            dist.all_reduce(x, op=dist.ReduceOp.SUM, group=group)
+    return solve_fn(G, b, w, sh_degree, lam, precision)
 
 
 def colorize_noalloc(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, precision="mixed",

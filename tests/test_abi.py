@@ -21,7 +21,7 @@ def test_header_declares_the_calls():
                  "icgs_render", "icgs_last_error", "icgs_last_required_instances", "icgs_last_stats",
                  "icgs_colorize_noalloc", "icgs_noalloc_scratch_bytes", "icgs_selftest_tc",
                  "icgs_refine_workspace_size", "icgs_colorize_refine", "icgs_colorize_host_workspace_size",
-                 "icgs_colorize_host"]:
+                 "icgs_colorize_host", "icgs_accumulate", "icgs_solve_workspace_size", "icgs_solve"]:
         assert want in names
 
 
@@ -65,6 +65,27 @@ def test_host_workspace_adds_the_staging_regions(lib):
                                                    ctypes.byref(opt))
     assert host32 - host16 == a(n_cams * h * w * K * 4) - a(n_cams * h * w * K * 2)
     assert host32 > a(n_cams * h * w * K * 4) + a(n * 16 * K * 4) + a(n)
+
+
+def test_solve_workspace_and_arguments(lib):
+    """icgs_solve's workspace holds the status block, lambda and the (hi, lo) normal equations;
+    bad arguments are refused before any device work."""
+    sc, cm, tg, opt, keep = _structs()
+    a = lambda x: (x + 255) // 256 * 256
+    n, K = 1000, 3
+    mixed = lib.icgs_solve_workspace_size(n, 3, K, ctypes.byref(opt))
+    assert mixed >= 2 * (a(n * 256 * 4) + a(n * 16 * K * 4) + a(n * 4))
+    opt.precision = icgs.PLAIN
+    plain = lib.icgs_solve_workspace_size(n, 3, K, ctypes.byref(opt))
+    assert plain < mixed
+    opt.precision = icgs.MIXED
+    assert lib.icgs_solve_workspace_size(n, 4, K, ctypes.byref(opt)) == 0  # sh_degree 4
+    assert lib.icgs_solve_workspace_size(n, 3, 0, ctypes.byref(opt)) == 0  # no channels
+    st = lib.icgs_solve(n, 3, K, None, None, None, ctypes.byref(opt), None, 0, None, None, None, None)
+    assert st == icgs.ERR_INVALID_ARG and "required" in lib.icgs_last_error().decode()
+    st = lib.icgs_solve(n, 3, K, ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.byref(opt),
+                        None, 0, ctypes.c_void_p(16), None, None, None)
+    assert st == icgs.ERR_WORKSPACE_TOO_SMALL
 
 
 def test_bad_arguments_rejected_on_host(lib):

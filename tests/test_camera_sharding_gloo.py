@@ -60,3 +60,49 @@ def test_two_rank_camera_shards_reproduce_single_process(tmp_path):
     assert seen.sum() > 30
     err = O.relative_errors(c_sharded[seen], ref[seen])
     assert err.max() < 1e-10
+
+
+def _oracle_accumulate(sc, cams, t, L, lam, precision):
+    V, S, _, _, _ = O.accumulate(sc, cams, t.numpy(), threads=1)
+    G, b, w = O.fold(V, S, O.view_basis(sc, cams, L))
+    return tuple(torch.from_numpy(np.ascontiguousarray(x)) for x in (G, b, w))
+
+
+def _oracle_solve(G, b, w, L, lam, precision):
+    c, status, _ = O.solve(G.numpy(), b.numpy(), w.numpy(), O.paper_lambda(L) if lam is None else np.asarray(lam))
+    return c
+
+
+def _rank_sharded(rank, world, port, out_path):
+    """The library's colorize_sharded (camera partition, all-reduce of G, b, w, solve) with the
+    oracle standing in for the GPU accumulate and solve."""
+    from paper_2604_17155_gb300 import icgs
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        sc, cams, t = _problem()
+        c = icgs.colorize_sharded(sc, cams, torch.from_numpy(t), 3, rank, world,
+                                  accumulate_fn=_oracle_accumulate, solve_fn=_oracle_solve)
+        np.save(out_path.replace(".npy", f"_{rank}.npy"), c)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_colorize_sharded_host_logic_two_ranks(tmp_path):
+    out = str(tmp_path / "c.npy")
+    mp.start_processes(_rank_sharded, args=(2, _free_port(), out), nprocs=2, join=True, start_method="spawn")
+    sc, cams, t = _problem()
+    ref = O.colorize(sc, cams, t, 3)["c"]
+    seen = np.abs(ref).reshape(ref.shape[0], -1).max(1) > 0
+    for rank in range(2):
+        c = np.load(out.replace(".npy", f"_{rank}.npy"))
+        assert O.relative_errors(c[seen], ref[seen]).max() < 1e-10
+
+
+def test_shard_partition_covers_every_camera_once():
+    from paper_2604_17155_gb300 import icgs
+    for n_cams, world in ((10, 2), (7, 3), (3, 4), (100, 8)):
+        parts = [icgs.shard_cameras(n_cams, r, world) for r in range(world)]
+        allc = np.sort(np.concatenate(parts))
+        assert np.array_equal(allc, np.arange(n_cams))
