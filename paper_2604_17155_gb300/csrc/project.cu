@@ -89,7 +89,7 @@ __device__ __forceinline__ int4 project_pair(const float* __restrict__ means, co
   const float mx3 = means[3 * i], my3 = means[3 * i + 1], mz3 = means[3 * i + 2];
   const float o = opac[i];
   const double zd = depth_f64(c, mx3, my3, mz3);
-  if (!(zd > (double)near_z) || !(__dmul_rn((double)o, 255.0) >= 1.0)) {
+  if (!(zd > (double)near_z) || !isfinite(zd) || !(__dmul_rn((double)o, 255.0) >= 1.0) || !isfinite(o)) {
     rect[ji] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
     return none;
   }
@@ -101,6 +101,12 @@ __device__ __forceinline__ int4 project_pair(const float* __restrict__ means, co
   const float iz = 1.0f / tz;
   const float qthr = 2.0f * logf(255.0f * o);
   const float sx = scales[3 * i], sy = scales[3 * i + 1], sz = scales[3 * i + 2];
+  // a non-finite scale would give an unbounded support (NaN and zero quaternions fail the
+  // determinant test below)
+  if (!(isfinite(sx) && isfinite(sy) && isfinite(sz))) {
+    rect[ji] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+    return none;
+  }
   {
     // Early cull. Sigma'_xx = |T_0 M|^2 + 0.3 <= |J_0|^2 |R|^2 s_max^2 + 0.3 with
     // |J_0| <= (f/z) sqrt(1 + lim^2) (the Jacobian's clamp), so the support half-width is at most

@@ -236,6 +236,37 @@ def test_degenerate_inputs(icgs):
     assert O.relative_errors(to_np(c), col["c"])[0] <= TOL_FP32
 
 
+def test_nonfinite_gaussians_are_dropped(icgs):
+    """Gaussians with NaN or infinite parameters (mean, scale, quaternion, opacity) or a zero
+    quaternion contribute nothing: they come back UNSEEN with zero coefficients, and every other
+    Gaussian matches the oracle run on the scene without them."""
+    sc, cams = _mid_scene(n=2000, seed=121, n_cams=8, w=80, h=60)
+    rng = np.random.default_rng(122)
+    bad = np.sort(rng.choice(sc.n, 60, replace=False))
+    means, scales, quats, opac = (x.copy() for x in (sc.means, sc.scales, sc.quats, sc.opacity))
+    kinds = np.arange(len(bad)) % 6
+    means[bad[kinds == 0], 1] = np.nan
+    scales[bad[kinds == 1], 0] = np.inf
+    quats[bad[kinds == 2]] = np.nan
+    quats[bad[kinds == 3]] = 0.0
+    opac[bad[kinds == 4]] = np.nan
+    means[bad[kinds == 5], 2] = np.inf
+    corrupt = W.Scene(means, scales, quats, opac)
+    good = np.setdiff1d(np.arange(sc.n), bad)
+    L = 3
+    t = O.render(sc.subset(good), cams, W.sh_coefficients(len(good), L, 3, seed=123), L).astype(np.float32)
+    col = O.colorize(sc.subset(good), cams, t.astype(np.float64), L)
+    gs, gc = _gpu(icgs, corrupt, cams)
+    c, status, chol = icgs.colorize(gs, gc, torch.tensor(t, device=DEV), L)
+    c, status = to_np(c), to_np(status)
+    assert np.isfinite(c).all()
+    assert (status[bad] == icgs.GAUSSIAN_UNSEEN).all() and (c[bad] == 0).all()
+    rep, err, checked = coefficient_report(c[good], col, tol=TOL_FP32)
+    print("non-finite dropped", rep)
+    assert rep["max_checked"] <= TOL_FP32
+    assert rep["bound_excess"] <= 0
+
+
 def test_adjoint_matches_oracle(icgs):
     sc, cams = _mid_scene(n=1500, seed=61, n_cams=8, w=64, h=48)
     L = 3
