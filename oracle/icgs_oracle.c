@@ -22,9 +22,10 @@
  * oracle.py.
  *
  * Decisions that must be taken identically on both sides are taken in a fixed precision here:
- * the depth used for ordering is the float32 rounding of the camera-space z evaluated in double
- * as ((W20 x + W21 y) + W22 z) + W23 with no fused multiply-add (this file must be compiled with
- * -ffp-contract=off); ties are broken by the Gaussian index. Threshold decisions on alpha and T
+ * the depth used for ordering (and for the near-plane test) is the float32 key
+ * fma(W22, z, fma(W21, y, fma(W20, x, W23))), each step one correctly rounded fused multiply-add
+ * in float32 (C99 fmaf); ties are broken by the Gaussian index. Everything else here is double
+ * with no contraction (compile with -ffp-contract=off). Threshold decisions on alpha and T
  * are taken in double; each one that falls within a relative margin `delta` of its threshold adds
  * the weight it decides to a per-Gaussian "stake", so a test can tell a threshold flip from an
  * arithmetic error.
@@ -51,7 +52,7 @@ typedef struct {
   double cxx, cxy, cyy;      /* 2D covariance incl. dilation */
   double ca, cb, cc;         /* conic = inverse 2D covariance */
   double depth;              /* camera-space z */
-  float key;                 /* float32 rounding of depth: the ordering key */
+  float key;                 /* float32 depth key (fused multiply-adds): the ordering key */
   double opacity;
   double qthr;               /* 2 ln(255 o): alpha >= 1/255 <=> q <= qthr (ignoring the 0.99 cap) */
   int32_t x0, x1, y0, y1;    /* candidate pixel box, inclusive */
@@ -81,10 +82,12 @@ static void project_one(const float* mean, const float* scale, const float* quat
   double tx = ((W[0] * x + W[1] * y) + W[2] * z) + W[3];
   double ty = ((W[4] * x + W[5] * y) + W[6] * z) + W[7];
   double tz = ((W[8] * x + W[9] * y) + W[10] * z) + W[11];
+  /* the ordering key: three float32 fused multiply-adds (W holds float32 values exactly) */
+  const float key = fmaf((float)W[10], mean[2], fmaf((float)W[9], mean[1], fmaf((float)W[8], mean[0], (float)W[11])));
   p->depth = tz;
-  p->key = (float)tz;
+  p->key = key;
   p->opacity = opac;
-  if (!(tz > c->near_z)) return;                 /* behind the near plane */
+  if (!(key > (float)c->near_z)) return;         /* behind the near plane (on the key) */
   if (!((double)opac * 255.0 >= 1.0)) return;    /* alpha < 1/255 everywhere */
 
   /* 3D covariance Sigma = R S S^T R^T */

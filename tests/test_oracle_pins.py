@@ -4,6 +4,8 @@ differences of the pinhole projection, brute force, dense QR least squares, and 
 the least-squares problem (Sec. 3, Eq. 2-15). These run on the CPU only."""
 import math
 
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
@@ -191,6 +193,41 @@ def test_projection_clamps_jacobian_outside_guard_band():
     for k in ("cov_xx", "cov_xy", "cov_yy"):  # equal up to the float32 rounding of the position
         np.testing.assert_allclose(p[k][0], p2[k][0], rtol=1e-6)
     np.testing.assert_allclose(p["mx"][0], f * float(np.float32(x)) / Z + 16.0, rtol=1e-12)
+
+
+def _round_f32(q):
+    """The float32 nearest to the rational q (ties to even), by exact comparison of neighbours."""
+    if q == 0:
+        return 0.0
+    a = np.float32(float(q))
+    cands = [np.nextafter(a, np.float32(-np.inf)), a, np.nextafter(a, np.float32(np.inf))]
+    return float(min(cands, key=lambda f: (abs(Fraction(float(f)) - q), int(np.float32(f).view(np.uint32)) & 1)))
+
+
+def test_depth_key_is_the_float32_fma_chain():
+    """The ordering key is fma(W22, z, fma(W21, y, fma(W20, x, W23))) in float32, each fused
+    multiply-add rounded once: checked against exact rational arithmetic, on rotated cameras."""
+    rng = np.random.default_rng(11)
+    for trial in range(4):
+        q = rng.standard_normal(4)
+        q /= np.linalg.norm(q)
+        w, x, y, z = q
+        R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                      [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                      [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+        t = rng.uniform(-1, 1, 3) + [0, 0, 6.0]
+        w2c = np.concatenate([R, t[:, None]], 1).astype(np.float32)[None]
+        cams = W.Cameras(64, 64, np.array([60.0], np.float32), np.array([60.0], np.float32),
+                         np.array([32.0], np.float32), np.array([32.0], np.float32), w2c)
+        sc = W.uniform_scene(200, 12 + trial, box=1.5)
+        key = O.project(sc, cams, 0)["key"]
+        Wf = [float(v) for v in w2c[0].reshape(-1)]
+        for i in range(sc.n):
+            mx, my, mz = (float(v) for v in sc.means[i])
+            k = _round_f32(Fraction(Wf[8]) * Fraction(mx) + Fraction(Wf[11]))
+            k = _round_f32(Fraction(Wf[9]) * Fraction(my) + Fraction(k))
+            k = _round_f32(Fraction(Wf[10]) * Fraction(mz) + Fraction(k))
+            assert key[i] == k, (trial, i, key[i], k)
 
 
 def test_near_plane_and_opacity_culling():
