@@ -202,6 +202,131 @@ __global__ void __launch_bounds__(kThreads, KC <= 3 ? 8 : (KC <= 8 ? 5 : 4)) k_b
   if (k0 == 0) add_pair_count(npairs, status);
 }
 
+// The same accumulation for up to 3 channels with two pixels per thread: CTAs of 128 threads, each
+// warp covering an 8x8 block. A hit's fixed costs (the ballot loop, the shared loads, the vote, the
+// warp reduction and the shared atomic) are shared by 64 pixels instead of 32: each thread adds its
+// two pixels' contributions before the reduction. The pixels of a thread are walked independently
+// (own transmittance, own stop), in the same depth order, through the same blend_step().
+constexpr int kThreads2 = kThreads / 2;
+
+template <int KC>
+__global__ void __launch_bounds__(kThreads2, 12) k_blend_accumulate2(
+    const uint32_t* __restrict__ tile_off, const uint64_t* __restrict__ entries, uint32_t capacity,
+    const ProjRec* __restrict__ rec, int64_t n, int width, int height, int tiles_x, int tiles,
+    const void* __restrict__ targets, int dtype, int K, int k0, int cam0, const float* __restrict__ sub_img,
+    float* __restrict__ acc, int RS, int64_t acc_cam_stride, DevStatus* status) {
+  static_assert(KC <= 3, "two pixels per thread: up to 3 channels");
+  constexpr int NV = KC + 1;
+  constexpr int NP = NextPow2<NV>::value;
+  constexpr int NP2 = 2 * NP;                     // two hits per reduction
+  constexpr int SHIFT2 = 5 - Log2<NP2>::value;
+  __shared__ float4 s_geo[kBatch], s_aux[kBatch];
+  __shared__ float2 s_half[kBatch];
+  __shared__ uint32_t s_id[kBatch];
+  __shared__ float s_acc[kBatch][NV];
+  __shared__ unsigned long long s_keys[kWalkSortCap];
+  const TileCtx c = tile_ctx<2>(tile_off, capacity, tiles, tiles_x, width, height);
+  const unsigned long long* list = stage_tile_list<kThreads2>(entries, c.b, c.len, s_keys);
+  const int lane = threadIdx.x & 31;
+  const bool inside1 = c.inside && c.py + 4 < height;
+  const float pyf1 = c.pyf + 4.0f;
+  float tv0[KC], tv1[KC];
+#pragma unroll
+  for (int k = 0; k < KC; ++k) tv0[k] = tv1[k] = 0.0f;
+  const int64_t row = (int64_t)width * K;
+  if (c.inside) {
+    const int64_t base = (((int64_t)(cam0 + c.j) * height + c.py) * width + c.px) * K + k0;
+    const int64_t ib = (((int64_t)c.j * height + c.py) * width + c.px) * K + k0;
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      if (k0 + k < K) {
+        tv0[k] = load_target(targets, base + k, dtype);
+        if (sub_img) tv0[k] -= sub_img[ib + k];  // refinement: residual targets t - img
+        if (inside1) {
+          tv1[k] = load_target(targets, base + 4 * row + k, dtype);
+          if (sub_img) tv1[k] -= sub_img[ib + 4 * row + k];
+        }
+      }
+    }
+  }
+  for (int k = threadIdx.x; k < kBatch * NV; k += kThreads2) (&s_acc[0][0])[k] = 0.0f;
+  const ProjRec* rec_cam = rec + (int64_t)c.j * n;
+  float* acc_cam = acc + (int64_t)c.j * acc_cam_stride;
+  float T0 = 1.0f, T1 = 1.0f;
+  bool done0 = !c.inside, done1 = !inside1;
+  uint32_t npairs = 0;
+  for (uint32_t start = 0; start < c.len; start += kBatch) {
+    const int nb = (int)min((uint32_t)kBatch, c.len - start);
+    __syncthreads();
+    load_batch(list, start, nb, rec_cam, n, c.ox, c.oy, s_geo, s_aux, s_half, s_id);
+    __syncthreads();
+    if (!__all_sync(kFull, done0 && done1)) {
+#pragma unroll
+      for (int half = 0; half < kBatch / 32; ++half) {
+        uint32_t bits = warp_hit_bits(s_geo, s_half, half * 32, nb, c);
+        while (bits) {
+          const int g1 = half * 32 + __ffs(bits) - 1;
+          bits &= bits - 1;
+          const int g2 = bits ? half * 32 + __ffs(bits) - 1 : -1;
+          bits &= bits - 1;
+          float w10 = 0.0f, w11 = 0.0f, w20 = 0.0f, w21 = 0.0f, al, ex;
+          bool cap;
+          {
+            const float4 geo = s_geo[g1], aux = s_aux[g1];
+            if (!done0) w10 = blend_step(geo, aux, c.pxf, c.pyf, T0, done0, al, ex, cap);
+            if (!done1) w11 = blend_step(geo, aux, c.pxf, pyf1, T1, done1, al, ex, cap);
+          }
+          if (g2 >= 0) {
+            const float4 geo = s_geo[g2], aux = s_aux[g2];
+            if (!done0) w20 = blend_step(geo, aux, c.pxf, c.pyf, T0, done0, al, ex, cap);
+            if (!done1) w21 = blend_step(geo, aux, c.pxf, pyf1, T1, done1, al, ex, cap);
+          }
+          const float w1 = __fadd_rn(w10, w11), w2 = __fadd_rn(w20, w21);
+          if (__any_sync(kFull, w1 > 0.0f || w2 > 0.0f)) {
+            npairs += (w10 > 0.0f) + (w11 > 0.0f) + (w20 > 0.0f) + (w21 > 0.0f);
+            float v[NP2];
+            v[0] = w1;
+            v[NP] = w2;
+#pragma unroll
+            for (int k = 0; k < KC; ++k) {
+              v[k + 1] = __fmaf_rn(w10, tv0[k], __fmul_rn(w11, tv1[k]));
+              v[NP + k + 1] = __fmaf_rn(w20, tv0[k], __fmul_rn(w21, tv1[k]));
+            }
+#pragma unroll
+            for (int k = NV; k < NP; ++k) {
+              v[k] = 0.0f;
+              v[NP + k] = 0.0f;
+            }
+            const float r = warp_transpose_reduce<NP2>(v, lane);
+            const int vi = lane >> SHIFT2, vk = vi & (NP - 1);
+            const int gg = vi < NP ? g1 : g2;
+            if ((lane & ((1 << SHIFT2) - 1)) == 0 && vk < NV && gg >= 0) atomicAdd(&s_acc[gg][vk], r);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nb) {
+      const int g = threadIdx.x;
+      if (s_acc[g][0] > 0.0f) {
+        float* dst = acc_cam + (int64_t)s_id[g] * RS;
+        if (KC == 3 && K == 3) {
+          atomicAdd(reinterpret_cast<float4*>(dst), make_float4(s_acc[g][0], s_acc[g][1], s_acc[g][2], s_acc[g][3]));
+        } else {
+          if (k0 == 0) atomicAdd(dst, s_acc[g][0]);
+#pragma unroll
+          for (int k = 0; k < KC; ++k)
+            if (k0 + k < K) atomicAdd(dst + 1 + k0 + k, s_acc[g][k + 1]);
+        }
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s_acc[g][k] = 0.0f;
+      }
+    }
+    if (__syncthreads_and(done0 && done1)) break;
+  }
+  if (k0 == 0) add_pair_count(npairs, status);
+}
+
 // ------------------------------------------------------------------------------------------
 // render: img = sum w C
 // ------------------------------------------------------------------------------------------
@@ -414,6 +539,14 @@ template <int KC>
 void accumulate_chunk(const Problem& p, int cb, int cam0, const void* targets, int dtype, int k0,
                       const float* sub_img, const Workspace& ws, cudaStream_t s) {
   const int64_t stride = p.L == 0 ? 0 : p.n * (int64_t)p.acc_stride;
+  if constexpr (KC <= 3) {
+    k_blend_accumulate2<KC><<<cb * p.tiles, kThreads2, 0, s>>>(ws.tile_off, ws.entries, p.capacity, ws.rec, p.n,
+                                                               p.width, p.height, p.tiles_x, p.tiles, targets, dtype,
+                                                               p.K, k0, cam0, sub_img, ws.acc, p.acc_stride, stride,
+                                                               ws.status);
+    note_launches(1);
+    return;
+  }
   k_blend_accumulate<KC><<<cb * p.tiles, kThreads, 0, s>>>(ws.tile_off, ws.entries, p.capacity, ws.rec, p.n,
                                                             p.width, p.height, p.tiles_x, p.tiles, targets, dtype,
                                                             p.K, k0, cam0, sub_img, ws.acc, p.acc_stride, stride,

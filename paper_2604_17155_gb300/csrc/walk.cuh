@@ -27,6 +27,11 @@ struct TileCtx {
   uint32_t b, len;
 };
 
+// ROWS = 1: CTAs of 256 threads, warp w covers the 8x4 block ((w&1)*8, (w>>1)*4) with one pixel
+// per lane. ROWS = 2: CTAs of 128 threads, warp w covers the 8x8 block ((w&1)*8, (w>>1)*8) and lane
+// l the two pixels (l&7, l>>3) and (l&7, (l>>3) + 4) of it; px, py, pyf and inside then describe
+// the first of the two (the second is 4 rows below).
+template <int ROWS = 1>
 __device__ __forceinline__ TileCtx tile_ctx(const uint32_t* tile_off, uint32_t capacity, int tiles,
                                             int tiles_x, int width, int height) {
   TileCtx c;
@@ -36,7 +41,7 @@ __device__ __forceinline__ TileCtx tile_ctx(const uint32_t* tile_off, uint32_t c
   const int tyi = c.t / tiles_x, txi = c.t - tyi * tiles_x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ox = txi * kTile, oy = tyi * kTile;
-  const int bx = (warp & 1) * 8, by = (warp >> 1) * 4;  // warp block, tile-relative
+  const int bx = (warp & 1) * 8, by = (warp >> 1) * 4 * ROWS;  // warp block, tile-relative
   c.px = ox + bx + (lane & 7);
   c.py = oy + by + (lane >> 3);
   c.inside = c.px < width && c.py < height;
@@ -47,7 +52,7 @@ __device__ __forceinline__ TileCtx tile_ctx(const uint32_t* tile_off, uint32_t c
   c.wx0 = (float)bx + 0.5f;
   c.wx1 = (float)bx + 7.5f;
   c.wy0 = (float)by + 0.5f;
-  c.wy1 = (float)by + 3.5f;
+  c.wy1 = (float)(by + 4 * ROWS) - 0.5f;
   const uint32_t b = min(tile_off[bid], capacity);
   uint32_t e = min(tile_off[bid + 1], capacity);
   if (e < b) e = b;
@@ -92,20 +97,20 @@ __device__ __forceinline__ unsigned long long cmpx_keep(unsigned long long a, un
 // exchanges inside a thread, strides below 32 are warp shuffles, and only strides 32..128 go
 // through shared memory (s, P keys), so a 256-key sort has 6 barrier-separated stages instead of 36.
 // On return s holds the sorted keys.
-template <int E>
+template <int E, int NT = kThreads>
 __device__ __forceinline__ void block_bitonic_sort(unsigned long long (&v)[E], unsigned long long* s, int P) {
   const int t = threadIdx.x;
   for (int k = 2; k <= P; k <<= 1) {
     for (int jj = k >> 1; jj > 0; jj >>= 1) {
-      if (jj >= kThreads) {
+      if (jj >= NT) {
 #pragma unroll
-        for (int m = 1; m < E; m <<= 1) {  // m = jj / 256, unrolled so that v is indexed statically
-          if (m * kThreads != jj) continue;
+        for (int m = 1; m < E; m <<= 1) {  // m = jj / NT, unrolled so that v is indexed statically
+          if (m * NT != jj) continue;
 #pragma unroll
           for (int e = 0; e < E; ++e) {
             const int pe = e ^ m;
             if (pe > e) {
-              const int i = e * kThreads + t;
+              const int i = e * NT + t;
               const unsigned long long a = v[e], b = v[pe];
               const bool up = (i & k) == 0;
               const bool swap = (a > b) == up;
@@ -116,25 +121,25 @@ __device__ __forceinline__ void block_bitonic_sort(unsigned long long (&v)[E], u
         }
       } else if (jj >= 32) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) s[e * kThreads + t] = v[e];
+        for (int e = 0; e < E; ++e) s[e * NT + t] = v[e];
         __syncthreads();
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          const int i = e * kThreads + t;
+          const int i = e * NT + t;
           v[e] = cmpx_keep(v[e], s[i ^ jj], i, jj, k);
         }
         __syncthreads();
       } else {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          const int i = e * kThreads + t;
+          const int i = e * NT + t;
           v[e] = cmpx_keep(v[e], __shfl_xor_sync(kFull, v[e], jj), i, jj, k);
         }
       }
     }
   }
 #pragma unroll
-  for (int e = 0; e < E; ++e) s[e * kThreads + t] = v[e];
+  for (int e = 0; e < E; ++e) s[e * NT + t] = v[e];
   __syncthreads();
 }
 
@@ -176,27 +181,35 @@ __device__ __forceinline__ void sort_keys_block(const unsigned long long* g, uin
 // The tile's depth-ordered list: sorted here into shared memory when it fits, else the global
 // slot range that the long-list sort has already ordered. Keys are unique ((depth bits << 32) |
 // index), so the ascending order is depth order with ties in index order.
+template <int NT = kThreads>
 __device__ __forceinline__ const unsigned long long* stage_tile_list(const uint64_t* __restrict__ entries,
                                                                      uint32_t b, uint32_t len,
                                                                      unsigned long long* s_keys) {
   const unsigned long long* g = reinterpret_cast<const unsigned long long*>(entries) + b;
   if (len > (uint32_t)kWalkSortCap) return g;  // uniform
-  if (len <= (uint32_t)kThreads) {
-    // one key per thread: strides below 32 by shuffles, 32..128 through shared memory (at most 6
+  if (len <= (uint32_t)NT) {
+    // one key per thread: strides below 32 by shuffles, 32..NT/2 through shared memory (at most 6
     // barrier-separated stages for 256 keys). Threads t >= P sort padding among themselves.
     int P = 32;
     while (P < (int)len) P <<= 1;
     unsigned long long v[1];
     v[0] = threadIdx.x < len ? g[threadIdx.x] : ~0ull;
-    block_bitonic_sort<1>(v, s_keys, P);
+    block_bitonic_sort<1, NT>(v, s_keys, P);
+    return s_keys;
+  }
+  if (NT < kThreads && len <= 2u * (uint32_t)NT) {  // small CTAs: two keys per thread
+    unsigned long long v[2];
+    v[0] = g[threadIdx.x];
+    v[1] = threadIdx.x + NT < len ? g[threadIdx.x + NT] : ~0ull;
+    block_bitonic_sort<2, NT>(v, s_keys, 2 * NT);
     return s_keys;
   }
   // longer lists: the plain network (a register-blocked one would cost the walk registers)
   int P = 2;
   while (P < (int)len) P <<= 1;
-  for (int k = threadIdx.x; k < P; k += kThreads) s_keys[k] = k < (int)len ? g[k] : ~0ull;
+  for (int k = threadIdx.x; k < P; k += NT) s_keys[k] = k < (int)len ? g[k] : ~0ull;
   __syncthreads();
-  bitonic_sort_smem<kThreads>(s_keys, P);
+  bitonic_sort_smem<NT>(s_keys, P);
   return s_keys;
 }
 
