@@ -407,7 +407,12 @@ def run_icgs(args, rank, world, local_rank):
     acc_rows = scene.n * (1 if L == 0 else cams.n)
     bytes_alg = target_bytes + inst * (8 + 32) + acc_rows * (1 + K) * 4 * 2
     tc = args.precision == "mixed" and K >= 16 and targets.dtype != torch.float32
-    kname = f"k_blend_accumulate_tc<{16 if K <= 16 else 32 if K <= 32 else 64}>" if tc else f"k_blend_accumulate<{min(K, 16)}>"
+    if tc:
+        kname = f"k_blend_accumulate_tc<{16 if K <= 16 else 32 if K <= 32 else 64}>"
+    elif K <= 3:
+        kname = f"k_blend_accumulate2<{K}>"  # two pixels per thread
+    else:
+        kname = f"k_blend_accumulate<{min(K, 16)}>"
     roof = {"kernel": kname, "bound": "alu", "achieved": achieved_tflops,
             "peak": fp32_peak / 1e12, "unit": "TFLOP/s", "frac": achieved_tflops / (fp32_peak / 1e12),
             "traffic": measured_traffic(args.workload, "tensor-core" if tc else "cuda-core",

@@ -1,17 +1,18 @@
-// blend.cu -- the per-tile front-to-back walks (Eq. 2, Eq. 4-6), one CTA of 256 threads per
-// 16x16 screen tile and one pixel per thread.
+// blend.cu -- the per-tile front-to-back walks (Eq. 2, Eq. 4-6), one CTA per 16x16 screen tile:
+// 256 threads with one pixel each, or (k_blend_accumulate2) 128 threads with two pixels each.
 //
 //   k_blend_accumulate  colorize: for every (pixel, Gaussian) blend weight w = alpha T (Eq. 4)
-//                       accumulate V = sum w (Eq. 5) and S_k = sum w t_k (Eq. 6 numerator). The
+//   (2: <= 3 channels)  accumulate V = sum w (Eq. 5) and S_k = sum w t_k (Eq. 6 numerator). The
 //                       tile's pixels are reduced per Gaussian inside each warp (a halving
-//                       "transpose" butterfly that leaves value v's warp sum in lane v * 32/NP) and
-//                       across warps with shared-memory atomics; then ONE global atomic group per
+//                       butterfly that leaves value v's warp sum in lane v * 32/NP) and across
+//                       warps with shared-memory atomics; then ONE global atomic group per
 //                       (Gaussian, tile) lands in the per-(camera, Gaussian) accumulator.
 //   k_blend_render      render: img_k = sum w C_k (Eq. 1-3) with C from the payload.
 //   k_blend_adjoint     gradient: dL/dt_k = sum w a_k and, per Gaussian, dL/do = sum over pixels of
 //                       (g T - sum_{n>m} g_n w_n / (1-alpha)) * alpha/o with g = beta + a . t.
 //
-// Warp w of a CTA covers the 8x4 pixel block ((w&1)*8, (w>>1)*4) of the tile. A warp skips a
+// Warp w of a CTA covers the 8x4 pixel block ((w&1)*8, (w>>1)*4) of the tile (8x8 blocks at
+// ((w&1)*8, (w>>1)*8) in the two-pixel walk). A warp skips a
 // Gaussian whose padded support box misses its block (a warp-uniform test), and skips a whole
 // batch once all its pixels stopped. Every walk takes its decisions through warp_hits() and
 // blend_step(), written with explicit round-to-nearest intrinsics, so all walks take the same
@@ -66,18 +67,43 @@ __device__ __forceinline__ float warp_transpose_reduce(float (&v)[NP], int lane)
   return r;
 }
 
+// The same warp sums without selects, for values held in lane-permuted slots: slot i of lane l
+// holds value index i ^ m(l), m(l) = (l >> (5 - log2 NP)) & (NP - 1). At each level a lane keeps its
+// lower half of slots and adds its partner's upper half, which holds the same value indices (the
+// partner's m differs in exactly that level's bit). Lane l returns the warp sum of value m(l).
+// The caller permutes its per-pixel factors once (they do not change during the walk).
+template <int NP>
+__device__ __forceinline__ float warp_permuted_reduce(float (&v)[NP]) {
+  constexpr int P = Log2<NP>::value;
+#pragma unroll
+  for (int lvl = 0; lvl < P; ++lvl) {
+    const int off = 16 >> lvl;
+    const int half = NP >> (lvl + 1);
+#pragma unroll
+    for (int i = 0; i < half; ++i) v[i] += __shfl_xor_sync(kFull, v[i + half], off);
+  }
+  float r = v[0];
+#pragma unroll
+  for (int off = 16 >> P; off > 0; off >>= 1) r += __shfl_xor_sync(kFull, r, off);
+  return r;
+}
 // ------------------------------------------------------------------------------------------
 // colorize: V and S per (camera, Gaussian)
 // ------------------------------------------------------------------------------------------
 template <int KC>
-__global__ void __launch_bounds__(kThreads, KC <= 3 ? 8 : (KC <= 8 ? 5 : 4)) k_blend_accumulate(
+__global__ void __launch_bounds__(kThreads, KC <= 8 ? 5 : 4) k_blend_accumulate(
     const uint32_t* __restrict__ tile_off, const uint64_t* __restrict__ entries, uint32_t capacity,
     const ProjRec* __restrict__ rec, int64_t n, int width, int height, int tiles_x, int tiles,
     const void* __restrict__ targets, int dtype, int K, int k0, int cam0, const float* __restrict__ sub_img,
     float* __restrict__ acc, int RS, int64_t acc_cam_stride, DevStatus* status) {
+  static_assert(KC >= 4, "up to 3 channels take the two-pixel walk");
   constexpr int NV = KC + 1;                      // V and S_0..S_{KC-1}
-  constexpr int NP = NextPow2<NV>::value;
-  constexpr int SHIFT = 5 - Log2<NP>::value;      // the sum of value v lands in lane v << SHIFT
+  // 16 channels reduce V on its own, so that the sums fill a 16-value reduction instead of a
+  // 32-value one padded with 15 zeros; otherwise V is value 0 of the reduction.
+  constexpr bool kSplitV = KC == 16;
+  constexpr int NS = kSplitV ? KC : NV;           // values in the warp reduction
+  constexpr int NP = NextPow2<NS>::value;
+  constexpr int SHIFT = 5 - Log2<NP>::value;      // lane l returns the sum of value l >> SHIFT
   __shared__ float4 s_geo[kBatch], s_aux[kBatch];
   __shared__ float2 s_half[kBatch];
   __shared__ uint32_t s_id[kBatch];
@@ -105,7 +131,28 @@ __global__ void __launch_bounds__(kThreads, KC <= 3 ? 8 : (KC <= 8 ? 5 : 4)) k_b
   const ProjRec* rec_cam = rec + (int64_t)c.j * n;
   float* acc_cam = acc + (int64_t)c.j * acc_cam_stride;
   const int my_value = lane >> SHIFT;
-  const bool reducer = (lane & ((1 << SHIFT) - 1)) == 0 && my_value < NV;
+  const bool reducer = (lane & ((1 << SHIFT) - 1)) == 0 && my_value < NS;
+  const int my_col = (kSplitV ? 1 : 0) + my_value;  // the s_acc column of this lane's sum
+  // Value q of a hit is w u[q], u = (1, t_0, .., t_{KC-1}, 0, ..), or the channels alone when V is
+  // reduced on its own. This lane keeps value q in slot q ^ my_value (warp_permuted_reduce), so u
+  // is permuted here once, by one conditional swap per bit of my_value.
+  float u[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    const int k = q - (kSplitV ? 0 : 1);
+    u[q] = k < 0 ? 1.0f : (k < KC ? tv[k >= 0 && k < KC ? k : 0] : 0.0f);
+  }
+#pragma unroll
+  for (int bit = 1; bit < NP; bit <<= 1) {
+    const bool sw = (my_value & bit) != 0;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      if (q & bit) continue;
+      const float x = u[q], y = u[q | bit];
+      u[q] = sw ? y : x;
+      u[q | bit] = sw ? x : y;
+    }
+  }
   float T = 1.0f;
   bool done = !c.inside;
   uint32_t npairs = 0;
@@ -117,43 +164,7 @@ __global__ void __launch_bounds__(kThreads, KC <= 3 ? 8 : (KC <= 8 ? 5 : 4)) k_b
     if (!__all_sync(kFull, done)) {
 #pragma unroll
       for (int half = 0; half < kBatch / 32; ++half) {
-       uint32_t bits = warp_hit_bits(s_geo, s_half, half * 32, nb, c);
-       if constexpr (NP <= 4) {
-        // two consecutive hits share one reduction of 2 NP values (their order is kept: the
-        // second Gaussian is blended with the transmittance the first one leaves)
-        constexpr int NP2 = 2 * NP;
-        constexpr int SHIFT2 = 5 - Log2<NP2>::value;
-        while (bits) {
-          const int g1 = half * 32 + __ffs(bits) - 1;
-          bits &= bits - 1;
-          const int g2 = bits ? half * 32 + __ffs(bits) - 1 : -1;
-          bits &= bits - 1;
-          float w1 = 0.0f, w2 = 0.0f, al, ex;
-          bool cap;
-          if (!done) w1 = blend_step(s_geo[g1], s_aux[g1], c.pxf, c.pyf, T, done, al, ex, cap);
-          if (g2 >= 0 && !done) w2 = blend_step(s_geo[g2], s_aux[g2], c.pxf, c.pyf, T, done, al, ex, cap);
-          if (__any_sync(kFull, w1 > 0.0f || w2 > 0.0f)) {
-            npairs += (w1 > 0.0f) + (w2 > 0.0f);
-            float v[NP2];
-            v[0] = w1;
-            v[NP] = w2;
-#pragma unroll
-            for (int k = 0; k < KC; ++k) {
-              v[k + 1] = w1 * tv[k];
-              v[NP + k + 1] = w2 * tv[k];
-            }
-#pragma unroll
-            for (int k = NV; k < NP; ++k) {
-              v[k] = 0.0f;
-              v[NP + k] = 0.0f;
-            }
-            const float r = warp_transpose_reduce<NP2>(v, lane);
-            const int vi = lane >> SHIFT2, vk = vi & (NP - 1);
-            const int gg = vi < NP ? g1 : g2;
-            if ((lane & ((1 << SHIFT2) - 1)) == 0 && vk < NV && gg >= 0) atomicAdd(&s_acc[gg][vk], r);
-          }
-        }
-       } else {
+        uint32_t bits = warp_hit_bits(s_geo, s_half, half * 32, nb, c);
         while (bits) {  // only the Gaussians whose box touches this warp's block, in depth order
           const int g = half * 32 + __ffs(bits) - 1;
           bits &= bits - 1;
@@ -163,16 +174,18 @@ __global__ void __launch_bounds__(kThreads, KC <= 3 ? 8 : (KC <= 8 ? 5 : 4)) k_b
           if (__any_sync(kFull, w > 0.0f)) {
             npairs += w > 0.0f;
             float v[NP];
-            v[0] = w;
 #pragma unroll
-            for (int k = 0; k < KC; ++k) v[k + 1] = w * tv[k];
+            for (int q = 0; q < NP; ++q) v[q] = __fmul_rn(w, u[q]);
+            const float r = warp_permuted_reduce<NP>(v);
+            if (reducer) atomicAdd(&s_acc[g][my_col], r);
+            if constexpr (kSplitV) {
+              float ws = w;
 #pragma unroll
-            for (int k = NV; k < NP; ++k) v[k] = 0.0f;
-            const float r = warp_transpose_reduce<NP>(v, lane);
-            if (reducer) atomicAdd(&s_acc[g][my_value], r);
+              for (int off = 16; off > 0; off >>= 1) ws += __shfl_xor_sync(kFull, ws, off);
+              if (lane == 1) atomicAdd(&s_acc[g][0], ws);
+            }
           }
         }
-       }
       }
     }
     __syncthreads();
@@ -180,19 +193,10 @@ __global__ void __launch_bounds__(kThreads, KC <= 3 ? 8 : (KC <= 8 ? 5 : 4)) k_b
       const int g = threadIdx.x;
       if (s_acc[g][0] > 0.0f) {
         float* dst = acc_cam + (int64_t)s_id[g] * RS;
-        if constexpr (KC == 3) {
-          if (K == 3) {
-            atomicAdd(reinterpret_cast<float4*>(dst), make_float4(s_acc[g][0], s_acc[g][1], s_acc[g][2], s_acc[g][3]));
-          } else {
-            if (k0 == 0) atomicAdd(dst, s_acc[g][0]);
-            for (int k = 0; k < KC && k0 + k < K; ++k) atomicAdd(dst + 1 + k0 + k, s_acc[g][k + 1]);
-          }
-        } else {
-          if (k0 == 0) atomicAdd(dst, s_acc[g][0]);
+        if (k0 == 0) atomicAdd(dst, s_acc[g][0]);
 #pragma unroll
-          for (int k = 0; k < KC; ++k)
-            if (k0 + k < K) atomicAdd(dst + 1 + k0 + k, s_acc[g][k + 1]);
-        }
+        for (int k = 0; k < KC; ++k)
+          if (k0 + k < K) atomicAdd(dst + 1 + k0 + k, s_acc[g][k + 1]);
 #pragma unroll
         for (int k = 0; k < NV; ++k) s_acc[g][k] = 0.0f;
       }
@@ -544,13 +548,12 @@ void accumulate_chunk(const Problem& p, int cb, int cam0, const void* targets, i
                                                                p.width, p.height, p.tiles_x, p.tiles, targets, dtype,
                                                                p.K, k0, cam0, sub_img, ws.acc, p.acc_stride, stride,
                                                                ws.status);
-    note_launches(1);
-    return;
+  } else {
+    k_blend_accumulate<KC><<<cb * p.tiles, kThreads, 0, s>>>(ws.tile_off, ws.entries, p.capacity, ws.rec, p.n,
+                                                              p.width, p.height, p.tiles_x, p.tiles, targets, dtype,
+                                                              p.K, k0, cam0, sub_img, ws.acc, p.acc_stride, stride,
+                                                              ws.status);
   }
-  k_blend_accumulate<KC><<<cb * p.tiles, kThreads, 0, s>>>(ws.tile_off, ws.entries, p.capacity, ws.rec, p.n,
-                                                            p.width, p.height, p.tiles_x, p.tiles, targets, dtype,
-                                                            p.K, k0, cam0, sub_img, ws.acc, p.acc_stride, stride,
-                                                            ws.status);
   note_launches(1);
 }
 
