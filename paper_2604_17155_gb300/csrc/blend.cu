@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kThreads, KC <= 8 ? 5 : 4) k_blend_accumulate(
     if (!__all_sync(kFull, done)) {
 #pragma unroll
       for (int half = 0; half < kBatch / 32; ++half) {
-        uint32_t bits = warp_hit_bits(s_geo, s_half, half * 32, nb, c);
+        uint32_t bits = warp_hit_bits<true>(s_geo, s_aux, s_half, half * 32, nb, c);
         while (bits) {  // only the Gaussians whose box touches this warp's block, in depth order
           const int g = half * 32 + __ffs(bits) - 1;
           bits &= bits - 1;
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kThreads2, 12) k_blend_accumulate2(
     if (!__all_sync(kFull, done0 && done1)) {
 #pragma unroll
       for (int half = 0; half < kBatch / 32; ++half) {
-        uint32_t bits = warp_hit_bits(s_geo, s_half, half * 32, nb, c);
+        uint32_t bits = warp_hit_bits<true>(s_geo, s_aux, s_half, half * 32, nb, c);
         while (bits) {
           const int g1 = half * 32 + __ffs(bits) - 1;
           bits &= bits - 1;
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_render(
     if (!__all_sync(kFull, done)) {
 #pragma unroll
       for (int half = 0; half < kBatch / 32; ++half) {
-        uint32_t bits = warp_hit_bits(s_geo, s_half, half * 32, nb, c);
+        uint32_t bits = warp_hit_bits(s_geo, s_aux, s_half, half * 32, nb, c);
         while (bits && !done) {
           const int g = half * 32 + __ffs(bits) - 1;
           bits &= bits - 1;
@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(kThreads, KC <= 4 ? 6 : (KC <= 16 ? 4 : (KC <=
       if (!__all_sync(kFull, done)) {
 #pragma unroll
         for (int half = 0; half < kBatch / 32; ++half) {
-          uint32_t bits = warp_hit_bits(s_geo, s_half, half * 32, nb, c);
+          uint32_t bits = warp_hit_bits(s_geo, s_aux, s_half, half * 32, nb, c);
           while (bits && !done) {
             const int g = half * 32 + __ffs(bits) - 1;
             bits &= bits - 1;
@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(kThreads, KC <= 4 ? 6 : (KC <= 16 ? 4 : (KC <=
     if (!__all_sync(kFull, done)) {
 #pragma unroll
       for (int half = 0; half < kBatch / 32; ++half) {
-       uint32_t bits = warp_hit_bits(s_geo, s_half, half * 32, nb, c);
+       uint32_t bits = warp_hit_bits(s_geo, s_aux, s_half, half * 32, nb, c);
        // dL/dalpha_m of one hit for this pixel (0 when skipped or capped); updates T and P
        auto d_opacity = [&](int g) -> float {
          if (done) return 0.0f;

@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(256, 2) k_blend_accumulate_tc(
     if (!__all_sync(0xFFFFFFFFu, done)) {
 #pragma unroll
       for (int q = 0; q < kG / 32; ++q) {
-        uint32_t bits = warp_hit_bits(s_geo, s_half, q * 32, nb, c);
+        uint32_t bits = warp_hit_bits(s_geo, s_aux, s_half, q * 32, nb, c);
         while (bits && !done) {  // only Gaussians whose box touches this warp's block, in depth order
           const int g = q * 32 + __ffs(bits) - 1;
           bits &= bits - 1;

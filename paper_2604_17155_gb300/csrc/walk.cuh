@@ -233,13 +233,54 @@ __device__ __forceinline__ bool warp_hits(const float4 geo, const float2 half, c
   return geo.x + half.x >= c.wx0 && geo.x - half.x <= c.wx1 && geo.y + half.y >= c.wy0 && geo.y - half.y <= c.wy1;
 }
 
-// Box-hit masks of this warp for the batch's Gaussians [base, base + 32): bit i is set when
-// Gaussian base + i (< nb) touches the warp's pixel block. One Gaussian per lane, one ballot;
-// iterating the set bits in ascending order keeps the depth order.
-__device__ __forceinline__ uint32_t warp_hit_bits(const float4* s_geo, const float2* s_half, int base, int nb,
-                                                  const TileCtx& c) {
+// Can blend_step take the Gaussian at some pixel centre of the warp's block, i.e. can
+// E = A dx^2 + Bc dx dy + C dy^2 reach E_thr there? E is concave with its peak (0) at the mean. Over
+// the rectangle R of the block's pixel centres it peaks at the mean if the mean lies in R, else on
+// the edge of R that faces the mean: x = the nearer x-edge when the mean lies outside R in x, or
+// y = the nearer y-edge when it lies outside in y (from a point of R off those edges, a small step
+// toward the mean stays in R and raises E), at the optimum of E along that edge, clamped to it.
+// The test rejects only when that peak falls short of E_thr by more than a rounding margin
+// (1e-5 of the terms' magnitude), far above the float32 error of the peak and of the per-pixel E,
+// so it never drops a Gaussian that some pixel's blend_step would take.
+__device__ __forceinline__ bool ellipse_reaches_block(const float4 geo, const float4 aux, const TileCtx& c) {
+  const float x0 = c.wx0 - geo.x, x1 = c.wx1 - geo.x;  // dx over the block
+  const float y0 = c.wy0 - geo.y, y1 = c.wy1 - geo.y;  // dy over the block
+  const bool out_x = x0 > 0.0f || x1 < 0.0f, out_y = y0 > 0.0f || y1 < 0.0f;
+  if (!out_x && !out_y) return true;
+  const float A = geo.z, Bc = geo.w, C = aux.x;  // A, C < 0
+  float best = -INFINITY, mag = 0.0f;
+  if (out_x) {
+    const float dx = x0 > 0.0f ? x0 : x1;
+    const float dy = fminf(fmaxf(__fdividef(-Bc * dx, 2.0f * C), y0), y1);
+    best = (A * dx + Bc * dy) * dx + C * dy * dy;
+    mag = (fabsf(A * dx) + fabsf(Bc * dy)) * fabsf(dx) + fabsf(C * dy) * fabsf(dy);
+  }
+  if (out_y) {
+    const float dy = y0 > 0.0f ? y0 : y1;
+    const float dx = fminf(fmaxf(__fdividef(-Bc * dy, 2.0f * A), x0), x1);
+    const float e = (A * dx + Bc * dy) * dx + C * dy * dy;
+    const float m = (fabsf(A * dx) + fabsf(Bc * dy)) * fabsf(dx) + fabsf(C * dy) * fabsf(dy);
+    best = fmaxf(best, e);
+    mag = fmaxf(mag, m);
+  }
+  return best + 1e-5f * mag + 1e-6f >= aux.z;
+}
+
+// Hit masks of this warp for the batch's Gaussians [base, base + 32): bit i is set when
+// Gaussian base + i (< nb) touches the warp's pixel block: its box, and with ELLIPSE also its
+// ellipse. One Gaussian per lane, one ballot; iterating the set bits in ascending order keeps the
+// depth order. The ellipse test removes about 15% of the box hits of an 8x8 block; it pays in the
+// issue-bound accumulate walks and costs latency in the tensor-core walk, so each walk chooses.
+template <bool ELLIPSE = false>
+__device__ __forceinline__ uint32_t warp_hit_bits(const float4* s_geo, const float4* s_aux, const float2* s_half,
+                                                  int base, int nb, const TileCtx& c) {
   const int g = base + (int)(threadIdx.x & 31);
-  const bool h = g < nb && warp_hits(s_geo[g], s_half[g], c);
+  bool h = false;
+  if (g < nb) {
+    const float4 geo = s_geo[g];
+    h = warp_hits(geo, s_half[g], c);
+    if constexpr (ELLIPSE) h = h && ellipse_reaches_block(geo, s_aux[g], c);
+  }
   return __ballot_sync(kFull, h);
 }
 
