@@ -1,8 +1,9 @@
 // solve.cu -- the normal equations and the batched regularised solve (Eq. 12-14, Alg. 1 lines 5-6).
 //
 //   k_fold          G_i += sum_j V_ij Y_ij Y_ij^T, b_i += sum_j Y_ij S_ij^T, w_i += sum_j V_ij over the
-//                   cameras of one pass (L > 0). One 16-lane group per Gaussian, lane r owns row r of
-//                   G_i and b_i. MIXED keeps a TwoSum compensation term per entry.
+//                   cameras of one pass (L > 0). One 8-lane group per Gaussian: lane r forms wrapped
+//                   diagonal r of the symmetric G_i and rows r, r + 8 of b_i. MIXED keeps a TwoSum
+//                   compensation term per entry.
 //   k_solve         A_i = G_i + w_i Lambda; Cholesky with the rows in registers of the group (pivots
 //                   and columns exchanged by shuffles); forward and back substitution per channel.
 //                   MIXED: the FP32 solution is refined in float-float against the compensated sums;
@@ -44,33 +45,65 @@ __device__ __forceinline__ F group_sum(F v) {
 // ------------------------------------------------------------------------------------------
 // fold
 // ------------------------------------------------------------------------------------------
+// One 8-lane group per Gaussian. G is symmetric, so the group forms only its B (B + 1) / 2 unique
+// unique entries only, by wrapped diagonals: lane r accumulates diagonal r, the entries
+// ((c + r) mod B, c) for c = 0..B-1, and for even B also the entry (r + B/2, r) of the half
+// diagonal B/2. Diagonals 0..ceil(B/2)-1 and that half diagonal hold every unordered pair {row, col}
+// exactly once. Per camera the column factor Y[c] is a compile-time index (a broadcast float4
+// load) and the row factor v Y[(c + r) mod B] is read from a doubled copy of the v Y row at the
+// lane's own offset r, so an entry costs one FMA. b rows r, r + 8 belong to lane r. G is written
+// out in full (both triangles), row-major like the sums of the single-camera-group layout.
+constexpr int kFoldGroup = 8;
+
+__device__ __forceinline__ unsigned fold_group_mask() {
+  return 0xFFu << (threadIdx.x & 24u);
+}
+
 template <int B, int KC, bool MIXED>
 __global__ void __launch_bounds__(kSolveThreads) k_fold(
     const float* __restrict__ means, int64_t n, const DevCam* __restrict__ cams, int cb,
     const float* __restrict__ acc, int K, int RS, int k0, bool first, bool want_gram, float* __restrict__ G,
     float* __restrict__ Glo, float* __restrict__ bvec, float* __restrict__ blo,
     float* __restrict__ wsum, float* __restrict__ wlo) {
-  // per lane: the basis of the camera it evaluates (rows padded so 16-byte stores do not collide)
+  constexpr int GS = kFoldGroup;
+  constexpr int ND = (B + 1) / 2;              // full wrapped diagonals (lanes 0..ND-1)
+  constexpr bool kHalf = (B % 2) == 0;         // even B: lanes 0..B/2-1 also take one entry of diagonal B/2
+  constexpr int NG = B + (kHalf ? 1 : 0);      // Gram slots of a lane
+  constexpr int NR = (B + GS - 1) / GS;        // b rows of a lane: r, r + 8
   constexpr int kYStride = (B + 3) / 4 * 4 + 4;
+  constexpr int kVStride = 2 * B + 1;          // odd: the four groups' rows fall in distinct banks
+  static_assert(ND <= GS, "one diagonal per lane");
   __shared__ __align__(16) float s_Y[kSolveThreads][kYStride];
-  const int64_t i = (blockIdx.x * (int64_t)kSolveThreads + threadIdx.x) / kGroup;
-  const int r = threadIdx.x % kGroup;
+  __shared__ float s_vY[kSolveThreads][kVStride];
+  const int64_t i = (blockIdx.x * (int64_t)kSolveThreads + threadIdx.x) / GS;
+  const int r = threadIdx.x % GS;
   if (i >= n) return;  // whole groups exit together
-  const bool row = r < B;
+  const bool diag = r < ND;
   const bool do_gram = k0 == 0 && want_gram;  // G (skipped by refinement, whose Gram is fixed)
   const bool do_w = k0 == 0;
-  float g[B], gl[B], bb[KC], bl[KC];
+  float* Gi = G + i * B * B;
+  float* Gli = MIXED ? Glo + i * B * B : nullptr;
+  float g[NG], gl[NG], bb[NR][KC], bl[NR][KC];
   float w = 0.0f, wl = 0.0f;
 #pragma unroll
-  for (int c = 0; c < B; ++c) { g[c] = 0.0f; gl[c] = 0.0f; }
+  for (int s = 0; s < NG; ++s) { g[s] = 0.0f; gl[s] = 0.0f; }
 #pragma unroll
-  for (int k = 0; k < KC; ++k) { bb[k] = 0.0f; bl[k] = 0.0f; }
-  if (!first && row) {
-    if (do_gram) {
+  for (int m = 0; m < NR; ++m)
 #pragma unroll
-      for (int c = 0; c < B; ++c) {
-        g[c] = G[(i * B + r) * B + c];
-        if (MIXED) gl[c] = Glo[(i * B + r) * B + c];
+    for (int k = 0; k < KC; ++k) { bb[m][k] = 0.0f; bl[m][k] = 0.0f; }
+  // slot s < B: entry ((s + r) mod B, s); slot B (even B): entry (r + B/2, r)
+  auto entry = [&](int s) -> int {
+    if (s < B) { const int row = s + r < B ? s + r : s + r - B; return row * B + s; }
+    return (r + B / 2) * B + r;
+  };
+  const bool half_slot = kHalf && r < B / 2;
+  if (!first) {
+    if (do_gram && diag) {
+#pragma unroll
+      for (int s = 0; s < NG; ++s) {
+        if (s == B && !half_slot) continue;
+        g[s] = Gi[entry(s)];
+        if (MIXED) gl[s] = Gli[entry(s)];
       }
     }
     if (do_w) {
@@ -78,104 +111,139 @@ __global__ void __launch_bounds__(kSolveThreads) k_fold(
       if (MIXED) wl = wlo[i];
     }
 #pragma unroll
-    for (int k = 0; k < KC; ++k)
-      if (k0 + k < K) {
-        bb[k] = bvec[(i * B + r) * K + k0 + k];
-        if (MIXED) bl[k] = blo[(i * B + r) * K + k0 + k];
+    for (int m = 0; m < NR; ++m) {
+      const int row = r + GS * m;
+      if (row < B) {
+#pragma unroll
+        for (int k = 0; k < KC; ++k)
+          if (k0 + k < K) {
+            bb[m][k] = bvec[(i * B + row) * K + k0 + k];
+            if (MIXED) bl[m][k] = blo[(i * B + row) * K + k0 + k];
+          }
       }
+    }
   }
   const float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
   const int64_t stride = n * (int64_t)RS;
   // MIXED: plain FP32 partial sums over blocks of kFoldBlock cameras, each block added to the
   // running (hi, lo) pair with one TwoSum
-  float pg[B], pb[KC], pw = 0.0f;
+  float pg[NG], pb[NR][KC], pw = 0.0f;
 #pragma unroll
-  for (int c = 0; c < B; ++c) pg[c] = 0.0f;
+  for (int s = 0; s < NG; ++s) pg[s] = 0.0f;
 #pragma unroll
-  for (int k = 0; k < KC; ++k) pb[k] = 0.0f;
-  const unsigned gm = group_mask();
-  const int gbase = threadIdx.x & ~(kGroup - 1);
-  // 16 cameras at a time: lane q loads camera jb + q's row (V, S) and evaluates its view direction
-  // and basis into s_Y; the group shares V, S by shuffles and reads the basis rows back
-  for (int jb = 0; jb < cb; jb += kGroup) {
-   float lv = 0.0f, ls[KC];
+  for (int m = 0; m < NR; ++m)
 #pragma unroll
-   for (int k = 0; k < KC; ++k) ls[k] = 0.0f;
-   if (jb + r < cb) {
-     const float* a = acc + (int64_t)(jb + r) * stride + i * RS;
-     lv = a[0];
+    for (int k = 0; k < KC; ++k) pb[m][k] = 0.0f;
+  const unsigned gm = fold_group_mask();
+  const int gbase = threadIdx.x & ~(GS - 1);
+  // 8 cameras at a time: lane q loads camera jb + q's row (V, S), evaluates its basis Y into s_Y
+  // and v Y (twice) into s_vY; the group shares V, S by shuffles and reads the rows back
+  for (int jb = 0; jb < cb; jb += GS) {
+    float lv = 0.0f, ls[KC];
 #pragma unroll
-     for (int k = 0; k < KC; ++k)
-       if (k0 + k < K) ls[k] = a[1 + k0 + k];
-   }
-   if (lv > 0.0f) {
-     const float3 d = view_dir(mu, cams[jb + r]);
-     float Yl[kYStride];
-     sh_basis<B>(d.x, d.y, d.z, Yl);
-#pragma unroll
-     for (int c4 = 0; c4 < (B + 3) / 4; ++c4)
-       reinterpret_cast<float4*>(s_Y[threadIdx.x])[c4] =
-           make_float4(Yl[4 * c4], 4 * c4 + 1 < B ? Yl[4 * c4 + 1] : 0.0f, 4 * c4 + 2 < B ? Yl[4 * c4 + 2] : 0.0f,
-                       4 * c4 + 3 < B ? Yl[4 * c4 + 3] : 0.0f);
-   }
-   __syncwarp(gm);
-   const int nj = min(kGroup, cb - jb);
-   for (int q = 0; q < nj; ++q) {
-    const int j = jb + q;
-    const float v = __shfl_sync(gm, lv, q, kGroup);
-    float sv[KC];
-#pragma unroll
-    for (int k = 0; k < KC; ++k) sv[k] = __shfl_sync(gm, ls[k], q, kGroup);
-    if (v > 0.0f) {
-      float Y[(B + 3) / 4 * 4];
-#pragma unroll
-      for (int c4 = 0; c4 < (B + 3) / 4; ++c4) {
-        const float4 y4 = reinterpret_cast<const float4*>(s_Y[gbase + q])[c4];
-        Y[4 * c4] = y4.x; Y[4 * c4 + 1] = y4.y; Y[4 * c4 + 2] = y4.z; Y[4 * c4 + 3] = y4.w;
-      }
-      const float Yr = row ? s_Y[gbase + q][r] : 0.0f;
-      if (do_gram) {
-        const float vy = v * Yr;
-#pragma unroll
-        for (int c = 0; c < B; ++c) {
-          if constexpr (MIXED) pg[c] = fmaf(vy, Y[c], pg[c]);
-          else g[c] = fmaf(vy, Y[c], g[c]);
-        }
-      }
-      if (do_w) {
-        if constexpr (MIXED) pw += v;
-        else w += v;
-      }
+    for (int k = 0; k < KC; ++k) ls[k] = 0.0f;
+    if (jb + r < cb) {
+      const float* a = acc + (int64_t)(jb + r) * stride + i * RS;
+      lv = a[0];
 #pragma unroll
       for (int k = 0; k < KC; ++k)
-        if (k0 + k < K) {
-          if constexpr (MIXED) pb[k] = fmaf(Yr, sv[k], pb[k]);
-          else bb[k] = fmaf(Yr, sv[k], bb[k]);
+        if (k0 + k < K) ls[k] = a[1 + k0 + k];
+    }
+    if (lv > 0.0f) {
+      const float3 d = view_dir(mu, cams[jb + r]);
+      float Yl[kYStride];
+      sh_basis<B>(d.x, d.y, d.z, Yl);
+#pragma unroll
+      for (int c4 = 0; c4 < (B + 3) / 4; ++c4)
+        reinterpret_cast<float4*>(s_Y[threadIdx.x])[c4] =
+            make_float4(Yl[4 * c4], 4 * c4 + 1 < B ? Yl[4 * c4 + 1] : 0.0f, 4 * c4 + 2 < B ? Yl[4 * c4 + 2] : 0.0f,
+                        4 * c4 + 3 < B ? Yl[4 * c4 + 3] : 0.0f);
+      if (do_gram) {
+#pragma unroll
+        for (int c = 0; c < B; ++c) {
+          const float vy = lv * Yl[c];
+          s_vY[threadIdx.x][c] = vy;
+          s_vY[threadIdx.x][c + B] = vy;
         }
-    }
-    if (MIXED && ((j % kFoldBlock) == kFoldBlock - 1 || j == cb - 1)) {
-#pragma unroll
-      for (int c = 0; c < B; ++c) {
-        two_sum_acc(g[c], gl[c], pg[c]);
-        pg[c] = 0.0f;
-      }
-      two_sum_acc(w, wl, pw);
-      pw = 0.0f;
-#pragma unroll
-      for (int k = 0; k < KC; ++k) {
-        two_sum_acc(bb[k], bl[k], pb[k]);
-        pb[k] = 0.0f;
       }
     }
-   }
-   __syncwarp(gm);
+    __syncwarp(gm);
+    const int nj = min(GS, cb - jb);
+    for (int q = 0; q < nj; ++q) {
+      const int j = jb + q;
+      const float v = __shfl_sync(gm, lv, q, GS);
+      float sv[KC];
+#pragma unroll
+      for (int k = 0; k < KC; ++k) sv[k] = __shfl_sync(gm, ls[k], q, GS);
+      if (v > 0.0f) {
+        const float* Yq = s_Y[gbase + q];
+        if (do_gram && diag) {
+          float Y[(B + 3) / 4 * 4];
+#pragma unroll
+          for (int c4 = 0; c4 < (B + 3) / 4; ++c4) {
+            const float4 y4 = reinterpret_cast<const float4*>(Yq)[c4];
+            Y[4 * c4] = y4.x; Y[4 * c4 + 1] = y4.y; Y[4 * c4 + 2] = y4.z; Y[4 * c4 + 3] = y4.w;
+          }
+          const float* vq = s_vY[gbase + q] + r;  // vq[c] = v Y[(c + r) mod B]
+#pragma unroll
+          for (int s = 0; s < B; ++s) {
+            if constexpr (MIXED) pg[s] = fmaf(vq[s], Y[s], pg[s]);
+            else g[s] = fmaf(vq[s], Y[s], g[s]);
+          }
+          if constexpr (kHalf) {
+            if (half_slot) {  // entry (r + B/2, r): v Y[r + B/2] Y[r]
+              if constexpr (MIXED) pg[B] = fmaf(vq[B / 2], Yq[r], pg[B]);
+              else g[B] = fmaf(vq[B / 2], Yq[r], g[B]);
+            }
+          }
+        }
+        if (do_w) {
+          if constexpr (MIXED) pw += v;
+          else w += v;
+        }
+#pragma unroll
+        for (int m = 0; m < NR; ++m) {
+          const int row = r + GS * m;
+          const float Yr = row < B ? Yq[row] : 0.0f;
+#pragma unroll
+          for (int k = 0; k < KC; ++k)
+            if (k0 + k < K) {
+              if constexpr (MIXED) pb[m][k] = fmaf(Yr, sv[k], pb[m][k]);
+              else bb[m][k] = fmaf(Yr, sv[k], bb[m][k]);
+            }
+        }
+      }
+      if (MIXED && ((j % kFoldBlock) == kFoldBlock - 1 || j == cb - 1)) {
+#pragma unroll
+        for (int s = 0; s < NG; ++s) {
+          two_sum_acc(g[s], gl[s], pg[s]);
+          pg[s] = 0.0f;
+        }
+        two_sum_acc(w, wl, pw);
+        pw = 0.0f;
+#pragma unroll
+        for (int m = 0; m < NR; ++m)
+#pragma unroll
+          for (int k = 0; k < KC; ++k) {
+            two_sum_acc(bb[m][k], bl[m][k], pb[m][k]);
+            pb[m][k] = 0.0f;
+          }
+      }
+    }
+    __syncwarp(gm);
   }
-  if (!row) return;
-  if (do_gram) {
+  if (do_gram && diag) {
 #pragma unroll
-    for (int c = 0; c < B; ++c) {
-      G[(i * B + r) * B + c] = g[c];
-      if (MIXED) Glo[(i * B + r) * B + c] = gl[c];
+    for (int s = 0; s < NG; ++s) {
+      if (s == B && !half_slot) continue;
+      const int e = entry(s);
+      const int row = e / B, col = e - row * B;
+      Gi[e] = g[s];
+      if (MIXED) Gli[e] = gl[s];
+      if (row != col) {  // the mirrored entry
+        Gi[col * B + row] = g[s];
+        if (MIXED) Gli[col * B + row] = gl[s];
+      }
     }
   }
   if (do_w && r == 0) {
@@ -183,11 +251,17 @@ __global__ void __launch_bounds__(kSolveThreads) k_fold(
     if (MIXED) wlo[i] = wl;
   }
 #pragma unroll
-  for (int k = 0; k < KC; ++k)
-    if (k0 + k < K) {
-      bvec[(i * B + r) * K + k0 + k] = bb[k];
-      if (MIXED) blo[(i * B + r) * K + k0 + k] = bl[k];
+  for (int m = 0; m < NR; ++m) {
+    const int row = r + GS * m;
+    if (row < B) {
+#pragma unroll
+      for (int k = 0; k < KC; ++k)
+        if (k0 + k < K) {
+          bvec[(i * B + row) * K + k0 + k] = bb[m][k];
+          if (MIXED) blo[(i * B + row) * K + k0 + k] = bl[m][k];
+        }
     }
+  }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -781,7 +855,7 @@ int payload_group(int B, int K, int arrays) {
 template <int B, bool MIXED>
 void fold_b(const Problem& p, const float* means, int cb, const Workspace& ws, bool first, bool want_gram,
             cudaStream_t s) {
-  const unsigned grid = (unsigned)((p.n * kGroup + kSolveThreads - 1) / kSolveThreads);
+  const unsigned grid = (unsigned)((p.n * kFoldGroup + kSolveThreads - 1) / kSolveThreads);
   for (int k0 = 0; k0 < p.K; k0 += 4) {
     k_fold<B, 4, MIXED><<<grid, kSolveThreads, 0, s>>>(means, p.n, ws.cams, cb, ws.acc, p.K, p.acc_stride, k0, first,
                                                         want_gram, ws.G, ws.Glo, ws.bvec, ws.blo, ws.wsum, ws.wlo);
