@@ -43,35 +43,12 @@ struct NextPow2 {
   static constexpr int value = N <= 1 ? 1 : N <= 2 ? 2 : N <= 4 ? 4 : N <= 8 ? 8 : N <= 16 ? 16 : 32;
 };
 
-// Warp sums of NP values (NP a power of two <= 32) with NP - 1 + 5 - log2(NP) shuffles: at each of
-// the first log2(NP) levels a lane keeps half of its values and trades the other half with its
-// partner. Lane l returns the warp sum of value index (l >> (5 - log2 NP)) & (NP - 1).
-template <int NP>
-__device__ __forceinline__ float warp_transpose_reduce(float (&v)[NP], int lane) {
-  constexpr int P = Log2<NP>::value;
-#pragma unroll
-  for (int lvl = 0; lvl < P; ++lvl) {
-    const int off = 16 >> lvl;
-    const int half = NP >> (lvl + 1);
-    const bool upper = (lane & off) != 0;
-#pragma unroll
-    for (int i = 0; i < half; ++i) {
-      const float send = upper ? v[i] : v[i + half];
-      const float keep = upper ? v[i + half] : v[i];
-      v[i] = keep + __shfl_xor_sync(kFull, send, off);
-    }
-  }
-  float r = v[0];
-#pragma unroll
-  for (int off = 16 >> P; off > 0; off >>= 1) r += __shfl_xor_sync(kFull, r, off);
-  return r;
-}
-
-// The same warp sums without selects, for values held in lane-permuted slots: slot i of lane l
-// holds value index i ^ m(l), m(l) = (l >> (5 - log2 NP)) & (NP - 1). At each level a lane keeps its
-// lower half of slots and adds its partner's upper half, which holds the same value indices (the
-// partner's m differs in exactly that level's bit). Lane l returns the warp sum of value m(l).
-// The caller permutes its per-pixel factors once (they do not change during the walk).
+// Warp sums of NP values (NP a power of two <= 32) with NP - 1 + 5 - log2(NP) shuffles and no
+// selects, for values held in lane-permuted slots: slot i of lane l holds value index i ^ m(l),
+// m(l) = (l >> (5 - log2 NP)) & (NP - 1). At each level a lane keeps its lower half of slots and
+// adds its partner's upper half, which holds the same value indices (the partner's m differs in
+// exactly that level's bit). Lane l returns the warp sum of value m(l). The caller permutes its
+// per-pixel factors once (they do not change during the walk).
 template <int NP>
 __device__ __forceinline__ float warp_permuted_reduce(float (&v)[NP]) {
   constexpr int P = Log2<NP>::value;
@@ -207,14 +184,14 @@ __global__ void __launch_bounds__(kThreads, KC <= 8 ? 5 : 4) k_blend_accumulate(
 }
 
 // The same accumulation for up to 3 channels with two pixels per thread: CTAs of 128 threads, each
-// warp covering an 8x8 block. A hit's fixed costs (the ballot loop, the shared loads, the vote, the
+// warp covering an 8x8 block, 10 CTAs (48 registers a thread) per SM. A hit's fixed costs (the ballot loop, the shared loads, the vote, the
 // warp reduction and the shared atomic) are shared by 64 pixels instead of 32: each thread adds its
 // two pixels' contributions before the reduction. The pixels of a thread are walked independently
 // (own transmittance, own stop), in the same depth order, through the same blend_step().
 constexpr int kThreads2 = kThreads / 2;
 
 template <int KC>
-__global__ void __launch_bounds__(kThreads2, 12) k_blend_accumulate2(
+__global__ void __launch_bounds__(kThreads2, 10) k_blend_accumulate2(
     const uint32_t* __restrict__ tile_off, const uint64_t* __restrict__ entries, uint32_t capacity,
     const ProjRec* __restrict__ rec, int64_t n, int width, int height, int tiles_x, int tiles,
     const void* __restrict__ targets, int dtype, int K, int k0, int cam0, const float* __restrict__ sub_img,
@@ -253,6 +230,33 @@ __global__ void __launch_bounds__(kThreads2, 12) k_blend_accumulate2(
       }
     }
   }
+  // Value h NP + k of a hit pair is hit h's weights times u[k], u = (1, t_0, .., t_{KC-1}, 0, ..),
+  // summed over the thread's two pixels. This lane keeps it in slot (h NP + k) ^ m
+  // (warp_permuted_reduce), so u is permuted here once, by one conditional swap per bit of mk, and
+  // the pair's two hits trade places when mh is set.
+  const int m = lane >> SHIFT2;
+  const bool mh = (m & NP) != 0;
+  const int mk = m & (NP - 1);
+  float u0[NP], u1[NP];
+  u0[0] = u1[0] = 1.0f;
+#pragma unroll
+  for (int k = 1; k < NP; ++k) {
+    u0[k] = k <= KC ? tv0[k <= KC ? k - 1 : 0] : 0.0f;
+    u1[k] = k <= KC ? tv1[k <= KC ? k - 1 : 0] : 0.0f;
+  }
+#pragma unroll
+  for (int bit = 1; bit < NP; bit <<= 1) {
+    const bool sw = (mk & bit) != 0;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      if (k & bit) continue;
+      const float x0 = u0[k], y0 = u0[k | bit], x1 = u1[k], y1 = u1[k | bit];
+      u0[k] = sw ? y0 : x0;
+      u0[k | bit] = sw ? x0 : y0;
+      u1[k] = sw ? y1 : x1;
+      u1[k | bit] = sw ? x1 : y1;
+    }
+  }
   for (int k = threadIdx.x; k < kBatch * NV; k += kThreads2) (&s_acc[0][0])[k] = 0.0f;
   const ProjRec* rec_cam = rec + (int64_t)c.j * n;
   float* acc_cam = acc + (int64_t)c.j * acc_cam_stride;
@@ -288,23 +292,17 @@ __global__ void __launch_bounds__(kThreads2, 12) k_blend_accumulate2(
           const float w1 = __fadd_rn(w10, w11), w2 = __fadd_rn(w20, w21);
           if (__any_sync(kFull, w1 > 0.0f || w2 > 0.0f)) {
             npairs += (w10 > 0.0f) + (w11 > 0.0f) + (w20 > 0.0f) + (w21 > 0.0f);
+            const float a0 = mh ? w20 : w10, a1 = mh ? w21 : w11;
+            const float c0 = mh ? w10 : w20, c1 = mh ? w11 : w21;
             float v[NP2];
-            v[0] = w1;
-            v[NP] = w2;
 #pragma unroll
-            for (int k = 0; k < KC; ++k) {
-              v[k + 1] = __fmaf_rn(w10, tv0[k], __fmul_rn(w11, tv1[k]));
-              v[NP + k + 1] = __fmaf_rn(w20, tv0[k], __fmul_rn(w21, tv1[k]));
+            for (int k = 0; k < NP; ++k) {
+              v[k] = __fmaf_rn(a0, u0[k], __fmul_rn(a1, u1[k]));
+              v[NP + k] = __fmaf_rn(c0, u0[k], __fmul_rn(c1, u1[k]));
             }
-#pragma unroll
-            for (int k = NV; k < NP; ++k) {
-              v[k] = 0.0f;
-              v[NP + k] = 0.0f;
-            }
-            const float r = warp_transpose_reduce<NP2>(v, lane);
-            const int vi = lane >> SHIFT2, vk = vi & (NP - 1);
-            const int gg = vi < NP ? g1 : g2;
-            if ((lane & ((1 << SHIFT2) - 1)) == 0 && vk < NV && gg >= 0) atomicAdd(&s_acc[gg][vk], r);
+            const float r = warp_permuted_reduce<NP2>(v);  // the warp sum of value index m
+            const int gg = mh ? g2 : g1;
+            if ((lane & ((1 << SHIFT2) - 1)) == 0 && mk < NV && gg >= 0) atomicAdd(&s_acc[gg][mk], r);
           }
         }
       }
