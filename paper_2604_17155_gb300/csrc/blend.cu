@@ -388,13 +388,91 @@ __global__ void __launch_bounds__(kThreads) k_blend_render(
   }
 }
 
+// The render with two pixels per thread (up to 4 channels): CTAs of 128 threads, each warp
+// covering an 8x8 block; the pixels (x, y) and (x, y + 4) of a thread are walked independently.
+// A hit costs little here (no reduction), so the warp keeps the plain box test.
+template <int KC>
+__global__ void __launch_bounds__(kThreads2, 10) k_blend_render2(
+    const uint32_t* __restrict__ tile_off, const uint64_t* __restrict__ entries, uint32_t capacity,
+    const ProjRec* __restrict__ rec, int64_t n, int width, int height, int tiles_x, int tiles,
+    const float* __restrict__ payload, int K, int k0, int cam0, float* __restrict__ images) {
+  static_assert(KC <= 4, "two pixels per thread: up to 4 channels");
+  __shared__ float4 s_geo[kBatch], s_aux[kBatch];
+  __shared__ float2 s_half[kBatch];
+  __shared__ uint32_t s_id[kBatch];
+  __shared__ float s_col[kBatch][KC];
+  __shared__ unsigned long long s_keys[kWalkSortCap];
+  const TileCtx c = tile_ctx<2>(tile_off, capacity, tiles, tiles_x, width, height);
+  const unsigned long long* list = stage_tile_list<kThreads2>(entries, c.b, c.len, s_keys);
+  const bool inside1 = c.inside && c.py + 4 < height;
+  const float pyf1 = c.pyf + 4.0f;
+  const ProjRec* rec_cam = rec + (int64_t)c.j * n;
+  const float* pay_cam = payload + (int64_t)c.j * n * K;
+  float img0[KC], img1[KC];
+#pragma unroll
+  for (int k = 0; k < KC; ++k) img0[k] = img1[k] = 0.0f;
+  float T0 = 1.0f, T1 = 1.0f;
+  bool done0 = !c.inside, done1 = !inside1;
+  for (uint32_t start = 0; start < c.len; start += kBatch) {
+    const int nb = (int)min((uint32_t)kBatch, c.len - start);
+    __syncthreads();
+    load_batch(list, start, nb, rec_cam, n, c.ox, c.oy, s_geo, s_aux, s_half, s_id);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nb * KC; idx += kThreads2) {
+      const int g = idx / KC, k = idx - g * KC;
+      s_col[g][k] = k0 + k < K ? pay_cam[(int64_t)s_id[g] * K + k0 + k] : 0.0f;
+    }
+    __syncthreads();
+    if (!__all_sync(kFull, done0 && done1)) {
+#pragma unroll
+      for (int half = 0; half < kBatch / 32; ++half) {
+        uint32_t bits = warp_hit_bits(s_geo, s_aux, s_half, half * 32, nb, c);
+        while (bits && !(done0 && done1)) {
+          const int g = half * 32 + __ffs(bits) - 1;
+          bits &= bits - 1;
+          const float4 geo = s_geo[g], aux = s_aux[g];
+          float al, ex;
+          bool cap;
+          if (!done0) {
+            const float w = blend_step(geo, aux, c.pxf, c.pyf, T0, done0, al, ex, cap);
+            if (w > 0.0f) {
+#pragma unroll
+              for (int k = 0; k < KC; ++k) img0[k] = fmaf(w, s_col[g][k], img0[k]);
+            }
+          }
+          if (!done1) {
+            const float w = blend_step(geo, aux, c.pxf, pyf1, T1, done1, al, ex, cap);
+            if (w > 0.0f) {
+#pragma unroll
+              for (int k = 0; k < KC; ++k) img1[k] = fmaf(w, s_col[g][k], img1[k]);
+            }
+          }
+        }
+      }
+    }
+    if (__syncthreads_and(done0 && done1)) break;
+  }
+  if (c.inside) {
+    float* dst = images + (((int64_t)(cam0 + c.j) * height + c.py) * width + c.px) * K + k0;
+#pragma unroll
+    for (int k = 0; k < KC; ++k)
+      if (k0 + k < K) dst[k] = img0[k];
+    if (inside1) {
+      dst += 4 * (int64_t)width * K;
+#pragma unroll
+      for (int k = 0; k < KC; ++k)
+        if (k0 + k < K) dst[k] = img1[k];
+    }
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // adjoint: dL/dt and dL/do. Payload per (camera, Gaussian) = (a_0..a_{K-1}, beta).
 // ------------------------------------------------------------------------------------------
-template <int KC>
+template <int KC, int NT = kThreads>
 __device__ __forceinline__ void load_payload(const float* __restrict__ pay_cam, int nb, int K, const uint32_t* s_id,
                                              float (*s_pay)[KC + 1]) {
-  for (int idx = threadIdx.x; idx < nb * (KC + 1); idx += kThreads) {
+  for (int idx = threadIdx.x; idx < nb * (KC + 1); idx += NT) {
     const int g = idx / (KC + 1), k = idx - g * (KC + 1);
     float v = 0.0f;
     if (k < KC) {
@@ -537,6 +615,178 @@ __global__ void __launch_bounds__(kThreads, KC <= 4 ? 6 : (KC <= 16 ? 4 : (KC <=
   }
 }
 
+// Pass 1 of the adjoint walk for one pixel and one staged Gaussian: F += g w and dL/dt += w a,
+// with g = a . t + beta.
+template <int KC>
+__device__ __forceinline__ void adjoint_gather(const float4 geo, const float4 aux, const float* pay,
+                                               const float (&tv)[KC], float pxf, float pyf, float& T, bool& done,
+                                               float& F, float (&gt)[KC]) {
+  float al, ex;
+  bool cap;
+  const float w = blend_step(geo, aux, pxf, pyf, T, done, al, ex, cap);
+  if (w > 0.0f) {
+    float gg = pay[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      gg = fmaf(pay[k], tv[k], gg);
+      gt[k] = fmaf(w, pay[k], gt[k]);
+    }
+    F = fmaf(gg, w, F);
+  }
+}
+
+// Pass 2 for one pixel and one staged Gaussian m: dL/dalpha_m = g_m T_m - (F - P_m) / (1 - alpha_m),
+// returned times dalpha/do = exp(-q/2) (0 when skipped or when alpha was capped); advances T and P.
+template <int KC>
+__device__ __forceinline__ float adjoint_step(const float4 geo, const float4 aux, const float* pay,
+                                              const float (&tv)[KC], float pxf, float pyf, float F, float& T,
+                                              float& P, bool& done) {
+  if (done) return 0.0f;
+  const float Tm = T;
+  float al = 0.0f, ex = 0.0f;
+  bool cap = false;
+  const float w = blend_step(geo, aux, pxf, pyf, T, done, al, ex, cap);
+  if (!(w > 0.0f)) return 0.0f;
+  float gg = pay[KC];
+#pragma unroll
+  for (int k = 0; k < KC; ++k) gg = fmaf(pay[k], tv[k], gg);
+  P = fmaf(gg, w, P);
+  const float dalpha = gg * Tm - __fdividef(F - P, 1.0f - al);
+  return cap ? 0.0f : dalpha * ex;
+}
+
+// The adjoint walk with two pixels per thread (up to 4 channels): CTAs of 128 threads, each warp
+// covering an 8x8 block. Pass 2 adds a thread's two pixels before the warp reduction, so one
+// reduction of a hit pair serves 64 pixels.
+template <int KC>
+__global__ void __launch_bounds__(kThreads2, KC <= 2 ? 10 : 8) k_blend_adjoint2(
+    const uint32_t* __restrict__ tile_off, const uint64_t* __restrict__ entries, uint32_t capacity,
+    const ProjRec* __restrict__ rec, int64_t n, int width, int height, int tiles_x, int tiles,
+    const void* __restrict__ targets, int dtype, const float* __restrict__ payload, int K, int cam0,
+    float* __restrict__ grad_t, float* __restrict__ grad_o) {
+  static_assert(KC <= 4, "two pixels per thread: up to 4 channels");
+  __shared__ float4 s_geo[kBatch], s_aux[kBatch];
+  __shared__ float2 s_half[kBatch];
+  __shared__ uint32_t s_id[kBatch];
+  __shared__ float s_pay[kBatch][KC + 1];
+  __shared__ float s_go[kBatch];
+  __shared__ unsigned long long s_keys[kWalkSortCap];
+  const TileCtx c = tile_ctx<2>(tile_off, capacity, tiles, tiles_x, width, height);
+  const unsigned long long* list = stage_tile_list<kThreads2>(entries, c.b, c.len, s_keys);
+  const int lane = threadIdx.x & 31;
+  const bool inside1 = c.inside && c.py + 4 < height;
+  const float pyf1 = c.pyf + 4.0f;
+  const ProjRec* rec_cam = rec + (int64_t)c.j * n;
+  const float* pay_cam = payload + (int64_t)c.j * n * (K + 1);
+  float tv0[KC], tv1[KC];
+#pragma unroll
+  for (int k = 0; k < KC; ++k) tv0[k] = tv1[k] = 0.0f;
+  const int64_t pix0 = ((int64_t)(cam0 + c.j) * height + c.py) * width + c.px;
+  const int64_t pix1 = pix0 + 4 * (int64_t)width;
+  if (c.inside) {
+#pragma unroll
+    for (int k = 0; k < KC; ++k)
+      if (k < K) {
+        tv0[k] = load_target(targets, pix0 * K + k, dtype);
+        if (inside1) tv1[k] = load_target(targets, pix1 * K + k, dtype);
+      }
+  }
+  // pass 1: F = sum_n g_n w_n and dL/dt = sum_n w_n a_n, per pixel
+  float F0 = 0.0f, F1 = 0.0f;
+  {
+    float gt0[KC], gt1[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) gt0[k] = gt1[k] = 0.0f;
+    float T0 = 1.0f, T1 = 1.0f;
+    bool done0 = !c.inside, done1 = !inside1;
+    for (uint32_t start = 0; start < c.len; start += kBatch) {
+      const int nb = (int)min((uint32_t)kBatch, c.len - start);
+      __syncthreads();
+      load_batch(list, start, nb, rec_cam, n, c.ox, c.oy, s_geo, s_aux, s_half, s_id);
+      __syncthreads();
+      load_payload<KC, kThreads2>(pay_cam, nb, K, s_id, s_pay);
+      __syncthreads();
+      if (!__all_sync(kFull, done0 && done1)) {
+#pragma unroll
+        for (int half = 0; half < kBatch / 32; ++half) {
+          uint32_t bits = warp_hit_bits<true>(s_geo, s_aux, s_half, half * 32, nb, c);
+          while (bits && !(done0 && done1)) {
+            const int g = half * 32 + __ffs(bits) - 1;
+            bits &= bits - 1;
+            const float4 geo = s_geo[g], aux = s_aux[g];
+            if (!done0) adjoint_gather<KC>(geo, aux, s_pay[g], tv0, c.pxf, c.pyf, T0, done0, F0, gt0);
+            if (!done1) adjoint_gather<KC>(geo, aux, s_pay[g], tv1, c.pxf, pyf1, T1, done1, F1, gt1);
+          }
+        }
+      }
+      if (__syncthreads_and(done0 && done1)) break;
+    }
+    if (grad_t && c.inside) {
+#pragma unroll
+      for (int k = 0; k < KC; ++k)
+        if (k < K) {
+          grad_t[pix0 * K + k] = gt0[k];
+          if (inside1) grad_t[pix1 * K + k] = gt1[k];
+        }
+    }
+  }
+  if (!grad_o) return;
+  // pass 2: dL/dalpha_m = g_m T_m - (F - P_m) / (1 - alpha_m), P_m = sum_{n<=m} g_n w_n
+  for (int k = threadIdx.x; k < kBatch; k += kThreads2) s_go[k] = 0.0f;
+  float T0 = 1.0f, T1 = 1.0f, P0 = 0.0f, P1 = 0.0f;
+  bool done0 = !c.inside, done1 = !inside1;
+  for (uint32_t start = 0; start < c.len; start += kBatch) {
+    const int nb = (int)min((uint32_t)kBatch, c.len - start);
+    __syncthreads();
+    load_batch(list, start, nb, rec_cam, n, c.ox, c.oy, s_geo, s_aux, s_half, s_id);
+    __syncthreads();
+    load_payload<KC, kThreads2>(pay_cam, nb, K, s_id, s_pay);
+    __syncthreads();
+    if (!__all_sync(kFull, done0 && done1)) {
+#pragma unroll
+      for (int half = 0; half < kBatch / 32; ++half) {
+        uint32_t bits = warp_hit_bits<true>(s_geo, s_aux, s_half, half * 32, nb, c);
+        // two consecutive hits (in depth order) share one warp reduction of their two values
+        while (bits) {
+          const int g1 = half * 32 + __ffs(bits) - 1;
+          bits &= bits - 1;
+          const int g2 = bits ? half * 32 + __ffs(bits) - 1 : -1;
+          bits &= bits - 1;
+          float d1, d2 = 0.0f;
+          {
+            const float4 geo = s_geo[g1], aux = s_aux[g1];
+            d1 = adjoint_step<KC>(geo, aux, s_pay[g1], tv0, c.pxf, c.pyf, F0, T0, P0, done0) +
+                 adjoint_step<KC>(geo, aux, s_pay[g1], tv1, c.pxf, pyf1, F1, T1, P1, done1);
+          }
+          if (g2 >= 0) {
+            const float4 geo = s_geo[g2], aux = s_aux[g2];
+            d2 = adjoint_step<KC>(geo, aux, s_pay[g2], tv0, c.pxf, c.pyf, F0, T0, P0, done0) +
+                 adjoint_step<KC>(geo, aux, s_pay[g2], tv1, c.pxf, pyf1, F1, T1, P1, done1);
+          }
+          if (__any_sync(kFull, d1 != 0.0f || d2 != 0.0f)) {
+            // lanes < 16 end with the sum of d1, lanes >= 16 with the sum of d2
+            const bool upper = (lane & 16) != 0;
+            float r = (upper ? d2 : d1) + __shfl_xor_sync(kFull, upper ? d1 : d2, 16);
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) r += __shfl_xor_sync(kFull, r, o);
+            if (lane == 0) atomicAdd(&s_go[g1], r);
+            if (lane == 16 && g2 >= 0) atomicAdd(&s_go[g2], r);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nb) {
+      const float v = s_go[threadIdx.x];
+      if (v != 0.0f) {
+        atomicAdd(grad_o + s_id[threadIdx.x], v);
+        s_go[threadIdx.x] = 0.0f;
+      }
+    }
+    if (__syncthreads_and(done0 && done1)) break;
+  }
+}
+
 template <int KC>
 void accumulate_chunk(const Problem& p, int cb, int cam0, const void* targets, int dtype, int k0,
                       const float* sub_img, const Workspace& ws, cudaStream_t s) {
@@ -558,9 +808,15 @@ void accumulate_chunk(const Problem& p, int cb, int cam0, const void* targets, i
 template <int KC>
 void render_chunk(const Problem& p, int cb, int cam0, int k0, const Workspace& ws, float* images,
                   cudaStream_t s) {
-  k_blend_render<KC><<<cb * p.tiles, kThreads, 0, s>>>(ws.tile_off, ws.entries, p.capacity, ws.rec, p.n,
-                                                        p.width, p.height, p.tiles_x, p.tiles, ws.payload, p.K,
-                                                        k0, cam0, images);
+  if constexpr (KC <= 4) {
+    k_blend_render2<KC><<<cb * p.tiles, kThreads2, 0, s>>>(ws.tile_off, ws.entries, p.capacity, ws.rec, p.n,
+                                                           p.width, p.height, p.tiles_x, p.tiles, ws.payload, p.K,
+                                                           k0, cam0, images);
+  } else {
+    k_blend_render<KC><<<cb * p.tiles, kThreads, 0, s>>>(ws.tile_off, ws.entries, p.capacity, ws.rec, p.n,
+                                                          p.width, p.height, p.tiles_x, p.tiles, ws.payload, p.K,
+                                                          k0, cam0, images);
+  }
   note_launches(1);
 }
 
@@ -606,15 +862,20 @@ void launch_blend_adjoint(const Problem& p, int cb, int cam0, const void* target
   k_blend_adjoint<KC><<<cb * p.tiles, kThreads, 0, s>>>(ws.tile_off, ws.entries, p.capacity, ws.rec, p.n,  \
                                                          p.width, p.height, p.tiles_x, p.tiles, targets,     \
                                                          dtype, ws.payload, p.K, cam0, grad_targets, go)
-  if (p.K == 1) ICGS_ADJ(1);
-  else if (p.K == 2) ICGS_ADJ(2);
-  else if (p.K == 3) ICGS_ADJ(3);
-  else if (p.K == 4) ICGS_ADJ(4);
+#define ICGS_ADJ2(KC)                                                                                        \
+  k_blend_adjoint2<KC><<<cb * p.tiles, kThreads2, 0, s>>>(ws.tile_off, ws.entries, p.capacity, ws.rec, p.n,  \
+                                                           p.width, p.height, p.tiles_x, p.tiles, targets,     \
+                                                           dtype, ws.payload, p.K, cam0, grad_targets, go)
+  if (p.K == 1) ICGS_ADJ2(1);
+  else if (p.K == 2) ICGS_ADJ2(2);
+  else if (p.K == 3) ICGS_ADJ2(3);
+  else if (p.K == 4) ICGS_ADJ2(4);
   else if (p.K <= 8) ICGS_ADJ(8);
   else if (p.K <= 16) ICGS_ADJ(16);
   else if (p.K <= 32) ICGS_ADJ(32);
   else ICGS_ADJ(64);
 #undef ICGS_ADJ
+#undef ICGS_ADJ2
   note_launches(1);
 }
 

@@ -123,3 +123,38 @@ def test_refinement_degrees(icgs, L):
     assert rep["p99_checked"] <= 1e-3
     assert rep["bound_excess"] <= 0
     assert mse2 < mse0
+
+
+@pytest.mark.parametrize("K", [1, 2, 4, 5])
+def test_render_and_adjoint_channel_counts(icgs, K):
+    """Render (Eq. 1-3) and the adjoint walk for other channel counts than RGB: 1, 2 and 4 channels
+    take the two-pixel walks, 5 channels the one-pixel walks (an 8-channel chunk)."""
+    L = 1
+    sc, cams = _scene(1500, 291 + K, 8, 70, 50)  # ragged 16x16 tiles
+    coeffs = W.sh_coefficients(sc.n, L, K, seed=301 + K)
+    ref = O.render(sc, cams, coeffs, L)
+    gs, gc = _gpu(icgs, sc, cams)
+    img = to_np(icgs.render(gs, gc, torch.tensor(coeffs, dtype=torch.float32, device=DEV), L))
+    d = np.abs(img - ref)
+    scale = np.abs(ref).max()
+    print(f"render K={K}: p99.9 |d| / max |ref| {np.percentile(d, 99.9) / scale:.2e}")
+    assert np.percentile(d, 99.9) <= 1e-4 * scale
+    assert float((d <= 1e-4 * scale).mean()) >= 0.999
+    t = ref.astype(np.float32)
+    t64 = t.astype(np.float64)
+    col = O.colorize(sc, cams, t64, L)
+    r = np.random.default_rng(311 + K).standard_normal(col["c"].shape)
+    gt_ref, go_ref = O.adjoint(sc, cams, t64, L, None, 2 * r * col["c"], col=col)
+    tt = torch.tensor(t, device=DEV)
+    c, status, chol = icgs.colorize(gs, gc, tt, L)
+    gcoef = torch.tensor(2 * r * col["c"], dtype=torch.float32, device=DEV)
+    gt, go = icgs.colorize_backward(gs, gc, tt, L, torch.tensor(col["c"], dtype=torch.float32, device=DEV), chol,
+                                    gcoef)
+    gt, go = to_np(gt), to_np(go)
+    dt = np.abs(gt - gt_ref)
+    rep, err, checked = coefficient_report(to_np(c), col)
+    eo = np.abs(go - go_ref)[checked] / np.maximum(np.abs(go_ref[checked]), 1e-3 * np.abs(go_ref).max())
+    print(f"adjoint K={K}: dL/dt p99.9 |d|/max {np.percentile(dt, 99.9) / np.abs(gt_ref).max():.2e}, "
+          f"dL/do p99 rel {np.percentile(eo, 99):.2e} over {checked.sum()}")
+    assert np.percentile(dt, 99.9) <= 1e-3 * np.abs(gt_ref).max()
+    assert np.percentile(eo, 99) <= 1e-2
