@@ -52,10 +52,10 @@ KERNEL_SOURCES = {
 }
 MEASURED_TRAFFIC = {
     # relight, 100 cameras: one full-size launch captured (profiles/blend_accumulate_relight.md)
-    ("relight", "cuda-core"): {"bytes_per_scene": 2148036352 + 288154112, "source_sha": "ef529cb48aaa1721"},
+    ("relight", "cuda-core"): {"bytes_per_scene": 2147759872 + 288225536, "source_sha": "a14471c6e8255ccd"},
     # features: a 10-camera launch captured and scaled by 150/10 cameras (the targets, the per-camera
     # tile lists and the per-camera accumulator re-streaming all grow with the camera count)
-    ("features", "tensor-core"): {"bytes_per_scene": 15 * (3255588608 + 1459511552), "source_sha": "e69476b081d0d62e"},
+    ("features", "tensor-core"): {"bytes_per_scene": 15 * (3254054656 + 1458599680), "source_sha": "7e5a1ce7e9fdf37f"},
 }
 
 
