@@ -464,7 +464,8 @@ __device__ __forceinline__ void exact_fold(const float* __restrict__ acc, int64_
 // FP32 solution is then refined in float-float against (G_hi + G_lo, b_hi + b_lo) for
 // kRefineStepsRefold steps. Below cond_tau (cond_tau * kRefoldFp64Scale after a re-fold), or with
 // a non-positive pivot, the Gaussian is solved in FP64.
-template <int B, bool MIXED>
+// NR: right-hand sides solved together (3 for RGB, else 4; the last group is padded with zeros)
+template <int B, bool MIXED, int NR>
 __global__ void __launch_bounds__(kSolveThreads) k_solve(
     int64_t n, int K, const float* __restrict__ G, const float* __restrict__ Glo,
     const float* __restrict__ bvec, const float* __restrict__ blo, const float* __restrict__ wsum,
@@ -546,44 +547,44 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(
         if (c <= r) s_Lg[r * (B + 1) + c] = a[c];
     }
     __syncwarp(group_mask());
-    for (int k0 = 0; k0 < K; k0 += 4) {
+    for (int k0 = 0; k0 < K; k0 += NR) {
       float bh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, bl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
       if (refold && k0 == 0) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) { bh[q] = rb_h[q]; bl[q] = rb_l[q]; }
+        for (int q = 0; q < NR; ++q) { bh[q] = rb_h[q]; bl[q] = rb_l[q]; }
       } else if (refold) {
         float gdummy[B], gldummy[B], wdummy = 0.0f, wldummy = 0.0f;
         exact_fold<B>(acc, cam_stride, i, RS, n_acc_cams, cams, mu, r, false, k0, K, gdummy, gldummy, wdummy,
                       wldummy, bh, bl, s_Y);
       } else {
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+        for (int q = 0; q < NR; ++q)
           if (k0 + q < K && row) {
             bh[q] = bvec[(i * B + r) * K + k0 + q];
             if (MIXED) bl[q] = blo[(i * B + r) * K + k0 + q];
           }
       }
-      // four channels at once (padding channels carry zeros)
-      float x[4];
+      // NR channels at once (padding channels carry zeros)
+      float x[NR];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < NR; ++q) {
         if (!(row && k0 + q < K)) { bh[q] = 0.0f; bl[q] = 0.0f; }
         x[q] = bh[q];
       }
-      group_chol_solve_rows<B, 4>(a, r, x, s_Lg);
+      group_chol_solve_rows<B, NR>(a, r, x, s_Lg);
       if constexpr (MIXED) {
 #pragma unroll 1
         for (int it = 0; it < steps; ++it) {
-          float res[4];
+          float res[NR];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) res[q] = refine_residual<B>(ghi, glo, wl_r, wl_lo, bh[q], bl[q], x[q], r);
-          group_chol_solve_rows<B, 4>(a, r, res, s_Lg);
+          for (int q = 0; q < NR; ++q) res[q] = refine_residual<B>(ghi, glo, wl_r, wl_lo, bh[q], bl[q], x[q], r);
+          group_chol_solve_rows<B, NR>(a, r, res, s_Lg);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) x[q] += res[q];
+          for (int q = 0; q < NR; ++q) x[q] += res[q];
         }
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+      for (int q = 0; q < NR; ++q)
         if (row && k0 + q < K) coeffs[(i * B + r) * K + k0 + q] = x[q];
     }
     if (chol && row) {
@@ -604,25 +605,25 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(
     if (c == r) ad[c] += wd * (double)lam_r;
   }
   group_cholesky<B, double>(ad, r);
-  for (int k0 = 0; k0 < K; k0 += 4) {
+  for (int k0 = 0; k0 < K; k0 += NR) {
     float bh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, bl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     if (refold && k0 == 0) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) { bh[q] = rb_h[q]; bl[q] = rb_l[q]; }
+      for (int q = 0; q < NR; ++q) { bh[q] = rb_h[q]; bl[q] = rb_l[q]; }
     } else if (refold) {
       float gdummy[B], gldummy[B], wdummy = 0.0f, wldummy = 0.0f;
       exact_fold<B>(acc, cam_stride, i, RS, n_acc_cams, cams, mu, r, false, k0, K, gdummy, gldummy, wdummy,
                     wldummy, bh, bl, s_Y);
     } else {
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+      for (int q = 0; q < NR; ++q)
         if (k0 + q < K && row) {
           bh[q] = bvec[(i * B + r) * K + k0 + q];
           bl[q] = blo[(i * B + r) * K + k0 + q];
         }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < NR; ++q) {
       if (k0 + q >= K) break;
       double x = row ? (double)bh[q] + (double)bl[q] : 0.0;
       group_chol_solve<B, double>(ad, r, x);
@@ -867,10 +868,16 @@ template <int B, bool MIXED>
 void solve_b(const Problem& p, const float* lam_dev, const Workspace& ws, float* coeffs, uint8_t* st,
              float* chol, const float* means, int n_acc_cams, cudaStream_t s) {
   const unsigned grid = (unsigned)((p.n * kGroup + kSolveThreads - 1) / kSolveThreads);
-  k_solve<B, MIXED><<<grid, kSolveThreads, 0, s>>>(p.n, p.K, ws.G, ws.Glo, ws.bvec, ws.blo, ws.wsum, ws.wlo,
-                                                       lam_dev, p.cond_tau, p.refold_tau, coeffs, st, chol,
-                                                       ws.status, ws.acc,
-                                                       p.acc_stride, n_acc_cams, ws.cams, means);
+  if (p.K == 3)
+    k_solve<B, MIXED, 3><<<grid, kSolveThreads, 0, s>>>(p.n, p.K, ws.G, ws.Glo, ws.bvec, ws.blo, ws.wsum, ws.wlo,
+                                                         lam_dev, p.cond_tau, p.refold_tau, coeffs, st, chol,
+                                                         ws.status, ws.acc,
+                                                         p.acc_stride, n_acc_cams, ws.cams, means);
+  else
+    k_solve<B, MIXED, 4><<<grid, kSolveThreads, 0, s>>>(p.n, p.K, ws.G, ws.Glo, ws.bvec, ws.blo, ws.wsum, ws.wlo,
+                                                         lam_dev, p.cond_tau, p.refold_tau, coeffs, st, chol,
+                                                         ws.status, ws.acc,
+                                                         p.acc_stride, n_acc_cams, ws.cams, means);
   note_launches(1);
 }
 
