@@ -24,6 +24,8 @@
 // than per instance. The order inside a tile is fixed later by the per-tile sort.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "icgs_device.cuh"
 #include "icgs_internal.h"
 
@@ -192,18 +194,21 @@ constexpr int kPerCta = 256 * kPerThread;     // Gaussians of one camera per CTA
 constexpr int kHistTiles = 12288;             // largest tile grid the shared-memory histograms take
 
 // One CTA per (camera, 2048 Gaussians): counts the CTA's instances per tile in shared memory, then
-// adds each nonzero bin to the global count with one atomic.
+// adds each nonzero bin to the global count with one atomic. The camera is the fast index of the
+// 1-D grid, so the CTAs of one chunk of Gaussians run together and read its parameters from DRAM
+// once (a scene larger than L2 would otherwise be re-read for every camera).
 __global__ void __launch_bounds__(256) k_project_hist(
     const float* __restrict__ means, const float* __restrict__ scales, const float* __restrict__ quats,
-    const float* __restrict__ opac, int64_t n, const DevCam* __restrict__ cams, int width, int height,
-    float near_z, int tiles_x, int tiles, ProjRec* __restrict__ rec, uint4* __restrict__ rect,
+    const float* __restrict__ opac, int64_t n, const DevCam* __restrict__ cams, int j0, int cbl, int width,
+    int height, float near_z, int tiles_x, int tiles, ProjRec* __restrict__ rec, uint4* __restrict__ rect,
     uint32_t* __restrict__ tile_count) {
   extern __shared__ uint32_t s_hist[];
-  const int j = blockIdx.y;
+  const int64_t chunk = blockIdx.x / cbl;
+  const int j = j0 + (int)(blockIdx.x - chunk * cbl);
   const DevCam& c = cams[j];
   for (int t = threadIdx.x; t < tiles; t += 256) s_hist[t] = 0u;
   __syncthreads();
-  const int64_t i0 = (int64_t)blockIdx.x * kPerCta;
+  const int64_t i0 = chunk * kPerCta;
   for (int r = 0; r < kPerThread; ++r) {
     const int64_t i = i0 + r * 256 + threadIdx.x;
     if (i >= n) break;
@@ -398,10 +403,16 @@ void launch_project(const Problem& p, const float* means, const float* scales, c
     const size_t smem = sizeof(uint32_t) * (size_t)p.tiles;
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(k_project_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid((unsigned)((p.n + kPerCta - 1) / kPerCta), (unsigned)cb);
-    k_project_hist<<<grid, 256, smem, s>>>(means, scales, quats, opac, p.n, ws.cams, p.width, p.height, p.near_z,
-                                           p.tiles_x, p.tiles, ws.rec, ws.rect, ws.tile_off);
-    note_launches(1);
+    const int64_t chunks = (p.n + kPerCta - 1) / kPerCta;
+    // cameras per launch so that the 1-D grid stays below 2^31 CTAs
+    const int per = (int)std::min<int64_t>(cb, std::max<int64_t>(1, 0x7FFFFFFF / std::max<int64_t>(chunks, 1)));
+    for (int j0 = 0; j0 < cb; j0 += per) {
+      const int cbl = std::min(per, cb - j0);
+      k_project_hist<<<(unsigned)(chunks * cbl), 256, smem, s>>>(means, scales, quats, opac, p.n, ws.cams, j0, cbl,
+                                                                 p.width, p.height, p.near_z, p.tiles_x, p.tiles,
+                                                                 ws.rec, ws.rect, ws.tile_off);
+      note_launches(1);
+    }
     return;
   }
   dim3 grid((unsigned)((p.n + 255) / 256), (unsigned)cb);

@@ -857,6 +857,12 @@ template <int B, bool MIXED>
 void fold_b(const Problem& p, const float* means, int cb, const Workspace& ws, bool first, bool want_gram,
             cudaStream_t s) {
   const unsigned grid = (unsigned)((p.n * kFoldGroup + kSolveThreads - 1) / kSolveThreads);
+  if (p.K == 3) {  // RGB: one launch of three channels (no zero fourth channel)
+    k_fold<B, 3, MIXED><<<grid, kSolveThreads, 0, s>>>(means, p.n, ws.cams, cb, ws.acc, p.K, p.acc_stride, 0, first,
+                                                        want_gram, ws.G, ws.Glo, ws.bvec, ws.blo, ws.wsum, ws.wlo);
+    note_launches(1);
+    return;
+  }
   for (int k0 = 0; k0 < p.K; k0 += 4) {
     k_fold<B, 4, MIXED><<<grid, kSolveThreads, 0, s>>>(means, p.n, ws.cams, cb, ws.acc, p.K, p.acc_stride, k0, first,
                                                         want_gram, ws.G, ws.Glo, ws.bvec, ws.blo, ws.wsum, ws.wlo);
