@@ -215,6 +215,46 @@ def test_long_tile_lists_and_capacity_retry(icgs):
     assert np.abs(img - ref).max() <= 1e-4 * np.abs(ref).max()
 
 
+def _stacked_tile_scene(n, seed):
+    """n small Gaussians stacked in front of the 16x16 tile whose pixels span [32, 48)^2 of a 64x64
+    camera, so that tile's list has about n keys."""
+    rng = np.random.default_rng(seed)
+    means = np.zeros((n, 3), np.float32)
+    depth = rng.uniform(2.0, 40.0, n)
+    means[:, 0] = rng.uniform(-1.5, 1.5, n) * depth / 400.0
+    means[:, 1] = rng.uniform(-1.5, 1.5, n) * depth / 400.0
+    means[:, 2] = depth
+    sc = W.Scene(means, np.full((n, 3), 1e-4, np.float32), rng.standard_normal((n, 4)).astype(np.float32),
+                 rng.uniform(0.005, 0.05, n).astype(np.float32))
+    w2c = np.concatenate([np.eye(3), np.zeros((3, 1))], 1).astype(np.float32)[None]
+    cams = W.Cameras(64, 64, np.array([400.0], np.float32), np.array([400.0], np.float32),
+                     np.array([40.0], np.float32), np.array([40.0], np.float32), w2c)
+    return sc, cams, rng
+
+
+# 3 FP32 channels: the CUDA-core walk, which sorts lists of up to 1024 keys itself and leaves longer
+# ones to the queued sort; 16 FP16 channels (MIXED): the tensor-core walk, whose lists are all
+# sorted beforehand. 2,500 keys: one shared-memory network; 9,000: runs plus merge-path merges.
+@pytest.mark.parametrize("K,dtype", [(3, "f32"), (16, "f16")])
+@pytest.mark.parametrize("n", [2500, 9000])
+def test_long_tile_list_sort_paths(icgs, K, dtype, n):
+    sc, cams, rng = _stacked_tile_scene(n, 43 + n + K)
+    t = rng.uniform(0, 1, (1, 64, 64, K)).astype(np.float32)
+    tt = torch.tensor(t, device=DEV)
+    if dtype == "f16":
+        tt = tt.half()
+    t_exact = tt.float().cpu().numpy().astype(np.float64)
+    col = O.colorize(sc, cams, t_exact, 0, [1e-5])
+    gs, gc = _gpu(icgs, sc, cams)
+    c, status, _ = icgs.colorize(gs, gc, tt, 0, lam=[1e-5])
+    assert icgs.last_stats()["instances"] > 0.9 * n
+    rep, err, checked = coefficient_report(to_np(c), col, w_min=1e-3)  # tiny, faint Gaussians
+    tol = TOL_FP32 if dtype == "f32" else TOL_BF16
+    print(f"long list n={n} K={K} {dtype}", rep)
+    assert rep["checked"] > 20
+    assert rep["max_checked"] <= tol
+
+
 def test_degenerate_inputs(icgs):
     cams = W.hemisphere_cameras(3, 4.0, 40, 30, 50.0)
     gc = icgs.Cameras.from_workload(cams)
