@@ -5,8 +5,9 @@
 // index order. For the tensor-core walk every list is sorted here, one CTA per tile (k_sort_tiles).
 // The CUDA-core walks sort lists of up to kWalkSortCap keys themselves; the longer ones are queued
 // (k_queue_tiles) and sorted by a persistent kernel (k_sort_queued). Up to kSortCap keys are sorted
-// in shared memory with the register/shuffle bitonic network; longer lists as runs of kSortCap keys
-// followed by merge-path merges between the slot range and a scratch range of the same place.
+// with a bitonic network over keys held in registers (blocked, 8 or 16 a thread, from 1025 keys);
+// longer lists as runs of kSortCap keys followed by merge-path merges between the slot range and a
+// scratch range of the same place.
 #include <cuda_runtime.h>
 
 #include "icgs_internal.h"
@@ -17,13 +18,79 @@ namespace icgs {
 namespace {
 
 constexpr int kSortThreads = 256;
-constexpr int kSortGrid = 152 * 6;  // persistent CTAs (32 KB of shared memory each)
+constexpr int kSortGrid = 152 * 6;  // CTAs of the queued sort (a grid-stride loop; three per SM are resident)
 
 __device__ __forceinline__ void tile_range(const uint32_t* tile_off, int t, uint32_t capacity,
                                            uint32_t& b, uint32_t& e) {
   b = min(tile_off[t], capacity);
   e = min(tile_off[t + 1], capacity);
   if (e < b) e = b;
+}
+
+// Ascending bitonic sort of the len (<= P = 256 E) keys at g, written to dst[0, len). The keys are
+// held blocked: thread t holds keys t E .. t E + E - 1 in v (padding ~0 beyond len). Strides below
+// E are exchanges inside a thread, strides E .. 16 E warp shuffles (the partner is thread
+// t ^ (stride / E)), and only the 6 stages with strides of 32 E or more go through shared memory
+// (s, P + P / E keys: one pad slot every E keys keeps those accesses free of bank conflicts).
+template <int E>
+__device__ __forceinline__ void sort_blocked(const unsigned long long* __restrict__ g, int len,
+                                             unsigned long long* s, unsigned long long* __restrict__ dst) {
+  constexpr int P = kSortThreads * E;
+  const int t = threadIdx.x;
+  const int i0 = t * E;
+  unsigned long long v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) v[e] = i0 + e < len ? g[i0 + e] : ~0ull;
+  auto pad = [](int i) { return i + i / E; };
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      if (jj < E) {
+#pragma unroll
+        for (int m = 1; m < E; m <<= 1) {  // m = jj, unrolled so that v is indexed statically
+          if (m != jj) continue;
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            if (e & m) continue;
+            const unsigned long long a = v[e], b = v[e | m];
+            const bool up = ((i0 + e) & k) == 0;
+            const bool swap = (a > b) == up;
+            v[e] = swap ? b : a;
+            v[e | m] = swap ? a : b;
+          }
+        }
+      } else if (jj < 32 * E) {
+        const int lm = jj / E;
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          v[e] = walk::cmpx_keep(v[e], __shfl_xor_sync(0xFFFFFFFFu, v[e], lm), i0 + e, jj, k);
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) s[pad(i0 + e)] = v[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = walk::cmpx_keep(v[e], s[pad((i0 + e) ^ jj)], i0 + e, jj, k);
+        __syncthreads();
+      }
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+    if (i0 + e < len) dst[i0 + e] = v[e];
+}
+
+// Sorts len (<= kSortCap) keys from g into dst: up to 1024 keys through the walks' shared-memory
+// sort, longer lists blocked (sort_blocked with 8 or 16 keys a thread). g may equal dst.
+__device__ __forceinline__ void sort_list(const unsigned long long* g, int len, unsigned long long* s,
+                                          unsigned long long* dst) {
+  if (len > 2048) {
+    sort_blocked<16>(g, len, s, dst);
+  } else if (len > 1024) {
+    sort_blocked<8>(g, len, s, dst);
+  } else {
+    walk::sort_keys_block<4>(g, (uint32_t)len, s);
+    for (int k = threadIdx.x; k < len; k += kSortThreads) dst[k] = s[k];
+  }
+  __syncthreads();
 }
 
 // Queues every tile whose list has more than min_len keys (one thread per tile; one counter
@@ -50,11 +117,11 @@ __global__ void __launch_bounds__(kSortThreads) k_queue_tiles(const uint32_t* __
 
 // Every tile list: sorted in place when it has at most kSortCap keys (one CTA per tile), queued
 // for k_sort_queued when longer.
-__global__ void __launch_bounds__(kSortThreads) k_sort_tiles(const uint32_t* __restrict__ tile_off,
+__global__ void __launch_bounds__(kSortThreads, 3) k_sort_tiles(const uint32_t* __restrict__ tile_off,
                                                              unsigned long long* __restrict__ entries,
                                                              uint32_t capacity, uint32_t* __restrict__ queue,
                                                              DevStatus* status) {
-  __shared__ unsigned long long s[kSortCap];
+  __shared__ unsigned long long s[kSortCap + kSortCap / 16];
   uint32_t b, e;
   tile_range(tile_off, blockIdx.x, capacity, b, e);
   const int n = (int)(e - b);
@@ -63,8 +130,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(const uint32_t* __r
     if (threadIdx.x == 0) queue[atomicAdd(&status->big_tiles, 1u)] = blockIdx.x;
     return;
   }
-  walk::sort_keys_block<kSortCap / kSortThreads>(entries + b, (uint32_t)n, s);
-  for (int k = threadIdx.x; k < n; k += kSortThreads) entries[b + k] = s[k];
+  sort_list(entries + b, n, s, entries + b);
 }
 
 // Number of elements of A among the first d outputs of merging A and B (keys are unique).
@@ -83,12 +149,12 @@ __device__ __forceinline__ int merge_path(const unsigned long long* A, int na, c
 // kSortCap keys is sorted in shared memory with the register/shuffle bitonic network sized to it;
 // a longer one as runs of kSortCap keys, then pairwise merge-path merges ping-ponging between its
 // slot range and the same range of the scratch array.
-__global__ void __launch_bounds__(kSortThreads) k_sort_queued(const uint32_t* __restrict__ tile_off,
+__global__ void __launch_bounds__(kSortThreads, 3) k_sort_queued(const uint32_t* __restrict__ tile_off,
                                                               unsigned long long* __restrict__ entries,
                                                               unsigned long long* __restrict__ scratch,
                                                               uint32_t capacity, const uint32_t* __restrict__ queue,
                                                               const DevStatus* status) {
-  __shared__ unsigned long long s[kSortCap];
+  __shared__ unsigned long long s[kSortCap + kSortCap / 16];
   const uint32_t count = status->big_tiles;
   for (uint32_t q = blockIdx.x; q < count; q += gridDim.x) {
     uint32_t b, e;
@@ -96,9 +162,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_queued(const uint32_t* __
     const int n = (int)(e - b);
     for (int r0 = 0; r0 < n; r0 += kSortCap) {  // sorted runs (the whole list when it fits)
       const int m = min(kSortCap, n - r0);
-      walk::sort_keys_block<kSortCap / kSortThreads>(entries + b + r0, (uint32_t)m, s);
-      for (int k = threadIdx.x; k < m; k += kSortThreads) entries[b + r0 + k] = s[k];
-      __syncthreads();
+      sort_list(entries + b + r0, m, s, entries + b + r0);
     }
     if (n <= kSortCap) continue;  // uniform
     unsigned long long* src = entries + b;
