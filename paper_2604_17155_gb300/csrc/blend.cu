@@ -1,5 +1,6 @@
 // blend.cu -- the per-tile front-to-back walks (Eq. 2, Eq. 4-6), one CTA per 16x16 screen tile:
-// 256 threads with one pixel each, or (k_blend_accumulate2) 128 threads with two pixels each.
+// 256 threads with one pixel each, or (the kernels named ...2, for up to 3 or 4 channels) 128
+// threads with two pixels each.
 //
 //   k_blend_accumulate  colorize: for every (pixel, Gaussian) blend weight w = alpha T (Eq. 4)
 //   (2: <= 3 channels)  accumulate V = sum w (Eq. 5) and S_k = sum w t_k (Eq. 6 numerator). The
@@ -8,15 +9,16 @@
 //                       warps with shared-memory atomics; then ONE global atomic group per
 //                       (Gaussian, tile) lands in the per-(camera, Gaussian) accumulator.
 //   k_blend_render      render: img_k = sum w C_k (Eq. 1-3) with C from the payload.
+//   (2: <= 4 channels)
 //   k_blend_adjoint     gradient: dL/dt_k = sum w a_k and, per Gaussian, dL/do = sum over pixels of
-//                       (g T - sum_{n>m} g_n w_n / (1-alpha)) * alpha/o with g = beta + a . t.
+//   (2: <= 4 channels)  (g T - sum_{n>m} g_n w_n / (1-alpha)) * alpha/o with g = beta + a . t.
 //
 // Warp w of a CTA covers the 8x4 pixel block ((w&1)*8, (w>>1)*4) of the tile (8x8 blocks at
-// ((w&1)*8, (w>>1)*8) in the two-pixel walk). A warp skips a
-// Gaussian whose padded support box misses its block (a warp-uniform test), and skips a whole
-// batch once all its pixels stopped. Every walk takes its decisions through warp_hits() and
-// blend_step(), written with explicit round-to-nearest intrinsics, so all walks take the same
-// threshold decisions for the same inputs.
+// ((w&1)*8, (w>>1)*8) in the two-pixel walks). A warp skips a Gaussian whose padded support box
+// misses its block (a warp-uniform ballot; the accumulate and adjoint walks then also test the
+// ellipse against the block), and skips a whole batch once all its pixels stopped. Every walk
+// takes its decisions through blend_step(), written with explicit round-to-nearest intrinsics, so
+// all walks take the same threshold decisions for the same inputs.
 #include <cuda_runtime.h>
 
 #include "icgs_device.cuh"

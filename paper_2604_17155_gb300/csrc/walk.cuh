@@ -92,11 +92,11 @@ __device__ __forceinline__ unsigned long long cmpx_keep(unsigned long long a, un
   return (lower == up) ? mn : mx;
 }
 
-// Ascending bitonic sort of P = 256 * E keys (E = 1, 2, 4, 8, 16) by the 256 threads of the CTA,
-// thread t holding keys t, t + 256, ..., t + 256 (E-1) in v. Strides of 256 or more are compare-
-// exchanges inside a thread, strides below 32 are warp shuffles, and only strides 32..128 go
-// through shared memory (s, P keys), so a 256-key sort has 6 barrier-separated stages instead of 36.
-// On return s holds the sorted keys.
+// Ascending bitonic sort of P = NT * E keys (E = 1, 2, 4, 8, 16; with E = 1, P may be smaller) by
+// the NT threads of the CTA, thread t holding keys t, t + NT, ..., t + NT (E-1) in v. Strides of NT
+// or more are compare-exchanges inside a thread, strides below 32 are warp shuffles, and only
+// strides 32..NT/2 go through shared memory (s, P keys), so a 256-key sort by 256 threads has 6
+// barrier-separated stages instead of 36. On return s holds the sorted keys.
 template <int E, int NT = kThreads>
 __device__ __forceinline__ void block_bitonic_sort(unsigned long long (&v)[E], unsigned long long* s, int P) {
   const int t = threadIdx.x;
