@@ -261,6 +261,13 @@ ICGS_API size_t icgs_noalloc_scratch_bytes(void);
 ICGS_API icgs_status icgs_selftest_tc(const void* A, const void* B, int32_t N, int32_t bf16, float* D,
                                       void* workspace, void* stream);
 
+/* Diagnostic, as icgs_selftest_tc for an MMA of M = 64 or 128 rows: D[M x N] = A[M x 256] *
+ * B[N x 256]^T, each row read back from the TMEM lane the walk reads it from. D_lanes (device float32
+ * [128 x N], may be NULL) receives the raw contents of all 128 TMEM lanes, which shows where the
+ * MMA placed each row. Invalid M or N: ICGS_ERR_INVALID_ARG. Synchronises `stream`. */
+ICGS_API icgs_status icgs_selftest_tc_rows(const void* A, int32_t M, const void* B, int32_t N, int32_t bf16, float* D,
+                                           float* D_lanes, void* workspace, void* stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 ICGS_API const char* icgs_last_error(void);
 

@@ -811,19 +811,25 @@ icgs_status icgs_render(const icgs_scene* scene, const icgs_cameras* cams, int32
   return finish(ws, s);
 }
 
-icgs_status icgs_selftest_tc(const void* A, const void* B, int32_t N, int32_t bf16, float* D, void* workspace,
-                             void* stream) {
+icgs_status icgs_selftest_tc_rows(const void* A, int32_t M, const void* B, int32_t N, int32_t bf16, float* D,
+                                  float* D_lanes, void* workspace, void* stream) {
   g_err[0] = '\0';
   if (!A || !B || !D || !workspace) return fail(ICGS_ERR_INVALID_ARG, "A, B, D and workspace are required");
+  if (M != 64 && M != 128) return fail(ICGS_ERR_INVALID_ARG, "M = %d must be 64 or 128", M);
   if (N != 32 && N != 80) return fail(ICGS_ERR_INVALID_ARG, "N = %d must be 32 or 80", N);
   if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(ICGS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Workspace ws;
   ws.status = static_cast<DevStatus*>(workspace);
   ICGS_TRY_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(DevStatus), s));
-  ICGS_TRY_CUDA(launch_tc_selftest(static_cast<const uint16_t*>(A), static_cast<const uint16_t*>(B), N, bf16 != 0, D,
-                                   ws.status, s));
+  ICGS_TRY_CUDA(launch_tc_selftest(static_cast<const uint16_t*>(A), M, static_cast<const uint16_t*>(B), N, bf16 != 0, D,
+                                   D_lanes, ws.status, s));
   return finish(ws, s);
+}
+
+icgs_status icgs_selftest_tc(const void* A, const void* B, int32_t N, int32_t bf16, float* D, void* workspace,
+                             void* stream) {
+  return icgs_selftest_tc_rows(A, 128, B, N, bf16, D, nullptr, workspace, stream);
 }
 
 const char* icgs_last_error(void) { return g_err; }

@@ -138,24 +138,33 @@ __device__ __forceinline__ float target_value(uint16_t raw, bool bf16) {
 }
 
 // Issues the 16 MMAs of one batch (K = 256 pixels) and commits them to mbar.
-template <int NB>
+template <int NB, int MG = kG>
 __device__ __forceinline__ void issue_batch(uint32_t a_addr, uint32_t b_addr, uint32_t d_tmem, uint32_t idesc,
                                             uint64_t* mbar) {
   tc_fence_after();
 #pragma unroll
   for (int ks = 0; ks < kKPix / 16; ++ks) {
     const int kb = ks >> 2, kk = ks & 3;
-    const uint64_t ad = desc_kmajor_sw128(a_addr + kb * (kG * 128) + kk * 32);
+    const uint64_t ad = desc_kmajor_sw128(a_addr + kb * (MG * 128) + kk * 32);
     const uint64_t bd = desc_kmajor_sw128(b_addr + kb * (NB * 128) + kk * 32);
     umma_f16(d_tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
   }
   umma_commit(mbar);
 }
 
-// ---- self-test: D[128 x N] = A[128 x 256] B[N x 256]^T through the same layout and MMA path ----
-template <int NB, bool BF16>
+// Row m of an M = 64 accumulator sits in TMEM lane (m % 16) + 32 (m / 16): rows 16w..16w+15 in
+// the first 16 lanes of warp w's 32-lane quarter (M = 128: row m in lane m).
+template <int MG>
+__device__ __forceinline__ int tmem_lane_of_row(int m) {
+  return MG == 128 ? m : (m & 15) + 32 * (m >> 4);
+}
+
+// ---- self-test: D[M x N] = A[M x 256] B[N x 256]^T through the same layout and MMA path ----
+// (M = 64 or 128). D_lanes, when given, receives the raw contents of all 128 TMEM lanes.
+template <int NB, bool BF16, int MG>
 __global__ void __launch_bounds__(256) k_tc_selftest(const uint16_t* __restrict__ A, const uint16_t* __restrict__ Bm,
-                                                     float* __restrict__ D, DevStatus* status) {
+                                                     float* __restrict__ D, float* __restrict__ D_lanes,
+                                                     DevStatus* status) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -163,9 +172,9 @@ __global__ void __launch_bounds__(256) k_tc_selftest(const uint16_t* __restrict_
   uint8_t* B_s = base + kG * kKPix * 2;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(B_s + NB * kKPix * 2);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
-  for (int e = threadIdx.x; e < kG * kKPix; e += blockDim.x) {
+  for (int e = threadIdx.x; e < MG * kKPix; e += blockDim.x) {
     const int m = e / kKPix, k = e % kKPix;
-    *reinterpret_cast<uint16_t*>(A_s + kmajor_sw128(m, k, kG)) = A[e];
+    *reinterpret_cast<uint16_t*>(A_s + kmajor_sw128(m, k, MG)) = A[e];
   }
   for (int e = threadIdx.x; e < NB * kKPix; e += blockDim.x) {
     const int nn = e / kKPix, k = e % kKPix;
@@ -181,19 +190,25 @@ __global__ void __launch_bounds__(256) k_tc_selftest(const uint16_t* __restrict_
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  if (threadIdx.x == 0) issue_batch<NB>(smem_u32(A_s), smem_u32(B_s), tmem, idesc_f16(kG, NB, BF16), mbar);
+  if (threadIdx.x == 0) issue_batch<NB, MG>(smem_u32(A_s), smem_u32(B_s), tmem, idesc_f16(MG, NB, BF16), mbar);
   const bool ok = mbar_wait_bounded(mbar, 0);
   if (!ok && (threadIdx.x & 31) == 0) atomicOr(&status->flags, kFlagTimeout);
   tc_fence_after();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp < 4 && ok) {
+    const int L = warp * 32 + lane;  // the TMEM lane this thread reads
+    // the row held in lane L, or -1 (M = 64 leaves lanes 16..31 of each quarter unused)
+    const int row = MG == 128 ? L : (lane < 16 ? 16 * warp + lane : -1);
 #pragma unroll
     for (int c0 = 0; c0 < NB; c0 += 16) {
       uint32_t r[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
       tmem_wait_ld();
 #pragma unroll
-      for (int q = 0; q < 16; ++q) D[(warp * 32 + lane) * NB + c0 + q] = __uint_as_float(r[q]);
+      for (int q = 0; q < 16; ++q) {
+        if (row >= 0) D[row * NB + c0 + q] = __uint_as_float(r[q]);
+        if (D_lanes) D_lanes[L * NB + c0 + q] = __uint_as_float(r[q]);
+      }
     }
   }
   if (!ok) mbar_wait_bounded(mbar, 0);
@@ -417,19 +432,26 @@ void launch_blend_accumulate_tc(const Problem& p, int cb, int cam0, const void* 
   else accumulate_tc_dispatch<false>(p, cb, cam0, targets, ws, s);
 }
 
-cudaError_t launch_tc_selftest(const uint16_t* A, const uint16_t* B, int N, bool bf16, float* D, DevStatus* status,
-                               cudaStream_t s) {
-#define ICGS_ST(NB, BF)                                                                                        \
+cudaError_t launch_tc_selftest(const uint16_t* A, int M, const uint16_t* B, int N, bool bf16, float* D, float* D_lanes,
+                               DevStatus* status, cudaStream_t s) {
+#define ICGS_ST(NB, BF, MG)                                                                                    \
   do {                                                                                                         \
-    cudaFuncSetAttribute(k_tc_selftest<NB, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,                 \
+    cudaFuncSetAttribute(k_tc_selftest<NB, BF, MG>, cudaFuncAttributeMaxDynamicSharedMemorySize,             \
                          (int)selftest_smem<NB>());                                                           \
-    k_tc_selftest<NB, BF><<<1, 256, selftest_smem<NB>(), s>>>(A, B, D, status);                                \
+    k_tc_selftest<NB, BF, MG><<<1, 256, selftest_smem<NB>(), s>>>(A, B, D, D_lanes, status);                   \
   } while (0)
-  if (N == 32 && bf16) ICGS_ST(32, true);
-  else if (N == 32) ICGS_ST(32, false);
-  else if (N == 80 && bf16) ICGS_ST(80, true);
-  else if (N == 80) ICGS_ST(80, false);
+#define ICGS_ST_M(NB, BF)                \
+  do {                                   \
+    if (M == 64) ICGS_ST(NB, BF, 64);    \
+    else ICGS_ST(NB, BF, 128);           \
+  } while (0)
+  if (M != 64 && M != 128) return cudaErrorInvalidValue;
+  if (N == 32 && bf16) ICGS_ST_M(32, true);
+  else if (N == 32) ICGS_ST_M(32, false);
+  else if (N == 80 && bf16) ICGS_ST_M(80, true);
+  else if (N == 80) ICGS_ST_M(80, false);
   else return cudaErrorInvalidValue;
+#undef ICGS_ST_M
 #undef ICGS_ST
   return cudaGetLastError();
 }

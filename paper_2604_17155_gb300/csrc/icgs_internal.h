@@ -116,7 +116,7 @@ void launch_blend_accumulate(const Problem& p, int cb, int cam0, const void* tar
 bool tc_accumulate_applies(const Problem& p, int dtype);
 void launch_blend_accumulate_tc(const Problem& p, int cb, int cam0, const void* targets, int dtype,
                                 const Workspace& ws, cudaStream_t s);
-cudaError_t launch_tc_selftest(const uint16_t* A, const uint16_t* B, int N, bool bf16, float* D,
+cudaError_t launch_tc_selftest(const uint16_t* A, int M, const uint16_t* B, int N, bool bf16, float* D, float* D_lanes,
                                DevStatus* status, cudaStream_t s);
 void launch_fold(const Problem& p, const float* means, int cb, bool first, bool want_gram, const Workspace& ws,
                  cudaStream_t s);

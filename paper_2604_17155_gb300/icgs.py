@@ -104,6 +104,8 @@ def load(path: str = LIB_PATH):
     lib.icgs_solve.restype = ctypes.c_int
     lib.icgs_selftest_tc.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, P, P, P]
     lib.icgs_selftest_tc.restype = ctypes.c_int
+    lib.icgs_selftest_tc_rows.argtypes = [P, ctypes.c_int32, P, ctypes.c_int32, ctypes.c_int32, P, P, P, P]
+    lib.icgs_selftest_tc_rows.restype = ctypes.c_int
     lib.icgs_set_stage_timing.argtypes = [ctypes.c_int]
     lib.icgs_set_stage_timing.restype = None
     lib.icgs_last_stage_ms.argtypes = [P, ctypes.c_int]
@@ -483,19 +485,23 @@ def colorize_refine(scene: Scene, cams: Cameras, targets, sh_degree, coeffs, cho
     return coeffs
 
 
-def selftest_tc(A, B, bf16=True):
-    """Diagnostic: A [128,256] @ B [N,256]^T (N = 32 or 80) through the tensor-core path of the
-    16-bit accumulate walk; A and B are 16-bit CUDA tensors. Returns float32 [128, N]."""
+def selftest_tc(A, B, bf16=True, lanes=False):
+    """Diagnostic: A [M,256] @ B [N,256]^T (M = 64 or 128, N = 32 or 80) through the tensor-core
+    path of the 16-bit accumulate walk; A and B are 16-bit CUDA tensors. Returns float32 [M, N],
+    and with lanes=True also the raw contents of the 128 TMEM lanes, float32 [128, N]."""
     torch = _torch()
     lib = load()
     A = A.contiguous()
     B = B.contiguous()
-    N = int(B.shape[0])
-    D = torch.empty((128, N), dtype=torch.float32, device=A.device)
+    M, N = int(A.shape[0]), int(B.shape[0])
+    D = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    DL = torch.full((128, N), float("nan"), dtype=torch.float32, device=A.device) if lanes else None
     ws = _ws.get(A.device, 256)
-    _check(lib.icgs_selftest_tc(ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()), N, 1 if bf16 else 0,
-                                ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(ws.data_ptr()), _stream_ptr(A.device)))
-    return D
+    _check(lib.icgs_selftest_tc_rows(ctypes.c_void_p(A.data_ptr()), M, ctypes.c_void_p(B.data_ptr()), N,
+                                     1 if bf16 else 0, ctypes.c_void_p(D.data_ptr()),
+                                     ctypes.c_void_p(DL.data_ptr() if lanes else 0), ctypes.c_void_p(ws.data_ptr()),
+                                     _stream_ptr(A.device)))
+    return (D, DL) if lanes else D
 
 
 def colorize_backward(scene: Scene, cams: Cameras, targets, sh_degree, coeffs, chol, grad_coeffs, lam=None,

@@ -19,7 +19,7 @@ def test_header_declares_the_calls():
     names = icgs.exported_names()
     for want in ["icgs_workspace_size", "icgs_colorize", "icgs_colorize_backward", "icgs_render_workspace_size",
                  "icgs_render", "icgs_last_error", "icgs_last_required_instances", "icgs_last_stats",
-                 "icgs_colorize_noalloc", "icgs_noalloc_scratch_bytes", "icgs_selftest_tc",
+                 "icgs_colorize_noalloc", "icgs_noalloc_scratch_bytes", "icgs_selftest_tc", "icgs_selftest_tc_rows",
                  "icgs_refine_workspace_size", "icgs_colorize_refine", "icgs_colorize_host_workspace_size",
                  "icgs_colorize_host", "icgs_accumulate", "icgs_solve_workspace_size", "icgs_solve"]:
         assert want in names
