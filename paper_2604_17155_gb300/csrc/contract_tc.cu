@@ -1,7 +1,8 @@
 // contract_tc.cu -- the blend-accumulate walk (Eq. 4-6) with its per-tile contraction on the
 // 5th-generation tensor cores (tcgen05), for 16-bit targets with 16..64 channels.
 //
-// Per tile and batch of G = 128 Gaussians (the MMA's M), the S terms of Eq. 6 summed over the tile's
+// Per tile and batch of G = 128 Gaussians (the MMA's M; 64 for up to 32 channels, which halves the
+// weight operand so that more CTAs fit on an SM), the S terms of Eq. 6 summed over the tile's
 // 256 pixels form a dense product
 //     D[g][n] = sum_p W[g][p] * B[n][p],   W[g][p] = alpha T of Gaussian g at pixel p (Eq. 4),
 // with B's rows 0..KT-1 the tile's target channels and rows KT..KT+15 all ones, so that the same
@@ -11,7 +12,7 @@
 // powers of two -- W by 2^14, the targets so that the tile's largest magnitude lands in
 // [2^14, 2^15) -- which makes every BF16 target exact in FP16, keeps small weights out of FP16's
 // subnormal range, and is undone exactly in the epilogue. One thread issues 16
-// tcgen05.mma (kind::f16, M=128, N=KT+16, K=16, FP32 accumulation in TMEM) and commits them to an
+// tcgen05.mma (kind::f16, M=G, N=KT+16, K=16, FP32 accumulation in TMEM) and commits them to an
 // mbarrier; warps 0-3 then read D back with tcgen05.ld (one Gaussian per thread) and add
 // (V, S_0..S_{KT-1}) to the accumulator with float4 atomics -- one atomic group per (Gaussian, tile).
 //
@@ -221,8 +222,15 @@ __global__ void __launch_bounds__(256) k_tc_selftest(const uint16_t* __restrict_
 }
 
 // ---- the accumulate walk with the tensor-core contraction --------------------------------------
-template <int KT, bool BF16_TARGETS>
-__global__ void __launch_bounds__(256, 2) k_blend_accumulate_tc(
+// MG: Gaussians per batch, the MMA M (128, or 64 for up to 32 channels: half the weight operand, so
+// that more CTAs fit on an SM). TMEM columns: the accumulator width rounded up to a power of two.
+template <int NB>
+__host__ __device__ constexpr uint32_t tmem_cols() {
+  return NB <= 32 ? 32u : (NB <= 64 ? 64u : 128u);
+}
+
+template <int KT, bool BF16_TARGETS, int MG>
+__global__ void __launch_bounds__(256, MG == 64 ? (KT <= 16 ? 4 : 3) : 2) k_blend_accumulate_tc(
     const uint32_t* __restrict__ tile_off, const uint64_t* __restrict__ entries, uint32_t capacity,
     const ProjRec* __restrict__ rec, int64_t n, int width, int height, int tiles_x, int tiles,
     const uint16_t* __restrict__ targets, int K, int cam0, float* __restrict__ acc, int RS,
@@ -231,13 +239,13 @@ __global__ void __launch_bounds__(256, 2) k_blend_accumulate_tc(
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-  uint8_t* A_s = base;                                 // kG x 256, 64 KB
-  uint8_t* B_s = base + kG * kKPix * 2;                // NB x 256
+  uint8_t* A_s = base;                                 // MG x 256 (32 or 64 KB)
+  uint8_t* B_s = base + MG * kKPix * 2;                // NB x 256
   float4* s_geo = reinterpret_cast<float4*>(B_s + NB * kKPix * 2);
-  float4* s_aux = s_geo + kG;
-  float2* s_half = reinterpret_cast<float2*>(s_aux + kG);
-  uint32_t* s_id = reinterpret_cast<uint32_t*>(s_half + kG);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(s_id + kG);
+  float4* s_aux = s_geo + MG;
+  float2* s_half = reinterpret_cast<float2*>(s_aux + MG);
+  uint32_t* s_id = reinterpret_cast<uint32_t*>(s_half + MG);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(s_id + MG);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
   uint32_t* s_tmax = tmem_slot + 1;  // [8]
 
@@ -295,7 +303,7 @@ __global__ void __launch_bounds__(256, 2) k_blend_accumulate_tc(
   const float v_scale_inv = ldexpf(1.0f, -kWScaleExp);
   if (threadIdx.x == 0) mbar_init(mbar, 1);
   if (warp == 0) {
-    tmem_alloc(tmem_slot, kTmemCols);
+    tmem_alloc(tmem_slot, tmem_cols<NB>());
     tmem_relinquish();
   }
   tc_fence_before();
@@ -303,23 +311,23 @@ __global__ void __launch_bounds__(256, 2) k_blend_accumulate_tc(
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t a_addr = smem_u32(A_s), b_addr = smem_u32(B_s);
-  constexpr uint32_t kIdesc = idesc_f16(kG, NB, false);
+  constexpr uint32_t kIdesc = idesc_f16(MG, NB, false);
   const ProjRec* rec_cam = rec + (int64_t)c.j * n;
   float* acc_cam = acc + (int64_t)c.j * acc_cam_stride;
   float T = 1.0f;
   bool done = !c.inside;
   uint32_t npairs = 0, phase = 0;
   bool timed_out = false;
-  for (uint32_t start = 0; start < c.len; start += kG) {
-    const int nb = (int)min((uint32_t)kG, c.len - start);
+  for (uint32_t start = 0; start < c.len; start += MG) {
+    const int nb = (int)min((uint32_t)MG, c.len - start);
     load_batch(reinterpret_cast<const unsigned long long*>(entries), c.b + start, nb, rec_cam, n, c.ox, c.oy, s_geo, s_aux,
                s_half, s_id);
     // the previous batch's MMAs have completed: clear W (16-byte stores), then write its nonzeros
-    for (int i = threadIdx.x; i < kG * kKPix * 2 / 16; i += 256) reinterpret_cast<uint4*>(A_s)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = threadIdx.x; i < MG * kKPix * 2 / 16; i += 256) reinterpret_cast<uint4*>(A_s)[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
     if (!__all_sync(0xFFFFFFFFu, done)) {
 #pragma unroll
-      for (int q = 0; q < kG / 32; ++q) {
+      for (int q = 0; q < MG / 32; ++q) {
         uint32_t bits = warp_hit_bits(s_geo, s_aux, s_half, q * 32, nb, c);
         while (bits && !done) {  // only Gaussians whose box touches this warp's block, in depth order
           const int g = q * 32 + __ffs(bits) - 1;
@@ -329,7 +337,7 @@ __global__ void __launch_bounds__(256, 2) k_blend_accumulate_tc(
           const float w = blend_step(s_geo[g], s_aux[g], c.pxf, c.pyf, T, done, al, ex, cap);
           if (w > 0.0f) {
             ++npairs;
-            *reinterpret_cast<uint16_t*>(A_s + kmajor_sw128(g, p, kG)) = half_bits(w * (float)(1 << kWScaleExp));
+            *reinterpret_cast<uint16_t*>(A_s + kmajor_sw128(g, p, MG)) = half_bits(w * (float)(1 << kWScaleExp));
           }
         }
       }
@@ -337,14 +345,15 @@ __global__ void __launch_bounds__(256, 2) k_blend_accumulate_tc(
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
-    if (threadIdx.x == 0) issue_batch<NB>(a_addr, b_addr, tmem, kIdesc, mbar);
+    if (threadIdx.x == 0) issue_batch<NB, MG>(a_addr, b_addr, tmem, kIdesc, mbar);
     const bool ok = mbar_wait_bounded(mbar, phase);
     phase ^= 1u;
     tc_fence_after();
     if (ok) {
-      // warps w and w+4 share TMEM lanes 32(w%4)..+31 (one Gaussian per thread) and split its chunks
+      // warps w and w+4 share TMEM lanes 32(w%4)..+31 (one Gaussian per thread) and split its chunks;
+      // with MG = 64 only the first 16 lanes of each quarter hold a Gaussian (tmem_lane_of_row)
       const int quarter = warp & 3, part = warp >> 2;
-      const int g = quarter * 32 + lane;
+      const int g = MG == 128 ? quarter * 32 + lane : (lane < 16 ? quarter * 16 + lane : MG);
       const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
       uint32_t vr[16];
       tmem_ld16(trow + (uint32_t)KT, vr);  // the ones block: every column holds V
@@ -387,7 +396,7 @@ __global__ void __launch_bounds__(256, 2) k_blend_accumulate_tc(
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, kTmemCols);
+    tmem_dealloc(tmem, tmem_cols<NB>());
   }
 }
 
@@ -395,18 +404,19 @@ template <int NB>
 constexpr size_t selftest_smem() {
   return 1024 + (size_t)kG * kKPix * 2 + (size_t)NB * kKPix * 2 + 16;
 }
-template <int KT>
+template <int KT, int MG>
 constexpr size_t tc_smem() {
-  return 1024 + (size_t)kG * kKPix * 2 + (size_t)(KT + 16) * kKPix * 2 + (size_t)kG * (16 + 16 + 8 + 4) + 64;
+  return 1024 + (size_t)MG * kKPix * 2 + (size_t)(KT + 16) * kKPix * 2 + (size_t)MG * (16 + 16 + 8 + 4) + 64;
 }
 
 template <int KT, bool BF16_TARGETS>
 void accumulate_tc(const Problem& p, int cb, int cam0, const void* targets, const Workspace& ws, cudaStream_t s) {
-  const size_t smem = tc_smem<KT>();
-  cudaFuncSetAttribute(k_blend_accumulate_tc<KT, BF16_TARGETS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  constexpr int MG = KT <= 32 ? 64 : 128;
+  const size_t smem = tc_smem<KT, MG>();
+  cudaFuncSetAttribute(k_blend_accumulate_tc<KT, BF16_TARGETS, MG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
   const int64_t stride = p.L == 0 ? 0 : p.n * (int64_t)p.acc_stride;
-  k_blend_accumulate_tc<KT, BF16_TARGETS><<<cb * p.tiles, 256, smem, s>>>(
+  k_blend_accumulate_tc<KT, BF16_TARGETS, MG><<<cb * p.tiles, 256, smem, s>>>(
       ws.tile_off, ws.entries, p.capacity, ws.rec, p.n, p.width, p.height, p.tiles_x, p.tiles,
       static_cast<const uint16_t*>(targets), p.K, cam0, ws.acc, p.acc_stride, stride, ws.status);
   note_launches(1);

@@ -111,8 +111,10 @@ def test_colorize_sh3_rgb(icgs, prec):
 
 
 # K = 1, 2: the two-pixel walk; 12: one 15-channel chunk; 20: a 16-channel chunk and a 7-channel
-# chunk; 16 and 64: the tensor-core walk (MIXED) and 16-channel chunks (PLAIN)
-@pytest.mark.parametrize("K,dtype", [(1, "f32"), (2, "f32"), (12, "f32"), (20, "f32"), (16, "f16"), (64, "bf16")])
+# chunk; 16, 24 and 64: the tensor-core walk (MIXED; M = 64 batches up to 32 channels, M = 128
+# beyond) and 16-channel chunks (PLAIN)
+@pytest.mark.parametrize("K,dtype", [(1, "f32"), (2, "f32"), (12, "f32"), (20, "f32"), (16, "f16"), (24, "bf16"),
+                                     (64, "bf16")])
 def test_colorize_channels_and_dtypes(icgs, K, dtype):
     sc, cams = _mid_scene(n=2500, seed=21, n_cams=12, w=96, h=72)
     rng = np.random.default_rng(22)
