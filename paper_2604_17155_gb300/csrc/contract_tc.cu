@@ -5,14 +5,14 @@
 // weight operand so that more CTAs fit on an SM), the S terms of Eq. 6 summed over the tile's
 // 256 pixels form a dense product
 //     D[g][n] = sum_p W[g][p] * B[n][p],   W[g][p] = alpha T of Gaussian g at pixel p (Eq. 4),
-// with B's rows 0..KT-1 the tile's target channels and rows KT..KT+15 all ones, so that the same
+// with B's rows 0..KT-1 the tile's target channels and the rows after them all ones, so that the same
 // product also yields V = sum_p W[g][p] (Eq. 5). The threads evaluate W exactly like the CUDA-core
 // walk (walk.cuh) and store it as FP16 into a K-major, 128-byte-swizzled shared-memory operand; the
 // tile's targets (BF16 or FP16) are transposed once into B as FP16. Both operands are scaled by
 // powers of two -- W by 2^14, the targets so that the tile's largest magnitude lands in
 // [2^14, 2^15) -- which makes every BF16 target exact in FP16, keeps small weights out of FP16's
 // subnormal range, and is undone exactly in the epilogue. One thread issues 16
-// tcgen05.mma (kind::f16, M=G, N=KT+16, K=16, FP32 accumulation in TMEM) and commits them to an
+// tcgen05.mma (kind::f16, M=G, N=KT+8, K=16, FP32 accumulation in TMEM) and commits them to an
 // mbarrier; warps 0-3 then read D back with tcgen05.ld (one Gaussian per thread) and add
 // (V, S_0..S_{KT-1}) to the accumulator with float4 atomics -- one atomic group per (Gaussian, tile).
 //
@@ -224,18 +224,25 @@ __global__ void __launch_bounds__(256) k_tc_selftest(const uint16_t* __restrict_
 // ---- the accumulate walk with the tensor-core contraction --------------------------------------
 // MG: Gaussians per batch, the MMA M (128, or 64 for up to 32 channels: half the weight operand, so
 // that more CTAs fit on an SM). TMEM columns: the accumulator width rounded up to a power of two.
+// Columns of B and of the accumulator: the KT target channels, then rows of ones that yield V (16
+// for M = 128, whose N must be a multiple of 16; 8 for M = 64, which allows multiples of 8).
+template <int KT, int MG>
+__host__ __device__ constexpr int tc_cols() {
+  return KT + (MG == 64 ? 8 : 16);
+}
+
 template <int NB>
 __host__ __device__ constexpr uint32_t tmem_cols() {
   return NB <= 32 ? 32u : (NB <= 64 ? 64u : 128u);
 }
 
 template <int KT, bool BF16_TARGETS, int MG>
-__global__ void __launch_bounds__(256, MG == 64 ? (KT <= 16 ? 4 : 3) : 2) k_blend_accumulate_tc(
+__global__ void __launch_bounds__(256, MG == 64 ? (KT <= 32 ? 4 : 3) : 2) k_blend_accumulate_tc(
     const uint32_t* __restrict__ tile_off, const uint64_t* __restrict__ entries, uint32_t capacity,
     const ProjRec* __restrict__ rec, int64_t n, int width, int height, int tiles_x, int tiles,
     const uint16_t* __restrict__ targets, int K, int cam0, float* __restrict__ acc, int RS,
     int64_t acc_cam_stride, DevStatus* status) {
-  constexpr int NB = KT + 16;  // target channels + 16 rows of ones (V)
+  constexpr int NB = tc_cols<KT, MG>();  // target channels + rows of ones (V)
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -256,7 +263,7 @@ __global__ void __launch_bounds__(256, MG == 64 ? (KT <= 16 ? 4 : 3) : 2) k_blen
   const int p = (c.py - ty0) * kTile + (c.px - tx0);  // this thread's pixel index in the tile (MMA k)
 
   // B: the tile's targets, transposed to [channel][pixel] and scaled by 2^s (the tile's largest
-  // magnitude in [2^14, 2^15)), then 16 rows of ones
+  // magnitude in [2^14, 2^15)), then the rows of ones
   float t_scale_inv;
   {
     const uint16_t* src = targets + ((((int64_t)(cam0 + c.j) * height + c.py) * width + c.px) * K);
@@ -350,35 +357,47 @@ __global__ void __launch_bounds__(256, MG == 64 ? (KT <= 16 ? 4 : 3) : 2) k_blen
     phase ^= 1u;
     tc_fence_after();
     if (ok) {
-      // warps w and w+4 share TMEM lanes 32(w%4)..+31 (one Gaussian per thread) and split its chunks;
-      // with MG = 64 only the first 16 lanes of each quarter hold a Gaussian (tmem_lane_of_row)
+      // warps w and w+4 share TMEM lanes 32(w%4)..+31 (one Gaussian per thread) and split its 16-column
+      // chunks; with MG = 64 only the first 16 lanes of each quarter hold a Gaussian (tmem_lane_of_row).
+      // The accumulator streams through registers a chunk at a time: chunk c adds the float4 groups
+      // 4c..4c+3 of the row (V, S_0, S_1, ..) and carries its last column into group 4c+4. Every
+      // tcgen05.ld is warp-uniform; only the atomics depend on the thread's Gaussian.
       const int quarter = warp & 3, part = warp >> 2;
       const int g = MG == 128 ? quarter * 32 + lane : (lane < 16 ? quarter * 16 + lane : MG);
       const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
-      uint32_t vr[16];
-      tmem_ld16(trow + (uint32_t)KT, vr);  // the ones block: every column holds V
-      float v[KT + 4];
-      {
-        uint32_t r[16];
+      constexpr int kCh = KT / 16;           // 16-column chunks of S
+      constexpr int kHalf = (kCh + 1) / 2;   // chunks of the warps 0-3
+      if (part == 0 || kCh > kHalf) {        // warp-uniform
+        uint32_t vr[16], r[16];
+        tmem_ld16(trow + (uint32_t)KT, vr);  // the ones block: every column holds V
+        if (part == 1) tmem_ld16(trow + (uint32_t)(16 * (kHalf - 1)), r);  // the column before this part
+        tmem_wait_ld();
+        const float V = __uint_as_float(vr[0]) * v_scale_inv;
+        float carry = part == 0 ? V : __uint_as_float(r[15]) * t_scale_inv;
+        const bool add = g < nb && V > 0.0f;
+        float* dst = acc_cam + (int64_t)(add ? s_id[g] : 0u) * RS;
+        const int c_begin = part == 0 ? 0 : kHalf, c_end = part == 0 ? kHalf : kCh;
 #pragma unroll
-        for (int c0 = 0; c0 < KT; c0 += 16) {
-          tmem_ld16(trow + (uint32_t)c0, r);
+        for (int c = 0; c < kCh; ++c) {
+          if (c < c_begin || c >= c_end) continue;  // warp-uniform
+          tmem_ld16(trow + (uint32_t)(16 * c), r);
           tmem_wait_ld();
+          float sv[16];
 #pragma unroll
-          for (int q = 0; q < 16; ++q) v[1 + c0 + q] = __uint_as_float(r[q]) * t_scale_inv;
+          for (int q = 0; q < 16; ++q) sv[q] = __uint_as_float(r[q]) * t_scale_inv;
+          if (add) {
+            float* d = dst + 16 * c;
+            if (16 * c < RS) atomicAdd(reinterpret_cast<float4*>(d), make_float4(carry, sv[0], sv[1], sv[2]));
+            if (16 * c + 4 < RS) atomicAdd(reinterpret_cast<float4*>(d + 4), make_float4(sv[3], sv[4], sv[5], sv[6]));
+            if (16 * c + 8 < RS) atomicAdd(reinterpret_cast<float4*>(d + 8), make_float4(sv[7], sv[8], sv[9], sv[10]));
+            if (16 * c + 12 < RS)
+              atomicAdd(reinterpret_cast<float4*>(d + 12), make_float4(sv[11], sv[12], sv[13], sv[14]));
+          }
+          carry = sv[15];
         }
-      }
-      tmem_wait_ld();
-      v[0] = __uint_as_float(vr[0]) * v_scale_inv;
-#pragma unroll
-      for (int q = KT + 1; q < KT + 4; ++q) v[q] = 0.0f;
-      if (g < nb && v[0] > 0.0f) {
-        float* dst = acc_cam + (int64_t)s_id[g] * RS;
-        constexpr int kChunks = (KT + 4) / 4;
-#pragma unroll
-        for (int q = 0; q < kChunks; ++q)
-          if ((q < (kChunks + 1) / 2) == (part == 0) && 4 * q < RS)
-            atomicAdd(reinterpret_cast<float4*>(dst + 4 * q), make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+        // the last group (S_{KT-1}, 0, 0, 0), by the warps that folded the last chunk
+        if (add && part == (kCh > kHalf ? 1 : 0) && 16 * kCh < RS)
+          atomicAdd(reinterpret_cast<float4*>(dst + 16 * kCh), make_float4(carry, 0.0f, 0.0f, 0.0f));
       }
     }
     if (!ok) timed_out = true;
@@ -406,12 +425,12 @@ constexpr size_t selftest_smem() {
 }
 template <int KT, int MG>
 constexpr size_t tc_smem() {
-  return 1024 + (size_t)MG * kKPix * 2 + (size_t)(KT + 16) * kKPix * 2 + (size_t)MG * (16 + 16 + 8 + 4) + 64;
+  return 1024 + (size_t)MG * kKPix * 2 + (size_t)tc_cols<KT, MG>() * kKPix * 2 + (size_t)MG * (16 + 16 + 8 + 4) + 64;
 }
 
 template <int KT, bool BF16_TARGETS>
 void accumulate_tc(const Problem& p, int cb, int cam0, const void* targets, const Workspace& ws, cudaStream_t s) {
-  constexpr int MG = KT <= 32 ? 64 : 128;
+  constexpr int MG = 64;
   const size_t smem = tc_smem<KT, MG>();
   cudaFuncSetAttribute(k_blend_accumulate_tc<KT, BF16_TARGETS, MG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
