@@ -55,7 +55,7 @@ MEASURED_TRAFFIC = {
     ("relight", "cuda-core"): {"bytes_per_scene": 2147759872 + 288225536, "source_sha": "38dccc2170c592a2"},
     # features: a 10-camera launch captured and scaled by 150/10 cameras (the targets, the per-camera
     # tile lists and the per-camera accumulator re-streaming all grow with the camera count)
-    ("features", "tensor-core"): {"bytes_per_scene": 15 * (3254054656 + 1458599680), "source_sha": "939019ec3e09d843"},
+    ("features", "tensor-core"): {"bytes_per_scene": 15 * (3256890368 + 1464636160), "source_sha": "b15d7e67ffa7ffb7"},
 }
 
 
