@@ -10,7 +10,7 @@ import pytest
 from oracle import oracle as O
 from paper_2604_17155_gb300 import workloads as W
 
-from _parity import TOL_FP32, coefficient_report, to_np
+from _parity import TOL_BF16, TOL_FP32, coefficient_report, to_np
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -59,6 +59,37 @@ def test_relight_fullsize_sampled():
     # every other sampled Gaussian is held to the flip-aware bound
     assert rep["checked"] >= 5
     assert rep["max_checked"] <= TOL_FP32
+    assert rep["bound_excess"] <= 0
+
+
+def test_masks_fullsize_sampled_tensor_core():
+    """The tensor-core walk (16 FP16 channels, MIXED) on the full-size segmentation scene:
+    3,000,000 Gaussians at 1600x1060, here with 4 cameras of the same rig shape. Targets are smooth
+    16-channel fields from the input generator, rounded to FP16 before either side sees them; the
+    oracle walks only the sampled Gaussians' candidate pixels (Eq. 5-6) and solves at L = 0."""
+    from paper_2604_17155_gb300 import build as B
+    B.build()
+    from paper_2604_17155_gb300 import icgs
+    scene = W.make_scene("segmentation", 2000)
+    cams = W.make_cameras("segmentation", n_cams=4)
+    t = W.fourier_fields(cams.n, cams.height, cams.width, 16, seed=2005, n_modes=4)
+    dev = "cuda"
+    gs = icgs.Scene.from_workload(scene, dev)
+    gc = icgs.Cameras.from_workload(cams)
+    tt = torch.tensor(t, device=dev).half()
+    t_exact = tt.float().cpu().numpy().astype(np.float64)
+    del t
+    c, status, _ = icgs.colorize(gs, gc, tt, 0, precision="mixed")
+    c = to_np(c)
+    st = to_np(status)
+    rng = np.random.default_rng(2006)
+    seen = np.where(st != icgs.GAUSSIAN_UNSEEN)[0]
+    sample = np.sort(rng.choice(seen, N_SAMPLE, replace=False))
+    ref = _sampled_oracle(scene, cams, t_exact, 0, sample)
+    rep, err, checked = coefficient_report(c[sample], ref, tol=TOL_BF16)
+    print("masks full size (tensor-core walk)", rep, icgs.last_stats())
+    assert rep["checked"] >= 5
+    assert rep["max_checked"] <= TOL_BF16
     assert rep["bound_excess"] <= 0
 
 
