@@ -466,7 +466,7 @@ __device__ __forceinline__ void exact_fold(const float* __restrict__ acc, int64_
 // a non-positive pivot, the Gaussian is solved in FP64.
 // NR: right-hand sides solved together (3 for RGB, else 4; the last group is padded with zeros)
 template <int B, bool MIXED, int NR>
-__global__ void __launch_bounds__(kSolveThreads) k_solve(
+__global__ void __launch_bounds__(kSolveThreads, 5) k_solve(
     int64_t n, int K, const float* __restrict__ G, const float* __restrict__ Glo,
     const float* __restrict__ bvec, const float* __restrict__ blo, const float* __restrict__ wsum,
     const float* __restrict__ wlo, const float* __restrict__ lam, float cond_tau, float refold_tau,
