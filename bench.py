@@ -230,6 +230,13 @@ def make_targets(workload, scene, cams, coeffs, gs, gc, dev, icgs):
     return t, 0
 
 
+def workload_config(workload, n, n_cams, width, height, L, K, dtype_name, precision, world, target_bytes):
+    """The `config` object of the JSON line; both arms describe the same workload with it."""
+    return {"workload": f"{workload}: {n} Gaussians, {n_cams} cameras {width}x{height}, L={L}, {K} channels {dtype_name}",
+            "precision": precision, "parallelism": f"replicas x{world}",
+            "l2": f"inputs larger than L2 ({target_bytes / 1e6:.0f} MB of targets per step)"}
+
+
 def run_reference(args, rank, world):
     """The oracle on the host cores, one bounded camera sample per step."""
     if rank != 0:
@@ -258,7 +265,8 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "relight: 200k Gaussians, 100 cameras 800x800, L=3 RGB", "precision": "fp64 oracle"},
+            "config": workload_config("relight", scene.n, cams.n, cams.width, cams.height, 3, 3, "float32", args.precision,
+                                      world, cams.n * cams.width * cams.height * 3 * 4),
             "cpu_baseline": {"value": ms, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -450,10 +458,8 @@ def run_icgs(args, rank, world, local_rank):
         "metric": METRIC, "value": ms_scene, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_max / args.steps, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if targets.dtype == torch.float32 else ("f16" if tc else "f32"), "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {scene.n} Gaussians, {cams.n} cameras {cams.width}x{cams.height}, "
-                               f"L={L}, {K} channels {str(targets.dtype).replace('torch.', '')}",
-                   "precision": args.precision, "parallelism": f"replicas x{world}",
-                   "l2": f"inputs larger than L2 ({target_bytes / 1e6:.0f} MB of targets per step)"},
+        "config": workload_config(args.workload, scene.n, cams.n, cams.width, cams.height, L, K,
+                                  str(targets.dtype).replace("torch.", ""), args.precision, world, target_bytes),
         "roofline": roof,
         "e2e": {"value": e2e_max / (args.steps * world), "unit": UNIT, "h2d_bytes_per_step": target_bytes,
                 "d2h_bytes_per_step": scene.n * B * K * 4 + scene.n, "call": "icgs_colorize_host"},
