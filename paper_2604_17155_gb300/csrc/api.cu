@@ -753,9 +753,13 @@ icgs_status icgs_colorize_refine(const icgs_scene* scene, const icgs_cameras* ca
       if (!(one_pass && step > 0))
         if ((st = bin_pass(p, scene, cb, false, wp, s)) != ICGS_OK) return st;
       launch_payload_render(p, scene->means, coeffs_inout, cb, wp, s);  // Alg. 1 line 8: render
-      launch_blend_render(p, cb, 0, wp, ws.img, s);
-      g_timer.mark(kPayload, s);
-      launch_blend_accumulate(p, cb, cam0, targets->data, (int)targets->dtype, ws.img, wp, s);  // line 9
+      if (launch_blend_refine(p, cb, cam0, targets->data, (int)targets->dtype, wp, s)) {  // lines 8-9, one walk
+        g_timer.mark(kPayload, s);
+      } else {
+        launch_blend_render(p, cb, 0, wp, ws.img, s);
+        g_timer.mark(kPayload, s);
+        launch_blend_accumulate(p, cb, cam0, targets->data, (int)targets->dtype, ws.img, wp, s);  // line 9
+      }
       g_timer.mark(kBlend, s);
       if (p.L > 0) {
         launch_fold(p, scene->means, cb, cam0 == 0, false, wp, s);

@@ -789,6 +789,191 @@ __global__ void __launch_bounds__(kThreads2, KC <= 2 ? 10 : 8) k_blend_adjoint2(
   }
 }
 
+// One refinement walk (Alg. 1 lines 8-9) for up to 3 channels, two pixels per thread: pass 1
+// renders the current colours of the thread's pixels (as k_blend_render2), pass 2 accumulates the
+// residual targets t - img (as k_blend_accumulate2 with a rendered image subtracted), over the tile
+// list sorted once. Same arithmetic as the two separate walks, without the image round trip.
+template <int KC>
+__global__ void __launch_bounds__(kThreads2, 10) k_blend_refine2(
+    const uint32_t* __restrict__ tile_off, const uint64_t* __restrict__ entries, uint32_t capacity,
+    const ProjRec* __restrict__ rec, int64_t n, int width, int height, int tiles_x, int tiles,
+    const void* __restrict__ targets, int dtype, int K, int cam0, const float* __restrict__ payload,
+    float* __restrict__ acc, int RS, int64_t acc_cam_stride, DevStatus* status) {
+  static_assert(KC <= 3, "two pixels per thread: up to 3 channels");
+  constexpr int NV = KC + 1;
+  constexpr int NP = NextPow2<NV>::value;
+  constexpr int NP2 = 2 * NP;
+  constexpr int SHIFT2 = 5 - Log2<NP2>::value;
+  __shared__ float4 s_geo[kBatch], s_aux[kBatch];
+  __shared__ float2 s_half[kBatch];
+  __shared__ uint32_t s_id[kBatch];
+  __shared__ float s_acc[kBatch][NV];
+  __shared__ float s_col[kBatch][KC];
+  __shared__ unsigned long long s_keys[kWalkSortCap];
+  const TileCtx c = tile_ctx<2>(tile_off, capacity, tiles, tiles_x, width, height);
+  const unsigned long long* list = stage_tile_list<kThreads2>(entries, c.b, c.len, s_keys);
+  const int lane = threadIdx.x & 31;
+  const bool inside1 = c.inside && c.py + 4 < height;
+  const float pyf1 = c.pyf + 4.0f;
+  const ProjRec* rec_cam = rec + (int64_t)c.j * n;
+  const float* pay_cam = payload + (int64_t)c.j * n * K;
+  // pass 1: the current render of both pixels
+  float img0[KC], img1[KC];
+#pragma unroll
+  for (int k = 0; k < KC; ++k) img0[k] = img1[k] = 0.0f;
+  {
+    float T0 = 1.0f, T1 = 1.0f;
+    bool done0 = !c.inside, done1 = !inside1;
+    for (uint32_t start = 0; start < c.len; start += kBatch) {
+      const int nb = (int)min((uint32_t)kBatch, c.len - start);
+      __syncthreads();
+      load_batch(list, start, nb, rec_cam, n, c.ox, c.oy, s_geo, s_aux, s_half, s_id);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nb * KC; idx += kThreads2) {
+        const int g = idx / KC, k = idx - g * KC;
+        s_col[g][k] = k < K ? pay_cam[(int64_t)s_id[g] * K + k] : 0.0f;
+      }
+      __syncthreads();
+      if (!__all_sync(kFull, done0 && done1)) {
+#pragma unroll
+        for (int half = 0; half < kBatch / 32; ++half) {
+          uint32_t bits = warp_hit_bits(s_geo, s_aux, s_half, half * 32, nb, c);
+          while (bits && !(done0 && done1)) {
+            const int g = half * 32 + __ffs(bits) - 1;
+            bits &= bits - 1;
+            const float4 geo = s_geo[g], aux = s_aux[g];
+            float al, ex;
+            bool cap;
+            if (!done0) {
+              const float w = blend_step(geo, aux, c.pxf, c.pyf, T0, done0, al, ex, cap);
+              if (w > 0.0f) {
+#pragma unroll
+                for (int k = 0; k < KC; ++k) img0[k] = fmaf(w, s_col[g][k], img0[k]);
+              }
+            }
+            if (!done1) {
+              const float w = blend_step(geo, aux, c.pxf, pyf1, T1, done1, al, ex, cap);
+              if (w > 0.0f) {
+#pragma unroll
+                for (int k = 0; k < KC; ++k) img1[k] = fmaf(w, s_col[g][k], img1[k]);
+              }
+            }
+          }
+        }
+      }
+      if (__syncthreads_and(done0 && done1)) break;
+    }
+  }
+  // residual targets t - img
+  float tv0[KC], tv1[KC];
+#pragma unroll
+  for (int k = 0; k < KC; ++k) tv0[k] = tv1[k] = 0.0f;
+  if (c.inside) {
+    const int64_t base = (((int64_t)(cam0 + c.j) * height + c.py) * width + c.px) * K;
+    const int64_t row = (int64_t)width * K;
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      if (k < K) {
+        tv0[k] = load_target(targets, base + k, dtype) - img0[k];
+        if (inside1) tv1[k] = load_target(targets, base + 4 * row + k, dtype) - img1[k];
+      }
+    }
+  }
+  // pass 2: the accumulate walk of k_blend_accumulate2 on the residuals
+  const int m = lane >> SHIFT2;
+  const bool mh = (m & NP) != 0;
+  const int mk = m & (NP - 1);
+  float u0[NP], u1[NP];
+  u0[0] = u1[0] = 1.0f;
+#pragma unroll
+  for (int k = 1; k < NP; ++k) {
+    u0[k] = k <= KC ? tv0[k <= KC ? k - 1 : 0] : 0.0f;
+    u1[k] = k <= KC ? tv1[k <= KC ? k - 1 : 0] : 0.0f;
+  }
+#pragma unroll
+  for (int bit = 1; bit < NP; bit <<= 1) {  // u[k] <- u[k ^ mk], one conditional swap per bit of mk
+    const bool sw = (mk & bit) != 0;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      if (k & bit) continue;
+      const float x0 = u0[k], y0 = u0[k | bit], x1 = u1[k], y1 = u1[k | bit];
+      u0[k] = sw ? y0 : x0;
+      u0[k | bit] = sw ? x0 : y0;
+      u1[k] = sw ? y1 : x1;
+      u1[k | bit] = sw ? x1 : y1;
+    }
+  }
+  for (int k = threadIdx.x; k < kBatch * NV; k += kThreads2) (&s_acc[0][0])[k] = 0.0f;
+  float* acc_cam = acc + (int64_t)c.j * acc_cam_stride;
+  float T0 = 1.0f, T1 = 1.0f;
+  bool done0 = !c.inside, done1 = !inside1;
+  uint32_t npairs = 0;
+  for (uint32_t start = 0; start < c.len; start += kBatch) {
+    const int nb = (int)min((uint32_t)kBatch, c.len - start);
+    __syncthreads();
+    load_batch(list, start, nb, rec_cam, n, c.ox, c.oy, s_geo, s_aux, s_half, s_id);
+    __syncthreads();
+    if (!__all_sync(kFull, done0 && done1)) {
+#pragma unroll
+      for (int half = 0; half < kBatch / 32; ++half) {
+        uint32_t bits = warp_hit_bits<true>(s_geo, s_aux, s_half, half * 32, nb, c);
+        while (bits) {
+          const int g1 = half * 32 + __ffs(bits) - 1;
+          bits &= bits - 1;
+          const int g2 = bits ? half * 32 + __ffs(bits) - 1 : -1;
+          bits &= bits - 1;
+          float w10 = 0.0f, w11 = 0.0f, w20 = 0.0f, w21 = 0.0f, al, ex;
+          bool cap;
+          {
+            const float4 geo = s_geo[g1], aux = s_aux[g1];
+            if (!done0) w10 = blend_step(geo, aux, c.pxf, c.pyf, T0, done0, al, ex, cap);
+            if (!done1) w11 = blend_step(geo, aux, c.pxf, pyf1, T1, done1, al, ex, cap);
+          }
+          if (g2 >= 0) {
+            const float4 geo = s_geo[g2], aux = s_aux[g2];
+            if (!done0) w20 = blend_step(geo, aux, c.pxf, c.pyf, T0, done0, al, ex, cap);
+            if (!done1) w21 = blend_step(geo, aux, c.pxf, pyf1, T1, done1, al, ex, cap);
+          }
+          const float w1 = __fadd_rn(w10, w11), w2 = __fadd_rn(w20, w21);
+          if (__any_sync(kFull, w1 > 0.0f || w2 > 0.0f)) {
+            npairs += (w10 > 0.0f) + (w11 > 0.0f) + (w20 > 0.0f) + (w21 > 0.0f);
+            const float a0 = mh ? w20 : w10, a1 = mh ? w21 : w11;
+            const float c0 = mh ? w10 : w20, c1 = mh ? w11 : w21;
+            float v[NP2];
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+              v[k] = __fmaf_rn(a0, u0[k], __fmul_rn(a1, u1[k]));
+              v[NP + k] = __fmaf_rn(c0, u0[k], __fmul_rn(c1, u1[k]));
+            }
+            const float r = warp_permuted_reduce<NP2>(v);  // the warp sum of value index m
+            const int gg = mh ? g2 : g1;
+            if ((lane & ((1 << SHIFT2) - 1)) == 0 && mk < NV && gg >= 0) atomicAdd(&s_acc[gg][mk], r);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nb) {
+      const int g = threadIdx.x;
+      if (s_acc[g][0] > 0.0f) {
+        float* dst = acc_cam + (int64_t)s_id[g] * RS;
+        if (KC == 3 && K == 3) {
+          atomicAdd(reinterpret_cast<float4*>(dst), make_float4(s_acc[g][0], s_acc[g][1], s_acc[g][2], s_acc[g][3]));
+        } else {
+          atomicAdd(dst, s_acc[g][0]);
+#pragma unroll
+          for (int k = 0; k < KC; ++k)
+            if (k < K) atomicAdd(dst + 1 + k, s_acc[g][k + 1]);
+        }
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s_acc[g][k] = 0.0f;
+      }
+    }
+    if (__syncthreads_and(done0 && done1)) break;
+  }
+  add_pair_count(npairs, status);
+}
+
 template <int KC>
 void accumulate_chunk(const Problem& p, int cb, int cam0, const void* targets, int dtype, int k0,
                       const float* sub_img, const Workspace& ws, cudaStream_t s) {
@@ -855,6 +1040,25 @@ void launch_blend_render(const Problem& p, int cb, int cam0, const Workspace& ws
     else if (kc <= 8) render_chunk<8>(p, cb, cam0, k0, ws, images, s);
     else render_chunk<16>(p, cb, cam0, k0, ws, images, s);
   }
+}
+
+// The refinement walk (render of the current colours, then accumulation of the residual targets)
+// in one kernel for up to 3 channels; returns false when the channel count needs the two walks.
+bool launch_blend_refine(const Problem& p, int cb, int cam0, const void* targets, int dtype, const Workspace& ws,
+                         cudaStream_t s) {
+  if (p.K > 3) return false;
+  const int64_t stride = p.L == 0 ? 0 : p.n * (int64_t)p.acc_stride;
+#define ICGS_REF(KC)                                                                                         \
+  k_blend_refine2<KC><<<cb * p.tiles, kThreads2, 0, s>>>(ws.tile_off, ws.entries, p.capacity, ws.rec, p.n,     \
+                                                          p.width, p.height, p.tiles_x, p.tiles, targets, dtype, \
+                                                          p.K, cam0, ws.payload, ws.acc, p.acc_stride, stride,   \
+                                                          ws.status)
+  if (p.K == 1) ICGS_REF(1);
+  else if (p.K == 2) ICGS_REF(2);
+  else ICGS_REF(3);
+#undef ICGS_REF
+  note_launches(1);
+  return true;
 }
 
 void launch_blend_adjoint(const Problem& p, int cb, int cam0, const void* targets, int dtype,

@@ -110,6 +110,8 @@ void launch_scatter(const Problem& p, int cb, const Workspace& ws, cudaStream_t 
 void launch_tile_sort(const Problem& p, int cb, bool sort_all, const Workspace& ws, cudaStream_t s);
 // sub_img (nullable, float32 [cb,H,W,K] of this pass's cameras): accumulate t - img instead of t
 // (refinement); forces the CUDA-core walk.
+bool launch_blend_refine(const Problem& p, int cb, int cam0, const void* targets, int dtype, const Workspace& ws,
+                         cudaStream_t s);
 void launch_blend_accumulate(const Problem& p, int cb, int cam0, const void* targets, int dtype,
                              const float* sub_img, const Workspace& ws, cudaStream_t s);
 // Tensor-core contraction of the accumulate walk (MIXED precision, 16-bit targets, 16..64 channels).

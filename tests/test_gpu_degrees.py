@@ -158,3 +158,22 @@ def test_render_and_adjoint_channel_counts(icgs, K):
           f"dL/do p99 rel {np.percentile(eo, 99):.2e} over {checked.sum()}")
     assert np.percentile(dt, 99.9) <= 1e-3 * np.abs(gt_ref).max()
     assert np.percentile(eo, 99) <= 1e-2
+
+
+def test_refinement_five_channels(icgs):
+    """Refinement with 5 channels: the render and the residual accumulation run as two walks (the
+    fused refinement walk covers up to 3 channels), against the oracle's refinement steps."""
+    L, K = 1, 5
+    sc, cams = _scene(2000, 321, 12, 96, 72)
+    t = O.render(sc, cams, W.sh_coefficients(sc.n, L, K, seed=331), L).astype(np.float32)
+    t64 = t.astype(np.float64)
+    col = O.colorize(sc, cams, t64, L)
+    ref = O.refine(sc, cams, t64, L, None, col, 2)
+    gs, gc = _gpu(icgs, sc, cams)
+    tt = torch.tensor(t, device=DEV)
+    c, status, chol = icgs.colorize(gs, gc, tt, L)
+    icgs.colorize_refine(gs, gc, tt, L, c, chol, 2)
+    rep, err, checked = coefficient_report(to_np(c), dict(col, c=ref), tol=1e-3)
+    print(f"refine K={K}", rep)
+    assert rep["p99_checked"] <= 1e-3
+    assert rep["bound_excess"] <= 0
