@@ -52,10 +52,10 @@ KERNEL_SOURCES = {
 }
 MEASURED_TRAFFIC = {
     # relight, 100 cameras: one full-size launch captured (profiles/blend_accumulate_relight.md)
-    ("relight", "cuda-core"): {"bytes_per_scene": 2147759872 + 288225536, "source_sha": "c3e11e5b0bc827b0"},
+    ("relight", "cuda-core"): {"bytes_per_scene": 2148486912 + 288519424, "source_sha": "be1ccf7fce8493cc"},
     # features: a 10-camera launch captured and scaled by 150/10 cameras (the targets, the per-camera
     # tile lists and the per-camera accumulator re-streaming all grow with the camera count)
-    ("features", "tensor-core"): {"bytes_per_scene": 15 * (3256890368 + 1464636160), "source_sha": "b15d7e67ffa7ffb7"},
+    ("features", "tensor-core"): {"bytes_per_scene": 15 * (3255703296 + 1463516416), "source_sha": "a52d454326bdcc64"},
 }
 
 
