@@ -177,3 +177,43 @@ def test_refinement_five_channels(icgs):
     print(f"refine K={K}", rep)
     assert rep["p99_checked"] <= 1e-3
     assert rep["bound_excess"] <= 0
+
+
+@pytest.mark.parametrize("K", [1, 2])
+def test_refinement_fused_walk_channel_counts(icgs, K):
+    """The fused refinement walk (render and residual accumulation in one kernel) for 1 and 2
+    channels, against the oracle's refinement steps."""
+    L = 1
+    sc, cams = _scene(2000, 341 + K, 12, 96, 72)
+    t = O.render(sc, cams, W.sh_coefficients(sc.n, L, K, seed=351 + K), L).astype(np.float32)
+    t64 = t.astype(np.float64)
+    col = O.colorize(sc, cams, t64, L)
+    ref = O.refine(sc, cams, t64, L, None, col, 2)
+    gs, gc = _gpu(icgs, sc, cams)
+    tt = torch.tensor(t, device=DEV)
+    c, status, chol = icgs.colorize(gs, gc, tt, L)
+    icgs.colorize_refine(gs, gc, tt, L, c, chol, 2)
+    rep, err, checked = coefficient_report(to_np(c), dict(col, c=ref), tol=1e-3)
+    print(f"refine K={K}", rep)
+    assert rep["p99_checked"] <= 1e-3
+    assert rep["bound_excess"] <= 0
+
+
+def test_refinement_over_camera_passes(icgs):
+    """Refinement with the cameras split into passes of 5 (binning redone per pass, the per-pass
+    residual sums folded across passes) gives the single-pass result."""
+    L, K = 1, 3
+    sc, cams = _scene(2000, 361, 12, 96, 72)
+    t = O.render(sc, cams, W.sh_coefficients(sc.n, L, K, seed=371), L).astype(np.float32)
+    gs, gc = _gpu(icgs, sc, cams)
+    tt = torch.tensor(t, device=DEV)
+    c0, status, chol = icgs.colorize(gs, gc, tt, L)
+    c1 = c0.clone()
+    c2 = c0.clone()
+    icgs.colorize_refine(gs, gc, tt, L, c1, chol, 2, cam_batch=0)
+    icgs.colorize_refine(gs, gc, tt, L, c2, chol, 2, cam_batch=5)
+    ok = to_np(status) != icgs.GAUSSIAN_UNSEEN
+    d = O.relative_errors(to_np(c2).astype(np.float64), to_np(c1).astype(np.float64))[ok]
+    print(f"refine passes of 5 vs one pass: p99 {np.percentile(d, 99):.2e}, max {d.max():.2e}")
+    # the same sums in another order of atomics: agreement to the FP32 path's tolerance
+    assert np.percentile(d, 99) <= 1e-4
