@@ -217,3 +217,23 @@ def test_refinement_over_camera_passes(icgs):
     print(f"refine passes of 5 vs one pass: p99 {np.percentile(d, 99):.2e}, max {d.max():.2e}")
     # the same sums in another order of atomics: agreement to the FP32 path's tolerance
     assert np.percentile(d, 99) <= 1e-4
+
+
+def test_adjoint_over_camera_passes(icgs):
+    """The adjoint with the cameras split into passes of 3 (lists rebuilt per pass, dL/do summed
+    over passes) gives the single-pass gradients."""
+    L, K = 1, 3
+    sc, cams = _scene(1500, 381, 8, 64, 48)
+    t = O.render(sc, cams, W.sh_coefficients(sc.n, L, K, seed=391), L).astype(np.float32)
+    gs, gc = _gpu(icgs, sc, cams)
+    tt = torch.tensor(t, device=DEV)
+    c, status, chol = icgs.colorize(gs, gc, tt, L)
+    r = torch.tensor(np.random.default_rng(401).standard_normal(tuple(c.shape)), dtype=torch.float32, device=DEV)
+    gt1, go1 = icgs.colorize_backward(gs, gc, tt, L, c, chol, 2 * r * c, cam_batch=0)
+    gt2, go2 = icgs.colorize_backward(gs, gc, tt, L, c, chol, 2 * r * c, cam_batch=3)
+    gt1, go1, gt2, go2 = to_np(gt1), to_np(go1), to_np(gt2), to_np(go2)
+    dt = np.abs(gt2 - gt1).max() / np.abs(gt1).max()
+    do = np.abs(go2 - go1).max() / np.abs(go1).max()
+    print(f"adjoint passes of 3 vs one pass: dL/dt {dt:.2e}, dL/do {do:.2e} (of max)")
+    assert dt <= 1e-6  # per pixel: the same walk, the same order
+    assert do <= 1e-5  # per Gaussian: the same terms, summed in another order
