@@ -55,7 +55,7 @@ MEASURED_TRAFFIC = {
     ("relight", "cuda-core"): {"bytes_per_scene": 2148486912 + 288519424, "source_sha": "be1ccf7fce8493cc"},
     # features: a 10-camera launch captured and scaled by 150/10 cameras (the targets, the per-camera
     # tile lists and the per-camera accumulator re-streaming all grow with the camera count)
-    ("features", "tensor-core"): {"bytes_per_scene": 15 * (3255703296 + 1463516416), "source_sha": "a52d454326bdcc64"},
+    ("features", "tensor-core"): {"bytes_per_scene": 15 * (3255527424 + 1463374848), "source_sha": "5d656c19d409fe9f"},
 }
 
 

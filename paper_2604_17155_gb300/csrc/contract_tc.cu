@@ -36,7 +36,7 @@ using namespace walk;
 constexpr int kG = 128;                 // Gaussians per batch (MMA M)
 constexpr int kKPix = 256;              // pixels per tile (MMA K in total, 16 instructions of 16)
 constexpr uint32_t kSpinLimit = 1u << 22;
-constexpr uint32_t kTmemCols = 128;     // power of two >= KT + 16 for KT <= 64
+constexpr uint32_t kTmemCols = 128;     // TMEM columns of the self-test (N <= 80)
 
 // ---- inline PTX ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -153,11 +153,12 @@ __device__ __forceinline__ void issue_batch(uint32_t a_addr, uint32_t b_addr, ui
   umma_commit(mbar);
 }
 
-// Row m of an M = 64 accumulator sits in TMEM lane (m % 16) + 32 (m / 16): rows 16w..16w+15 in
-// the first 16 lanes of warp w's 32-lane quarter (M = 128: row m in lane m).
+// The accumulator row held in TMEM lane 32 q + l (the lane a thread l of a warp with quarter q
+// reads), or -1: M = 128 puts row m in lane m; M = 64 puts row m in lane (m % 16) + 32 (m / 16),
+// i.e. rows 16q..16q+15 in the first 16 lanes of quarter q.
 template <int MG>
-__device__ __forceinline__ int tmem_lane_of_row(int m) {
-  return MG == 128 ? m : (m & 15) + 32 * (m >> 4);
+__device__ __forceinline__ int tmem_row_of_lane(int q, int l) {
+  return MG == 128 ? q * 32 + l : (l < 16 ? q * 16 + l : -1);
 }
 
 // ---- self-test: D[M x N] = A[M x 256] B[N x 256]^T through the same layout and MMA path ----
@@ -198,8 +199,7 @@ __global__ void __launch_bounds__(256) k_tc_selftest(const uint16_t* __restrict_
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp < 4 && ok) {
     const int L = warp * 32 + lane;  // the TMEM lane this thread reads
-    // the row held in lane L, or -1 (M = 64 leaves lanes 16..31 of each quarter unused)
-    const int row = MG == 128 ? L : (lane < 16 ? 16 * warp + lane : -1);
+    const int row = tmem_row_of_lane<MG>(warp, lane);
 #pragma unroll
     for (int c0 = 0; c0 < NB; c0 += 16) {
       uint32_t r[16];
@@ -358,12 +358,12 @@ __global__ void __launch_bounds__(256, MG == 64 ? (KT <= 32 ? 4 : 3) : 2) k_blen
     tc_fence_after();
     if (ok) {
       // warps w and w+4 share TMEM lanes 32(w%4)..+31 (one Gaussian per thread) and split its 16-column
-      // chunks; with MG = 64 only the first 16 lanes of each quarter hold a Gaussian (tmem_lane_of_row).
+      // chunks; with MG = 64 only the first 16 lanes of each quarter hold a Gaussian (tmem_row_of_lane).
       // The accumulator streams through registers a chunk at a time: chunk c adds the float4 groups
       // 4c..4c+3 of the row (V, S_0, S_1, ..) and carries its last column into group 4c+4. Every
       // tcgen05.ld is warp-uniform; only the atomics depend on the thread's Gaussian.
       const int quarter = warp & 3, part = warp >> 2;
-      const int g = MG == 128 ? quarter * 32 + lane : (lane < 16 ? quarter * 16 + lane : MG);
+      const int g = tmem_row_of_lane<MG>(quarter, lane);
       const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
       constexpr int kCh = KT / 16;           // 16-column chunks of S
       constexpr int kHalf = (kCh + 1) / 2;   // chunks of the warps 0-3
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(256, MG == 64 ? (KT <= 32 ? 4 : 3) : 2) k_blen
         tmem_wait_ld();
         const float V = __uint_as_float(vr[0]) * v_scale_inv;
         float carry = part == 0 ? V : __uint_as_float(r[15]) * t_scale_inv;
-        const bool add = g < nb && V > 0.0f;
+        const bool add = g >= 0 && g < nb && V > 0.0f;
         float* dst = acc_cam + (int64_t)(add ? s_id[g] : 0u) * RS;
         const int c_begin = part == 0 ? 0 : kHalf, c_end = part == 0 ? kHalf : kCh;
 #pragma unroll
