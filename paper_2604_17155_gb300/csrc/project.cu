@@ -189,14 +189,18 @@ __device__ __forceinline__ int4 project_pair(const float* __restrict__ means, co
   return make_int4(tx0, ty0, tx1, ty1);
 }
 
-constexpr int kPerThread = 8;                 // Gaussians per thread in the histogram kernels
-constexpr int kPerCta = 256 * kPerThread;     // Gaussians of one camera per CTA
+// Gaussians per thread in the histogram kernels (a CTA takes 256 PT Gaussians of one camera). Each
+// CTA zeroes and flushes one histogram bin per tile, so large tile grids take 16 a thread, which
+// halves that per-CTA cost; smaller ones take 8, which keeps more CTAs in flight.
+constexpr int kBigTileGrid = 4096;
+__host__ __device__ constexpr int hist_per_cta(int per_thread) { return 256 * per_thread; }
 constexpr int kHistTiles = 12288;             // largest tile grid the shared-memory histograms take
 
-// One CTA per (camera, 2048 Gaussians): counts the CTA's instances per tile in shared memory, then
+// One CTA per (camera, 256 PT Gaussians): counts the CTA's instances per tile in shared memory, then
 // adds each nonzero bin to the global count with one atomic. The camera is the fast index of the
 // 1-D grid, so the CTAs of one chunk of Gaussians run together and read its parameters from DRAM
 // once (a scene larger than L2 would otherwise be re-read for every camera).
+template <int PT>
 __global__ void __launch_bounds__(256) k_project_hist(
     const float* __restrict__ means, const float* __restrict__ scales, const float* __restrict__ quats,
     const float* __restrict__ opac, int64_t n, const DevCam* __restrict__ cams, int j0, int cbl, int width,
@@ -208,8 +212,8 @@ __global__ void __launch_bounds__(256) k_project_hist(
   const DevCam& c = cams[j];
   for (int t = threadIdx.x; t < tiles; t += 256) s_hist[t] = 0u;
   __syncthreads();
-  const int64_t i0 = chunk * kPerCta;
-  for (int r = 0; r < kPerThread; ++r) {
+  const int64_t i0 = chunk * hist_per_cta(PT);
+  for (int r = 0; r < PT; ++r) {
     const int64_t i = i0 + r * 256 + threadIdx.x;
     if (i >= n) break;
     const int4 tr = project_pair(means, scales, quats, opac, i, c, width, height, near_z, (int64_t)j * n + i, rec, rect);
@@ -263,6 +267,7 @@ __global__ void __launch_bounds__(256) k_scatter(
 
 // Same CTA tiling as k_project_hist: the CTA counts its instances per tile, reserves one contiguous
 // run per tile with a single global atomic, then places its instances with shared-memory cursors.
+template <int PT>
 __global__ void __launch_bounds__(256) k_scatter_hist(
     int64_t n, const uint4* __restrict__ rect, int tiles_x, int tiles, const uint32_t* __restrict__ tile_off,
     uint32_t* __restrict__ tile_cur, uint64_t* __restrict__ entries, uint32_t capacity, DevStatus* status) {
@@ -272,8 +277,8 @@ __global__ void __launch_bounds__(256) k_scatter_hist(
   const int j = blockIdx.y;
   for (int t = threadIdx.x; t < tiles; t += 256) s_cnt[t] = 0u;
   __syncthreads();
-  const int64_t i0 = (int64_t)blockIdx.x * kPerCta;
-  for (int r = 0; r < kPerThread; ++r) {
+  const int64_t i0 = (int64_t)blockIdx.x * hist_per_cta(PT);
+  for (int r = 0; r < PT; ++r) {
     const int64_t i = i0 + r * 256 + threadIdx.x;
     if (i >= n) break;
     const uint4 rc = rect[(int64_t)j * n + i];
@@ -291,7 +296,7 @@ __global__ void __launch_bounds__(256) k_scatter_hist(
   }
   __syncthreads();
   bool overflow = false;
-  for (int r = 0; r < kPerThread; ++r) {
+  for (int r = 0; r < PT; ++r) {
     const int64_t i = i0 + r * 256 + threadIdx.x;
     if (i >= n) break;
     const uint4 rc = rect[(int64_t)j * n + i];
@@ -401,16 +406,18 @@ void launch_project(const Problem& p, const float* means, const float* scales, c
                     const float* opac, int cb, const Workspace& ws, cudaStream_t s) {
   if (p.tiles <= kHistTiles) {
     const size_t smem = sizeof(uint32_t) * (size_t)p.tiles;
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_project_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int64_t chunks = (p.n + kPerCta - 1) / kPerCta;
+    const bool big = p.tiles >= kBigTileGrid;
+    auto kern = big ? k_project_hist<16> : k_project_hist<8>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int per_cta = hist_per_cta(big ? 16 : 8);
+    const int64_t chunks = (p.n + per_cta - 1) / per_cta;
     // cameras per launch so that the 1-D grid stays below 2^31 CTAs
     const int per = (int)std::min<int64_t>(cb, std::max<int64_t>(1, 0x7FFFFFFF / std::max<int64_t>(chunks, 1)));
     for (int j0 = 0; j0 < cb; j0 += per) {
       const int cbl = std::min(per, cb - j0);
-      k_project_hist<<<(unsigned)(chunks * cbl), 256, smem, s>>>(means, scales, quats, opac, p.n, ws.cams, j0, cbl,
-                                                                 p.width, p.height, p.near_z, p.tiles_x, p.tiles,
-                                                                 ws.rec, ws.rect, ws.tile_off);
+      kern<<<(unsigned)(chunks * cbl), 256, smem, s>>>(means, scales, quats, opac, p.n, ws.cams, j0, cbl, p.width,
+                                                       p.height, p.near_z, p.tiles_x, p.tiles, ws.rec, ws.rect,
+                                                       ws.tile_off);
       note_launches(1);
     }
     return;
@@ -433,11 +440,13 @@ void launch_scan(const Problem& p, int cb, const Workspace& ws, cudaStream_t s) 
 void launch_scatter(const Problem& p, int cb, const Workspace& ws, cudaStream_t s) {
   if (p.tiles <= kHistTiles) {
     const size_t smem = 2 * sizeof(uint32_t) * (size_t)p.tiles;
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_scatter_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid((unsigned)((p.n + kPerCta - 1) / kPerCta), (unsigned)cb);
-    k_scatter_hist<<<grid, 256, smem, s>>>(p.n, ws.rect, p.tiles_x, p.tiles, ws.tile_off, ws.tile_cur, ws.entries,
-                                           p.capacity, ws.status);
+    const bool big = p.tiles >= kBigTileGrid;
+    auto kern = big ? k_scatter_hist<16> : k_scatter_hist<8>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int per_cta = hist_per_cta(big ? 16 : 8);
+    dim3 grid((unsigned)((p.n + per_cta - 1) / per_cta), (unsigned)cb);
+    kern<<<grid, 256, smem, s>>>(p.n, ws.rect, p.tiles_x, p.tiles, ws.tile_off, ws.tile_cur, ws.entries, p.capacity,
+                                 ws.status);
     note_launches(1);
     return;
   }
