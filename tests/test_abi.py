@@ -120,3 +120,15 @@ def test_backward_rejects_too_many_channels(lib):
     st = lib.icgs_colorize_backward(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(opt),
                                     ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), None, 0, None, None, None)
     assert st == icgs.ERR_UNSUPPORTED
+
+
+def test_tc_selftest_rows_rejects_bad_shapes_on_host(lib):
+    """icgs_selftest_tc_rows takes M = 64 or 128 rows and N = 32 or 80 columns; anything else is
+    refused on the host with a message, before any device work."""
+    p = ctypes.c_void_p(256)
+    st = lib.icgs_selftest_tc_rows(p, 32, p, 32, 1, p, None, p, None)
+    assert st == icgs.ERR_INVALID_ARG and "M = 32" in lib.icgs_last_error().decode()
+    st = lib.icgs_selftest_tc_rows(p, 64, p, 48, 1, p, None, p, None)
+    assert st == icgs.ERR_INVALID_ARG and "N = 48" in lib.icgs_last_error().decode()
+    st = lib.icgs_selftest_tc_rows(None, 64, p, 32, 1, p, None, p, None)
+    assert st == icgs.ERR_INVALID_ARG and "required" in lib.icgs_last_error().decode()
