@@ -26,9 +26,10 @@
  * fma(W22, z, fma(W21, y, fma(W20, x, W23))), each step one correctly rounded fused multiply-add
  * in float32 (C99 fmaf); ties are broken by the Gaussian index. Everything else here is double
  * with no contraction (compile with -ffp-contract=off). Threshold decisions on alpha and T
- * are taken in double; each one that falls within a relative margin `delta` of its threshold adds
- * the weight it decides to a per-Gaussian "stake", so a test can tell a threshold flip from an
- * arithmetic error.
+ * are taken in double. A renderer that computes alpha and T in lower precision can take a decision
+ * that falls close to its threshold the other way; walk_pixel records, per Gaussian, an upper bound
+ * on how much weight such flips can move (its "stake"; see walk_pixel), so a test can tell a
+ * threshold flip from an arithmetic error.
  */
 #include <math.h>
 #include <stdint.h>
@@ -62,6 +63,11 @@ typedef struct {
 #define ALPHA_MAX 0.99
 #define T_MIN 1e-4
 #define DILATION 0.3
+
+/* Test-only scale factors of the two thresholds (1 = the renderer's values). A test moves a
+ * threshold by a relative amount within the stake margin to flip, on purpose, every decision that
+ * lies that close to it, and checks the result against the stake-derived bound. */
+static double g_alpha_min_scale = 1.0, g_t_min_scale = 1.0;
 
 /* Rotation matrix of the unit quaternion (w,x,y,z) (Hamilton convention). */
 static void quat_to_rot(const float* qf, double R[9]) {
@@ -194,14 +200,43 @@ typedef struct {
   int32_t clamped;      /* alpha hit the 0.99 cap */
 } ocontrib_t;
 
+/* Stake bookkeeping of one pixel's walk. A decision is "near" its threshold when alpha lies within
+ * relative margin delta_a of 1/255, or T(1 - alpha) within delta_t (+ the T perturbation already at
+ * stake, below) of 1e-4. Each entry is an upper bound on |dV|, the change of the pixel's weight of
+ * that Gaussian when any set of near decisions is taken the other way:
+ *   own[i]  the Gaussian's own near decision: alpha_hi T' for an alpha decision (alpha_hi =
+ *           (1 + delta_a)/255 bounds alpha there), alpha T' for a stop decision;
+ *   up[i]   near decisions in front of it: rel * w for a contributor, where rel bounds
+ *           |T_other / T - 1| (each alpha flip scales T by (1 - alpha)^(+-1), so rel grows by the
+ *           factor 1 + alpha_hi / (1 - alpha_hi); a stop in front at stake adds 1, since the other
+ *           side may then drop the Gaussian); and, behind a stop at stake, T' min(alpha, 0.99) for
+ *           every Gaussian the other side could still take (alpha >= (1 - delta_a)/255);
+ *   tw[i]   the same amounts times the pixel's target norm |t_p|_2, for the bound on the
+ *           coefficients (the pair's right-hand side moves by dV t_p).
+ * T' = T (1 + rel) bounds the other side's transmittance. */
+typedef struct {
+  double delta_a, delta_t;
+  double* own;
+  double* up;
+  double* tw;
+  double tnorm;
+  int hits;      /* stake entries added in this pixel */
+} ostake_t;
+
+static void stake_add(ostake_t* sk, double* arr, int32_t i, double v) {
+  arr[i] += v;
+  if (sk->tw) sk->tw[i] += v * sk->tnorm;
+  sk->hits++;
+}
+
 /* Walks `list` (indices in depth order) for the pixel with centre (pxc, pyc). Writes the
- * contributors to `out` and returns their number. If stake arrays are given, threshold decisions
- * within relative margin delta add the weight they decide to them (see the file header). */
+ * contributors to `out` and returns their number. With `sk`, near decisions add their stake. */
 static int walk_pixel(const oproj_t* P, const int32_t* list, int len, double pxc, double pyc,
-                      ocontrib_t* out, double delta, double* stake_own, double* stake_up) {
+                      ocontrib_t* out, ostake_t* sk) {
+  const double amin = ALPHA_MIN * g_alpha_min_scale, tmin = T_MIN * g_t_min_scale;
   double T = 1.0;
   int m = 0;
-  double rel_up = 0.0; /* relative change of T, at stake, in front of the current Gaussian */
+  double rel = 0.0; /* bound on |T_other / T - 1| behind the Gaussians walked so far */
   for (int k = 0; k < len; ++k) {
     const oproj_t* g = P + list[k];
     double dx = pxc - g->mx, dy = pyc - g->my;
@@ -209,25 +244,30 @@ static int walk_pixel(const oproj_t* P, const int32_t* list, int len, double pxc
     double e = exp(-0.5 * q);
     double oe = g->opacity * e;
     double alpha = oe < ALPHA_MAX ? oe : ALPHA_MAX;
-    if (stake_own && fabs(alpha - ALPHA_MIN) <= delta * ALPHA_MIN) {
-      stake_own[list[k]] += ALPHA_MIN * T;
-      rel_up += ALPHA_MIN;
+    const double rel_front = rel; /* in front of this Gaussian: its own decisions do not count */
+    if (sk && fabs(alpha - amin) <= sk->delta_a * amin) {
+      const double a_hi = amin * (1.0 + sk->delta_a);
+      stake_add(sk, sk->own, list[k], a_hi * T * (1.0 + rel_front));
+      rel = (1.0 + rel) * (1.0 + a_hi / (1.0 - a_hi)) - 1.0;
     }
-    if (alpha < ALPHA_MIN) continue;
+    if (alpha < amin) continue;
     double test_T = T * (1.0 - alpha);
-    if (stake_own && fabs(test_T - T_MIN) <= delta * T_MIN) {
-      stake_own[list[k]] += alpha * T;
-      rel_up += 1.0;
+    int stop_at_stake = 0;
+    if (sk && fabs(test_T - tmin) <= (sk->delta_t + rel_front) * tmin) {
+      stake_add(sk, sk->own, list[k], alpha * T * (1.0 + rel_front));
+      rel += 1.0;
+      stop_at_stake = 1;
     }
-    if (test_T < T_MIN) {
-      if (stake_up && rel_up > 0.0) {
-        /* everything behind a stop decided within the margin is at stake */
+    if (test_T < tmin) {
+      if (sk && stop_at_stake) {
+        /* the other side may go on: everything behind that it could take is at stake */
         for (int r = k + 1; r < len; ++r) {
           const oproj_t* h = P + list[r];
           double ex = pxc - h->mx, ey = pyc - h->my;
           double qq = h->ca * ex * ex + 2.0 * h->cb * ex * ey + h->cc * ey * ey;
           double aa = h->opacity * exp(-0.5 * qq);
-          if (aa >= ALPHA_MIN) stake_up[list[r]] += T * (aa < ALPHA_MAX ? aa : ALPHA_MAX);
+          if (aa >= amin * (1.0 - sk->delta_a))
+            stake_add(sk, sk->up, list[r], T * (1.0 + rel_front) * (aa < ALPHA_MAX ? aa : ALPHA_MAX));
         }
       }
       break;
@@ -238,7 +278,7 @@ static int walk_pixel(const oproj_t* P, const int32_t* list, int len, double pxc
     out[m].w = alpha * T;
     out[m].e = e;
     out[m].clamped = oe >= ALPHA_MAX;
-    if (stake_up && rel_up > 0.0) stake_up[list[k]] += rel_up * out[m].w;
+    if (sk && rel_front > 0.0) stake_add(sk, sk->up, list[k], rel_front * out[m].w);
     ++m;
     T = test_T;
   }
@@ -314,9 +354,11 @@ typedef struct {
   const double* targets;     /* [H,W,K] */
   double* V;                 /* [n] */
   double* S;                 /* [n,K] */
-  double* stake_own;         /* [n] or NULL */
-  double* stake_up;          /* [n] or NULL */
-  double delta;
+  ostake_t stake;            /* stake arrays (own NULL: no bookkeeping) */
+  uint8_t* pix_flag;         /* [H,W] or NULL: 1 where the pixel's walk has a near decision (or,
+                                with `dirty`, a contributor marked dirty) */
+  double* flag_w;            /* [n] or NULL: each Gaussian's weight in such pixels */
+  const uint8_t* dirty;      /* [n] or NULL: Gaussians whose sums a flip elsewhere may have moved */
   int64_t pairs;
   ocontrib_t* scratch;
   /* render */
@@ -327,6 +369,7 @@ typedef struct {
   int32_t* out_pix;
   int32_t* out_gid;
   double* out_w;
+  double* out_T;             /* or NULL */
   /* adjoint */
   const double* a;           /* [n,K] dL/dS */
   const double* beta;        /* [n]   dL/dV */
@@ -336,8 +379,23 @@ typedef struct {
 
 static void visit_accumulate(void* vctx, int32_t px, int32_t py, const int32_t* list, int len) {
   octx_t* c = (octx_t*)vctx;
-  int m = walk_pixel(c->P, list, len, px + 0.5, py + 0.5, c->scratch, c->delta, c->stake_own, c->stake_up);
   const double* t = c->targets + ((int64_t)py * c->cam->width + px) * c->K;
+  ostake_t sk = c->stake;
+  const int with_stake = sk.own != NULL && sk.up != NULL;
+  if (with_stake) {
+    double nn = 0.0;
+    for (int k = 0; k < c->K; ++k) nn += t[k] * t[k];
+    sk.tnorm = sqrt(nn);
+  }
+  sk.hits = 0;
+  int m = walk_pixel(c->P, list, len, px + 0.5, py + 0.5, c->scratch, with_stake ? &sk : NULL);
+  int flagged = sk.hits > 0;
+  for (int r = 0; r < m && !flagged && c->dirty; ++r) flagged = c->dirty[c->scratch[r].i] != 0;
+  if (flagged) {
+    if (c->pix_flag) c->pix_flag[(int64_t)py * c->cam->width + px] = 1;
+    if (c->flag_w)
+      for (int r = 0; r < m; ++r) c->flag_w[c->scratch[r].i] += c->scratch[r].w;
+  }
   for (int r = 0; r < m; ++r) {
     int32_t i = c->scratch[r].i;
     double w = c->scratch[r].w;
@@ -349,7 +407,7 @@ static void visit_accumulate(void* vctx, int32_t px, int32_t py, const int32_t* 
 
 static void visit_render(void* vctx, int32_t px, int32_t py, const int32_t* list, int len) {
   octx_t* c = (octx_t*)vctx;
-  int m = walk_pixel(c->P, list, len, px + 0.5, py + 0.5, c->scratch, 0.0, NULL, NULL);
+  int m = walk_pixel(c->P, list, len, px + 0.5, py + 0.5, c->scratch, NULL);
   double* img = c->image + ((int64_t)py * c->cam->width + px) * c->K;
   for (int r = 0; r < m; ++r)
     for (int k = 0; k < c->K; ++k) img[k] += c->scratch[r].w * c->colors[(int64_t)c->scratch[r].i * c->K + k];
@@ -358,12 +416,13 @@ static void visit_render(void* vctx, int32_t px, int32_t py, const int32_t* list
 
 static void visit_weights(void* vctx, int32_t px, int32_t py, const int32_t* list, int len) {
   octx_t* c = (octx_t*)vctx;
-  int m = walk_pixel(c->P, list, len, px + 0.5, py + 0.5, c->scratch, 0.0, NULL, NULL);
+  int m = walk_pixel(c->P, list, len, px + 0.5, py + 0.5, c->scratch, NULL);
   for (int r = 0; r < m; ++r) {
     if (c->count < c->cap) {
       c->out_pix[c->count] = py * c->cam->width + px;
       c->out_gid[c->count] = c->scratch[r].i;
       c->out_w[c->count] = c->scratch[r].w;
+      if (c->out_T) c->out_T[c->count] = c->scratch[r].T;
     }
     c->count++;
   }
@@ -374,7 +433,7 @@ static void visit_weights(void* vctx, int32_t px, int32_t py, const int32_t* lis
  * dF/dalpha_n = g_n T_n - (sum_{l>n} g_l w_l) / (1 - alpha_n); dalpha/do = e unless capped. */
 static void visit_adjoint(void* vctx, int32_t px, int32_t py, const int32_t* list, int len) {
   octx_t* c = (octx_t*)vctx;
-  int m = walk_pixel(c->P, list, len, px + 0.5, py + 0.5, c->scratch, 0.0, NULL, NULL);
+  int m = walk_pixel(c->P, list, len, px + 0.5, py + 0.5, c->scratch, NULL);
   int K = c->K;
   const double* t = c->targets + ((int64_t)py * c->cam->width + px) * K;
   double* gt = c->grad_t + ((int64_t)py * c->cam->width + px) * K;
@@ -437,16 +496,23 @@ int icgso_project(int64_t n, const float* means, const float* scales, const floa
 }
 
 /* V_i = sum_pixels alpha_i T_i (Eq. 4-5), S_ik = sum_pixels alpha_i T_i t_k (numerator of Eq. 6).
- * V, S, stake_own, stake_up are accumulated into (the caller zeroes them). Returns the number of
- * (pixel, Gaussian) pairs with nonzero weight, or -1 on allocation failure. */
+ * V, S and the stakes (walk_pixel; stake_own or stake_up NULL: none; stake_tw may be NULL) are accumulated
+ * into (the caller zeroes them). delta_a, delta_t: the relative margins of the alpha and stop
+ * decisions. pix_flag [H,W] (may be NULL) is set to 1 at every pixel whose walk has a near decision
+ * or, with dirty [n] (may be NULL), a contributor marked dirty; flag_w [n] (may be NULL) accumulates
+ * each Gaussian's weight in those pixels. Returns the number of (pixel, Gaussian) pairs with nonzero weight, or -1 on
+ * allocation failure. */
 int64_t icgso_accumulate(int64_t n, const float* means, const float* scales, const float* quats,
                          const float* opac, const ocam_t* cam, int32_t K, const double* targets,
-                         const uint8_t* mask, int32_t brute, double delta, double* V, double* S,
-                         double* stake_own, double* stake_up) {
+                         const uint8_t* mask, int32_t brute, double delta_a, double delta_t, double* V,
+                         double* S, double* stake_own, double* stake_up, double* stake_tw,
+                         uint8_t* pix_flag, double* flag_w, const uint8_t* dirty) {
   octx_t ctx;
   memset(&ctx, 0, sizeof ctx);
   ctx.K = K; ctx.targets = targets; ctx.V = V; ctx.S = S;
-  ctx.stake_own = stake_own; ctx.stake_up = stake_up; ctx.delta = delta;
+  ctx.stake.delta_a = delta_a; ctx.stake.delta_t = delta_t;
+  ctx.stake.own = stake_own; ctx.stake.up = stake_up; ctx.stake.tw = stake_own ? stake_tw : NULL;
+  ctx.pix_flag = pix_flag; ctx.flag_w = flag_w; ctx.dirty = dirty;
   if (run_camera(n, means, scales, quats, opac, cam, mask, brute, visit_accumulate, &ctx)) return -1;
   return ctx.pairs;
 }
@@ -463,14 +529,15 @@ int64_t icgso_render(int64_t n, const float* means, const float* scales, const f
   return ctx.pairs;
 }
 
-/* Lists every (pixel, Gaussian, weight) with nonzero weight, up to `cap` entries; returns the
- * total count (call again with a larger cap if it exceeds cap). */
+/* Lists every (pixel, Gaussian, weight) with nonzero weight, and the transmittance in front of the
+ * Gaussian (T may be NULL), up to `cap` entries; returns the total count (call again with a larger
+ * cap if it exceeds cap). */
 int64_t icgso_weights(int64_t n, const float* means, const float* scales, const float* quats,
                       const float* opac, const ocam_t* cam, const uint8_t* mask, int32_t brute,
-                      int64_t cap, int32_t* pix, int32_t* gid, double* w) {
+                      int64_t cap, int32_t* pix, int32_t* gid, double* w, double* T) {
   octx_t ctx;
   memset(&ctx, 0, sizeof ctx);
-  ctx.cap = cap; ctx.out_pix = pix; ctx.out_gid = gid; ctx.out_w = w;
+  ctx.cap = cap; ctx.out_pix = pix; ctx.out_gid = gid; ctx.out_w = w; ctx.out_T = T;
   if (run_camera(n, means, scales, quats, opac, cam, mask, brute, visit_weights, &ctx)) return -1;
   return ctx.count;
 }
@@ -485,6 +552,13 @@ int64_t icgso_adjoint(int64_t n, const float* means, const float* scales, const 
   ctx.K = K; ctx.targets = targets; ctx.a = a; ctx.beta = beta; ctx.grad_t = grad_t; ctx.grad_o = grad_o;
   if (run_camera(n, means, scales, quats, opac, cam, NULL, 0, visit_adjoint, &ctx)) return -1;
   return ctx.pairs;
+}
+
+/* Test-only: scales the alpha threshold 1/255 and the stop threshold 1e-4 by the given factors
+ * (1, 1 restores them). Not thread-safe: call it while no walk is running. */
+void icgso_set_threshold_scale(double alpha_scale, double t_scale) {
+  g_alpha_min_scale = alpha_scale;
+  g_t_min_scale = t_scale;
 }
 
 /* Real orthonormal spherical harmonics (Eq. 3), degree 0..L, index l*l + l + m (m = -l..l):

@@ -61,16 +61,18 @@ def _load():
         i64, i32, dbl = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
         lib.icgso_project.argtypes = [i64, P, P, P, P, P, P]
         lib.icgso_project.restype = ctypes.c_int
-        lib.icgso_accumulate.argtypes = [i64, P, P, P, P, P, i32, P, P, i32, dbl, P, P, P, P]
+        lib.icgso_accumulate.argtypes = [i64, P, P, P, P, P, i32, P, P, i32, dbl, dbl, P, P, P, P, P, P, P, P]
         lib.icgso_accumulate.restype = i64
         lib.icgso_render.argtypes = [i64, P, P, P, P, P, i32, P, P, i32, P]
         lib.icgso_render.restype = i64
-        lib.icgso_weights.argtypes = [i64, P, P, P, P, P, P, i32, i64, P, P, P]
+        lib.icgso_weights.argtypes = [i64, P, P, P, P, P, P, i32, i64, P, P, P, P]
         lib.icgso_weights.restype = i64
         lib.icgso_adjoint.argtypes = [i64, P, P, P, P, P, i32, P, P, P, P, P]
         lib.icgso_adjoint.restype = i64
         lib.icgso_sh_basis.argtypes = [i32, i64, P, P]
         lib.icgso_sh_basis.restype = ctypes.c_int
+        lib.icgso_set_threshold_scale.argtypes = [dbl, dbl]
+        lib.icgso_set_threshold_scale.restype = None
         _lib = lib
     return _lib
 
@@ -153,33 +155,81 @@ def project(scene, cams, j):
     return {k: out[:, i] for i, k in enumerate(names)}
 
 
-def accumulate(scene, cams, targets, mask=None, brute=False, delta=1e-3, threads=None):
-    """Per-camera visibility sums (Eq. 5) and weighted target sums (Eq. 6 numerator).
+# Relative margins within which a threshold decision counts as "near" (icgs_oracle.c, walk_pixel):
+# alpha against 1/255 and T (1 - alpha) against 1e-4. A near decision may be taken the other way
+# by a renderer whose alpha and T carry float32 rounding; the oracle records what it could move.
+# Each margin is at least ten times the largest relative error of the float32 walk's alpha (front
+# pairs, T = 1) and of its weights alpha T measured against this oracle on the GB300
+# (tests/test_gpu_weights.py, which also checks that no decision outside the margins differs).
+DELTA_ALPHA = 4e-5
+DELTA_T = 2e-4
 
-    targets: [C,H,W,K]; mask: optional [C,H,W] bool of the pixels to walk.
-    Returns V [C,N], S [C,N,K], stake_own [C,N], stake_up [C,N], pairs [C]."""
+
+def accumulate_stakes(scene, cams, targets, mask=None, brute=False, delta=(DELTA_ALPHA, DELTA_T), threads=None,
+                      flags=False, dirty=None):
+    """Per-camera visibility sums (Eq. 5) and weighted target sums (Eq. 6 numerator), with the
+    stake of the near threshold decisions (walk_pixel in icgs_oracle.c).
+
+    targets: [C,H,W,K]; mask: optional [C,H,W] bool of the pixels to walk; delta: (margin of the
+    alpha decision, margin of the stop decision), relative. Returns a dict of V [C,N], S [C,N,K],
+    stake_own, stake_up [C,N] (bounds on |dV| from a Gaussian's own near decisions and from those in
+    front of it), stake_tw [C,N] (the same weighted by the pixels' target norms), pairs [C]; with
+    flags=True also pix_flag [C,H,W] (pixels whose walk has a near decision) and flag_w [C,N]
+    (each Gaussian's weight in those pixels); dirty [N] bool (optional) also flags every pixel that
+    one of those Gaussians contributes to."""
     lib = _load()
     m, s, q, o = _scene_arrays(scene)
     C, N = cams.n, scene.n
     K = targets.shape[-1]
+    da, dt = (float(delta), float(delta)) if np.isscalar(delta) else (float(delta[0]), float(delta[1]))
     V = np.zeros((C, N)); S = np.zeros((C, N, K))
-    so = np.zeros((C, N)); su = np.zeros((C, N))
+    so = np.zeros((C, N)); su = np.zeros((C, N)); stw = np.zeros((C, N))
+    pf = np.zeros((C, cams.height, cams.width), np.uint8) if flags else None
+    fw = np.zeros((C, N)) if flags else None
     pairs = np.zeros(C, np.int64)
+    dm = None if dirty is None else np.ascontiguousarray(dirty, np.uint8)
 
     def one(j):
         t = np.ascontiguousarray(targets[j], np.float64)
         mk = None if mask is None else np.ascontiguousarray(mask[j], np.uint8)
         c = _ocam(cams, j)
         r = lib.icgso_accumulate(N, _ptr(m), _ptr(s), _ptr(q), _ptr(o), ctypes.byref(c), K, _ptr(t),
-                                 _ptr(mk), int(brute), float(delta), _ptr(V[j]), _ptr(S[j]),
-                                 _ptr(so[j]), _ptr(su[j]))
+                                 _ptr(mk), int(brute), da, dt, _ptr(V[j]), _ptr(S[j]),
+                                 _ptr(so[j]), _ptr(su[j]), _ptr(stw[j]),
+                                 None if pf is None else _ptr(pf[j]), None if fw is None else _ptr(fw[j]), _ptr(dm))
         if r < 0:
             raise MemoryError("oracle accumulate failed")
         pairs[j] = r
 
     with ThreadPoolExecutor(_threads(threads)) as ex:
         list(ex.map(one, range(C)))
-    return V, S, so, su, pairs
+    out = dict(V=V, S=S, stake_own=so, stake_up=su, stake_tw=stw, pairs=pairs)
+    if flags:
+        out.update(pix_flag=pf, flag_w=fw)
+    return out
+
+
+def accumulate(scene, cams, targets, mask=None, brute=False, delta=(DELTA_ALPHA, DELTA_T), threads=None):
+    """accumulate_stakes() as a tuple: V [C,N], S [C,N,K], stake_own [C,N], stake_up [C,N], pairs [C]."""
+    a = accumulate_stakes(scene, cams, targets, mask=mask, brute=brute, delta=delta, threads=threads)
+    return a["V"], a["S"], a["stake_own"], a["stake_up"], a["pairs"]
+
+
+class threshold_scale:
+    """Test-only context: the alpha threshold 1/255 and the stop threshold 1e-4 scaled by the given
+    factors inside the block (icgso_set_threshold_scale). Flips, on purpose, every decision that
+    close to a threshold."""
+
+    def __init__(self, alpha_scale=1.0, t_scale=1.0):
+        self.a, self.t = float(alpha_scale), float(t_scale)
+
+    def __enter__(self):
+        _load().icgso_set_threshold_scale(self.a, self.t)
+        return self
+
+    def __exit__(self, *exc):
+        _load().icgso_set_threshold_scale(1.0, 1.0)
+        return False
 
 
 def camera_colors(scene, cams, coeffs, sh_degree):
@@ -209,21 +259,24 @@ def render(scene, cams, coeffs, sh_degree, mask=None, brute=False, threads=None)
     return img
 
 
-def weights(scene, cams, j, brute=False):
+def weights(scene, cams, j, brute=False, mask=None, with_T=False):
     """Every nonzero per-pixel visibility V_{i,x,y} (Eq. 4) of camera j:
-    (pixel index y*W+x, Gaussian index, weight)."""
+    (pixel index y*W+x, Gaussian index, weight), and with with_T the transmittance in front of the
+    Gaussian. mask: optional [H,W] bool of the pixels to walk."""
     lib = _load()
     m, s, q, o = _scene_arrays(scene)
     c = _ocam(cams, j)
+    mk = None if mask is None else np.ascontiguousarray(mask, np.uint8)
     cap = 1 << 16
     while True:
         pix = np.empty(cap, np.int32); gid = np.empty(cap, np.int32); w = np.empty(cap, np.float64)
-        cnt = lib.icgso_weights(scene.n, _ptr(m), _ptr(s), _ptr(q), _ptr(o), ctypes.byref(c), None,
-                                int(brute), cap, _ptr(pix), _ptr(gid), _ptr(w))
+        T = np.empty(cap, np.float64) if with_T else None
+        cnt = lib.icgso_weights(scene.n, _ptr(m), _ptr(s), _ptr(q), _ptr(o), ctypes.byref(c), _ptr(mk),
+                                int(brute), cap, _ptr(pix), _ptr(gid), _ptr(w), _ptr(T))
         if cnt < 0:
             raise MemoryError("oracle weights failed")
         if cnt <= cap:
-            return pix[:cnt], gid[:cnt], w[:cnt]
+            return (pix[:cnt], gid[:cnt], w[:cnt], T[:cnt]) if with_T else (pix[:cnt], gid[:cnt], w[:cnt])
         cap = int(cnt)
 
 
@@ -252,16 +305,59 @@ def solve(G, b, w, lam):
     return c, status, A
 
 
-def colorize(scene, cams, targets, sh_degree, lam=None, mask=None, delta=1e-3, threads=None):
+def colorize(scene, cams, targets, sh_degree, lam=None, mask=None, delta=(DELTA_ALPHA, DELTA_T), threads=None,
+             flags=False):
     """The single-shot colorization of Alg. 1 (lines 1-6). Returns a dict with the coefficients
     c [N,(L+1)^2,K], status [N], and the intermediate V, S, G, b, w, stakes and pair count."""
     lam = paper_lambda(sh_degree) if lam is None else np.asarray(lam, np.float64)
-    V, S, so, su, pairs = accumulate(scene, cams, targets, mask=mask, delta=delta, threads=threads)
+    a = accumulate_stakes(scene, cams, targets, mask=mask, delta=delta, threads=threads, flags=flags)
     Y = view_basis(scene, cams, sh_degree)
-    G, b, w = fold(V, S, Y)
+    G, b, w = fold(a["V"], a["S"], Y)
     c, status, A = solve(G, b, w, lam)
-    return dict(c=c, status=status, V=V, S=S, Y=Y, G=G, b=b, w=w, A=A, lam=lam,
-                stake_own=so, stake_up=su, pairs=pairs)
+    out = dict(a, c=c, status=status, Y=Y, G=G, b=b, w=w, A=A, lam=lam)
+    return out
+
+
+def flip_bound(c, A, Y, lam, stake, stake_tw, w=None, chunk=4096, with_gamma=False):
+    """Per-Gaussian upper bound on ||c'_i - c_i||_F when the near threshold decisions that produced
+    the sums are taken the other way in any combination (the walk's stake, icgs_oracle.c).
+
+    Each flipped (pixel, Gaussian) pair moves V_ij by some dV with sum |dV| <= stake_ij, and S_ij
+    by dV t_p (t_p the pixel's target), so A_i = G_i + w_i Lambda and b_i move by
+      dA = sum dV (Y_ij Y_ij^T + Lambda),   db = sum dV Y_ij t_p^T   (Eq. 12-14).
+    Exactly, c' - c = (A + dA)^-1 (db - dA c) = (I + M dA)^-1 M (db - dA c) with M = A^-1, so
+      ||c' - c|| <= beta / (1 - gamma),
+      beta  = sum_j [ ||M Y_ij|| (stake_tw_ij + ||c^T Y_ij|| stake_ij) + ||M Lambda c||_F stake_ij ],
+      gamma = sum_j stake_ij (||M Y_ij|| ||Y_ij|| + ||M Lambda||_2)  (a bound on ||M dA||_2),
+    using ||t_p - c^T Y|| <= ||t_p|| + ||c^T Y||. Infinite where gamma >= 1.
+    c [N,B,K], A [N,B,B], Y [C,N,B], lam [B], stake and stake_tw [C,N] (own + up). Returns [N]
+    (and gamma [N] with with_gamma: any solve with A moves by at most gamma / (1 - gamma) relative)."""
+    N = c.shape[0]
+    lam = np.asarray(lam, np.float64)
+    out = np.zeros(N)
+    gam = np.zeros(N)
+    live = (stake > 0).any(0)
+    if w is not None:
+        live &= w > 0
+    idx = np.where(live)[0]
+    Lam = np.diag(lam)
+    for k0 in range(0, len(idx), chunk):
+        ii = idx[k0:k0 + chunk]
+        Ai = A[ii]
+        Yi = Y[:, ii, :]                                            # [C,n,B]
+        MY = np.linalg.solve(Ai, Yi.transpose(1, 2, 0))             # [n,B,C]
+        nMY = np.linalg.norm(MY, axis=1)                            # [n,C]
+        nY = np.linalg.norm(Yi, axis=2).T                           # [n,C]
+        ncol = np.linalg.norm(np.einsum("cnb,nbk->nck", Yi, c[ii]), axis=2)   # [n,C]
+        nMLc = np.linalg.norm(np.linalg.solve(Ai, lam[None, :, None] * c[ii]).reshape(len(ii), -1), axis=1)
+        nML = np.linalg.norm(np.linalg.solve(Ai, np.broadcast_to(Lam, Ai.shape)), ord=2, axis=(1, 2))
+        s = stake[:, ii].T
+        st = stake_tw[:, ii].T
+        beta = (nMY * (st + ncol * s)).sum(1) + nMLc * s.sum(1)
+        gamma = (s * nMY * nY).sum(1) + nML * s.sum(1)
+        out[ii] = np.where(gamma < 1.0, beta / np.maximum(1.0 - gamma, 1e-300), np.inf)
+        gam[ii] = gamma
+    return (out, gam) if with_gamma else out
 
 
 def refine(scene, cams, targets, sh_degree, lam, col, n_steps, threads=None):

@@ -325,7 +325,7 @@ def test_bruteforce_equals_scatter_bitwise():
         c = O._ocam(cams, j)
         tj = np.ascontiguousarray(t[j])
         lib.icgso_accumulate(sc.n, O._ptr(m), O._ptr(s), O._ptr(q), O._ptr(o), O.ctypes.byref(c), 3, O._ptr(tj),
-                             None, 1, 0.0, O._ptr(V[j]), O._ptr(S[j]), None, None)
+                             None, 1, 0.0, 0.0, O._ptr(V[j]), O._ptr(S[j]), None, None, None, None, None, None)
     np.testing.assert_array_equal(a[0], V)
     np.testing.assert_array_equal(a[1], S)
     coeffs = W.sh_coefficients(sc.n, 2, 3, seed=4)
@@ -469,7 +469,8 @@ def _loss(c, r):
 
 
 def test_adjoint_targets_exact_central_difference():
-    """L = sum r c^2 is quadratic in the targets, so a central difference is exact."""
+    """L = sum r c^2 is quadratic in the targets, so a central difference (h = 1e-3) is exact up to
+    rounding; 64 random pixels of the targets."""
     sc, cams = _tiny_random(31, n=30, n_cams=6, size=24)
     rng = np.random.default_rng(32)
     t = rng.uniform(0, 1, (cams.n, 24, 24, 3))
@@ -478,7 +479,7 @@ def test_adjoint_targets_exact_central_difference():
     col = O.colorize(sc, cams, t, L)
     gt, go = O.adjoint(sc, cams, t, L, None, 2 * r * col["c"], col=col)
     idx = np.argwhere(np.abs(gt) > 0)
-    pick = idx[rng.choice(len(idx), 24, replace=False)]
+    pick = idx[rng.choice(len(idx), 64, replace=False)]
     h = 1e-3
     for (j, y, x, k) in pick:
         tp = t.copy(); tp[j, y, x, k] += h
@@ -488,33 +489,44 @@ def test_adjoint_targets_exact_central_difference():
 
 
 def test_adjoint_opacity_central_difference():
-    sc, cams = _tiny_random(33, n=30, n_cams=6, size=24)
+    """Central differences (h = 1e-3) of L = sum r c^2 in 64 random opacities against the analytic
+    adjoint. A sample whose +-h evaluations change any contributor set (the alpha >= 1/255 or stop
+    decision of any pair) is redrawn and counted; opacities within h of the 0.99 cap are not drawn,
+    so no clamp changes either."""
+    sc, cams = _tiny_random(33, n=200, n_cams=6, size=32)
     rng = np.random.default_rng(34)
-    t = rng.uniform(0, 1, (cams.n, 24, 24, 3))
+    t = rng.uniform(0, 1, (cams.n, 32, 32, 3))
     L = 3
     r = rng.standard_normal((sc.n, 16, 3))
     col = O.colorize(sc, cams, t, L)
     gt, go = O.adjoint(sc, cams, t, L, None, 2 * r * col["c"], col=col)
-    h = 1e-4
+    h = 1e-3
+
+    def contributors(scene):
+        return [tuple(map(np.ndarray.tobytes, O.weights(scene, cams, j)[:2])) for j in range(cams.n)]
+
+    base = contributors(sc)
     checked = redrawn = 0
     for i in rng.permutation(sc.n):
-        if col["w"][i] == 0:
+        if col["w"][i] == 0 or sc.opacity[i] + 2 * h >= 0.99:
             continue
-        res = []
+        res, same = [], True
         for sgn in (1, -1):
             s2 = sc.subset(np.arange(sc.n)); s2.opacity[i] = np.float32(sc.opacity[i] + sgn * h)
             res.append(O.colorize(s2, cams, t, L))
-        # the step in float32 opacity is what the oracle sees
-        dh = float(np.float32(sc.opacity[i] + h)) - float(np.float32(sc.opacity[i] - h))
-        if not all(np.array_equal(x["pairs"], col["pairs"]) for x in res):
+            same = same and contributors(s2) == base
+        if not same:
             redrawn += 1
             continue
+        # the step in float32 opacity is what the oracle sees
+        dh = float(np.float32(sc.opacity[i] + h)) - float(np.float32(sc.opacity[i] - h))
         fd = (_loss(res[0]["c"], r) - _loss(res[1]["c"], r)) / dh
         assert fd == pytest.approx(go[i], rel=2e-3, abs=1e-6 * np.abs(go).max())
         checked += 1
-        if checked == 12:
+        if checked == 64:
             break
-    assert checked == 12
+    print(f"opacity FD: {checked} checked, {redrawn} redrawn")
+    assert checked == 64
 
 
 # ------------------------------------------------------------------------------------------
@@ -564,3 +576,139 @@ def test_refinement_step_is_preconditioned_render_gradient():
             cm = c0.copy(); cm[i, m, 0] -= h
             grad[i, m, 0] = (energy(cp) - energy(cm)) / (2 * h)
         np.testing.assert_allclose(col["A"][i] @ step[i, :, 0], -grad[i, :, 0], rtol=1e-6, atol=1e-9)
+
+
+# ------------------------------------------------------------------------------------------
+# Near-threshold stake (walk_pixel): what a flip of an alpha or stop decision can move
+# ------------------------------------------------------------------------------------------
+DA, DT = O.DELTA_ALPHA, O.DELTA_T
+
+
+def _centre_stack(opacities, depths=None, t=(0.3, 0.4, 0.5), px=16, scales=None):
+    """Gaussians centred on pixel (16, 16) of a 33x33 camera (projected mean = that pixel's
+    centre, so alpha there = opacity), front to back; walk pixel (px, 16) only. Returns the
+    accumulate_stakes dict and the scene."""
+    k = len(opacities)
+    depths = [2.0 + 0.25 * i for i in range(k)] if depths is None else depths
+    cams = one_camera(33, 33, cx=16.5, cy=16.5)
+    sc = scene_of([[0, 0, d] for d in depths], [[0.05] * 3] * k if scales is None else scales, opacities)
+    tgt = np.zeros((1, 33, 33, 3))
+    tgt[0, 16, px] = t
+    mask = np.zeros((1, 33, 33), bool)
+    mask[0, 16, px] = True
+    return O.accumulate_stakes(sc, cams, tgt, mask=mask, flags=True), sc
+
+
+def test_stake_alpha_near_threshold_taken():
+    """alpha = (1 + DA/2)/255 in front of an opaque-ish Gaussian: the oracle takes it (weight alpha),
+    and a renderer that skips it moves that weight and scales the T behind by 1/(1 - alpha). The
+    stake bounds both with alpha_hi = (1 + DA)/255: own = alpha_hi, up(back) = w_back alpha_hi/(1 - alpha_hi)."""
+    o_f = float(np.float32((1 + 0.5 * DA) / 255))
+    o_b = float(np.float32(0.5))
+    a, _ = _centre_stack([o_f, o_b])
+    a_hi = (1 + DA) / 255
+    w_b = o_b * (1 - o_f)
+    assert a["V"][0, 0] == pytest.approx(o_f, rel=1e-15)
+    assert a["V"][0, 1] == pytest.approx(w_b, rel=1e-15)
+    assert a["stake_own"][0, 0] == pytest.approx(a_hi, rel=1e-14)
+    assert a["stake_up"][0, 0] == 0.0 and a["stake_own"][0, 1] == 0.0
+    assert a["stake_up"][0, 1] == pytest.approx(w_b * a_hi / (1 - a_hi), rel=1e-14)
+    tn = math.sqrt(0.3 ** 2 + 0.4 ** 2 + 0.5 ** 2)
+    np.testing.assert_allclose(a["stake_tw"][0], (a["stake_own"][0] + a["stake_up"][0]) * tn, rtol=1e-14)
+    assert a["pix_flag"][0, 16, 16] == 1 and a["pix_flag"].sum() == 1
+    np.testing.assert_allclose(a["flag_w"][0], a["V"][0], rtol=1e-15)
+
+
+def test_stake_alpha_near_threshold_skipped():
+    """alpha = (1 - DA/2)/255 two pixels off the mean of the front Gaussian (isotropic, projected
+    variance (f s / Z)^2 + 0.3): skipped by the oracle (no weight), at stake all the same. (An opacity
+    below 1/255 would not do: both sides cull such a Gaussian exactly, on its float32 opacity.)"""
+    f, Z, s_f = 40.0, 2.0, float(np.float32(0.05))
+    var = (f * s_f / Z) ** 2 + 0.3
+    o_f = float(np.float32((1 - 0.5 * DA) / 255 * math.exp(4.0 / (2 * var))))
+    o_b = float(np.float32(0.5))
+    a, _ = _centre_stack([o_f, o_b], px=18, scales=[[s_f] * 3, [1.0] * 3])
+    alpha = o_f * math.exp(-4.0 / (2 * var))
+    assert abs(alpha * 255 - 1) <= DA and alpha < 1 / 255
+    a_hi = (1 + DA) / 255
+    w_b = a["V"][0, 1]
+    assert a["V"][0, 0] == 0.0 and w_b == pytest.approx(o_b, rel=1e-2)
+    assert a["stake_own"][0, 0] == pytest.approx(a_hi, rel=1e-14)
+    assert a["stake_up"][0, 1] == pytest.approx(w_b * a_hi / (1 - a_hi), rel=1e-14)
+    assert a["stake_up"][0, 0] == 0.0 and a["stake_own"][0, 1] == 0.0
+
+
+def test_no_stake_outside_the_margins():
+    o_f = float(np.float32((1 + 3 * DA) / 255))
+    a, _ = _centre_stack([o_f, 0.5, 0.5])
+    assert a["stake_own"].sum() == 0 and a["stake_up"].sum() == 0 and a["stake_tw"].sum() == 0
+    assert a["pix_flag"].sum() == 0 and a["flag_w"].sum() == 0
+
+
+def _stop_stack(rel_offset):
+    """Two Gaussians of opacity 0.95, then a third whose test T (1 - alpha) lands at
+    1e-4 (1 + rel_offset), then a fourth of opacity 0.3."""
+    o = float(np.float32(0.95))
+    T2 = (1 - o) ** 2
+    o3 = float(np.float32(1 - 1e-4 * (1 + rel_offset) / T2))
+    return [o, o, o3, float(np.float32(0.3))], T2
+
+
+def test_stake_stop_near_threshold_continued():
+    """test T = 1e-4 (1 + DT/2): the oracle takes the third Gaussian (weight alpha3 T2) and then
+    stops before the fourth, whose own stop decision is then also at stake (the T in front of it
+    may be the other side's)."""
+    ops, T2 = _stop_stack(0.5 * DT)
+    a, _ = _centre_stack(ops)
+    o3 = ops[2]
+    w3 = o3 * T2
+    tt = T2 * (1 - o3)
+    assert tt >= 1e-4 and abs(tt - 1e-4) <= DT * 1e-4
+    assert a["V"][0, 2] == pytest.approx(w3, rel=1e-13)
+    assert a["stake_own"][0, 2] == pytest.approx(w3, rel=1e-13)   # the weight a stop there would drop
+    # the fourth: T in front = tt, perturbation bound rel = 1; its own stop (tt * 0.7 < 1e-4) is
+    # decided within (DT + 1) of 1e-4, so its weight alpha4 tt (1 + 1) is at stake and the oracle stops
+    assert a["V"][0, 3] == 0.0
+    assert a["stake_own"][0, 3] == pytest.approx(ops[3] * tt * 2.0, rel=1e-13)
+    assert a["stake_own"][0, :2].sum() == 0 and a["stake_up"].sum() == 0
+
+
+def test_stake_stop_near_threshold_stopped():
+    """test T = 1e-4 (1 - DT/2): the oracle stops before the third Gaussian; a renderer that goes on
+    takes alpha3 T2 and could still take the fourth (bounded by T2 alpha4)."""
+    ops, T2 = _stop_stack(-0.5 * DT)
+    a, _ = _centre_stack(ops)
+    o3 = ops[2]
+    assert a["V"][0, 2] == 0.0 and a["V"][0, 3] == 0.0
+    assert a["stake_own"][0, 2] == pytest.approx(o3 * T2, rel=1e-13)
+    assert a["stake_up"][0, 3] == pytest.approx(T2 * ops[3], rel=1e-13)
+    assert a["stake_own"][0, 3] == 0.0
+
+
+def test_stake_bounds_every_planted_flip():
+    """Brute force: moving a threshold by 0.9 of its margin flips every decision that close to it.
+    Every change of V (and of S, through the target norms) on random scenes stays within the stake,
+    and every coefficient change within oracle.flip_bound."""
+    da, dt = 1e-3, 1e-3  # wider than the defaults, so that these small scenes have near decisions
+    for seed in (5, 6):
+        sc, cams = _tiny_random(seed, n=60, n_cams=6, size=32)
+        rng = np.random.default_rng(seed)
+        t = rng.uniform(0, 1, (cams.n, 32, 32, 3))
+        L = 2
+        col = O.colorize(sc, cams, t, L, delta=(da, dt))
+        stake = col["stake_own"] + col["stake_up"]
+        fb = O.flip_bound(col["c"], col["A"], col["Y"], col["lam"], stake, col["stake_tw"], w=col["w"])
+        moved = 0
+        for sa, st in ((1 + 0.9 * da, 1), (1 - 0.9 * da, 1), (1, 1 + 0.9 * dt), (1, 1 - 0.9 * dt),
+                       (1 - 0.9 * da, 1 + 0.9 * dt)):
+            with O.threshold_scale(sa, st):
+                c2 = O.colorize(sc, cams, t, L, delta=(da, dt))
+            dV = np.abs(c2["V"] - col["V"])
+            dS = np.linalg.norm(c2["S"] - col["S"], axis=-1)
+            assert (dV <= stake * (1 + 1e-12) + 1e-300).all()
+            assert (dS <= col["stake_tw"] * (1 + 1e-12) + 1e-300).all()
+            seen = (col["w"] > 0) & (c2["w"] > 0)
+            d = np.linalg.norm((c2["c"] - col["c"]).reshape(sc.n, -1), axis=1)
+            assert (d[seen] <= fb[seen] * (1 + 1e-9)).all()
+            moved += int((dV > 0).sum())
+        assert moved > 0
