@@ -20,8 +20,9 @@
  *     1.3 * (width/2)/fx, 1.3 * (height/2)/fy;
  *   - alpha = min(0.99, opacity * exp(-q/2)); pairs with alpha < 1/255 are skipped; the walk of a
  *     pixel stops before the first Gaussian that would bring T below 1e-4;
- *   - depth order: ascending float32(z), z evaluated in double as ((W20 x + W21 y) + W22 z) + W23
- *     with no fused multiply-add; equal keys in ascending Gaussian index;
+ *   - depth order: ascending float32 key fma(W22, z, fma(W21, y, fma(W20, x, W23))), three
+ *     correctly rounded float32 fused multiply-adds (the near-plane test uses the same key); equal
+ *     keys in ascending Gaussian index;
  *   - SH: real orthonormal harmonics, index l*l+l+m (m = -l..l), degree 1 = sqrt(3/(4 pi))*(y,z,x);
  *     no 0.5 colour offset and no clamp (Eq. 3 is linear).
  *
@@ -29,9 +30,13 @@
  *   - Pointers named "device" are CUDA device pointers owned by the caller; "host" pointers are
  *     read during the call only. The library never allocates device memory: every call takes a
  *     caller-owned workspace of at least the size returned by the matching *_workspace_size call.
- *   - All work is enqueued on `stream` (a cudaStream_t, NULL = legacy default stream). Each call
- *     ends by copying a small status block back to the host and synchronising `stream`, so results
- *     are complete when the call returns ICGS_OK.
+ *   - All work is enqueued on `stream` (a cudaStream_t, NULL = legacy default stream). The plain
+ *     calls end by copying a small status block back to the host and synchronising `stream`, so
+ *     results are complete when the call returns ICGS_OK. Their *_async twins (icgs_colorize_async,
+ *     icgs_colorize_backward_async, icgs_colorize_refine_async, icgs_render_async) never
+ *     synchronise: they check the arguments on the host, enqueue the work and return; the device
+ *     status (capacity overflow, timeouts, non-finite targets) stays in the workspace until
+ *     icgs_async_status reads it.
  *   - Calls on different streams with different workspaces may run concurrently.
  *   - On error the call returns a negative icgs_status; icgs_last_error() gives a message (per host
  *     thread). Outputs are then unspecified.
@@ -61,19 +66,22 @@ typedef enum {
                                          for; icgs_last_required_instances() gives the count to pass
                                          as icgs_options.instance_capacity */
   ICGS_ERR_UNSUPPORTED = -5,          /* valid request this build does not implement */
-  ICGS_ERR_DEVICE_TIMEOUT = -6        /* a bounded wait inside a kernel gave up (the kernel freed its
+  ICGS_ERR_DEVICE_TIMEOUT = -6,       /* a bounded wait inside a kernel gave up (the kernel freed its
                                          resources and returned; results are unspecified) */
+  ICGS_ERR_NONFINITE_INPUT = -7       /* a target value that a walk read (a pixel of a tile that some
+                                         Gaussian's support box reaches) is NaN or infinite; the
+                                         results are unspecified. Detected by the accumulate walks of
+                                         colorize and refine */
 } icgs_status;
 
 typedef enum { ICGS_F32 = 0, ICGS_BF16 = 1, ICGS_F16 = 2 } icgs_dtype;
 
 typedef enum {
   ICGS_PRECISION_PLAIN = 0, /* FP32 weights, CUDA-core contraction, plain FP32 fold and Cholesky */
-  ICGS_PRECISION_MIXED = 1  /* compensated FP32 fold, FP32 Cholesky refined in float-float;
-                               ill-conditioned Gaussians re-folded exactly from the per-camera sums
-                               (one pass) and, below cond_tau, solved in FP64; 16-bit targets
-                               with >= 16 channels contract on tcgen05 tensor cores (BF16/FP16
-                               in, FP32 acc) */
+  ICGS_PRECISION_MIXED = 1  /* fold with exact float-float products and compensated sums, FP32
+                               Cholesky refined in float-float against them; below cond_tau
+                               solved in FP64; 16-bit targets with >= 16 channels contract on
+                               tcgen05 tensor cores (BF16/FP16 in, FP32 acc) */
 } icgs_precision;
 
 /* Per-Gaussian status written to status_out. */
@@ -114,10 +122,11 @@ typedef struct {
                                   (<= 0 selects 1e-3); for a re-folded Gaussian (below) the test
                                   is against cond_tau * 1e-2 */
   float refold_tau;            /* MIXED, every camera in one pass: a Gaussian whose pivot ratio is
-                                  below refold_tau is re-folded exactly (float-float products and
-                                  sums) from its per-camera sums, removing the rounding of the
-                                  fast fold that the condition number amplifies. <= 0 selects
-                                  1e-2; > 1 re-folds every Gaussian */
+                                  below refold_tau is re-folded from its per-camera sums (a second,
+                                  independent float-float evaluation of its G, b, w) before the
+                                  solve. The MIXED fold itself forms every product and sum exactly
+                                  in float-float, so this is a cross-check, off by default: <= 0
+                                  selects none; > 1 re-folds every Gaussian */
   int32_t cam_batch;           /* cameras accumulated per pass; <= 0 selects min(n_cams, 128) */
   int64_t instance_capacity;   /* (Gaussian, tile) instances per pass the workspace holds; <= 0
                                   selects an estimate (see ICGS_ERR_CAPACITY) */
@@ -130,19 +139,44 @@ ICGS_API size_t icgs_workspace_size(const icgs_scene* scene, const icgs_cameras*
 /* Colorize (Alg. 1 lines 1-6, Eq. 14). Writes
  *   coeffs_out  device [n,(L+1)^2,K] float32: c_i (zero for Gaussians no pixel sees),
  *   status_out  device [n] uint8 (nullable): ICGS_GAUSSIAN_{OK,UNSEEN,FP64},
- *   chol_out    device [n,(L+1)^2((L+1)^2+1)/2] float32 (nullable): row-packed lower Cholesky
- *               factor of A_i = G_i + w_i Lambda (rows 0..B-1, row r holds L_r0..L_rr), which
- *               icgs_colorize_backward takes. */
+ *   chol_out    device [n, 3P] float32 (nullable), P = B(B+1)/2 with B = (L+1)^2: the solve record
+ *               that icgs_colorize_backward and icgs_colorize_refine take. Per Gaussian: the
+ *               row-packed lower Cholesky factor of A_i = G_i + w_i Lambda (P floats; row r holds
+ *               L_r0..L_rr), then A_i itself in float-float, row-packed lower triangle, P hi parts
+ *               followed by P lo parts (A = hi + lo; lo is 0 in PLAIN precision). The adjoint refines
+ *               its solve with A_i against the factor's rounding. Unseen Gaussians: all zero. */
 ICGS_API icgs_status icgs_colorize(const icgs_scene* scene, const icgs_cameras* cams,
                           const icgs_targets* targets, const icgs_options* opt,
                           void* workspace, size_t workspace_bytes,
                           float* coeffs_out, uint8_t* status_out, float* chol_out, void* stream);
 
+/* Several target sets on one geometry (Sec. 4: the same scene captured under different lightings;
+ * Sec. 3: the inverse of G_i + w_i Lambda is shared by every channel). sets[0..n_sets-1] are target
+ * image stacks of the same cameras, each with its own dtype and channel count K_s (1 <= n_sets <=
+ * 64). The projection, binning and depth sort run once per camera pass for all sets, each set is
+ * walked once (the tensor-core walk where it applies to that set), and one factorisation of A_i
+ * solves every set's channels as right-hand sides. Writes
+ *   coeffs_out  device [n,(L+1)^2,sum_s K_s] float32: the sets' coefficients, channels in set order
+ *               (identical arithmetic to icgs_colorize on the concatenated channels),
+ *   status_out, chol_out as for icgs_colorize (one record: the factorisation is shared),
+ *   keep_out    device [n, sum_s K_s] uint8 (nullable; needs sh_degree 0): the segmentation
+ *               threshold of Sec. 5, fused into the solve: 1 where the Gaussian's colour
+ *               c_i0 Y_0 >= threshold (the paper filters Gaussians below 0.6), 0 elsewhere and for
+ *               unseen Gaussians; with sh_degree > 0 ICGS_ERR_UNSUPPORTED.
+ * Workspace: icgs_sets_workspace_size() bytes (the colorize workspace of all channels plus one
+ * accumulator per set). Synchronises `stream`. The pair count of icgs_last_stats sums the sets. */
+ICGS_API size_t icgs_sets_workspace_size(const icgs_scene* scene, const icgs_cameras* cams, int32_t n_sets,
+                                         const icgs_targets* sets, const icgs_options* opt);
+ICGS_API icgs_status icgs_colorize_sets(const icgs_scene* scene, const icgs_cameras* cams, int32_t n_sets,
+                                        const icgs_targets* sets, const icgs_options* opt, void* workspace,
+                                        size_t workspace_bytes, float* coeffs_out, uint8_t* status_out,
+                                        float* chol_out, float threshold, uint8_t* keep_out, void* stream);
+
 /* Iterative refinement (Alg. 1 lines 7-10). Repeats n_steps times: render the images of the current
  * coefficients (Eq. 1-3), accumulate the visibility-weighted residual targets t - img as in Eq. 6
  * (V, Y and w are those of the fixed geometry), and update
  *     c_i <- c_i + A_i^-1 (sum_j Y_ij S_res_ij^T - w_i Lambda c_i)
- * with the factor of A_i = G_i + w_i Lambda that icgs_colorize returned (chol). coeffs_inout (device
+ * with the factor of A_i = G_i + w_i Lambda in the solve record icgs_colorize returned (chol, [n, 3P]). coeffs_inout (device
  * [n,(L+1)^2,K] float32) holds the coefficients of icgs_colorize on entry and the refined ones on
  * return. The residual walk always runs on CUDA cores (FP32), whatever the target dtype. Needs the
  * workspace size icgs_refine_workspace_size returns. */
@@ -154,10 +188,12 @@ ICGS_API icgs_status icgs_colorize_refine(const icgs_scene* scene, const icgs_ca
                                           size_t workspace_bytes, float* coeffs_inout, void* stream);
 
 /* Adjoint of icgs_colorize for a loss L(c): given dL/dc (grad_coeffs, device [n,(L+1)^2,K]),
- * the coefficients and Cholesky factors returned by icgs_colorize on the same inputs, writes
+ * the coefficients and solve records (chol, [n, 3P]) returned by icgs_colorize on the same inputs,
+ * writes
  *   grad_targets  device [n_cams,height,width,K] float32 (nullable): dL/dt,
  *   grad_opacity  device [n] float32 (nullable): dL/d(opacity) (overwritten, not accumulated).
- * The blend lists are recomputed, not stored. With u_i = A_i^-1 dL/dc_i: dL/dS_ij = Y_ij^T u_i,
+ * The blend lists are recomputed, not stored. With u_i = A_i^-1 dL/dc_i (the factor's solve, refined
+ * twice in float-float against the record's A_i): dL/dS_ij = Y_ij^T u_i,
  * dL/dV_ij = -sum_k u_ik^T (Y_ij Y_ij^T + Lambda) c_ik, and the per-pixel walk applies
  * d(alpha_m T_m)/d(alpha_n) (Eq. 2). Threshold decisions (alpha >= 1/255, the T stop, the 0.99 cap)
  * are held fixed, as in any rasterizer's gradient. */
@@ -226,30 +262,66 @@ ICGS_API icgs_status icgs_colorize_host(const icgs_scene* scene, const icgs_came
 
 /* Camera sharding of the normal equations (Eq. 12-14). The sums over cameras split over any
  * partition of the cameras: a caller with several GPUs (or several calls on one GPU) accumulates
- * each subset with icgs_accumulate, adds the results elementwise (an all-reduce across GPUs), and
- * solves once with icgs_solve. The paper has no such split; it is the same arithmetic in two steps.
+ * each subset with icgs_accumulate, sums the results elementwise (across GPUs a reduce-scatter over
+ * contiguous Gaussian ranges, so each GPU receives the totals of its own range), and solves each
+ * range with icgs_solve. The paper has no such split; it is the same arithmetic in two steps.
  *
- * icgs_accumulate: the normal equations of these cameras, written as float64 device arrays
- *   G_out [n, (L+1)^2, (L+1)^2]  sum_j V_ij Y_ij Y_ij^T (full symmetric matrix),
- *   b_out [n, (L+1)^2, channels] sum_j Y_ij S_ij^T,
- *   w_out [n]                    sum_j V_ij.
- * MIXED returns its compensated sums (hi + lo) in float64; add shards in float64. Workspace:
- * icgs_workspace_size() bytes (DEVICE, 256-byte aligned). Synchronises `stream`. */
+ * Packed layout, per Gaussian, icgs_normal_size(L, K) = P + B K + 1 doubles (B = (L+1)^2,
+ * P = B(B+1)/2): the upper triangle of G_i = sum_j V_ij Y_ij Y_ij^T row by row (row r holds columns
+ * r..B-1), then b_i = sum_j Y_ij S_ij^T as [B,K] row-major, then w_i = sum_j V_ij. MIXED returns its
+ * compensated sums (hi + lo) rounded once to double; add shards in double.
+ *
+ * icgs_accumulate: these cameras' sums, sums_out DEVICE [n, icgs_normal_size(L,K)] float64.
+ *   Workspace: icgs_workspace_size() bytes (DEVICE, 256-byte aligned). Synchronises `stream`. */
+ICGS_API int64_t icgs_normal_size(int32_t sh_degree, int32_t channels);
 ICGS_API icgs_status icgs_accumulate(const icgs_scene* scene, const icgs_cameras* cams,
                                      const icgs_targets* targets, const icgs_options* opt, void* workspace,
-                                     size_t workspace_bytes, double* G_out, double* b_out, double* w_out,
-                                     void* stream);
+                                     size_t workspace_bytes, double* sums_out, void* stream);
 
-/* icgs_solve: c_i = (G_i + w_i Lambda)^-1 b_i (Eq. 14) from float64 device sums laid out as
- * icgs_accumulate writes them, with the precision, lambda and cond_tau of opt (scene and camera
- * fields are not used). MIXED factorises in FP32 and refines in float-float against the sums split
- * into (hi, lo); below cond_tau it solves in FP64. There is no exact re-fold: the per-camera sums are
- * not available here. Outputs as for icgs_colorize (device). Workspace: icgs_solve_workspace_size()
- * bytes (DEVICE, 256-byte aligned). Synchronises `stream`. */
+/* icgs_solve: c_i = (G_i + w_i Lambda)^-1 b_i (Eq. 14) for n Gaussians from their packed float64
+ * device sums (any contiguous range of rows icgs_accumulate wrote, or their sum over shards), with
+ * the precision, lambda and cond_tau of opt (scene and camera fields are not used). MIXED
+ * factorises in FP32 and refines in float-float against the sums split into (hi, lo); below
+ * cond_tau it solves in FP64. There is no exact re-fold: the per-camera sums are not available here.
+ * Outputs as for icgs_colorize (device, n rows). Workspace: icgs_solve_workspace_size() bytes
+ * (DEVICE, 256-byte aligned). Synchronises `stream`. */
 ICGS_API size_t icgs_solve_workspace_size(int64_t n, int32_t sh_degree, int32_t channels, const icgs_options* opt);
-ICGS_API icgs_status icgs_solve(int64_t n, int32_t sh_degree, int32_t channels, const double* G, const double* b,
-                                const double* w, const icgs_options* opt, void* workspace, size_t workspace_bytes,
-                                float* coeffs_out, uint8_t* status_out, float* chol_out, void* stream);
+ICGS_API icgs_status icgs_solve(int64_t n, int32_t sh_degree, int32_t channels, const double* sums,
+                                const icgs_options* opt, void* workspace, size_t workspace_bytes, float* coeffs_out,
+                                uint8_t* status_out, float* chol_out, void* stream);
+
+/* Enqueue-only forms of icgs_colorize, icgs_colorize_backward, icgs_colorize_refine and
+ * icgs_render: the same arguments, checks and work, but the call returns as soon as the work is on
+ * `stream`, with no synchronisation and no device-to-host copy (the camera table and lambda reach
+ * the device as kernel parameters). A returned ICGS_OK means only that the arguments were valid and
+ * every launch was accepted; outputs and workspace must stay allocated, and the host arrays
+ * (cameras, lambda) may be released at once. The call's device outcome is read, after the work has
+ * finished, by icgs_async_status on the same workspace. Stage timing is not recorded, and
+ * icgs_last_stats reports the call only after icgs_async_status. */
+ICGS_API icgs_status icgs_colorize_async(const icgs_scene* scene, const icgs_cameras* cams,
+                                        const icgs_targets* targets, const icgs_options* opt, void* workspace,
+                                        size_t workspace_bytes, float* coeffs_out, uint8_t* status_out,
+                                        float* chol_out, void* stream);
+ICGS_API icgs_status icgs_colorize_backward_async(const icgs_scene* scene, const icgs_cameras* cams,
+                                                 const icgs_targets* targets, const icgs_options* opt,
+                                                 const float* coeffs, const float* chol, const float* grad_coeffs,
+                                                 void* workspace, size_t workspace_bytes, float* grad_targets,
+                                                 float* grad_opacity, void* stream);
+ICGS_API icgs_status icgs_colorize_refine_async(const icgs_scene* scene, const icgs_cameras* cams,
+                                               const icgs_targets* targets, const icgs_options* opt, int32_t n_steps,
+                                               const float* chol, void* workspace, size_t workspace_bytes,
+                                               float* coeffs_inout, void* stream);
+ICGS_API icgs_status icgs_render_async(const icgs_scene* scene, const icgs_cameras* cams, int32_t sh_degree,
+                                      int32_t channels, const float* coeffs, int64_t instance_capacity,
+                                      void* workspace, size_t workspace_bytes, float* images_out, void* stream);
+
+/* The device outcome of the last *_async call that used `workspace` (DEVICE, the same pointer):
+ * copies the status block back on `stream` and synchronises `stream`, so call it where the caller
+ * joins the work (every earlier call on that workspace has then finished). Returns ICGS_OK,
+ * ICGS_ERR_CAPACITY (icgs_last_required_instances() then gives the count to pass), or
+ * ICGS_ERR_DEVICE_TIMEOUT / ICGS_ERR_NONFINITE_INPUT; updates icgs_last_stats (the kernel count
+ * is not known here and reads 0). */
+ICGS_API icgs_status icgs_async_status(const void* workspace, void* stream);
 
 /* Size in bytes of the built-in scratch icgs_colorize_noalloc works in. */
 ICGS_API size_t icgs_noalloc_scratch_bytes(void);
@@ -267,6 +339,13 @@ ICGS_API icgs_status icgs_selftest_tc(const void* A, const void* B, int32_t N, i
  * MMA placed each row. Invalid M or N: ICGS_ERR_INVALID_ARG. Synchronises `stream`. */
 ICGS_API icgs_status icgs_selftest_tc_rows(const void* A, int32_t M, const void* B, int32_t N, int32_t bf16, float* D,
                                            float* D_lanes, void* workspace, void* stream);
+
+/* Diagnostic, for testing the failure path: sets, for the calls of this host thread, the time limit
+ * of the tensor-core walk's bounded mbarrier waits (limit_ns <= 0 restores the default, 1 s) and
+ * whether the walk issues its MMAs (issue_mma = 0: it issues none, so each wait runs out with no
+ * tensor-core work in flight, the kernel frees its TMEM and returns, and the call reports
+ * ICGS_ERR_DEVICE_TIMEOUT). Call icgs_debug_tc_wait(0, 1) to restore normal operation. */
+ICGS_API void icgs_debug_tc_wait(int64_t limit_ns, int32_t issue_mma);
 
 /* Message of the last failed call on this host thread ("" if none). */
 ICGS_API const char* icgs_last_error(void);

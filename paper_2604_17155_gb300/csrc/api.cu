@@ -141,6 +141,7 @@ Workspace carve(char* base, const Problem& p, int need) {
   if (need & kNeedBackward) {
     ws.payload = reinterpret_cast<float*>(take(sizeof(float) * (size_t)cbn * (K + 1)));
     ws.u = reinterpret_cast<float*>(take(sizeof(float) * n * B * K));
+    ws.u_lo = reinterpret_cast<float*>(take(sizeof(float) * n * B * K));
     ws.reg = reinterpret_cast<float*>(take(sizeof(float) * n));
   } else if (need & kNeedRender) {
     ws.payload = reinterpret_cast<float*>(take(sizeof(float) * (size_t)cbn * K));
@@ -189,7 +190,7 @@ icgs_status setup(const icgs_scene* sc, const icgs_cameras* cams, int K, int L, 
   p.B = (L + 1) * (L + 1);
   p.precision = precision;
   p.cond_tau = cond_tau > 0.0f ? cond_tau : 1e-3f;
-  p.refold_tau = refold_tau > 0.0f ? refold_tau : 1e-2f;
+  p.refold_tau = refold_tau > 0.0f ? refold_tau : 0.0f;
   p.cam_batch = cam_batch > 0 ? std::min(cam_batch, p.n_cams) : std::min(p.n_cams, 128);
   p.cam_batch = std::min(p.cam_batch, 65535);  // grid y dimension of the per-pair kernels
   if ((int64_t)p.cam_batch * p.tiles > 0x7FFFFFFFll)
@@ -239,14 +240,41 @@ void default_lambda(int L, float* lam) {
     for (int m = -l; m <= l; ++m) lam[l * l + l + m] = band[l];
 }
 
+// The camera table and lambda travel to the workspace as kernel parameters (copied at launch, up to
+// 32 KB on sm_70 and later), so no call waits on, or keeps alive, pageable host memory.
+constexpr int kUploadCams = 128;
+struct UploadBatch {
+  DevCam cams[kUploadCams];
+  float lam[kMaxSH];
+  int count;  // cameras in this batch
+  int n_lam;  // lambda entries (first batch only)
+};
+static_assert(sizeof(UploadBatch) + 2 * sizeof(void*) <= 32000, "kernel parameter space");
+
+__global__ void k_upload(const UploadBatch batch, DevCam* __restrict__ dst, float* __restrict__ lam_dst) {
+  const int t = threadIdx.x;
+  if (t < batch.count) dst[t] = batch.cams[t];
+  if (t < batch.n_lam) lam_dst[t] = batch.lam[t];
+}
+
 icgs_status upload_common(const Problem& p, const icgs_cameras* cams, const float* lam_host,
                           const Workspace& ws, cudaStream_t s) {
   const std::vector<DevCam> dc = build_cams(cams);
   g_launches = 0;
   ICGS_TRY_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(DevStatus), s));
-  ICGS_TRY_CUDA(cudaMemcpyAsync(ws.cams, dc.data(), sizeof(DevCam) * dc.size(), cudaMemcpyHostToDevice, s));
-  if (lam_host) ICGS_TRY_CUDA(cudaMemcpyAsync(ws.lam, lam_host, sizeof(float) * p.B, cudaMemcpyHostToDevice, s));
-  // pageable copies are staged before they return, so dc may go out of scope now
+  UploadBatch batch;
+  for (size_t j0 = 0; j0 < dc.size(); j0 += kUploadCams) {
+    std::memset(&batch, 0, sizeof batch);
+    batch.count = (int)std::min(dc.size() - j0, (size_t)kUploadCams);
+    std::memcpy(batch.cams, dc.data() + j0, sizeof(DevCam) * (size_t)batch.count);
+    if (j0 == 0 && lam_host) {
+      batch.n_lam = p.B;
+      std::memcpy(batch.lam, lam_host, sizeof(float) * (size_t)p.B);
+    }
+    k_upload<<<1, kUploadCams, 0, s>>>(batch, ws.cams + j0, ws.lam);
+    ICGS_TRY_CUDA(cudaGetLastError());
+    icgs::note_launches(1);
+  }
   g_timer.begin(s);
   return ICGS_OK;
 }
@@ -269,18 +297,16 @@ icgs_status bin_pass(const Problem& p, const icgs_scene* sc, int cb, bool sort_a
   return ICGS_OK;
 }
 
-icgs_status finish(const Workspace& ws, cudaStream_t s) {
-  ICGS_TRY_CUDA(cudaGetLastError());
-  DevStatus st;
-  ICGS_TRY_CUDA(cudaMemcpyAsync(&st, ws.status, sizeof st, cudaMemcpyDeviceToHost, s));
-  ICGS_TRY_CUDA(cudaStreamSynchronize(s));
-  g_timer.collect();
+// The outcome a call's device status block reports (read back after the work has finished).
+icgs_status status_of(const DevStatus& st) {
   g_required = (int64_t)st.instances_needed;
   if (st.flags & kFlagTimeout)
     return fail(ICGS_ERR_DEVICE_TIMEOUT, "a bounded wait for the tensor-core MMAs gave up");
   if (st.flags & kFlagOverflow)
     return fail(ICGS_ERR_CAPACITY, "a pass needed %lld (Gaussian, tile) instances; pass at least that as "
                 "icgs_options.instance_capacity", (long long)st.instances_needed);
+  if (st.flags & kFlagNonfinite)
+    return fail(ICGS_ERR_NONFINITE_INPUT, "a target value read by the walk is NaN or infinite");
   g_stats[0] = (int64_t)st.instances_total;
   g_stats[1] = (int64_t)st.contrib_pairs;
   g_stats[2] = (int64_t)st.fp64_count;
@@ -288,6 +314,27 @@ icgs_status finish(const Workspace& ws, cudaStream_t s) {
   g_stats[4] = (int64_t)st.refold_count;
   return ICGS_OK;
 }
+
+// End of a call: synchronous calls copy the status block back and synchronise `s`; enqueue-only
+// calls (sync false) only check that every launch was accepted.
+icgs_status finish(const Workspace& ws, cudaStream_t s, bool sync = true) {
+  ICGS_TRY_CUDA(cudaGetLastError());
+  if (!sync) return ICGS_OK;
+  DevStatus st;
+  ICGS_TRY_CUDA(cudaMemcpyAsync(&st, ws.status, sizeof st, cudaMemcpyDeviceToHost, s));
+  ICGS_TRY_CUDA(cudaStreamSynchronize(s));
+  g_timer.collect();
+  return status_of(st);
+}
+
+// Enqueue-only calls record no stage events (reading them back needs a synchronisation).
+struct TimerPause {
+  bool was;
+  explicit TimerPause(bool pause) : was(g_timer.on) {
+    if (pause) g_timer.on = false;
+  }
+  ~TimerPause() { g_timer.on = was; }
+};
 
 icgs_status check_targets(const icgs_targets* t) {
   if (!t || !t->data) return fail(ICGS_ERR_INVALID_ARG, "targets must not be NULL");
@@ -334,9 +381,10 @@ size_t icgs_workspace_size(const icgs_scene* scene, const icgs_cameras* cams, co
   return carve(nullptr, p, kNeedAccumulate | kNeedBackward).total;
 }
 
-icgs_status icgs_colorize(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
-                          const icgs_options* opt, void* workspace, size_t workspace_bytes, float* coeffs_out,
-                          uint8_t* status_out, float* chol_out, void* stream) {
+static icgs_status colorize_impl(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
+                                 const icgs_options* opt, void* workspace, size_t workspace_bytes, float* coeffs_out,
+                                 uint8_t* status_out, float* chol_out, void* stream, bool sync) {
+  TimerPause pause(!sync);
   g_err[0] = '\0';
   if (!opt) return fail(ICGS_ERR_INVALID_ARG, "options must not be NULL");
   icgs_status st = check_targets(targets);
@@ -375,6 +423,130 @@ icgs_status icgs_colorize(const icgs_scene* scene, const icgs_cameras* cams, con
   }
   launch_solve(p, ws.lam, lam, ws, coeffs_out, status_out, chol_out, scene->means,
                p.cam_batch >= p.n_cams ? p.n_cams : 0, s);
+  g_timer.mark(kSolve, s);
+  return finish(ws, s, sync);
+}
+
+namespace {
+
+// ---- target sets: several target images on one geometry ----
+constexpr int kMaxSets = 64;
+
+icgs_status check_sets(int32_t n_sets, const icgs_targets* sets, int& K_total) {
+  if (n_sets < 1 || n_sets > kMaxSets || !sets)
+    return fail(ICGS_ERR_INVALID_ARG, "n_sets = %d must be in 1..%d with a sets array", n_sets, kMaxSets);
+  K_total = 0;
+  for (int k = 0; k < n_sets; ++k) {
+    icgs_status st = check_targets(&sets[k]);
+    if (st != ICGS_OK) return st;
+    K_total += sets[k].channels;
+  }
+  return ICGS_OK;
+}
+
+int acc_stride_of(int K) { return (1 + K + 3) & ~3; }
+
+// Rows of an accumulator: one per Gaussian (L = 0, summed over every pass) or per (camera of the
+// pass, Gaussian) (L > 0, folded after each pass).
+int64_t acc_rows(const Problem& p) { return p.L == 0 ? p.n : (int64_t)p.cam_batch * p.n; }
+
+// Bytes of the per-set accumulator regions that follow the colorize workspace of the combined
+// channels; offs (nullable) receives each region's offset from the end of that workspace.
+size_t set_regions(const Problem& p, int32_t n_sets, const icgs_targets* sets, size_t* offs) {
+  size_t off = 0;
+  for (int k = 0; k < n_sets; ++k) {
+    if (offs) offs[k] = off;
+    off += align256(sizeof(float) * (size_t)acc_rows(p) * (size_t)acc_stride_of(sets[k].channels));
+  }
+  return off;
+}
+
+}  // namespace
+
+size_t icgs_sets_workspace_size(const icgs_scene* scene, const icgs_cameras* cams, int32_t n_sets,
+                                const icgs_targets* sets, const icgs_options* opt) {
+  int K = 0;
+  if (!opt || check_sets(n_sets, sets, K) != ICGS_OK) return 0;
+  Problem p;
+  if (setup(scene, cams, K, opt->sh_degree, opt->precision, opt->cond_tau, opt->refold_tau, opt->cam_batch,
+            opt->instance_capacity, p) != ICGS_OK)
+    return 0;
+  return carve(nullptr, p, kNeedAccumulate).total + set_regions(p, n_sets, sets, nullptr);
+}
+
+icgs_status icgs_colorize_sets(const icgs_scene* scene, const icgs_cameras* cams, int32_t n_sets,
+                               const icgs_targets* sets, const icgs_options* opt, void* workspace,
+                               size_t workspace_bytes, float* coeffs_out, uint8_t* status_out, float* chol_out,
+                               float threshold, uint8_t* keep_out, void* stream) {
+  g_err[0] = '\0';
+  if (!opt) return fail(ICGS_ERR_INVALID_ARG, "options must not be NULL");
+  int K = 0;
+  icgs_status st = check_sets(n_sets, sets, K);
+  if (st != ICGS_OK) return st;
+  Problem p;
+  st = setup(scene, cams, K, opt->sh_degree, opt->precision, opt->cond_tau, opt->refold_tau, opt->cam_batch,
+             opt->instance_capacity, p);
+  if (st != ICGS_OK) return st;
+  if (!coeffs_out && p.n > 0) return fail(ICGS_ERR_INVALID_ARG, "coeffs_out must not be NULL");
+  if (keep_out && p.L != 0)
+    return fail(ICGS_ERR_UNSUPPORTED, "the threshold epilogue needs sh_degree 0 (view-independent values)");
+  if (!std::isfinite(threshold)) return fail(ICGS_ERR_INVALID_ARG, "threshold must be finite");
+  float lam[kMaxSH];
+  if ((st = lambda_of(opt, p.L, lam)) != ICGS_OK) return st;
+  size_t offs[kMaxSets];
+  const size_t base_bytes = carve(nullptr, p, kNeedAccumulate).total;
+  const size_t need = base_bytes + set_regions(p, n_sets, sets, offs);
+  if (!workspace || workspace_bytes < need)
+    return fail(ICGS_ERR_WORKSPACE_TOO_SMALL, "workspace of %zu bytes, need %zu", workspace_bytes, need);
+  if (reinterpret_cast<uintptr_t>(workspace) % 256)
+    return fail(ICGS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(workspace);
+  const Workspace ws = carve(base, p, kNeedAccumulate);
+  float* set_acc[kMaxSets];
+  Problem ps[kMaxSets];
+  bool any_tc = false;
+  for (int k = 0, col0 = 0; k < n_sets; col0 += sets[k].channels, ++k) {
+    set_acc[k] = reinterpret_cast<float*>(base + base_bytes + offs[k]);
+    ps[k] = p;
+    ps[k].K = sets[k].channels;
+    ps[k].acc_stride = acc_stride_of(sets[k].channels);
+    any_tc = any_tc || tc_accumulate_applies(ps[k], (int)sets[k].dtype);
+  }
+  if (p.n == 0) return ICGS_OK;
+  if ((st = upload_common(p, cams, lam, ws, s)) != ICGS_OK) return st;
+  auto zero_accs = [&](int64_t rows) -> icgs_status {
+    ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)rows * p.acc_stride, s));
+    for (int k = 0; k < n_sets; ++k)
+      ICGS_TRY_CUDA(cudaMemsetAsync(set_acc[k], 0, sizeof(float) * (size_t)rows * ps[k].acc_stride, s));
+    return ICGS_OK;
+  };
+  auto merge_all = [&](int64_t rows) {
+    for (int k = 0, col0 = 0; k < n_sets; col0 += sets[k].channels, ++k)
+      launch_merge_set(rows, ps[k].K, ps[k].acc_stride, set_acc[k], p.acc_stride, col0, ws.acc, s);
+  };
+  if (p.L == 0 && (st = zero_accs(p.n)) != ICGS_OK) return st;
+  for (int cam0 = 0; cam0 < p.n_cams; cam0 += p.cam_batch) {
+    const int cb = std::min(p.cam_batch, p.n_cams - cam0);
+    Workspace wp = ws;
+    wp.cams = ws.cams + cam0;
+    if (p.L > 0 && (st = zero_accs((int64_t)cb * p.n)) != ICGS_OK) return st;
+    if ((st = bin_pass(p, scene, cb, any_tc, wp, s)) != ICGS_OK) return st;  // one binning for every set
+    for (int k = 0; k < n_sets; ++k) {
+      Workspace wk = wp;
+      wk.acc = set_acc[k];
+      launch_blend_accumulate(ps[k], cb, cam0, sets[k].data, (int)sets[k].dtype, nullptr, wk, s);
+    }
+    g_timer.mark(kBlend, s);
+    if (p.L > 0) {
+      merge_all((int64_t)cb * p.n);
+      launch_fold(p, scene->means, cb, cam0 == 0, true, wp, s);
+      g_timer.mark(kFold, s);
+    }
+  }
+  if (p.L == 0) merge_all(p.n);
+  launch_solve(p, ws.lam, lam, ws, coeffs_out, status_out, chol_out, scene->means,
+               p.cam_batch >= p.n_cams ? p.n_cams : 0, s, threshold, keep_out);
   g_timer.mark(kSolve, s);
   return finish(ws, s);
 }
@@ -526,9 +698,15 @@ icgs_status icgs_colorize_host(const icgs_scene* scene, const icgs_cameras* cams
   return finish(ws, s);
 }
 
+int64_t icgs_normal_size(int32_t sh_degree, int32_t channels) {
+  if (sh_degree < 0 || sh_degree > 3 || channels < 1) return 0;
+  const int64_t B = (int64_t)(sh_degree + 1) * (sh_degree + 1);
+  return B * (B + 1) / 2 + B * channels + 1;
+}
+
 icgs_status icgs_accumulate(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
-                            const icgs_options* opt, void* workspace, size_t workspace_bytes, double* G_out,
-                            double* b_out, double* w_out, void* stream) {
+                            const icgs_options* opt, void* workspace, size_t workspace_bytes, double* sums_out,
+                            void* stream) {
   g_err[0] = '\0';
   if (!opt) return fail(ICGS_ERR_INVALID_ARG, "options must not be NULL");
   icgs_status st = check_targets(targets);
@@ -537,7 +715,7 @@ icgs_status icgs_accumulate(const icgs_scene* scene, const icgs_cameras* cams, c
   st = setup(scene, cams, targets->channels, opt->sh_degree, opt->precision, opt->cond_tau, opt->refold_tau,
              opt->cam_batch, opt->instance_capacity, p);
   if (st != ICGS_OK) return st;
-  if ((!G_out || !b_out || !w_out) && p.n > 0) return fail(ICGS_ERR_INVALID_ARG, "G_out, b_out and w_out are required");
+  if (!sums_out && p.n > 0) return fail(ICGS_ERR_INVALID_ARG, "sums_out is required");
   const Workspace need = carve(nullptr, p, kNeedAccumulate);
   if (!workspace || workspace_bytes < need.total)
     return fail(ICGS_ERR_WORKSPACE_TOO_SMALL, "workspace of %zu bytes, need %zu", workspace_bytes, need.total);
@@ -563,7 +741,7 @@ icgs_status icgs_accumulate(const icgs_scene* scene, const icgs_cameras* cams, c
       g_timer.mark(kFold, s);
     }
   }
-  launch_export_normal(p, ws, G_out, b_out, w_out, s);
+  launch_export_normal(p, ws, sums_out, s);
   return finish(ws, s);
 }
 
@@ -627,15 +805,14 @@ size_t icgs_solve_workspace_size(int64_t n, int32_t sh_degree, int32_t channels,
   return carve_solve(nullptr, p).total;
 }
 
-icgs_status icgs_solve(int64_t n, int32_t sh_degree, int32_t channels, const double* G, const double* b,
-                       const double* w, const icgs_options* opt, void* workspace, size_t workspace_bytes,
-                       float* coeffs_out, uint8_t* status_out, float* chol_out, void* stream) {
+icgs_status icgs_solve(int64_t n, int32_t sh_degree, int32_t channels, const double* sums, const icgs_options* opt,
+                       void* workspace, size_t workspace_bytes, float* coeffs_out, uint8_t* status_out,
+                       float* chol_out, void* stream) {
   g_err[0] = '\0';
   Problem p;
   icgs_status st = setup_solve(n, sh_degree, channels, opt, p);
   if (st != ICGS_OK) return st;
-  if (p.n > 0 && (!G || !b || !w || !coeffs_out))
-    return fail(ICGS_ERR_INVALID_ARG, "G, b, w and coeffs_out are required");
+  if (p.n > 0 && (!sums || !coeffs_out)) return fail(ICGS_ERR_INVALID_ARG, "sums and coeffs_out are required");
   float lam[kMaxSH];
   if ((st = lambda_of(opt, p.L, lam)) != ICGS_OK) return st;
   const Workspace need = carve_solve(nullptr, p);
@@ -650,17 +827,18 @@ icgs_status icgs_solve(int64_t n, int32_t sh_degree, int32_t channels, const dou
   ICGS_TRY_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(DevStatus), s));
   ICGS_TRY_CUDA(cudaMemcpyAsync(ws.lam, lam, sizeof(float) * p.B, cudaMemcpyHostToDevice, s));
   g_timer.begin(s);
-  launch_import_normal(p, ws, G, b, w, s);
+  launch_import_normal(p, ws, sums, s);
   // the per-camera sums are not available here: no exact re-fold, FP64 below cond_tau
   launch_solve(p, ws.lam, lam, ws, coeffs_out, status_out, chol_out, nullptr, 0, s);
   g_timer.mark(kSolve, s);
   return finish(ws, s);
 }
 
-icgs_status icgs_colorize_backward(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
-                                   const icgs_options* opt, const float* coeffs, const float* chol,
-                                   const float* grad_coeffs, void* workspace, size_t workspace_bytes,
-                                   float* grad_targets, float* grad_opacity, void* stream) {
+static icgs_status backward_impl(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
+                                 const icgs_options* opt, const float* coeffs, const float* chol,
+                                 const float* grad_coeffs, void* workspace, size_t workspace_bytes,
+                                 float* grad_targets, float* grad_opacity, void* stream, bool sync) {
+  TimerPause pause(!sync);
   g_err[0] = '\0';
   if (!opt) return fail(ICGS_ERR_INVALID_ARG, "options must not be NULL");
   icgs_status st = check_targets(targets);
@@ -684,7 +862,7 @@ icgs_status icgs_colorize_backward(const icgs_scene* scene, const icgs_cameras* 
   if (p.n == 0) {
     if (grad_targets)
       ICGS_TRY_CUDA(cudaMemsetAsync(grad_targets, 0, sizeof(float) * (size_t)p.n_cams * p.width * p.height * p.K, s));
-    ICGS_TRY_CUDA(cudaStreamSynchronize(s));
+    if (sync) ICGS_TRY_CUDA(cudaStreamSynchronize(s));
     return ICGS_OK;
   }
   if ((st = upload_common(p, cams, lam, ws, s)) != ICGS_OK) return st;
@@ -702,7 +880,7 @@ icgs_status icgs_colorize_backward(const icgs_scene* scene, const icgs_cameras* 
     launch_blend_adjoint(p, cb, cam0, targets->data, (int)targets->dtype, wp, grad_targets, grad_opacity != nullptr, s);
     g_timer.mark(kBlend, s);
   }
-  return finish(ws, s);
+  return finish(ws, s, sync);
 }
 
 size_t icgs_refine_workspace_size(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
@@ -715,9 +893,10 @@ size_t icgs_refine_workspace_size(const icgs_scene* scene, const icgs_cameras* c
   return carve(nullptr, p, kNeedRefine).total;
 }
 
-icgs_status icgs_colorize_refine(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
-                                 const icgs_options* opt, int32_t n_steps, const float* chol, void* workspace,
-                                 size_t workspace_bytes, float* coeffs_inout, void* stream) {
+static icgs_status refine_impl(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
+                               const icgs_options* opt, int32_t n_steps, const float* chol, void* workspace,
+                               size_t workspace_bytes, float* coeffs_inout, void* stream, bool sync) {
+  TimerPause pause(!sync);
   g_err[0] = '\0';
   if (!opt) return fail(ICGS_ERR_INVALID_ARG, "options must not be NULL");
   icgs_status st = check_targets(targets);
@@ -769,7 +948,7 @@ icgs_status icgs_colorize_refine(const icgs_scene* scene, const icgs_cameras* ca
     launch_refine_update(p, ws.lam, lam, chol, ws, coeffs_inout, s);  // line 10
     g_timer.mark(kSolve, s);
   }
-  return finish(ws, s);
+  return finish(ws, s, sync);
 }
 
 size_t icgs_render_workspace_size(const icgs_scene* scene, const icgs_cameras* cams, int32_t sh_degree,
@@ -779,9 +958,10 @@ size_t icgs_render_workspace_size(const icgs_scene* scene, const icgs_cameras* c
   return carve(nullptr, p, kNeedRender).total;
 }
 
-icgs_status icgs_render(const icgs_scene* scene, const icgs_cameras* cams, int32_t sh_degree, int32_t channels,
-                        const float* coeffs, int64_t instance_capacity, void* workspace, size_t workspace_bytes,
-                        float* images_out, void* stream) {
+static icgs_status render_impl(const icgs_scene* scene, const icgs_cameras* cams, int32_t sh_degree,
+                               int32_t channels, const float* coeffs, int64_t instance_capacity, void* workspace,
+                               size_t workspace_bytes, float* images_out, void* stream, bool sync) {
+  TimerPause pause(!sync);
   g_err[0] = '\0';
   Problem p;
   icgs_status st = setup(scene, cams, channels, sh_degree, ICGS_PRECISION_PLAIN, 0.0f, 0.0f, 0, instance_capacity, p);
@@ -798,7 +978,7 @@ icgs_status icgs_render(const icgs_scene* scene, const icgs_cameras* cams, int32
   const Workspace ws = carve(static_cast<char*>(workspace), p, kNeedRender);
   if (p.n == 0) {
     ICGS_TRY_CUDA(cudaMemsetAsync(images_out, 0, sizeof(float) * (size_t)p.n_cams * p.width * p.height * p.K, s));
-    ICGS_TRY_CUDA(cudaStreamSynchronize(s));
+    if (sync) ICGS_TRY_CUDA(cudaStreamSynchronize(s));
     return ICGS_OK;
   }
   if ((st = upload_common(p, cams, nullptr, ws, s)) != ICGS_OK) return st;
@@ -812,7 +992,77 @@ icgs_status icgs_render(const icgs_scene* scene, const icgs_cameras* cams, int32
     launch_blend_render(p, cb, cam0, wp, images_out, s);
     g_timer.mark(kBlend, s);
   }
-  return finish(ws, s);
+  return finish(ws, s, sync);
+}
+
+icgs_status icgs_colorize(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
+                          const icgs_options* opt, void* workspace, size_t workspace_bytes, float* coeffs_out,
+                          uint8_t* status_out, float* chol_out, void* stream) {
+  return colorize_impl(scene, cams, targets, opt, workspace, workspace_bytes, coeffs_out, status_out, chol_out, stream,
+                       true);
+}
+
+icgs_status icgs_colorize_async(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
+                                const icgs_options* opt, void* workspace, size_t workspace_bytes, float* coeffs_out,
+                                uint8_t* status_out, float* chol_out, void* stream) {
+  return colorize_impl(scene, cams, targets, opt, workspace, workspace_bytes, coeffs_out, status_out, chol_out, stream,
+                       false);
+}
+
+icgs_status icgs_colorize_backward(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
+                                   const icgs_options* opt, const float* coeffs, const float* chol,
+                                   const float* grad_coeffs, void* workspace, size_t workspace_bytes,
+                                   float* grad_targets, float* grad_opacity, void* stream) {
+  return backward_impl(scene, cams, targets, opt, coeffs, chol, grad_coeffs, workspace, workspace_bytes, grad_targets,
+                       grad_opacity, stream, true);
+}
+
+icgs_status icgs_colorize_backward_async(const icgs_scene* scene, const icgs_cameras* cams,
+                                         const icgs_targets* targets, const icgs_options* opt, const float* coeffs,
+                                         const float* chol, const float* grad_coeffs, void* workspace,
+                                         size_t workspace_bytes, float* grad_targets, float* grad_opacity,
+                                         void* stream) {
+  return backward_impl(scene, cams, targets, opt, coeffs, chol, grad_coeffs, workspace, workspace_bytes, grad_targets,
+                       grad_opacity, stream, false);
+}
+
+icgs_status icgs_colorize_refine(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
+                                 const icgs_options* opt, int32_t n_steps, const float* chol, void* workspace,
+                                 size_t workspace_bytes, float* coeffs_inout, void* stream) {
+  return refine_impl(scene, cams, targets, opt, n_steps, chol, workspace, workspace_bytes, coeffs_inout, stream, true);
+}
+
+icgs_status icgs_colorize_refine_async(const icgs_scene* scene, const icgs_cameras* cams,
+                                       const icgs_targets* targets, const icgs_options* opt, int32_t n_steps,
+                                       const float* chol, void* workspace, size_t workspace_bytes,
+                                       float* coeffs_inout, void* stream) {
+  return refine_impl(scene, cams, targets, opt, n_steps, chol, workspace, workspace_bytes, coeffs_inout, stream, false);
+}
+
+icgs_status icgs_render(const icgs_scene* scene, const icgs_cameras* cams, int32_t sh_degree, int32_t channels,
+                        const float* coeffs, int64_t instance_capacity, void* workspace, size_t workspace_bytes,
+                        float* images_out, void* stream) {
+  return render_impl(scene, cams, sh_degree, channels, coeffs, instance_capacity, workspace, workspace_bytes,
+                     images_out, stream, true);
+}
+
+icgs_status icgs_render_async(const icgs_scene* scene, const icgs_cameras* cams, int32_t sh_degree,
+                              int32_t channels, const float* coeffs, int64_t instance_capacity, void* workspace,
+                              size_t workspace_bytes, float* images_out, void* stream) {
+  return render_impl(scene, cams, sh_degree, channels, coeffs, instance_capacity, workspace, workspace_bytes,
+                     images_out, stream, false);
+}
+
+icgs_status icgs_async_status(const void* workspace, void* stream) {
+  g_err[0] = '\0';
+  if (!workspace) return fail(ICGS_ERR_INVALID_ARG, "workspace must not be NULL");
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(ICGS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DevStatus st;
+  ICGS_TRY_CUDA(cudaMemcpyAsync(&st, workspace, sizeof st, cudaMemcpyDeviceToHost, s));
+  ICGS_TRY_CUDA(cudaStreamSynchronize(s));
+  g_launches = 0;
+  return status_of(st);
 }
 
 icgs_status icgs_selftest_tc_rows(const void* A, int32_t M, const void* B, int32_t N, int32_t bf16, float* D,
@@ -830,6 +1080,8 @@ icgs_status icgs_selftest_tc_rows(const void* A, int32_t M, const void* B, int32
                                    D_lanes, ws.status, s));
   return finish(ws, s);
 }
+
+void icgs_debug_tc_wait(int64_t limit_ns, int32_t issue_mma) { set_tc_wait_diagnostic(limit_ns, issue_mma != 0); }
 
 icgs_status icgs_selftest_tc(const void* A, const void* B, int32_t N, int32_t bf16, float* D, void* workspace,
                              void* stream) {

@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(kThreads, KC <= 8 ? 5 : 4) k_blend_accumulate(
 #pragma unroll
     for (int k = 0; k < KC; ++k)
       if (k0 + k < K) tv[k] = load_target(targets, base + k, dtype);
+    check_finite(tv, status);
     if (sub_img) {  // refinement: residual targets t - img, img of this pass's cameras
       const int64_t ib = (((int64_t)c.j * height + c.py) * width + c.px) * K + k0;
 #pragma unroll
@@ -231,6 +232,8 @@ __global__ void __launch_bounds__(kThreads2, 10) k_blend_accumulate2(
         }
       }
     }
+    check_finite(tv0, status);
+    check_finite(tv1, status);
   }
   // Value h NP + k of a hit pair is hit h's weights times u[k], u = (1, t_0, .., t_{KC-1}, 0, ..),
   // summed over the thread's two pixels. This lane keeps it in slot (h NP + k) ^ m
@@ -878,6 +881,8 @@ __global__ void __launch_bounds__(kThreads2, 10) k_blend_refine2(
         if (inside1) tv1[k] = load_target(targets, base + 4 * row + k, dtype) - img1[k];
       }
     }
+    check_finite(tv0, status);
+    check_finite(tv1, status);
   }
   // pass 2: the accumulate walk of k_blend_accumulate2 on the residuals
   const int m = lane >> SHIFT2;

@@ -16,9 +16,11 @@
 // mbarrier; warps 0-3 then read D back with tcgen05.ld (one Gaussian per thread) and add
 // (V, S_0..S_{KT-1}) to the accumulator with float4 atomics -- one atomic group per (Gaussian, tile).
 //
-// Every wait on the mbarrier is bounded: after kSpinLimit polls the kernel sets kFlagTimeout in the
-// status block (reported as ICGS_ERR_DEVICE_TIMEOUT), waits once more (also bounded) for the MMAs it
-// issued, frees its TMEM and returns.
+// Every wait on the mbarrier is bounded in time (1 s by %globaltimer): past the limit the kernel
+// sets kFlagTimeout in the status block (reported as ICGS_ERR_DEVICE_TIMEOUT), waits once more
+// (also bounded) for the MMAs it issued, frees its TMEM and returns. A diagnostic entry point
+// (icgs_debug_tc_wait) shortens the limit and can leave the MMAs unissued, so that a test drives a
+// wait past its limit with nothing in flight.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -35,7 +37,7 @@ using namespace walk;
 
 constexpr int kG = 128;                 // Gaussians per batch (MMA M)
 constexpr int kKPix = 256;              // pixels per tile (MMA K in total, 16 instructions of 16)
-constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // bounded mbarrier waits give up after 1 s
 constexpr uint32_t kTmemCols = 128;     // TMEM columns of the self-test (N <= 80)
 
 // ---- inline PTX ---------------------------------------------------------------------------
@@ -72,11 +74,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait; returns false (and the caller reports a timeout) after kSpinLimit polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t parity) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it)
-    if (mbar_try_wait(mbar, parity)) return true;
-  return false;
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait; returns false (and the caller reports a timeout) once limit_ns have passed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t parity, uint64_t limit_ns = kWaitLimitNs) {
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(mbar, parity))
+    if (global_ns() - t0 > limit_ns) return false;
+  return true;
 }
 
 // D[tmem] (+)= A[smem] * B[smem]^T, both operands K-major, kind::f16 (BF16 or FP16 in, FP32 out)
@@ -241,7 +249,7 @@ __global__ void __launch_bounds__(256, MG == 64 ? (KT <= 32 ? 4 : 3) : 2) k_blen
     const uint32_t* __restrict__ tile_off, const uint64_t* __restrict__ entries, uint32_t capacity,
     const ProjRec* __restrict__ rec, int64_t n, int width, int height, int tiles_x, int tiles,
     const uint16_t* __restrict__ targets, int K, int cam0, float* __restrict__ acc, int RS,
-    int64_t acc_cam_stride, DevStatus* status) {
+    int64_t acc_cam_stride, DevStatus* status, uint64_t wait_limit_ns, bool issue_mma) {
   constexpr int NB = tc_cols<KT, MG>();  // target channels + rows of ones (V)
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -285,8 +293,14 @@ __global__ void __launch_bounds__(256, MG == 64 ? (KT <= 32 ? 4 : 3) : 2) k_blen
       for (int k = 0; k < KT; ++k) tv[k] = (c.inside && k < K) ? src[k] : (uint16_t)0;
     }
     float tmax = 0.0f;
+    bool bad = false;
 #pragma unroll
-    for (int k = 0; k < KT; ++k) tmax = fmaxf(tmax, fabsf(target_value(tv[k], BF16_TARGETS)));
+    for (int k = 0; k < KT; ++k) {
+      const float x = target_value(tv[k], BF16_TARGETS);
+      tmax = fmaxf(tmax, fabsf(x));
+      bad |= !isfinite(x);
+    }
+    if (bad) atomicOr(&status->flags, kFlagNonfinite);
     // non-negative floats order like their bit patterns
     uint32_t m = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(tmax));
     if (lane == 0) s_tmax[warp] = m;
@@ -352,8 +366,8 @@ __global__ void __launch_bounds__(256, MG == 64 ? (KT <= 32 ? 4 : 3) : 2) k_blen
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
-    if (threadIdx.x == 0) issue_batch<NB, MG>(a_addr, b_addr, tmem, kIdesc, mbar);
-    const bool ok = mbar_wait_bounded(mbar, phase);
+    if (threadIdx.x == 0 && issue_mma) issue_batch<NB, MG>(a_addr, b_addr, tmem, kIdesc, mbar);
+    const bool ok = mbar_wait_bounded(mbar, phase, wait_limit_ns);
     phase ^= 1u;
     tc_fence_after();
     if (ok) {
@@ -404,7 +418,7 @@ __global__ void __launch_bounds__(256, MG == 64 ? (KT <= 32 ? 4 : 3) : 2) k_blen
     tc_fence_before();
     if (__syncthreads_or(timed_out)) {
       if ((threadIdx.x & 31) == 0) atomicOr(&status->flags, kFlagTimeout);
-      mbar_wait_bounded(mbar, phase ^ 1u);  // give the outstanding MMAs a last chance to finish
+      mbar_wait_bounded(mbar, phase ^ 1u, wait_limit_ns);  // give the outstanding MMAs a last chance to finish
       break;
     }
     if (__syncthreads_and(done)) break;
@@ -428,6 +442,11 @@ constexpr size_t tc_smem() {
   return 1024 + (size_t)MG * kKPix * 2 + (size_t)tc_cols<KT, MG>() * kKPix * 2 + (size_t)MG * (16 + 16 + 8 + 4) + 64;
 }
 
+// Diagnostic settings of this host thread (icgs_debug_tc_wait): the walk's wait limit and whether
+// it issues its MMAs.
+thread_local uint64_t g_wait_limit_ns = kWaitLimitNs;
+thread_local bool g_issue_mma = true;
+
 template <int KT, bool BF16_TARGETS>
 void accumulate_tc(const Problem& p, int cb, int cam0, const void* targets, const Workspace& ws, cudaStream_t s) {
   constexpr int MG = 64;
@@ -437,7 +456,8 @@ void accumulate_tc(const Problem& p, int cb, int cam0, const void* targets, cons
   const int64_t stride = p.L == 0 ? 0 : p.n * (int64_t)p.acc_stride;
   k_blend_accumulate_tc<KT, BF16_TARGETS, MG><<<cb * p.tiles, 256, smem, s>>>(
       ws.tile_off, ws.entries, p.capacity, ws.rec, p.n, p.width, p.height, p.tiles_x, p.tiles,
-      static_cast<const uint16_t*>(targets), p.K, cam0, ws.acc, p.acc_stride, stride, ws.status);
+      static_cast<const uint16_t*>(targets), p.K, cam0, ws.acc, p.acc_stride, stride, ws.status, g_wait_limit_ns,
+      g_issue_mma);
   note_launches(1);
 }
 
@@ -450,6 +470,11 @@ void accumulate_tc_dispatch(const Problem& p, int cb, int cam0, const void* targ
 }
 
 }  // namespace
+
+void set_tc_wait_diagnostic(int64_t limit_ns, bool issue_mma) {
+  g_wait_limit_ns = limit_ns > 0 ? (uint64_t)limit_ns : kWaitLimitNs;
+  g_issue_mma = issue_mma;
+}
 
 bool tc_accumulate_applies(const Problem& p, int dtype) {
   return p.precision == 1 && (dtype == 1 || dtype == 2) && p.K >= 16 && p.K <= 64;

@@ -17,6 +17,11 @@ constexpr int kSortCap = 4096;       // tile lists up to this length are sorted 
 constexpr uint32_t kMaxCapacity = 0x7FFFFFF0u;
 constexpr uint8_t kGaussOk = 0, kGaussUnseen = 1, kGaussFp64 = 2;  // icgs.h ICGS_GAUSSIAN_*
 
+// The per-Gaussian solve record the colorize calls write (chol_out) and the adjoint and refinement
+// read: P = B (B + 1) / 2 floats each of the row-packed lower Cholesky factor L of A = G + w Lambda,
+// then A itself in float-float, row-packed lower triangle, hi parts then lo parts.
+__host__ __device__ constexpr int solve_record_floats(int B) { return 3 * (B * (B + 1) / 2); }
+
 // Device status block at the start of every workspace; read back at the end of each call.
 struct DevStatus {
   uint32_t flags;             // kFlag* bits
@@ -28,7 +33,8 @@ struct DevStatus {
   uint32_t refold_count;      // Gaussians re-folded exactly from the per-camera sums
 };
 constexpr uint32_t kFlagOverflow = 1u;
-constexpr uint32_t kFlagTimeout = 2u;  // a bounded device-side wait gave up
+constexpr uint32_t kFlagTimeout = 2u;    // a bounded device-side wait gave up
+constexpr uint32_t kFlagNonfinite = 4u;  // a walk read a NaN or infinite target value
 
 // One camera as the kernels see it (built on the host from icgs_cameras).
 struct DevCam {
@@ -73,7 +79,8 @@ struct Workspace {
   float* blo = nullptr;            // [n * B * K]
   float* wsum = nullptr;           // [n]
   float* wlo = nullptr;            // [n]
-  float* u = nullptr;              // [n * B * K] backward: A^-1 dL/dc
+  float* u = nullptr;              // [n * B * K] backward: A^-1 dL/dc, hi part
+  float* u_lo = nullptr;           // [n * B * K] backward: its lo part (float-float)
   float* reg = nullptr;            // [n] backward: sum_mk lambda_m u_mk c_mk
   float* grad_o_acc = nullptr;     // [n]
   float* lam = nullptr;            // [B] Tikhonov weights
@@ -92,7 +99,7 @@ struct Problem {
   uint32_t capacity = 0;
   int precision = 0;
   float cond_tau = 1e-3f;       // MIXED: FP64 solve below this pivot ratio
-  float refold_tau = 1e-2f;     // MIXED, single pass: exact re-fold below this pivot ratio
+  float refold_tau = 0.0f;      // MIXED, single pass: exact re-fold below this pivot ratio (0: none)
   int mode = 0;                     // 0 colorize, 1 backward, 2 render
 };
 
@@ -118,6 +125,9 @@ void launch_blend_accumulate(const Problem& p, int cb, int cam0, const void* tar
 bool tc_accumulate_applies(const Problem& p, int dtype);
 void launch_blend_accumulate_tc(const Problem& p, int cb, int cam0, const void* targets, int dtype,
                                 const Workspace& ws, cudaStream_t s);
+// Diagnostic (this host thread): the tensor-core walk's wait limit (<= 0: the default 1 s) and
+// whether it issues its MMAs (false: every wait runs out, with nothing in flight).
+void set_tc_wait_diagnostic(int64_t limit_ns, bool issue_mma);
 cudaError_t launch_tc_selftest(const uint16_t* A, int M, const uint16_t* B, int N, bool bf16, float* D, float* D_lanes,
                                DevStatus* status, cudaStream_t s);
 void launch_fold(const Problem& p, const float* means, int cb, bool first, bool want_gram, const Workspace& ws,
@@ -127,13 +137,17 @@ void launch_refine_update(const Problem& p, const float* lam_dev, const float* l
                           const Workspace& ws, float* coeffs, cudaStream_t s);
 // means/cams/n_acc_cams: when every camera was accumulated in one pass (n_acc_cams > 0), a MIXED
 // solve re-folds each Gaussian it flags in FP64 from the per-camera sums still in ws.acc.
+// keep (nullable, L = 0 only): per Gaussian and channel, 1 where the colour c Y_0 reaches tau.
 void launch_solve(const Problem& p, const float* lam_dev, const float* lam_host, const Workspace& ws,
                   float* coeffs, uint8_t* status, float* chol, const float* means, int n_acc_cams,
-                  cudaStream_t s);
-// The normal equations of the current workspace as double (hi + lo), and back (camera sharding).
-void launch_export_normal(const Problem& p, const Workspace& ws, double* G, double* b, double* w, cudaStream_t s);
-void launch_import_normal(const Problem& p, const Workspace& ws, const double* G, const double* b, const double* w,
-                          cudaStream_t s);
+                  cudaStream_t s, float tau = 0.0f, uint8_t* keep = nullptr);
+// Copies one target set's accumulator rows (V, S_0..S_{Ks-1}, row stride RSs) into the combined
+// rows (stride RS): S to columns 1 + col0.., V only for the first set (col0 == 0).
+void launch_merge_set(int64_t rows, int Ks, int RSs, const float* src, int RS, int col0, float* dst, cudaStream_t s);
+// The normal equations of the current workspace as packed doubles (hi + lo; per Gaussian the upper
+// triangle of G row by row, then b [B,K], then w), and back (camera sharding).
+void launch_export_normal(const Problem& p, const Workspace& ws, double* sums, cudaStream_t s);
+void launch_import_normal(const Problem& p, const Workspace& ws, const double* sums, cudaStream_t s);
 void launch_payload_render(const Problem& p, const float* means, const float* coeffs, int cb,
                            const Workspace& ws, cudaStream_t s);
 void launch_blend_render(const Problem& p, int cb, int cam0, const Workspace& ws, float* images,

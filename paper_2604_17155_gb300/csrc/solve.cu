@@ -2,8 +2,8 @@
 //
 //   k_fold          G_i += sum_j V_ij Y_ij Y_ij^T, b_i += sum_j Y_ij S_ij^T, w_i += sum_j V_ij over the
 //                   cameras of one pass (L > 0). One 8-lane group per Gaussian: lane r forms wrapped
-//                   diagonal r of the symmetric G_i and rows r, r + 8 of b_i. MIXED keeps a TwoSum
-//                   compensation term per entry.
+//                   diagonal r of the symmetric G_i and rows r, r + 8 of b_i. MIXED forms every
+//                   product exactly (TwoProduct) and keeps a TwoSum compensation term per entry.
 //   k_solve         A_i = G_i + w_i Lambda; Cholesky with the rows in registers of the group (pivots
 //                   and columns exchanged by shuffles); forward and back substitution per channel.
 //                   MIXED: the FP32 solution is refined in float-float against the compensated sums;
@@ -15,6 +15,7 @@
 //   k_payload_*     per (camera, Gaussian): C = Y . c (render) or (a = Y . u, beta) (adjoint).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "icgs_device.cuh"
@@ -27,7 +28,6 @@ namespace {
 constexpr int kGroup = 16;
 constexpr int kSolveThreads = 128;  // 8 Gaussians per CTA
 constexpr float kY0 = 0.28209479177387814f;
-constexpr int kFoldBlock = 4;  // cameras summed in plain FP32 before a compensated add (MIXED)
 
 // Shuffles name only the 16 lanes of the caller's group, so a neighbouring group that has
 // finished (or never started) in the same warp does not take part.
@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_fold(
   static_assert(ND <= GS, "one diagonal per lane");
   __shared__ __align__(16) float s_Y[kSolveThreads][kYStride];
   __shared__ float s_vY[kSolveThreads][kVStride];
+  __shared__ float s_vYl[MIXED ? kSolveThreads : 1][MIXED ? kVStride : 1];  // lo parts of v Y (MIXED)
   const int64_t i = (blockIdx.x * (int64_t)kSolveThreads + threadIdx.x) / GS;
   const int r = threadIdx.x % GS;
   if (i >= n) return;  // whole groups exit together
@@ -125,15 +126,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_fold(
   }
   const float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
   const int64_t stride = n * (int64_t)RS;
-  // MIXED: plain FP32 partial sums over blocks of kFoldBlock cameras, each block added to the
-  // running (hi, lo) pair with one TwoSum
-  float pg[NG], pb[NR][KC], pw = 0.0f;
-#pragma unroll
-  for (int s = 0; s < NG; ++s) pg[s] = 0.0f;
-#pragma unroll
-  for (int m = 0; m < NR; ++m)
-#pragma unroll
-    for (int k = 0; k < KC; ++k) pb[m][k] = 0.0f;
+  // MIXED: every product is exact in float-float (v Y_r split by an FMA, then each entry's product
+  // split again) and every addition a TwoSum into the running (hi, lo) pair, so G, b and w are the
+  // sums of the float32 basis to about 2^-44 relative -- the same basis the adjoint's payload uses
   const unsigned gm = fold_group_mask();
   const int gbase = threadIdx.x & ~(GS - 1);
   // 8 cameras at a time: lane q loads camera jb + q's row (V, S), evaluates its basis Y into s_Y
@@ -164,6 +159,11 @@ __global__ void __launch_bounds__(kSolveThreads) k_fold(
           const float vy = lv * Yl[c];
           s_vY[threadIdx.x][c] = vy;
           s_vY[threadIdx.x][c + B] = vy;
+          if constexpr (MIXED) {
+            const float vyl = fmaf(lv, Yl[c], -vy);
+            s_vYl[threadIdx.x][c] = vyl;
+            s_vYl[threadIdx.x][c + B] = vyl;
+          }
         }
       }
     }
@@ -185,20 +185,33 @@ __global__ void __launch_bounds__(kSolveThreads) k_fold(
             Y[4 * c4] = y4.x; Y[4 * c4 + 1] = y4.y; Y[4 * c4 + 2] = y4.z; Y[4 * c4 + 3] = y4.w;
           }
           const float* vq = s_vY[gbase + q] + r;  // vq[c] = v Y[(c + r) mod B]
+          const float* vql = s_vYl[MIXED ? gbase + q : 0] + (MIXED ? r : 0);
 #pragma unroll
           for (int s = 0; s < B; ++s) {
-            if constexpr (MIXED) pg[s] = fmaf(vq[s], Y[s], pg[s]);
-            else g[s] = fmaf(vq[s], Y[s], g[s]);
+            if constexpr (MIXED) {
+              const float p = vq[s] * Y[s];
+              const float e = fmaf(vq[s], Y[s], -p) + vql[s] * Y[s];
+              two_sum_acc(g[s], gl[s], p);
+              gl[s] += e;
+            } else {
+              g[s] = fmaf(vq[s], Y[s], g[s]);
+            }
           }
           if constexpr (kHalf) {
             if (half_slot) {  // entry (r + B/2, r): v Y[r + B/2] Y[r]
-              if constexpr (MIXED) pg[B] = fmaf(vq[B / 2], Yq[r], pg[B]);
-              else g[B] = fmaf(vq[B / 2], Yq[r], g[B]);
+              if constexpr (MIXED) {
+                const float p = vq[B / 2] * Yq[r];
+                const float e = fmaf(vq[B / 2], Yq[r], -p) + vql[B / 2] * Yq[r];
+                two_sum_acc(g[B], gl[B], p);
+                gl[B] += e;
+              } else {
+                g[B] = fmaf(vq[B / 2], Yq[r], g[B]);
+              }
             }
           }
         }
         if (do_w) {
-          if constexpr (MIXED) pw += v;
+          if constexpr (MIXED) two_sum_acc(w, wl, v);
           else w += v;
         }
 #pragma unroll
@@ -208,26 +221,15 @@ __global__ void __launch_bounds__(kSolveThreads) k_fold(
 #pragma unroll
           for (int k = 0; k < KC; ++k)
             if (k0 + k < K) {
-              if constexpr (MIXED) pb[m][k] = fmaf(Yr, sv[k], pb[m][k]);
-              else bb[m][k] = fmaf(Yr, sv[k], bb[m][k]);
+              if constexpr (MIXED) {
+                const float p = Yr * sv[k];
+                two_sum_acc(bb[m][k], bl[m][k], p);
+                bl[m][k] += fmaf(Yr, sv[k], -p);
+              } else {
+                bb[m][k] = fmaf(Yr, sv[k], bb[m][k]);
+              }
             }
         }
-      }
-      if (MIXED && ((j % kFoldBlock) == kFoldBlock - 1 || j == cb - 1)) {
-#pragma unroll
-        for (int s = 0; s < NG; ++s) {
-          two_sum_acc(g[s], gl[s], pg[s]);
-          pg[s] = 0.0f;
-        }
-        two_sum_acc(w, wl, pw);
-        pw = 0.0f;
-#pragma unroll
-        for (int m = 0; m < NR; ++m)
-#pragma unroll
-          for (int k = 0; k < KC; ++k) {
-            two_sum_acc(bb[m][k], bl[m][k], pb[m][k]);
-            pb[m][k] = 0.0f;
-          }
       }
     }
     __syncwarp(gm);
@@ -481,11 +483,18 @@ __global__ void __launch_bounds__(kSolveThreads, 5) k_solve(
   const bool row = r < B;
   float w = wsum[i];
   const float lam_r = row ? lam[r] : 0.0f;
+  constexpr int P = B * (B + 1) / 2;
+  float* rec = chol ? chol + i * solve_record_floats(B) : nullptr;
   if (!(w > 0.0f)) {
     if (row) {
       for (int k = 0; k < K; ++k) coeffs[(i * B + r) * K + k] = 0.0f;
-      if (chol)
-        for (int c = 0; c <= r; ++c) chol[i * (B * (B + 1) / 2) + r * (r + 1) / 2 + c] = 0.0f;  // no register array
+      if (rec)
+        for (int c = 0; c <= r; ++c) {  // no register array
+          const int e = r * (r + 1) / 2 + c;
+          rec[e] = 0.0f;
+          rec[P + e] = 0.0f;
+          rec[2 * P + e] = 0.0f;
+        }
     }
     if (r == 0 && status_out) status_out[i] = kGaussUnseen;
     return;
@@ -495,6 +504,14 @@ __global__ void __launch_bounds__(kSolveThreads, 5) k_solve(
   for (int c = 0; c < B; ++c) {
     a[c] = row ? G[(i * B + r) * B + c] : 0.0f;
     if (c == r) a[c] += w * lam_r;
+  }
+  if (!MIXED && rec && row) {  // PLAIN: A in FP32 (no compensation term)
+#pragma unroll
+    for (int c = 0; c < B; ++c)
+      if (c <= r) {
+        rec[P + r * (r + 1) / 2 + c] = a[c];
+        rec[2 * P + r * (r + 1) / 2 + c] = 0.0f;
+      }
   }
   float minratio = group_cholesky<B, float>(a, r);
   // MIXED: rows of G_hi, G_lo (and w_lo) for the residuals of the refinement
@@ -534,6 +551,20 @@ __global__ void __launch_bounds__(kSolveThreads, 5) k_solve(
         glo[c] = row ? Glo[(i * B + r) * B + c] : 0.0f;
       }
     }
+  }
+  if (MIXED && rec && row) {  // A = (G_hi + G_lo) + (w_hi + w_lo) Lambda in float-float
+#pragma unroll
+    for (int c = 0; c < B; ++c)
+      if (c <= r) {
+        float hi = ghi[c], lo = glo[c];
+        if (c == r) {
+          const float p = w * lam_r;
+          two_sum_acc(hi, lo, p);
+          lo += fmaf(w, lam_r, -p) + wl * lam_r;
+        }
+        rec[P + r * (r + 1) / 2 + c] = hi;
+        rec[2 * P + r * (r + 1) / 2 + c] = lo;
+      }
   }
   const bool fp64 = MIXED && !(minratio >= (refold ? cond_tau * kRefoldFp64Scale : cond_tau));
   if (!fp64) {
@@ -590,7 +621,7 @@ __global__ void __launch_bounds__(kSolveThreads, 5) k_solve(
     if (chol && row) {
 #pragma unroll
       for (int c = 0; c < B; ++c)
-        if (c <= r) chol[i * (B * (B + 1) / 2) + r * (r + 1) / 2 + c] = a[c];
+        if (c <= r) chol[i * solve_record_floats(B) + r * (r + 1) / 2 + c] = a[c];
     }
     if (r == 0 && status_out) status_out[i] = kGaussOk;
     return;
@@ -633,7 +664,7 @@ __global__ void __launch_bounds__(kSolveThreads, 5) k_solve(
   if (chol && row) {
 #pragma unroll
     for (int c = 0; c < B; ++c)
-      if (c <= r) chol[i * (B * (B + 1) / 2) + r * (r + 1) / 2 + c] = (float)ad[c];
+      if (c <= r) chol[i * solve_record_floats(B) + r * (r + 1) / 2 + c] = (float)ad[c];
   }
   if (r == 0) {
     if (status_out) status_out[i] = kGaussFp64;
@@ -641,10 +672,12 @@ __global__ void __launch_bounds__(kSolveThreads, 5) k_solve(
   }
 }
 
-// L = 0: acc[i] = (V, S_0..S_{K-1}) summed over every camera.
+// L = 0: acc[i] = (V, S_0..S_{K-1}) summed over every camera. keep (nullable) receives, per
+// Gaussian and channel, whether the colour c Y_0 reaches tau (the segmentation threshold; 0 for
+// Gaussians no camera sees).
 __global__ void k_solve_l0(int64_t n, int K, int RS, const float* __restrict__ acc, float lam0,
                            float* __restrict__ coeffs, uint8_t* __restrict__ status_out,
-                           float* __restrict__ chol) {
+                           float* __restrict__ chol, float tau, uint8_t* __restrict__ keep) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= n * (int64_t)K) return;
   const int64_t i = idx / K;
@@ -653,59 +686,121 @@ __global__ void k_solve_l0(int64_t n, int K, int RS, const float* __restrict__ a
   float c = 0.0f;
   if (V > 0.0f) {
     // (Y0^2 V + V lambda) c = Y0 S
-    const float A = V * (kY0 * kY0 + lam0);
+    const float y = kY0 * kY0 + lam0;
+    const float A = V * y;
     c = kY0 * acc[i * RS + 1 + k] / A;
-    if (k == 0 && chol) chol[i] = sqrtf(A);
+    if (k == 0 && chol) {  // record: sqrt(A), then A = V y exactly as hi + lo
+      chol[3 * i] = sqrtf(A);
+      chol[3 * i + 1] = A;
+      chol[3 * i + 2] = fmaf(V, y, -A);
+    }
   } else if (k == 0 && chol) {
-    chol[i] = 0.0f;
+    chol[3 * i] = 0.0f;
+    chol[3 * i + 1] = 0.0f;
+    chol[3 * i + 2] = 0.0f;
   }
   coeffs[i * K + k] = c;
+  if (keep) keep[i * K + k] = (V > 0.0f && c * kY0 >= tau) ? 1 : 0;
   if (k == 0 && status_out) status_out[i] = V > 0.0f ? kGaussOk : kGaussUnseen;
 }
 
 // ------------------------------------------------------------------------------------------
 // adjoint preparation: u = A^-1 g from the factor, reg = sum_mk lambda_m u_mk c_mk
 // ------------------------------------------------------------------------------------------
+// The FP32 solve with the stored factor is refined twice in float-float against A = A_hi + A_lo of
+// the record (the same sums the forward solve used), so u carries the forward's accuracy instead of
+// the factor's rounding amplified by the condition number.
+constexpr int kAdjointRefineSteps = 2;
+
+// Residual g - (A_hi + A_lo)(x_hi + x_lo) of row r in float-float (TwoProduct / TwoSum), for an
+// iterate that is itself float-float.
+template <int B>
+__device__ __forceinline__ float residual_ff(const float (&ahi)[B], const float (&alo)[B], float g, float x_hi,
+                                            float x_lo, int r) {
+  const unsigned m = group_mask();
+  float s = 0.0f, comp = 0.0f;
+#pragma unroll
+  for (int c = 0; c < B; ++c) {
+    const float xh = __shfl_sync(m, x_hi, c, kGroup);
+    const float xl = __shfl_sync(m, x_lo, c, kGroup);
+    const float p = ahi[c] * xh;
+    const float e = fmaf(ahi[c], xh, -p);
+    two_sum_acc(s, comp, p);
+    comp += e + alo[c] * xh + ahi[c] * xl;
+  }
+  return r < B ? (g - s) - comp : 0.0f;
+}
+
 template <int B>
 __global__ void __launch_bounds__(kSolveThreads) k_adjoint_prep(
     int64_t n, int K, const float* __restrict__ chol, const float* __restrict__ grad_c,
     const float* __restrict__ coeffs, const float* __restrict__ lam, float* __restrict__ u,
-    float* __restrict__ reg) {
+    float* __restrict__ u_lo, float* __restrict__ reg) {
+  constexpr int P = B * (B + 1) / 2;
   const int64_t i = (blockIdx.x * (int64_t)kSolveThreads + threadIdx.x) / kGroup;
   const int r = threadIdx.x % kGroup;
   if (i >= n) return;
   const bool row = r < B;
-  float a[B];
+  const float* rec = chol + i * solve_record_floats(B);
+  float a[B], ahi[B], alo[B];
 #pragma unroll
-  for (int c = 0; c < B; ++c) a[c] = (row && c <= r) ? chol[i * (B * (B + 1) / 2) + r * (r + 1) / 2 + c] : 0.0f;
+  for (int c = 0; c < B; ++c) {
+    a[c] = (row && c <= r) ? rec[r * (r + 1) / 2 + c] : 0.0f;
+    const int hi = r > c ? r : c, lo = r > c ? c : r;  // row r of the symmetric A from its lower triangle
+    ahi[c] = row ? rec[P + hi * (hi + 1) / 2 + lo] : 0.0f;
+    alo[c] = row ? rec[2 * P + hi * (hi + 1) / 2 + lo] : 0.0f;
+  }
   const float l00 = __shfl_sync(group_mask(), a[0], 0, kGroup);
   const bool seen = l00 > 0.0f;
-  float rg = 0.0f;
+  double rg = 0.0;  // sum lambda_m u_mk c_mk: large u terms can cancel, so in double (per Gaussian only)
   for (int k = 0; k < K; ++k) {
-    float x = row ? grad_c[(i * B + r) * K + k] : 0.0f;
-    if (seen) group_chol_solve<B, float>(a, r, x);
-    else x = 0.0f;
+    const float g = row ? grad_c[(i * B + r) * K + k] : 0.0f;
+    float xh = 0.0f, xl = 0.0f;
+    if (seen) {
+      xh = g;
+      group_chol_solve<B, float>(a, r, xh);
+#pragma unroll 1
+      for (int it = 0; it < kAdjointRefineSteps; ++it) {
+        float d = residual_ff<B>(ahi, alo, g, xh, xl, r);
+        group_chol_solve<B, float>(a, r, d);
+        float e = 0.0f;
+        two_sum_acc(xh, e, d);  // (xh, e) = xh + d exactly
+        xl += e;
+        const float t = xh + xl;  // renormalise the pair
+        xl = xl - (t - xh);
+        xh = t;
+      }
+    }
     if (row) {
-      u[(i * B + r) * K + k] = x;
-      rg = fmaf(lam[r] * x, coeffs[(i * B + r) * K + k], rg);
+      u[(i * B + r) * K + k] = xh;
+      u_lo[(i * B + r) * K + k] = xl;
+      rg += (double)lam[r] * (double)coeffs[(i * B + r) * K + k] * ((double)xh + (double)xl);
     }
   }
-  rg = group_sum(rg);
-  if (r == 0) reg[i] = rg;
+  const unsigned m = group_mask();
+#pragma unroll
+  for (int o = kGroup / 2; o > 0; o >>= 1) rg += __shfl_xor_sync(m, rg, o, kGroup);
+  if (r == 0) reg[i] = (float)rg;
 }
 
 __global__ void k_adjoint_prep_l0(int64_t n, int K, const float* __restrict__ chol,
                                   const float* __restrict__ grad_c, const float* __restrict__ coeffs,
-                                  float lam0, float* __restrict__ u, float* __restrict__ reg) {
+                                  float lam0, float* __restrict__ u, float* __restrict__ u_lo,
+                                  float* __restrict__ reg) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const float l = chol[i];
-  const float inv = l > 0.0f ? 1.0f / (l * l) : 0.0f;
+  const float A = chol[3 * i + 1], A_lo = chol[3 * i + 2];  // record: sqrt(A), A_hi, A_lo
   float rg = 0.0f;
   for (int k = 0; k < K; ++k) {
-    const float x = grad_c[i * K + k] * inv;
+    const float g = grad_c[i * K + k];
+    float x = 0.0f, xl = 0.0f;
+    if (A > 0.0f) {
+      x = g / A;
+      xl = (fmaf(-A, x, g) - A_lo * x) / A;  // one float-float correction, kept as the lo part
+    }
     u[i * K + k] = x;
-    rg = fmaf(lam0 * x, coeffs[i * K + k], rg);
+    u_lo[i * K + k] = xl;
+    rg = fmaf(lam0 * (x + xl), coeffs[i * K + k], rg);
   }
   reg[i] = rg;
 }
@@ -724,7 +819,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_refine_update(
   const bool row = r < B;
   float a[B];
 #pragma unroll
-  for (int c = 0; c < B; ++c) a[c] = (row && c <= r) ? chol[i * (B * (B + 1) / 2) + r * (r + 1) / 2 + c] : 0.0f;
+  for (int c = 0; c < B; ++c) a[c] = (row && c <= r) ? chol[i * solve_record_floats(B) + r * (r + 1) / 2 + c] : 0.0f;
   const float l00 = __shfl_sync(group_mask(), a[0], 0, kGroup);
   if (!(l00 > 0.0f)) return;  // unseen: the coefficients stay 0 (whole group)
   const float w = wsum[i] + (MIXED ? wlo[i] : 0.0f);
@@ -803,11 +898,16 @@ __global__ void __launch_bounds__(kPayThreads) k_payload_render(int64_t n, int K
   }
 }
 
+// a = Y . u and Y . c per (camera, Gaussian) in float-float: for an ill-conditioned A, u = A^-1 g
+// is large along directions that the basis of the well-weighted cameras nearly annihilates, so the
+// dot products cancel heavily; with u = u_hi + u_lo from the refined solve and the same float32
+// basis the fold used, they keep the accuracy of the forward solve.
 template <int B>
 __global__ void __launch_bounds__(kPayThreads) k_payload_adjoint(int64_t n, int K, int G, const float* __restrict__ means,
                                                                  const DevCam* __restrict__ cams, int cb,
                                                                  const float* __restrict__ coeffs,
                                                                  const float* __restrict__ u,
+                                                                 const float* __restrict__ u_lo,
                                                                  const float* __restrict__ reg,
                                                                  float* __restrict__ payload) {
   extern __shared__ float s_rows[];
@@ -816,6 +916,7 @@ __global__ void __launch_bounds__(kPayThreads) k_payload_adjoint(int64_t n, int 
   const int gcount = (int)min((int64_t)G, n - i0);
   stage_rows(coeffs, i0, gcount, BK, RW, s_rows);
   stage_rows(u, i0, gcount, BK, RW, s_rows + G * RW);
+  stage_rows(u_lo, i0, gcount, BK, RW, s_rows + 2 * G * RW);
   __syncthreads();
   const int g = threadIdx.x % G, lanes = kPayThreads / G, cl = threadIdx.x / G;
   if (g >= gcount) return;
@@ -823,24 +924,33 @@ __global__ void __launch_bounds__(kPayThreads) k_payload_adjoint(int64_t n, int 
   const float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
   const float* ci = s_rows + g * RW;
   const float* ui = s_rows + (G + g) * RW;
+  const float* li = s_rows + (2 * G + g) * RW;
   const float rg = reg[i];
   for (int j = cl; j < cb; j += lanes) {
     const float3 d = view_dir(mu, cams[j]);
     float Y[B];
     sh_basis<B>(d.x, d.y, d.z, Y);
     float* out = payload + ((int64_t)j * n + i) * (K + 1);
-    float beta = -rg;
+    float beta = -rg, beta_c = 0.0f;
     for (int k = 0; k < K; ++k) {
-      float a = 0.0f, yc = 0.0f;
+      float a = 0.0f, a_c = 0.0f, yc = 0.0f, yc_c = 0.0f;
 #pragma unroll
       for (int m = 0; m < B; ++m) {
-        a = fmaf(Y[m], ui[m * K + k], a);
-        yc = fmaf(Y[m], ci[m * K + k], yc);
+        const float uh = ui[m * K + k], cm = ci[m * K + k];
+        const float p = Y[m] * uh, q = Y[m] * cm;
+        two_sum_acc(a, a_c, p);
+        a_c += fmaf(Y[m], uh, -p) + Y[m] * li[m * K + k];
+        two_sum_acc(yc, yc_c, q);
+        yc_c += fmaf(Y[m], cm, -q);
       }
+      a += a_c;
+      yc += yc_c;
       out[k] = a;
-      beta = fmaf(-a, yc, beta);
+      const float pb = -a * yc;
+      two_sum_acc(beta, beta_c, pb);
+      beta_c += fmaf(-a, yc, -pb);
     }
-    out[K] = beta;
+    out[K] = beta + beta_c;
   }
 }
 
@@ -903,39 +1013,59 @@ void launch_fold(const Problem& p, const float* means, int cb, bool first, bool 
 }
 
 // ------------------------------------------------------------------------------------------
-// normal equations in and out (camera sharding): the sums of Eq. 12-14 as double, hi + lo
+// normal equations in and out (camera sharding): per Gaussian R = P + B K + 1 doubles, P = B(B+1)/2:
+// the upper triangle of G row by row (r <= c), then b [B,K], then w; hi + lo combined in double
 // ------------------------------------------------------------------------------------------
 namespace {
 
 constexpr double kY0d = 0.28209479177387814;
 
-__global__ void k_export_normal(int64_t nG, int64_t nb, int64_t n, const float* __restrict__ G,
-                                const float* __restrict__ Glo, const float* __restrict__ b,
-                                const float* __restrict__ blo, const float* __restrict__ w,
-                                const float* __restrict__ wlo, double* __restrict__ Gd, double* __restrict__ bd,
-                                double* __restrict__ wd) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nG + nb + n; e += stride) {
-    if (e < nG) Gd[e] = (double)G[e] + (Glo ? (double)Glo[e] : 0.0);
-    else if (e < nG + nb) bd[e - nG] = (double)b[e - nG] + (blo ? (double)blo[e - nG] : 0.0);
-    else wd[e - nG - nb] = (double)w[e - nG - nb] + (wlo ? (double)wlo[e - nG - nb] : 0.0);
+// (r, c) of packed upper-triangle entry k of a B x B matrix (rows r = 0..B-1 hold c = r..B-1)
+__device__ __forceinline__ void packed_rc(int k, int B, int& r, int& c) {
+  r = 0;
+  while (k >= B - r) {
+    k -= B - r;
+    ++r;
+  }
+  c = r + k;
+}
+__device__ __forceinline__ int packed_index(int r, int c, int B) {  // r <= c
+  return r * B - r * (r - 1) / 2 + (c - r);
+}
+
+__global__ void k_export_packed(int64_t n, int B, int K, const float* __restrict__ G, const float* __restrict__ Glo,
+                                const float* __restrict__ b, const float* __restrict__ blo,
+                                const float* __restrict__ w, const float* __restrict__ wlo, double* __restrict__ out) {
+  const int P = B * (B + 1) / 2, R = P + B * K + 1;
+  const int64_t total = n * (int64_t)R, stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += stride) {
+    const int64_t i = e / R;
+    const int k = (int)(e - i * R);
+    double v;
+    if (k < P) {
+      int r, c;
+      packed_rc(k, B, r, c);
+      const int64_t idx = (i * B + r) * B + c;
+      v = (double)G[idx] + (Glo ? (double)Glo[idx] : 0.0);
+    } else if (k < P + B * K) {
+      const int64_t idx = i * B * K + (k - P);
+      v = (double)b[idx] + (blo ? (double)blo[idx] : 0.0);
+    } else {
+      v = (double)w[i] + (wlo ? (double)wlo[i] : 0.0);
+    }
+    out[e] = v;
   }
 }
 
 // L = 0: acc[i] = (V, S_0..S_{K-1}) gives G = Y0^2 V, b = Y0 S, w = V
-__global__ void k_export_normal_l0(int64_t n, int K, int RS, const float* __restrict__ acc, double* __restrict__ Gd,
-                                   double* __restrict__ bd, double* __restrict__ wd) {
+__global__ void k_export_packed_l0(int64_t n, int K, int RS, const float* __restrict__ acc, double* __restrict__ out) {
+  const int R = K + 2;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= n * (int64_t)(K + 1)) return;
-  const int64_t i = e / (K + 1);
-  const int k = (int)(e - i * (K + 1));
+  if (e >= n * (int64_t)R) return;
+  const int64_t i = e / R;
+  const int k = (int)(e - i * R);
   const double V = (double)acc[i * RS];
-  if (k == K) {
-    Gd[i] = kY0d * kY0d * V;
-    wd[i] = V;
-  } else {
-    bd[i * K + k] = kY0d * (double)acc[i * RS + 1 + k];
-  }
+  out[e] = k == 0 ? kY0d * kY0d * V : (k <= K ? kY0d * (double)acc[i * RS + k] : V);
 }
 
 __device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
@@ -943,74 +1073,103 @@ __device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
   lo = (float)(x - (double)hi);
 }
 
-__global__ void k_import_normal(int64_t nG, int64_t nb, int64_t n, const double* __restrict__ Gd,
-                                const double* __restrict__ bd, const double* __restrict__ wd, float* __restrict__ G,
+__global__ void k_import_packed(int64_t n, int B, int K, const double* __restrict__ in, float* __restrict__ G,
                                 float* __restrict__ Glo, float* __restrict__ b, float* __restrict__ blo,
                                 float* __restrict__ w, float* __restrict__ wlo) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nG + nb + n; e += stride) {
+  const int P = B * (B + 1) / 2, R = P + B * K + 1, E = B * B + B * K + 1;
+  const int64_t total = n * (int64_t)E, stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += stride) {
+    const int64_t i = e / E;
+    const int k = (int)(e - i * E);
+    const double* row = in + i * R;
     float hi, lo;
-    if (e < nG) {
-      split_double(Gd[e], hi, lo);
-      G[e] = hi;
-      if (Glo) Glo[e] = lo;
-    } else if (e < nG + nb) {
-      split_double(bd[e - nG], hi, lo);
-      b[e - nG] = hi;
-      if (blo) blo[e - nG] = lo;
+    if (k < B * B) {
+      const int r = k / B, c = k - r * B;
+      split_double(row[r <= c ? packed_index(r, c, B) : packed_index(c, r, B)], hi, lo);
+      G[i * B * B + k] = hi;
+      if (Glo) Glo[i * B * B + k] = lo;
+    } else if (k < B * B + B * K) {
+      const int kk = k - B * B;
+      split_double(row[P + kk], hi, lo);
+      b[i * B * K + kk] = hi;
+      if (blo) blo[i * B * K + kk] = lo;
     } else {
-      split_double(wd[e - nG - nb], hi, lo);
-      w[e - nG - nb] = hi;
-      if (wlo) wlo[e - nG - nb] = lo;
+      split_double(row[R - 1], hi, lo);
+      w[i] = hi;
+      if (wlo) wlo[i] = lo;
     }
   }
 }
 
 // L = 0: back to acc[i] = (V, S) with V = w, S = b / Y0
-__global__ void k_import_normal_l0(int64_t n, int K, int RS, const double* __restrict__ bd,
-                                   const double* __restrict__ wd, float* __restrict__ acc) {
+__global__ void k_import_packed_l0(int64_t n, int K, int RS, const double* __restrict__ in, float* __restrict__ acc) {
+  const int R = K + 2;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n * (int64_t)(K + 1)) return;
   const int64_t i = e / (K + 1);
   const int k = (int)(e - i * (K + 1));
-  if (k == K) acc[i * RS] = (float)wd[i];
-  else acc[i * RS + 1 + k] = (float)(bd[i * K + k] / kY0d);
+  const double* row = in + i * R;
+  if (k == K) acc[i * RS] = (float)row[R - 1];
+  else acc[i * RS + 1 + k] = (float)(row[1 + k] / kY0d);
 }
 
 }  // namespace
 
-void launch_export_normal(const Problem& p, const Workspace& ws, double* G, double* b, double* w, cudaStream_t s) {
+void launch_export_normal(const Problem& p, const Workspace& ws, double* sums, cudaStream_t s) {
   if (p.B == 1) {
-    const int64_t m = p.n * (int64_t)(p.K + 1);
-    k_export_normal_l0<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(p.n, p.K, p.acc_stride, ws.acc, G, b, w);
+    const int64_t m = p.n * (int64_t)(p.K + 2);
+    k_export_packed_l0<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(p.n, p.K, p.acc_stride, ws.acc, sums);
   } else {
     const bool mixed = p.precision == 1;
-    k_export_normal<<<1216, 256, 0, s>>>(p.n * p.B * p.B, p.n * p.B * p.K, p.n, ws.G, mixed ? ws.Glo : nullptr,
-                                         ws.bvec, mixed ? ws.blo : nullptr, ws.wsum, mixed ? ws.wlo : nullptr, G, b, w);
+    k_export_packed<<<1216, 256, 0, s>>>(p.n, p.B, p.K, ws.G, mixed ? ws.Glo : nullptr, ws.bvec,
+                                         mixed ? ws.blo : nullptr, ws.wsum, mixed ? ws.wlo : nullptr, sums);
   }
   note_launches(1);
 }
 
-void launch_import_normal(const Problem& p, const Workspace& ws, const double* G, const double* b, const double* w,
-                          cudaStream_t s) {
+void launch_import_normal(const Problem& p, const Workspace& ws, const double* sums, cudaStream_t s) {
   if (p.B == 1) {
     const int64_t m = p.n * (int64_t)(p.K + 1);
-    k_import_normal_l0<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(p.n, p.K, p.acc_stride, b, w, ws.acc);
+    k_import_packed_l0<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(p.n, p.K, p.acc_stride, sums, ws.acc);
   } else {
     const bool mixed = p.precision == 1;
-    k_import_normal<<<1216, 256, 0, s>>>(p.n * p.B * p.B, p.n * p.B * p.K, p.n, G, b, w, ws.G,
-                                         mixed ? ws.Glo : nullptr, ws.bvec, mixed ? ws.blo : nullptr, ws.wsum,
-                                         mixed ? ws.wlo : nullptr);
+    k_import_packed<<<1216, 256, 0, s>>>(p.n, p.B, p.K, sums, ws.G, mixed ? ws.Glo : nullptr, ws.bvec,
+                                         mixed ? ws.blo : nullptr, ws.wsum, mixed ? ws.wlo : nullptr);
   }
+  note_launches(1);
+}
+
+// Merges one target set's accumulator rows into the combined rows: S_0..S_{Ks-1} of the set into
+// columns 1 + col0.., and V (column 0) from the first set only.
+__global__ void k_merge_set(int64_t rows, int Ks, int RSs, const float* __restrict__ src, int RS, int col0,
+                            float* __restrict__ dst) {
+  const int W = Ks + 1;
+  const int64_t total = rows * W, stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += stride) {
+    const int64_t r = e / W;
+    const int k = (int)(e - r * W);
+    if (k == 0) {
+      if (col0 == 0) dst[r * RS] = src[r * RSs];
+    } else {
+      dst[r * RS + col0 + k] = src[r * RSs + k];
+    }
+  }
+}
+
+void launch_merge_set(int64_t rows, int Ks, int RSs, const float* src, int RS, int col0, float* dst, cudaStream_t s) {
+  const int64_t m = rows * (int64_t)(Ks + 1);
+  const unsigned grid = (unsigned)std::min<int64_t>((m + 255) / 256, 152 * 16);
+  k_merge_set<<<grid, 256, 0, s>>>(rows, Ks, RSs, src, RS, col0, dst);
   note_launches(1);
 }
 
 void launch_solve(const Problem& p, const float* lam_dev, const float* lam_host, const Workspace& ws,
                   float* coeffs, uint8_t* status, float* chol, const float* means, int n_acc_cams,
-                  cudaStream_t s) {
+                  cudaStream_t s, float tau, uint8_t* keep) {
   if (p.B == 1) {
     const int64_t m = p.n * (int64_t)p.K;
-    k_solve_l0<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(p.n, p.K, p.acc_stride, ws.acc, lam_host[0], coeffs, status, chol);
+    k_solve_l0<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(p.n, p.K, p.acc_stride, ws.acc, lam_host[0], coeffs, status, chol,
+                                                           tau, keep);
     note_launches(1);
     return;
   }
@@ -1065,28 +1224,31 @@ void launch_adjoint_prepare(const Problem& p, const float* lam_dev, const float*
                                 const Workspace& ws, cudaStream_t s) {
   if (p.B == 1) {
     k_adjoint_prep_l0<<<(unsigned)((p.n + 255) / 256), 256, 0, s>>>(p.n, p.K, chol, grad_coeffs, coeffs,
-                                                                     lam_host[0], ws.u, ws.reg);
+                                                                     lam_host[0], ws.u, ws.u_lo, ws.reg);
     note_launches(1);
     return;
   }
   const unsigned grid = (unsigned)((p.n * kGroup + kSolveThreads - 1) / kSolveThreads);
   if (p.B == 4)
-    k_adjoint_prep<4><<<grid, kSolveThreads, 0, s>>>(p.n, p.K, chol, grad_coeffs, coeffs, lam_dev, ws.u, ws.reg);
+    k_adjoint_prep<4><<<grid, kSolveThreads, 0, s>>>(p.n, p.K, chol, grad_coeffs, coeffs, lam_dev, ws.u, ws.u_lo,
+                                                      ws.reg);
   else if (p.B == 9)
-    k_adjoint_prep<9><<<grid, kSolveThreads, 0, s>>>(p.n, p.K, chol, grad_coeffs, coeffs, lam_dev, ws.u, ws.reg);
+    k_adjoint_prep<9><<<grid, kSolveThreads, 0, s>>>(p.n, p.K, chol, grad_coeffs, coeffs, lam_dev, ws.u, ws.u_lo,
+                                                      ws.reg);
   else
-    k_adjoint_prep<16><<<grid, kSolveThreads, 0, s>>>(p.n, p.K, chol, grad_coeffs, coeffs, lam_dev, ws.u, ws.reg);
+    k_adjoint_prep<16><<<grid, kSolveThreads, 0, s>>>(p.n, p.K, chol, grad_coeffs, coeffs, lam_dev, ws.u, ws.u_lo,
+                                                      ws.reg);
   note_launches(1);
 }
 
 void launch_payload_adjoint(const Problem& p, const float* means, const float* coeffs, int cb,
                             const Workspace& ws, cudaStream_t s) {
-  const int G = payload_group(p.B, p.K, 2);
+  const int G = payload_group(p.B, p.K, 3);
   const unsigned grid = (unsigned)((p.n + G - 1) / G);
-  const size_t smem = 2 * (size_t)G * ((p.B * p.K) | 1) * sizeof(float);
+  const size_t smem = 3 * (size_t)G * ((p.B * p.K) | 1) * sizeof(float);
 #define ICGS_PAYADJ(BB)                                                                              \
   k_payload_adjoint<BB><<<grid, kPayThreads, smem, s>>>(p.n, p.K, G, means, ws.cams, cb, coeffs, ws.u, \
-                                                        ws.reg, ws.payload)
+                                                        ws.u_lo, ws.reg, ws.payload)
   if (p.B == 1) ICGS_PAYADJ(1);
   else if (p.B == 4) ICGS_PAYADJ(4);
   else if (p.B == 9) ICGS_PAYADJ(9);

@@ -334,6 +334,16 @@ __device__ __forceinline__ void load_batch(const unsigned long long* list, uint3
   }
 }
 
+// Flags a non-finite target value in the status block (the call then fails with
+// ICGS_ERR_NONFINITE_INPUT); the atomic runs only on that rare path.
+template <int N>
+__device__ __forceinline__ void check_finite(const float (&v)[N], DevStatus* status) {
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < N; ++k) bad |= !isfinite(v[k]);
+  if (bad) atomicOr(&status->flags, kFlagNonfinite);
+}
+
 __device__ __forceinline__ void add_pair_count(uint32_t npairs, DevStatus* status) {
   const uint32_t warp_sum = __reduce_add_sync(kFull, npairs);
   if ((threadIdx.x & 31) == 0 && warp_sum) atomicAdd((unsigned long long*)&status->contrib_pairs, (unsigned long long)warp_sum);

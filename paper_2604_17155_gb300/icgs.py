@@ -18,9 +18,18 @@ HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "icgs.h")
 
 OK, ERR_INVALID_ARG, ERR_WORKSPACE_TOO_SMALL, ERR_CUDA, ERR_CAPACITY, ERR_UNSUPPORTED, ERR_DEVICE_TIMEOUT = \
     0, -1, -2, -3, -4, -5, -6
+ERR_NONFINITE_INPUT = -7
 F32, BF16, F16 = 0, 1, 2
 PLAIN, MIXED = 0, 1
 GAUSSIAN_OK, GAUSSIAN_UNSEEN, GAUSSIAN_FP64 = 0, 1, 2
+
+
+def solve_record_floats(sh_degree):
+    """Floats per Gaussian of the solve record colorize() returns (the `chol` tensor): the
+    row-packed lower Cholesky factor of A = G + w Lambda, then A itself in float-float (hi parts,
+    then lo parts), each B (B + 1) / 2 floats with B = (L + 1)^2."""
+    B = (sh_degree + 1) ** 2
+    return 3 * (B * (B + 1) // 2)
 
 
 class IcgsError(RuntimeError):
@@ -96,16 +105,34 @@ def load(path: str = LIB_PATH):
     lib.icgs_colorize_host_workspace_size.restype = S
     lib.icgs_colorize_host.argtypes = [P, P, P, P, P, S, P, P, P, P]
     lib.icgs_colorize_host.restype = ctypes.c_int
-    lib.icgs_accumulate.argtypes = [P, P, P, P, P, S, P, P, P, P]
+    lib.icgs_normal_size.argtypes = [ctypes.c_int32, ctypes.c_int32]
+    lib.icgs_normal_size.restype = ctypes.c_int64
+    lib.icgs_accumulate.argtypes = [P, P, P, P, P, S, P, P]
     lib.icgs_accumulate.restype = ctypes.c_int
     lib.icgs_solve_workspace_size.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P]
     lib.icgs_solve_workspace_size.restype = S
-    lib.icgs_solve.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, S, P, P, P, P]
+    lib.icgs_solve.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P, P, P, S, P, P, P, P]
     lib.icgs_solve.restype = ctypes.c_int
     lib.icgs_selftest_tc.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, P, P, P]
     lib.icgs_selftest_tc.restype = ctypes.c_int
     lib.icgs_selftest_tc_rows.argtypes = [P, ctypes.c_int32, P, ctypes.c_int32, ctypes.c_int32, P, P, P, P]
     lib.icgs_selftest_tc_rows.restype = ctypes.c_int
+    lib.icgs_colorize_async.argtypes = [P, P, P, P, P, S, P, P, P, P]
+    lib.icgs_colorize_async.restype = ctypes.c_int
+    lib.icgs_colorize_backward_async.argtypes = [P, P, P, P, P, P, P, P, S, P, P, P]
+    lib.icgs_colorize_backward_async.restype = ctypes.c_int
+    lib.icgs_colorize_refine_async.argtypes = [P, P, P, P, ctypes.c_int32, P, P, S, P, P]
+    lib.icgs_colorize_refine_async.restype = ctypes.c_int
+    lib.icgs_render_async.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int64, P, S, P, P]
+    lib.icgs_render_async.restype = ctypes.c_int
+    lib.icgs_async_status.argtypes = [P, P]
+    lib.icgs_async_status.restype = ctypes.c_int
+    lib.icgs_sets_workspace_size.argtypes = [P, P, ctypes.c_int32, P, P]
+    lib.icgs_sets_workspace_size.restype = S
+    lib.icgs_colorize_sets.argtypes = [P, P, ctypes.c_int32, P, P, P, S, P, P, P, ctypes.c_float, P, P]
+    lib.icgs_colorize_sets.restype = ctypes.c_int
+    lib.icgs_debug_tc_wait.argtypes = [ctypes.c_int64, ctypes.c_int32]
+    lib.icgs_debug_tc_wait.restype = None
     lib.icgs_set_stage_timing.argtypes = [ctypes.c_int]
     lib.icgs_set_stage_timing.restype = None
     lib.icgs_last_stage_ms.argtypes = [P, ctypes.c_int]
@@ -277,7 +304,8 @@ def _run_with_capacity(device, size_fn, call_fn, capacity):
 def colorize(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, precision="mixed",
              cond_tau=0.0, cam_batch=0, instance_capacity=0, opacity=None, refold_tau=0.0):
     """Alg. 1 lines 1-6: per-Gaussian SH coefficients [n,(L+1)^2,K] (float32), status [n] (uint8)
-    and the row-packed Cholesky factors [n, B(B+1)/2] of A_i = G_i + w_i Lambda."""
+    and the solve records [n, solve_record_floats(L)]: the Cholesky factor of A_i = G_i + w_i Lambda
+    and A_i itself in float-float (what colorize_backward and colorize_refine take)."""
     torch = _torch()
     lib = load()
     dev = targets.device
@@ -285,7 +313,7 @@ def colorize(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, precisio
     K = int(targets.shape[-1])
     coeffs = torch.empty((scene.n, B, K), dtype=torch.float32, device=dev)
     status = torch.empty((scene.n,), dtype=torch.uint8, device=dev)
-    chol = torch.empty((scene.n, B * (B + 1) // 2), dtype=torch.float32, device=dev)
+    chol = torch.empty((scene.n, solve_record_floats(sh_degree)), dtype=torch.float32, device=dev)
     sc = scene._struct(opacity)
     cm = cams._struct()
     tg = _targets_struct(targets)
@@ -303,6 +331,88 @@ def colorize(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, precisio
 
     _run_with_capacity(dev, size_fn, call_fn, instance_capacity)
     return coeffs, status, chol
+
+
+def colorize_sets(scene: Scene, cams: Cameras, target_sets, sh_degree, lam=None, precision="mixed", cond_tau=0.0,
+                  cam_batch=0, instance_capacity=0, refold_tau=0.0, threshold=None):
+    """icgs_colorize_sets: several target stacks of the same cameras (a list of CUDA tensors
+    [n_cams,H,W,K_s], each float32, bfloat16 or float16) colorized on one geometry with one shared
+    factorisation. Returns coefficients [n,(L+1)^2,sum K_s] (channels in set order), status [n],
+    solve records, and, with threshold given (sh_degree 0 only), keep [n, sum K_s] uint8: 1 where
+    the Gaussian's colour reaches the threshold (Sec. 5 uses 0.6)."""
+    torch = _torch()
+    lib = load()
+    if not target_sets:
+        raise ValueError("at least one target set is required")
+    dev = target_sets[0].device
+    B = (sh_degree + 1) ** 2
+    structs = [_targets_struct(t) for t in target_sets]
+    arr = (_Targets * len(structs))(*structs)
+    K = sum(int(t.shape[-1]) for t in target_sets)
+    coeffs = torch.empty((scene.n, B, K), dtype=torch.float32, device=dev)
+    status = torch.empty((scene.n,), dtype=torch.uint8, device=dev)
+    chol = torch.empty((scene.n, solve_record_floats(sh_degree)), dtype=torch.float32, device=dev)
+    keep = torch.empty((scene.n, K), dtype=torch.uint8, device=dev) if threshold is not None else None
+    sc = scene._struct()
+    cm = cams._struct()
+
+    def size_fn(cap):
+        o, _keep = _options(sh_degree, lam, precision, cond_tau, cam_batch, cap, refold_tau)
+        return lib.icgs_sets_workspace_size(ctypes.byref(sc), ctypes.byref(cm), len(structs), arr, ctypes.byref(o))
+
+    def call_fn(ptr, nbytes, cap):
+        o, _keep = _options(sh_degree, lam, precision, cond_tau, cam_batch, cap, refold_tau)
+        return lib.icgs_colorize_sets(ctypes.byref(sc), ctypes.byref(cm), len(structs), arr, ctypes.byref(o),
+                                      ctypes.c_void_p(ptr), nbytes, ctypes.c_void_p(coeffs.data_ptr()),
+                                      ctypes.c_void_p(status.data_ptr()), ctypes.c_void_p(chol.data_ptr()),
+                                      float(threshold if threshold is not None else 0.0),
+                                      ctypes.c_void_p(keep.data_ptr() if keep is not None else 0), _stream_ptr(dev))
+
+    _run_with_capacity(dev, size_fn, call_fn, instance_capacity)
+    return coeffs, status, chol, keep
+
+
+class AsyncColorize:
+    """A colorize enqueued by colorize_async(): owns its workspace and outputs until wait()."""
+
+    def __init__(self, workspace, stream, outputs):
+        self.workspace = workspace
+        self.stream = stream
+        self.outputs = outputs
+
+    def wait(self):
+        """Joins the call (synchronises its stream) and returns (coeffs, status, chol); raises
+        IcgsError with the device outcome (ERR_CAPACITY, ERR_NONFINITE_INPUT, ...) if it failed."""
+        _check(load().icgs_async_status(ctypes.c_void_p(self.workspace.data_ptr()), self.stream))
+        return self.outputs
+
+
+def colorize_async(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, precision="mixed", cond_tau=0.0,
+                   cam_batch=0, instance_capacity=0, opacity=None, refold_tau=0.0):
+    """colorize() through icgs_colorize_async on the current stream: returns at once, before the
+    work has run, with a handle whose wait() joins it. The call has its own workspace, so several
+    may run concurrently on different streams. A capacity overflow surfaces in wait() (no retry)."""
+    torch = _torch()
+    lib = load()
+    dev = targets.device
+    B = (sh_degree + 1) ** 2
+    K = int(targets.shape[-1])
+    coeffs = torch.empty((scene.n, B, K), dtype=torch.float32, device=dev)
+    status = torch.empty((scene.n,), dtype=torch.uint8, device=dev)
+    chol = torch.empty((scene.n, solve_record_floats(sh_degree)), dtype=torch.float32, device=dev)
+    sc = scene._struct(opacity)
+    cm = cams._struct()
+    tg = _targets_struct(targets)
+    o, _keep = _options(sh_degree, lam, precision, cond_tau, cam_batch, instance_capacity, refold_tau)
+    nbytes = lib.icgs_workspace_size(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(o))
+    if nbytes == 0:
+        _check(ERR_INVALID_ARG)
+    ws = torch.empty(int(nbytes), dtype=torch.uint8, device=dev)
+    stream = _stream_ptr(dev)
+    _check(lib.icgs_colorize_async(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(o),
+                                   ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(coeffs.data_ptr()),
+                                   ctypes.c_void_p(status.data_ptr()), ctypes.c_void_p(chol.data_ptr()), stream))
+    return AsyncColorize(ws, stream, (coeffs, status, chol))
 
 
 def colorize_host(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, precision="mixed",
@@ -349,19 +459,23 @@ def colorize_host(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, pre
     return coeffs, status
 
 
+def normal_size(sh_degree, channels):
+    """Doubles per Gaussian of the packed normal equations (icgs_normal_size): the upper triangle
+    of G row by row, then b [B,K], then w."""
+    B = (sh_degree + 1) ** 2
+    return B * (B + 1) // 2 + B * channels + 1
+
+
 def accumulate(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, precision="mixed", cam_batch=0,
                instance_capacity=0, opacity=None):
-    """icgs_accumulate: the normal equations of these cameras (Eq. 12-14) as float64 device tensors
-    G [n,B,B], b [n,B,K], w [n] (B = (L+1)^2). Sums over disjoint camera subsets add up to the sums
-    over their union."""
+    """icgs_accumulate: the normal equations of these cameras (Eq. 12-14) as packed float64 device
+    sums [n, normal_size(L, K)]. Sums over disjoint camera subsets add up to the sums over their
+    union."""
     torch = _torch()
     lib = load()
     dev = targets.device
-    B = (sh_degree + 1) ** 2
     K = int(targets.shape[-1])
-    G = torch.empty((scene.n, B, B), dtype=torch.float64, device=dev)
-    b = torch.empty((scene.n, B, K), dtype=torch.float64, device=dev)
-    w = torch.empty((scene.n,), dtype=torch.float64, device=dev)
+    sums = torch.empty((scene.n, normal_size(sh_degree, K)), dtype=torch.float64, device=dev)
     sc = scene._struct(opacity)
     cm = cams._struct()
     tg = _targets_struct(targets)
@@ -373,38 +487,37 @@ def accumulate(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, precis
     def call_fn(ptr, nbytes, cap):
         o, _keep = _options(sh_degree, lam, precision, 0.0, cam_batch, cap)
         return lib.icgs_accumulate(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(o),
-                                   ctypes.c_void_p(ptr), nbytes, ctypes.c_void_p(G.data_ptr()),
-                                   ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(w.data_ptr()), _stream_ptr(dev))
+                                   ctypes.c_void_p(ptr), nbytes, ctypes.c_void_p(sums.data_ptr()), _stream_ptr(dev))
 
     _run_with_capacity(dev, size_fn, call_fn, instance_capacity)
-    return G, b, w
+    return sums
 
 
-def solve(G, b, w, sh_degree, lam=None, precision="mixed", cond_tau=0.0):
-    """icgs_solve: coefficients [n,B,K] float32, status [n] uint8 and Cholesky factors from float64
-    device sums G [n,B,B], b [n,B,K], w [n] (as accumulate() returns them, or their sum over
-    camera subsets)."""
+def solve(sums, sh_degree, lam=None, precision="mixed", cond_tau=0.0):
+    """icgs_solve: coefficients [n,B,K] float32, status [n] uint8 and solve records from packed
+    float64 device sums [n, normal_size(L, K)] (as accumulate() returns them, their sum over camera
+    subsets, or any contiguous range of their rows)."""
     torch = _torch()
     lib = load()
-    dev = G.device
-    n = int(w.shape[0])
+    dev = sums.device
+    n = int(sums.shape[0])
     B = (sh_degree + 1) ** 2
-    K = int(b.shape[-1])
-    for x, shape in ((G, (n, B, B)), (b, (n, B, K)), (w, (n,))):
-        if x.dtype != torch.float64 or not x.is_cuda or not x.is_contiguous() or tuple(x.shape) != shape:
-            raise ValueError(f"expected a contiguous float64 CUDA tensor of shape {shape}")
+    P = B * (B + 1) // 2
+    K = (int(sums.shape[1]) - P - 1) // B
+    if (sums.dtype != torch.float64 or not sums.is_cuda or not sums.is_contiguous() or sums.dim() != 2
+            or K < 1 or normal_size(sh_degree, K) != sums.shape[1]):
+        raise ValueError("expected contiguous float64 CUDA sums [n, normal_size(L, K)]")
     coeffs = torch.empty((n, B, K), dtype=torch.float32, device=dev)
     status = torch.empty((n,), dtype=torch.uint8, device=dev)
-    chol = torch.empty((n, B * (B + 1) // 2), dtype=torch.float32, device=dev)
+    chol = torch.empty((n, solve_record_floats(sh_degree)), dtype=torch.float32, device=dev)
     o, _keep = _options(sh_degree, lam, precision, cond_tau, 0, 0)
     nbytes = lib.icgs_solve_workspace_size(n, sh_degree, K, ctypes.byref(o))
     if nbytes == 0:
         _check(ERR_INVALID_ARG)
     ws = _ws.get(dev, nbytes)
-    _check(lib.icgs_solve(n, sh_degree, K, ctypes.c_void_p(G.data_ptr()), ctypes.c_void_p(b.data_ptr()),
-                          ctypes.c_void_p(w.data_ptr()), ctypes.byref(o), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
-                          ctypes.c_void_p(coeffs.data_ptr()), ctypes.c_void_p(status.data_ptr()),
-                          ctypes.c_void_p(chol.data_ptr()), _stream_ptr(dev)))
+    _check(lib.icgs_solve(n, sh_degree, K, ctypes.c_void_p(sums.data_ptr()), ctypes.byref(o),
+                          ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(coeffs.data_ptr()),
+                          ctypes.c_void_p(status.data_ptr()), ctypes.c_void_p(chol.data_ptr()), _stream_ptr(dev)))
     return coeffs, status, chol
 
 
@@ -413,25 +526,53 @@ def shard_cameras(n_cams, rank, world):
     return np.arange(rank, n_cams, world)
 
 
+def shard_gaussians(n, rank, world):
+    """The contiguous Gaussian range [lo, hi) a rank solves: ranges of ceil(n / world) rows."""
+    chunk = -(-n // world)
+    return min(n, rank * chunk), min(n, (rank + 1) * chunk)
+
+
 def colorize_sharded(scene, cams, targets, sh_degree, rank, world, group=None, lam=None, precision="mixed",
-                     accumulate_fn=None, solve_fn=None):
-    """Camera-sharded colorize: this rank accumulates the normal equations of its round-robin share
-    of the cameras, the ranks sum them (one torch.distributed all-reduce each of G, b and w; NCCL
-    for GPU tensors), and every rank solves. targets holds all cameras' images; only this rank's
-    slice is read. accumulate_fn(scene, cams_subset, targets_subset, sh_degree, lam, precision) ->
-    (G, b, w) and solve_fn(G, b, w, sh_degree, lam, precision) -> result default to accumulate()
-    and solve()."""
+                     gather=True, accumulate_fn=None, solve_fn=None):
+    """Camera-sharded colorize. This rank accumulates the packed normal equations of its round-robin
+    share of the cameras; one torch.distributed reduce-scatter (sum; NCCL for GPU tensors) leaves it
+    the totals of its contiguous Gaussian range (shard_gaussians); it solves that range; with
+    gather=True one all-gather replicates the coefficients. targets holds all cameras' images;
+    only this rank's slice is read.
+
+    accumulate_fn(scene, cams_subset, targets_subset, sh_degree, lam, precision) -> sums [n, R]
+    float64 and solve_fn(sums_range, sh_degree, lam, precision) -> (coeffs, status, chol) default to
+    accumulate() and solve(). Returns dict(coeffs=[n,B,K] with gather else the range's rows,
+    status and chol of the range, range=(lo, hi))."""
+    torch = _torch()
     import torch.distributed as dist
     accumulate_fn = accumulate_fn or (lambda sc, cm, t, L, lm, pr: accumulate(sc, cm, t, L, lam=lm, precision=pr))
-    solve_fn = solve_fn or (lambda G, b, w, L, lm, pr: solve(G, b, w, L, lam=lm, precision=pr))
+    solve_fn = solve_fn or (lambda s, L, lm, pr: solve(s, L, lam=lm, precision=pr))
     mine = shard_cameras(cams.n, rank, world)
-    idx = _torch().as_tensor(mine, device=targets.device)
-    G, b, w = accumulate_fn(scene, cams.subset(mine), targets.index_select(0, idx).contiguous(), sh_degree, lam,
-                            precision)
+    idx = torch.as_tensor(mine, device=targets.device)
+    sums = accumulate_fn(scene, cams.subset(mine), targets.index_select(0, idx).contiguous(), sh_degree, lam,
+                         precision)
+    n, R = int(sums.shape[0]), int(sums.shape[1])
+    lo, hi = shard_gaussians(n, rank, world)
     if world > 1:
-        for x in (G, b, w):
-            dist.all_reduce(x, op=dist.ReduceOp.SUM, group=group)
-    return solve_fn(G, b, w, sh_degree, lam, precision)
+        chunk = -(-n // world)
+        full = sums
+        if chunk * world != n:
+            full = torch.zeros((chunk * world, R), dtype=sums.dtype, device=sums.device)
+            full[:n] = sums
+        part = torch.empty((chunk, R), dtype=sums.dtype, device=sums.device)
+        dist.reduce_scatter_tensor(part, full, op=dist.ReduceOp.SUM, group=group)
+        sums = part[:hi - lo].contiguous()
+    coeffs, status, chol = solve_fn(sums, sh_degree, lam, precision)
+    out = dict(coeffs=coeffs, status=status, chol=chol, range=(lo, hi))
+    if gather and world > 1:
+        chunk = -(-n // world)
+        mine_c = torch.zeros((chunk,) + tuple(coeffs.shape[1:]), dtype=coeffs.dtype, device=coeffs.device)
+        mine_c[:hi - lo] = coeffs
+        allc = torch.empty((chunk * world,) + tuple(coeffs.shape[1:]), dtype=coeffs.dtype, device=coeffs.device)
+        dist.all_gather_into_tensor(allc, mine_c, group=group)
+        out["coeffs"] = allc[:n]
+    return out
 
 
 def colorize_noalloc(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, precision="mixed",
@@ -447,7 +588,7 @@ def colorize_noalloc(scene: Scene, cams: Cameras, targets, sh_degree, lam=None, 
     K = int(targets.shape[-1])
     coeffs = torch.empty((scene.n, B, K), dtype=torch.float32, device=dev)
     status = torch.empty((scene.n,), dtype=torch.uint8, device=dev)
-    chol = torch.empty((scene.n, B * (B + 1) // 2), dtype=torch.float32, device=dev)
+    chol = torch.empty((scene.n, solve_record_floats(sh_degree)), dtype=torch.float32, device=dev)
     sc = scene._struct(opacity)
     cm = cams._struct()
     tg = _targets_struct(targets)

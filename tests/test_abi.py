@@ -21,7 +21,9 @@ def test_header_declares_the_calls():
                  "icgs_render", "icgs_last_error", "icgs_last_required_instances", "icgs_last_stats",
                  "icgs_colorize_noalloc", "icgs_noalloc_scratch_bytes", "icgs_selftest_tc", "icgs_selftest_tc_rows",
                  "icgs_refine_workspace_size", "icgs_colorize_refine", "icgs_colorize_host_workspace_size",
-                 "icgs_colorize_host", "icgs_accumulate", "icgs_solve_workspace_size", "icgs_solve"]:
+                 "icgs_colorize_host", "icgs_accumulate", "icgs_solve_workspace_size", "icgs_solve",
+                 "icgs_normal_size", "icgs_colorize_async", "icgs_colorize_backward_async",
+                 "icgs_colorize_refine_async", "icgs_render_async", "icgs_async_status", "icgs_debug_tc_wait"]:
         assert want in names
 
 
@@ -81,11 +83,21 @@ def test_solve_workspace_and_arguments(lib):
     opt.precision = icgs.MIXED
     assert lib.icgs_solve_workspace_size(n, 4, K, ctypes.byref(opt)) == 0  # sh_degree 4
     assert lib.icgs_solve_workspace_size(n, 3, 0, ctypes.byref(opt)) == 0  # no channels
-    st = lib.icgs_solve(n, 3, K, None, None, None, ctypes.byref(opt), None, 0, None, None, None, None)
+    st = lib.icgs_solve(n, 3, K, None, ctypes.byref(opt), None, 0, None, None, None, None)
     assert st == icgs.ERR_INVALID_ARG and "required" in lib.icgs_last_error().decode()
-    st = lib.icgs_solve(n, 3, K, ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.byref(opt),
-                        None, 0, ctypes.c_void_p(16), None, None, None)
+    st = lib.icgs_solve(n, 3, K, ctypes.c_void_p(16), ctypes.byref(opt), None, 0, ctypes.c_void_p(16), None, None,
+                        None)
     assert st == icgs.ERR_WORKSPACE_TOO_SMALL
+
+
+def test_packed_normal_size():
+    """Packed normal equations per Gaussian: the upper triangle of the B x B Gram, B K right-hand
+    side entries and w (B = (L+1)^2)."""
+    lib = icgs.load()
+    for L, K in ((0, 1), (0, 16), (1, 3), (3, 3), (3, 64)):
+        B = (L + 1) ** 2
+        assert lib.icgs_normal_size(L, K) == icgs.normal_size(L, K) == B * (B + 1) // 2 + B * K + 1
+    assert lib.icgs_normal_size(4, 3) == 0 and lib.icgs_normal_size(0, 0) == 0
 
 
 def test_bad_arguments_rejected_on_host(lib):
@@ -132,3 +144,27 @@ def test_tc_selftest_rows_rejects_bad_shapes_on_host(lib):
     assert st == icgs.ERR_INVALID_ARG and "N = 48" in lib.icgs_last_error().decode()
     st = lib.icgs_selftest_tc_rows(None, 64, p, 32, 1, p, None, p, None)
     assert st == icgs.ERR_INVALID_ARG and "required" in lib.icgs_last_error().decode()
+
+
+def test_async_calls_reject_bad_arguments_on_host(lib):
+    """The enqueue-only calls check their arguments on the host exactly like the synchronous ones,
+    and icgs_async_status refuses a missing or misaligned workspace, all before any device work."""
+    sc, cm, tg, opt, keep = _structs()
+    st = lib.icgs_colorize_async(None, ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(opt), None, 0, None, None,
+                                 None, None)
+    assert st == icgs.ERR_INVALID_ARG and "NULL" in lib.icgs_last_error().decode()
+    st = lib.icgs_colorize_async(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(opt),
+                                 ctypes.c_void_p(256), 1024, ctypes.c_void_p(16), None, None, None)
+    assert st == icgs.ERR_WORKSPACE_TOO_SMALL
+    st = lib.icgs_render_async(ctypes.byref(sc), ctypes.byref(cm), 5, 3, ctypes.c_void_p(16), 0, None, 0,
+                               ctypes.c_void_p(16), None)
+    assert st == icgs.ERR_INVALID_ARG and "sh_degree" in lib.icgs_last_error().decode()
+    st = lib.icgs_colorize_backward_async(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(opt),
+                                          None, None, None, None, 0, None, None, None)
+    assert st == icgs.ERR_INVALID_ARG and "required" in lib.icgs_last_error().decode()
+    st = lib.icgs_colorize_refine_async(ctypes.byref(sc), ctypes.byref(cm), ctypes.byref(tg), ctypes.byref(opt), -1,
+                                        None, None, 0, None, None)
+    assert st == icgs.ERR_INVALID_ARG and "n_steps" in lib.icgs_last_error().decode()
+    assert lib.icgs_async_status(None, None) == icgs.ERR_INVALID_ARG
+    assert lib.icgs_async_status(ctypes.c_void_p(4096 + 16), None) == icgs.ERR_INVALID_ARG
+    assert "aligned" in lib.icgs_last_error().decode()

@@ -1,5 +1,5 @@
 """The benchmark's reference arm (the FP64 oracle on the host cores) on CPU: one step over a
-one-camera sample prints a single JSON line with the contract's fields, the same metric and
+one-camera sample (of the relighting workload, to stay quick on CPU) prints a single JSON line with the contract's fields, the same metric and
 config as the library arm, and a cpu_baseline that describes the run."""
 import json
 import os
@@ -10,8 +10,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_json_line():
-    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0", "--cpu-sample-cams", "1"], cwd=ROOT, capture_output=True, text=True,
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "relight",
+                        "--steps", "1", "--warmup", "0", "--ref-cams", "1"], cwd=ROOT, capture_output=True, text=True,
                        timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]

@@ -8,7 +8,8 @@ import pytest
 from oracle import oracle as O
 from paper_2604_17155_gb300 import workloads as W
 
-from _parity import TOL_FP32, coefficient_report, psnr_delta, to_np
+from _parity import (ADJ_TOL_O, ADJ_TOL_T, TOL_FP32, adjoint_flags, adjoint_report, coefficient_report, psnr_delta,
+                     to_np)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -71,14 +72,24 @@ def test_colorize_degrees(icgs, L, prec):
     # the factor reproduces A = G + w Lambda of the oracle for the well-seen Gaussians
     B = (L + 1) ** 2
     ch = to_np(chol).astype(np.float64)
+    P = B * (B + 1) // 2
+    assert ch.shape[1] == 3 * P
     ok = checked
     Lf = np.zeros((ok.sum(), B, B))
     rows, cols = np.tril_indices(B)
-    Lf[:, rows, cols] = ch[ok]
+    Lf[:, rows, cols] = ch[ok, :P]
     A_gpu = Lf @ np.transpose(Lf, (0, 2, 1))
     A_ref = col["A"][ok]
     rel = np.abs(A_gpu - A_ref).max(axis=(1, 2)) / np.abs(A_ref).max(axis=(1, 2))
     assert np.percentile(rel, 99) <= 1e-4
+    # the record's A = hi + lo (what the adjoint refines against)
+    Af = np.zeros((ok.sum(), B, B))
+    Af[:, rows, cols] = ch[ok, P:2 * P] + ch[ok, 2 * P:]
+    Af = Af + np.transpose(Af, (0, 2, 1)) - Af * np.eye(B)[None]
+    relA = np.abs(Af - A_ref).max(axis=(1, 2)) / np.abs(A_ref).max(axis=(1, 2))
+    print(f"record A: max rel {relA.max():.2e}")
+    # MIXED: the compensated sums; PLAIN: FP32 sums over the cameras, one rounding per term
+    assert relA.max() <= (1e-5 if prec == "mixed" else 1e-3)
 
 
 @pytest.mark.parametrize("L", [0, 1])
@@ -99,8 +110,10 @@ def test_adjoint_degrees(icgs, L):
     dt = np.abs(gt - gt_ref)
     rep, err, checked = coefficient_report(to_np(c), col)
     eo = np.abs(go - go_ref)[checked] / np.maximum(np.abs(go_ref[checked]), 1e-3 * np.abs(go_ref).max())
+    arep = adjoint_report(gt, go, gt_ref, go_ref, col, adjoint_flags(sc, cams, t64, col))
     print(f"adjoint L={L}: dL/dt p99.9 |d|/max {np.percentile(dt, 99.9) / np.abs(gt_ref).max():.2e}, "
-          f"dL/do p99 rel {np.percentile(eo, 99):.2e} over {checked.sum()}")
+          f"dL/do p99 rel {np.percentile(eo, 99):.2e} over {checked.sum()}", arep)
+    assert arep["dt_max_clean"] <= ADJ_TOL_T and arep["do_max_clean"] <= ADJ_TOL_O
     assert np.percentile(dt, 99.9) <= 1e-3 * np.abs(gt_ref).max()
     assert np.percentile(eo, 99) <= 1e-2
 
@@ -154,8 +167,10 @@ def test_render_and_adjoint_channel_counts(icgs, K):
     dt = np.abs(gt - gt_ref)
     rep, err, checked = coefficient_report(to_np(c), col)
     eo = np.abs(go - go_ref)[checked] / np.maximum(np.abs(go_ref[checked]), 1e-3 * np.abs(go_ref).max())
+    arep = adjoint_report(gt, go, gt_ref, go_ref, col, adjoint_flags(sc, cams, t64, col))
     print(f"adjoint K={K}: dL/dt p99.9 |d|/max {np.percentile(dt, 99.9) / np.abs(gt_ref).max():.2e}, "
-          f"dL/do p99 rel {np.percentile(eo, 99):.2e} over {checked.sum()}")
+          f"dL/do p99 rel {np.percentile(eo, 99):.2e} over {checked.sum()}", arep)
+    assert arep["dt_max_clean"] <= ADJ_TOL_T and arep["do_max_clean"] <= ADJ_TOL_O
     assert np.percentile(dt, 99.9) <= 1e-3 * np.abs(gt_ref).max()
     assert np.percentile(eo, 99) <= 1e-2
 

@@ -10,7 +10,7 @@ import pytest
 from oracle import oracle as O
 from paper_2604_17155_gb300 import workloads as W
 
-from _parity import TOL_BF16, TOL_FP32, coefficient_report, to_np
+from _parity import ADJ_TOL_O, ADJ_TOL_T, TOL_BF16, TOL_FP32, adjoint_flags, adjoint_report, coefficient_report, to_np
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -26,12 +26,14 @@ def _sampled_oracle(scene, cams, targets, L, sample, threads=None):
         for k in range(len(sample)):
             if p["visible"][k]:
                 mask[j, int(p["y0"][k]):int(p["y1"][k]) + 1, int(p["x0"][k]):int(p["x1"][k]) + 1] = True
-    V, S, so, su, pairs = O.accumulate(scene, cams, targets, mask=mask, threads=threads)
+    a = O.accumulate_stakes(scene, cams, targets, mask=mask, threads=threads)
     sub = scene.subset(sample)
     Y = O.view_basis(sub, cams, L)
-    G, b, w = O.fold(V[:, sample], S[:, sample], Y)
-    c, status, A = O.solve(G, b, w, O.paper_lambda(L))
-    return dict(c=c, w=w, A=A, stake_own=so[:, sample], stake_up=su[:, sample])
+    G, b, w = O.fold(a["V"][:, sample], a["S"][:, sample], Y)
+    lam = O.paper_lambda(L)
+    c, status, A = O.solve(G, b, w, lam)
+    return dict(c=c, w=w, A=A, Y=Y, lam=lam, stake_own=a["stake_own"][:, sample], stake_up=a["stake_up"][:, sample],
+                stake_tw=a["stake_tw"][:, sample])
 
 
 def test_relight_fullsize_sampled():
@@ -55,9 +57,10 @@ def test_relight_fullsize_sampled():
     ref = _sampled_oracle(scene, cams, t.astype(np.float64), L, sample)
     rep, err, checked = coefficient_report(c[sample], ref, tol=TOL_FP32)
     print("relight full size", rep, icgs.last_stats())
-    # with 100 cameras most Gaussians have some near-threshold pixel: the strict set is small and
-    # every other sampled Gaussian is held to the flip-aware bound
-    assert rep["checked"] >= 5
+    # every sampled Gaussian is held to the tolerance plus its flip bound; "checked" ones (bound at
+    # most a tenth of the tolerance) to the tolerance
+    assert rep["unbounded"] == 0 and rep["checked"] >= 8
+    assert rep["within_2tol"] >= N_SAMPLE // 2
     assert rep["max_checked"] <= TOL_FP32
     assert rep["bound_excess"] <= 0
 
@@ -111,11 +114,14 @@ def test_relight_adjoint_fullsize_against_fp64_reference():
     tt = torch.tensor(t, device=dev)
     c, status, chol = icgs.colorize(gs, gc, tt, L)
     r = np.random.default_rng(2006).standard_normal((scene.n, 16, 3))
-    gcoef = torch.tensor(2.0 * r, dtype=torch.float32, device=dev) * c
-    gt, go = icgs.colorize_backward(gs, gc, tt, L, c, chol, gcoef)
-    gt, go = to_np(gt), to_np(go)
     col = O.colorize(scene, cams, t64, L)
+    # the same dL/dc and coefficients on both sides (the oracle's), the GPU's own solve records
+    gcoef = torch.tensor(2.0 * r * col["c"], dtype=torch.float32, device=dev)
+    gt, go = icgs.colorize_backward(gs, gc, tt, L, torch.tensor(col["c"], dtype=torch.float32, device=dev), chol, gcoef)
+    gt, go = to_np(gt), to_np(go)
     gt_ref, go_ref = O.adjoint(scene, cams, t64, L, None, 2.0 * r * col["c"], col=col)
+    arep = adjoint_report(gt, go, gt_ref, go_ref, col, adjoint_flags(scene, cams, t64, col))
+    print("adjoint full size, clean sets:", arep)
     dt = np.abs(gt - gt_ref)
     scale_t = np.abs(gt_ref).max()
     rep, err, checked = coefficient_report(to_np(c), col, tol=TOL_FP32)
@@ -137,6 +143,13 @@ def test_relight_adjoint_fullsize_against_fp64_reference():
             print(f"  pivot ratio [{lo:g}, {hi:g}): {sel.sum()} checked, p99 {np.percentile(err[sel], 99):.2e} "
                   f"max {err[sel].max():.2e}")
     assert np.percentile(dt, 99.9) <= 1e-3 * scale_t
-    assert np.percentile(eo, 99) <= 1e-2
-    assert rep["p99_checked"] <= TOL_FP32
+    # dL/dt: the worst pixel of those no near decision and no flip-affected Gaussian touches (about
+    # 1% of the 64 M pixels at 100 cameras); dL/do: with 100 cameras every Gaussian shares some
+    # pixel with a flip-affected one, so the clean set is empty and the bound is the 99th percentile
+    assert arep["clean_pixels"] >= 100_000
+    assert arep["dt_max_clean"] <= ADJ_TOL_T
+    if arep["clean_gaussians"] > 0:
+        assert arep["do_max_clean"] <= ADJ_TOL_O
+    assert arep["do_p99_all"] <= ADJ_TOL_O
+    assert rep["max_checked"] <= TOL_FP32
     assert rep["bound_excess"] <= 0.0

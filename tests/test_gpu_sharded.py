@@ -1,8 +1,9 @@
-"""Camera sharding of the normal equations on the GPU (icgs_accumulate, icgs_solve): the sums of
-Eq. 12-14 over disjoint camera subsets add up to the sums over all cameras, so accumulating two
-shards separately, adding them and solving once gives the single-call result. Also checked: one
-shard equal to every camera reproduces icgs_colorize, and the sharded result matches the FP64
-oracle. One GPU, one process: the cross-GPU all-reduce itself is covered by the gloo test."""
+"""Camera sharding of the normal equations on the GPU (icgs_accumulate, icgs_solve, packed float64
+sums): the sums of Eq. 12-14 over disjoint camera subsets add up to the sums over all cameras, so
+accumulating two shards separately, adding them and solving once gives the single-call result, and
+solving contiguous Gaussian ranges of the summed rows separately gives the same rows. Also checked:
+one shard equal to every camera reproduces icgs_colorize, and the sharded result matches the FP64
+oracle. One GPU, one process: the cross-GPU reduce-scatter itself is covered by the gloo tests."""
 import numpy as np
 import pytest
 
@@ -46,18 +47,23 @@ def test_two_shards_add_up_to_one_call(icgs, L, prec):
     tt = torch.tensor(t, device=DEV)
     c_one, s_one, _ = icgs.colorize(gs, gc, tt, L, precision=prec)
     # every camera in one shard: the same sums as icgs_colorize's own fold
-    G, b, w = icgs.accumulate(gs, gc, tt, L, precision=prec)
-    c_all, s_all, _ = icgs.solve(G, b, w, L, precision=prec)
-    # two round-robin shards, added, solved once
+    sums_all = icgs.accumulate(gs, gc, tt, L, precision=prec)
+    c_all, s_all, _ = icgs.solve(sums_all, L, precision=prec)
+    # two round-robin shards, added, solved once -- and solved as two Gaussian ranges
     parts = [icgs.shard_cameras(cams.n, r, 2) for r in range(2)]
     sums = [icgs.accumulate(gs, gc.subset(p), tt[torch.as_tensor(p, device=DEV)].contiguous(), L, precision=prec)
             for p in parts]
-    G2, b2, w2 = (sums[0][k] + sums[1][k] for k in range(3))
-    c_two, s_two, _ = icgs.solve(G2.contiguous(), b2.contiguous(), w2.contiguous(), L, precision=prec)
+    total = (sums[0] + sums[1]).contiguous()
+    c_two, s_two, _ = icgs.solve(total, L, precision=prec)
+    for r in range(3):
+        lo, hi = icgs.shard_gaussians(sc.n, r, 3)
+        c_r, s_r, _ = icgs.solve(total[lo:hi].contiguous(), L, precision=prec)
+        assert torch.equal(c_r, c_two[lo:hi]) and torch.equal(s_r, s_two[lo:hi])
     s_one, s_all, s_two = to_np(s_one), to_np(s_all), to_np(s_two)
     unseen = icgs.GAUSSIAN_UNSEEN
     assert np.array_equal(s_one == unseen, s_all == unseen)
     assert np.array_equal(s_one == unseen, s_two == unseen)
+    w, w2 = sums_all[:, -1], total[:, -1]
     rel_w = float((torch.abs(w2 - w) / torch.clamp(w, min=1e-30)).max())
     ok = (s_one != unseen) & (to_np(w) >= 1.0)
     e_all = _max_rel(to_np(c_all), to_np(c_one), ok)
@@ -79,15 +85,19 @@ def test_sharded_against_oracle(icgs):
     tt = torch.tensor(t, device=DEV)
     parts = [icgs.shard_cameras(cams.n, r, 3) for r in range(3)]
     sums = [icgs.accumulate(gs, gc.subset(p), tt[torch.as_tensor(p, device=DEV)].contiguous(), L) for p in parts]
-    G, b, w = (sum(x[k] for x in sums).contiguous() for k in range(3))
-    c, status, chol = icgs.solve(G, b, w, L)
+    total = sum(sums).contiguous()
+    c, status, chol = icgs.solve(total, L)
     rep, err, checked = coefficient_report(to_np(c), col, tol=TOL_FP32)
     print("three shards vs oracle", rep, icgs.last_stats())
-    assert rep["p99_checked"] <= TOL_FP32
+    assert rep["max_checked"] <= TOL_FP32
     assert rep["bound_excess"] <= 0
-    # the sums themselves against the oracle's G, b, w
+    # the sums themselves against the oracle's G, b, w (packed: upper triangle of G, b, w)
     ok = col["w"] >= 1.0
-    gw = np.abs(to_np(w) - col["w"])[ok] / col["w"][ok]
-    gG = np.abs(G.cpu().numpy() - col["G"]).max(axis=(1, 2))[ok] / np.abs(col["G"]).max(axis=(1, 2))[ok]
+    B = (L + 1) ** 2
+    r_, c_ = np.triu_indices(B)
+    tot = total.cpu().numpy()
+    w = tot[:, -1]
+    gw = np.abs(w - col["w"])[ok] / col["w"][ok]
+    gG = np.abs(tot[:, :len(r_)] - col["G"][:, r_, c_]).max(axis=1)[ok] / np.abs(col["G"]).max(axis=(1, 2))[ok]
     print(f"sums vs oracle: w p99 {np.percentile(gw, 99):.1e}, G p99 {np.percentile(gG, 99):.1e}")
     assert np.percentile(gw, 99) <= 1e-4 and np.percentile(gG, 99) <= 1e-4
