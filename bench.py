@@ -1,19 +1,29 @@
 #!/usr/bin/env python
 """Benchmark of the instant-colorization hot path (Alg. 1 lines 1-6) on one GB300.
 
-Workload ("relight", the relighting-shaped scene): 200,000 Gaussians from 40 anisotropic clusters in
-a radius-4 ball, 100 cameras on a radius-6 hemisphere at 800x800, fov 45 deg; RGB float32 targets
-rendered from random degree-3 SH coefficients (DC ~ U(0,1), higher ~ N(0,0.1)); L = 3 with the
-paper's per-band lambda. A step is one full icgs_colorize call: projection, binning, depth sort,
-blend-accumulate, fold and the regularised solve for every Gaussian.
+Headline workload ("segmentation", the large segmentation scene): 3,000,000 Gaussians from 40
+anisotropic clusters in a radius-10 ball, 200 cameras on a radius-15 hemisphere at 1600x1060,
+fov 55 deg; 16-class one-hot masks (a Voronoi partition of space with 16 seeds, each view's label
+render arg-maxed, FP16), SH degree 0, lambda_0 = 1e-5. A step is one full icgs_colorize call over
+the scene: projection, binning, depth sort, the blend-accumulate walk (the 16-channel contraction
+on tcgen05 tensor cores in MIXED precision), and the per-Gaussian solve.
 
-  value        ms per colorized scene (device-resident targets, CUDA events), whole job
-  e2e          the same through icgs_colorize_host: pinned H2D of the targets and D2H of the
-               coefficients inside the timed region
-  roofline     the blend-accumulate kernel (dominant), timed live with CUDA events on its stream
-  cpu_baseline the FP64 oracle on the host cores, on a sample of cameras, scaled to a scene
+The same line carries, as extra keys, the other workloads measured the same way:
+  segmentation_rgb  the RGB SH-degree-3 pass on the same scene and rig (FP32 targets rendered from
+                    random degree-3 coefficients);
+  relight           200,000 Gaussians, 100 cameras 800x800, L = 3 RGB (plus its adjoint and one
+                    refinement step);
+  features          1,000,000 Gaussians, 150 cameras 1000x750, 64 BF16 channels, L = 0.
 
-`--impl reference` times the oracle (CPU) on the same workload and prints the reference line.
+Per workload:
+  value / ms_per_scene  ms per colorized scene (device-resident targets, CUDA events), whole job
+  e2e                   the same through icgs_colorize_host: pinned H2D of the targets and D2H of
+                        the coefficients and status inside the timed region
+  plain_fp32            the plain FP32 path on the same inputs, and MIXED's speedup over it
+  roofline              the dominant (walk) kernel, timed live with CUDA events on its stream
+  cpu_baseline          the FP64 oracle on the host cores, on a sample of cameras, scaled to a scene
+
+`--impl reference` times the oracle (CPU) on the headline workload and prints the reference line.
 Multi-GPU (torchrun): every rank colorizes its own replica of the scene (weak scaling).
 """
 from __future__ import annotations
@@ -36,22 +46,30 @@ if ROOT not in sys.path:
 
 from paper_2604_17155_gb300 import workloads as W  # noqa: E402
 
-WORKLOAD = "relight"
-SEED = 2000
+HEADLINE = "segmentation"
+EXTRAS = ("segmentation_rgb", "relight", "features")
 METRIC = "colorize ms/scene"
 UNIT = "ms/scene"
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
-# DRAM bytes (read + write) of the dominant kernel per scene, from one ncu capture each
-# (profiles/ holds the summaries and the commands). A figure is reported only while the kernel's
-# source files hash to the value it was captured with; after any change it is null until re-captured.
+# scene (workload name in workloads.py), seed, SH degree, target kind of each benchmark workload
+SPECS = {
+    "segmentation": dict(scene="segmentation", seed=4000, L=0, target="masks"),
+    "segmentation_rgb": dict(scene="segmentation", seed=4000, L=3, target="rgb"),
+    "relight": dict(scene="relight", seed=2000, L=3, target="rgb"),
+    "features": dict(scene="features", seed=3000, L=0, target="features"),
+}
+
+# DRAM bytes (read + write) of the walk kernel per scene, from one ncu capture each (the profiles
+# directory holds the summaries and the commands). A figure is reported only while the kernel's
+# source files hash to the value it was captured with; after any change it is null until
+# re-captured.
 KERNEL_SOURCES = {
     "cuda-core": ["blend.cu", "walk.cuh", "icgs_device.cuh", "icgs_internal.h"],
     "tensor-core": ["contract_tc.cu", "walk.cuh", "icgs_device.cuh", "icgs_internal.h"],
 }
 MEASURED_TRAFFIC = {
-    # relight, 100 cameras: one full-size launch captured (profiles/blend_accumulate_relight.md)
+    # relight, 100 cameras: one full-size launch captured
     ("relight", "cuda-core"): {"bytes_per_scene": 2148486912 + 288519424, "source_sha": "be1ccf7fce8493cc"},
     # features: a 10-camera launch captured and scaled by 150/10 cameras (the targets, the per-camera
     # tile lists and the per-camera accumulator re-streaming all grow with the camera count)
@@ -65,7 +83,7 @@ def kernel_source_sha(kind):
     import hashlib
     import re
     m = hashlib.sha256()
-    base = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2604_17155_gb300", "csrc")
+    base = os.path.join(ROOT, "paper_2604_17155_gb300", "csrc")
     for f in KERNEL_SOURCES[kind]:
         with open(os.path.join(base, f), encoding="utf-8") as fh:
             src = fh.read()
@@ -75,35 +93,41 @@ def kernel_source_sha(kind):
     return m.hexdigest()[:16]
 
 
-def measured_traffic(workload, kind, n_cams_full, n_cams):
+def measured_traffic(workload, kind, full_rig):
     t = MEASURED_TRAFFIC.get((workload, kind))
-    if t is None or n_cams != n_cams_full or kernel_source_sha(kind) != t["source_sha"]:
+    if t is None or not full_rig or kernel_source_sha(kind) != t["source_sha"]:
         return None
     return t["bytes_per_scene"]
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="icgs", choices=["icgs", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "plain"])
-    ap.add_argument("--cpu-sample-cams", type=int, default=0, help="cameras in the oracle sample (0: host cores)")
+    ap.add_argument("--workload", default=HEADLINE, choices=list(SPECS),
+                    help="the workload of the headline value (default: the large segmentation masks)")
+    ap.add_argument("--extras", default=",".join(EXTRAS),
+                    help="comma-separated workloads measured as extra keys ('' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cams", type=int, default=0, help="profiling only: use the first N cameras of the rig")
-    ap.add_argument("--workload", default="relight", choices=["relight", "features", "segmentation", "segmentation_rgb"],
-                    help="relight (the headline); the others document the feature / mask / large-RGB workloads")
-    return ap.parse_args()
+    ap.add_argument("--ref-cams", type=int, default=0,
+                    help="cameras in each step's oracle sample of the reference arm (0: one per core, up to 16)")
+    ap.add_argument("--cams", type=int, default=0, help="profiling only: use the first N cameras of each rig")
+    return ap.parse_args(argv)
 
 
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         d = json.load(open(path))
-        return dict(hbm_gbs=float(d["hbm_gbs"]), sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)), source="measured")
+        return dict(hbm_gbs=float(d["hbm_gbs"]), bf16_tflops=float(d["bf16_tflops"]),
+                    bf16_tflops_sustained=float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                    sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)), source="measured")
     except Exception:
-        return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+        return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0, sm_max_mhz=2070.0,
+                    source="fallback")
 
 
 # ------------------------------------------------------------------------------------------
@@ -156,40 +180,23 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------
-# oracle baseline (host cores)
+# workloads
 # ------------------------------------------------------------------------------------------
-def oracle_sample_ms_per_scene(scene, cams, targets_host_fn, n_sample, threads):
-    """Times the oracle's colorize on n_sample cameras (all Gaussians, all pixels), scaled to the
-    full rig: per-camera walk time x cameras + the fold and solve of every Gaussian."""
-    from oracle import oracle as O
-    O.build()
-    idx = np.linspace(0, cams.n - 1, n_sample).round().astype(int)
-    sub = cams.subset(idx)
-    t_host = targets_host_fn(idx)
-    t0 = time.perf_counter()
-    V, S, _, _, pairs = O.accumulate(scene, sub, t_host, threads=threads)
-    t1 = time.perf_counter()
-    Y = O.view_basis(scene, sub, 3)
-    G, b, w = O.fold(V, S, Y)
-    O.solve(G, b, w, O.paper_lambda(3))
-    t2 = time.perf_counter()
-    walk_per_cam = (t1 - t0) / n_sample * min(threads, n_sample)  # wall time of one camera on one core
-    fold_per_cam = (t2 - t1) / n_sample
-    ms = 1e3 * (walk_per_cam * cams.n / threads + fold_per_cam * cams.n)
-    return ms, int(pairs.sum()), idx, (t2 - t0)
-
-
-# ------------------------------------------------------------------------------------------
-def make_workload(n_cams=0, workload=WORKLOAD):
-    name = {"relight": "relight", "features": "features", "segmentation": "segmentation",
-            "segmentation_rgb": "segmentation"}[workload]
-    seed = {"relight": SEED, "features": 3000, "segmentation": 4000, "segmentation_rgb": 4000}[workload]
-    scene = W.make_scene(name, seed)
-    cams = W.make_cameras(name)
+def make_workload(name, n_cams=0):
+    sp = SPECS[name]
+    scene = W.make_scene(sp["scene"], sp["seed"])
+    cams = W.make_cameras(sp["scene"])
     if n_cams:
         cams = cams.subset(np.arange(min(n_cams, cams.n)))
-    coeffs = W.sh_coefficients(scene.n, 3, 3, seed + 1)
-    return scene, cams, coeffs
+    return scene, cams
+
+
+def rgb_coefficients(name, scene):
+    return W.sh_coefficients(scene.n, 3, 3, SPECS[name]["seed"] + 1)
+
+
+def mask_labels(scene):
+    return W.voronoi_labels(scene.means, 16, 4002, W.WORKLOADS["segmentation"]["radius"])
 
 
 def device_fourier_fields(n_views, height, width, channels, seed, dev, n_modes=32, max_freq=4.0):
@@ -213,63 +220,334 @@ def device_fourier_fields(n_views, height, width, channels, seed, dev, n_modes=3
     return out
 
 
-def make_targets(workload, scene, cams, coeffs, gs, gc, dev, icgs):
-    """Device-resident targets of each workload and its (L, lambda)."""
+def make_targets(name, scene, cams, gs, gc, dev, icgs):
+    """Device-resident targets of a workload (generated by the library's render or on the device)."""
     import torch
-    if workload in ("relight", "segmentation_rgb"):
-        return icgs.render(gs, gc, torch.tensor(coeffs, device=dev), 3), 3
-    if workload == "features":
-        return device_fourier_fields(cams.n, cams.height, cams.width, 64, 3002, dev), 0
-    # segmentation: one-hot labels of a 16-cell Voronoi partition, rendered per view, argmax -> FP16
-    labels = W.voronoi_labels(scene.means, 16, 4002, W.WORKLOADS["segmentation"]["radius"])
-    img = icgs.render(gs, gc, torch.tensor(W.one_hot_dc(labels, 16), device=dev), 0)
+    kind = SPECS[name]["target"]
+    if kind == "rgb":
+        return icgs.render(gs, gc, torch.tensor(rgb_coefficients(name, scene), device=dev), 3)
+    if kind == "features":
+        return device_fourier_fields(cams.n, cams.height, cams.width, 64, 3002, dev)
+    # masks: one-hot labels of a 16-cell Voronoi partition, rendered per view, arg-maxed -> FP16
+    img = icgs.render(gs, gc, torch.tensor(W.one_hot_dc(mask_labels(scene), 16), device=dev), 0)
     t = torch.empty(img.shape, dtype=torch.float16, device=dev)
     for v in range(img.shape[0]):  # per view, to keep the int64 temporaries small
         t[v] = torch.nn.functional.one_hot(img[v].argmax(-1), 16).to(torch.float16)
     del img
-    return t, 0
+    return t
 
 
-def workload_config(workload, n, n_cams, width, height, L, K, dtype_name, precision, world, target_bytes):
+def workload_config(name, n, n_cams, width, height, L, K, dtype_name, precision, world, target_bytes):
     """The `config` object of the JSON line; both arms describe the same workload with it."""
-    return {"workload": f"{workload}: {n} Gaussians, {n_cams} cameras {width}x{height}, L={L}, {K} channels {dtype_name}",
+    return {"workload": f"{name}: {n} Gaussians, {n_cams} cameras {width}x{height}, L={L}, {K} channels {dtype_name}",
             "precision": precision, "parallelism": f"replicas x{world}",
             "l2": f"inputs larger than L2 ({target_bytes / 1e6:.0f} MB of targets per step)"}
 
 
+# ------------------------------------------------------------------------------------------
+# oracle baseline (host cores)
+# ------------------------------------------------------------------------------------------
+def strip_mask(cams, every):
+    """Pixel mask [C,H,W] of every `every`-th strip of 16 image rows (the oracle builds its
+    per-pixel lists strip by strip and skips strips without a selected pixel)."""
+    m = np.zeros((cams.n, cams.height, cams.width), bool)
+    for y0 in range(0, cams.height, 16 * every):
+        m[:, y0:y0 + 16] = True
+    return m
+
+
+def oracle_sample(scene, cams, L, K, targets_host_fn, idx, threads, strip_every=1):
+    """Times the oracle's colorize on the cameras idx (all Gaussians; all pixels, or every
+    strip_every-th 16-row strip): the walk, then the fold and solve of every Gaussian. Returns
+    (walk seconds, fold+solve seconds, contributing pairs)."""
+    from oracle import oracle as O
+    O.build()
+    sub = cams.subset(idx)
+    t_host = targets_host_fn(idx)
+    mask = strip_mask(sub, strip_every) if strip_every > 1 else None
+    t0 = time.perf_counter()
+    V, S, _, _, pairs = O.accumulate(scene, sub, t_host, mask=mask, threads=threads)
+    t1 = time.perf_counter()
+    fs = oracle_fold_solve(scene, sub, V, S, L)
+    return t1 - t0, fs, int(pairs.sum())
+
+
+FOLD_SAMPLE = 200_000
+
+
+def oracle_fold_solve(scene, cams, V, S, L):
+    """Seconds the oracle's fold and solve (Eq. 12-14) take for every Gaussian: timed on the first
+    FOLD_SAMPLE Gaussians and scaled by n / FOLD_SAMPLE (both are linear in the Gaussian count)."""
+    from oracle import oracle as O
+    m = min(scene.n, FOLD_SAMPLE)
+    t0 = time.perf_counter()
+    if L == 0:
+        w = V[:, :m].sum(0)
+        O.solve((w / (4 * math.pi))[:, None, None], S[:, :m].sum(0)[:, None, :] / math.sqrt(4 * math.pi), w,
+                O.paper_lambda(0))
+    else:
+        G, b, w = O.fold(V[:, :m], S[:, :m], O.view_basis(scene.subset(np.arange(m)), cams, L))
+        O.solve(G, b, w, O.paper_lambda(L))
+    return (time.perf_counter() - t0) * scene.n / m
+
+
+def cpu_baseline(name, scene, cams, L, K, targets_host_fn):
+    """The oracle on all host cores (one camera per core, all pixels) and on one core (one camera,
+    every 4th strip of rows), each extrapolated to the whole rig."""
+    cores = os.cpu_count() or 1
+    n_all = min(cores, 16, cams.n)
+    idx = np.linspace(0, cams.n - 1, n_all).round().astype(int)
+    walk, fold, pairs = oracle_sample(scene, cams, L, K, targets_host_fn, idx, cores)
+    # cameras run in parallel, one per core: the walk of n_all cameras took `walk` seconds of wall time
+    ms_all = 1e3 * (walk * cams.n / n_all + fold * cams.n / n_all)
+    every = 4
+    walk1, fold1, _ = oracle_sample(scene, cams, L, K, targets_host_fn, idx[:1], 1, strip_every=every)
+    ms_one = 1e3 * (walk1 * every * cams.n + fold1 * cams.n)
+    return {"value": ms_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_all} of {cams.n} cameras (all Gaussians and pixels), one per core; walk x {cams.n}/{n_all} "
+                      f"and fold/solve (of {min(scene.n, FOLD_SAMPLE)} Gaussians x {scene.n}/{min(scene.n, FOLD_SAMPLE)})"
+                      f" x {cams.n}/{n_all} (extrapolated)",
+            "single_core": {"value": ms_one, "unit": UNIT, "cores": 1,
+                            "sample": f"1 camera, every {every}th 16-row strip; walk x {every} x {cams.n} cameras, "
+                                      f"fold/solve x {cams.n} (extrapolated)"},
+            "pairs_oracle_sample": pairs}
+
+
+# ------------------------------------------------------------------------------------------
+# the reference arm: the oracle on the headline workload
+# ------------------------------------------------------------------------------------------
 def run_reference(args, rank, world):
-    """The oracle on the host cores, one bounded camera sample per step."""
+    """The oracle on the host cores, one bounded sample per step: one camera per core, every 8th
+    16-row strip of pixels, extrapolated to the rig."""
     if rank != 0:
         return
     from oracle import oracle as O
     O.build()
-    scene, cams, coeffs = make_workload()
+    name = args.workload
+    sp = SPECS[name]
+    scene, cams = make_workload(name, args.cams)
     cores = os.cpu_count() or 1
-    n_sample = args.cpu_sample_cams or min(cores, 8)
+    n_sample = min(args.ref_cams or min(cores, 16), cams.n)
+    every = 8
     idx = np.linspace(0, cams.n - 1, n_sample).round().astype(int)
     sub = cams.subset(idx)
-    targets = O.render(scene, sub, coeffs, 3, threads=cores)  # oracle-rendered targets of the sample
+    mask = strip_mask(sub, every)
+    L = sp["L"]
+    if sp["target"] == "masks":
+        img = O.render(scene, sub, W.one_hot_dc(mask_labels(scene), 16), 0, mask=mask, threads=cores)
+        targets = (np.eye(16, dtype=np.float32)[img.argmax(-1)] * mask[..., None]).astype(np.float32)
+        del img
+        K, dname = 16, "float16"
+    elif sp["target"] == "rgb":
+        targets = O.render(scene, sub, rgb_coefficients(name, scene), 3, mask=mask, threads=cores)
+        K, dname = 3, "float32"
+    else:
+        targets = W.fourier_fields(sub.n, cams.height, cams.width, 64, 3002)
+        K, dname = 64, "bfloat16"
     times = []
     for step in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        V, S, _, _, pairs = O.accumulate(scene, sub, targets, threads=cores)
+        V, S, _, _, pairs = O.accumulate(scene, sub, targets, mask=mask, threads=cores)
         t1 = time.perf_counter()
-        G, b, w = O.fold(V, S, O.view_basis(scene, sub, 3))
-        O.solve(G, b, w, O.paper_lambda(3))
-        t2 = time.perf_counter()
+        fs = oracle_fold_solve(scene, sub, V, S, L)
         if step >= args.warmup:
-            walk = (t1 - t0) * min(cores, n_sample) / n_sample
-            times.append(1e3 * (walk * cams.n / cores + (t2 - t1) / n_sample * cams.n))
+            times.append(1e3 * ((t1 - t0) * every * cams.n / n_sample + fs * cams.n / n_sample))
     ms = float(np.mean(times))
-    sample = f"{n_sample} of {cams.n} cameras (all 200,000 Gaussians, all 800x800 pixels) per step, scaled to {cams.n}"
+    sample = (f"{n_sample} of {cams.n} cameras, one per core, every {every}th 16-row strip of pixels (all "
+              f"{scene.n} Gaussians) per step; walk x {every} x {cams.n}/{n_sample}; fold/solve of "
+              f"{min(scene.n, FOLD_SAMPLE)} Gaussians x {scene.n}/{min(scene.n, FOLD_SAMPLE)} x {cams.n}/{n_sample}")
+    target_bytes = cams.n * cams.width * cams.height * K * (4 if dname == "float32" else 2)
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": workload_config("relight", scene.n, cams.n, cams.width, cams.height, 3, 3, "float32", args.precision,
-                                      world, cams.n * cams.width * cams.height * 3 * 4),
+            "config": workload_config(name, scene.n, cams.n, cams.width, cams.height, L, K, dname, args.precision,
+                                      world, target_bytes),
             "cpu_baseline": {"value": ms, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# the library arm
+# ------------------------------------------------------------------------------------------
+def walk_roofline(name, kind, K, L, blend_ms, stats, target_bytes, n, n_cams, tiles, pk, sm_count, full_rig):
+    """Roofline of the walk (blend-accumulate) kernel, from its CUDA-event time per scene.
+    Algorithmic work (the method's own, per the survey's accounting):
+      flops  contributing pairs x (15 FP32 ops + 1 exp for the weight + 2 (1 + K) for V and S),
+      bytes  targets read once + 8 B list entry and 32 B Gaussian record per (Gaussian, tile)
+             instance + the accumulator read-modify-write (1 + K floats per row and pass)."""
+    pairs = stats["contrib_pairs"]
+    inst = stats["instances"]
+    sec = blend_ms * 1e-3
+    flops = pairs * (15 + 2 * (1 + K))
+    fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6
+    acc_rows = n * (1 if L == 0 else n_cams)
+    bytes_alg = target_bytes + inst * (8 + 32) + acc_rows * (1 + K) * 4 * 2
+    hbm = {"algorithmic_bytes": bytes_alg, "achieved_gbs": bytes_alg / sec / 1e9, "peak_gbs": pk["hbm_gbs"],
+           "frac": bytes_alg / sec / 1e9 / pk["hbm_gbs"], "peak_source": pk["source"]}
+    alu = {"algorithmic_flops": flops, "achieved_tflops": flops / sec / 1e12, "peak_tflops": fp32_peak / 1e12,
+           "frac": flops / sec / fp32_peak,
+           "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {pk['sm_max_mhz']:.0f} MHz"}
+    traffic = measured_traffic(name, kind, full_rig)
+    if kind == "tensor-core":
+        # a5 with 16-bit targets: bound by the target bytes (HBM) plus the tensor-core contraction
+        # (survey 8(d)). The tensor view counts the dense MMA work issued: one
+        # [64 x 256] x [256 x (K + 8)] product per batch of 64 Gaussians of a tile list.
+        batches = inst / 64.0 + n_cams * tiles
+        kpad = 16 if K <= 16 else (32 if K <= 32 else 64)
+        mma_flops = batches * 2 * 64 * 256 * (kpad + 8)
+        tensor = {"issued_mma_flops": mma_flops, "achieved_tflops": mma_flops / sec / 1e12,
+                  "peak_tflops": pk["bf16_tflops"], "frac": mma_flops / sec / 1e12 / pk["bf16_tflops"],
+                  "peak_source": f"{pk['source']} dense bf16 (fp16 has the same rate)"}
+        kname = f"k_blend_accumulate_tc<{kpad}>"
+        roof = {"kernel": kname, "bound": "hbm", "achieved": hbm["achieved_gbs"], "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": hbm["frac"], "traffic": traffic,
+                "traffic_unit": "bytes per scene (DRAM read + write, ncu)", "peak_source": pk["source"],
+                "tensor_view": tensor, "alu_view": alu}
+    else:
+        kname = f"k_blend_accumulate2<{K}>" if K <= 3 else f"k_blend_accumulate<{min(K, 16)}>"
+        roof = {"kernel": kname, "bound": "alu", "achieved": alu["achieved_tflops"], "peak": alu["peak_tflops"],
+                "unit": "TFLOP/s", "frac": alu["frac"], "traffic": traffic,
+                "traffic_unit": "bytes per scene (DRAM read + write, ncu)", "peak_source": alu["peak_source"],
+                "hbm_view": hbm}
+    return roof
+
+
+def measure(name, args, world, dev, icgs, with_e2e, with_cpu):
+    """Times one workload: MIXED (or --precision) colorize on device-resident targets, the plain
+    FP32 path, optionally the host-buffer call and the oracle. Returns the per-workload record."""
+    import torch
+    sp = SPECS[name]
+    scene, cams = make_workload(name, args.cams)
+    gs = icgs.Scene.from_workload(scene, dev)
+    gc = icgs.Cameras.from_workload(cams)
+    with torch.no_grad():
+        targets = make_targets(name, scene, cams, gs, gc, dev, icgs)
+    torch.cuda.synchronize(dev)
+    L = sp["L"]
+    K = int(targets.shape[-1])
+    B = (L + 1) ** 2
+    target_bytes = targets.numel() * targets.element_size()
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(fn, n):
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        barrier()
+        t = torch.tensor([e0.elapsed_time(e1)], device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def step():
+        return icgs.colorize(gs, gc, targets, L, precision=args.precision)
+
+    for _ in range(args.warmup):
+        step()
+    # ---- device-resident timed region (stage events on the same stream) ----
+    icgs.set_stage_timing(True)
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    stage_sum = {}
+
+    def step_staged():
+        step()
+        for k, v in icgs.last_stage_ms().items():
+            stage_sum[k] = stage_sum.get(k, 0.0) + v
+
+    elapsed = timed(step_staged, args.steps)
+    clocks = sampler.stop()
+    icgs.set_stage_timing(False)
+    stats = icgs.last_stats()
+    stage_ms = {k: v / args.steps for k, v in stage_sum.items() if v > 0}
+    ms_scene = elapsed / args.steps
+    rec = {"ms_per_scene": ms_scene, "stage_ms": stage_ms, "clocks": clocks,
+           "gpu_launches": stats["launches"] * args.steps, "instances": stats["instances"],
+           "contrib_pairs": stats["contrib_pairs"], "fp64_gaussians": stats["fp64"],
+           "refolded_gaussians": stats["refold"],
+           "blend_contribs_per_s": stats["contrib_pairs"] / (stage_ms.get("blend", float("nan")) * 1e-3)}
+    tc = args.precision == "mixed" and K >= 16 and targets.dtype != torch.float32
+    rec["walk"] = "tensor-core" if tc else "cuda-core"
+    rec["dtype"] = "f16" if tc else "f32"
+    rec["dtype_detail"] = ("weights FP32; the (Gaussian x pixel) x (pixel x channel) contraction on tcgen05 in FP16 "
+                           "with FP32 accumulation (BF16 targets rescaled per tile by powers of two, exactly); fold "
+                           "and solve FP32 / FP64" if tc else
+                           "FP32 walk and fold; MIXED: compensated sums, float-float refinement, FP64 for flagged "
+                           "Gaussians")
+    rec["config"] = workload_config(name, scene.n, cams.n, cams.width, cams.height, L, K,
+                                    str(targets.dtype).replace("torch.", ""), args.precision, world, target_bytes)
+    props = torch.cuda.get_device_properties(dev)
+    tiles = ((cams.width + 15) // 16) * ((cams.height + 15) // 16)
+    full_rig = cams.n == W.make_cameras(sp["scene"]).n
+    rec["roofline"] = walk_roofline(name, rec["walk"], K, L, stage_ms.get("blend", float("nan")), stats, target_bytes,
+                                    scene.n, cams.n, tiles, peaks(), props.multi_processor_count, full_rig)
+    rec["roofline"]["sm_count"] = props.multi_processor_count
+
+    # ---- the plain FP32 path on the same inputs ----
+    if args.precision == "mixed":
+        n_plain = max(3, min(args.steps, 5))
+        icgs.colorize(gs, gc, targets, L, precision="plain")
+        plain_ms = timed(lambda: icgs.colorize(gs, gc, targets, L, precision="plain"), n_plain) / n_plain
+        rec["plain_fp32"] = {"ms_per_scene": plain_ms, "mixed_speedup": plain_ms / ms_scene}
+
+    # ---- end to end through the C ABI with host buffers (icgs_colorize_host) ----
+    if with_e2e:
+        host_t = torch.empty(targets.shape, dtype=targets.dtype, pin_memory=True)
+        host_t.copy_(targets)
+        host_c = torch.empty((scene.n, B, K), dtype=torch.float32, pin_memory=True)
+        host_s = torch.empty((scene.n,), dtype=torch.uint8, pin_memory=True)
+
+        def e2e_step():
+            icgs.colorize_host(gs, gc, host_t, L, precision=args.precision, coeffs_out=host_c, status_out=host_s)
+
+        e2e_step()
+        e2e_ms = timed(e2e_step, args.steps) / args.steps
+        rec["e2e"] = {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": target_bytes,
+                      "d2h_bytes_per_step": scene.n * B * K * 4 + scene.n, "call": "icgs_colorize_host"}
+        del host_t, host_c, host_s
+
+    # ---- relight extras: the adjoint (dL/dt, dL/do for L = sum r c^2) and refinement steps ----
+    if name == "relight":
+        c, st, chol = icgs.colorize(gs, gc, targets, L, precision=args.precision)
+        r = torch.randn(c.shape, generator=torch.Generator(device=dev).manual_seed(5005), device=dev)
+        gcoef = 2.0 * r * c
+        icgs.colorize_backward(gs, gc, targets, L, c, chol, gcoef, precision=args.precision)
+        n_adj = max(3, min(args.steps, 5))
+        adj_ms = timed(lambda: icgs.colorize_backward(gs, gc, targets, L, c, chol, gcoef, precision=args.precision),
+                       n_adj) / n_adj
+        rec["adjoint"] = {"ms_per_scene": adj_ms,
+                          "outputs": f"dL/dt [{cams.n},{cams.height},{cams.width},{K}] and dL/do [{scene.n}]",
+                          "launches": icgs.last_stats()["launches"]}
+        c_ref = c.clone()
+        icgs.colorize_refine(gs, gc, targets, L, c_ref, chol, 1, precision=args.precision)  # warm-up
+        n_ref, per_call = 3, 2
+
+        def refine_call():
+            c_ref.copy_(c)
+            icgs.colorize_refine(gs, gc, targets, L, c_ref, chol, per_call, precision=args.precision)
+
+        rec["refine"] = {"ms_per_step": timed(refine_call, n_ref) / (n_ref * per_call),
+                         "step": "render + residual accumulate + fold of b + update, all cameras",
+                         "launches_per_call": icgs.last_stats()["launches"]}
+
+    # ---- the oracle on the host cores ----
+    if with_cpu:
+        def targets_host(idx):
+            return targets[torch.as_tensor(idx, device=dev)].double().cpu().numpy()
+        rec["cpu_baseline"] = cpu_baseline(name, scene, cams, L, K, targets_host)
+    del targets
+    torch.cuda.empty_cache()
+    return rec
 
 
 def run_icgs(args, rank, world, local_rank):
@@ -281,197 +559,25 @@ def run_icgs(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    scene, cams, coeffs = make_workload(args.cams, args.workload)
-    gs = icgs.Scene.from_workload(scene, dev)
-    gc = icgs.Cameras.from_workload(cams)
-    with torch.no_grad():
-        targets, L = make_targets(args.workload, scene, cams, coeffs, gs, gc, dev, icgs)
-    torch.cuda.synchronize(dev)
-    K = int(targets.shape[-1])
-    B = (L + 1) ** 2
-    target_bytes = targets.numel() * targets.element_size()
-
-    def step():
-        return icgs.colorize(gs, gc, targets, L, precision=args.precision)
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize(dev)
-
-    for _ in range(args.warmup):
-        step()
-    stats_warm = icgs.last_stats()
-    stream = torch.cuda.current_stream(dev)
-
-    # ---- device-resident timed region (stage events on the same stream) ----
-    icgs.set_stage_timing(True)
-    sampler = ClockSampler(local_rank)
-    sampler.start()
-    stage_sum = {}
-    barrier()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-        for k, v in icgs.last_stage_ms().items():
-            stage_sum[k] = stage_sum.get(k, 0.0) + v
-    ev1.record(stream)
-    barrier()
-    clocks = sampler.stop()
-    icgs.set_stage_timing(False)
-    elapsed = ev0.elapsed_time(ev1)
-    stats = icgs.last_stats()
-    t = torch.tensor([elapsed], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    elapsed_max = float(t.item())
-    stage_ms = {k: v / args.steps for k, v in stage_sum.items() if v > 0}
-
-    # ---- end to end through the C ABI with host buffers (icgs_colorize_host): every step copies
-    # the targets from pinned host memory (staged per camera chunk, overlapped with the walk) and
-    # returns the coefficients and status to pinned host memory ----
-    host_t = torch.empty(targets.shape, dtype=targets.dtype, pin_memory=True)
-    host_t.copy_(targets)
-    host_c = torch.empty((scene.n, B, K), dtype=torch.float32, pin_memory=True)
-    host_s = torch.empty((scene.n,), dtype=torch.uint8, pin_memory=True)
-    icgs.colorize_host(gs, gc, host_t, L, precision=args.precision, coeffs_out=host_c, status_out=host_s)
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        icgs.colorize_host(gs, gc, host_t, L, precision=args.precision, coeffs_out=host_c, status_out=host_s)
-    e1.record(stream)
-    barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    t = torch.tensor([e2e_ms], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    e2e_max = float(t.item())
-
-    # ---- the plain FP32 path on the same inputs ----
-    plain = None
-    if args.precision == "mixed":
-        n_plain = max(3, min(args.steps, 5))
-        icgs.colorize(gs, gc, targets, L, precision="plain")
-        barrier()
-        p0 = torch.cuda.Event(enable_timing=True)
-        p1 = torch.cuda.Event(enable_timing=True)
-        p0.record(stream)
-        for _ in range(n_plain):
-            icgs.colorize(gs, gc, targets, L, precision="plain")
-        p1.record(stream)
-        barrier()
-        plain_ms = p0.elapsed_time(p1) / n_plain
-        plain = {"ms_per_scene": plain_ms, "mixed_speedup": plain_ms / (elapsed_max / args.steps)}
-
-    # ---- the adjoint (the differentiation workload: dL/dt and dL/d(opacity) for L = sum r c^2) ----
-    adjoint = None
-    if args.workload == "relight":
-        c, st, chol = icgs.colorize(gs, gc, targets, L, precision=args.precision)
-        r = torch.randn(c.shape, generator=torch.Generator(device=dev).manual_seed(5005), device=dev)
-        gcoef = 2.0 * r * c
-        icgs.colorize_backward(gs, gc, targets, L, c, chol, gcoef, precision=args.precision)
-        n_adj = max(3, min(args.steps, 5))
-        barrier()
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        for _ in range(n_adj):
-            icgs.colorize_backward(gs, gc, targets, L, c, chol, gcoef, precision=args.precision)
-        a1.record(stream)
-        barrier()
-        adjoint = {"ms_per_scene": a0.elapsed_time(a1) / n_adj, "outputs": f"dL/dt [{cams.n},{cams.height},{cams.width},{K}] and dL/do [{scene.n}]",
-                   "launches": icgs.last_stats()["launches"]}
-
-    # ---- iterative refinement (Alg. 1 lines 7-10): render, accumulate the residual, update ----
-    refine = None
-    if args.workload == "relight":
-        c, st, chol = icgs.colorize(gs, gc, targets, L, precision=args.precision)
-        c_ref = c.clone()
-        icgs.colorize_refine(gs, gc, targets, L, c_ref, chol, 1, precision=args.precision)  # warm-up
-        n_ref, steps_per_call = 3, 2
-        barrier()
-        r0 = torch.cuda.Event(enable_timing=True)
-        r1 = torch.cuda.Event(enable_timing=True)
-        r0.record(stream)
-        for _ in range(n_ref):
-            c_ref.copy_(c)
-            icgs.colorize_refine(gs, gc, targets, L, c_ref, chol, steps_per_call, precision=args.precision)
-        r1.record(stream)
-        barrier()
-        refine = {"ms_per_step": r0.elapsed_time(r1) / (n_ref * steps_per_call),
-                  "step": "render + residual accumulate + fold of b + update, all cameras",
-                  "launches_per_call": icgs.last_stats()["launches"]}
-
+    with_cpu = world == 1 and not args.no_cpu_baseline
+    head = measure(args.workload, args, world, dev, icgs, True, with_cpu)
+    extras = {}
+    for name in [x for x in args.extras.split(",") if x and x != args.workload]:
+        extras[name] = measure(name, args, world, dev, icgs, name == "relight", with_cpu)
     if rank != 0:
         return
-    pk = peaks()
-    ms_scene = elapsed_max / (args.steps * world)
-    blend_ms = stage_ms.get("blend", float("nan"))
-    pairs = stats["contrib_pairs"]
-    inst = stats["instances"]
-    # algorithmic work of the blend-accumulate kernel per launch (one launch per scene here):
-    # per contributing pair: weight (~15 FP32 ops + 1 exp) and accumulation 2(1+K)
-    flops = pairs * (15 + 2 * (1 + K))
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6
-    achieved_tflops = flops / (blend_ms * 1e-3) / 1e12
-    acc_rows = scene.n * (1 if L == 0 else cams.n)
-    bytes_alg = target_bytes + inst * (8 + 32) + acc_rows * (1 + K) * 4 * 2
-    tc = args.precision == "mixed" and K >= 16 and targets.dtype != torch.float32
-    if tc:
-        kname = f"k_blend_accumulate_tc<{16 if K <= 16 else 32 if K <= 32 else 64}>"
-    elif K <= 3:
-        kname = f"k_blend_accumulate2<{K}>"  # two pixels per thread
-    else:
-        kname = f"k_blend_accumulate<{min(K, 16)}>"
-    roof = {"kernel": kname, "bound": "alu", "achieved": achieved_tflops,
-            "peak": fp32_peak / 1e12, "unit": "TFLOP/s", "frac": achieved_tflops / (fp32_peak / 1e12),
-            "traffic": measured_traffic(args.workload, "tensor-core" if tc else "cuda-core",
-                                        W.make_cameras({"relight": "relight", "features": "features"}.get(
-                                            args.workload, "segmentation")).n, cams.n),
-            "traffic_unit": "bytes per scene (DRAM read + write, ncu)",
-            "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {pk['sm_max_mhz']:.0f} MHz",
-            "hbm_view": {"algorithmic_bytes": bytes_alg, "achieved_gbs": bytes_alg / (blend_ms * 1e-3) / 1e9,
-                         "peak_gbs": pk["hbm_gbs"], "frac": bytes_alg / (blend_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
-                         "peak_source": pk["source"]}}
-    cpu = None
-    if world == 1 and not args.no_cpu_baseline and args.workload == "relight":
-        cores = os.cpu_count() or 1
-        n_sample = args.cpu_sample_cams or min(cores, 16)
-
-        def targets_host(idx):
-            return targets[torch.as_tensor(idx, device=dev)].double().cpu().numpy()
-
-        ms_cpu, opairs, idx, wall = oracle_sample_ms_per_scene(scene, cams, targets_host, n_sample, cores)
-        # the GPU's contributing-pair count on the same camera sample, for the pair-count cross-check
-        sub = icgs.Cameras.from_workload(cams.subset(idx))
-        icgs.colorize(gs, sub, targets[torch.as_tensor(idx, device=dev)].contiguous(), L, precision=args.precision)
-        gpairs = icgs.last_stats()["contrib_pairs"]
-        cpu = {"value": ms_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{n_sample} of {cams.n} cameras, all Gaussians and pixels, walk x {cams.n}/{cores} cores "
-                         f"+ fold/solve x {cams.n}/{n_sample}; {wall:.1f} s of CPU wall time",
-               "pairs_oracle_sample": opairs, "pairs_gpu_sample": gpairs}
+    launches = head["gpu_launches"]
     line = {
-        "metric": METRIC, "value": ms_scene, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": elapsed_max / args.steps, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if targets.dtype == torch.float32 else ("f16" if tc else "f32"), "data": "synthetic",
-        "config": workload_config(args.workload, scene.n, cams.n, cams.width, cams.height, L, K,
-                                  str(targets.dtype).replace("torch.", ""), args.precision, world, target_bytes),
-        "roofline": roof,
-        "e2e": {"value": e2e_max / (args.steps * world), "unit": UNIT, "h2d_bytes_per_step": target_bytes,
-                "d2h_bytes_per_step": scene.n * B * K * 4 + scene.n, "call": "icgs_colorize_host"},
-        "cpu_baseline": cpu,
-        "clocks": clocks,
-        "gpu_launches": stats["launches"] * args.steps,
-        "blend_contribs_per_s": pairs / (blend_ms * 1e-3),
-        "stage_ms": stage_ms,
-        "instances": inst, "contrib_pairs": pairs, "fp64_gaussians": stats["fp64"], "refolded_gaussians": stats["refold"],
-        "plain_fp32": plain,
-        "adjoint": adjoint,
-        "refine": refine,
+        "metric": METRIC, "value": head["ms_per_scene"] / world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_scene"], "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": head["dtype"], "dtype_detail": head["dtype_detail"], "data": "synthetic",
+        "config": head["config"], "roofline": head["roofline"], "e2e": head["e2e"],
+        "cpu_baseline": head.get("cpu_baseline"), "clocks": head["clocks"], "gpu_launches": launches,
+        "walk": head["walk"], "blend_contribs_per_s": head["blend_contribs_per_s"], "stage_ms": head["stage_ms"],
+        "instances": head["instances"], "contrib_pairs": head["contrib_pairs"],
+        "fp64_gaussians": head["fp64_gaussians"], "refolded_gaussians": head["refolded_gaussians"],
+        "plain_fp32": head.get("plain_fp32"),
+        "extra_workloads": extras,
     }
     print(json.dumps(line), flush=True)
 
@@ -481,7 +587,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
+    if world > 1 and args.impl != "reference":
         import torch
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         torch.cuda.set_device(local_rank)
@@ -492,7 +598,7 @@ def main():
         else:
             run_icgs(args, rank, world, local_rank)
     finally:
-        if world > 1:
+        if world > 1 and args.impl != "reference":
             import torch
             torch.distributed.destroy_process_group()
 
