@@ -115,6 +115,8 @@ def parse(argv=None):
     ap.add_argument("--ref-cams", type=int, default=0,
                     help="cameras in each step's oracle sample of the reference arm (0: one per core, up to 16)")
     ap.add_argument("--cams", type=int, default=0, help="profiling only: use the first N cameras of each rig")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="profiling only: the targets, W warm-up and K timed colorize calls of --workload, nothing else")
     return ap.parse_args(argv)
 
 
@@ -550,6 +552,22 @@ def measure(name, args, world, dev, icgs, with_e2e, with_cpu):
     return rec
 
 
+def run_profile_step(args, dev, icgs):
+    """Only the colorize calls of one workload (for launch lists and kernel captures)."""
+    import torch
+    sp = SPECS[args.workload]
+    scene, cams = make_workload(args.workload, args.cams)
+    gs = icgs.Scene.from_workload(scene, dev)
+    gc = icgs.Cameras.from_workload(cams)
+    with torch.no_grad():
+        targets = make_targets(args.workload, scene, cams, gs, gc, dev, icgs)
+    for _ in range(args.warmup + args.steps):
+        icgs.colorize(gs, gc, targets, sp["L"], precision=args.precision)
+    torch.cuda.synchronize(dev)
+    print(json.dumps({"profile_step": args.workload, "cams": cams.n, "calls": args.warmup + args.steps,
+                      "stats": icgs.last_stats()}), flush=True)
+
+
 def run_icgs(args, rank, world, local_rank):
     import torch
 
@@ -559,6 +577,9 @@ def run_icgs(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
+    if args.profile_step:
+        run_profile_step(args, dev, icgs)
+        return
     with_cpu = world == 1 and not args.no_cpu_baseline
     head = measure(args.workload, args, world, dev, icgs, True, with_cpu)
     extras = {}

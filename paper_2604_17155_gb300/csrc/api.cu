@@ -362,6 +362,16 @@ icgs_status lambda_of(const icgs_options* opt, int L, float* lam) {
 
 void icgs::note_launches(int count) { g_launches += count; }
 
+size_t icgs::colorize_workspace_bytes(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
+                                      const icgs_options* opt) {
+  if (!targets || !opt) return 0;
+  Problem p;
+  if (setup(scene, cams, targets->channels, opt->sh_degree, opt->precision, opt->cond_tau, opt->refold_tau, opt->cam_batch,
+            opt->instance_capacity, p) != ICGS_OK)
+    return 0;
+  return carve(nullptr, p, kNeedAccumulate).total;
+}
+
 void icgs::set_error_message(const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);

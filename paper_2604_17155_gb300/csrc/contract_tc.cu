@@ -256,13 +256,15 @@ __global__ void __launch_bounds__(256, MG == 64 ? (KT <= 32 ? 4 : 3) : 2) k_blen
   uint8_t* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
   uint8_t* A_s = base;                                 // MG x 256 (32 or 64 KB)
   uint8_t* B_s = base + MG * kKPix * 2;                // NB x 256
-  float4* s_geo = reinterpret_cast<float4*>(B_s + NB * kKPix * 2);
-  float4* s_aux = s_geo + MG;
-  float2* s_half = reinterpret_cast<float2*>(s_aux + MG);
-  uint32_t* s_id = reinterpret_cast<uint32_t*>(s_half + MG);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(s_id + MG);
+  // staging of two batches: batch b in buffer b & 1, the next one loaded while b's MMAs run
+  float4* s_geo2 = reinterpret_cast<float4*>(B_s + NB * kKPix * 2);  // [2][MG]
+  float4* s_aux2 = s_geo2 + 2 * MG;                                  // [2][MG]
+  float2* s_half2 = reinterpret_cast<float2*>(s_aux2 + 2 * MG);      // [2][MG]
+  uint32_t* s_id2 = reinterpret_cast<uint32_t*>(s_half2 + 2 * MG);   // [2][MG]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(s_id2 + 2 * MG);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
   uint32_t* s_tmax = tmem_slot + 1;  // [8]
+  uint32_t* s_timeout = s_tmax + 8;  // set by a thread whose wait gave up
 
   const TileCtx c = tile_ctx(tile_off, capacity, tiles, tiles_x, width, height);
   if (c.len == 0) return;  // uniform: nothing binned to this tile
@@ -322,30 +324,37 @@ __global__ void __launch_bounds__(256, MG == 64 ? (KT <= 32 ? 4 : 3) : 2) k_blen
     for (int k = KT; k < NB; ++k) *reinterpret_cast<uint16_t*>(B_s + kmajor_sw128(k, p, NB)) = (uint16_t)0x3C00u;
   }
   const float v_scale_inv = ldexpf(1.0f, -kWScaleExp);
-  if (threadIdx.x == 0) mbar_init(mbar, 1);
+  const ProjRec* rec_cam = rec + (int64_t)c.j * n;
+  if (threadIdx.x == 0) {
+    mbar_init(mbar, 1);
+    *s_timeout = 0u;
+  }
   if (warp == 0) {
     tmem_alloc(tmem_slot, tmem_cols<NB>());
     tmem_relinquish();
   }
+  // the first batch's staging, and W cleared
+  load_batch(reinterpret_cast<const unsigned long long*>(entries), c.b, (int)min((uint32_t)MG, c.len), rec_cam, n,
+             c.ox, c.oy, s_geo2, s_aux2, s_half2, s_id2);
+  for (int i = threadIdx.x; i < MG * kKPix * 2 / 16; i += 256) reinterpret_cast<uint4*>(A_s)[i] = make_uint4(0, 0, 0, 0);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t a_addr = smem_u32(A_s), b_addr = smem_u32(B_s);
   constexpr uint32_t kIdesc = idesc_f16(MG, NB, false);
-  const ProjRec* rec_cam = rec + (int64_t)c.j * n;
   float* acc_cam = acc + (int64_t)c.j * acc_cam_stride;
   float T = 1.0f;
   bool done = !c.inside;
   uint32_t npairs = 0, phase = 0;
-  bool timed_out = false;
-  for (uint32_t start = 0; start < c.len; start += MG) {
+  // Two CTA barriers per batch: one before the MMA issue (W written), one at the end (the next
+  // batch's staging loaded, W cleared, the done count and the timeout flag published).
+  for (uint32_t start = 0, buf = 0; start < c.len; start += MG, buf ^= 1u) {
     const int nb = (int)min((uint32_t)MG, c.len - start);
-    load_batch(reinterpret_cast<const unsigned long long*>(entries), c.b + start, nb, rec_cam, n, c.ox, c.oy, s_geo, s_aux,
-               s_half, s_id);
-    // the previous batch's MMAs have completed: clear W (16-byte stores), then write its nonzeros
-    for (int i = threadIdx.x; i < MG * kKPix * 2 / 16; i += 256) reinterpret_cast<uint4*>(A_s)[i] = make_uint4(0, 0, 0, 0);
-    __syncthreads();
+    const float4* s_geo = s_geo2 + buf * MG;
+    const float4* s_aux = s_aux2 + buf * MG;
+    const float2* s_half = s_half2 + buf * MG;
+    const uint32_t* s_id = s_id2 + buf * MG;
     if (!__all_sync(0xFFFFFFFFu, done)) {
 #pragma unroll
       for (int q = 0; q < MG / 32; ++q) {
@@ -367,6 +376,13 @@ __global__ void __launch_bounds__(256, MG == 64 ? (KT <= 32 ? 4 : 3) : 2) k_blen
     tc_fence_before();
     __syncthreads();
     if (threadIdx.x == 0 && issue_mma) issue_batch<NB, MG>(a_addr, b_addr, tmem, kIdesc, mbar);
+    // while the MMAs run: stage the next batch in the other buffer (its readers finished at the
+    // last end-of-batch barrier)
+    const uint32_t next = start + MG;
+    if (next < c.len)
+      load_batch(reinterpret_cast<const unsigned long long*>(entries), c.b + next, (int)min((uint32_t)MG, c.len - next),
+                 rec_cam, n, c.ox, c.oy, s_geo2 + (buf ^ 1u) * MG, s_aux2 + (buf ^ 1u) * MG,
+                 s_half2 + (buf ^ 1u) * MG, s_id2 + (buf ^ 1u) * MG);
     const bool ok = mbar_wait_bounded(mbar, phase, wait_limit_ns);
     phase ^= 1u;
     tc_fence_after();
@@ -414,14 +430,20 @@ __global__ void __launch_bounds__(256, MG == 64 ? (KT <= 32 ? 4 : 3) : 2) k_blen
           atomicAdd(reinterpret_cast<float4*>(dst + 16 * kCh), make_float4(carry, 0.0f, 0.0f, 0.0f));
       }
     }
-    if (!ok) timed_out = true;
+    if (!ok) {
+      *s_timeout = 1u;
+    } else if (next < c.len) {
+      // this batch's MMAs have completed: clear W for the next batch (16-byte stores)
+      for (int i = threadIdx.x; i < MG * kKPix * 2 / 16; i += 256) reinterpret_cast<uint4*>(A_s)[i] = make_uint4(0, 0, 0, 0);
+    }
     tc_fence_before();
-    if (__syncthreads_or(timed_out)) {
-      if ((threadIdx.x & 31) == 0) atomicOr(&status->flags, kFlagTimeout);
+    const int n_done = __syncthreads_count(done);
+    if (*s_timeout) {
+      if (threadIdx.x == 0) atomicOr(&status->flags, kFlagTimeout);
       mbar_wait_bounded(mbar, phase ^ 1u, wait_limit_ns);  // give the outstanding MMAs a last chance to finish
       break;
     }
-    if (__syncthreads_and(done)) break;
+    if (n_done == (int)blockDim.x) break;
   }
   const uint32_t warp_sum = __reduce_add_sync(0xFFFFFFFFu, npairs);
   if (lane == 0 && warp_sum) atomicAdd((unsigned long long*)&status->contrib_pairs, (unsigned long long)warp_sum);
@@ -439,7 +461,7 @@ constexpr size_t selftest_smem() {
 }
 template <int KT, int MG>
 constexpr size_t tc_smem() {
-  return 1024 + (size_t)MG * kKPix * 2 + (size_t)tc_cols<KT, MG>() * kKPix * 2 + (size_t)MG * (16 + 16 + 8 + 4) + 64;
+  return 1024 + (size_t)MG * kKPix * 2 + (size_t)tc_cols<KT, MG>() * kKPix * 2 + 2 * (size_t)MG * (16 + 16 + 8 + 4) + 64;
 }
 
 // Diagnostic settings of this host thread (icgs_debug_tc_wait): the walk's wait limit and whether

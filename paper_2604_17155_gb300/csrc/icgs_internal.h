@@ -6,6 +6,8 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/icgs.h"
+
 namespace icgs {
 
 constexpr int kTile = 16;            // screen tiles are 16x16 pixels; one CTA of 256 threads each
@@ -105,6 +107,10 @@ struct Problem {
 
 // Kernel launches of the current call on this host thread (for the benchmark's launch count).
 void note_launches(int count);
+
+// Bytes of workspace icgs_colorize itself needs (icgs_workspace_size also covers the adjoint).
+size_t colorize_workspace_bytes(const icgs_scene* scene, const icgs_cameras* cams, const icgs_targets* targets,
+                                const icgs_options* opt);
 
 // Replaces the message icgs_last_error() returns on this host thread (printf-style).
 void set_error_message(const char* fmt, ...);

@@ -80,10 +80,9 @@ icgs_status icgs_colorize_noalloc(const icgs_scene* scene, const icgs_cameras* c
   if (st != ICGS_OK) return st;
   icgs_options o = *opt;
   if (o.instance_capacity <= 0) {
-    // give the (Gaussian, tile) instance buffers whatever the fixed regions leave free; the size
-    // query covers colorize and its adjoint, so it bounds what icgs_colorize itself will take
+    // give the (Gaussian, tile) instance buffers whatever colorize's fixed regions leave free
     o.instance_capacity = 1;
-    const size_t fixed = icgs_workspace_size(scene, cams, targets, &o);
+    const size_t fixed = icgs::colorize_workspace_bytes(scene, cams, targets, &o);
     if (fixed == 0) return icgs_colorize(scene, cams, targets, &o, scratch, kScratchBytes, coeffs_out, status_out,
                                          chol_out, stream);  // invalid arguments: let colorize report them
     if (fixed + 2 * 256 + 16 > kScratchBytes) {

@@ -2,12 +2,13 @@
 //
 // After binning, each tile owns a contiguous slot range of 64-bit keys (float32 depth bits << 32 |
 // Gaussian index); the keys are unique, so sorting them ascending gives depth order with ties in
-// index order. For the tensor-core walk every list is sorted here, one CTA per tile (k_sort_tiles).
-// The CUDA-core walks sort lists of up to kWalkSortCap keys themselves; the longer ones are queued
-// (k_queue_tiles) and sorted by a persistent kernel (k_sort_queued). Up to kSortCap keys are sorted
-// with a bitonic network over keys held in registers (blocked, 8 or 16 a thread, from 1025 keys);
-// longer lists as runs of kSortCap keys followed by merge-path merges between the slot range and a
-// scratch range of the same place.
+// index order. For the tensor-core walk every list is sorted here, one CTA per tile (k_sort_tiles):
+// up to 1024 keys with the walks' register/shuffle bitonic network, 1025..kSortCap keys as sorted
+// runs of 1024 merged in shared memory (no padding to a power of two). The CUDA-core walks sort
+// lists of up to kWalkSortCap keys themselves; the longer ones are queued (k_queue_tiles) and sorted
+// by a persistent kernel (k_sort_queued): up to kSortCap keys with a bitonic network over keys held
+// in registers (blocked, 8 or 16 a thread, from 1025 keys), longer lists as runs of kSortCap keys
+// followed by merge-path merges between the slot range and a scratch range of the same place.
 #include <cuda_runtime.h>
 
 #include "icgs_internal.h"
@@ -115,13 +116,55 @@ __global__ void __launch_bounds__(kSortThreads) k_queue_tiles(const uint32_t* __
   if (want) queue[base + __popc(ballot & ((1u << lane) - 1u))] = (uint32_t)t;
 }
 
+// Number of elements of A among the first d outputs of merging A and B (keys are unique).
+__device__ __forceinline__ int merge_path(const unsigned long long* A, int na, const unsigned long long* B,
+                                          int nb, int d);
+
+// Sorts len (1024 < len <= kSortCap) keys from g into dst without padding the list to a power of
+// two: runs of 1024 keys are sorted in shared memory by the register/shuffle network of the walks,
+// then merged pairwise (merge path: every thread produces an equal share of each merge's outputs)
+// between the two shared buffers s0 and s1 (kSortCap keys each).
+__device__ __forceinline__ void sort_runs_merge(const unsigned long long* g, int len, unsigned long long* s0,
+                                                unsigned long long* s1, unsigned long long* __restrict__ dst) {
+  constexpr int kRun = 1024;
+  for (int r0 = 0; r0 < len; r0 += kRun) walk::sort_keys_block<4>(g + r0, (uint32_t)min(kRun, len - r0), s0 + r0);
+  unsigned long long* src = s0;
+  unsigned long long* out = s1;
+  for (int width = kRun; width < len; width <<= 1) {
+    for (int lo = 0; lo < len; lo += 2 * width) {
+      const int na = min(width, len - lo);
+      const int nb = max(0, min(width, len - lo - width));
+      const unsigned long long* A = src + lo;
+      const unsigned long long* Bp = src + lo + na;
+      const int tot = na + nb;
+      const int per = (tot + kSortThreads - 1) / kSortThreads;
+      const int d0 = min(tot, (int)threadIdx.x * per), d1 = min(tot, d0 + per);
+      if (d0 < d1) {
+        int ia = merge_path(A, na, Bp, nb, d0);
+        int ib = d0 - ia;
+        for (int d = d0; d < d1; ++d) {
+          const bool takeA = ib >= nb || (ia < na && A[ia] < Bp[ib]);
+          out[lo + d] = takeA ? A[ia++] : Bp[ib++];
+        }
+      }
+    }
+    __syncthreads();
+    unsigned long long* t = src;
+    src = out;
+    out = t;
+  }
+  for (int k = threadIdx.x; k < len; k += kSortThreads) dst[k] = src[k];
+  __syncthreads();
+}
+
 // Every tile list: sorted in place when it has at most kSortCap keys (one CTA per tile), queued
-// for k_sort_queued when longer.
+// for k_sort_queued when longer. Up to 1024 keys: the walks' shared-memory network; longer:
+// sorted runs merged in shared memory.
 __global__ void __launch_bounds__(kSortThreads, 3) k_sort_tiles(const uint32_t* __restrict__ tile_off,
                                                              unsigned long long* __restrict__ entries,
                                                              uint32_t capacity, uint32_t* __restrict__ queue,
                                                              DevStatus* status) {
-  __shared__ unsigned long long s[kSortCap + kSortCap / 16];
+  extern __shared__ unsigned long long s_dyn[];  // 2 x kSortCap keys
   uint32_t b, e;
   tile_range(tile_off, blockIdx.x, capacity, b, e);
   const int n = (int)(e - b);
@@ -130,7 +173,12 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_tiles(const uint32_t* 
     if (threadIdx.x == 0) queue[atomicAdd(&status->big_tiles, 1u)] = blockIdx.x;
     return;
   }
-  sort_list(entries + b, n, s, entries + b);
+  if (n > 1024) {
+    sort_runs_merge(entries + b, n, s_dyn, s_dyn + kSortCap, entries + b);
+  } else {
+    walk::sort_keys_block<4>(entries + b, (uint32_t)n, s_dyn);
+    for (int k = threadIdx.x; k < n; k += kSortThreads) entries[b + k] = s_dyn[k];
+  }
 }
 
 // Number of elements of A among the first d outputs of merging A and B (keys are unique).
@@ -204,9 +252,12 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_queued(const uint32_t*
 void launch_tile_sort(const Problem& p, int cb, bool sort_all, const Workspace& ws, cudaStream_t s) {
   const int ntiles = cb * p.tiles;
   cudaMemsetAsync(&ws.status->big_tiles, 0, sizeof(uint32_t), s);
-  if (sort_all)
-    k_sort_tiles<<<ntiles, kSortThreads, 0, s>>>(ws.tile_off, reinterpret_cast<unsigned long long*>(ws.entries),
-                                                 p.capacity, ws.big_list, ws.status);
+  if (sort_all) {
+    const int smem = 2 * kSortCap * (int)sizeof(unsigned long long);
+    cudaFuncSetAttribute(k_sort_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_sort_tiles<<<ntiles, kSortThreads, smem, s>>>(ws.tile_off, reinterpret_cast<unsigned long long*>(ws.entries),
+                                                    p.capacity, ws.big_list, ws.status);
+  }
   else
     k_queue_tiles<<<(ntiles + kSortThreads - 1) / kSortThreads, kSortThreads, 0, s>>>(
         ws.tile_off, ntiles, p.capacity, walk::kWalkSortCap, ws.big_list, ws.status);

@@ -63,6 +63,36 @@ def test_noalloc_matches_colorize_on_two_calls(icgs, L):
         assert err <= TOL_FP32
 
 
+def test_noalloc_fits_a_problem_only_colorize_itself_fits(icgs):
+    """The scratch is sized against colorize's own workspace, not the larger colorize + adjoint one
+    icgs_workspace_size reports: a problem whose combined workspace exceeds the scratch by the
+    adjoint's regions still runs, and matches icgs_colorize."""
+    import ctypes
+    lib = icgs.load()
+    cams = W.hemisphere_cameras(8, 4.0, 64, 48, 50.0)
+    gc = icgs.Cameras.from_workload(cams)
+    scratch = lib.icgs_noalloc_scratch_bytes()
+    n_pick, both = None, 0
+    tg = icgs._Targets(icgs.F32, 3, 16)
+    o, _keep = icgs._options(3, None, "mixed", 0.0, 0, 1, 0.0)
+    for n in range(2000, 200000, 1000):  # the smallest scene whose colorize + adjoint workspace overflows
+        sz = icgs._Scene(n, 16, 16, 16, 16)  # sizes only: the pointers are never dereferenced
+        both = lib.icgs_workspace_size(ctypes.byref(sz), ctypes.byref(gc._struct()), ctypes.byref(tg), ctypes.byref(o))
+        if both > scratch:
+            n_pick = n
+            break
+    assert n_pick is not None
+    sc = W.cluster_scene(n_pick, 94, radius=1.5, log_scale_mean=-3.6, log_scale_std=0.4)
+    gs = icgs.Scene.from_workload(sc, "cuda")
+    t = O.render(sc, cams, W.sh_coefficients(sc.n, 3, 3, seed=95), 3).astype(np.float32)
+    tt = torch.tensor(t, device="cuda")
+    c_ref, s_ref, _ = icgs.colorize(gs, gc, tt, 3)
+    c, s, _ = icgs.colorize_noalloc(gs, gc, tt, 3)
+    print(f"noalloc near the limit: {n_pick} Gaussians, colorize + adjoint workspace {both} > scratch {scratch}")
+    assert torch.equal(s, s_ref)
+    assert _compare(c, c_ref, s_ref) <= TOL_FP32
+
+
 def test_noalloc_rejects_problems_beyond_its_scratch(icgs):
     # 2,000,000 Gaussians x 8 cameras need far more than the built-in scratch for their
     # per-(camera, Gaussian) records alone; the call must refuse before touching the GPU
