@@ -1093,6 +1093,39 @@ icgs_status icgs_selftest_tc_rows(const void* A, int32_t M, const void* B, int32
 
 void icgs_debug_tc_wait(int64_t limit_ns, int32_t issue_mma) { set_tc_wait_diagnostic(limit_ns, issue_mma != 0); }
 
+size_t icgs_sort_workspace_size(int32_t ntiles, int64_t nkeys) {
+  if (ntiles < 0 || nkeys < 0) return 0;
+  return align256(sizeof(DevStatus)) + align256(sizeof(uint32_t) * (size_t)ntiles) +
+         align256(sizeof(uint64_t) * (size_t)nkeys);
+}
+
+icgs_status icgs_sort_tile_lists(const uint32_t* tile_off, uint64_t* keys, int32_t ntiles, int64_t nkeys, int32_t all,
+                                 void* workspace, size_t workspace_bytes, void* stream) {
+  g_err[0] = '\0';
+  if (ntiles < 0 || nkeys < 0) return fail(ICGS_ERR_INVALID_ARG, "ntiles = %d and nkeys = %lld must be >= 0", ntiles, (long long)nkeys);
+  if (nkeys > (int64_t)kMaxCapacity) return fail(ICGS_ERR_INVALID_ARG, "nkeys = %lld exceeds %u", (long long)nkeys, kMaxCapacity);
+  if (!tile_off || !workspace || (nkeys > 0 && !keys)) return fail(ICGS_ERR_INVALID_ARG, "tile_off, keys and workspace are required");
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(ICGS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  const size_t need = icgs_sort_workspace_size(ntiles, nkeys);
+  if (workspace_bytes < need)
+    return fail(ICGS_ERR_WORKSPACE_TOO_SMALL, "workspace holds %zu bytes, the sort needs %zu", workspace_bytes, need);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(workspace);
+  Workspace ws;
+  ws.status = reinterpret_cast<DevStatus*>(base);
+  ws.big_list = reinterpret_cast<uint32_t*>(base + align256(sizeof(DevStatus)));
+  ws.entries_tmp = reinterpret_cast<uint64_t*>(base + align256(sizeof(DevStatus)) + align256(sizeof(uint32_t) * (size_t)ntiles));
+  ws.tile_off = const_cast<uint32_t*>(tile_off);
+  ws.entries = keys;
+  Problem p;
+  p.tiles = ntiles;
+  p.capacity = (uint32_t)nkeys;
+  ICGS_TRY_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(DevStatus), s));
+  g_launches = 0;
+  if (ntiles > 0) launch_tile_sort(p, 1, all != 0, ws, s);
+  return finish(ws, s);
+}
+
 icgs_status icgs_selftest_tc(const void* A, const void* B, int32_t N, int32_t bf16, float* D, void* workspace,
                              void* stream) {
   return icgs_selftest_tc_rows(A, 128, B, N, bf16, D, nullptr, workspace, stream);

@@ -1,9 +1,9 @@
 // contract_tc.cu -- the blend-accumulate walk (Eq. 4-6) with its per-tile contraction on the
 // 5th-generation tensor cores (tcgen05), for 16-bit targets with 16..64 channels.
 //
-// Per tile and batch of G = 128 Gaussians (the MMA's M; 64 for up to 32 channels, which halves the
-// weight operand so that more CTAs fit on an SM), the S terms of Eq. 6 summed over the tile's
-// 256 pixels form a dense product
+// Per tile and batch of MG = 64 Gaussians (the MMA's M; 64 rather than 128 halves the weight
+// operand, so that 3-4 CTAs fit on an SM), the S terms of Eq. 6 summed over the tile's 256 pixels
+// form a dense product
 //     D[g][n] = sum_p W[g][p] * B[n][p],   W[g][p] = alpha T of Gaussian g at pixel p (Eq. 4),
 // with B's rows 0..KT-1 the tile's target channels and the rows after them all ones, so that the same
 // product also yields V = sum_p W[g][p] (Eq. 5). The threads evaluate W exactly like the CUDA-core
@@ -12,9 +12,11 @@
 // powers of two -- W by 2^14, the targets so that the tile's largest magnitude lands in
 // [2^14, 2^15) -- which makes every BF16 target exact in FP16, keeps small weights out of FP16's
 // subnormal range, and is undone exactly in the epilogue. One thread issues 16
-// tcgen05.mma (kind::f16, M=G, N=KT+8, K=16, FP32 accumulation in TMEM) and commits them to an
-// mbarrier; warps 0-3 then read D back with tcgen05.ld (one Gaussian per thread) and add
-// (V, S_0..S_{KT-1}) to the accumulator with float4 atomics -- one atomic group per (Gaussian, tile).
+// tcgen05.mma (kind::f16, M=MG, N=KT+8, K=16, FP32 accumulation in TMEM) and commits them to an
+// mbarrier; while they run, the next batch's Gaussians are staged in a second buffer; the warps then
+// read D back with tcgen05.ld (one Gaussian per thread, the chunks split between warps w and w+4)
+// and add (V, S_0..S_{KT-1}) to the accumulator with float4 atomics -- one atomic group per
+// (Gaussian, tile). A batch costs two CTA barriers.
 //
 // Every wait on the mbarrier is bounded in time (1 s by %globaltimer): past the limit the kernel
 // sets kFlagTimeout in the status block (reported as ICGS_ERR_DEVICE_TIMEOUT), waits once more
@@ -35,7 +37,7 @@ namespace {
 
 using namespace walk;
 
-constexpr int kG = 128;                 // Gaussians per batch (MMA M)
+constexpr int kG = 128;                 // rows of the self-test MMA (the walk uses MG = 64)
 constexpr int kKPix = 256;              // pixels per tile (MMA K in total, 16 instructions of 16)
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // bounded mbarrier waits give up after 1 s
 constexpr uint32_t kTmemCols = 128;     // TMEM columns of the self-test (N <= 80)

@@ -15,7 +15,7 @@ constexpr int kTilePixels = kTile * kTile;
 constexpr int kMaxSH = 16;           // (L+1)^2 for L = 3
 // A payload CTA stages at least one Gaussian's (L+1)^2 x K coefficients in 48 KB of shared memory.
 constexpr int kMaxPayloadRow = 12287;
-constexpr int kSortCap = 4096;       // tile lists up to this length are sorted in shared memory
+constexpr int kSortCap = 4096;       // tile lists up to this length are sorted in shared memory at once
 constexpr uint32_t kMaxCapacity = 0x7FFFFFF0u;
 constexpr uint8_t kGaussOk = 0, kGaussUnseen = 1, kGaussFp64 = 2;  // icgs.h ICGS_GAUSSIAN_*
 
@@ -27,7 +27,8 @@ __host__ __device__ constexpr int solve_record_floats(int B) { return 3 * (B * (
 // Device status block at the start of every workspace; read back at the end of each call.
 struct DevStatus {
   uint32_t flags;             // kFlag* bits
-  uint32_t big_tiles;         // tiles longer than kSortCap in the current pass
+  uint32_t big_tiles;         // tiles queued for the long-list sort in the current pass
+  uint32_t sort_next;         // next tile of the persistent tile sort (work counter)
   uint64_t instances_needed;  // max over passes of (Gaussian, tile) instances
   uint64_t instances_total;   // sum over passes
   uint64_t contrib_pairs;     // pixel-Gaussian pairs with nonzero weight (sum over passes)

@@ -2,96 +2,39 @@
 //
 // After binning, each tile owns a contiguous slot range of 64-bit keys (float32 depth bits << 32 |
 // Gaussian index); the keys are unique, so sorting them ascending gives depth order with ties in
-// index order. For the tensor-core walk every list is sorted here, one CTA per tile (k_sort_tiles):
-// up to 1024 keys with the walks' register/shuffle bitonic network, 1025..kSortCap keys as sorted
-// runs of 1024 merged in shared memory (no padding to a power of two). The CUDA-core walks sort
-// lists of up to kWalkSortCap keys themselves; the longer ones are queued (k_queue_tiles) and sorted
-// by a persistent kernel (k_sort_queued): up to kSortCap keys with a bitonic network over keys held
-// in registers (blocked, 8 or 16 a thread, from 1025 keys), longer lists as runs of kSortCap keys
-// followed by merge-path merges between the slot range and a scratch range of the same place.
+// index order. Every sort here is the stable LSD radix sort of radix.cuh, in shared memory.
+// For the tensor-core walk every list is sorted here: lists of up to kWarpSortCap keys by a
+// persistent kernel in which each warp sorts one tile at a time (k_sort_tiles, no CTA barrier),
+// longer lists queued. The CUDA-core walks sort lists of up to kWalkSortCap keys themselves; the
+// longer ones are queued (k_queue_tiles). Queued lists go to a persistent kernel with one CTA per
+// list (k_sort_queued): up to kSortCap keys by the block radix sort at once, longer lists as sorted
+// runs of kSortCap keys followed by merge-path merges between the slot range and a scratch range
+// of the same place.
 #include <cuda_runtime.h>
 
 #include "icgs_internal.h"
+#include "radix.cuh"
 #include "walk.cuh"
 
 namespace icgs {
 
 namespace {
 
-constexpr int kSortThreads = 256;
-constexpr int kSortGrid = 152 * 6;  // CTAs of the queued sort (a grid-stride loop; three per SM are resident)
+constexpr int kSortThreads = radix::kThreads;  // CTA of the queued sort
+constexpr int kWarpSortCap = 1024;             // longest list a warp sorts alone
+constexpr int kWarpSortWarps = 4;              // warps per CTA of k_sort_tiles
+constexpr int kWarpSortChunk = 4;              // tiles a warp claims per work-counter increment
+
+struct WarpSortSmem {
+  unsigned long long a[kWarpSortCap], b[kWarpSortCap];
+  radix::WarpScratch sc;
+};
 
 __device__ __forceinline__ void tile_range(const uint32_t* tile_off, int t, uint32_t capacity,
                                            uint32_t& b, uint32_t& e) {
   b = min(tile_off[t], capacity);
   e = min(tile_off[t + 1], capacity);
   if (e < b) e = b;
-}
-
-// Ascending bitonic sort of the len (<= P = 256 E) keys at g, written to dst[0, len). The keys are
-// held blocked: thread t holds keys t E .. t E + E - 1 in v (padding ~0 beyond len). Strides below
-// E are exchanges inside a thread, strides E .. 16 E warp shuffles (the partner is thread
-// t ^ (stride / E)), and only the 6 stages with strides of 32 E or more go through shared memory
-// (s, P + P / E keys: one pad slot every E keys keeps those accesses free of bank conflicts).
-template <int E>
-__device__ __forceinline__ void sort_blocked(const unsigned long long* __restrict__ g, int len,
-                                             unsigned long long* s, unsigned long long* __restrict__ dst) {
-  constexpr int P = kSortThreads * E;
-  const int t = threadIdx.x;
-  const int i0 = t * E;
-  unsigned long long v[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) v[e] = i0 + e < len ? g[i0 + e] : ~0ull;
-  auto pad = [](int i) { return i + i / E; };
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int jj = k >> 1; jj > 0; jj >>= 1) {
-      if (jj < E) {
-#pragma unroll
-        for (int m = 1; m < E; m <<= 1) {  // m = jj, unrolled so that v is indexed statically
-          if (m != jj) continue;
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            if (e & m) continue;
-            const unsigned long long a = v[e], b = v[e | m];
-            const bool up = ((i0 + e) & k) == 0;
-            const bool swap = (a > b) == up;
-            v[e] = swap ? b : a;
-            v[e | m] = swap ? a : b;
-          }
-        }
-      } else if (jj < 32 * E) {
-        const int lm = jj / E;
-#pragma unroll
-        for (int e = 0; e < E; ++e)
-          v[e] = walk::cmpx_keep(v[e], __shfl_xor_sync(0xFFFFFFFFu, v[e], lm), i0 + e, jj, k);
-      } else {
-#pragma unroll
-        for (int e = 0; e < E; ++e) s[pad(i0 + e)] = v[e];
-        __syncthreads();
-#pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = walk::cmpx_keep(v[e], s[pad((i0 + e) ^ jj)], i0 + e, jj, k);
-        __syncthreads();
-      }
-    }
-  }
-#pragma unroll
-  for (int e = 0; e < E; ++e)
-    if (i0 + e < len) dst[i0 + e] = v[e];
-}
-
-// Sorts len (<= kSortCap) keys from g into dst: up to 1024 keys through the walks' shared-memory
-// sort, longer lists blocked (sort_blocked with 8 or 16 keys a thread). g may equal dst.
-__device__ __forceinline__ void sort_list(const unsigned long long* g, int len, unsigned long long* s,
-                                          unsigned long long* dst) {
-  if (len > 2048) {
-    sort_blocked<16>(g, len, s, dst);
-  } else if (len > 1024) {
-    sort_blocked<8>(g, len, s, dst);
-  } else {
-    walk::sort_keys_block<4>(g, (uint32_t)len, s);
-    for (int k = threadIdx.x; k < len; k += kSortThreads) dst[k] = s[k];
-  }
-  __syncthreads();
 }
 
 // Queues every tile whose list has more than min_len keys (one thread per tile; one counter
@@ -116,68 +59,44 @@ __global__ void __launch_bounds__(kSortThreads) k_queue_tiles(const uint32_t* __
   if (want) queue[base + __popc(ballot & ((1u << lane) - 1u))] = (uint32_t)t;
 }
 
-// Number of elements of A among the first d outputs of merging A and B (keys are unique).
-__device__ __forceinline__ int merge_path(const unsigned long long* A, int na, const unsigned long long* B,
-                                          int nb, int d);
-
-// Sorts len (1024 < len <= kSortCap) keys from g into dst without padding the list to a power of
-// two: runs of 1024 keys are sorted in shared memory by the register/shuffle network of the walks,
-// then merged pairwise (merge path: every thread produces an equal share of each merge's outputs)
-// between the two shared buffers s0 and s1 (kSortCap keys each).
-__device__ __forceinline__ void sort_runs_merge(const unsigned long long* g, int len, unsigned long long* s0,
-                                                unsigned long long* s1, unsigned long long* __restrict__ dst) {
-  constexpr int kRun = 1024;
-  for (int r0 = 0; r0 < len; r0 += kRun) walk::sort_keys_block<4>(g + r0, (uint32_t)min(kRun, len - r0), s0 + r0);
-  unsigned long long* src = s0;
-  unsigned long long* out = s1;
-  for (int width = kRun; width < len; width <<= 1) {
-    for (int lo = 0; lo < len; lo += 2 * width) {
-      const int na = min(width, len - lo);
-      const int nb = max(0, min(width, len - lo - width));
-      const unsigned long long* A = src + lo;
-      const unsigned long long* Bp = src + lo + na;
-      const int tot = na + nb;
-      const int per = (tot + kSortThreads - 1) / kSortThreads;
-      const int d0 = min(tot, (int)threadIdx.x * per), d1 = min(tot, d0 + per);
-      if (d0 < d1) {
-        int ia = merge_path(A, na, Bp, nb, d0);
-        int ib = d0 - ia;
-        for (int d = d0; d < d1; ++d) {
-          const bool takeA = ib >= nb || (ia < na && A[ia] < Bp[ib]);
-          out[lo + d] = takeA ? A[ia++] : Bp[ib++];
-        }
-      }
+// Every tile list of the pass, by warps that claim kWarpSortChunk tiles at a time from the work
+// counter: lists of up to kWarpSortCap keys are sorted in place by the claiming warp, longer ones
+// queued for k_sort_queued.
+__global__ void __launch_bounds__(32 * kWarpSortWarps) k_sort_tiles(const uint32_t* __restrict__ tile_off,
+                                                                    unsigned long long* __restrict__ entries,
+                                                                    uint32_t capacity, int ntiles,
+                                                                    uint32_t* __restrict__ queue, DevStatus* status) {
+  extern __shared__ __align__(16) unsigned long long s_dyn[];  // kWarpSortWarps x WarpSortSmem
+  WarpSortSmem& m = reinterpret_cast<WarpSortSmem*>(s_dyn)[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < radix::kBins; i += 32) m.sc.match[i] = 0u;
+  __syncwarp();
+  while (true) {
+    uint32_t t0 = 0;
+    if (lane == 0) t0 = atomicAdd(&status->sort_next, (uint32_t)kWarpSortChunk);
+    t0 = __shfl_sync(0xFFFFFFFFu, t0, 0);
+    if (t0 >= (uint32_t)ntiles) break;
+    const int t1 = min(ntiles, (int)t0 + kWarpSortChunk);
+    {  // start the chunk's keys towards L2 while the first list is sorted
+      uint32_t cb, ce, cx;
+      tile_range(tile_off, (int)t0, capacity, cb, cx);
+      tile_range(tile_off, t1 - 1, capacity, cx, ce);
+      const char* p0 = reinterpret_cast<const char*>(entries + cb);
+      const size_t bytes = (size_t)(ce - cb) * sizeof(unsigned long long);
+      for (size_t o = (size_t)lane * 128; o < bytes; o += 32 * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(p0 + o));
     }
-    __syncthreads();
-    unsigned long long* t = src;
-    src = out;
-    out = t;
-  }
-  for (int k = threadIdx.x; k < len; k += kSortThreads) dst[k] = src[k];
-  __syncthreads();
-}
-
-// Every tile list: sorted in place when it has at most kSortCap keys (one CTA per tile), queued
-// for k_sort_queued when longer. Up to 1024 keys: the walks' shared-memory network; longer:
-// sorted runs merged in shared memory.
-__global__ void __launch_bounds__(kSortThreads, 3) k_sort_tiles(const uint32_t* __restrict__ tile_off,
-                                                             unsigned long long* __restrict__ entries,
-                                                             uint32_t capacity, uint32_t* __restrict__ queue,
-                                                             DevStatus* status) {
-  extern __shared__ unsigned long long s_dyn[];  // 2 x kSortCap keys
-  uint32_t b, e;
-  tile_range(tile_off, blockIdx.x, capacity, b, e);
-  const int n = (int)(e - b);
-  if (n <= 1) return;
-  if (n > kSortCap) {
-    if (threadIdx.x == 0) queue[atomicAdd(&status->big_tiles, 1u)] = blockIdx.x;
-    return;
-  }
-  if (n > 1024) {
-    sort_runs_merge(entries + b, n, s_dyn, s_dyn + kSortCap, entries + b);
-  } else {
-    walk::sort_keys_block<4>(entries + b, (uint32_t)n, s_dyn);
-    for (int k = threadIdx.x; k < n; k += kSortThreads) entries[b + k] = s_dyn[k];
+    for (int t = (int)t0; t < t1; ++t) {
+      uint32_t b, e;
+      tile_range(tile_off, t, capacity, b, e);
+      const int n = (int)(e - b);
+      if (n <= 1) continue;
+      if (n > kWarpSortCap) {
+        if (lane == 0) queue[atomicAdd(&status->big_tiles, 1u)] = (uint32_t)t;
+        continue;
+      }
+      radix::warp_sort(entries + b, n, m.a, m.b, m.sc);
+    }
   }
 }
 
@@ -193,16 +112,28 @@ __device__ __forceinline__ int merge_path(const unsigned long long* A, int na, c
   return lo;
 }
 
+// Sorts the m (1 < m <= kSortCap) keys at g in place with the block radix sort sized to m.
+__device__ __forceinline__ void block_sort_list(unsigned long long* g, int m, unsigned long long* a,
+                                                unsigned long long* b, radix::BlockScratch& sc) {
+  if (m <= 1024) radix::block_sort<4>(g, m, a, b, sc);
+  else if (m <= 2048) radix::block_sort<8>(g, m, a, b, sc);
+  else if (m <= 3072) radix::block_sort<12>(g, m, a, b, sc);
+  else radix::block_sort<16>(g, m, a, b, sc);
+}
+
 // Sorts the queued tile lists in place, a grid-stride loop over the queue. A list of up to
-// kSortCap keys is sorted in shared memory with the register/shuffle bitonic network sized to it;
-// a longer one as runs of kSortCap keys, then pairwise merge-path merges ping-ponging between its
-// slot range and the same range of the scratch array.
-__global__ void __launch_bounds__(kSortThreads, 3) k_sort_queued(const uint32_t* __restrict__ tile_off,
+// kSortCap keys is sorted at once by the block radix sort; a longer one as runs of kSortCap keys,
+// then pairwise merge-path merges ping-ponging between its slot range and the same range of the
+// scratch array.
+__global__ void __launch_bounds__(kSortThreads) k_sort_queued(const uint32_t* __restrict__ tile_off,
                                                               unsigned long long* __restrict__ entries,
                                                               unsigned long long* __restrict__ scratch,
                                                               uint32_t capacity, const uint32_t* __restrict__ queue,
                                                               const DevStatus* status) {
-  __shared__ unsigned long long s[kSortCap + kSortCap / 16];
+  extern __shared__ __align__(16) unsigned long long s_dyn[];  // 2 x kSortCap keys
+  __shared__ radix::BlockScratch sc;
+  for (int i = threadIdx.x; i < radix::kWarps * radix::kBins; i += kSortThreads) sc.match[i] = 0u;
+  __syncthreads();
   const uint32_t count = status->big_tiles;
   for (uint32_t q = blockIdx.x; q < count; q += gridDim.x) {
     uint32_t b, e;
@@ -210,7 +141,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_queued(const uint32_t*
     const int n = (int)(e - b);
     for (int r0 = 0; r0 < n; r0 += kSortCap) {  // sorted runs (the whole list when it fits)
       const int m = min(kSortCap, n - r0);
-      sort_list(entries + b + r0, m, s, entries + b + r0);
+      if (m > 1) block_sort_list(entries + b + r0, m, s_dyn, s_dyn + kSortCap, sc);
     }
     if (n <= kSortCap) continue;  // uniform
     unsigned long long* src = entries + b;
@@ -244,26 +175,39 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_queued(const uint32_t*
   }
 }
 
+int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
 }  // namespace
 
-// sort_all: order every tile list here (walks that read the lists from global memory): one CTA per
-// tile, lists longer than kSortCap queued. Otherwise only the lists longer than the walks'
-// shared-memory sort (kWalkSortCap), queued and sorted by the persistent kernel.
+// sort_all: order every tile list here (walks that read the lists from global memory). Otherwise
+// only the lists longer than the walks' shared-memory sort (kWalkSortCap) are queued and sorted.
 void launch_tile_sort(const Problem& p, int cb, bool sort_all, const Workspace& ws, cudaStream_t s) {
+  static_assert(kWarpSortCap == walk::kWalkSortCap, "both paths queue the lists longer than 1024 keys");
   const int ntiles = cb * p.tiles;
-  cudaMemsetAsync(&ws.status->big_tiles, 0, sizeof(uint32_t), s);
+  const int sms = sm_count();
+  cudaMemsetAsync(&ws.status->big_tiles, 0, 2 * sizeof(uint32_t), s);  // big_tiles, sort_next
   if (sort_all) {
-    const int smem = 2 * kSortCap * (int)sizeof(unsigned long long);
+    const int smem = kWarpSortWarps * (int)sizeof(WarpSortSmem);
     cudaFuncSetAttribute(k_sort_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_sort_tiles<<<ntiles, kSortThreads, smem, s>>>(ws.tile_off, reinterpret_cast<unsigned long long*>(ws.entries),
-                                                    p.capacity, ws.big_list, ws.status);
-  }
-  else
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_tiles, 32 * kWarpSortWarps, smem);
+    const int grid = sms * (per_sm > 0 ? per_sm : 1);
+    k_sort_tiles<<<grid, 32 * kWarpSortWarps, smem, s>>>(ws.tile_off, reinterpret_cast<unsigned long long*>(ws.entries),
+                                                         p.capacity, ntiles, ws.big_list, ws.status);
+  } else {
     k_queue_tiles<<<(ntiles + kSortThreads - 1) / kSortThreads, kSortThreads, 0, s>>>(
         ws.tile_off, ntiles, p.capacity, walk::kWalkSortCap, ws.big_list, ws.status);
-  k_sort_queued<<<kSortGrid, kSortThreads, 0, s>>>(ws.tile_off, reinterpret_cast<unsigned long long*>(ws.entries),
-                                                   reinterpret_cast<unsigned long long*>(ws.entries_tmp), p.capacity,
-                                                   ws.big_list, ws.status);
+  }
+  const int qsmem = 2 * kSortCap * (int)sizeof(unsigned long long);
+  cudaFuncSetAttribute(k_sort_queued, cudaFuncAttributeMaxDynamicSharedMemorySize, qsmem);
+  k_sort_queued<<<sms * 2, kSortThreads, qsmem, s>>>(ws.tile_off, reinterpret_cast<unsigned long long*>(ws.entries),
+                                                     reinterpret_cast<unsigned long long*>(ws.entries_tmp), p.capacity,
+                                                     ws.big_list, ws.status);
   note_launches(2);
 }
 

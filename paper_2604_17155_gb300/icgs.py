@@ -133,6 +133,10 @@ def load(path: str = LIB_PATH):
     lib.icgs_colorize_sets.restype = ctypes.c_int
     lib.icgs_debug_tc_wait.argtypes = [ctypes.c_int64, ctypes.c_int32]
     lib.icgs_debug_tc_wait.restype = None
+    lib.icgs_sort_workspace_size.argtypes = [ctypes.c_int32, ctypes.c_int64]
+    lib.icgs_sort_workspace_size.restype = S
+    lib.icgs_sort_tile_lists.argtypes = [P, P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, P, S, P]
+    lib.icgs_sort_tile_lists.restype = ctypes.c_int
     lib.icgs_set_stage_timing.argtypes = [ctypes.c_int]
     lib.icgs_set_stage_timing.restype = None
     lib.icgs_last_stage_ms.argtypes = [P, ctypes.c_int]
@@ -643,6 +647,24 @@ def selftest_tc(A, B, bf16=True, lanes=False):
                                      ctypes.c_void_p(DL.data_ptr() if lanes else 0), ctypes.c_void_p(ws.data_ptr()),
                                      _stream_ptr(A.device)))
     return (D, DL) if lanes else D
+
+
+def sort_tile_lists(tile_off, keys, all_lists=True):
+    """Diagnostic: the library's depth sort of tile lists, in place. tile_off: int32 CUDA tensor
+    [ntiles + 1] (non-decreasing from 0); keys: int64 CUDA tensor, each (float32 depth bits << 32)
+    | Gaussian index. all_lists=False sorts only the lists longer than 1024 keys."""
+    lib = load()
+    if tile_off.dtype != _torch().int32 or keys.dtype != _torch().int64:
+        raise ValueError("tile_off must be int32 and keys int64")
+    if not (tile_off.is_contiguous() and keys.is_contiguous()):
+        raise ValueError("tile_off and keys must be contiguous")
+    ntiles, nkeys = int(tile_off.numel()) - 1, int(keys.numel())
+    size = lib.icgs_sort_workspace_size(ntiles, nkeys)
+    ws = _ws.get(keys.device, size)
+    _check(lib.icgs_sort_tile_lists(ctypes.c_void_p(tile_off.data_ptr()), ctypes.c_void_p(keys.data_ptr()), ntiles,
+                                    nkeys, 1 if all_lists else 0, ctypes.c_void_p(ws.data_ptr()), size,
+                                    _stream_ptr(keys.device)))
+    return keys
 
 
 def colorize_backward(scene: Scene, cams: Cameras, targets, sh_degree, coeffs, chol, grad_coeffs, lam=None,
