@@ -109,6 +109,13 @@ Workspace carve(char* base, const Problem& p, int need) {
   ws.big_list = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (size_t)ct));
   ws.entries = reinterpret_cast<uint64_t*>(take(sizeof(uint64_t) * (size_t)p.capacity));
   ws.entries_tmp = reinterpret_cast<uint64_t*>(take(sizeof(uint64_t) * (size_t)p.capacity));
+  const size_t cells = (size_t)spatial_cells();
+  ws.order = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (size_t)p.n));
+  ws.cell_off = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (cells + 1)));
+  ws.cell_cur = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * cells));
+  ws.cell_tmp = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (cells / 1024 + 2)));
+  ws.cell_box = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * 8));
+  ws.packed = reinterpret_cast<float4*>(take(sizeof(float4) * 3 * (size_t)p.n));
   const size_t B = (size_t)p.B, K = (size_t)p.K, n = (size_t)p.n;
   if (need & kNeedAccumulate) {
     ws.acc = reinterpret_cast<float*>(take(sizeof(float) * (p.L == 0 ? n : (size_t)cbn) * (size_t)p.acc_stride));
@@ -281,9 +288,11 @@ icgs_status upload_common(const Problem& p, const icgs_cameras* cams, const floa
 
 // sort_all: every tile list is ordered in global memory (the tensor-core walk reads them there);
 // otherwise only the long lists are, and the CUDA-core walks sort the rest in shared memory.
-icgs_status bin_pass(const Problem& p, const icgs_scene* sc, int cb, bool sort_all, const Workspace& wp,
+// first: the call's first pass, which also computes the Gaussians' processing order.
+icgs_status bin_pass(const Problem& p, const icgs_scene* sc, int cb, bool sort_all, bool first, const Workspace& wp,
                      cudaStream_t s) {
   const int64_t ct = (int64_t)cb * p.tiles;
+  if (first) launch_spatial_order(p, sc->means, sc->scales, sc->quats, sc->opacity, wp, s);
   ICGS_TRY_CUDA(cudaMemsetAsync(wp.tile_off, 0, sizeof(uint32_t) * (size_t)(ct + 1), s));
   ICGS_TRY_CUDA(cudaMemsetAsync(wp.tile_cur, 0, sizeof(uint32_t) * (size_t)ct, s));
   launch_project(p, sc->means, sc->scales, sc->quats, sc->opacity, cb, wp, s);
@@ -423,7 +432,7 @@ static icgs_status colorize_impl(const icgs_scene* scene, const icgs_cameras* ca
     wp.cams = ws.cams + cam0;
     if (p.L > 0)
       ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)cb * (size_t)p.n * p.acc_stride, s));
-    if ((st = bin_pass(p, scene, cb, tc_accumulate_applies(p, (int)targets->dtype), wp, s)) != ICGS_OK) return st;
+    if ((st = bin_pass(p, scene, cb, tc_accumulate_applies(p, (int)targets->dtype), cam0 == 0, wp, s)) != ICGS_OK) return st;
     launch_blend_accumulate(p, cb, cam0, targets->data, (int)targets->dtype, nullptr, wp, s);
     g_timer.mark(kBlend, s);
     if (p.L > 0) {
@@ -541,7 +550,7 @@ icgs_status icgs_colorize_sets(const icgs_scene* scene, const icgs_cameras* cams
     Workspace wp = ws;
     wp.cams = ws.cams + cam0;
     if (p.L > 0 && (st = zero_accs((int64_t)cb * p.n)) != ICGS_OK) return st;
-    if ((st = bin_pass(p, scene, cb, any_tc, wp, s)) != ICGS_OK) return st;  // one binning for every set
+    if ((st = bin_pass(p, scene, cb, any_tc, cam0 == 0, wp, s)) != ICGS_OK) return st;  // one binning for every set
     for (int k = 0; k < n_sets; ++k) {
       Workspace wk = wp;
       wk.acc = set_acc[k];
@@ -684,7 +693,7 @@ icgs_status icgs_colorize_host(const icgs_scene* scene, const icgs_cameras* cams
     if (p.L > 0)
       ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)cb * (size_t)p.n * p.acc_stride, s));
     // projection, binning and sorting need no targets: they run while the first chunks arrive
-    if ((st = bin_pass(p, scene, cb, tc_accumulate_applies(p, dtype), wp, s)) != ICGS_OK) return st;
+    if ((st = bin_pass(p, scene, cb, tc_accumulate_applies(p, dtype), cam0 == 0, wp, s)) != ICGS_OK) return st;
     for (; chunk < chunk_cam0.size() && chunk_cam0[chunk] < cam0 + cb; ++chunk) {
       const int j0 = chunk_cam0[chunk] - cam0, jc = chunk_n[chunk];
       ICGS_TRY_CUDA(cudaStreamWaitEvent(s, hp->ready[chunk], 0));
@@ -743,7 +752,7 @@ icgs_status icgs_accumulate(const icgs_scene* scene, const icgs_cameras* cams, c
     wp.cams = ws.cams + cam0;
     if (p.L > 0)
       ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)cb * (size_t)p.n * p.acc_stride, s));
-    if ((st = bin_pass(p, scene, cb, tc_accumulate_applies(p, (int)targets->dtype), wp, s)) != ICGS_OK) return st;
+    if ((st = bin_pass(p, scene, cb, tc_accumulate_applies(p, (int)targets->dtype), cam0 == 0, wp, s)) != ICGS_OK) return st;
     launch_blend_accumulate(p, cb, cam0, targets->data, (int)targets->dtype, nullptr, wp, s);
     g_timer.mark(kBlend, s);
     if (p.L > 0) {
@@ -884,7 +893,7 @@ static icgs_status backward_impl(const icgs_scene* scene, const icgs_cameras* ca
     const int cb = std::min(p.cam_batch, p.n_cams - cam0);
     Workspace wp = ws;
     wp.cams = ws.cams + cam0;
-    if ((st = bin_pass(p, scene, cb, false, wp, s)) != ICGS_OK) return st;
+    if ((st = bin_pass(p, scene, cb, false, cam0 == 0, wp, s)) != ICGS_OK) return st;
     launch_payload_adjoint(p, scene->means, coeffs, cb, wp, s);
     g_timer.mark(kPayload, s);
     launch_blend_adjoint(p, cb, cam0, targets->data, (int)targets->dtype, wp, grad_targets, grad_opacity != nullptr, s);
@@ -940,7 +949,7 @@ static icgs_status refine_impl(const icgs_scene* scene, const icgs_cameras* cams
       if (p.L > 0)
         ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)cb * (size_t)p.n * p.acc_stride, s));
       if (!(one_pass && step > 0))
-        if ((st = bin_pass(p, scene, cb, false, wp, s)) != ICGS_OK) return st;
+        if ((st = bin_pass(p, scene, cb, false, step == 0 && cam0 == 0, wp, s)) != ICGS_OK) return st;
       launch_payload_render(p, scene->means, coeffs_inout, cb, wp, s);  // Alg. 1 line 8: render
       if (launch_blend_refine(p, cb, cam0, targets->data, (int)targets->dtype, wp, s)) {  // lines 8-9, one walk
         g_timer.mark(kPayload, s);
@@ -996,7 +1005,7 @@ static icgs_status render_impl(const icgs_scene* scene, const icgs_cameras* cams
     const int cb = std::min(p.cam_batch, p.n_cams - cam0);
     Workspace wp = ws;
     wp.cams = ws.cams + cam0;
-    if ((st = bin_pass(p, scene, cb, false, wp, s)) != ICGS_OK) return st;
+    if ((st = bin_pass(p, scene, cb, false, cam0 == 0, wp, s)) != ICGS_OK) return st;
     launch_payload_render(p, scene->means, coeffs, cb, wp, s);
     g_timer.mark(kPayload, s);
     launch_blend_render(p, cb, cam0, wp, images_out, s);

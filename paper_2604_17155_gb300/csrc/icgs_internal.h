@@ -67,13 +67,19 @@ struct Workspace {
   DevStatus* status = nullptr;
   DevCam* cams = nullptr;
   ProjRec* rec = nullptr;          // [cb * n]
-  uint4* rect = nullptr;           // [cb * n] (tx0|ty0<<16, tx1|ty1<<16, depth key bits, 0)
+  uint4* rect = nullptr;           // [cb * n] by processing position: (tx0|ty0<<16, tx1|ty1<<16, depth key bits, 0)
   uint32_t* tile_off = nullptr;    // [cb * T + 1] counts, then exclusive offsets
   uint32_t* tile_cur = nullptr;    // [cb * T]
   uint32_t* scan_tmp = nullptr;    // [scan blocks + 1]
   uint32_t* big_list = nullptr;    // [cb * T]
   uint64_t* entries = nullptr;     // [capacity] (depth key << 32 | index)
   uint64_t* entries_tmp = nullptr; // [capacity] merge buffer for long tiles
+  uint32_t* order = nullptr;       // [n] Gaussians in processing order (Morton cells of the scene box)
+  uint32_t* cell_off = nullptr;    // [cells + 1] counts, then offsets of the cells in order
+  uint32_t* cell_cur = nullptr;    // [cells]
+  uint32_t* cell_tmp = nullptr;    // [cells / 1024 + 2] scan block sums
+  uint32_t* cell_box = nullptr;    // [6] order keys of the scene box (min xyz, max xyz)
+  float4* packed = nullptr;        // [3 n] parameters by processing position (mean, o), (scale, qw), (qxyz, 0)
   float* payload = nullptr;        // [cb * n * (K+1)] per (camera, Gaussian) colour / adjoint terms
   float* acc = nullptr;            // [cb * n * RS] (L>0) or [n * RS] (L=0), RS = acc_stride
   float* G = nullptr;              // [n * B * B] Gram rows, hi
@@ -120,6 +126,10 @@ void set_error_message(const char* fmt, ...);
 void launch_project(const Problem& p, const float* means, const float* scales, const float* quats,
                     const float* opac, int cb, const Workspace& ws, cudaStream_t s);
 void launch_scan(const Problem& p, int cb, const Workspace& ws, cudaStream_t s);
+// Cells of the processing order, and the order itself (ws.order; once per call, before the passes).
+int spatial_cells();
+void launch_spatial_order(const Problem& p, const float* means, const float* scales, const float* quats,
+                          const float* opac, const Workspace& ws, cudaStream_t s);
 void launch_scatter(const Problem& p, int cb, const Workspace& ws, cudaStream_t s);
 void launch_tile_sort(const Problem& p, int cb, bool sort_all, const Workspace& ws, cudaStream_t s);
 // sub_img (nullable, float32 [cb,H,W,K] of this pass's cameras): accumulate t - img instead of t

@@ -86,16 +86,19 @@ constexpr float kOpacityMin = 0x1.010102p-8f;
 
 // Projects Gaussian i into camera c, writes its record and tile rectangle at slot ji and returns
 // the rectangle (tx0, ty0, tx1, ty1); tx0 > tx1 when the Gaussian has no pixel in the image.
-__device__ __forceinline__ int4 project_pair(const float* __restrict__ means, const float* __restrict__ scales,
-                                             const float* __restrict__ quats, const float* __restrict__ opac,
-                                             int64_t i, const DevCam& c, int width, int height, float near_z,
-                                             int64_t ji, ProjRec* __restrict__ rec, uint4* __restrict__ rect) {
+// The parameters of one Gaussian as the projection reads them: mo = (mean, opacity),
+// sq = (scale, quaternion w), qv = (quaternion x, y, z, unused); loaded by the caller (which may
+// fetch them ahead of use). The record goes to rec[ji] (indexed by camera and Gaussian), the tile
+// rectangle to rect[jp] (indexed by camera and processing position).
+__device__ __forceinline__ int4 project_pair(const float4 mo, const float4 sq, const float4 qv, const DevCam& c,
+                                             int width, int height, float near_z, int64_t ji, int64_t jp,
+                                             ProjRec* __restrict__ rec, uint4* __restrict__ rect) {
   const int4 none = make_int4(1, 0, 0, 0);
-  const float mx3 = means[3 * i], my3 = means[3 * i + 1], mz3 = means[3 * i + 2];
-  const float o = opac[i];
+  const float mx3 = mo.x, my3 = mo.y, mz3 = mo.z;
+  const float o = mo.w;
   const float key = depth_key(c, mx3, my3, mz3);
   if (!(key > near_z) || !isfinite(key) || !(o >= kOpacityMin) || !isfinite(o)) {
-    rect[ji] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+    rect[jp] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
     return none;
   }
   float tz_lo, tx_lo, ty_lo;
@@ -104,11 +107,11 @@ __device__ __forceinline__ int4 project_pair(const float* __restrict__ means, co
   const float ty = affine_ff(c.w[4], c.w[5], c.w[6], c.w[7], mx3, my3, mz3, ty_lo);
   const float iz = 1.0f / tz;
   const float qthr = 2.0f * logf(255.0f * o);
-  const float sx = scales[3 * i], sy = scales[3 * i + 1], sz = scales[3 * i + 2];
+  const float sx = sq.x, sy = sq.y, sz = sq.z;
   // a non-finite scale would give an unbounded support (NaN and zero quaternions fail the
   // determinant test below)
   if (!(isfinite(sx) && isfinite(sy) && isfinite(sz))) {
-    rect[ji] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+    rect[jp] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
     return none;
   }
   {
@@ -122,13 +125,13 @@ __device__ __forceinline__ int4 project_pair(const float* __restrict__ means, co
     const float hmax = sqrtf(fmaxf(qthr, 0.0f) * (fz * fz * jb * c.rnorm2 * smax * smax + 0.3f)) * 1.001f + 1.0f;
     const float mxa = fmaf(c.fx, tx * iz, c.cx), mya = fmaf(c.fy, ty * iz, c.cy);
     if (mxa + hmax < 0.0f || mxa - hmax > (float)width || mya + hmax < 0.0f || mya - hmax > (float)height) {
-      rect[ji] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+      rect[jp] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
       return none;
     }
   }
 
   // 3D covariance Sigma = M M^T with M = R(q) diag(s)
-  float qw = quats[4 * i], qx = quats[4 * i + 1], qy = quats[4 * i + 2], qz = quats[4 * i + 3];
+  float qw = sq.w, qx = qv.x, qy = qv.y, qz = qv.z;
   const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
   qw *= qn; qx *= qn; qy *= qn; qz *= qn;
   const float r00 = 1.f - 2.f * (qy * qy + qz * qz), r01 = 2.f * (qx * qy - qw * qz), r02 = 2.f * (qx * qz + qw * qy);
@@ -160,7 +163,7 @@ __device__ __forceinline__ int4 project_pair(const float* __restrict__ means, co
   const float mx = pixel_ff(c.fx, c.cx, tx, tx_lo, tz, tz_lo, iz, mx_lo);
   const float my = pixel_ff(c.fy, c.cy, ty, ty_lo, tz, tz_lo, iz, my_lo);
   if (!(det > 0.0f) || !isfinite(mx) || !isfinite(my)) {
-    rect[ji] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+    rect[jp] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
     return none;
   }
   const float idet = 1.0f / det;
@@ -171,7 +174,7 @@ __device__ __forceinline__ int4 project_pair(const float* __restrict__ means, co
   const float fx0 = fmaxf(ceilf(mx - hx - 0.5f), 0.0f), fx1 = fminf(floorf(mx + hx - 0.5f), (float)(width - 1));
   const float fy0 = fmaxf(ceilf(my - hy - 0.5f), 0.0f), fy1 = fminf(floorf(my + hy - 0.5f), (float)(height - 1));
   if (!(fx0 <= fx1) || !(fy0 <= fy1)) {
-    rect[ji] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+    rect[jp] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
     return none;
   }
   const int tx0 = (int)fx0 / kTile, tx1 = (int)fx1 / kTile;
@@ -184,7 +187,7 @@ __device__ __forceinline__ int4 project_pair(const float* __restrict__ means, co
                       pack_half2(__float2half_ru(hx), __float2half_ru(hy)));
   r.par = make_float4(cc2 * idet, -cb2 * idet, ca2 * idet, o);
   rec[ji] = r;
-  rect[ji] = make_uint4((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16),
+  rect[jp] = make_uint4((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16),
                         __float_as_uint(key), 0u);
   return make_int4(tx0, ty0, tx1, ty1);
 }
@@ -203,22 +206,35 @@ constexpr int kHistTiles = 12288;             // largest tile grid the shared-me
 // 1-D grid, so the CTAs of one chunk of Gaussians run together and read its parameters from DRAM
 // once (a scene larger than L2 would otherwise be re-read for every camera).
 template <int PT>
-__global__ void __launch_bounds__(256) k_project_hist(
-    const float* __restrict__ means, const float* __restrict__ scales, const float* __restrict__ quats,
-    const float* __restrict__ opac, int64_t n, const DevCam* __restrict__ cams, int j0, int cbl, int width,
-    int height, float near_z, int tiles_x, int tiles, ProjRec* __restrict__ rec, uint4* __restrict__ rect,
-    uint32_t* __restrict__ tile_count) {
+__global__ void __launch_bounds__(256, 4) k_project_hist(
+    const float4* __restrict__ packed, const uint32_t* __restrict__ order, int64_t n, const DevCam* __restrict__ cams,
+    int j0, int cbl, int width, int height, float near_z, int tiles_x, int tiles, ProjRec* __restrict__ rec,
+    uint4* __restrict__ rect, uint32_t* __restrict__ tile_count) {
   extern __shared__ uint32_t s_hist[];
   const int64_t chunk = blockIdx.x / cbl;
   const int j = j0 + (int)(blockIdx.x - chunk * cbl);
   const DevCam& c = cams[j];
   for (int t = threadIdx.x; t < tiles; t += 256) s_hist[t] = 0u;
   __syncthreads();
-  const int64_t i0 = chunk * hist_per_cta(PT);
+  const int64_t p0 = chunk * hist_per_cta(PT);
+  // the Gaussian at processing position q and its mean and opacity, fetched one step ahead
+  int64_t i_next = 0;
+  float4 mo_next = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  if (p0 + threadIdx.x < n) {
+    i_next = order[p0 + threadIdx.x];
+    mo_next = packed[3 * (p0 + threadIdx.x)];
+  }
   for (int r = 0; r < PT; ++r) {
-    const int64_t i = i0 + r * 256 + threadIdx.x;
-    if (i >= n) break;
-    const int4 tr = project_pair(means, scales, quats, opac, i, c, width, height, near_z, (int64_t)j * n + i, rec, rect);
+    const int64_t q = p0 + r * 256 + threadIdx.x;
+    if (q >= n) break;
+    const float4 mo = mo_next;
+    const int64_t i = i_next;
+    if (r + 1 < PT && q + 256 < n) {
+      i_next = order[q + 256];
+      mo_next = packed[3 * (q + 256)];
+    }
+    const int4 tr = project_pair(mo, packed[3 * q + 1], packed[3 * q + 2], c, width, height, near_z,
+                                 (int64_t)j * n + i, (int64_t)j * n + q, rec, rect);
     for (int ty = tr.y; ty <= tr.w; ++ty)
       for (int tx = tr.x; tx <= tr.z; ++tx) atomicAdd(&s_hist[ty * tiles_x + tx], 1u);
   }
@@ -230,31 +246,31 @@ __global__ void __launch_bounds__(256) k_project_hist(
 
 // Fallback for tile grids beyond kHistTiles: one global atomic per instance.
 __global__ void __launch_bounds__(256) k_project(
-    const float* __restrict__ means, const float* __restrict__ scales,
-    const float* __restrict__ quats, const float* __restrict__ opac, int64_t n,
+    const float4* __restrict__ packed, const uint32_t* __restrict__ order, int64_t n,
     const DevCam* __restrict__ cams, int width, int height, float near_z, int tiles_x, int tiles,
     ProjRec* __restrict__ rec, uint4* __restrict__ rect, uint32_t* __restrict__ tile_count) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
-  if (i >= n) return;
-  const int4 tr = project_pair(means, scales, quats, opac, i, cams[j], width, height, near_z, (int64_t)j * n + i, rec, rect);
+  if (q >= n) return;
+  const int64_t i = order[q];
+  const int4 tr = project_pair(packed[3 * q], packed[3 * q + 1], packed[3 * q + 2], cams[j], width, height, near_z,
+                               (int64_t)j * n + i, (int64_t)j * n + q, rec, rect);
   uint32_t* base = tile_count + (int64_t)j * tiles;
   for (int ty = tr.y; ty <= tr.w; ++ty)
     for (int tx = tr.x; tx <= tr.z; ++tx) atomicAdd(base + ty * tiles_x + tx, 1u);
 }
 
 __global__ void __launch_bounds__(256) k_scatter(
-    int64_t n, const uint4* __restrict__ rect, int tiles_x, int tiles,
+    int64_t n, const uint4* __restrict__ rect, const uint32_t* __restrict__ order, int tiles_x, int tiles,
     const uint32_t* __restrict__ tile_off, uint32_t* __restrict__ tile_cur, uint64_t* __restrict__ entries,
     uint32_t capacity, DevStatus* status) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
-  if (i >= n) return;
-  const int64_t ji = (int64_t)j * n + i;
-  const uint4 rc = rect[ji];
+  if (q >= n) return;
+  const uint4 rc = rect[(int64_t)j * n + q];
   const int tx0 = rc.x & 0xFFFF, ty0 = rc.x >> 16, tx1 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
   if (rc.x == 0xFFFFFFFFu) return;
-  const uint64_t key = ((uint64_t)rc.z << 32) | (uint64_t)(uint32_t)i;
+  const uint64_t key = ((uint64_t)rc.z << 32) | (uint64_t)order[q];
   bool overflow = false;
   for (int ty = ty0; ty <= ty1; ++ty)
     for (int tx = tx0; tx <= tx1; ++tx) {
@@ -267,11 +283,13 @@ __global__ void __launch_bounds__(256) k_scatter(
   if (overflow) atomicOr(&status->flags, kFlagOverflow);
 }
 
-// Same CTA tiling as k_project_hist: the CTA counts its instances per tile, reserves one contiguous
-// run per tile with a single global atomic, then places its instances with shared-memory cursors.
+// Same CTA tiling as k_project_hist (processing positions, rectangles indexed by position): the
+// CTA counts its instances per tile, reserves one contiguous run per tile with a single global
+// atomic, then places its instances with shared-memory cursors.
 template <int PT>
 __global__ void __launch_bounds__(256) k_scatter_hist(
-    int64_t n, const uint4* __restrict__ rect, int tiles_x, int tiles, const uint32_t* __restrict__ tile_off,
+    int64_t n, const uint4* __restrict__ rect, const uint32_t* __restrict__ order, int tiles_x, int tiles,
+    const uint32_t* __restrict__ tile_off,
     uint32_t* __restrict__ tile_cur, uint64_t* __restrict__ entries, uint32_t capacity, DevStatus* status) {
   extern __shared__ uint32_t s_mem[];
   uint32_t* s_cnt = s_mem;          // [tiles] count, then running cursor
@@ -279,41 +297,177 @@ __global__ void __launch_bounds__(256) k_scatter_hist(
   const int j = blockIdx.y;
   for (int t = threadIdx.x; t < tiles; t += 256) s_cnt[t] = 0u;
   __syncthreads();
+  // The rectangles are read kGroup at a time (all loads in flight before the first is used), and
+  // the per-tile reservations kFlush tiles at a time, so that global round trips overlap.
+  constexpr int kGroup = 4, kFlush = 8;
+  static_assert(PT % kGroup == 0, "whole groups of rectangles");
   const int64_t i0 = (int64_t)blockIdx.x * hist_per_cta(PT);
-  for (int r = 0; r < PT; ++r) {
-    const int64_t i = i0 + r * 256 + threadIdx.x;
-    if (i >= n) break;
-    const uint4 rc = rect[(int64_t)j * n + i];
-    if (rc.x == 0xFFFFFFFFu) continue;
-    const int tx0 = rc.x & 0xFFFF, ty0 = rc.x >> 16, tx1 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
-    for (int ty = ty0; ty <= ty1; ++ty)
-      for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&s_cnt[ty * tiles_x + tx], 1u);
+  const uint4* rect_j = rect + (int64_t)j * n;
+  for (int r0 = 0; r0 < PT; r0 += kGroup) {
+    uint4 rcs[kGroup];
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+      const int64_t q = i0 + (r0 + u) * 256 + threadIdx.x;
+      rcs[u] = q < n ? rect_j[q] : make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+      const uint4 rc = rcs[u];
+      if (rc.x == 0xFFFFFFFFu) continue;
+      const int tx0 = rc.x & 0xFFFF, ty0 = rc.x >> 16, tx1 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
+      for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&s_cnt[ty * tiles_x + tx], 1u);
+    }
   }
   __syncthreads();
   const int64_t tj = (int64_t)j * tiles;
-  for (int t = threadIdx.x; t < tiles; t += 256) {
-    const uint32_t cnt = s_cnt[t];
-    s_base[t] = cnt ? tile_off[tj + t] + atomicAdd(tile_cur + tj + t, cnt) : 0u;
-    s_cnt[t] = 0u;
+  for (int t0 = threadIdx.x; t0 < tiles; t0 += 256 * kFlush) {
+    uint32_t cnt[kFlush], old[kFlush], off[kFlush];
+#pragma unroll
+    for (int u = 0; u < kFlush; ++u) {
+      const int t = t0 + 256 * u;
+      cnt[u] = t < tiles ? s_cnt[t] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kFlush; ++u) {
+      const int t = t0 + 256 * u;
+      old[u] = 0u;
+      off[u] = 0u;
+      if (cnt[u]) {
+        old[u] = atomicAdd(tile_cur + tj + t, cnt[u]);
+        off[u] = tile_off[tj + t];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kFlush; ++u) {
+      const int t = t0 + 256 * u;
+      if (t < tiles) {
+        s_base[t] = off[u] + old[u];
+        s_cnt[t] = 0u;
+      }
+    }
   }
   __syncthreads();
   bool overflow = false;
-  for (int r = 0; r < PT; ++r) {
-    const int64_t i = i0 + r * 256 + threadIdx.x;
-    if (i >= n) break;
-    const uint4 rc = rect[(int64_t)j * n + i];
-    if (rc.x == 0xFFFFFFFFu) continue;
-    const int tx0 = rc.x & 0xFFFF, ty0 = rc.x >> 16, tx1 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
-    const uint64_t key = ((uint64_t)rc.z << 32) | (uint64_t)(uint32_t)i;
-    for (int ty = ty0; ty <= ty1; ++ty)
-      for (int tx = tx0; tx <= tx1; ++tx) {
-        const int t = ty * tiles_x + tx;
-        const uint64_t slot = (uint64_t)s_base[t] + atomicAdd(&s_cnt[t], 1u);
-        if (slot < capacity) entries[slot] = key;
-        else overflow = true;
-      }
+  for (int r0 = 0; r0 < PT; r0 += kGroup) {
+    uint4 rcs[kGroup];
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+      const int64_t q = i0 + (r0 + u) * 256 + threadIdx.x;
+      rcs[u] = q < n ? rect_j[q] : make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+      const uint4 rc = rcs[u];
+      if (rc.x == 0xFFFFFFFFu) continue;
+      const int64_t q = i0 + (r0 + u) * 256 + threadIdx.x;
+      const int tx0 = rc.x & 0xFFFF, ty0 = rc.x >> 16, tx1 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
+      const uint64_t key = ((uint64_t)rc.z << 32) | (uint64_t)order[q];
+      for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx) {
+          const int t = ty * tiles_x + tx;
+          const uint64_t slot = (uint64_t)s_base[t] + atomicAdd(&s_cnt[t], 1u);
+          if (slot < capacity) entries[slot] = key;
+          else overflow = true;
+        }
+    }
   }
   if (overflow) atomicOr(&status->flags, kFlagOverflow);
+}
+
+// ---- processing order: the Gaussians by cell of a 64^3 grid over the scene's bounding box, cells
+// in Morton order. The CTAs of the projection and the scatter take consecutive positions of this
+// order, so that each covers a compact part of the scene and touches few screen tiles (one global
+// atomic per touched tile). Results do not depend on the order. ----
+constexpr int kCellBits = 6;
+constexpr int kCells = 1 << (3 * kCellBits);
+
+// float <-> unsigned key with the same order (finite values)
+__device__ __forceinline__ uint32_t f2key(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key2f(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+// box[0..2] = min keys of x, y, z (initialised to 0xFFFFFFFF), box[3..5] = max keys (initialised to 0),
+// over the finite means
+__global__ void __launch_bounds__(256) k_bounds(const float* __restrict__ means, int64_t n, uint32_t* __restrict__ box) {
+  uint32_t lo[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu}, hi[3] = {0u, 0u, 0u};
+  for (int64_t i = blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+    const float x = means[3 * i], y = means[3 * i + 1], z = means[3 * i + 2];
+    if (!(isfinite(x) && isfinite(y) && isfinite(z))) continue;
+    const uint32_t k[3] = {f2key(x), f2key(y), f2key(z)};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = min(lo[a], k[a]);
+      hi[a] = max(hi[a], k[a]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = __reduce_min_sync(0xFFFFFFFFu, lo[a]);
+    hi[a] = __reduce_max_sync(0xFFFFFFFFu, hi[a]);
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      atomicMin(box + a, lo[a]);
+      atomicMax(box + 3 + a, hi[a]);
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t spread3(uint32_t x) {  // bit b of x to bit 3 b
+  uint32_t r = 0u;
+#pragma unroll
+  for (int b = 0; b < kCellBits; ++b) r |= ((x >> b) & 1u) << (3 * b);
+  return r;
+}
+
+// Morton cell of Gaussian i (cell 0 for a non-finite mean, or before any finite mean was seen)
+__device__ __forceinline__ uint32_t cell_of(const float* __restrict__ means, int64_t i, const uint32_t* __restrict__ box) {
+  uint32_t code = 0u;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float x = means[3 * i + a];
+    if (!isfinite(x) || box[a] > box[3 + a]) return 0u;
+    const float lo = key2f(box[a]), hi = key2f(box[3 + a]);
+    const float t = (hi > lo) ? (x - lo) / (hi - lo) * (float)(1 << kCellBits) : 0.0f;
+    const uint32_t c = (uint32_t)fminf(fmaxf(t, 0.0f), (float)((1 << kCellBits) - 1));
+    code |= spread3(c) << a;
+  }
+  return code;
+}
+
+__global__ void __launch_bounds__(256) k_cell_count(const float* __restrict__ means, int64_t n,
+                                                    const uint32_t* __restrict__ box, uint32_t* __restrict__ count) {
+  const int64_t i = blockIdx.x * (int64_t)256 + threadIdx.x;
+  if (i < n) atomicAdd(count + cell_of(means, i, box), 1u);
+}
+
+__global__ void __launch_bounds__(256) k_cell_place(const float* __restrict__ means, int64_t n,
+                                                    const uint32_t* __restrict__ box, const uint32_t* __restrict__ off,
+                                                    uint32_t* __restrict__ cur, uint32_t* __restrict__ order) {
+  const int64_t i = blockIdx.x * (int64_t)256 + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t cell = cell_of(means, i, box);
+  order[off[cell] + atomicAdd(cur + cell, 1u)] = (uint32_t)i;
+}
+
+// The parameters of the Gaussian at each processing position, packed as three float4:
+// (mean, opacity), (scale, quaternion w), (quaternion x, y, z, 0).
+__global__ void __launch_bounds__(256) k_pack_params(const float* __restrict__ means, const float* __restrict__ scales,
+                                                     const float* __restrict__ quats, const float* __restrict__ opac,
+                                                     const uint32_t* __restrict__ order, int64_t n,
+                                                     float4* __restrict__ packed) {
+  const int64_t q = blockIdx.x * (int64_t)256 + threadIdx.x;
+  if (q >= n) return;
+  const int64_t i = order[q];
+  packed[3 * q] = make_float4(means[3 * i], means[3 * i + 1], means[3 * i + 2], opac[i]);
+  packed[3 * q + 1] = make_float4(scales[3 * i], scales[3 * i + 1], scales[3 * i + 2], quats[4 * i]);
+  packed[3 * q + 2] = make_float4(quats[4 * i + 1], quats[4 * i + 2], quats[4 * i + 3], 0.0f);
 }
 
 // ---- exclusive scan of uint32 counts (reduce, scan the block sums, add) ----
@@ -371,8 +525,10 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_sums(uint32_t* __restrict__
   if (threadIdx.x == 0) {
     const unsigned long long tot = carry;
     *total_out = tot > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)tot;
-    if (tot > status->instances_needed) status->instances_needed = tot;
-    status->instances_total += tot;
+    if (status) {  // the instance counts of a binning pass
+      if (tot > status->instances_needed) status->instances_needed = tot;
+      status->instances_total += tot;
+    }
   }
 }
 
@@ -417,7 +573,7 @@ void launch_project(const Problem& p, const float* means, const float* scales, c
     const int per = (int)std::min<int64_t>(cb, std::max<int64_t>(1, 0x7FFFFFFF / std::max<int64_t>(chunks, 1)));
     for (int j0 = 0; j0 < cb; j0 += per) {
       const int cbl = std::min(per, cb - j0);
-      kern<<<(unsigned)(chunks * cbl), 256, smem, s>>>(means, scales, quats, opac, p.n, ws.cams, j0, cbl, p.width,
+      kern<<<(unsigned)(chunks * cbl), 256, smem, s>>>(ws.packed, ws.order, p.n, ws.cams, j0, cbl, p.width,
                                                        p.height, p.near_z, p.tiles_x, p.tiles, ws.rec, ws.rect,
                                                        ws.tile_off);
       note_launches(1);
@@ -425,7 +581,7 @@ void launch_project(const Problem& p, const float* means, const float* scales, c
     return;
   }
   dim3 grid((unsigned)((p.n + 255) / 256), (unsigned)cb);
-  k_project<<<grid, 256, 0, s>>>(means, scales, quats, opac, p.n, ws.cams, p.width, p.height, p.near_z,
+  k_project<<<grid, 256, 0, s>>>(ws.packed, ws.order, p.n, ws.cams, p.width, p.height, p.near_z,
                                  p.tiles_x, p.tiles, ws.rec, ws.rect, ws.tile_off);
   note_launches(1);
 }
@@ -439,6 +595,27 @@ void launch_scan(const Problem& p, int cb, const Workspace& ws, cudaStream_t s) 
   note_launches(3);
 }
 
+int spatial_cells() { return kCells; }
+
+void launch_spatial_order(const Problem& p, const float* means, const float* scales, const float* quats,
+                          const float* opac, const Workspace& ws, cudaStream_t s) {
+  if (p.n == 0) return;
+  cudaMemsetAsync(ws.cell_box, 0xFF, 3 * sizeof(uint32_t), s);
+  cudaMemsetAsync(ws.cell_box + 3, 0, 3 * sizeof(uint32_t), s);
+  cudaMemsetAsync(ws.cell_off, 0, sizeof(uint32_t) * (size_t)(kCells + 1), s);
+  cudaMemsetAsync(ws.cell_cur, 0, sizeof(uint32_t) * (size_t)kCells, s);
+  const unsigned grid = (unsigned)((p.n + 255) / 256);
+  k_bounds<<<std::min(grid, 152u * 8u), 256, 0, s>>>(means, p.n, ws.cell_box);
+  k_cell_count<<<grid, 256, 0, s>>>(means, p.n, ws.cell_box, ws.cell_off);
+  const int nblocks = (kCells + kScanBlock - 1) / kScanBlock;
+  k_scan_reduce<<<nblocks, kScanBlock, 0, s>>>(ws.cell_off, kCells, ws.cell_tmp);
+  k_scan_sums<<<1, kScanBlock, 0, s>>>(ws.cell_tmp, nblocks, nullptr, ws.cell_off + kCells);
+  k_scan_apply<<<nblocks, kScanBlock, 0, s>>>(ws.cell_off, kCells, ws.cell_tmp);
+  k_cell_place<<<grid, 256, 0, s>>>(means, p.n, ws.cell_box, ws.cell_off, ws.cell_cur, ws.order);
+  k_pack_params<<<grid, 256, 0, s>>>(means, scales, quats, opac, ws.order, p.n, ws.packed);
+  note_launches(7);
+}
+
 void launch_scatter(const Problem& p, int cb, const Workspace& ws, cudaStream_t s) {
   if (p.tiles <= kHistTiles) {
     const size_t smem = 2 * sizeof(uint32_t) * (size_t)p.tiles;
@@ -447,13 +624,13 @@ void launch_scatter(const Problem& p, int cb, const Workspace& ws, cudaStream_t 
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int per_cta = hist_per_cta(big ? 16 : 4);
     dim3 grid((unsigned)((p.n + per_cta - 1) / per_cta), (unsigned)cb);
-    kern<<<grid, 256, smem, s>>>(p.n, ws.rect, p.tiles_x, p.tiles, ws.tile_off, ws.tile_cur, ws.entries, p.capacity,
-                                 ws.status);
+    kern<<<grid, 256, smem, s>>>(p.n, ws.rect, ws.order, p.tiles_x, p.tiles, ws.tile_off, ws.tile_cur, ws.entries,
+                                 p.capacity, ws.status);
     note_launches(1);
     return;
   }
   dim3 grid((unsigned)((p.n + 255) / 256), (unsigned)cb);
-  k_scatter<<<grid, 256, 0, s>>>(p.n, ws.rect, p.tiles_x, p.tiles, ws.tile_off, ws.tile_cur,
+  k_scatter<<<grid, 256, 0, s>>>(p.n, ws.rect, ws.order, p.tiles_x, p.tiles, ws.tile_off, ws.tile_cur,
                                  ws.entries, p.capacity, ws.status);
   note_launches(1);
 }
