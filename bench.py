@@ -504,6 +504,8 @@ def measure(name, args, world, dev, icgs, with_e2e, with_cpu):
 
     # ---- end to end through the C ABI with host buffers (icgs_colorize_host) ----
     if with_e2e:
+        old_cpus = bind_gpu_local_cpus(dev)
+        local_cpus = host_cpus()
         host_t = torch.empty(targets.shape, dtype=targets.dtype, pin_memory=True)
         host_t.copy_(targets)
         host_c = torch.empty((scene.n, B, K), dtype=torch.float32, pin_memory=True)
@@ -514,8 +516,16 @@ def measure(name, args, world, dev, icgs, with_e2e, with_cpu):
 
         e2e_step()
         e2e_ms = timed(e2e_step, args.steps) / args.steps
+        # the pinned-to-device copy rate the end-to-end figure rests on (one plain copy of the targets)
+        scratch = torch.empty_like(targets)
+        scratch.copy_(host_t, non_blocking=True)
+        copy_ms = timed(lambda: scratch.copy_(host_t, non_blocking=True), 2) / 2
+        del scratch
         rec["e2e"] = {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": target_bytes,
-                      "d2h_bytes_per_step": scene.n * B * K * 4 + scene.n, "call": "icgs_colorize_host"}
+                      "d2h_bytes_per_step": scene.n * B * K * 4 + scene.n, "call": "icgs_colorize_host",
+                      "h2d_copy_gbs": target_bytes / copy_ms / 1e6, "host_cpus": local_cpus}
+        if old_cpus is not None:
+            os.sched_setaffinity(0, old_cpus)
         del host_t, host_c, host_s
 
     # ---- relight extras: the adjoint (dL/dt, dL/do for L = sum r c^2) and refinement steps ----
@@ -550,6 +560,38 @@ def measure(name, args, world, dev, icgs, with_e2e, with_cpu):
     del targets
     torch.cuda.empty_cache()
     return rec
+
+
+def bind_gpu_local_cpus(dev):
+    """Runs this process on the host CPUs attached to the GPU (the PCI device's local_cpulist), so
+    that pinned host memory allocated now lies next to it and host-to-device copies do not cross
+    sockets. Returns the previous CPU set (to restore), or None where the system does not expose
+    the list."""
+    import torch
+    try:
+        old = os.sched_getaffinity(0)
+        pr = torch.cuda.get_device_properties(dev)
+        bus = "%04x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        with open(f"/sys/bus/pci/devices/{bus}/local_cpulist") as fh:
+            spec = fh.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+        cpus &= old
+        if cpus:
+            os.sched_setaffinity(0, cpus)
+            return old
+    except (OSError, ValueError, AttributeError):
+        pass
+    return None
+
+
+def host_cpus():
+    try:
+        return len(os.sched_getaffinity(0))
+    except OSError:
+        return None
 
 
 def run_profile_step(args, dev, icgs):

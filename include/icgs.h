@@ -350,14 +350,13 @@ ICGS_API void icgs_debug_tc_wait(int64_t limit_ns, int32_t issue_mma);
 /* Diagnostic: the depth sort of the tile lists (the "depth ordered list" of Eq. 2) as the colorize
  * calls run it. tile_off: device uint32 [ntiles + 1], non-decreasing from 0, delimits the lists in
  * keys; keys: device uint64 [nkeys], each (float32 depth bits << 32) | Gaussian index with a
- * positive finite depth, unique within its list. all != 0 sorts every list ascending in place;
- * all == 0 only the lists longer than 1024 keys (the ones the CUDA-core walks leave to the
- * separate sort). Keys past nkeys are not touched (a list is cut at nkeys). workspace: device,
- * 256-byte aligned, at least icgs_sort_workspace_size(ntiles, nkeys) bytes (else
- * ICGS_ERR_WORKSPACE_TOO_SMALL). Synchronises `stream`. */
+ * positive finite depth, unique within its list. Every list is sorted ascending in place; keys
+ * past nkeys are not touched (a list is cut at nkeys). workspace: device, 256-byte aligned, at
+ * least icgs_sort_workspace_size(ntiles, nkeys) bytes (else ICGS_ERR_WORKSPACE_TOO_SMALL).
+ * Synchronises `stream`. */
 ICGS_API size_t icgs_sort_workspace_size(int32_t ntiles, int64_t nkeys);
 ICGS_API icgs_status icgs_sort_tile_lists(const uint32_t* tile_off, uint64_t* keys, int32_t ntiles, int64_t nkeys,
-                                          int32_t all, void* workspace, size_t workspace_bytes, void* stream);
+                                          void* workspace, size_t workspace_bytes, void* stream);
 
 /* Message of the last failed call on this host thread ("" if none). */
 ICGS_API const char* icgs_last_error(void);

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -286,11 +287,9 @@ icgs_status upload_common(const Problem& p, const icgs_cameras* cams, const floa
   return ICGS_OK;
 }
 
-// sort_all: every tile list is ordered in global memory (the tensor-core walk reads them there);
-// otherwise only the long lists are, and the CUDA-core walks sort the rest in shared memory.
-// first: the call's first pass, which also computes the Gaussians' processing order.
-icgs_status bin_pass(const Problem& p, const icgs_scene* sc, int cb, bool sort_all, bool first, const Workspace& wp,
-                     cudaStream_t s) {
+// Projection, binning and the depth sort of every tile list (the walks read the sorted lists from
+// global memory). first: the call's first pass, which also computes the Gaussians' processing order.
+icgs_status bin_pass(const Problem& p, const icgs_scene* sc, int cb, bool first, const Workspace& wp, cudaStream_t s) {
   const int64_t ct = (int64_t)cb * p.tiles;
   if (first) launch_spatial_order(p, sc->means, sc->scales, sc->quats, sc->opacity, wp, s);
   ICGS_TRY_CUDA(cudaMemsetAsync(wp.tile_off, 0, sizeof(uint32_t) * (size_t)(ct + 1), s));
@@ -301,7 +300,7 @@ icgs_status bin_pass(const Problem& p, const icgs_scene* sc, int cb, bool sort_a
   g_timer.mark(kScan, s);
   launch_scatter(p, cb, wp, s);
   g_timer.mark(kScatter, s);
-  launch_tile_sort(p, cb, sort_all, wp, s);
+  launch_tile_sort(p, cb, wp, s);
   g_timer.mark(kSort, s);
   return ICGS_OK;
 }
@@ -432,7 +431,7 @@ static icgs_status colorize_impl(const icgs_scene* scene, const icgs_cameras* ca
     wp.cams = ws.cams + cam0;
     if (p.L > 0)
       ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)cb * (size_t)p.n * p.acc_stride, s));
-    if ((st = bin_pass(p, scene, cb, tc_accumulate_applies(p, (int)targets->dtype), cam0 == 0, wp, s)) != ICGS_OK) return st;
+    if ((st = bin_pass(p, scene, cb, cam0 == 0, wp, s)) != ICGS_OK) return st;
     launch_blend_accumulate(p, cb, cam0, targets->data, (int)targets->dtype, nullptr, wp, s);
     g_timer.mark(kBlend, s);
     if (p.L > 0) {
@@ -524,13 +523,11 @@ icgs_status icgs_colorize_sets(const icgs_scene* scene, const icgs_cameras* cams
   const Workspace ws = carve(base, p, kNeedAccumulate);
   float* set_acc[kMaxSets];
   Problem ps[kMaxSets];
-  bool any_tc = false;
   for (int k = 0, col0 = 0; k < n_sets; col0 += sets[k].channels, ++k) {
     set_acc[k] = reinterpret_cast<float*>(base + base_bytes + offs[k]);
     ps[k] = p;
     ps[k].K = sets[k].channels;
     ps[k].acc_stride = acc_stride_of(sets[k].channels);
-    any_tc = any_tc || tc_accumulate_applies(ps[k], (int)sets[k].dtype);
   }
   if (p.n == 0) return ICGS_OK;
   if ((st = upload_common(p, cams, lam, ws, s)) != ICGS_OK) return st;
@@ -550,7 +547,7 @@ icgs_status icgs_colorize_sets(const icgs_scene* scene, const icgs_cameras* cams
     Workspace wp = ws;
     wp.cams = ws.cams + cam0;
     if (p.L > 0 && (st = zero_accs((int64_t)cb * p.n)) != ICGS_OK) return st;
-    if ((st = bin_pass(p, scene, cb, any_tc, cam0 == 0, wp, s)) != ICGS_OK) return st;  // one binning for every set
+    if ((st = bin_pass(p, scene, cb, cam0 == 0, wp, s)) != ICGS_OK) return st;  // one binning for every set
     for (int k = 0; k < n_sets; ++k) {
       Workspace wk = wp;
       wk.acc = set_acc[k];
@@ -693,7 +690,7 @@ icgs_status icgs_colorize_host(const icgs_scene* scene, const icgs_cameras* cams
     if (p.L > 0)
       ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)cb * (size_t)p.n * p.acc_stride, s));
     // projection, binning and sorting need no targets: they run while the first chunks arrive
-    if ((st = bin_pass(p, scene, cb, tc_accumulate_applies(p, dtype), cam0 == 0, wp, s)) != ICGS_OK) return st;
+    if ((st = bin_pass(p, scene, cb, cam0 == 0, wp, s)) != ICGS_OK) return st;
     for (; chunk < chunk_cam0.size() && chunk_cam0[chunk] < cam0 + cb; ++chunk) {
       const int j0 = chunk_cam0[chunk] - cam0, jc = chunk_n[chunk];
       ICGS_TRY_CUDA(cudaStreamWaitEvent(s, hp->ready[chunk], 0));
@@ -752,7 +749,7 @@ icgs_status icgs_accumulate(const icgs_scene* scene, const icgs_cameras* cams, c
     wp.cams = ws.cams + cam0;
     if (p.L > 0)
       ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)cb * (size_t)p.n * p.acc_stride, s));
-    if ((st = bin_pass(p, scene, cb, tc_accumulate_applies(p, (int)targets->dtype), cam0 == 0, wp, s)) != ICGS_OK) return st;
+    if ((st = bin_pass(p, scene, cb, cam0 == 0, wp, s)) != ICGS_OK) return st;
     launch_blend_accumulate(p, cb, cam0, targets->data, (int)targets->dtype, nullptr, wp, s);
     g_timer.mark(kBlend, s);
     if (p.L > 0) {
@@ -893,7 +890,7 @@ static icgs_status backward_impl(const icgs_scene* scene, const icgs_cameras* ca
     const int cb = std::min(p.cam_batch, p.n_cams - cam0);
     Workspace wp = ws;
     wp.cams = ws.cams + cam0;
-    if ((st = bin_pass(p, scene, cb, false, cam0 == 0, wp, s)) != ICGS_OK) return st;
+    if ((st = bin_pass(p, scene, cb, cam0 == 0, wp, s)) != ICGS_OK) return st;
     launch_payload_adjoint(p, scene->means, coeffs, cb, wp, s);
     g_timer.mark(kPayload, s);
     launch_blend_adjoint(p, cb, cam0, targets->data, (int)targets->dtype, wp, grad_targets, grad_opacity != nullptr, s);
@@ -949,7 +946,7 @@ static icgs_status refine_impl(const icgs_scene* scene, const icgs_cameras* cams
       if (p.L > 0)
         ICGS_TRY_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(float) * (size_t)cb * (size_t)p.n * p.acc_stride, s));
       if (!(one_pass && step > 0))
-        if ((st = bin_pass(p, scene, cb, false, step == 0 && cam0 == 0, wp, s)) != ICGS_OK) return st;
+        if ((st = bin_pass(p, scene, cb, step == 0 && cam0 == 0, wp, s)) != ICGS_OK) return st;
       launch_payload_render(p, scene->means, coeffs_inout, cb, wp, s);  // Alg. 1 line 8: render
       if (launch_blend_refine(p, cb, cam0, targets->data, (int)targets->dtype, wp, s)) {  // lines 8-9, one walk
         g_timer.mark(kPayload, s);
@@ -1005,7 +1002,7 @@ static icgs_status render_impl(const icgs_scene* scene, const icgs_cameras* cams
     const int cb = std::min(p.cam_batch, p.n_cams - cam0);
     Workspace wp = ws;
     wp.cams = ws.cams + cam0;
-    if ((st = bin_pass(p, scene, cb, false, cam0 == 0, wp, s)) != ICGS_OK) return st;
+    if ((st = bin_pass(p, scene, cb, cam0 == 0, wp, s)) != ICGS_OK) return st;
     launch_payload_render(p, scene->means, coeffs, cb, wp, s);
     g_timer.mark(kPayload, s);
     launch_blend_render(p, cb, cam0, wp, images_out, s);
@@ -1108,7 +1105,7 @@ size_t icgs_sort_workspace_size(int32_t ntiles, int64_t nkeys) {
          align256(sizeof(uint64_t) * (size_t)nkeys);
 }
 
-icgs_status icgs_sort_tile_lists(const uint32_t* tile_off, uint64_t* keys, int32_t ntiles, int64_t nkeys, int32_t all,
+icgs_status icgs_sort_tile_lists(const uint32_t* tile_off, uint64_t* keys, int32_t ntiles, int64_t nkeys,
                                  void* workspace, size_t workspace_bytes, void* stream) {
   g_err[0] = '\0';
   if (ntiles < 0 || nkeys < 0) return fail(ICGS_ERR_INVALID_ARG, "ntiles = %d and nkeys = %lld must be >= 0", ntiles, (long long)nkeys);
@@ -1131,7 +1128,7 @@ icgs_status icgs_sort_tile_lists(const uint32_t* tile_off, uint64_t* keys, int32
   p.capacity = (uint32_t)nkeys;
   ICGS_TRY_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(DevStatus), s));
   g_launches = 0;
-  if (ntiles > 0) launch_tile_sort(p, 1, all != 0, ws, s);
+  if (ntiles > 0) launch_tile_sort(p, 1, ws, s);
   return finish(ws, s);
 }
 

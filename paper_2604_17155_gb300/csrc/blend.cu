@@ -87,9 +87,8 @@ __global__ void __launch_bounds__(kThreads, KC <= 8 ? 5 : 4) k_blend_accumulate(
   __shared__ float2 s_half[kBatch];
   __shared__ uint32_t s_id[kBatch];
   __shared__ float s_acc[kBatch][NV];
-  __shared__ unsigned long long s_keys[kWalkSortCap];
   const TileCtx c = tile_ctx(tile_off, capacity, tiles, tiles_x, width, height);
-  const unsigned long long* list = stage_tile_list(entries, c.b, c.len, s_keys);
+  const unsigned long long* list = tile_list(entries, c.b);
   const int lane = threadIdx.x & 31;
   float tv[KC];
 #pragma unroll
@@ -208,9 +207,8 @@ __global__ void __launch_bounds__(kThreads2, 10) k_blend_accumulate2(
   __shared__ float2 s_half[kBatch];
   __shared__ uint32_t s_id[kBatch];
   __shared__ float s_acc[kBatch][NV];
-  __shared__ unsigned long long s_keys[kWalkSortCap];
   const TileCtx c = tile_ctx<2>(tile_off, capacity, tiles, tiles_x, width, height);
-  const unsigned long long* list = stage_tile_list<kThreads2>(entries, c.b, c.len, s_keys);
+  const unsigned long long* list = tile_list(entries, c.b);
   const int lane = threadIdx.x & 31;
   const bool inside1 = c.inside && c.py + 4 < height;
   const float pyf1 = c.pyf + 4.0f;
@@ -346,9 +344,8 @@ __global__ void __launch_bounds__(kThreads) k_blend_render(
   __shared__ float2 s_half[kBatch];
   __shared__ uint32_t s_id[kBatch];
   __shared__ float s_col[kBatch][KC];
-  __shared__ unsigned long long s_keys[kWalkSortCap];
   const TileCtx c = tile_ctx(tile_off, capacity, tiles, tiles_x, width, height);
-  const unsigned long long* list = stage_tile_list(entries, c.b, c.len, s_keys);
+  const unsigned long long* list = tile_list(entries, c.b);
   const ProjRec* rec_cam = rec + (int64_t)c.j * n;
   const float* pay_cam = payload + (int64_t)c.j * n * K;
   float img[KC];
@@ -406,9 +403,8 @@ __global__ void __launch_bounds__(kThreads2, 10) k_blend_render2(
   __shared__ float2 s_half[kBatch];
   __shared__ uint32_t s_id[kBatch];
   __shared__ float s_col[kBatch][KC];
-  __shared__ unsigned long long s_keys[kWalkSortCap];
   const TileCtx c = tile_ctx<2>(tile_off, capacity, tiles, tiles_x, width, height);
-  const unsigned long long* list = stage_tile_list<kThreads2>(entries, c.b, c.len, s_keys);
+  const unsigned long long* list = tile_list(entries, c.b);
   const bool inside1 = c.inside && c.py + 4 < height;
   const float pyf1 = c.pyf + 4.0f;
   const ProjRec* rec_cam = rec + (int64_t)c.j * n;
@@ -500,9 +496,8 @@ __global__ void __launch_bounds__(kThreads, KC <= 4 ? 6 : (KC <= 16 ? 4 : (KC <=
   __shared__ uint32_t s_id[kBatch];
   __shared__ float s_pay[kBatch][KC + 1];
   __shared__ float s_go[kBatch];
-  __shared__ unsigned long long s_keys[kWalkSortCap];
   const TileCtx c = tile_ctx(tile_off, capacity, tiles, tiles_x, width, height);
-  const unsigned long long* list = stage_tile_list(entries, c.b, c.len, s_keys);
+  const unsigned long long* list = tile_list(entries, c.b);
   const int lane = threadIdx.x & 31;
   const ProjRec* rec_cam = rec + (int64_t)c.j * n;
   const float* pay_cam = payload + (int64_t)c.j * n * (K + 1);
@@ -675,9 +670,8 @@ __global__ void __launch_bounds__(kThreads2, KC <= 2 ? 10 : 8) k_blend_adjoint2(
   __shared__ uint32_t s_id[kBatch];
   __shared__ float s_pay[kBatch][KC + 1];
   __shared__ float s_go[kBatch];
-  __shared__ unsigned long long s_keys[kWalkSortCap];
   const TileCtx c = tile_ctx<2>(tile_off, capacity, tiles, tiles_x, width, height);
-  const unsigned long long* list = stage_tile_list<kThreads2>(entries, c.b, c.len, s_keys);
+  const unsigned long long* list = tile_list(entries, c.b);
   const int lane = threadIdx.x & 31;
   const bool inside1 = c.inside && c.py + 4 < height;
   const float pyf1 = c.pyf + 4.0f;
@@ -812,9 +806,8 @@ __global__ void __launch_bounds__(kThreads2, 10) k_blend_refine2(
   __shared__ uint32_t s_id[kBatch];
   __shared__ float s_acc[kBatch][NV];
   __shared__ float s_col[kBatch][KC];
-  __shared__ unsigned long long s_keys[kWalkSortCap];
   const TileCtx c = tile_ctx<2>(tile_off, capacity, tiles, tiles_x, width, height);
-  const unsigned long long* list = stage_tile_list<kThreads2>(entries, c.b, c.len, s_keys);
+  const unsigned long long* list = tile_list(entries, c.b);
   const int lane = threadIdx.x & 31;
   const bool inside1 = c.inside && c.py + 4 < height;
   const float pyf1 = c.pyf + 4.0f;

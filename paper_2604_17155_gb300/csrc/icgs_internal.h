@@ -131,7 +131,7 @@ int spatial_cells();
 void launch_spatial_order(const Problem& p, const float* means, const float* scales, const float* quats,
                           const float* opac, const Workspace& ws, cudaStream_t s);
 void launch_scatter(const Problem& p, int cb, const Workspace& ws, cudaStream_t s);
-void launch_tile_sort(const Problem& p, int cb, bool sort_all, const Workspace& ws, cudaStream_t s);
+void launch_tile_sort(const Problem& p, int cb, const Workspace& ws, cudaStream_t s);
 // sub_img (nullable, float32 [cb,H,W,K] of this pass's cameras): accumulate t - img instead of t
 // (refinement); forces the CUDA-core walk.
 bool launch_blend_refine(const Problem& p, int cb, int cam0, const void* targets, int dtype, const Workspace& ws,

@@ -2,19 +2,16 @@
 //
 // After binning, each tile owns a contiguous slot range of 64-bit keys (float32 depth bits << 32 |
 // Gaussian index); the keys are unique, so sorting them ascending gives depth order with ties in
-// index order. Every sort here is the stable LSD radix sort of radix.cuh, in shared memory.
-// For the tensor-core walk every list is sorted here: lists of up to kWarpSortCap keys by a
+// index order. Every sort here is the stable LSD radix sort of radix.cuh, in shared memory, and
+// every list of a pass is sorted before the walks read it: lists of up to kWarpSortCap keys by a
 // persistent kernel in which each warp sorts one tile at a time (k_sort_tiles, no CTA barrier),
-// longer lists queued. The CUDA-core walks sort lists of up to kWalkSortCap keys themselves; the
-// longer ones are queued (k_queue_tiles). Queued lists go to a persistent kernel with one CTA per
-// list (k_sort_queued): up to kSortCap keys by the block radix sort at once, longer lists as sorted
-// runs of kSortCap keys followed by merge-path merges between the slot range and a scratch range
-// of the same place.
+// longer lists queued for a persistent kernel with one CTA per list (k_sort_queued): up to
+// kSortCap keys by the block radix sort at once, longer lists as sorted runs of kSortCap keys
+// followed by merge-path merges between the slot range and a scratch range of the same place.
 #include <cuda_runtime.h>
 
 #include "icgs_internal.h"
 #include "radix.cuh"
-#include "walk.cuh"
 
 namespace icgs {
 
@@ -35,28 +32,6 @@ __device__ __forceinline__ void tile_range(const uint32_t* tile_off, int t, uint
   b = min(tile_off[t], capacity);
   e = min(tile_off[t + 1], capacity);
   if (e < b) e = b;
-}
-
-// Queues every tile whose list has more than min_len keys (one thread per tile; one counter
-// atomic per warp).
-__global__ void __launch_bounds__(kSortThreads) k_queue_tiles(const uint32_t* __restrict__ tile_off, int ntiles,
-                                                              uint32_t capacity, int min_len,
-                                                              uint32_t* __restrict__ queue, DevStatus* status) {
-  const int t = blockIdx.x * kSortThreads + threadIdx.x;
-  bool want = false;
-  if (t < ntiles) {
-    uint32_t b, e;
-    tile_range(tile_off, t, capacity, b, e);
-    const uint32_t n = e - b;
-    want = n > 1u && n > (uint32_t)min_len;
-  }
-  const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, want);
-  if (!ballot) return;  // uniform per warp
-  const int lane = threadIdx.x & 31;
-  uint32_t base = 0;
-  if (lane == 0) base = atomicAdd(&status->big_tiles, (uint32_t)__popc(ballot));
-  base = __shfl_sync(0xFFFFFFFFu, base, 0);
-  if (want) queue[base + __popc(ballot & ((1u << lane) - 1u))] = (uint32_t)t;
 }
 
 // Every tile list of the pass, by warps that claim kWarpSortChunk tiles at a time from the work
@@ -184,25 +159,18 @@ int sm_count() {
 
 }  // namespace
 
-// sort_all: order every tile list here (walks that read the lists from global memory). Otherwise
-// only the lists longer than the walks' shared-memory sort (kWalkSortCap) are queued and sorted.
-void launch_tile_sort(const Problem& p, int cb, bool sort_all, const Workspace& ws, cudaStream_t s) {
-  static_assert(kWarpSortCap == walk::kWalkSortCap, "both paths queue the lists longer than 1024 keys");
+// Orders every tile list of the pass: the warp-per-list kernel, then the queued long lists.
+void launch_tile_sort(const Problem& p, int cb, const Workspace& ws, cudaStream_t s) {
   const int ntiles = cb * p.tiles;
   const int sms = sm_count();
   cudaMemsetAsync(&ws.status->big_tiles, 0, 2 * sizeof(uint32_t), s);  // big_tiles, sort_next
-  if (sort_all) {
-    const int smem = kWarpSortWarps * (int)sizeof(WarpSortSmem);
-    cudaFuncSetAttribute(k_sort_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_tiles, 32 * kWarpSortWarps, smem);
-    const int grid = sms * (per_sm > 0 ? per_sm : 1);
-    k_sort_tiles<<<grid, 32 * kWarpSortWarps, smem, s>>>(ws.tile_off, reinterpret_cast<unsigned long long*>(ws.entries),
-                                                         p.capacity, ntiles, ws.big_list, ws.status);
-  } else {
-    k_queue_tiles<<<(ntiles + kSortThreads - 1) / kSortThreads, kSortThreads, 0, s>>>(
-        ws.tile_off, ntiles, p.capacity, walk::kWalkSortCap, ws.big_list, ws.status);
-  }
+  const int smem = kWarpSortWarps * (int)sizeof(WarpSortSmem);
+  cudaFuncSetAttribute(k_sort_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_tiles, 32 * kWarpSortWarps, smem);
+  const int grid = sms * (per_sm > 0 ? per_sm : 1);
+  k_sort_tiles<<<grid, 32 * kWarpSortWarps, smem, s>>>(ws.tile_off, reinterpret_cast<unsigned long long*>(ws.entries),
+                                                       p.capacity, ntiles, ws.big_list, ws.status);
   const int qsmem = 2 * kSortCap * (int)sizeof(unsigned long long);
   cudaFuncSetAttribute(k_sort_queued, cudaFuncAttributeMaxDynamicSharedMemorySize, qsmem);
   k_sort_queued<<<sms * 2, kSortThreads, qsmem, s>>>(ws.tile_off, reinterpret_cast<unsigned long long*>(ws.entries),

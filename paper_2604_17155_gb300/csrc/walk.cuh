@@ -61,156 +61,11 @@ __device__ __forceinline__ TileCtx tile_ctx(const uint32_t* tile_off, uint32_t c
   return c;
 }
 
-// Ascending bitonic sort of s[0, P) (P a power of two) by the NT threads of the CTA; the pair
-// indices are formed with shifts and masks (the strides are powers of two).
-template <int NT>
-__device__ __forceinline__ void bitonic_sort_smem(unsigned long long* s, int P) {
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int jj = k >> 1; jj > 0; jj >>= 1) {
-      for (int t = threadIdx.x; t < (P >> 1); t += NT) {
-        const int i = ((t & ~(jj - 1)) << 1) | (t & (jj - 1));
-        const int l = i + jj;
-        const unsigned long long a = s[i], b = s[l];
-        if ((a > b) == ((i & k) == 0)) {
-          s[i] = b;
-          s[l] = a;
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
-constexpr int kWalkSortCap = 1024;  // tile lists up to this length are sorted inside the walk
-
-// Keeps min or max of (a, partner) so that element i ends up ordered against element i ^ jj in a
-// bitonic merge of span k.
-__device__ __forceinline__ unsigned long long cmpx_keep(unsigned long long a, unsigned long long partner, int i,
-                                                        int jj, int k) {
-  const bool lower = (i & jj) == 0, up = (i & k) == 0;
-  const unsigned long long mn = a < partner ? a : partner, mx = a < partner ? partner : a;
-  return (lower == up) ? mn : mx;
-}
-
-// Ascending bitonic sort of P = NT * E keys (E = 1, 2, 4, 8, 16; with E = 1, P may be smaller) by
-// the NT threads of the CTA, thread t holding keys t, t + NT, ..., t + NT (E-1) in v. Strides of NT
-// or more are compare-exchanges inside a thread, strides below 32 are warp shuffles, and only
-// strides 32..NT/2 go through shared memory (s, P keys), so a 256-key sort by 256 threads has 6
-// barrier-separated stages instead of 36. On return s holds the sorted keys.
-template <int E, int NT = kThreads>
-__device__ __forceinline__ void block_bitonic_sort(unsigned long long (&v)[E], unsigned long long* s, int P) {
-  const int t = threadIdx.x;
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int jj = k >> 1; jj > 0; jj >>= 1) {
-      if (jj >= NT) {
-#pragma unroll
-        for (int m = 1; m < E; m <<= 1) {  // m = jj / NT, unrolled so that v is indexed statically
-          if (m * NT != jj) continue;
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            const int pe = e ^ m;
-            if (pe > e) {
-              const int i = e * NT + t;
-              const unsigned long long a = v[e], b = v[pe];
-              const bool up = (i & k) == 0;
-              const bool swap = (a > b) == up;
-              v[e] = swap ? b : a;
-              v[pe] = swap ? a : b;
-            }
-          }
-        }
-      } else if (jj >= 32) {
-#pragma unroll
-        for (int e = 0; e < E; ++e) s[e * NT + t] = v[e];
-        __syncthreads();
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int i = e * NT + t;
-          v[e] = cmpx_keep(v[e], s[i ^ jj], i, jj, k);
-        }
-        __syncthreads();
-      } else {
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int i = e * NT + t;
-          v[e] = cmpx_keep(v[e], __shfl_xor_sync(kFull, v[e], jj), i, jj, k);
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int e = 0; e < E; ++e) s[e * NT + t] = v[e];
-  __syncthreads();
-}
-
-template <int E>
-__device__ __forceinline__ void sort_into_smem(const unsigned long long* g, uint32_t len, unsigned long long* s,
-                                               int P) {
-  unsigned long long v[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int i = e * kThreads + (int)threadIdx.x;
-    v[e] = i < (int)len ? g[i] : ~0ull;
-  }
-  block_bitonic_sort<E>(v, s, P);
-}
-
-// Sorts the len (<= 256 * MAXE) keys at g into s[0, len) (ascending); callable by all threads.
-// Lists of up to 256 keys take the plain network padded to the next power of two (short lists
-// are the common case and pay for fewer stages); longer ones take block_bitonic_sort.
-template <int MAXE>
-__device__ __forceinline__ void sort_keys_block(const unsigned long long* g, uint32_t len, unsigned long long* s) {
-  if (len <= (uint32_t)kThreads) {  // one key per thread (threads t >= P sort padding)
-    int P = 32;
-    while (P < (int)len) P <<= 1;
-    unsigned long long v[1];
-    v[0] = threadIdx.x < len ? g[threadIdx.x] : ~0ull;
-    block_bitonic_sort<1>(v, s, P);
-    return;
-  }
-  int P = kThreads;
-  while (P < (int)len) P <<= 1;
-  const int E = P / kThreads;
-  if (E == 1) sort_into_smem<1>(g, len, s, P);
-  else if (E == 2 || MAXE == 2) sort_into_smem<(MAXE < 2 ? 1 : 2)>(g, len, s, P);
-  else if (E == 4 || MAXE == 4) sort_into_smem<(MAXE < 4 ? 1 : 4)>(g, len, s, P);
-  else if (E == 8 || MAXE == 8) sort_into_smem<(MAXE < 8 ? 1 : 8)>(g, len, s, P);
-  else sort_into_smem<(MAXE < 16 ? 1 : 16)>(g, len, s, P);
-}
-
-// The tile's depth-ordered list: sorted here into shared memory when it fits, else the global
-// slot range that the long-list sort has already ordered. Keys are unique ((depth bits << 32) |
-// index), so the ascending order is depth order with ties in index order.
-template <int NT = kThreads>
-__device__ __forceinline__ const unsigned long long* stage_tile_list(const uint64_t* __restrict__ entries,
-                                                                     uint32_t b, uint32_t len,
-                                                                     unsigned long long* s_keys) {
-  const unsigned long long* g = reinterpret_cast<const unsigned long long*>(entries) + b;
-  if (len > (uint32_t)kWalkSortCap) return g;  // uniform
-  if (len <= (uint32_t)NT) {
-    // one key per thread: strides below 32 by shuffles, 32..NT/2 through shared memory (at most 6
-    // barrier-separated stages for 256 keys). Threads t >= P sort padding among themselves.
-    int P = 32;
-    while (P < (int)len) P <<= 1;
-    unsigned long long v[1];
-    v[0] = threadIdx.x < len ? g[threadIdx.x] : ~0ull;
-    block_bitonic_sort<1, NT>(v, s_keys, P);
-    return s_keys;
-  }
-  if (NT < kThreads && len <= 2u * (uint32_t)NT) {  // small CTAs: two keys per thread
-    unsigned long long v[2];
-    v[0] = g[threadIdx.x];
-    v[1] = threadIdx.x + NT < len ? g[threadIdx.x + NT] : ~0ull;
-    block_bitonic_sort<2, NT>(v, s_keys, 2 * NT);
-    return s_keys;
-  }
-  // longer lists: the plain network (a register-blocked one would cost the walk registers)
-  int P = 2;
-  while (P < (int)len) P <<= 1;
-  for (int k = threadIdx.x; k < P; k += NT) s_keys[k] = k < (int)len ? g[k] : ~0ull;
-  __syncthreads();
-  bitonic_sort_smem<NT>(s_keys, P);
-  return s_keys;
+// The tile's depth-ordered list: its slot range in global memory, sorted by the tile sort before
+// the walk. Keys are unique ((depth bits << 32) | index), so the ascending order is depth order
+// with ties in index order.
+__device__ __forceinline__ const unsigned long long* tile_list(const uint64_t* __restrict__ entries, uint32_t b) {
+  return reinterpret_cast<const unsigned long long*>(entries) + b;
 }
 
 // A Gaussian of the current batch as the walk evaluates it, staged in shared memory:

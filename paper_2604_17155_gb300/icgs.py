@@ -135,7 +135,7 @@ def load(path: str = LIB_PATH):
     lib.icgs_debug_tc_wait.restype = None
     lib.icgs_sort_workspace_size.argtypes = [ctypes.c_int32, ctypes.c_int64]
     lib.icgs_sort_workspace_size.restype = S
-    lib.icgs_sort_tile_lists.argtypes = [P, P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, P, S, P]
+    lib.icgs_sort_tile_lists.argtypes = [P, P, ctypes.c_int32, ctypes.c_int64, P, S, P]
     lib.icgs_sort_tile_lists.restype = ctypes.c_int
     lib.icgs_set_stage_timing.argtypes = [ctypes.c_int]
     lib.icgs_set_stage_timing.restype = None
@@ -649,10 +649,10 @@ def selftest_tc(A, B, bf16=True, lanes=False):
     return (D, DL) if lanes else D
 
 
-def sort_tile_lists(tile_off, keys, all_lists=True):
+def sort_tile_lists(tile_off, keys):
     """Diagnostic: the library's depth sort of tile lists, in place. tile_off: int32 CUDA tensor
     [ntiles + 1] (non-decreasing from 0); keys: int64 CUDA tensor, each (float32 depth bits << 32)
-    | Gaussian index. all_lists=False sorts only the lists longer than 1024 keys."""
+    | Gaussian index."""
     lib = load()
     if tile_off.dtype != _torch().int32 or keys.dtype != _torch().int64:
         raise ValueError("tile_off must be int32 and keys int64")
@@ -662,7 +662,7 @@ def sort_tile_lists(tile_off, keys, all_lists=True):
     size = lib.icgs_sort_workspace_size(ntiles, nkeys)
     ws = _ws.get(keys.device, size)
     _check(lib.icgs_sort_tile_lists(ctypes.c_void_p(tile_off.data_ptr()), ctypes.c_void_p(keys.data_ptr()), ntiles,
-                                    nkeys, 1 if all_lists else 0, ctypes.c_void_p(ws.data_ptr()), size,
+                                    nkeys, ctypes.c_void_p(ws.data_ptr()), size,
                                     _stream_ptr(keys.device)))
     return keys
 

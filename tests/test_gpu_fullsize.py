@@ -1,6 +1,6 @@
-"""Parity at the benchmark's full size and launch configuration (relighting-shaped scene:
-200,000 Gaussians, 100 cameras 800x800, L = 3, one pass over all cameras, MIXED precision) on a
-seeded sample of Gaussians. The oracle walks only the pixels inside the sampled Gaussians'
+"""Parity at the benchmarks' full scene sizes and launch configuration (relighting-shaped scene:
+200,000 Gaussians, 100 cameras 800x800, L = 3, one pass over all cameras, MIXED precision; the
+segmentation and feature scenes with a few cameras of their rigs) on a seeded sample of Gaussians. The oracle walks only the pixels inside the sampled Gaussians'
 candidate boxes, which gives their visibility sums V, S exactly (Eq. 5-6), then folds and solves
 them (Eq. 12-14). The targets are smooth synthetic fields from the input generator, so no oracle
 input comes from the CUDA path."""
@@ -91,6 +91,38 @@ def test_masks_fullsize_sampled_tensor_core():
     ref = _sampled_oracle(scene, cams, t_exact, 0, sample)
     rep, err, checked = coefficient_report(c[sample], ref, tol=TOL_BF16)
     print("masks full size (tensor-core walk)", rep, icgs.last_stats())
+    assert rep["checked"] >= 5
+    assert rep["max_checked"] <= TOL_BF16
+    assert rep["bound_excess"] <= 0
+
+
+def test_features_fullsize_sampled_tensor_core():
+    """The tensor-core walk with 64 BF16 channels (MIXED) on the full-size feature scene:
+    1,000,000 Gaussians at 1000x750, here with 4 cameras of the same rig shape. Targets are smooth
+    64-channel fields from the input generator, rounded to BF16 before either side sees them; the
+    oracle walks only the sampled Gaussians' candidate pixels (Eq. 5-6) and solves at L = 0."""
+    from paper_2604_17155_gb300 import build as B
+    B.build()
+    from paper_2604_17155_gb300 import icgs
+    scene = W.make_scene("features", 3000)
+    cams = W.make_cameras("features", n_cams=4)
+    t = W.fourier_fields(cams.n, cams.height, cams.width, 64, seed=3005, n_modes=4)
+    dev = "cuda"
+    gs = icgs.Scene.from_workload(scene, dev)
+    gc = icgs.Cameras.from_workload(cams)
+    tt = torch.tensor(t, device=dev).bfloat16()
+    t_exact = tt.float().cpu().numpy().astype(np.float64)
+    del t
+    c, status, _ = icgs.colorize(gs, gc, tt, 0, precision="mixed")
+    assert icgs.last_stats()["contrib_pairs"] > 0
+    c = to_np(c)
+    st = to_np(status)
+    rng = np.random.default_rng(3006)
+    seen = np.where(st != icgs.GAUSSIAN_UNSEEN)[0]
+    sample = np.sort(rng.choice(seen, N_SAMPLE, replace=False))
+    ref = _sampled_oracle(scene, cams, t_exact, 0, sample)
+    rep, err, checked = coefficient_report(c[sample], ref, tol=TOL_BF16)
+    print("features full size (tensor-core walk)", rep, icgs.last_stats())
     assert rep["checked"] >= 5
     assert rep["max_checked"] <= TOL_BF16
     assert rep["bound_excess"] <= 0

@@ -152,8 +152,9 @@ def test_colorize_channels_and_dtypes(icgs, K, dtype):
 
 def test_exact_refold_of_every_gaussian(icgs):
     """refold_tau > 1 re-folds every seen Gaussian exactly (float-float products and sums) from its
-    resident per-camera sums: every one is counted, and parity with the FP64 oracle is at least as
-    tight as with the default threshold, whose fast fold rounds each product and partial sum."""
+    resident per-camera sums: every one is counted, and parity with the FP64 oracle is as tight as
+    with the default MIXED fold, which is exact as well. The two calls' V and S differ only in the
+    order of the walk's float atomics, so their error percentiles agree to well within 1%."""
     sc, cams = _mid_scene()
     L = 3
     t = O.render(sc, cams, W.sh_coefficients(sc.n, L, 3, seed=13), L).astype(np.float32)
@@ -169,7 +170,7 @@ def test_exact_refold_of_every_gaussian(icgs):
     assert stats["refold"] == int((to_np(s1) != icgs.GAUSSIAN_UNSEEN).sum())
     assert rep1["max_checked"] <= TOL_FP32
     assert rep1["bound_excess"] <= 0
-    assert rep1["p99_checked"] <= rep0["p99_checked"]
+    assert rep1["p99_checked"] <= 1.01 * rep0["p99_checked"]
 
 
 def test_camera_passes_match_single_pass(icgs):
@@ -285,9 +286,9 @@ def _stacked_tile_scene(n, seed):
     return sc, cams, rng
 
 
-# 3 FP32 channels: the CUDA-core walk, which sorts lists of up to 1024 keys itself and leaves longer
-# ones to the queued sort; 16 FP16 channels (MIXED): the tensor-core walk, whose lists are all
-# sorted beforehand. 2,500 keys: one shared-memory network; 9,000: runs plus merge-path merges.
+# 3 FP32 channels: the CUDA-core walk; 16 FP16 channels (MIXED): the tensor-core walk. Both read
+# lists sorted beforehand: 2,500 keys by the block radix sort at once; 9,000: runs plus merge-path
+# merges.
 @pytest.mark.parametrize("K,dtype", [(3, "f32"), (16, "f16")])
 @pytest.mark.parametrize("n", [2500, 9000])
 def test_long_tile_list_sort_paths(icgs, K, dtype, n):

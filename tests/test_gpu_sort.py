@@ -57,27 +57,25 @@ def _lists(seed, lengths, kinds):
     return np.concatenate(keys).view(np.int64), np.array(off, np.int64)
 
 
-def _expected(keys, off, all_lists):
+def _expected(keys, off):
     out = keys.copy()
     for t in range(len(off) - 1):
         b, e = off[t], off[t + 1]
-        if all_lists or e - b > 1024:
-            out[b:e] = np.sort(keys[b:e])
+        out[b:e] = np.sort(keys[b:e])
     return out
 
 
 KINDS = ["uniform", "octaves", "wide", "narrow", "few", "one"]
 
 
-@pytest.mark.parametrize("all_lists", [True, False])
-def test_sort_every_path_bit_exact(icgs, all_lists):
+def test_sort_every_path_bit_exact(icgs):
     lengths = [n for n in LENGTHS for _ in range(len(KINDS))]
-    keys, off = _lists(7 + all_lists, lengths, KINDS)
+    keys, off = _lists(7, lengths, KINDS)
     assert all(len(np.unique(keys[off[t]:off[t + 1]])) == off[t + 1] - off[t] for t in range(len(off) - 1))
     g_keys = torch.tensor(keys, device=DEV)
-    icgs.sort_tile_lists(torch.tensor(off, dtype=torch.int32, device=DEV), g_keys, all_lists=all_lists)
+    icgs.sort_tile_lists(torch.tensor(off, dtype=torch.int32, device=DEV), g_keys)
     got = g_keys.cpu().numpy()
-    exp = _expected(keys, off, all_lists)
+    exp = _expected(keys, off)
     bad = np.nonzero(got != exp)[0]
     assert bad.size == 0, f"{bad.size} keys out of place, first at {bad[:5]}"
 
@@ -90,7 +88,7 @@ def test_sort_many_lists_headline_lengths(icgs):
     keys, off = _lists(12, lengths, KINDS[:5])
     g_keys = torch.tensor(keys, device=DEV)
     icgs.sort_tile_lists(torch.tensor(off, dtype=torch.int32, device=DEV), g_keys)
-    assert np.array_equal(g_keys.cpu().numpy(), _expected(keys, off, True))
+    assert np.array_equal(g_keys.cpu().numpy(), _expected(keys, off))
 
 
 def test_sort_cut_at_key_count(icgs):
@@ -100,7 +98,7 @@ def test_sort_cut_at_key_count(icgs):
     buf = torch.tensor(keys, device=DEV)
     icgs.sort_tile_lists(torch.tensor(off, dtype=torch.int32, device=DEV), buf[:cut])
     got = buf.cpu().numpy()
-    exp = _expected(keys[:cut], np.minimum(off, cut), True)
+    exp = _expected(keys[:cut], np.minimum(off, cut))
     assert np.array_equal(got[:cut], exp)
     assert np.array_equal(got[cut:], keys[cut:])
 
@@ -112,6 +110,6 @@ def test_sort_rejects_small_workspace(icgs):
     keys = torch.zeros(4, dtype=torch.int64, device=DEV)
     need = lib.icgs_sort_workspace_size(2, 4)
     ws = torch.empty(need, dtype=torch.uint8, device=DEV)
-    st = lib.icgs_sort_tile_lists(ctypes.c_void_p(off.data_ptr()), ctypes.c_void_p(keys.data_ptr()), 2, 4, 1,
+    st = lib.icgs_sort_tile_lists(ctypes.c_void_p(off.data_ptr()), ctypes.c_void_p(keys.data_ptr()), 2, 4,
                                   ctypes.c_void_p(ws.data_ptr()), need - 1, None)
     assert st == icgs.ERR_WORKSPACE_TOO_SMALL
