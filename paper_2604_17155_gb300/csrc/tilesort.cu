@@ -21,6 +21,7 @@ constexpr int kSortThreads = radix::kThreads;  // CTA of the queued sort
 constexpr int kWarpSortCap = 1024;             // longest list a warp sorts alone
 constexpr int kWarpSortWarps = 4;              // warps per CTA of k_sort_tiles
 constexpr int kWarpSortChunk = 4;              // tiles a warp claims per work-counter increment
+constexpr int kMidCap = 2048;                  // queued lists up to this length: the 4-CTA-per-SM kernel
 
 struct WarpSortSmem {
   unsigned long long a[kWarpSortCap], b[kWarpSortCap];
@@ -66,8 +67,11 @@ __global__ void __launch_bounds__(32 * kWarpSortWarps) k_sort_tiles(const uint32
       tile_range(tile_off, t, capacity, b, e);
       const int n = (int)(e - b);
       if (n <= 1) continue;
-      if (n > kWarpSortCap) {
-        if (lane == 0) queue[atomicAdd(&status->big_tiles, 1u)] = (uint32_t)t;
+      if (n > kWarpSortCap) {  // queued: up to kMidCap keys from the front, longer lists from the back
+        if (lane == 0) {
+          if (n <= kMidCap) queue[atomicAdd(&status->big_tiles, 1u)] = (uint32_t)t;
+          else queue[ntiles - 1 - (int)atomicAdd(&status->long_tiles, 1u)] = (uint32_t)t;
+        }
         continue;
       }
       radix::warp_sort(entries + b, n, m.a, m.b, m.sc);
@@ -87,41 +91,44 @@ __device__ __forceinline__ int merge_path(const unsigned long long* A, int na, c
   return lo;
 }
 
-// Sorts the m (1 < m <= kSortCap) keys at g in place with the block radix sort sized to m.
+// Sorts the m (1 < m <= CAP) keys at g in place with the block radix sort sized to m.
+template <int CAP>
 __device__ __forceinline__ void block_sort_list(unsigned long long* g, int m, unsigned long long* a,
                                                 unsigned long long* b, radix::BlockScratch& sc) {
   if (m <= 1024) radix::block_sort<4>(g, m, a, b, sc);
-  else if (m <= 2048) radix::block_sort<8>(g, m, a, b, sc);
+  else if (CAP <= 2048 || m <= 2048) radix::block_sort<8>(g, m, a, b, sc);
   else if (m <= 3072) radix::block_sort<12>(g, m, a, b, sc);
   else radix::block_sort<16>(g, m, a, b, sc);
 }
 
-// Sorts the queued tile lists in place, a grid-stride loop over the queue. A list of up to
-// kSortCap keys is sorted at once by the block radix sort; a longer one as runs of kSortCap keys,
-// then pairwise merge-path merges ping-ponging between its slot range and the same range of the
-// scratch array.
-__global__ void __launch_bounds__(kSortThreads) k_sort_queued(const uint32_t* __restrict__ tile_off,
-                                                              unsigned long long* __restrict__ entries,
-                                                              unsigned long long* __restrict__ scratch,
-                                                              uint32_t capacity, const uint32_t* __restrict__ queue,
-                                                              const DevStatus* status) {
-  extern __shared__ __align__(16) unsigned long long s_dyn[];  // 2 x kSortCap keys
+// Sorts the queued tile lists in place, a grid-stride loop over one queue: with CAP = kMidCap the
+// lists of up to kMidCap keys (queue[0, big_tiles)), with CAP = kSortCap the longer ones (the last
+// long_tiles entries of the queue). A list of up to CAP keys is sorted at once by the block radix
+// sort; a longer one as runs of CAP keys, then pairwise merge-path merges ping-ponging between its
+// slot range and the same range of the scratch array.
+template <int CAP>
+__global__ void __launch_bounds__(kSortThreads, CAP <= 2048 ? 4 : 2) k_sort_queued(
+    const uint32_t* __restrict__ tile_off, unsigned long long* __restrict__ entries,
+    unsigned long long* __restrict__ scratch, uint32_t capacity, const uint32_t* __restrict__ queue, int ntiles,
+    const DevStatus* status) {
+  extern __shared__ __align__(16) unsigned long long s_dyn[];  // 2 x CAP keys
   __shared__ radix::BlockScratch sc;
   for (int i = threadIdx.x; i < radix::kWarps * radix::kBins; i += kSortThreads) sc.match[i] = 0u;
   __syncthreads();
-  const uint32_t count = status->big_tiles;
+  const bool mid = CAP == kMidCap;
+  const uint32_t count = mid ? status->big_tiles : status->long_tiles;
   for (uint32_t q = blockIdx.x; q < count; q += gridDim.x) {
     uint32_t b, e;
-    tile_range(tile_off, queue[q], capacity, b, e);
+    tile_range(tile_off, queue[mid ? (int)q : ntiles - 1 - (int)q], capacity, b, e);
     const int n = (int)(e - b);
-    for (int r0 = 0; r0 < n; r0 += kSortCap) {  // sorted runs (the whole list when it fits)
-      const int m = min(kSortCap, n - r0);
-      if (m > 1) block_sort_list(entries + b + r0, m, s_dyn, s_dyn + kSortCap, sc);
+    for (int r0 = 0; r0 < n; r0 += CAP) {  // sorted runs (the whole list when it fits)
+      const int m = min(CAP, n - r0);
+      if (m > 1) block_sort_list<CAP>(entries + b + r0, m, s_dyn, s_dyn + CAP, sc);
     }
-    if (n <= kSortCap) continue;  // uniform
+    if (n <= CAP) continue;  // uniform
     unsigned long long* src = entries + b;
     unsigned long long* dst = scratch + b;
-    for (int width = kSortCap; width < n; width <<= 1) {
+    for (int width = CAP; width < n; width <<= 1) {
       for (int lo = 0; lo < n; lo += 2 * width) {
         const int na = min(width, n - lo);
         const int nb = max(0, min(width, n - lo - width));
@@ -163,7 +170,7 @@ int sm_count() {
 void launch_tile_sort(const Problem& p, int cb, const Workspace& ws, cudaStream_t s) {
   const int ntiles = cb * p.tiles;
   const int sms = sm_count();
-  cudaMemsetAsync(&ws.status->big_tiles, 0, 2 * sizeof(uint32_t), s);  // big_tiles, sort_next
+  cudaMemsetAsync(&ws.status->big_tiles, 0, 3 * sizeof(uint32_t), s);  // big_tiles, sort_next, long_tiles
   const int smem = kWarpSortWarps * (int)sizeof(WarpSortSmem);
   cudaFuncSetAttribute(k_sort_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   int per_sm = 0;
@@ -171,12 +178,17 @@ void launch_tile_sort(const Problem& p, int cb, const Workspace& ws, cudaStream_
   const int grid = sms * (per_sm > 0 ? per_sm : 1);
   k_sort_tiles<<<grid, 32 * kWarpSortWarps, smem, s>>>(ws.tile_off, reinterpret_cast<unsigned long long*>(ws.entries),
                                                        p.capacity, ntiles, ws.big_list, ws.status);
+  unsigned long long* entries = reinterpret_cast<unsigned long long*>(ws.entries);
+  unsigned long long* scratch = reinterpret_cast<unsigned long long*>(ws.entries_tmp);
+  const int msmem = 2 * kMidCap * (int)sizeof(unsigned long long);
+  cudaFuncSetAttribute(k_sort_queued<kMidCap>, cudaFuncAttributeMaxDynamicSharedMemorySize, msmem);
+  k_sort_queued<kMidCap><<<sms * 4, kSortThreads, msmem, s>>>(ws.tile_off, entries, scratch, p.capacity, ws.big_list,
+                                                              ntiles, ws.status);
   const int qsmem = 2 * kSortCap * (int)sizeof(unsigned long long);
-  cudaFuncSetAttribute(k_sort_queued, cudaFuncAttributeMaxDynamicSharedMemorySize, qsmem);
-  k_sort_queued<<<sms * 2, kSortThreads, qsmem, s>>>(ws.tile_off, reinterpret_cast<unsigned long long*>(ws.entries),
-                                                     reinterpret_cast<unsigned long long*>(ws.entries_tmp), p.capacity,
-                                                     ws.big_list, ws.status);
-  note_launches(2);
+  cudaFuncSetAttribute(k_sort_queued<kSortCap>, cudaFuncAttributeMaxDynamicSharedMemorySize, qsmem);
+  k_sort_queued<kSortCap><<<sms * 2, kSortThreads, qsmem, s>>>(ws.tile_off, entries, scratch, p.capacity, ws.big_list,
+                                                               ntiles, ws.status);
+  note_launches(3);
 }
 
 }  // namespace icgs
