@@ -70,10 +70,12 @@ KERNEL_SOURCES = {
 }
 MEASURED_TRAFFIC = {
     # relight, 100 cameras: one full-size launch captured
-    ("relight", "cuda-core"): {"bytes_per_scene": 2148486912 + 288519424, "source_sha": "be1ccf7fce8493cc"},
+    ("relight", "cuda-core"): {"bytes_per_scene": 2141210112 + 288054784, "source_sha": "adcbffaec13b5c45"},
     # features: a 10-camera launch captured and scaled by 150/10 cameras (the targets, the per-camera
     # tile lists and the per-camera accumulator re-streaming all grow with the camera count)
-    ("features", "tensor-core"): {"bytes_per_scene": 15 * (3255527424 + 1463374848), "source_sha": "5d656c19d409fe9f"},
+    ("features", "tensor-core"): {"bytes_per_scene": 15 * (3270208768 + 1464393984), "source_sha": "d28554a1fadb6a1d"},
+    # segmentation masks: a 4-camera launch captured and scaled by 200/4 cameras (as above)
+    ("segmentation", "tensor-core"): {"bytes_per_scene": 50 * (1783149568 + 503274240), "source_sha": "d28554a1fadb6a1d"},
 }
 
 
