@@ -27,7 +27,7 @@ __host__ __device__ constexpr int solve_record_floats(int B) { return 3 * (B * (
 // Device status block at the start of every workspace; read back at the end of each call.
 struct DevStatus {
   uint32_t flags;             // kFlag* bits
-  uint32_t big_tiles;         // tiles of 1025..2048 keys queued for the block sort in the current pass
+  uint32_t big_tiles;         // tiles of 1025..2048 keys queued (from the front of the queue) in the current pass
   uint32_t sort_next;         // next tile of the persistent tile sort (work counter)
   uint32_t long_tiles;        // tiles of more than 2048 keys queued (from the end of the queue)
   uint64_t instances_needed;  // max over passes of (Gaussian, tile) instances

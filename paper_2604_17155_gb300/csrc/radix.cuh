@@ -150,10 +150,12 @@ __device__ __forceinline__ void warp_passes(unsigned long long* a, unsigned long
   }
 }
 
-// Sorts the n (1 < n <= 65535) keys at g in place with one warp; a and b are its two shared
-// buffers of at least n keys, ws.match must be zero (it is again on return).
-__device__ __forceinline__ void warp_sort(unsigned long long* g, int n, unsigned long long* a, unsigned long long* b,
-                                          WarpScratch& ws) {
+// Sorts the n (1 < n <= 65535) keys at g with one warp; a and b are its two shared buffers of at
+// least n keys, ws.match must be zero (it is again on return). Returns the buffer (a or b) that
+// holds the sorted keys; WRITE also writes them back to g.
+template <bool WRITE>
+__device__ __forceinline__ const unsigned long long* warp_sort_keys(unsigned long long* g, int n, unsigned long long* a,
+                                                                    unsigned long long* b, WarpScratch& ws) {
   const int lane = threadIdx.x & 31;
   // every key of the list in flight at once (asynchronous 8-byte copies into a), then one wait
   for (int pos = lane; pos < n; pos += 32) {
@@ -187,7 +189,7 @@ __device__ __forceinline__ void warp_sort(unsigned long long* g, int n, unsigned
     bool t = false;
     for (int pos = lane; pos < n; pos += 32) {  // write out; a tie means another sort and write
       const unsigned long long k = r[pos];
-      g[pos] = k;
+      if (WRITE) g[pos] = k;
       t |= pos > 0 && key_word(k, true) == key_word(r[pos - 1], true);
     }
     tie = __any_sync(kFull, t);
@@ -200,10 +202,19 @@ __device__ __forceinline__ void warp_sort(unsigned long long* g, int n, unsigned
     __syncwarp();
     warp_scan(ws.count[cur], 0u);
     warp_passes(a, b, n, np, cur, n_lo + n_hi, n_lo, lmin, hmin, ws);
-    const unsigned long long* o = np & 1 ? b : a;
-    for (int pos = lane; pos < n; pos += 32) g[pos] = o[pos];
+    if (WRITE) {
+      const unsigned long long* o = np & 1 ? b : a;
+      for (int pos = lane; pos < n; pos += 32) g[pos] = o[pos];
+    }
   }
   __syncwarp();
+  return np & 1 ? b : a;
+}
+
+// Sorts the n (1 < n <= 65535) keys at g in place with one warp (warp_sort_keys, written back).
+__device__ __forceinline__ void warp_sort(unsigned long long* g, int n, unsigned long long* a, unsigned long long* b,
+                                          WarpScratch& ws) {
+  warp_sort_keys<true>(g, n, a, b, ws);
 }
 
 // ---------------------------------------------------------------------------------------------
