@@ -150,6 +150,34 @@ __device__ __forceinline__ void warp_passes(unsigned long long* a, unsigned long
   }
 }
 
+// Rounds of odd-even transposition tried on a list in depth order before it is sorted again.
+constexpr int kTieRounds = 8;
+
+// r[0, n) is in depth order (ascending depth word) with equal depths in arbitrary order: sorts the
+// runs of equal depths by the full key with odd-even transposition (a pair in two runs is in order
+// already, so only pairs inside a run swap). Returns false when kTieRounds rounds did not settle
+// every run; r then holds a permutation of the keys. One warp.
+__device__ __forceinline__ bool warp_fix_ties(unsigned long long* r, int n) {
+  const int lane = threadIdx.x & 31;
+  for (int round = 0; round < kTieRounds; ++round) {
+    bool sw = false;
+#pragma unroll
+    for (int phase = 0; phase < 2; ++phase) {
+      for (int pos = 2 * lane + phase; pos + 1 < n; pos += 64) {
+        const unsigned long long x = r[pos], y = r[pos + 1];
+        if (x > y) {
+          r[pos] = y;
+          r[pos + 1] = x;
+          sw = true;
+        }
+      }
+      __syncwarp();
+    }
+    if (!__any_sync(kFull, sw)) return true;
+  }
+  return false;
+}
+
 // Sorts the n (1 < n <= 65535) keys at g with one warp; a and b are its two shared buffers of at
 // least n keys, ws.match must be zero (it is again on return). Returns the buffer (a or b) that
 // holds the sorted keys; WRITE also writes them back to g.
@@ -193,6 +221,15 @@ __device__ __forceinline__ const unsigned long long* warp_sort_keys(unsigned lon
       t |= pos > 0 && key_word(k, true) == key_word(r[pos - 1], true);
     }
     tie = __any_sync(kFull, t);
+  }
+  if (tie && n_hi > 0) {  // uniform over the warp: try the runs of equal depths by transposition
+    unsigned long long* r = np & 1 ? b : a;
+    if (warp_fix_ties(r, n)) {
+      if (WRITE)
+        for (int pos = lane; pos < n; pos += 32) g[pos] = r[pos];
+      __syncwarp();
+      return r;
+    }
   }
   if (tie) {  // uniform over the warp: index order first, then depth order again
     const unsigned long long* r = np & 1 ? b : a;
@@ -340,6 +377,31 @@ __device__ __forceinline__ void block_sort(unsigned long long* g, int n, unsigne
     for (int pos = (int)threadIdx.x + 1; pos < n; pos += kThreads)
       t |= key_word(r[pos], true) == key_word(r[pos - 1], true);
     tie = __syncthreads_or(t) != 0;
+  }
+  if (tie && bh > 0) {  // uniform over the CTA: try the runs of equal depths by transposition
+    unsigned long long* r = np & 1 ? b : a;
+    bool fixed = false;
+    for (int round = 0; round < kTieRounds && !fixed; ++round) {
+      bool sw = false;
+#pragma unroll
+      for (int phase = 0; phase < 2; ++phase) {
+        for (int pos = 2 * (int)threadIdx.x + phase; pos + 1 < n; pos += 2 * kThreads) {
+          const unsigned long long x = r[pos], y = r[pos + 1];
+          if (x > y) {
+            r[pos] = y;
+            r[pos + 1] = x;
+            sw = true;
+          }
+        }
+        __syncthreads();
+      }
+      fixed = __syncthreads_or(sw) == 0;
+    }
+    if (fixed) {
+      for (int pos = threadIdx.x; pos < n; pos += kThreads) g[pos] = r[pos];
+      __syncthreads();
+      return;
+    }
   }
   if (tie) {  // uniform over the CTA
     for (int s = 0; s < bl; s += 8, ++np) block_pass<R>(np & 1 ? b : a, np & 1 ? a : b, n, false, l0, s, sc);
