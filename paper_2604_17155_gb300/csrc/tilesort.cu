@@ -22,7 +22,7 @@ constexpr int kSortThreads = radix::kThreads;  // CTA of the queued sort
 constexpr int kWarpSortCap = 1024;             // longest list a warp sorts alone
 constexpr int kWarpSortWarps = 4;              // warps per CTA of k_sort_tiles
 constexpr int kWarpSortChunk = 4;              // tiles a warp claims per work-counter increment
-constexpr int kMidCap = 2048;                  // queued lists up to this length: the 4-CTA-per-SM kernel
+constexpr int kMidCap = 2 * kWarpSortCap;       // queued lists up to this length: two warps each (k_sort_pairs)
 
 struct WarpSortSmem {
   unsigned long long a[kWarpSortCap], b[kWarpSortCap];
