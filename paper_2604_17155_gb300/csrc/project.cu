@@ -351,18 +351,19 @@ __global__ void __launch_bounds__(256) k_scatter_hist(
   bool overflow = false;
   for (int r0 = 0; r0 < PT; r0 += kGroup) {
     uint4 rcs[kGroup];
+    uint32_t ids[kGroup];
 #pragma unroll
     for (int u = 0; u < kGroup; ++u) {
       const int64_t q = i0 + (r0 + u) * 256 + threadIdx.x;
       rcs[u] = q < n ? rect_j[q] : make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+      ids[u] = q < n ? order[q] : 0u;
     }
 #pragma unroll
     for (int u = 0; u < kGroup; ++u) {
       const uint4 rc = rcs[u];
       if (rc.x == 0xFFFFFFFFu) continue;
-      const int64_t q = i0 + (r0 + u) * 256 + threadIdx.x;
       const int tx0 = rc.x & 0xFFFF, ty0 = rc.x >> 16, tx1 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
-      const uint64_t key = ((uint64_t)rc.z << 32) | (uint64_t)order[q];
+      const uint64_t key = ((uint64_t)rc.z << 32) | (uint64_t)ids[u];
       for (int ty = ty0; ty <= ty1; ++ty)
         for (int tx = tx0; tx <= tx1; ++tx) {
           const int t = ty * tiles_x + tx;
