@@ -96,6 +96,39 @@ def test_masks_fullsize_sampled_tensor_core():
     assert rep["bound_excess"] <= 0
 
 
+def test_masks_fullsize_spread_cameras_tensor_core():
+    """The same 3,000,000-Gaussian segmentation scene with 17 cameras spread over the whole
+    200-camera rig (every 12th), so that every sampled Gaussian's sums gather many viewpoints:
+    16 FP16 channels on the tensor-core walk against the oracle's walk of the sampled Gaussians'
+    candidate pixels (Eq. 5-6), solved at L = 0."""
+    from paper_2604_17155_gb300 import build as B
+    B.build()
+    from paper_2604_17155_gb300 import icgs
+    scene = W.make_scene("segmentation", 2000)
+    cams = W.make_cameras("segmentation").subset(np.arange(0, 200, 12))
+    assert cams.n == 17
+    t = W.fourier_fields(cams.n, cams.height, cams.width, 16, seed=2007, n_modes=4)
+    dev = "cuda"
+    gs = icgs.Scene.from_workload(scene, dev)
+    gc = icgs.Cameras.from_workload(cams)
+    tt = torch.tensor(t, device=dev).half()
+    del t
+    t_exact = tt.float().cpu().numpy().astype(np.float64)
+    c, status, _ = icgs.colorize(gs, gc, tt, 0, precision="mixed")
+    del tt
+    c = to_np(c)
+    st = to_np(status)
+    rng = np.random.default_rng(2008)
+    seen = np.where(st != icgs.GAUSSIAN_UNSEEN)[0]
+    sample = np.sort(rng.choice(seen, N_SAMPLE, replace=False))
+    ref = _sampled_oracle(scene, cams, t_exact, 0, sample)
+    rep, err, checked = coefficient_report(c[sample], ref, tol=TOL_BF16)
+    print("masks full size, 17 spread cameras (tensor-core walk)", rep, icgs.last_stats())
+    assert rep["checked"] >= 5
+    assert rep["max_checked"] <= TOL_BF16
+    assert rep["bound_excess"] <= 0
+
+
 def test_features_fullsize_sampled_tensor_core():
     """The tensor-core walk with 64 BF16 channels (MIXED) on the full-size feature scene:
     1,000,000 Gaussians at 1000x750, here with 4 cameras of the same rig shape. Targets are smooth
