@@ -249,8 +249,9 @@ ICGS_API icgs_status icgs_colorize_noalloc(const icgs_scene* scene, const icgs_c
  *                  colorize workspace followed by the staged targets, coefficients and status.
  * The targets are copied to the device in chunks of cameras, alternating between two copy streams
  * owned by the library (one pair per host thread and device), and each chunk's walk waits only for
- * its own copy, so the
- * copies overlap the projection, binning and the walk of earlier chunks. The call synchronises
+ * its own copy, so the copies overlap the projection, binning and the walk of earlier chunks. Each
+ * copy is enqueued two chunks ahead of its walk: with pageable memory, where an enqueue holds the
+ * host until the copy is done, the walks already enqueued still run meanwhile. The call synchronises
  * `stream` before returning. The staging region is overwritten only after the work already queued
  * on `stream` has finished. Errors as for icgs_colorize. */
 ICGS_API size_t icgs_colorize_host_workspace_size(const icgs_scene* scene, const icgs_cameras* cams,

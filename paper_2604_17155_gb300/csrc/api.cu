@@ -672,12 +672,24 @@ icgs_status icgs_colorize_host(const icgs_scene* scene, const icgs_cameras* cams
   // read it) has finished
   ICGS_TRY_CUDA(cudaEventRecord(hp->start, s));
   for (int k = 0; k < 2; ++k) ICGS_TRY_CUDA(cudaStreamWaitEvent(hp->copy[k], hp->start, 0));
-  for (size_t c = 0; c < chunk_cam0.size(); ++c) {
-    const size_t off = (size_t)chunk_cam0[c] * cam_bytes;
-    cudaStream_t cs = hp->copy[c & 1];
-    ICGS_TRY_CUDA(cudaMemcpyAsync(t_dev + off, t_host + off, (size_t)chunk_n[c] * cam_bytes, cudaMemcpyHostToDevice, cs));
-    ICGS_TRY_CUDA(cudaEventRecord(hp->ready[c], cs));
-  }
+  // Copies are enqueued kCopyAhead chunks ahead of the walk that reads them, interleaved with the
+  // compute launches: from page-locked memory every call returns at once and the copies run
+  // behind the binning and the walks; from pageable memory, where each copy holds the host until
+  // it is done, the walks already enqueued still run while the next chunk is copied.
+  constexpr size_t kCopyAhead = 2;
+  size_t copied = 0;
+  auto enqueue_copy = [&]() -> icgs_status {
+    if (copied >= chunk_cam0.size()) return ICGS_OK;
+    const size_t off = (size_t)chunk_cam0[copied] * cam_bytes;
+    cudaStream_t cs = hp->copy[copied & 1];
+    ICGS_TRY_CUDA(cudaMemcpyAsync(t_dev + off, t_host + off, (size_t)chunk_n[copied] * cam_bytes,
+                                  cudaMemcpyHostToDevice, cs));
+    ICGS_TRY_CUDA(cudaEventRecord(hp->ready[copied], cs));
+    ++copied;
+    return ICGS_OK;
+  };
+  for (size_t k = 0; k < kCopyAhead; ++k)
+    if ((st = enqueue_copy()) != ICGS_OK) return st;
 
   if ((st = upload_common(p, cams, lam, ws, s)) != ICGS_OK) return st;
   if (p.L == 0)
@@ -693,6 +705,8 @@ icgs_status icgs_colorize_host(const icgs_scene* scene, const icgs_cameras* cams
     if ((st = bin_pass(p, scene, cb, cam0 == 0, wp, s)) != ICGS_OK) return st;
     for (; chunk < chunk_cam0.size() && chunk_cam0[chunk] < cam0 + cb; ++chunk) {
       const int j0 = chunk_cam0[chunk] - cam0, jc = chunk_n[chunk];
+      while (copied < chunk_cam0.size() && copied < chunk + 1 + kCopyAhead)
+        if ((st = enqueue_copy()) != ICGS_OK) return st;
       ICGS_TRY_CUDA(cudaStreamWaitEvent(s, hp->ready[chunk], 0));
       Workspace wc = wp;  // the chunk's cameras are a contiguous slice of the pass
       wc.tile_off = wp.tile_off + (size_t)j0 * p.tiles;
