@@ -310,6 +310,8 @@ icgs_status status_of(const DevStatus& st) {
   g_required = (int64_t)st.instances_needed;
   if (st.flags & kFlagTimeout)
     return fail(ICGS_ERR_DEVICE_TIMEOUT, "a bounded wait for the tensor-core MMAs gave up");
+  if (st.flags & kFlagLayout)
+    return fail(ICGS_ERR_UNSUPPORTED, "the tensor-core walk needs a 128-byte aligned dynamic shared memory base");
   if (st.flags & kFlagOverflow)
     return fail(ICGS_ERR_CAPACITY, "a pass needed %lld (Gaussian, tile) instances; pass at least that as "
                 "icgs_options.instance_capacity", (long long)st.instances_needed);

@@ -128,8 +128,8 @@ __device__ __forceinline__ uint32_t kmajor_sw128(int row, int k, int rows) {
 // offset >> 4 in bits 16-29 (unused for swizzled K-major; 1 by convention), stride byte offset
 // >> 4 in bits 32-45 (1024 B between 8-row atoms), descriptor version 1 in bits 46-47, layout type
 // in bits 61-63 (2 = 128-byte swizzle).
-__device__ __forceinline__ uint64_t desc_kmajor_sw128(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+__device__ __forceinline__ uint64_t desc_kmajor_sw128(uint32_t saddr, uint32_t sbo = 1024) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(sbo >> 4) << 32) |
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
@@ -161,6 +161,62 @@ __device__ __forceinline__ void issue_batch(uint32_t a_addr, uint32_t b_addr, ui
     umma_f16(d_tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
   }
   umma_commit(mbar);
+}
+
+// ---- B of the 16-channel walk in 11 KB ---------------------------------------------------------
+// B is [24 x 256]: 16 target rows (two 8-row atoms per K block of 64 pixels) and 8 rows of ones. An
+// MMA reads its three atoms at start, start + SBO and start + 2 SBO, and every MMA has its own
+// descriptor, so each K block kb gets its own stride s_kb (in KB) and puts its two target atoms at
+// 2 s_kb and s_kb KB below one shared atom of ones. With s = 1, 3, 4, 5 the eight target atoms and
+// the ones occupy KB 0, 2, 4-10 of an 11 KB region (ones at KB 10); KB 1 and 3 hold the staged
+// geometry. The ones' values do not depend on the pixel, so every K block may read the same atom.
+__host__ __device__ constexpr int b16_stride_kb(int kb) { return kb == 0 ? 1 : kb + 2; }
+constexpr uint32_t kB16Ones = 10 * 1024;  // offset of the ones atom in the region
+constexpr uint32_t kB16Bytes = 11 * 1024;
+constexpr uint32_t kB16Geo = 1 * 1024, kB16Aux = 3 * 1024;  // the holes
+
+// byte offset of B[channel k][pixel p] (k < 16) in the region
+__device__ __forceinline__ uint32_t b16_offset(int k, int p) {
+  const int kb = p >> 6, s = b16_stride_kb(kb);
+  const uint32_t atom = kB16Ones - (uint32_t)((k < 8 ? 2 : 1) * s) * 1024u;
+  return atom + (uint32_t)((k & 7) * 128 + ((((p & 63) >> 3) ^ (k & 7)) << 4) + ((p & 7) << 1));
+}
+
+// The 16 MMAs of one batch of the 16-channel walk (N = 24: columns 0-15 the targets, 16-23 V).
+template <int MG>
+__device__ __forceinline__ void issue_batch_b16(uint32_t a_addr, uint32_t b_region, uint32_t d_tmem, uint32_t idesc,
+                                                uint64_t* mbar) {
+  tc_fence_after();
+#pragma unroll
+  for (int ks = 0; ks < kKPix / 16; ++ks) {
+    const int kb = ks >> 2, kk = ks & 3, sk = b16_stride_kb(kb);
+    const uint64_t ad = desc_kmajor_sw128(a_addr + kb * (MG * 128) + kk * 32);
+    const uint64_t bd = desc_kmajor_sw128(b_region + kB16Ones - (uint32_t)(2 * sk) * 1024u + kk * 32, (uint32_t)sk * 1024u);
+    umma_f16(d_tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+  }
+  umma_commit(mbar);
+}
+
+// Staging of a batch for the walk (M = 64). The thread that stages Gaussian g is the one that adds
+// row g's sums in the epilogue -- lane g % 16 of warp g / 16, since TMEM holds row g in lane g % 16
+// of quarter g / 16 -- so the Gaussian's index stays in that thread's register from staging to
+// epilogue. Warps 4-7 read the same quarters for the later accumulator columns (more than 16
+// channels); their lanes < 16 load only the index (need_id).
+__device__ __forceinline__ uint32_t stage_tc(const unsigned long long* list, uint32_t first, int nb,
+                                             const ProjRec* __restrict__ rec_cam, int64_t n, float ox, float oy,
+                                             float4* s_geo, float4* s_aux, int g, bool writer, bool need_id) {
+  uint32_t id = 0;
+  if (g >= 0 && g < nb && (writer || need_id)) {
+    id = min((uint32_t)list[first + g], (uint32_t)(n - 1));
+    if (writer) {
+      const ProjRec r = rec_cam[id];
+      float4 geo, aux;
+      stage_record(r, ox, oy, geo, aux);
+      s_geo[g] = geo;
+      s_aux[g] = aux;
+    }
+  }
+  return id;
 }
 
 // The accumulator row held in TMEM lane 32 q + l (the lane a thread l of a warp with quarter q
@@ -246,27 +302,40 @@ __host__ __device__ constexpr uint32_t tmem_cols() {
   return NB <= 32 ? 32u : (NB <= 64 ? 64u : 128u);
 }
 
+template <int KT, int MG>
+__host__ __device__ constexpr int tc_ctas_per_sm() {
+  return MG == 64 ? (KT <= 16 ? 5 : (KT <= 32 ? 4 : 3)) : 2;
+}
+
 template <int KT, bool BF16_TARGETS, int MG>
-__global__ void __launch_bounds__(256, MG == 64 ? (KT <= 32 ? 4 : 3) : 2) k_blend_accumulate_tc(
+__global__ void __launch_bounds__(256, tc_ctas_per_sm<KT, MG>()) k_blend_accumulate_tc(
     const uint32_t* __restrict__ tile_off, const uint64_t* __restrict__ entries, uint32_t capacity,
     const ProjRec* __restrict__ rec, int64_t n, int width, int height, int tiles_x, int tiles,
     const uint16_t* __restrict__ targets, int K, int cam0, float* __restrict__ acc, int RS,
     int64_t acc_cam_stride, DevStatus* status, uint64_t wait_limit_ns, bool issue_mma) {
+  static_assert(MG == 64, "staging and epilogue map Gaussian g to TMEM lane g % 16 of quarter g / 16 (M = 64)");
   constexpr int NB = tc_cols<KT, MG>();  // target channels + rows of ones (V)
+  constexpr bool kB16 = KT == 16;        // B in the 11 KB region (b16_offset)
   extern __shared__ uint8_t smem_raw[];
+  // The barrier and flags (48 bytes) sit in front of the 1024-byte aligned operands, inside the
+  // 1 KB the layout allows for alignment: from a base that is 128-byte aligned the operands then
+  // start at most 1024 bytes in. A base that is not is reported (kFlagLayout) before any work.
   const uint32_t raw = smem_u32(smem_raw);
-  uint8_t* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-  uint8_t* A_s = base;                                 // MG x 256 (32 or 64 KB)
-  uint8_t* B_s = base + MG * kKPix * 2;                // NB x 256
-  // staging of two batches: batch b in buffer b & 1, the next one loaded while b's MMAs run
-  float4* s_geo2 = reinterpret_cast<float4*>(B_s + NB * kKPix * 2);  // [2][MG]
-  float4* s_aux2 = s_geo2 + 2 * MG;                                  // [2][MG]
-  float2* s_half2 = reinterpret_cast<float2*>(s_aux2 + 2 * MG);      // [2][MG]
-  uint32_t* s_id2 = reinterpret_cast<uint32_t*>(s_half2 + 2 * MG);   // [2][MG]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(s_id2 + 2 * MG);
+  if (raw & 127u) {
+    if (threadIdx.x == 0) atomicOr(&status->flags, kFlagLayout);
+    return;
+  }
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
-  uint32_t* s_tmax = tmem_slot + 1;  // [8]
-  uint32_t* s_timeout = s_tmax + 8;  // set by a thread whose wait gave up
+  uint32_t* s_timeout = tmem_slot + 1;  // set by a thread whose wait gave up
+  uint32_t* s_tmax = s_timeout + 1;     // [8]
+  uint8_t* base = smem_raw + (((raw + 48u + 1023u) & ~1023u) - raw);
+  uint8_t* A_s = base;                                 // MG x 256 (32 KB)
+  uint8_t* B_s = base + MG * kKPix * 2;                // NB x 256, or the 11 KB region
+  // The batch's geometry is read only by the pixel walk, which ends at the first barrier of the
+  // batch: the next batch is staged into the same buffer while the MMAs run.
+  float4* s_geo = reinterpret_cast<float4*>(kB16 ? B_s + kB16Geo : B_s + NB * kKPix * 2);  // [MG]
+  float4* s_aux = kB16 ? reinterpret_cast<float4*>(B_s + kB16Aux) : s_geo + MG;             // [MG]
 
   const TileCtx c = tile_ctx(tile_off, capacity, tiles, tiles_x, width, height);
   if (c.len == 0) return;  // uniform: nothing binned to this tile
@@ -320,10 +389,15 @@ __global__ void __launch_bounds__(256, MG == 64 ? (KT <= 32 ? 4 : 3) : 2) k_blen
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
       const float v = ldexpf(target_value(tv[k], BF16_TARGETS), sexp);
-      *reinterpret_cast<uint16_t*>(B_s + kmajor_sw128(k, p, NB)) = half_bits(v);
+      *reinterpret_cast<uint16_t*>(B_s + (kB16 ? b16_offset(k, p) : kmajor_sw128(k, p, NB))) = half_bits(v);
     }
+    if constexpr (kB16) {
+      if (threadIdx.x < 64)
+        reinterpret_cast<uint4*>(B_s + kB16Ones)[threadIdx.x] = make_uint4(0x3C003C00u, 0x3C003C00u, 0x3C003C00u, 0x3C003C00u);
+    } else {
 #pragma unroll
-    for (int k = KT; k < NB; ++k) *reinterpret_cast<uint16_t*>(B_s + kmajor_sw128(k, p, NB)) = (uint16_t)0x3C00u;
+      for (int k = KT; k < NB; ++k) *reinterpret_cast<uint16_t*>(B_s + kmajor_sw128(k, p, NB)) = (uint16_t)0x3C00u;
+    }
   }
   const float v_scale_inv = ldexpf(1.0f, -kWScaleExp);
   const ProjRec* rec_cam = rec + (int64_t)c.j * n;
@@ -336,8 +410,13 @@ __global__ void __launch_bounds__(256, MG == 64 ? (KT <= 32 ? 4 : 3) : 2) k_blen
     tmem_relinquish();
   }
   // the first batch's staging, and W cleared
-  load_batch(reinterpret_cast<const unsigned long long*>(entries), c.b, (int)min((uint32_t)MG, c.len), rec_cam, n,
-             c.ox, c.oy, s_geo2, s_aux2, s_half2, s_id2);
+  constexpr int kCh = KT / 16;          // 16-column chunks of S in the epilogue
+  constexpr int kHalf = (kCh + 1) / 2;  // chunks of the warps 0-3
+  const int g_own = tmem_row_of_lane<MG>(warp & 3, lane);  // the batch row this thread stages and adds
+  const bool stager = warp < 4, need_id = warp < 4 || kCh > kHalf;
+  const unsigned long long* list = reinterpret_cast<const unsigned long long*>(entries);
+  uint32_t my_id = stage_tc(list, c.b, (int)min((uint32_t)MG, c.len), rec_cam, n, c.ox, c.oy, s_geo, s_aux, g_own,
+                            stager, need_id);
   for (int i = threadIdx.x; i < MG * kKPix * 2 / 16; i += 256) reinterpret_cast<uint4*>(A_s)[i] = make_uint4(0, 0, 0, 0);
   tc_fence_before();
   __syncthreads();
@@ -353,14 +432,10 @@ __global__ void __launch_bounds__(256, MG == 64 ? (KT <= 32 ? 4 : 3) : 2) k_blen
   // batch's staging loaded, W cleared, the done count and the timeout flag published).
   for (uint32_t start = 0, buf = 0; start < c.len; start += MG, buf ^= 1u) {
     const int nb = (int)min((uint32_t)MG, c.len - start);
-    const float4* s_geo = s_geo2 + buf * MG;
-    const float4* s_aux = s_aux2 + buf * MG;
-    const float2* s_half = s_half2 + buf * MG;
-    const uint32_t* s_id = s_id2 + buf * MG;
     if (!__all_sync(0xFFFFFFFFu, done)) {
 #pragma unroll
       for (int q = 0; q < MG / 32; ++q) {
-        uint32_t bits = warp_hit_bits(s_geo, s_aux, s_half, q * 32, nb, c);
+        uint32_t bits = warp_hit_bits_packed(s_geo, s_aux, q * 32, nb, c);
         while (bits && !done) {  // only Gaussians whose box touches this warp's block, in depth order
           const int g = q * 32 + __ffs(bits) - 1;
           bits &= bits - 1;
@@ -377,14 +452,17 @@ __global__ void __launch_bounds__(256, MG == 64 ? (KT <= 32 ? 4 : 3) : 2) k_blen
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
-    if (threadIdx.x == 0 && issue_mma) issue_batch<NB, MG>(a_addr, b_addr, tmem, kIdesc, mbar);
-    // while the MMAs run: stage the next batch in the other buffer (its readers finished at the
-    // last end-of-batch barrier)
+    if (threadIdx.x == 0 && issue_mma) {
+      if constexpr (kB16) issue_batch_b16<MG>(a_addr, b_addr, tmem, kIdesc, mbar);
+      else issue_batch<NB, MG>(a_addr, b_addr, tmem, kIdesc, mbar);
+    }
+    // while the MMAs run: stage the next batch (the pixel walk of this one has ended; each
+    // thread keeps this batch's index for the epilogue)
     const uint32_t next = start + MG;
+    uint32_t next_id = 0;
     if (next < c.len)
-      load_batch(reinterpret_cast<const unsigned long long*>(entries), c.b + next, (int)min((uint32_t)MG, c.len - next),
-                 rec_cam, n, c.ox, c.oy, s_geo2 + (buf ^ 1u) * MG, s_aux2 + (buf ^ 1u) * MG,
-                 s_half2 + (buf ^ 1u) * MG, s_id2 + (buf ^ 1u) * MG);
+      next_id = stage_tc(list, c.b + next, (int)min((uint32_t)MG, c.len - next), rec_cam, n, c.ox, c.oy, s_geo, s_aux,
+                         g_own, stager, need_id);
     const bool ok = mbar_wait_bounded(mbar, phase, wait_limit_ns);
     phase ^= 1u;
     tc_fence_after();
@@ -395,10 +473,8 @@ __global__ void __launch_bounds__(256, MG == 64 ? (KT <= 32 ? 4 : 3) : 2) k_blen
       // 4c..4c+3 of the row (V, S_0, S_1, ..) and carries its last column into group 4c+4. Every
       // tcgen05.ld is warp-uniform; only the atomics depend on the thread's Gaussian.
       const int quarter = warp & 3, part = warp >> 2;
-      const int g = tmem_row_of_lane<MG>(quarter, lane);
+      const int g = g_own;
       const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
-      constexpr int kCh = KT / 16;           // 16-column chunks of S
-      constexpr int kHalf = (kCh + 1) / 2;   // chunks of the warps 0-3
       if (part == 0 || kCh > kHalf) {        // warp-uniform
         uint32_t vr[16], r[16];
         tmem_ld16(trow + (uint32_t)KT, vr);  // the ones block: every column holds V
@@ -407,7 +483,7 @@ __global__ void __launch_bounds__(256, MG == 64 ? (KT <= 32 ? 4 : 3) : 2) k_blen
         const float V = __uint_as_float(vr[0]) * v_scale_inv;
         float carry = part == 0 ? V : __uint_as_float(r[15]) * t_scale_inv;
         const bool add = g >= 0 && g < nb && V > 0.0f;
-        float* dst = acc_cam + (int64_t)(add ? s_id[g] : 0u) * RS;
+        float* dst = acc_cam + (int64_t)(add ? my_id : 0u) * RS;
         const int c_begin = part == 0 ? 0 : kHalf, c_end = part == 0 ? kHalf : kCh;
 #pragma unroll
         for (int c = 0; c < kCh; ++c) {
@@ -432,6 +508,7 @@ __global__ void __launch_bounds__(256, MG == 64 ? (KT <= 32 ? 4 : 3) : 2) k_blen
           atomicAdd(reinterpret_cast<float4*>(dst + 16 * kCh), make_float4(carry, 0.0f, 0.0f, 0.0f));
       }
     }
+    my_id = next_id;
     if (!ok) {
       *s_timeout = 1u;
     } else if (next < c.len) {
@@ -461,10 +538,22 @@ template <int NB>
 constexpr size_t selftest_smem() {
   return 1024 + (size_t)kG * kKPix * 2 + (size_t)NB * kKPix * 2 + 16;
 }
+// the barrier and flags with the alignment slack (1 KB), W, and B (with the staged geometry in its
+// holes at 16 channels, after it otherwise)
 template <int KT, int MG>
 constexpr size_t tc_smem() {
-  return 1024 + (size_t)MG * kKPix * 2 + (size_t)tc_cols<KT, MG>() * kKPix * 2 + 2 * (size_t)MG * (16 + 16 + 8 + 4) + 64;
+  return 1024 + (size_t)MG * kKPix * 2 +
+         (KT == 16 ? (size_t)kB16Bytes : (size_t)tc_cols<KT, MG>() * kKPix * 2 + (size_t)MG * 32);
 }
+// CTAs per SM that the shared memory admits: each CTA's share rounded up to 1 KB, plus 1 KB the
+// system reserves per CTA, out of the SM's 228 KB
+template <int KT, int MG>
+constexpr int tc_smem_ctas() {
+  return (int)((228 * 1024) / ((tc_smem<KT, MG>() + 1023) / 1024 * 1024 + 1024));
+}
+static_assert(tc_smem_ctas<16, 64>() >= tc_ctas_per_sm<16, 64>(), "shared memory of the 16-channel walk");
+static_assert(tc_smem_ctas<32, 64>() >= tc_ctas_per_sm<32, 64>(), "shared memory of the 32-channel walk");
+static_assert(tc_smem_ctas<64, 64>() >= tc_ctas_per_sm<64, 64>(), "shared memory of the 64-channel walk");
 
 // Diagnostic settings of this host thread (icgs_debug_tc_wait): the walk's wait limit and whether
 // it issues its MMAs.
@@ -477,6 +566,8 @@ void accumulate_tc(const Problem& p, int cb, int cam0, const void* targets, cons
   const size_t smem = tc_smem<KT, MG>();
   cudaFuncSetAttribute(k_blend_accumulate_tc<KT, BF16_TARGETS, MG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
+  cudaFuncSetAttribute(k_blend_accumulate_tc<KT, BF16_TARGETS, MG>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       (int)cudaSharedmemCarveoutMaxShared);
   const int64_t stride = p.L == 0 ? 0 : p.n * (int64_t)p.acc_stride;
   k_blend_accumulate_tc<KT, BF16_TARGETS, MG><<<cb * p.tiles, 256, smem, s>>>(
       ws.tile_off, ws.entries, p.capacity, ws.rec, p.n, p.width, p.height, p.tiles_x, p.tiles,

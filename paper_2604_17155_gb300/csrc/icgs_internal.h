@@ -39,6 +39,7 @@ struct DevStatus {
 constexpr uint32_t kFlagOverflow = 1u;
 constexpr uint32_t kFlagTimeout = 2u;    // a bounded device-side wait gave up
 constexpr uint32_t kFlagNonfinite = 4u;  // a walk read a NaN or infinite target value
+constexpr uint32_t kFlagLayout = 8u;     // a kernel found its shared memory base misaligned and did nothing
 
 // One camera as the kernels see it (built on the host from icgs_cameras).
 struct DevCam {

@@ -70,7 +70,7 @@ __device__ __forceinline__ const unsigned long long* tile_list(const uint64_t* _
 
 // A Gaussian of the current batch as the walk evaluates it, staged in shared memory:
 //   geo  = (mean_x - ox, mean_y - oy, A, Bc)
-//   aux  = (C, opacity, E_thr, 0)
+//   aux  = (C, opacity, E_thr, packed half-sizes: the record's box.w, unused by the step)
 //   half = (half-width, half-height) of the support box (read by the warp ballot only)
 // with the conic (a, b, c) scaled by -log2(e)/2: A = -a log2(e)/2, Bc = -b log2(e), C = -c log2(e)/2,
 // so that E = A dx^2 + Bc dx dy + C dy^2 = -q log2(e)/2 and exp(-q/2) = 2^E. E_thr is the fast-reject
@@ -172,21 +172,54 @@ __device__ __forceinline__ float blend_step(const float4 geo, const float4 aux, 
 // combined there, where the result is small and float32 holds it closely. The fast-reject
 // threshold is 2 ln(255 o) with a relative margin of 1e-4 (and 1e-4 absolute), beyond which
 // alpha < 1/255 holds by more than the float32 error of alpha.
+// The staged (geo, aux) of one record; aux.w carries the record's packed support half-sizes.
+__device__ __forceinline__ void stage_record(const ProjRec& r, float ox, float oy, float4& geo, float4& aux) {
+  const float2 lo = unpack_half2(r.box.z);
+  const float qthr = __fmaf_rn(2.0f * logf(255.0f * r.par.w), 1.0001f, 1e-4f);
+  geo = make_float4(__fadd_rn(__fsub_rn(r.box.x, ox), __fmul_rn(lo.x, kMeanLoScaleInv)),
+                    __fadd_rn(__fsub_rn(r.box.y, oy), __fmul_rn(lo.y, kMeanLoScaleInv)), -kHalfLog2e * r.par.x,
+                    -2.0f * kHalfLog2e * r.par.y);
+  aux = make_float4(-kHalfLog2e * r.par.z, r.par.w, -kHalfLog2e * qthr, r.box.w);
+}
+
 __device__ __forceinline__ void load_batch(const unsigned long long* list, uint32_t first, int nb,
                                            const ProjRec* __restrict__ rec_cam, int64_t n, float ox, float oy,
                                            float4* s_geo, float4* s_aux, float2* s_half, uint32_t* s_id) {
   if ((int)threadIdx.x < nb) {
     const uint32_t id = min((uint32_t)list[first + threadIdx.x], (uint32_t)(n - 1));
     const ProjRec r = rec_cam[id];
-    const float2 lo = unpack_half2(r.box.z), half = unpack_half2(r.box.w);
-    const float qthr = __fmaf_rn(2.0f * logf(255.0f * r.par.w), 1.0001f, 1e-4f);
+    float4 geo, aux;
+    stage_record(r, ox, oy, geo, aux);
     s_id[threadIdx.x] = id;
-    s_geo[threadIdx.x] = make_float4(__fadd_rn(__fsub_rn(r.box.x, ox), __fmul_rn(lo.x, kMeanLoScaleInv)),
-                                     __fadd_rn(__fsub_rn(r.box.y, oy), __fmul_rn(lo.y, kMeanLoScaleInv)),
-                                     -kHalfLog2e * r.par.x, -2.0f * kHalfLog2e * r.par.y);
-    s_aux[threadIdx.x] = make_float4(-kHalfLog2e * r.par.z, r.par.w, -kHalfLog2e * qthr, 0.0f);
-    s_half[threadIdx.x] = half;
+    s_geo[threadIdx.x] = geo;
+    s_aux[threadIdx.x] = aux;
+    s_half[threadIdx.x] = unpack_half2(r.box.w);
   }
+}
+
+// load_batch without the separate half-size array: the ballot reads the half-sizes from aux.w
+// (warp_hit_bits_packed).
+__device__ __forceinline__ void load_batch_packed(const unsigned long long* list, uint32_t first, int nb,
+                                                  const ProjRec* __restrict__ rec_cam, int64_t n, float ox, float oy,
+                                                  float4* s_geo, float4* s_aux, uint32_t* s_id) {
+  if ((int)threadIdx.x < nb) {
+    const uint32_t id = min((uint32_t)list[first + threadIdx.x], (uint32_t)(n - 1));
+    const ProjRec r = rec_cam[id];
+    float4 geo, aux;
+    stage_record(r, ox, oy, geo, aux);
+    s_id[threadIdx.x] = id;
+    s_geo[threadIdx.x] = geo;
+    s_aux[threadIdx.x] = aux;
+  }
+}
+
+// warp_hit_bits (box test only) for batches staged by load_batch_packed.
+__device__ __forceinline__ uint32_t warp_hit_bits_packed(const float4* s_geo, const float4* s_aux, int base, int nb,
+                                                         const TileCtx& c) {
+  const int g = base + (int)(threadIdx.x & 31);
+  bool h = false;
+  if (g < nb) h = warp_hits(s_geo[g], unpack_half2(s_aux[g].w), c);
+  return __ballot_sync(kFull, h);
 }
 
 // Flags a non-finite target value in the status block (the call then fails with
