@@ -427,6 +427,10 @@ __global__ void __launch_bounds__(256, tc_ctas_per_sm<KT, MG>()) k_blend_accumul
   float* acc_cam = acc + (int64_t)c.j * acc_cam_stride;
   float T = 1.0f;
   bool done = !c.inside;
+  // kmajor_sw128(g, p, MG) split into this pixel's part and the Gaussian's: the row's 128 bytes at
+  // g * 128 (8-row atoms of 1024 bytes), the 16-byte chunk (p % 64) / 8 XOR-ed with g % 8
+  uint8_t* const a_pix = A_s + (p >> 6) * (MG * 128) + ((p & 7) << 1);
+  const int a_chunk = ((p & 63) >> 3) << 4;
   uint32_t npairs = 0, phase = 0;
   // Two CTA barriers per batch: one before the MMA issue (W written), one at the end (the next
   // batch's staging loaded, W cleared, the done count and the timeout flag published).
@@ -439,13 +443,11 @@ __global__ void __launch_bounds__(256, tc_ctas_per_sm<KT, MG>()) k_blend_accumul
         while (bits && !done) {  // only Gaussians whose box touches this warp's block, in depth order
           const int g = q * 32 + __ffs(bits) - 1;
           bits &= bits - 1;
-          float al, ex;
-          bool cap;
-          const float w = blend_step(s_geo[g], s_aux[g], c.pxf, c.pyf, T, done, al, ex, cap);
-          if (w > 0.0f) {
-            ++npairs;
-            *reinterpret_cast<uint16_t*>(A_s + kmajor_sw128(g, p, MG)) = half_bits(w * (float)(1 << kWScaleExp));
-          }
+          const float w = blend_weight(s_geo[g], s_aux[g], c.pxf, c.pyf, T, done);
+          npairs += w > 0.0f ? 1u : 0u;
+          // W starts the batch cleared, so a skipped step may store its 0 (one branch fewer)
+          *reinterpret_cast<uint16_t*>(a_pix + (g << 7) + (((g << 4) ^ a_chunk) & 0x70)) =
+              half_bits(w * (float)(1 << kWScaleExp));
         }
       }
     }

@@ -166,6 +166,25 @@ __device__ __forceinline__ float blend_step(const float4 geo, const float4 aux, 
   return w;
 }
 
+// blend_step without branches, for walks that only need w: the same decisions (the fast reject,
+// alpha >= 1/255, the stop when T (1 - alpha) < 1e-4) taken as predicates on values that every
+// lane computes, so a warp whose lanes disagree does not split. Returns w (0 if skipped).
+__device__ __forceinline__ float blend_weight(const float4 geo, const float4 aux, float pxf, float pyf, float& T,
+                                              bool& done) {
+  const float dx = __fsub_rn(pxf, geo.x), dy = __fsub_rn(pyf, geo.y);
+  const float E = __fmaf_rn(__fmaf_rn(geo.z, dx, __fmul_rn(geo.w, dy)), dx, __fmul_rn(__fmul_rn(aux.x, dy), dy));
+  const float e = ex2_approx(E);
+  const float alpha = fminf(kAlphaMax, __fmul_rn(aux.y, e));
+  const float tT = __fmul_rn(T, __fsub_rn(1.0f, alpha));
+  const bool take = E >= aux.z && alpha >= kAlphaMin;
+  const bool stop = take && tT < kTMin;
+  const bool keep = take && !stop;
+  const float w = keep ? __fmul_rn(alpha, T) : 0.0f;
+  T = keep ? tT : T;
+  done = done || stop;
+  return w;
+}
+
 // Slot ranges are only fully written when the pass fit its capacity; an overflowed pass (reported
 // to the caller as ICGS_ERR_CAPACITY) may leave stale slots, so indices are clamped to the scene.
 // The staged mean is relative to the tile origin (ox, oy): the record's hi and lo parts are
