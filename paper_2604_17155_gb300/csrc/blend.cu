@@ -147,9 +147,7 @@ __global__ void __launch_bounds__(kThreads, KC <= 8 ? 5 : 4) k_blend_accumulate(
         while (bits) {  // only the Gaussians whose box touches this warp's block, in depth order
           const int g = half * 32 + __ffs(bits) - 1;
           bits &= bits - 1;
-          float w = 0.0f, al, ex;
-          bool cap;
-          if (!done) w = blend_step(s_geo[g], s_aux[g], c.pxf, c.pyf, T, done, al, ex, cap);
+          const float w = blend_weight<true>(s_geo[g], s_aux[g], c.pxf, c.pyf, T, done);
           if (__any_sync(kFull, w > 0.0f)) {
             npairs += w > 0.0f;
             float v[NP];
@@ -280,17 +278,14 @@ __global__ void __launch_bounds__(kThreads2, 10) k_blend_accumulate2(
           bits &= bits - 1;
           const int g2 = bits ? half * 32 + __ffs(bits) - 1 : -1;
           bits &= bits - 1;
-          float w10 = 0.0f, w11 = 0.0f, w20 = 0.0f, w21 = 0.0f, al, ex;
-          bool cap;
-          {
-            const float4 geo = s_geo[g1], aux = s_aux[g1];
-            if (!done0) w10 = blend_step(geo, aux, c.pxf, c.pyf, T0, done0, al, ex, cap);
-            if (!done1) w11 = blend_step(geo, aux, c.pxf, pyf1, T1, done1, al, ex, cap);
-          }
+          float w20 = 0.0f, w21 = 0.0f;
+          const float4 geo1 = s_geo[g1], aux1 = s_aux[g1];
+          const float w10 = blend_weight<true>(geo1, aux1, c.pxf, c.pyf, T0, done0);
+          const float w11 = blend_weight<true>(geo1, aux1, c.pxf, pyf1, T1, done1);
           if (g2 >= 0) {
             const float4 geo = s_geo[g2], aux = s_aux[g2];
-            if (!done0) w20 = blend_step(geo, aux, c.pxf, c.pyf, T0, done0, al, ex, cap);
-            if (!done1) w21 = blend_step(geo, aux, c.pxf, pyf1, T1, done1, al, ex, cap);
+            w20 = blend_weight<true>(geo, aux, c.pxf, c.pyf, T0, done0);
+            w21 = blend_weight<true>(geo, aux, c.pxf, pyf1, T1, done1);
           }
           const float w1 = __fadd_rn(w10, w11), w2 = __fadd_rn(w20, w21);
           if (__any_sync(kFull, w1 > 0.0f || w2 > 0.0f)) {
@@ -920,17 +915,14 @@ __global__ void __launch_bounds__(kThreads2, 10) k_blend_refine2(
           bits &= bits - 1;
           const int g2 = bits ? half * 32 + __ffs(bits) - 1 : -1;
           bits &= bits - 1;
-          float w10 = 0.0f, w11 = 0.0f, w20 = 0.0f, w21 = 0.0f, al, ex;
-          bool cap;
-          {
-            const float4 geo = s_geo[g1], aux = s_aux[g1];
-            if (!done0) w10 = blend_step(geo, aux, c.pxf, c.pyf, T0, done0, al, ex, cap);
-            if (!done1) w11 = blend_step(geo, aux, c.pxf, pyf1, T1, done1, al, ex, cap);
-          }
+          float w20 = 0.0f, w21 = 0.0f;
+          const float4 geo1 = s_geo[g1], aux1 = s_aux[g1];
+          const float w10 = blend_weight<true>(geo1, aux1, c.pxf, c.pyf, T0, done0);
+          const float w11 = blend_weight<true>(geo1, aux1, c.pxf, pyf1, T1, done1);
           if (g2 >= 0) {
             const float4 geo = s_geo[g2], aux = s_aux[g2];
-            if (!done0) w20 = blend_step(geo, aux, c.pxf, c.pyf, T0, done0, al, ex, cap);
-            if (!done1) w21 = blend_step(geo, aux, c.pxf, pyf1, T1, done1, al, ex, cap);
+            w20 = blend_weight<true>(geo, aux, c.pxf, c.pyf, T0, done0);
+            w21 = blend_weight<true>(geo, aux, c.pxf, pyf1, T1, done1);
           }
           const float w1 = __fadd_rn(w10, w11), w2 = __fadd_rn(w20, w21);
           if (__any_sync(kFull, w1 > 0.0f || w2 > 0.0f)) {

@@ -168,7 +168,9 @@ __device__ __forceinline__ float blend_step(const float4 geo, const float4 aux, 
 
 // blend_step without branches, for walks that only need w: the same decisions (the fast reject,
 // alpha >= 1/255, the stop when T (1 - alpha) < 1e-4) taken as predicates on values that every
-// lane computes, so a warp whose lanes disagree does not split. Returns w (0 if skipped).
+// lane computes, so a warp whose lanes disagree does not split. Returns w (0 if skipped). With
+// LIVE a pixel already done takes nothing (for walks that call it on every pixel of the warp).
+template <bool LIVE = false>
 __device__ __forceinline__ float blend_weight(const float4 geo, const float4 aux, float pxf, float pyf, float& T,
                                               bool& done) {
   const float dx = __fsub_rn(pxf, geo.x), dy = __fsub_rn(pyf, geo.y);
@@ -176,7 +178,7 @@ __device__ __forceinline__ float blend_weight(const float4 geo, const float4 aux
   const float e = ex2_approx(E);
   const float alpha = fminf(kAlphaMax, __fmul_rn(aux.y, e));
   const float tT = __fmul_rn(T, __fsub_rn(1.0f, alpha));
-  const bool take = E >= aux.z && alpha >= kAlphaMin;
+  const bool take = (!LIVE || !done) && E >= aux.z && alpha >= kAlphaMin;
   const bool stop = take && tT < kTMin;
   const bool keep = take && !stop;
   const float w = keep ? __fmul_rn(alpha, T) : 0.0f;
