@@ -440,14 +440,23 @@ __global__ void __launch_bounds__(256, tc_ctas_per_sm<KT, MG>()) k_blend_accumul
 #pragma unroll
       for (int q = 0; q < MG / 32; ++q) {
         uint32_t bits = warp_hit_bits_packed(s_geo, s_aux, q * 32, nb, c);
-        while (bits && !done) {  // only Gaussians whose box touches this warp's block, in depth order
-          const int g = q * 32 + __ffs(bits) - 1;
+        while (bits && !done) {  // two hits a step: both alphas first (independent of T)
+          const int g1 = q * 32 + __ffs(bits) - 1;
           bits &= bits - 1;
-          const float w = blend_weight(s_geo[g], s_aux[g], c.pxf, c.pyf, T, done);
-          npairs += w > 0.0f ? 1u : 0u;
-          // W starts the batch cleared, so a skipped step may store its 0 (one branch fewer)
-          *reinterpret_cast<uint16_t*>(a_pix + (g << 7) + (((g << 4) ^ a_chunk) & 0x70)) =
-              half_bits(w * (float)(1 << kWScaleExp));
+          const bool has2 = bits != 0;  // warp-uniform
+          const int g2 = has2 ? q * 32 + __ffs(bits) - 1 : g1;
+          bits &= bits - 1;
+          const StepAlpha a1 = blend_alpha(s_geo[g1], s_aux[g1], c.pxf, c.pyf);
+          StepAlpha a2 = blend_alpha(s_geo[g2], s_aux[g2], c.pxf, c.pyf);
+          a2.ok = a2.ok && has2;
+          const float w1 = blend_take(a1, T, done);
+          const float w2 = blend_take<true>(a2, T, done);
+          npairs += (w1 > 0.0f ? 1u : 0u) + (w2 > 0.0f ? 1u : 0u);
+          *reinterpret_cast<uint16_t*>(a_pix + (g1 << 7) + (((g1 << 4) ^ a_chunk) & 0x70)) =
+              half_bits(w1 * (float)(1 << kWScaleExp));
+          if (has2)
+            *reinterpret_cast<uint16_t*>(a_pix + (g2 << 7) + (((g2 << 4) ^ a_chunk) & 0x70)) =
+                half_bits(w2 * (float)(1 << kWScaleExp));
         }
       }
     }

@@ -168,23 +168,34 @@ __device__ __forceinline__ float blend_step(const float4 geo, const float4 aux, 
 
 // blend_step without branches, for walks that only need w: the same decisions (the fast reject,
 // alpha >= 1/255, the stop when T (1 - alpha) < 1e-4) taken as predicates on values that every
-// lane computes, so a warp whose lanes disagree does not split. Returns w (0 if skipped). With
-// LIVE a pixel already done takes nothing (for walks that call it on every pixel of the warp).
-template <bool LIVE = false>
-__device__ __forceinline__ float blend_weight(const float4 geo, const float4 aux, float pxf, float pyf, float& T,
-                                              bool& done) {
+// lane computes, so a warp whose lanes disagree does not split. blend_alpha is the part that does
+// not depend on T; blend_take applies one alpha to the pixel's transmittance and returns w (0 if
+// skipped). With LIVE a pixel already done takes nothing (for walks that call it on every pixel).
+struct StepAlpha {
+  float alpha;
+  bool ok;  // past the fast reject and alpha >= 1/255
+};
+__device__ __forceinline__ StepAlpha blend_alpha(const float4 geo, const float4 aux, float pxf, float pyf) {
   const float dx = __fsub_rn(pxf, geo.x), dy = __fsub_rn(pyf, geo.y);
   const float E = __fmaf_rn(__fmaf_rn(geo.z, dx, __fmul_rn(geo.w, dy)), dx, __fmul_rn(__fmul_rn(aux.x, dy), dy));
-  const float e = ex2_approx(E);
-  const float alpha = fminf(kAlphaMax, __fmul_rn(aux.y, e));
-  const float tT = __fmul_rn(T, __fsub_rn(1.0f, alpha));
-  const bool take = (!LIVE || !done) && E >= aux.z && alpha >= kAlphaMin;
+  const float alpha = fminf(kAlphaMax, __fmul_rn(aux.y, ex2_approx(E)));
+  return {alpha, E >= aux.z && alpha >= kAlphaMin};
+}
+template <bool LIVE = false>
+__device__ __forceinline__ float blend_take(const StepAlpha a, float& T, bool& done) {
+  const float tT = __fmul_rn(T, __fsub_rn(1.0f, a.alpha));
+  const bool take = (!LIVE || !done) && a.ok;
   const bool stop = take && tT < kTMin;
   const bool keep = take && !stop;
-  const float w = keep ? __fmul_rn(alpha, T) : 0.0f;
+  const float w = keep ? __fmul_rn(a.alpha, T) : 0.0f;
   T = keep ? tT : T;
   done = done || stop;
   return w;
+}
+template <bool LIVE = false>
+__device__ __forceinline__ float blend_weight(const float4 geo, const float4 aux, float pxf, float pyf, float& T,
+                                              bool& done) {
+  return blend_take<LIVE>(blend_alpha(geo, aux, pxf, pyf), T, done);
 }
 
 // Slot ranges are only fully written when the pass fit its capacity; an overflowed pass (reported
