@@ -147,9 +147,8 @@ __global__ void __launch_bounds__(kThreads, KC <= 8 ? 5 : 4) k_blend_accumulate(
         while (bits) {  // only the Gaussians whose box touches this warp's block, in depth order
           const int g = half * 32 + __ffs(bits) - 1;
           bits &= bits - 1;
-          const float w = blend_weight<true>(s_geo[g], s_aux[g], c.pxf, c.pyf, T, done);
+          const float w = blend_weight<true>(s_geo[g], s_aux[g], c.pxf, c.pyf, T, done, npairs);
           if (__any_sync(kFull, w > 0.0f)) {
-            npairs += w > 0.0f;
             float v[NP];
 #pragma unroll
             for (int q = 0; q < NP; ++q) v[q] = __fmul_rn(w, u[q]);
@@ -280,16 +279,15 @@ __global__ void __launch_bounds__(kThreads2, 10) k_blend_accumulate2(
           bits &= bits - 1;
           float w20 = 0.0f, w21 = 0.0f;
           const float4 geo1 = s_geo[g1], aux1 = s_aux[g1];
-          const float w10 = blend_weight<true>(geo1, aux1, c.pxf, c.pyf, T0, done0);
-          const float w11 = blend_weight<true>(geo1, aux1, c.pxf, pyf1, T1, done1);
+          const float w10 = blend_weight<true>(geo1, aux1, c.pxf, c.pyf, T0, done0, npairs);
+          const float w11 = blend_weight<true>(geo1, aux1, c.pxf, pyf1, T1, done1, npairs);
           if (g2 >= 0) {
             const float4 geo = s_geo[g2], aux = s_aux[g2];
-            w20 = blend_weight<true>(geo, aux, c.pxf, c.pyf, T0, done0);
-            w21 = blend_weight<true>(geo, aux, c.pxf, pyf1, T1, done1);
+            w20 = blend_weight<true>(geo, aux, c.pxf, c.pyf, T0, done0, npairs);
+            w21 = blend_weight<true>(geo, aux, c.pxf, pyf1, T1, done1, npairs);
           }
           const float w1 = __fadd_rn(w10, w11), w2 = __fadd_rn(w20, w21);
           if (__any_sync(kFull, w1 > 0.0f || w2 > 0.0f)) {
-            npairs += (w10 > 0.0f) + (w11 > 0.0f) + (w20 > 0.0f) + (w21 > 0.0f);
             const float a0 = mh ? w20 : w10, a1 = mh ? w21 : w11;
             const float c0 = mh ? w10 : w20, c1 = mh ? w11 : w21;
             float v[NP2];
@@ -917,16 +915,15 @@ __global__ void __launch_bounds__(kThreads2, 10) k_blend_refine2(
           bits &= bits - 1;
           float w20 = 0.0f, w21 = 0.0f;
           const float4 geo1 = s_geo[g1], aux1 = s_aux[g1];
-          const float w10 = blend_weight<true>(geo1, aux1, c.pxf, c.pyf, T0, done0);
-          const float w11 = blend_weight<true>(geo1, aux1, c.pxf, pyf1, T1, done1);
+          const float w10 = blend_weight<true>(geo1, aux1, c.pxf, c.pyf, T0, done0, npairs);
+          const float w11 = blend_weight<true>(geo1, aux1, c.pxf, pyf1, T1, done1, npairs);
           if (g2 >= 0) {
             const float4 geo = s_geo[g2], aux = s_aux[g2];
-            w20 = blend_weight<true>(geo, aux, c.pxf, c.pyf, T0, done0);
-            w21 = blend_weight<true>(geo, aux, c.pxf, pyf1, T1, done1);
+            w20 = blend_weight<true>(geo, aux, c.pxf, c.pyf, T0, done0, npairs);
+            w21 = blend_weight<true>(geo, aux, c.pxf, pyf1, T1, done1, npairs);
           }
           const float w1 = __fadd_rn(w10, w11), w2 = __fadd_rn(w20, w21);
           if (__any_sync(kFull, w1 > 0.0f || w2 > 0.0f)) {
-            npairs += (w10 > 0.0f) + (w11 > 0.0f) + (w20 > 0.0f) + (w21 > 0.0f);
             const float a0 = mh ? w20 : w10, a1 = mh ? w21 : w11;
             const float c0 = mh ? w10 : w20, c1 = mh ? w11 : w21;
             float v[NP2];

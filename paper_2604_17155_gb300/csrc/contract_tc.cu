@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(256, tc_ctas_per_sm<KT, MG>()) k_blend_accumul
   const uint32_t a_addr = smem_u32(A_s), b_addr = smem_u32(B_s);
   constexpr uint32_t kIdesc = idesc_f16(MG, NB, false);
   float* acc_cam = acc + (int64_t)c.j * acc_cam_stride;
-  float T = 1.0f;
+  float T = (float)(1 << kWScaleExp);  // the transmittance times 2^14 (blend_take)
   bool done = !c.inside;
   // kmajor_sw128(g, p, MG) split into this pixel's part and the Gaussian's: the row's 128 bytes at
   // g * 128 (8-row atoms of 1024 bytes), the 16-byte chunk (p % 64) / 8 XOR-ed with g % 8
@@ -449,14 +449,11 @@ __global__ void __launch_bounds__(256, tc_ctas_per_sm<KT, MG>()) k_blend_accumul
           const StepAlpha a1 = blend_alpha(s_geo[g1], s_aux[g1], c.pxf, c.pyf);
           StepAlpha a2 = blend_alpha(s_geo[g2], s_aux[g2], c.pxf, c.pyf);
           a2.ok = a2.ok && has2;
-          const float w1 = blend_take(a1, T, done);
-          const float w2 = blend_take<true>(a2, T, done);
-          npairs += (w1 > 0.0f ? 1u : 0u) + (w2 > 0.0f ? 1u : 0u);
-          *reinterpret_cast<uint16_t*>(a_pix + (g1 << 7) + (((g1 << 4) ^ a_chunk) & 0x70)) =
-              half_bits(w1 * (float)(1 << kWScaleExp));
-          if (has2)
-            *reinterpret_cast<uint16_t*>(a_pix + (g2 << 7) + (((g2 << 4) ^ a_chunk) & 0x70)) =
-                half_bits(w2 * (float)(1 << kWScaleExp));
+          // T carries the factor 2^14 of W, so the weights come out scaled
+          const float w1 = blend_take<false, kWScaleExp>(a1, T, done, npairs);
+          const float w2 = blend_take<true, kWScaleExp>(a2, T, done, npairs);
+          *reinterpret_cast<uint16_t*>(a_pix + (g1 << 7) + (((g1 << 4) ^ a_chunk) & 0x70)) = half_bits(w1);
+          if (has2) *reinterpret_cast<uint16_t*>(a_pix + (g2 << 7) + (((g2 << 4) ^ a_chunk) & 0x70)) = half_bits(w2);
         }
       }
     }

@@ -170,7 +170,11 @@ __device__ __forceinline__ float blend_step(const float4 geo, const float4 aux, 
 // alpha >= 1/255, the stop when T (1 - alpha) < 1e-4) taken as predicates on values that every
 // lane computes, so a warp whose lanes disagree does not split. blend_alpha is the part that does
 // not depend on T; blend_take applies one alpha to the pixel's transmittance and returns w (0 if
-// skipped). With LIVE a pixel already done takes nothing (for walks that call it on every pixel).
+// skipped), counting a taken step in npairs. With LIVE a pixel already done takes nothing (for walks
+// that call it on every pixel). With TEXP the walk carries T scaled by 2^TEXP (from 2^TEXP down), so
+// that w comes out scaled by 2^TEXP too; the stop compares with the threshold scaled the same way.
+// Scaling by a power of two commutes with rounding for these normal values, so the decisions and
+// the scaled weights are exactly those of the unscaled step.
 struct StepAlpha {
   float alpha;
   bool ok;  // past the fast reject and alpha >= 1/255
@@ -181,12 +185,14 @@ __device__ __forceinline__ StepAlpha blend_alpha(const float4 geo, const float4 
   const float alpha = fminf(kAlphaMax, __fmul_rn(aux.y, ex2_approx(E)));
   return {alpha, E >= aux.z && alpha >= kAlphaMin};
 }
-template <bool LIVE = false>
-__device__ __forceinline__ float blend_take(const StepAlpha a, float& T, bool& done) {
+template <bool LIVE = false, int TEXP = 0>
+__device__ __forceinline__ float blend_take(const StepAlpha a, float& T, bool& done, uint32_t& npairs) {
+  constexpr float kTMinScaled = kTMin * (float)(1 << TEXP);
   const float tT = __fmul_rn(T, __fsub_rn(1.0f, a.alpha));
   const bool take = (!LIVE || !done) && a.ok;
-  const bool stop = take && tT < kTMin;
+  const bool stop = take && tT < kTMinScaled;
   const bool keep = take && !stop;
+  npairs += keep ? 1u : 0u;
   const float w = keep ? __fmul_rn(a.alpha, T) : 0.0f;
   T = keep ? tT : T;
   done = done || stop;
@@ -194,8 +200,8 @@ __device__ __forceinline__ float blend_take(const StepAlpha a, float& T, bool& d
 }
 template <bool LIVE = false>
 __device__ __forceinline__ float blend_weight(const float4 geo, const float4 aux, float pxf, float pyf, float& T,
-                                              bool& done) {
-  return blend_take<LIVE>(blend_alpha(geo, aux, pxf, pyf), T, done);
+                                              bool& done, uint32_t& npairs) {
+  return blend_take<LIVE>(blend_alpha(geo, aux, pxf, pyf), T, done, npairs);
 }
 
 // Slot ranges are only fully written when the pass fit its capacity; an overflowed pass (reported
