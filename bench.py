@@ -70,12 +70,12 @@ KERNEL_SOURCES = {
 }
 MEASURED_TRAFFIC = {
     # relight, 100 cameras: one full-size launch captured
-    ("relight", "cuda-core"): {"bytes_per_scene": 2141210112 + 288054784, "source_sha": "adcbffaec13b5c45"},
+    ("relight", "cuda-core"): {"bytes_per_scene": 2141550080 + 288479744, "source_sha": "6a638ba3bc449478"},
     # features: a 10-camera launch captured and scaled by 150/10 cameras (the targets, the per-camera
     # tile lists and the per-camera accumulator re-streaming all grow with the camera count)
-    ("features", "tensor-core"): {"bytes_per_scene": 15 * (3270208768 + 1464393984), "source_sha": "d28554a1fadb6a1d"},
+    ("features", "tensor-core"): {"bytes_per_scene": 15 * (3269992960 + 1474306816), "source_sha": "20d0fdd2229ede4b"},
     # segmentation masks: a 4-camera launch captured and scaled by 200/4 cameras (as above)
-    ("segmentation", "tensor-core"): {"bytes_per_scene": 50 * (1783149568 + 503274240), "source_sha": "d28554a1fadb6a1d"},
+    ("segmentation", "tensor-core"): {"bytes_per_scene": 50 * (1781662976 + 502753280), "source_sha": "20d0fdd2229ede4b"},
 }
 
 
