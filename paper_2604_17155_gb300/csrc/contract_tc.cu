@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256) k_tc_selftest(const uint16_t* __restrict_
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   if (threadIdx.x == 0) issue_batch<NB, MG>(smem_u32(A_s), smem_u32(B_s), tmem, idesc_f16(MG, NB, BF16), mbar);
-  const bool ok = mbar_wait_bounded(mbar, 0);
+  const bool ok = __all_sync(0xFFFFFFFFu, mbar_wait_bounded(mbar, 0));  // warp-uniform for tcgen05.ld
   if (!ok && (threadIdx.x & 31) == 0) atomicOr(&status->flags, kFlagTimeout);
   tc_fence_after();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -471,7 +471,8 @@ __global__ void __launch_bounds__(256, tc_ctas_per_sm<KT, MG>()) k_blend_accumul
     if (next < c.len)
       next_id = stage_tc(list, c.b + next, (int)min((uint32_t)MG, c.len - next), rec_cam, n, c.ox, c.oy, s_geo, s_aux,
                          g_own, stager, need_id);
-    const bool ok = mbar_wait_bounded(mbar, phase, wait_limit_ns);
+    // warp-uniform: the epilogue's tcgen05.ld needs whole warps
+    const bool ok = __all_sync(0xFFFFFFFFu, mbar_wait_bounded(mbar, phase, wait_limit_ns));
     phase ^= 1u;
     tc_fence_after();
     if (ok) {
