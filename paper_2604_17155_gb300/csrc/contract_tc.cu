@@ -209,11 +209,13 @@ __device__ __forceinline__ uint32_t stage_tc(const unsigned long long* list, uin
   if (g >= 0 && g < nb && (writer || need_id)) {
     id = min((uint32_t)list[first + g], (uint32_t)(n - 1));
     if (writer) {
+      // aux = (C, opacity, the slot's row offset in W, packed half-sizes): the walk's step needs no
+      // fast-reject threshold (blend_alpha_noreject), so the third value carries g * 128 +
+      // (g % 8) * 16, the Gaussian's part of its weights' swizzled address
       const ProjRec r = rec_cam[id];
-      float4 geo, aux;
-      stage_record(r, ox, oy, geo, aux);
-      s_geo[g] = geo;
-      s_aux[g] = aux;
+      s_geo[g] = stage_geo(r, ox, oy);
+      s_aux[g] = make_float4(-kHalfLog2e * r.par.z, r.par.w, __uint_as_float((uint32_t)((g << 7) | ((g & 7) << 4))),
+                             r.box.w);
     }
   }
   return id;
@@ -446,14 +448,16 @@ __global__ void __launch_bounds__(256, tc_ctas_per_sm<KT, MG>()) k_blend_accumul
           const bool has2 = bits != 0;  // warp-uniform
           const int g2 = has2 ? q * 32 + __ffs(bits) - 1 : g1;
           bits &= bits - 1;
-          const StepAlpha a1 = blend_alpha(s_geo[g1], s_aux[g1], c.pxf, c.pyf);
-          StepAlpha a2 = blend_alpha(s_geo[g2], s_aux[g2], c.pxf, c.pyf);
+          const float4 aux1 = s_aux[g1], aux2 = s_aux[g2];
+          const StepAlpha a1 = blend_alpha_noreject(s_geo[g1], aux1, c.pxf, c.pyf);
+          StepAlpha a2 = blend_alpha_noreject(s_geo[g2], aux2, c.pxf, c.pyf);
           a2.ok = a2.ok && has2;
           // T carries the factor 2^14 of W, so the weights come out scaled
           const float w1 = blend_take<false, kWScaleExp>(a1, T, done, npairs);
           const float w2 = blend_take<true, kWScaleExp>(a2, T, done, npairs);
-          *reinterpret_cast<uint16_t*>(a_pix + (g1 << 7) + (((g1 << 4) ^ a_chunk) & 0x70)) = half_bits(w1);
-          if (has2) *reinterpret_cast<uint16_t*>(a_pix + (g2 << 7) + (((g2 << 4) ^ a_chunk) & 0x70)) = half_bits(w2);
+          // the staged row offset XOR this pixel's chunk: kmajor_sw128(g, p, MG) - (a_pix - A_s)
+          *reinterpret_cast<uint16_t*>(a_pix + (__float_as_uint(aux1.z) ^ a_chunk)) = half_bits(w1);
+          if (has2) *reinterpret_cast<uint16_t*>(a_pix + (__float_as_uint(aux2.z) ^ a_chunk)) = half_bits(w2);
         }
       }
     }

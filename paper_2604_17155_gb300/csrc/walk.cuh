@@ -185,6 +185,18 @@ __device__ __forceinline__ StepAlpha blend_alpha(const float4 geo, const float4 
   const float alpha = fminf(kAlphaMax, __fmul_rn(aux.y, ex2_approx(E)));
   return {alpha, E >= aux.z && alpha >= kAlphaMin};
 }
+// blend_alpha without the fast reject, for walks that compute alpha for every step anyway: the
+// reject only ever drops steps whose alpha is below 1/255 (E < E_thr implies o 2^E < 1/255 by its
+// margin), so alpha >= 1/255 alone takes the same decisions. Alpha is clamped by a select, which
+// keeps a NaN product NaN so that it fails the test, as it failed the reject. aux.z is not read.
+__device__ __forceinline__ StepAlpha blend_alpha_noreject(const float4 geo, const float4 aux, float pxf, float pyf) {
+  const float dx = __fsub_rn(pxf, geo.x), dy = __fsub_rn(pyf, geo.y);
+  const float E = __fmaf_rn(__fmaf_rn(geo.z, dx, __fmul_rn(geo.w, dy)), dx, __fmul_rn(__fmul_rn(aux.x, dy), dy));
+  const float oe = __fmul_rn(aux.y, ex2_approx(E));
+  const float alpha = oe > kAlphaMax ? kAlphaMax : oe;
+  return {alpha, alpha >= kAlphaMin};
+}
+
 template <bool LIVE = false, int TEXP = 0>
 __device__ __forceinline__ float blend_take(const StepAlpha a, float& T, bool& done, uint32_t& npairs) {
   constexpr float kTMinScaled = kTMin * (float)(1 << TEXP);
@@ -210,13 +222,18 @@ __device__ __forceinline__ float blend_weight(const float4 geo, const float4 aux
 // combined there, where the result is small and float32 holds it closely. The fast-reject
 // threshold is 2 ln(255 o) with a relative margin of 1e-4 (and 1e-4 absolute), beyond which
 // alpha < 1/255 holds by more than the float32 error of alpha.
+// The staged geometry of one record: the tile-relative mean and the scaled conic (A, Bc).
+__device__ __forceinline__ float4 stage_geo(const ProjRec& r, float ox, float oy) {
+  const float2 lo = unpack_half2(r.box.z);
+  return make_float4(__fadd_rn(__fsub_rn(r.box.x, ox), __fmul_rn(lo.x, kMeanLoScaleInv)),
+                     __fadd_rn(__fsub_rn(r.box.y, oy), __fmul_rn(lo.y, kMeanLoScaleInv)), -kHalfLog2e * r.par.x,
+                     -2.0f * kHalfLog2e * r.par.y);
+}
+
 // The staged (geo, aux) of one record; aux.w carries the record's packed support half-sizes.
 __device__ __forceinline__ void stage_record(const ProjRec& r, float ox, float oy, float4& geo, float4& aux) {
-  const float2 lo = unpack_half2(r.box.z);
   const float qthr = __fmaf_rn(2.0f * logf(255.0f * r.par.w), 1.0001f, 1e-4f);
-  geo = make_float4(__fadd_rn(__fsub_rn(r.box.x, ox), __fmul_rn(lo.x, kMeanLoScaleInv)),
-                    __fadd_rn(__fsub_rn(r.box.y, oy), __fmul_rn(lo.y, kMeanLoScaleInv)), -kHalfLog2e * r.par.x,
-                    -2.0f * kHalfLog2e * r.par.y);
+  geo = stage_geo(r, ox, oy);
   aux = make_float4(-kHalfLog2e * r.par.z, r.par.w, -kHalfLog2e * qthr, r.box.w);
 }
 
