@@ -73,9 +73,9 @@ MEASURED_TRAFFIC = {
     ("relight", "cuda-core"): {"bytes_per_scene": 2141550080 + 288479744, "source_sha": "6a638ba3bc449478"},
     # features: a 10-camera launch captured and scaled by 150/10 cameras (the targets, the per-camera
     # tile lists and the per-camera accumulator re-streaming all grow with the camera count)
-    ("features", "tensor-core"): {"bytes_per_scene": 15 * (3270337280 + 1473545728), "source_sha": "17107391b7e67f54"},
+    ("features", "tensor-core"): {"bytes_per_scene": 15 * (3270310656 + 1473606912), "source_sha": "912af52a3bb4b57b"},
     # segmentation masks: a 4-camera launch captured and scaled by 200/4 cameras (as above)
-    ("segmentation", "tensor-core"): {"bytes_per_scene": 50 * (1781001472 + 501828864), "source_sha": "17107391b7e67f54"},
+    ("segmentation", "tensor-core"): {"bytes_per_scene": 50 * (1781086720 + 501826560), "source_sha": "912af52a3bb4b57b"},
 }
 
 
