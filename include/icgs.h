@@ -65,7 +65,10 @@ typedef enum {
   ICGS_ERR_CAPACITY = -4,             /* more (Gaussian, tile) instances than the workspace was sized
                                          for; icgs_last_required_instances() gives the count to pass
                                          as icgs_options.instance_capacity */
-  ICGS_ERR_UNSUPPORTED = -5,          /* valid request this build does not implement */
+  ICGS_ERR_UNSUPPORTED = -5,          /* valid request this build does not implement; also reported
+                                         after the work when the tensor-core walk found its dynamic
+                                         shared memory base not 128-byte aligned (that walk then did
+                                         nothing; results are unspecified) */
   ICGS_ERR_DEVICE_TIMEOUT = -6,       /* a bounded wait inside a kernel gave up (the kernel freed its
                                          resources and returned; results are unspecified) */
   ICGS_ERR_NONFINITE_INPUT = -7       /* a target value that a walk read (a pixel of a tile that some
