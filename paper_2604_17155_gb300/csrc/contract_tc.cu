@@ -2,21 +2,23 @@
 // 5th-generation tensor cores (tcgen05), for 16-bit targets with 16..64 channels.
 //
 // Per tile and batch of MG = 64 Gaussians (the MMA's M; 64 rather than 128 halves the weight
-// operand, so that 3-4 CTAs fit on an SM), the S terms of Eq. 6 summed over the tile's 256 pixels
+// operand, so that 3-5 CTAs fit on an SM), the S terms of Eq. 6 summed over the tile's 256 pixels
 // form a dense product
 //     D[g][n] = sum_p W[g][p] * B[n][p],   W[g][p] = alpha T of Gaussian g at pixel p (Eq. 4),
 // with B's rows 0..KT-1 the tile's target channels and the rows after them all ones, so that the same
-// product also yields V = sum_p W[g][p] (Eq. 5). The threads evaluate W exactly like the CUDA-core
-// walk (walk.cuh) and store it as FP16 into a K-major, 128-byte-swizzled shared-memory operand; the
-// tile's targets (BF16 or FP16) are transposed once into B as FP16. Both operands are scaled by
-// powers of two -- W by 2^14, the targets so that the tile's largest magnitude lands in
-// [2^14, 2^15) -- which makes every BF16 target exact in FP16, keeps small weights out of FP16's
-// subnormal range, and is undone exactly in the epilogue. One thread issues 16
-// tcgen05.mma (kind::f16, M=MG, N=KT+8, K=16, FP32 accumulation in TMEM) and commits them to an
-// mbarrier; while they run, the next batch's Gaussians are staged in a second buffer; the warps then
-// read D back with tcgen05.ld (one Gaussian per thread, the chunks split between warps w and w+4)
-// and add (V, S_0..S_{KT-1}) to the accumulator with float4 atomics -- one atomic group per
-// (Gaussian, tile). A batch costs two CTA barriers.
+// product also yields V = sum_p W[g][p] (Eq. 5). The threads evaluate W with the same decisions as
+// the CUDA-core walks (walk.cuh: branch-free, two hits a step) and store it as FP16 into a K-major,
+// 128-byte-swizzled shared-memory operand; the tile's targets (BF16 or FP16) are transposed once
+// into B as FP16. Both operands are scaled by powers of two -- W by 2^14 (the walk carries T scaled
+// so), the targets so that the tile's largest magnitude lands in [2^14, 2^15) -- which makes every
+// BF16 target exact in FP16, keeps small weights out of FP16's subnormal range, and is undone exactly
+// in the epilogue. One thread issues 16 tcgen05.mma (kind::f16, M=MG, N=KT+8, K=16, FP32
+// accumulation in TMEM) and commits them to an mbarrier; while they run, the next batch's Gaussians
+// are staged (the geometry into the buffer the walk has finished with, each index into the register
+// of the thread that adds its row); the warps then read D back with tcgen05.ld (one Gaussian per
+// thread, the chunks split between warps w and w+4) and add (V, S_0..S_{KT-1}) to the accumulator
+// with float4 atomics -- one atomic group per (Gaussian, tile). A batch costs two CTA barriers. At 16
+// channels the whole layout takes 44 KiB (five CTAs per SM): see b16_offset and tc_smem.
 //
 // Every wait on the mbarrier is bounded in time (1 s by %globaltimer): past the limit the kernel
 // sets kFlagTimeout in the status block (reported as ICGS_ERR_DEVICE_TIMEOUT), waits once more
