@@ -65,7 +65,7 @@ typedef enum {
   ICGS_ERR_CAPACITY = -4,             /* more (Gaussian, tile) instances than the workspace was sized
                                          for; icgs_last_required_instances() gives the count to pass
                                          as icgs_options.instance_capacity */
-  ICGS_ERR_UNSUPPORTED = -5,          /* valid request this build does not implement; also reported
+  ICGS_ERR_UNSUPPORTED = -5,          /* valid request the library does not implement; also reported
                                          after the work when the tensor-core walk found its dynamic
                                          shared memory base not 128-byte aligned (that walk then did
                                          nothing; results are unspecified) */
